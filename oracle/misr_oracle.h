@@ -1,0 +1,88 @@
+/*
+ * FP64 CPU oracle for the SCG solve of the multi-image super-resolution (MISR) objective.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg load this library.  It shares no code with the CUDA library.
+ *
+ * Problem (Sec. 3.1):
+ *   image formation   y_k = A_k x + noise,  A_k = D B M_k             (Eq. 1)
+ *   data term         sum_k || A_k x - y_k ||_2^2                      (Eq. 6)
+ *   prior (BTV)       sum_d gamma(d) || x - S_d x ||_1,
+ *                     d = (dx, dy), dx, dy in [0, w-1], gamma = alpha^(dx+dy)   (Eq. 8)
+ *   objective         J(x) = data + lambda * prior                     (Eq. 9)
+ *   solver            Moller's scaled conjugate gradient (Sec. 3.1, Algorithm 1, Table 1)
+ *
+ * Readings where the paper is silent (each is stated where it is used in the .c file):
+ *   M_k  translation by the integer HR shift t_k = f * s_k (s_k in LR px), x zero outside
+ *   B    convolution with the PSF h (normalised to sum 1), zero outside the HR grid
+ *   D    sampling at HR position (f i, f j)
+ *   |.|  in the BTV term is smoothed as psi(t) = sqrt(t^2 + eps^2) - eps  (eps = 0: |t|)
+ *   pairs (q, q + d) enter the BTV sum only when both pixels lie inside the grid
+ *
+ * Parity pins: tests/test_oracle_pins.py.  Every function here is pinned by at least one
+ * check that does not call the oracle twice: a dense D*B*M product built from the textbook
+ * matrices, closed-form BTV values, central finite differences, exact recovery, a dense
+ * normal-equation solve and conjugate-gradient identities.
+ */
+#ifndef MISR_ORACLE_H
+#define MISR_ORACLE_H
+
+#define ORC_MAXK 64
+#define ORC_MAXPSF 15
+
+enum { ORC_REG_BTV = 0, ORC_REG_TIKHONOV = 1 };
+enum { ORC_HV_EXACT = 0, ORC_HV_FD = 1 };
+
+typedef struct {
+    int h, w;                 /* LR frame size (rows, cols) */
+    int K, f;                 /* number of frames, magnification factor */
+    int ty[ORC_MAXK];         /* integer HR shift of frame k, rows */
+    int tx[ORC_MAXK];         /* integer HR shift of frame k, cols */
+    int psf_size;             /* odd */
+    double psf[ORC_MAXPSF * ORC_MAXPSF];  /* row-major, normalised to sum 1 */
+    double lambda;            /* regulariser weight */
+    double btv_alpha;         /* spatial decay alpha of gamma(d) */
+    int btv_w;                /* BTV window w */
+    double eps;               /* Charbonnier smoothing of |.| */
+    int reg;                  /* ORC_REG_BTV or ORC_REG_TIKHONOV */
+} orc_problem;
+
+/* one row of the SCG trace per iteration (failed iterations included) */
+typedef struct {
+    double E;        /* J(x_k) before the step */
+    double J_trial;  /* J(x_k + alpha_k p_k) */
+    double alpha, delta, mu;   /* step, scaled curvature, p.r */
+    double lam;      /* Moller's lambda after the iteration's updates */
+    double Delta;    /* comparison parameter */
+    double pn2;      /* |p_k|^2 */
+    double rn2;      /* |r|^2 after the iteration */
+    double accept;   /* 1 accepted, 0 rejected */
+} orc_trace_row;
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+int orc_init(orc_problem *P, int h, int w, int K, int f, const double *shifts_lr,
+             const double *psf, int psf_size, double lambda, double btv_alpha, int btv_w,
+             double eps, int reg);
+int orc_threads(void);
+void orc_forward(const orc_problem *P, int k, const double *x, double *out);
+void orc_adjoint(const orc_problem *P, int k, const double *e, double *out);
+double orc_reg_value(const orc_problem *P, const double *x);
+void orc_reg_grad(const orc_problem *P, const double *x, double *g);
+void orc_reg_hessvec(const orc_problem *P, const double *x, const double *p, double *out);
+double orc_reg_curvature(const orc_problem *P, const double *x, const double *p);
+double orc_objective(const orc_problem *P, const double *x, const double *y);
+double orc_gradient(const orc_problem *P, const double *x, const double *y, double *g);
+void orc_hessvec(const orc_problem *P, const double *x, const double *p, double *out);
+double orc_curvature(const orc_problem *P, const double *x, const double *p);
+void orc_shift_add(const orc_problem *P, const double *y, double *x0);
+void orc_log_convert(const unsigned short *counts, long n, double flat_field, double *y);
+int orc_scg(const orc_problem *P, const double *y, const double *x0, int iters, int hv_mode,
+            double *x_out, orc_trace_row *trace);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,61 @@
+"""Textbook dense matrices D, B, M_k of the image-formation model y_k = D B M_k x (Eq. 1).
+
+Each factor is built on its own, entry by entry, from its definition, and multiplied with
+numpy.  Used only to pin the oracle's loop implementation on tiny grids.
+"""
+import numpy as np
+
+
+def idx(u, v, W):
+    return u * W + v
+
+
+def decimation(h, w, f):
+    """D: (h*w) x (H*W), D[(i,j), (f i, f j)] = 1."""
+    H, W = f * h, f * w
+    D = np.zeros((h * w, H * W))
+    for i in range(h):
+        for j in range(w):
+            D[i * w + j, idx(f * i, f * j, W)] = 1.0
+    return D
+
+
+def blur(H, W, psf):
+    """B: convolution with the PSF, zero outside the grid:
+    (B z)(u, v) = sum_{a,b} h(a, b) z(u - a, v - b)."""
+    S = psf.shape[0]
+    R = S // 2
+    B = np.zeros((H * W, H * W))
+    for u in range(H):
+        for v in range(W):
+            for a in range(-R, R + 1):
+                for b in range(-R, R + 1):
+                    uu, vv = u - a, v - b
+                    if 0 <= uu < H and 0 <= vv < W:
+                        B[idx(u, v, W), idx(uu, vv, W)] += psf[a + R, b + R]
+    return B
+
+
+def motion(H, W, ty, tx):
+    """M_k: integer translation, (M x)(u, v) = x(u + ty, v + tx), zero outside the grid."""
+    M = np.zeros((H * W, H * W))
+    for u in range(H):
+        for v in range(W):
+            uu, vv = u + ty, v + tx
+            if 0 <= uu < H and 0 <= vv < W:
+                M[idx(u, v, W), idx(uu, vv, W)] = 1.0
+    return M
+
+
+def system_matrices(h, w, f, shifts_lr, psf):
+    """A_k = D B M_k for every frame; psf is normalised to sum 1 here."""
+    H, W = f * h, f * w
+    psf = np.asarray(psf, dtype=np.float64)
+    psf = psf / psf.sum()
+    D = decimation(h, w, f)
+    B = blur(H, W, psf)
+    out = []
+    for dx, dy in shifts_lr:
+        ty, tx = int(round(f * dy)), int(round(f * dx))
+        out.append(D @ B @ motion(H, W, ty, tx))
+    return out

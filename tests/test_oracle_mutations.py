@@ -1,0 +1,49 @@
+"""Mutation check of the oracle pins: plant plausible mistakes in copies of the oracle's C
+source (a flipped convolution, a dropped mask, a wrong sign, factor, weight or update) and
+check that the pin suite fails for every one of them.  The mistakes are planted on the CPU,
+in the oracle only."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "misr_oracle.c")
+
+MUTANTS = {
+    "convolution_flipped": ("int bu = f * i - a;", "int bu = f * i + a;"),
+    "blur_padding_dropped": ("if (bu < 0 || bu >= H) continue;", "/* row padding dropped */"),
+    "shift_sign": ("int u = bu + ty;", "int u = bu - ty;"),
+    "gamma_exponent": ("return pow(P->btv_alpha, dx + dy);", "return pow(P->btv_alpha, dx > dy ? dx : dy);"),
+    "btv_window_short": ("for (int dy = 0; dy < P->btv_w; ++dy) {\n        for (int dx = 0; dx < P->btv_w; ++dx) {\n            if (dx == 0 && dy == 0) continue;\n#pragma omp parallel for schedule(static)\n            for (int u = 0; u < H; ++u) {\n                double s = 0;\n                if (u + dy < H)",
+                         "for (int dy = 0; dy < P->btv_w - 1; ++dy) {\n        for (int dx = 0; dx < P->btv_w; ++dx) {\n            if (dx == 0 && dy == 0) continue;\n#pragma omp parallel for schedule(static)\n            for (int u = 0; u < H; ++u) {\n                double s = 0;\n                if (u + dy < H)"),
+    "dpsi_sign": ("if (eps > 0) return t / sqrt(t * t + eps * eps);", "if (eps > 0) return -t / sqrt(t * t + eps * eps);"),
+    "d2psi_power": ("return eps * eps / (s * sqrt(s));", "return eps * eps / s;"),
+    "grad_factor_2_dropped": ("for (long i = 0; i < n; ++i) g[i] += 2.0 * t[i];", "for (long i = 0; i < n; ++i) g[i] += t[i];"),
+    "hessvec_factor": ("for (long i = 0; i < n; ++i) out[i] += 2.0 * t[i];", "for (long i = 0; i < n; ++i) out[i] += t[i];"),
+    "beta_fletcher_reeves": ("const double beta = (rr_new - rr_cross) / mu;", "const double beta = rr_new / dot(r, r, n);"),
+    "lambda_not_reduced": ("if (Delta >= 0.75) lam = lam / 4.0;", "if (Delta >= 0.75) lam = lam / 2.0;"),
+    "delta_not_scaled": ("delta += (lam - lam_bar) * pn2;", "delta += 0.0 * (lam - lam_bar) * pn2;"),
+    "shift_add_no_average": ("x0[i] = cnt[i] > 0 ? x0[i] / cnt[i] : 0.0;", "x0[i] = x0[i];"),
+    "log_convert_no_clamp": ("double c = counts[i] < 1 ? 1.0 : (double)counts[i];", "double c = (double)counts[i] + 1e-300;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    mut = src.replace(old, new, 1)
+    cfile = tmp_path / "misr_oracle.c"
+    cfile.write_text(mut)
+    (tmp_path / "misr_oracle.h").write_text(open(os.path.join(ROOT, "oracle", "misr_oracle.h")).read())
+    lib = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", str(lib), str(cfile), "-lm"],
+                   check=True, capture_output=True)
+    env = dict(os.environ, MISR_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pin suite"
