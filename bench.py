@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: SR projections per second for the detector-scale workload.
+
+Workload: 4 LR frames of 2048 x 2048 float32 with half-pixel detector shifts, factor 2 ->
+4096 x 4096 HR, 5x5 Gaussian PSF (sigma 0.5 HR px), BTV prior lambda 0.01, alpha 0.4, w 3,
+eps 1e-3, 100 SCG iterations from multi-image interpolation.  One step = one full SR solve of
+one projection (prepare, initial gradient, 100 fused SCG passes, output).  Synthetic data:
+a seeded phantom, frames made with the library's forward operator plus Gaussian noise.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl misr|reference]
+
+Under torchrun (N > 1) every rank solves its own projections (independent problems, no
+collective on the data path); rank 0 prints one JSON line with the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gen  # noqa: E402
+
+METRIC = "SR projections/s (2048^2->4096^2, 100 SCG it)"
+UNIT = "projections/s"
+WORKLOADS = {
+    "detector": dict(h=2048, w=2048, f=2, iters=100, seed=gen.CONFIG_SEEDS["detector"],
+                     desc="4 x 2048^2 fp32 frames -> 4096^2 HR, f=2, half-pixel shifts, 5x5 Gaussian PSF "
+                          "sigma 0.5, lambda 0.01, BTV alpha 0.4 w 3 eps 1e-3, 100 SCG iterations"),
+    "tiny": dict(h=64, w=64, f=2, iters=50, seed=gen.CONFIG_SEEDS["tiny"],
+                 desc="4 x 64^2 fp32 frames -> 128^2 HR, f=2, 50 SCG iterations"),
+}
+PASS_BYTES_PER_PX = 28  # fused pass: read x, r, p_old, Y; write x', r', p (float32)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def load_traffic(kernel_tag):
+    """Per-launch DRAM bytes of the fused pass from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "scg_pass_traffic.json")) as fh:
+            d = json.load(fh)
+        if d.get("kernel_source_sha1") == kernel_tag:
+            return float(d["dram_bytes_per_launch_4096"])
+    except Exception:
+        pass
+    return None
+
+
+def kernel_source_tag():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("misr_device.cuh", "misr_api.cu"):
+        with open(os.path.join(ROOT, "paper_2108_04315_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu_index), "-lms", "100"], stdout=self.tmp,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, flags in rows for i, v in enumerate(flags) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(plan, wl, device):
+    """Phantom and frames y = A x_true + noise, made on the device with the library's forward op."""
+    import torch
+    H, W = wl["f"] * wl["h"], wl["f"] * wl["w"]
+    xt = torch.from_numpy(gen.phantom(H, W, wl["seed"]).astype(np.float32)).to(device)
+    y = plan.forward(xt)
+    noise = torch.from_numpy(gen.gaussian_noise((4, wl["h"], wl["w"]), 0.01, wl["seed"] + 1).astype(np.float32))
+    y += noise.to(device)
+    torch.cuda.synchronize()
+    return xt, y
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle on the host cores: initial gradient plus 2 SCG iterations at full size,
+    extrapolated to the workload's iteration count."""
+    from oracle import oracle
+    P = oracle.Problem(wl["h"], wl["w"], wl["f"], gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), lam=0.01)
+    xt = gen.phantom(P.H, P.W, wl["seed"])
+    y = P.forward_all(xt) + gen.gaussian_noise((4, wl["h"], wl["w"]), 0.01, wl["seed"] + 1)
+    t = time.perf_counter()
+    x0 = P.shift_add(y)
+    P.scg(y, x0, 0)
+    t0 = time.perf_counter() - t
+    t = time.perf_counter()
+    x0 = P.shift_add(y)
+    P.scg(y, x0, 2)
+    t2 = time.perf_counter() - t
+    t_iter = max((t2 - t0) / 2.0, 1e-9)
+    per_proj = t0 + wl["iters"] * t_iter
+    return {"value": 1.0 / per_proj, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, full-size problem: init {t0:.2f} s + 2 SCG iterations "
+                      f"({t_iter:.2f} s each), extrapolated to {wl['iters']} iterations"}
+
+
+def run_reference(args, wl):
+    """Reference arm: the FP64 oracle as it stands, on the host cores."""
+    from oracle import oracle
+    P = oracle.Problem(wl["h"], wl["w"], wl["f"], gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), lam=0.01)
+    xt = gen.phantom(P.H, P.W, wl["seed"])
+    y = P.forward_all(xt) + gen.gaussian_noise((4, wl["h"], wl["w"]), 0.01, wl["seed"] + 1)
+    x0 = P.shift_add(y)
+
+    def init_time():
+        t = time.perf_counter()
+        P.scg(y, P.shift_add(y), 0)
+        return time.perf_counter() - t
+
+    def step_time():
+        t = time.perf_counter()
+        P.scg(y, P.shift_add(y), 1)
+        return time.perf_counter() - t
+
+    for _ in range(max(0, min(args.warmup, 1))):
+        step_time()
+    t_init = init_time()
+    steps = [step_time() for _ in range(args.steps)]
+    t_iter = max(statistics.median(steps) - t_init, 1e-9)
+    per_proj = t_init + wl["iters"] * t_iter
+    value = 1.0 / per_proj
+    sample = (f"FP64 oracle, full-size problem; each step = init + 1 SCG iteration "
+              f"(median {statistics.median(steps):.2f} s, init {t_init:.2f} s), extrapolated to {wl['iters']} iterations")
+    del x0
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_proj * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": wl["desc"], "lr": [wl["h"], wl["w"]], "K": 4, "factor": wl["f"], "iters": wl["iters"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="misr", choices=["misr", "reference"])
+    ap.add_argument("--workload", default="detector", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, wl)), flush=True)
+        return
+
+    import torch
+    from paper_2108_04315_b300.binding import Plan
+
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    stream = torch.cuda.current_stream()
+    H, W = wl["f"] * wl["h"], wl["f"] * wl["w"]
+    shifts, psf = gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)
+    plan = Plan(wl["h"], wl["w"], wl["f"], shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3,
+                iters=wl["iters"])
+    plan0 = Plan(wl["h"], wl["w"], wl["f"], shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, iters=0)
+    xt, y = make_inputs(plan, wl, device)
+    x = torch.empty((H, W), dtype=torch.float32, device=device)
+
+    for _ in range(max(args.warmup, 3)):
+        plan.solve(y, x, stats=False)
+        plan0.solve(y, x, stats=False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # timed region: K full solves, inputs resident in HBM (working set 470 MB > 126 MB L2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.solve(y, x, stats=False)
+        ev1.record(stream)
+        ev1.synchronize()
+        barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    # per-pass time: the same solves with 0 SCG iterations, on the same stream
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(args.steps):
+        plan0.solve(y, x, stats=False)
+    ev3.record(stream)
+    ev3.synchronize()
+    ms0 = ev2.elapsed_time(ev3)
+    pass_ms = max((ms_total - ms0) / args.steps / wl["iters"], 1e-9)
+    st = plan.solve(y, x, stats=True)[1]
+
+    if dist is not None:
+        t = torch.tensor([ms_total], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * args.steps / (ms_total / 1e3)
+
+    # end to end through the C ABI with host buffers (page-locked): H2D frames, D2H image
+    y_host = y.cpu().pin_memory()
+    x_host = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    yh, xh = y_host.numpy(), x_host.numpy()
+    plan.solve_host(yh, xh)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        plan.solve_host(yh, xh)
+    e2e_s = time.perf_counter() - t
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 4),
+           "d2h_bytes_per_step": int(H * W * 4)}
+
+    peak, peak_kind = load_peaks()
+    achieved = PASS_BYTES_PER_PX * H * W / (pass_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "lr": [wl["h"], wl["w"]], "K": 4, "factor": wl["f"],
+                   "iters": wl["iters"], "hr_pixels": H * W,
+                   "l2": "no flush: per-solve working set 7 HR float32 images = %d MB > 126 MB L2"
+                         % (7 * H * W * 4 // 2**20),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": load_traffic(kernel_source_tag()),
+                     "kernel": "scg_pass_kernel<32,64,256>", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": PASS_BYTES_PER_PX * H * W,
+                     "ms_per_launch": pass_ms},
+        "e2e": e2e,
+        "gpu_launches": args.steps * (wl["iters"] + 3),
+        "clocks": clocks,
+        "solve": {"J_final": st["J_final"], "accepted": st["accepted"], "iters_done": st["iters_done"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.close()
+    plan0.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * misr.h -- C ABI of the B300 (sm_103a) multi-image super-resolution solver.
+ *
+ * The library solves, on one GPU, the MAP problem of Sec. 3.1 of the paper
+ *     min_x  J(x) = sum_k || D B M_k x - y_k ||_2^2 + lambda * sum_d gamma(d) || x - S_d x ||_1
+ * (Eq. 1 image formation, Eq. 6 data term, Eq. 8 BTV prior, Eq. 9 objective) with Moller's
+ * scaled conjugate gradient (Sec. 3.1, Algorithm 1, Table 1), for K low-resolution (LR)
+ * frames taken with known subpixel detector shifts (Sec. 3.2).
+ *
+ * Conventions for every call:
+ *  - Images are row-major, densely packed.  An LR frame is lr_h x lr_w; the K frames of one
+ *    projection are stored back to back (K * lr_h * lr_w elements).  The HR image is
+ *    (factor * lr_h) x (factor * lr_w) float32.
+ *  - "_dev" pointers are CUDA device pointers on the device that was current when the plan
+ *    was created; "_host" pointers are host memory.  The caller owns every buffer it passes;
+ *    the library never frees or retains them past the call (asynchronous calls read them
+ *    until the stream reaches that point).
+ *  - misr_stream_t is a cudaStream_t (0 = the legacy default stream).
+ *  - Every call returns a misr_status and never aborts; on failure misr_last_error() gives a
+ *    thread-local description.  A call that fails leaves the caller's buffers untouched
+ *    unless stated otherwise.
+ *  - One plan runs one solve at a time: its workspace holds a single SCG state.  Calls on the
+ *    same plan must be ordered (one stream, or synchronised).
+ */
+#ifndef MISR_H
+#define MISR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MISR_OK = 0,
+    MISR_EINVAL = 1,    /* invalid argument or descriptor */
+    MISR_ENOMEM = 2,    /* device or host allocation failed */
+    MISR_ECUDA = 3,     /* a CUDA runtime call failed */
+    MISR_EAGAIN = 4,    /* not ready yet / no free slot */
+    MISR_ETIMEOUT = 5,  /* a bounded wait ran out */
+    MISR_ENOTIMPL = 6   /* valid request this build does not support */
+} misr_status;
+
+/* element types of the LR frames and of the iterate */
+enum { MISR_F32 = 0, MISR_U16 = 1, MISR_BF16 = 2 };
+
+/* how the SCG start point x_1 is formed */
+enum {
+    MISR_X0_ZERO = 0,       /* x_1 = 0 */
+    MISR_X0_SHIFT_ADD = 1,  /* multi-image interpolation (Sec. 4.1.1): each LR sample placed
+                               at the HR pixel it was taken at, 0 where no sample falls */
+    MISR_X0_GIVEN = 2       /* x_1 = the caller's x buffer on entry */
+};
+
+/* Problem descriptor, copied by misr_plan_create (the pointers are read only during it). */
+typedef struct misr_desc {
+    int32_t lr_h, lr_w;      /* LR frame rows, columns (>= 1) */
+    int32_t K;               /* number of frames, 1 <= K <= factor^2 */
+    int32_t factor;          /* magnification f, 1 <= f <= 8; HR = f*lr_h x f*lr_w */
+    const float *shifts;     /* host, K pairs (dx, dy) in LR px; f*dx and f*dy must be integers
+                                in [0, f-1] and the K pairs distinct (one frame per HR phase) */
+    const float *psf;        /* host, psf_size^2 row-major PSF of B (Eq. 1); must be separable;
+                                normalised to sum 1 by the plan; B is a convolution with it */
+    int32_t psf_size;        /* odd, 1..5 */
+    double lambda;           /* regulariser weight lambda of Eq. 9 (>= 0) */
+    double btv_alpha;        /* decay alpha of gamma(d) = alpha^(dx+dy), Eq. 8 */
+    int32_t btv_w;           /* BTV window w of Eq. 8, 1..3 */
+    double eps;              /* > 0: |t| of Eq. 8 is smoothed as sqrt(t^2+eps^2) - eps */
+    int32_t iters;           /* SCG iterations, rejected ones included (Algorithm 1), 0..1e6 */
+    int32_t x0_mode;         /* MISR_X0_* */
+    int32_t in_dtype;        /* MISR_F32 frames, or MISR_U16 detector counts c converted on the
+                                device to line integrals y = ln(flat_field) - ln(max(c, 1)) */
+    float flat_field;        /* I0 for MISR_U16 (> 0) */
+    int32_t iterate_dtype;   /* MISR_F32 */
+} misr_desc;
+
+/* Solve summary.  J_final, rnorm2 are FP64 reductions computed on the device. */
+typedef struct misr_stats {
+    int32_t iters_done;      /* SCG iterations run (rejected ones included) */
+    int32_t accepted;        /* iterations whose step was accepted */
+    int32_t status;          /* misr_status of the solve */
+    int32_t reserved;
+    double J_final;          /* J(x) at the returned x */
+    double rnorm2;           /* |grad J(x)|^2 at the returned x */
+    double lambda_scg;       /* Moller's scale parameter at the end */
+} misr_stats;
+
+typedef struct misr_plan_s *misr_plan_t;
+typedef void *misr_stream_t;
+
+/* Number of float64 columns per row of misr_get_trace, in this order:
+ * E (J before the step), J_trial, alpha, delta, mu, lambda_scg, Delta, |p|^2, |r|^2, accept. */
+#define MISR_TRACE_COLS 10
+/* Number of float64 sums returned by misr_pass_probe, in this order:
+ * J_data(x'), J_data(x') - J_data(x), R_BTV(x') (Eq. 8, without lambda), |r'|^2, r'.r,
+ * p.r', |p|^2, r'.H(x')r', r'.H(x')p, p.H(x')p. */
+#define MISR_PASS_SUMS 10
+
+const char *misr_version(void);
+/* Thread-local text of the last failure of a call made by this thread ("" if none). */
+const char *misr_last_error(void);
+
+/* Validate the descriptor and build a plan on the current device: the separable PSF taps,
+ * the phase-to-frame table and the device workspace of one solve (7 HR float32 images plus
+ * O(tiles) partial sums), allocated here with cudaMalloc.  The plan stands for the paper's
+ * system matrices "computed once at the beginning of the CT acquisition and shared by all
+ * the rotation angles" (Sec. 3.2); no matrix is formed.
+ * Errors: MISR_EINVAL (descriptor), MISR_ENOMEM, MISR_ECUDA, MISR_ENOTIMPL. */
+misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out);
+
+/* Synchronise the plan's work and free its workspace.  NULL is accepted. */
+misr_status misr_plan_destroy(misr_plan_t plan);
+
+/* Device bytes the plan holds. */
+misr_status misr_plan_workspace_bytes(misr_plan_t plan, size_t *bytes);
+
+/* y_k = D B M_k x for every frame (Eq. 1 without noise): x_dev is the HR float32 image,
+ * y_dev receives K float32 frames.  Asynchronous on stream.  Used to synthesise
+ * acquisitions. */
+misr_status misr_forward(misr_plan_t plan, const float *x_dev, float *y_dev, misr_stream_t stream);
+
+/* Objective and gradient at x (Eq. 9 and its gradient 2 sum_k A_k^T (A_k x - y_k) +
+ * lambda grad R): y_dev holds the K frames (in_dtype), x_dev the HR image, g_dev receives
+ * grad J(x) (HR float32).  Blocking: *J_out (may be NULL) is valid on return. */
+misr_status misr_gradient(misr_plan_t plan, const void *y_dev, const float *x_dev, float *g_dev,
+                          double *J_out, misr_stream_t stream);
+
+/* One fused SCG pass on explicit inputs (the per-iteration work of Algorithm 1):
+ *   p' = r + beta * p_old,  x' = x + alpha * p',  r' = -grad J(x'),
+ * and the sums listed at MISR_PASS_SUMS, where H(x') is the exact Hessian of J at x'.
+ * All images are HR float32 device buffers; y_dev holds the K frames.  Blocking: sums
+ * (host, MISR_PASS_SUMS doubles) is valid on return.  Exposed so that each pass can be
+ * compared with an independent implementation. */
+misr_status misr_pass_probe(misr_plan_t plan, const void *y_dev, const float *x_dev,
+                            const float *r_dev, const float *p_old_dev, double alpha, double beta,
+                            float *x_out_dev, float *r_out_dev, float *p_out_dev, double *sums,
+                            misr_stream_t stream);
+
+/* Full SCG solve (Algorithm 1 on one GPU, desc.iters iterations, failed ones included).
+ * y_dev: K frames (in_dtype).  x_dev: HR float32 output (and the start point for
+ * MISR_X0_GIVEN).  Asynchronous on stream unless stats is non-NULL, in which case the call
+ * synchronises the stream and fills *stats. */
+misr_status misr_solve(misr_plan_t plan, const void *y_dev, float *x_dev, misr_stream_t stream,
+                       misr_stats *stats);
+
+/* misr_solve on host buffers: copies y_host to the device, solves, copies x back to x_host,
+ * all inside the call (blocking).  Page-locked host buffers give the fastest copies.  The
+ * plan allocates the device copies on first use. */
+misr_status misr_solve_host(misr_plan_t plan, const void *y_host, float *x_host, misr_stats *stats);
+
+/* Copy the per-iteration trace of the plan's last completed solve (MISR_TRACE_COLS doubles
+ * per iteration) into out (host, max_rows rows); *rows receives the number written.
+ * Synchronises with the plan's last solve. */
+misr_status misr_get_trace(misr_plan_t plan, double *out, int32_t max_rows, int32_t *rows);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MISR_H */

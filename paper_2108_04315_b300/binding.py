@@ -1,0 +1,246 @@
+"""ctypes binding of libmisr.so (the C ABI in include/misr.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.  The
+functions carry the C names; `Plan` wraps a plan for torch tensors (device memory and streams
+come from PyTorch).  Importing this module fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmisr.so")
+
+MISR_OK, MISR_EINVAL, MISR_ENOMEM, MISR_ECUDA, MISR_EAGAIN, MISR_ETIMEOUT, MISR_ENOTIMPL = range(7)
+MISR_F32, MISR_U16, MISR_BF16 = 0, 1, 2
+MISR_X0_ZERO, MISR_X0_SHIFT_ADD, MISR_X0_GIVEN = 0, 1, 2
+MISR_TRACE_COLS = 10
+MISR_PASS_SUMS = 10
+TRACE_FIELDS = ("E", "J_trial", "alpha", "delta", "mu", "lam", "Delta", "pn2", "rn2", "accept")
+PASS_SUM_FIELDS = ("J_data", "dJ_data", "R_btv", "rr", "rr_cross", "pr", "pp", "a", "b", "c")
+
+
+class misr_desc(C.Structure):
+    _fields_ = [
+        ("lr_h", C.c_int32), ("lr_w", C.c_int32), ("K", C.c_int32), ("factor", C.c_int32),
+        ("shifts", C.POINTER(C.c_float)), ("psf", C.POINTER(C.c_float)), ("psf_size", C.c_int32),
+        ("lambda_", C.c_double), ("btv_alpha", C.c_double), ("btv_w", C.c_int32),
+        ("eps", C.c_double), ("iters", C.c_int32), ("x0_mode", C.c_int32),
+        ("in_dtype", C.c_int32), ("flat_field", C.c_float), ("iterate_dtype", C.c_int32),
+    ]
+
+
+class misr_stats(C.Structure):
+    _fields_ = [
+        ("iters_done", C.c_int32), ("accepted", C.c_int32), ("status", C.c_int32),
+        ("reserved", C.c_int32), ("J_final", C.c_double), ("rnorm2", C.c_double),
+        ("lambda_scg", C.c_double),
+    ]
+
+
+class MisrError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = int(status)
+        super().__init__(f"{where} failed with status {status}: {misr_last_error()}")
+
+
+_lib = None
+VP = C.c_void_p
+DP = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libmisr.so (built in-tree by paper_2108_04315_b300/build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2108_04315_b300/build.py` "
+                              "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        L.misr_version.restype = C.c_char_p
+        L.misr_last_error.restype = C.c_char_p
+        L.misr_plan_create.argtypes = [C.POINTER(misr_desc), C.POINTER(VP)]
+        L.misr_plan_destroy.argtypes = [VP]
+        L.misr_plan_workspace_bytes.argtypes = [VP, C.POINTER(C.c_size_t)]
+        L.misr_forward.argtypes = [VP, VP, VP, VP]
+        L.misr_gradient.argtypes = [VP, VP, VP, VP, DP, VP]
+        L.misr_pass_probe.argtypes = [VP, VP, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, DP, VP]
+        L.misr_solve.argtypes = [VP, VP, VP, VP, C.POINTER(misr_stats)]
+        L.misr_solve_host.argtypes = [VP, VP, VP, C.POINTER(misr_stats)]
+        L.misr_get_trace.argtypes = [VP, DP, C.c_int32, C.POINTER(C.c_int32)]
+        for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_forward",
+                     "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_get_trace"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != MISR_OK:
+        raise MisrError(status, where)
+
+
+# ---------------------------------------------------------------- C names, thin wrappers
+def misr_version() -> str:
+    return lib().misr_version().decode()
+
+
+def misr_last_error() -> str:
+    return lib().misr_last_error().decode()
+
+
+def misr_plan_create(desc: misr_desc) -> int:
+    h = VP()
+    _check(lib().misr_plan_create(C.byref(desc), C.byref(h)), "misr_plan_create")
+    return h.value
+
+
+def misr_plan_destroy(plan: int) -> None:
+    _check(lib().misr_plan_destroy(VP(plan)), "misr_plan_destroy")
+
+
+def misr_plan_workspace_bytes(plan: int) -> int:
+    n = C.c_size_t()
+    _check(lib().misr_plan_workspace_bytes(VP(plan), C.byref(n)), "misr_plan_workspace_bytes")
+    return n.value
+
+
+def misr_forward(plan: int, x_dev: int, y_dev: int, stream: int = 0) -> None:
+    _check(lib().misr_forward(VP(plan), VP(x_dev), VP(y_dev), VP(stream)), "misr_forward")
+
+
+def misr_gradient(plan: int, y_dev: int, x_dev: int, g_dev: int, stream: int = 0) -> float:
+    J = C.c_double()
+    _check(lib().misr_gradient(VP(plan), VP(y_dev), VP(x_dev), VP(g_dev), C.byref(J), VP(stream)),
+           "misr_gradient")
+    return J.value
+
+
+def misr_pass_probe(plan, y_dev, x_dev, r_dev, p_old_dev, alpha, beta, x_out, r_out, p_out, stream=0):
+    sums = (C.c_double * MISR_PASS_SUMS)()
+    _check(lib().misr_pass_probe(VP(plan), VP(y_dev), VP(x_dev), VP(r_dev), VP(p_old_dev), float(alpha),
+                                 float(beta), VP(x_out), VP(r_out), VP(p_out), sums, VP(stream)),
+           "misr_pass_probe")
+    return dict(zip(PASS_SUM_FIELDS, list(sums)))
+
+
+def misr_solve(plan: int, y_dev: int, x_dev: int, stream: int = 0, want_stats: bool = True):
+    st = misr_stats()
+    _check(lib().misr_solve(VP(plan), VP(y_dev), VP(x_dev), VP(stream), C.byref(st) if want_stats else None),
+           "misr_solve")
+    return _stats_dict(st) if want_stats else None
+
+
+def misr_solve_host(plan: int, y_host: int, x_host: int):
+    st = misr_stats()
+    _check(lib().misr_solve_host(VP(plan), VP(y_host), VP(x_host), C.byref(st)), "misr_solve_host")
+    return _stats_dict(st)
+
+
+def misr_get_trace(plan: int, max_rows: int):
+    buf = np.zeros((max(1, max_rows), MISR_TRACE_COLS), dtype=np.float64)
+    rows = C.c_int32()
+    _check(lib().misr_get_trace(VP(plan), buf.ctypes.data_as(DP), int(max_rows), C.byref(rows)), "misr_get_trace")
+    buf = buf[: rows.value]
+    return {k: buf[:, i].copy() for i, k in enumerate(TRACE_FIELDS)}
+
+
+def _stats_dict(st: misr_stats):
+    return {"iters_done": st.iters_done, "accepted": st.accepted, "status": st.status,
+            "J_final": st.J_final, "rnorm2": st.rnorm2, "lambda_scg": st.lambda_scg}
+
+
+# ---------------------------------------------------------------- torch convenience layer
+def make_desc(lr_h, lr_w, factor, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, iters=100,
+              x0_mode=MISR_X0_SHIFT_ADD, in_dtype=MISR_F32, flat_field=40000.0, iterate_dtype=MISR_F32):
+    sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float32).reshape(-1))
+    ps = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
+    d = misr_desc()
+    d.lr_h, d.lr_w, d.K, d.factor = int(lr_h), int(lr_w), len(sh) // 2, int(factor)
+    d.shifts = sh.ctypes.data_as(C.POINTER(C.c_float))
+    d.psf = ps.ctypes.data_as(C.POINTER(C.c_float))
+    d.psf_size = int(ps.shape[0])
+    d.lambda_, d.btv_alpha, d.btv_w, d.eps = float(lam), float(btv_alpha), int(btv_w), float(eps)
+    d.iters, d.x0_mode, d.in_dtype = int(iters), int(x0_mode), int(in_dtype)
+    d.flat_field, d.iterate_dtype = float(flat_field), int(iterate_dtype)
+    d._keep = (sh, ps)  # keep the host arrays alive while the descriptor is used
+    return d
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A plan plus torch-tensor entry points.  Tensors must be contiguous CUDA tensors on the
+    plan's device: y (K, h, w) float32 or uint16-as-int16/uint16, x (H, W) float32."""
+
+    def __init__(self, lr_h, lr_w, factor, shifts, psf, **kw):
+        self.desc = make_desc(lr_h, lr_w, factor, shifts, psf, **kw)
+        self.h, self.w, self.f = int(lr_h), int(lr_w), int(factor)
+        self.K = self.desc.K
+        self.H, self.W = self.f * self.h, self.f * self.w
+        self.iters = self.desc.iters
+        self.handle = misr_plan_create(self.desc)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            misr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ptr(t, dtype=None):
+        assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+        if dtype is not None:
+            assert t.dtype == dtype, (t.dtype, dtype)
+        return int(t.data_ptr())
+
+    def workspace_bytes(self):
+        return misr_plan_workspace_bytes(self.handle)
+
+    def forward(self, x, y_out=None, stream=None):
+        import torch
+        if y_out is None:
+            y_out = torch.empty((self.K, self.h, self.w), dtype=torch.float32, device=x.device)
+        misr_forward(self.handle, self._ptr(x, torch.float32), self._ptr(y_out, torch.float32), _stream_handle(stream))
+        return y_out
+
+    def gradient(self, y, x, stream=None):
+        import torch
+        g = torch.empty_like(x)
+        J = misr_gradient(self.handle, self._ptr(y), self._ptr(x, torch.float32), self._ptr(g), _stream_handle(stream))
+        return J, g
+
+    def pass_probe(self, y, x, r, p_old, alpha, beta, stream=None):
+        import torch
+        xo, ro, po = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+        sums = misr_pass_probe(self.handle, self._ptr(y), self._ptr(x, torch.float32), self._ptr(r, torch.float32),
+                               self._ptr(p_old, torch.float32), alpha, beta, self._ptr(xo), self._ptr(ro),
+                               self._ptr(po), _stream_handle(stream))
+        return xo, ro, po, sums
+
+    def solve(self, y, x_out=None, stream=None, stats=True):
+        import torch
+        if x_out is None:
+            x_out = torch.empty((self.H, self.W), dtype=torch.float32, device=y.device)
+        st = misr_solve(self.handle, self._ptr(y), self._ptr(x_out, torch.float32), _stream_handle(stream), stats)
+        return x_out, st
+
+    def solve_host(self, y_host: np.ndarray, x_host: np.ndarray):
+        assert y_host.flags.c_contiguous and x_host.flags.c_contiguous and x_host.dtype == np.float32
+        return misr_solve_host(self.handle, y_host.ctypes.data, x_host.ctypes.data)
+
+    def trace(self):
+        return misr_get_trace(self.handle, self.iters)

@@ -1,0 +1,491 @@
+// C ABI of the sm_103a MISR solver (declared in include/misr.h): plans, workspace, CUDA-graph
+// replay of the SCG iteration, and the entry points.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "misr.h"
+#include "misr_device.cuh"
+
+using namespace misr;
+
+namespace {
+
+thread_local std::string g_err;
+
+misr_status fail(misr_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return fail(MISR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// the tile shape of the fused pass
+constexpr int TILE_H = 32, TILE_W = 64, PASS_NT = 256;
+using PassGeo = Geo<TILE_H, TILE_W>;
+// passes captured per CUDA graph replay
+constexpr int GRAPH_CHUNK = 50;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+
+misr_status get_encode_tiled() {
+    if (g_encode_tiled) return MISR_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(MISR_ECUDA, "cuTensorMapEncodeTiled unavailable: %s", cudaGetErrorString(e));
+    g_encode_tiled = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return MISR_OK;
+}
+
+// 2-D float32 tensor map over an H x W image with the given row pitch (floats); box of
+// box_w x box_h elements; out-of-bounds elements read as 0 or as NaN.
+misr_status make_map(CUtensorMap *m, float *base, int W, int H, int pitch, int box_w, int box_h, bool nan_fill) {
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA
+                                         : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MISR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MISR_OK;
+}
+
+}  // namespace
+
+struct misr_plan_s {
+    int device = 0;
+    misr_desc d{};
+    DevProblem hp{};              // host mirror of the device problem record
+    DevProblem *dprob = nullptr;  // device problem record
+    int2 *dtile = nullptr;        // tile map of the fused pass
+    char *ws = nullptr;           // one allocation for everything above and below
+    size_t ws_bytes = 0;
+    size_t n = 0, m_total = 0;    // HR pixels, LR samples of all frames
+    size_t n_pitched = 0;         // H * pitch
+    cudaStream_t cap = nullptr;   // private stream used for graph capture
+    cudaGraphExec_t chunk = nullptr;
+    int chunk_len = 0;
+    cudaEvent_t done_ev = nullptr;
+    bool solved = false;
+    ScgState *st_host = nullptr;  // page-locked copy of the state
+    void *io_y = nullptr;         // device buffers of misr_solve_host
+    float *io_x = nullptr;
+};
+
+static misr_status validate(const misr_desc *d) {
+    if (!d) return fail(MISR_EINVAL, "desc is NULL");
+    if (d->lr_h < 1 || d->lr_w < 1) return fail(MISR_EINVAL, "lr_h, lr_w must be >= 1");
+    if (d->factor < 1 || d->factor > MAXF) return fail(MISR_EINVAL, "factor must be in [1, %d]", MAXF);
+    if (d->K < 1 || d->K > d->factor * d->factor || d->K > MAXK)
+        return fail(MISR_EINVAL, "K must be in [1, factor^2]");
+    if ((int64_t)d->factor * d->lr_h > (1 << 20) || (int64_t)d->factor * d->lr_w > (1 << 20))
+        return fail(MISR_EINVAL, "HR image side above 2^20");
+    if (!d->shifts) return fail(MISR_EINVAL, "shifts is NULL");
+    if (!d->psf) return fail(MISR_EINVAL, "psf is NULL");
+    if (d->psf_size < 1 || d->psf_size > 2 * PSF_R + 1 || d->psf_size % 2 == 0)
+        return fail(MISR_EINVAL, "psf_size must be odd and <= %d", 2 * PSF_R + 1);
+    if (!(d->lambda >= 0)) return fail(MISR_EINVAL, "lambda must be >= 0");
+    if (!(d->eps > 0)) return fail(MISR_EINVAL, "eps must be > 0");
+    if (d->btv_w < 1 || d->btv_w > BTV_W) return fail(MISR_EINVAL, "btv_w must be in [1, %d]", BTV_W);
+    if (!(d->btv_alpha >= 0)) return fail(MISR_EINVAL, "btv_alpha must be >= 0");
+    if (d->iters < 0 || d->iters > 1000000) return fail(MISR_EINVAL, "iters must be in [0, 1e6]");
+    if (d->x0_mode < 0 || d->x0_mode > 2) return fail(MISR_EINVAL, "bad x0_mode");
+    if (d->in_dtype != MISR_F32 && d->in_dtype != MISR_U16) return fail(MISR_EINVAL, "in_dtype must be MISR_F32 or MISR_U16");
+    if (d->in_dtype == MISR_U16 && !(d->flat_field > 0)) return fail(MISR_EINVAL, "flat_field must be > 0");
+    if (d->iterate_dtype == MISR_BF16) return fail(MISR_ENOTIMPL, "BF16 iterate not available in this build");
+    if (d->iterate_dtype != MISR_F32) return fail(MISR_EINVAL, "iterate_dtype must be MISR_F32");
+    return MISR_OK;
+}
+
+// Separable PSF taps.  h = u v^T with sum h = 1 implies h = rowsum colsum^T, so the PSF is
+// accepted when it equals the outer product of its row and column sums.
+static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
+    const int S = d->psf_size, R = S / 2;
+    double sum = 0;
+    for (int i = 0; i < S * S; ++i) sum += d->psf[i];
+    if (!(sum > 0)) return fail(MISR_EINVAL, "PSF must have a positive sum");
+    std::vector<double> h(S * S), rs(S, 0.0), cs(S, 0.0);
+    double hmax = 0;
+    for (int i = 0; i < S * S; ++i) { h[i] = d->psf[i] / sum; hmax = std::max(hmax, std::fabs(h[i])); }
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) { rs[a] += h[a * S + b]; cs[b] += h[a * S + b]; }
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b)
+            if (std::fabs(h[a * S + b] - rs[a] * cs[b]) > 1e-6 * hmax)
+                return fail(MISR_EINVAL, "PSF is not separable");
+    for (int i = 0; i < 2 * PSF_R + 1; ++i) { hy[i] = 0.f; hx[i] = 0.f; }
+    for (int a = -R; a <= R; ++a) { hy[a + PSF_R] = (float)rs[a + R]; hx[a + PSF_R] = (float)cs[a + R]; }
+    return MISR_OK;
+}
+
+static misr_status set_pass_attrs() {
+    static bool done = false;
+    if (done) return MISR_OK;
+    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
+    done = true;
+    return MISR_OK;
+}
+
+static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double beta, cudaStream_t s) {
+    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<p->hp.n_tiles, PASS_NT, PassGeo::SMEM_BYTES, s>>>(
+        p->dprob, p->dtile, mode, alpha, beta);
+    CK(cudaGetLastError());
+    return MISR_OK;
+}
+
+static int grid_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    return (int)std::min<size_t>(std::max<size_t>(b, 1), 148 * 16);
+}
+
+static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float *x_given, int flags,
+                                  cudaStream_t s) {
+    const float log_i0 = p->d.in_dtype == MISR_U16 ? logf(p->d.flat_field) : 0.f;
+    prepare_kernel<<<grid_for(p->n_pitched, 256), 256, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, x_given,
+                                                       p->d.x0_mode, flags);
+    CK(cudaGetLastError());
+    return MISR_OK;
+}
+
+extern "C" {
+
+const char *misr_version(void) { return "misr-b300 0.2 (sm_103a, TMA-fed fused SCG pass 32x64)"; }
+
+const char *misr_last_error(void) { return g_err.c_str(); }
+
+misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
+    if (!out) return fail(MISR_EINVAL, "out is NULL");
+    *out = nullptr;
+    misr_status s = validate(desc);
+    if (s != MISR_OK) return s;
+    const misr_desc &d = *desc;
+    const int f = d.factor;
+    DevProblem hp{};
+    hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
+    hp.H = f * d.lr_h; hp.W = f * d.lr_w;
+    hp.pitch = (hp.W + 3) & ~3;
+    hp.iters = d.iters;
+    for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
+    for (int k = 0; k < d.K; ++k) {
+        const double tx = (double)f * d.shifts[2 * k], ty = (double)f * d.shifts[2 * k + 1];
+        const double rx = std::floor(tx + 0.5), ry = std::floor(ty + 0.5);
+        if (std::fabs(tx - rx) > 1e-4 || std::fabs(ty - ry) > 1e-4)
+            return fail(MISR_ENOTIMPL, "frame %d: shift times factor is not an integer (subpixel HR warps not supported)", k);
+        if (rx < 0 || rx > f - 1 || ry < 0 || ry > f - 1)
+            return fail(MISR_EINVAL, "frame %d: shift must lie in [0, 1 - 1/f] LR px", k);
+        const int ph = (int)ry * f + (int)rx;
+        if (hp.frame_of_phase[ph] >= 0) return fail(MISR_EINVAL, "frames %d and %d sample the same HR phase", hp.frame_of_phase[ph], k);
+        hp.frame_of_phase[ph] = k;
+        hp.ty[k] = (int)ry; hp.tx[k] = (int)rx;
+    }
+    s = psf_taps(desc, hp.hy, hp.hx);
+    if (s != MISR_OK) return s;
+    hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
+    double eps_pairs = 0;
+    for (int dy = 0; dy < BTV_W; ++dy)
+        for (int dx = 0; dx < BTV_W; ++dx) {
+            const int dd = dy * BTV_W + dx;
+            float g = 0.f;
+            if (dd != 0 && dx < d.btv_w && dy < d.btv_w) g = (float)std::pow(d.btv_alpha, dx + dy);
+            hp.gamma[dd] = g;
+            if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
+        }
+    hp.eps_pairs = d.eps * eps_pairs;
+    hp.tiles_y = (hp.H + TILE_H - 1) / TILE_H;
+    hp.tiles_x = (hp.W + TILE_W - 1) / TILE_W;
+    hp.n_tiles = hp.tiles_y * hp.tiles_x;
+
+    misr_plan_t p = new (std::nothrow) misr_plan_s();
+    if (!p) return fail(MISR_ENOMEM, "host allocation failed");
+    p->d = d;
+    p->d.shifts = nullptr;
+    p->d.psf = nullptr;
+    cudaGetDevice(&p->device);
+    p->n = (size_t)hp.H * hp.W;
+    p->n_pitched = (size_t)hp.H * hp.pitch;
+    p->m_total = (size_t)d.K * d.lr_h * d.lr_w;
+
+    // workspace: X[2], R[2], P[2], Y | partials | counter | state | trace | problem | tile map
+    const size_t img = align_up(p->n_pitched * sizeof(float), 256);
+    size_t off = 0;
+    const size_t o_img = off; off += 7 * img;
+    const size_t o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(double), 256);
+    const size_t o_cnt = off; off += 256;
+    const size_t o_st = off; off += align_up(sizeof(ScgState), 256);
+    const size_t o_tr = off; off += align_up((size_t)std::max(d.iters, 1) * TRACE_COLS * sizeof(double), 256);
+    const size_t o_pr = off; off += align_up(sizeof(DevProblem), 256);
+    const size_t o_tm = off; off += align_up((size_t)hp.n_tiles * sizeof(int2), 256);
+    p->ws_bytes = off;
+    cudaError_t e = cudaMalloc((void **)&p->ws, off);
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return fail(MISR_ENOMEM, "cudaMalloc(%zu) failed: %s", off, cudaGetErrorString(e));
+    }
+    char *b = p->ws;
+    for (int i = 0; i < 2; ++i) {
+        hp.X[i] = (float *)(b + o_img + (0 + i) * img);
+        hp.Rv[i] = (float *)(b + o_img + (2 + i) * img);
+        hp.Pv[i] = (float *)(b + o_img + (4 + i) * img);
+    }
+    hp.Y = (float *)(b + o_img + 6 * img);
+    hp.partials = (double *)(b + o_part);
+    hp.counter = (unsigned int *)(b + o_cnt);
+    hp.st = (ScgState *)(b + o_st);
+    hp.trace = (double *)(b + o_tr);
+    p->dprob = (DevProblem *)(b + o_pr);
+    p->dtile = (int2 *)(b + o_tm);
+    {
+        misr_status ms = get_encode_tiled();
+        for (int i = 0; i < 2 && ms == MISR_OK; ++i) {
+            ms = make_map(&hp.tmX[i], hp.X[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
+            if (ms == MISR_OK) ms = make_map(&hp.tmR[i], hp.Rv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
+            if (ms == MISR_OK) ms = make_map(&hp.tmP[i], hp.Pv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
+        }
+        if (ms == MISR_OK) ms = make_map(&hp.tmY, hp.Y, hp.W, hp.H, hp.pitch, PassGeo::EW, PassGeo::EH, true);
+        if (ms != MISR_OK) {
+            cudaFree(p->ws);
+            delete p;
+            return ms;
+        }
+    }
+    p->hp = hp;
+
+    std::vector<int2> tiles(hp.n_tiles);
+    for (int t = 0; t < hp.n_tiles; ++t) tiles[t] = make_int2(0, t);
+    misr_status rs = MISR_OK;
+    do {
+        if ((e = cudaMemset(p->ws, 0, off)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(p->dprob, &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(p->dtile, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming)) != cudaSuccess) break;
+        if ((e = cudaMallocHost((void **)&p->st_host, sizeof(ScgState))) != cudaSuccess) break;
+        rs = set_pass_attrs();
+    } while (0);
+    if (e != cudaSuccess || rs != MISR_OK) {
+        misr_status r = rs != MISR_OK ? rs : fail(MISR_ECUDA, "plan setup: %s", cudaGetErrorString(e));
+        misr_plan_destroy(p);
+        return r;
+    }
+    *out = p;
+    return MISR_OK;
+}
+
+misr_status misr_plan_destroy(misr_plan_t p) {
+    if (!p) return MISR_OK;
+    DeviceGuard g(p->device);
+    cudaDeviceSynchronize();
+    if (p->chunk) cudaGraphExecDestroy(p->chunk);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->done_ev) cudaEventDestroy(p->done_ev);
+    if (p->st_host) cudaFreeHost(p->st_host);
+    if (p->io_y) cudaFree(p->io_y);
+    if (p->io_x) cudaFree(p->io_x);
+    if (p->ws) cudaFree(p->ws);
+    delete p;
+    return MISR_OK;
+}
+
+misr_status misr_plan_workspace_bytes(misr_plan_t p, size_t *bytes) {
+    if (!p || !bytes) return fail(MISR_EINVAL, "NULL argument");
+    *bytes = p->ws_bytes;
+    return MISR_OK;
+}
+
+misr_status misr_forward(misr_plan_t p, const float *x_dev, float *y_dev, misr_stream_t stream) {
+    if (!p || !x_dev || !y_dev) return fail(MISR_EINVAL, "NULL argument");
+    DeviceGuard g(p->device);
+    forward_kernel<<<grid_for(p->m_total, 256), 256, 0, (cudaStream_t)stream>>>(p->dprob, 0, x_dev, y_dev);
+    CK(cudaGetLastError());
+    return MISR_OK;
+}
+
+misr_status misr_pass_probe(misr_plan_t p, const void *y_dev, const float *x_dev, const float *r_dev,
+                            const float *p_old_dev, double alpha, double beta, float *x_out_dev,
+                            float *r_out_dev, float *p_out_dev, double *sums, misr_stream_t stream) {
+    if (!p || !y_dev || !x_dev || !r_dev || !p_old_dev || !sums) return fail(MISR_EINVAL, "NULL argument");
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(MISR_EINVAL, "alpha, beta must be finite");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t wb = (size_t)p->hp.W * sizeof(float), pb = (size_t)p->hp.pitch * sizeof(float);
+    const size_t hrows = (size_t)p->hp.H;
+    misr_status r = launch_prepare(p, y_dev, nullptr, 4, s);
+    if (r != MISR_OK) return r;
+    CK(cudaMemcpy2DAsync(p->hp.X[0], pb, x_dev, wb, wb, hrows, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpy2DAsync(p->hp.Rv[0], pb, r_dev, wb, wb, hrows, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpy2DAsync(p->hp.Pv[0], pb, p_old_dev, wb, wb, hrows, cudaMemcpyDeviceToDevice, s));
+    r = launch_pass(p, MODE_PROBE, alpha, beta, s);
+    if (r != MISR_OK) return r;
+    if (x_out_dev) CK(cudaMemcpy2DAsync(x_out_dev, wb, p->hp.X[1], pb, wb, hrows, cudaMemcpyDeviceToDevice, s));
+    if (r_out_dev) CK(cudaMemcpy2DAsync(r_out_dev, wb, p->hp.Rv[1], pb, wb, hrows, cudaMemcpyDeviceToDevice, s));
+    if (p_out_dev) CK(cudaMemcpy2DAsync(p_out_dev, wb, p->hp.Pv[1], pb, wb, hrows, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(p->st_host, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (p->st_host->status != DEV_OK) return fail(MISR_ETIMEOUT, "a tile load of the fused pass did not complete in time");
+    for (int i = 0; i < NPART; ++i) sums[i] = p->st_host->sums[i];
+    sums[P_JB] -= p->hp.eps_pairs;   // R_BTV(x') without lambda
+    return MISR_OK;
+}
+
+misr_status misr_gradient(misr_plan_t p, const void *y_dev, const float *x_dev, float *g_dev, double *J_out,
+                          misr_stream_t stream) {
+    if (!p || !y_dev || !x_dev || !g_dev) return fail(MISR_EINVAL, "NULL argument");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int saved = p->d.x0_mode;
+    p->d.x0_mode = MISR_X0_GIVEN;
+    misr_status r = launch_prepare(p, y_dev, x_dev, 1 | 2 | 4, s);
+    p->d.x0_mode = saved;
+    if (r != MISR_OK) return r;
+    r = launch_pass(p, MODE_PROBE, 0.0, 0.0, s);
+    if (r != MISR_OK) return r;
+    scale_copy_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->hp.Rv[1], p->hp.pitch, -1.f, g_dev, p->hp.H, p->hp.W);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(p->st_host, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (p->st_host->status != DEV_OK) return fail(MISR_ETIMEOUT, "a tile load of the fused pass did not complete in time");
+    if (J_out) {
+        const double *S = p->st_host->sums;
+        *J_out = S[P_JD] + (double)p->hp.lambda * (S[P_JB] - p->hp.eps_pairs);
+    }
+    return MISR_OK;
+}
+
+static misr_status ensure_graph(misr_plan_t p) {
+    const int want = std::max(1, std::min(p->d.iters, GRAPH_CHUNK));
+    if (p->chunk && p->chunk_len == want) return MISR_OK;
+    if (p->chunk) { cudaGraphExecDestroy(p->chunk); p->chunk = nullptr; }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    misr_status r = MISR_OK;
+    for (int i = 0; i < want && r == MISR_OK; ++i) r = launch_pass(p, MODE_ITER, 0.0, 0.0, p->cap);
+    cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
+    if (r != MISR_OK) { if (graph) cudaGraphDestroy(graph); return r; }
+    if (e != cudaSuccess) return fail(MISR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&p->chunk, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MISR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    p->chunk_len = want;
+    return MISR_OK;
+}
+
+static misr_status fill_stats(misr_plan_t p, misr_stats *st) {
+    const ScgState &h = *p->st_host;
+    if (h.status == DEV_TMA_TIMEOUT) {
+        st->status = MISR_ETIMEOUT;
+        return fail(MISR_ETIMEOUT, "a tile load of the fused pass did not complete in time; the solve stopped");
+    }
+    st->iters_done = h.iter;
+    st->accepted = h.accepted;
+    st->status = MISR_OK;
+    st->reserved = 0;
+    st->J_final = h.E;
+    st->rnorm2 = h.rn2;
+    st->lambda_scg = h.lam;
+    return MISR_OK;
+}
+
+misr_status misr_solve(misr_plan_t p, const void *y_dev, float *x_dev, misr_stream_t stream, misr_stats *stats) {
+    if (!p || !y_dev || !x_dev) return fail(MISR_EINVAL, "NULL argument");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    misr_status r = ensure_graph(p);
+    if (r != MISR_OK) return r;
+    r = launch_prepare(p, y_dev, x_dev, 1 | 2 | 4, s);
+    if (r != MISR_OK) return r;
+    r = launch_pass(p, MODE_INIT, 0.0, 0.0, s);
+    if (r != MISR_OK) return r;
+    for (int done = 0; done < p->d.iters; done += p->chunk_len) CK(cudaGraphLaunch(p->chunk, s));
+    finalize_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->dprob, 0, x_dev);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(p->done_ev, s));
+    p->solved = true;
+    if (stats) {
+        CK(cudaMemcpyAsync(p->st_host, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return fill_stats(p, stats);
+    }
+    return MISR_OK;
+}
+
+misr_status misr_solve_host(misr_plan_t p, const void *y_host, float *x_host, misr_stats *stats) {
+    if (!p || !y_host || !x_host) return fail(MISR_EINVAL, "NULL argument");
+    DeviceGuard g(p->device);
+    misr_status gr = ensure_graph(p);   // capture on the private stream before it queues copies
+    if (gr != MISR_OK) return gr;
+    const size_t ybytes = p->m_total * (p->d.in_dtype == MISR_U16 ? 2 : 4);
+    const size_t xbytes = p->n * sizeof(float);
+    if (!p->io_y) {
+        cudaError_t e = cudaMalloc(&p->io_y, ybytes);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(MISR_ENOMEM, "cudaMalloc y: %s", cudaGetErrorString(e)); }
+    }
+    if (!p->io_x) {
+        cudaError_t e = cudaMalloc((void **)&p->io_x, xbytes);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(MISR_ENOMEM, "cudaMalloc x: %s", cudaGetErrorString(e)); }
+    }
+    cudaStream_t s = p->cap;
+    CK(cudaMemcpyAsync(p->io_y, y_host, ybytes, cudaMemcpyHostToDevice, s));
+    if (p->d.x0_mode == MISR_X0_GIVEN) CK(cudaMemcpyAsync(p->io_x, x_host, xbytes, cudaMemcpyHostToDevice, s));
+    misr_status r = misr_solve(p, p->io_y, p->io_x, (misr_stream_t)s, nullptr);
+    if (r != MISR_OK) return r;
+    CK(cudaMemcpyAsync(x_host, p->io_x, xbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p->st_host, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (stats) return fill_stats(p, stats);
+    return MISR_OK;
+}
+
+misr_status misr_get_trace(misr_plan_t p, double *out, int32_t max_rows, int32_t *rows) {
+    if (!p || !out || !rows || max_rows < 0) return fail(MISR_EINVAL, "bad argument");
+    DeviceGuard g(p->device);
+    *rows = 0;
+    if (!p->solved) return MISR_OK;
+    CK(cudaEventSynchronize(p->done_ev));
+    CK(cudaMemcpy(p->st_host, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost));
+    const int n = std::min(p->st_host->iter, (int)max_rows);
+    if (n > 0) CK(cudaMemcpy(out, p->hp.trace, (size_t)n * TRACE_COLS * sizeof(double), cudaMemcpyDeviceToHost));
+    *rows = n;
+    return MISR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every entry point
+declared in include/*.h, and rejects invalid descriptors on the host (MISR_EINVAL /
+MISR_ENOTIMPL) before touching the device."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(misr_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2108_04315_b300 import build, binding
+    build.build()
+    return binding.lib()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for want in ("misr_plan_create", "misr_plan_destroy", "misr_solve", "misr_solve_host", "misr_forward",
+                 "misr_gradient", "misr_pass_probe", "misr_get_trace", "misr_last_error", "misr_version"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_version_string(L):
+    from paper_2108_04315_b300 import binding
+    assert "sm_103a" in binding.misr_version()
+
+
+def _desc(**kw):
+    import gen
+    from paper_2108_04315_b300 import binding
+    base = dict(lr_h=16, lr_w=16, factor=2, shifts=gen.half_pixel_shifts(), psf=gen.gaussian_psf(5, 0.5))
+    base.update(kw)
+    return binding.make_desc(**base)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(factor=0), "EINVAL"),
+    (dict(lr_h=0), "EINVAL"),
+    (dict(shifts=[(0.0, 0.0)] * 5), "EINVAL"),                    # K > f^2
+    (dict(shifts=[(0.0, 0.0), (0.0, 0.0)]), "EINVAL"),            # same phase twice
+    (dict(shifts=[(0.25, 0.0)]), "ENOTIMPL"),                     # f*s not an integer
+    (dict(shifts=[(1.0, 0.0)]), "EINVAL"),                        # shift beyond [0, 1-1/f]
+    (dict(psf=np.ones((4, 4))), "EINVAL"),                        # even PSF
+    (dict(psf=np.ones((7, 7))), "EINVAL"),                        # PSF larger than 5x5
+    (dict(psf=np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1.0]])), "EINVAL"),   # not separable
+    (dict(eps=0.0), "EINVAL"),
+    (dict(btv_w=4), "EINVAL"),
+    (dict(lam=-1.0), "EINVAL"),
+    (dict(iters=-1), "EINVAL"),
+    (dict(in_dtype=7), "EINVAL"),
+    (dict(iterate_dtype=2), "ENOTIMPL"),
+])
+def test_invalid_descriptor_rejected_on_host(L, kw, status):
+    from paper_2108_04315_b300 import binding
+    d = _desc(**kw)
+    h = C.c_void_p()
+    rc = L.misr_plan_create(C.byref(d), C.byref(h))
+    assert rc == getattr(binding, "MISR_" + status), binding.misr_last_error()
+    assert h.value is None
+    assert binding.misr_last_error()
+
+
+def test_null_arguments_rejected(L):
+    from paper_2108_04315_b300 import binding
+    assert L.misr_plan_create(None, None) == binding.MISR_EINVAL
+    assert L.misr_solve(None, None, None, None, None) == binding.MISR_EINVAL
+    assert L.misr_plan_destroy(None) == binding.MISR_OK
