@@ -39,7 +39,7 @@ misr_status fail(misr_status s, const char *fmt, ...) {
     } while (0)
 
 // the tile shape of the fused pass
-constexpr int TILE_H = 32, TILE_W = 64, PASS_NT = 256;
+constexpr int TILE_H = 32, TILE_W = 64, PASS_NT = 512;
 using PassGeo = Geo<TILE_H, TILE_W>;
 // passes captured per CUDA graph replay
 constexpr int GRAPH_CHUNK = 50;
@@ -161,13 +161,29 @@ static misr_status set_pass_attrs() {
     if (done) return MISR_OK;
     CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
+    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
+                            cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     done = true;
     return MISR_OK;
 }
 
+// CTAs of the fused pass resident on the whole GPU (the L2 prefetch distance)
+static int resident_ctas() {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scg_pass_kernel<TILE_H, TILE_W, PASS_NT>, PASS_NT,
+                                                  PassGeo::SMEM_BYTES);
+    cudaGetLastError();
+    cached = sms * per_sm;
+    return cached;
+}
+
 static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double beta, cudaStream_t s) {
     scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<p->hp.n_tiles, PASS_NT, PassGeo::SMEM_BYTES, s>>>(
-        p->dprob, p->dtile, mode, alpha, beta);
+        p->dprob, p->dtile, mode, alpha, beta, resident_ctas());
     CK(cudaGetLastError());
     return MISR_OK;
 }
@@ -233,6 +249,11 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     hp.tiles_y = (hp.H + TILE_H - 1) / TILE_H;
     hp.tiles_x = (hp.W + TILE_W - 1) / TILE_W;
     hp.n_tiles = hp.tiles_y * hp.tiles_x;
+    // two-level reduction: groups of at least 64 tiles, at most 1024 groups (their sums are
+    // staged in the freed tile buffers of the last CTA)
+    hp.group = 64;
+    while ((hp.n_tiles + hp.group - 1) / hp.group > 1024) hp.group *= 2;
+    hp.n_groups = (hp.n_tiles + hp.group - 1) / hp.group;
 
     misr_plan_t p = new (std::nothrow) misr_plan_s();
     if (!p) return fail(MISR_ENOMEM, "host allocation failed");
@@ -249,6 +270,8 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     size_t off = 0;
     const size_t o_img = off; off += 7 * img;
     const size_t o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(double), 256);
+    const size_t o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(double), 256);
+    const size_t o_gcnt = off; off += align_up((size_t)hp.n_groups * sizeof(unsigned int), 256);
     const size_t o_cnt = off; off += 256;
     const size_t o_st = off; off += align_up(sizeof(ScgState), 256);
     const size_t o_tr = off; off += align_up((size_t)std::max(d.iters, 1) * TRACE_COLS * sizeof(double), 256);
@@ -270,6 +293,8 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     hp.Y = (float *)(b + o_img + 6 * img);
     hp.partials = (double *)(b + o_part);
     hp.counter = (unsigned int *)(b + o_cnt);
+    hp.gpartials = (double *)(b + o_gpart);
+    hp.gcount = (unsigned int *)(b + o_gcnt);
     hp.st = (ScgState *)(b + o_st);
     hp.trace = (double *)(b + o_tr);
     p->dprob = (DevProblem *)(b + o_pr);

@@ -23,6 +23,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tma.cuh"
 
 namespace misr {
@@ -55,6 +57,7 @@ struct ScgState {
     double sums[NPART];
     int cur, pcur;    // which half of the X/R and P double buffers holds x_k, r_k / p_{k-1}
     int success, iter, accepted, done, status, iters;
+    float alpha_f, beta_f;   // alpha and beta rounded once for the FP32 pass
 };
 
 struct DevProblem {
@@ -67,8 +70,11 @@ struct DevProblem {
     double eps_pairs;                             // eps * sum_d gamma_d * #pairs_d
     float *X[2], *Rv[2], *Pv[2];                  // x, r (double buffered), p (double buffered)
     float *Y;                                     // interleaved frames, NaN where unsampled
-    double *partials;                             // [n_tiles][NPART]
-    unsigned int *counter;                        // tiles finished in the current pass
+    double *partials;                             // [n_tiles][NPART] per-tile sums
+    double *gpartials;                            // [n_groups][NPART] per-group sums
+    unsigned int *gcount;                         // [n_groups] tiles of the group finished
+    unsigned int *counter;                        // groups finished in the current pass
+    int group, n_groups;                          // tiles per group, number of groups
     ScgState *st;
     double *trace;                                // [iters][TRACE_COLS]
     int ty[MAXK], tx[MAXK];
@@ -141,6 +147,8 @@ __device__ inline void scg_tail(const DevProblem &P, ScgState *st, const double 
     }
     st->delta = delta;
     st->alpha = st->mu / delta;
+    st->alpha_f = (float)st->alpha;
+    st->beta_f = (float)st->beta;
     if (!(st->pn2 > 0.0) || !isfinite(st->alpha)) st->done = 1;
 }
 
@@ -164,9 +172,10 @@ struct Geo {
     static constexpr int GH = TH + 4, GW = TW + 4;
     static constexpr int DH = TH + 6, DW = TW + 8;
     static constexpr int CH = TH + 4, CW = TW;
-    static constexpr int S1 = XH * EW, S2 = EH * GW, S3 = 3 * DH * DW, S4 = CH * CW;
-    static constexpr int S12 = S1 > S2 ? S1 : S2, S34 = S3 > S4 ? S3 : S4;
-    static constexpr int SC = S12 > S34 ? S12 : S34;
+    static constexpr int HS1 = XH * EW, HS2 = EH * GW, HS3 = CH * CW;
+    static constexpr int HS12 = HS1 > HS2 ? HS1 : HS2;
+    static constexpr int HS = HS12 > HS3 ? HS12 : HS3;
+    static constexpr int SC = 3 * DH * DW + HS;          // psi' planes + one horizontal blur
     static constexpr int FLOATS = 3 * XH * XW + EH * EW + GH * GW + SC;
     static constexpr size_t TMA_BYTES = sizeof(float) * (3 * XH * XW + EH * EW);
     static constexpr size_t SMEM_BYTES = 128 /*align slack*/ + sizeof(float) * FLOATS + TH * TW + 64;
@@ -191,6 +200,27 @@ __device__ __forceinline__ void ld4v(const float *p, float *v) {
 }
 __device__ __forceinline__ void st4v(float *p, const float *v) { st4(p, make_float4(v[0], v[1], v[2], v[3])); }
 
+// packed two-lane FP32 arithmetic (one instruction for two values)
+__device__ __forceinline__ unsigned long long f2u(float2 a) { return *reinterpret_cast<unsigned long long *>(&a); }
+__device__ __forceinline__ float2 u2f(unsigned long long a) { return *reinterpret_cast<float2 *>(&a); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {   // a * b + c
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 f2rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
 // Frame mask of the forward blur at sample coordinate c (one axis) for tap offset a:
 // the tap reads coordinate c - a, dropped when c - a < (c mod f).
 __device__ __forceinline__ bool fwd_tap_ok(int c, int a, int f) { return c < 0 || (c - a) >= (c % f); }
@@ -198,16 +228,31 @@ __device__ __forceinline__ bool fwd_tap_ok(int c, int a, int f) { return c < 0 |
 // sits at u + a; the tap exists when u >= ((u + a) mod f).
 __device__ __forceinline__ bool adj_tap_ok(int u, int a, int f) { return (u + a) < 0 || u >= ((u + a) % f); }
 
+
+// per-thread partial sums of a pass (FP32; combined across the CTA in FP64).  a, b, c hold
+// the full curvature forms: 2 sum (B v)(B w) over sampled pixels + lambda * prior part.
 struct PassAcc {
-    float jd, dj, jb, rr, rrx, pr, pp, ad, bd, cd, ab, bb, cb;
+    float jd, dj, jb, rr, rrx, pr, pp, a, b, c;
 };
+
+// per-problem constants staged in shared memory at CTA start
+enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_N = 32 };
 
 // ---------------------------------------------------------------------------------------
 // Body of the fused pass on one tile.  BORDER: the tile's halo reaches outside the image, so
 // frame masks, BTV pair validity and image bounds are checked; interior tiles skip them.
+//
+// Work is split into 4-pixel row items and scheduled in nine barrier intervals.  The BTV
+// gradient rounds (psi' planes, backward gather) depend only on x', so each is paired with a
+// data-term stage in one combined item loop; BTV items come first in the index space so a
+// thread's BTV items (and their register accumulators) are the same in every interval.
+//   I1 A: p, x'                I2 psi(dy=0) + B1          I3 gather(0) + B2 (residual)
+//   I4 psi(1) + C1             I5 gather(1) + C2          I6 psi(2) + horizontal blur of p
+//   I7 gather(2) + r'          I8 horizontal blur of r'   I9 curvature forms (owned)
 template <int TH, int TW, int NT, bool BORDER>
-__device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsigned char *smp, int y0, int x0,
-                                          float alpha, float beta, float *Xn, float *Rn, float *Pn, PassAcc &A) {
+__device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsigned char *smp, const float *cs,
+                                          uint64_t *ybar, int y0, int x0, float alpha, float beta, float *Xn,
+                                          float *Rn, float *Pn, PassAcc &A) {
     using G = Geo<TH, TW>;
     constexpr int XH = G::XH, XW = G::XW, EH = G::EH, EW = G::EW, GH = G::GH, GW = G::GW;
     constexpr int DH = G::DH, DW = G::DW, CH = G::CH, CW = G::CW;
@@ -216,16 +261,27 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
     float *RB = PB + XH * XW;
     float *YB = RB + XH * XW;
     float *GB = YB + EH * EW;
-    float *SC = GB + GH * GW;
+    float *PL = GB + GH * GW;           // 3 psi' planes of DH x DW
+    float *HS = PL + 3 * DH * DW;       // horizontal blurs: x' (B1), E (C1), p (E)
+    float *HR = RB;                     // horizontal blur of r' (r is dead by then)
     const int tid = threadIdx.x;
     const int H = P.H, W = P.W, f = P.f, pitch = P.pitch;
-    float hx[5], hy[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) { hx[i] = P.hx[i]; hy[i] = P.hy[i]; }
-    const float lambda = P.lambda, eps2 = P.eps2;
+    const float eps2 = cs[C_EPS2], lambda = cs[C_LAMBDA];
 
-    // --- A: p = r + beta p_old, x' = x + alpha p on the X box; owned pixels go to HBM
-    for (int it = tid; it < XH * XW / 4; it += NT) {
+    constexpr int ND = DH * DW / 4;                  // BTV items (D grid, origin (-4, -4))
+    constexpr int NDI = (ND + NT - 1) / NT;
+    constexpr int N_A = XH * XW / 4, N_B1 = XH * EW / 4, N_B2 = EH * EW / 4, N_C1 = EH * GW / 4;
+    constexpr int N_C2 = GH * GW / 4, N_HP = CH * CW / 4, N_HR = CH * CW / 4, N_E = TH * TW / 4;
+    float2 facc[NDI][2], bacc[NDI][2];
+    float2 jb2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < NDI; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) { facc[i][h] = make_float2(0.f, 0.f); bacc[i][h] = make_float2(0.f, 0.f); }
+
+    // ---------------- item bodies
+    // A: p = r + beta p_old, x' = x + alpha p on the X box; owned pixels go to HBM
+    auto item_A = [&](int it) {
         const int r = it / (XW / 4), c4 = it - r * (XW / 4);
         const float4 rv = ld4(RB + 4 * it), pov = ld4(PB + 4 * it), xv = ld4(XB + 4 * it);
         float4 pv, xn;
@@ -253,12 +309,9 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
                 }
             }
         }
-    }
-    __syncthreads();
-
-    // --- B1: forward horizontal blur of x' on (X rows) x (E cols)
-    float *H1 = SC;
-    for (int it = tid; it < XH * EW / 4; it += NT) {
+    };
+    // B1: forward horizontal blur of x' on (X rows) x (E cols)
+    auto item_B1 = [&](int it) {
         const int r = it / (EW / 4), e = 4 * (it - r * (EW / 4));
         float in[8];
         ld8_off2(XB + r * XW + e + 2, in);   // x' at E cols e-2 .. e+5
@@ -270,51 +323,44 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 - b];
                 if (BORDER && !fwd_tap_ok(x0 - 4 + e + j, b, f)) v = 0.f;
-                s = fmaf(hx[b + 2], v, s);
+                s = fmaf(cs[C_HX + b + 2], v, s);
             }
             out[j] = s;
         }
-        st4v(H1 + r * EW + e, out);
-    }
-    __syncthreads();
-
-    // --- B2: vertical blur -> Z, residual E = Z - Y (0 where Y is NaN: unsampled or outside)
-    for (int it = tid; it < (EH / 2) * (EW / 4); it += NT) {
-        const int m = it / (EW / 4), e = 4 * (it - m * (EW / 4)), n = 2 * m;
-        float rows[6][4];
+        st4v(HS + r * EW + e, out);
+    };
+    // B2: vertical blur -> Z, residual E = Z - Y (0 where Y is NaN: unsampled or outside)
+    auto item_B2 = [&](int it) {
+        const int n = it / (EW / 4), e = 4 * (it - n * (EW / 4));
+        const int gy = y0 - 4 + n;
+        float2 z[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-        for (int i = 0; i < 6; ++i) ld4v(H1 + (n + i) * EW + e, rows[i]);
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int gy = y0 - 4 + n + rr;
-            float yv[4], ev[4];
-            ld4v(YB + (n + rr) * EW + e, yv);
-            const bool own_row = (n + rr - 4) >= 0 && (n + rr - 4) < TH;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float z = 0.f;
-#pragma unroll
-                for (int a = -2; a <= 2; ++a) {
-                    float v = rows[rr + 2 - a][j];
-                    if (BORDER && !fwd_tap_ok(gy, a, f)) v = 0.f;
-                    z = fmaf(hy[a + 2], v, z);
-                }
-                const bool smp_ok = !isnan(yv[j]);
-                ev[j] = smp_ok ? z - yv[j] : 0.f;
-                const int oc = e + j - 4;
-                if (own_row && oc >= 0 && oc < TW) {
-                    smp[(n + rr - 4) * TW + oc] = smp_ok;
-                    A.jd = fmaf(ev[j], ev[j], A.jd);
-                }
-            }
-            st4v(YB + (n + rr) * EW + e, ev);
+        for (int a = -2; a <= 2; ++a) {
+            const float4 v = ld4(HS + (n + 2 - a) * EW + e);
+            const float2 h = bc2((BORDER && !fwd_tap_ok(gy, a, f)) ? 0.f : cs[C_HY + a + 2]);
+            z[0] = f2fma(h, make_float2(v.x, v.y), z[0]);
+            z[1] = f2fma(h, make_float2(v.z, v.w), z[1]);
         }
-    }
-    __syncthreads();
-
-    // --- C1: adjoint horizontal blur of E on (E rows) x (G cols)
-    float *H2 = SC;
-    for (int it = tid; it < EH * GW / 4; it += NT) {
+        const float zz[4] = {z[0].x, z[0].y, z[1].x, z[1].y};
+        float yv[4], ev[4];
+        ld4v(YB + n * EW + e, yv);
+        const bool own = (n - 4) >= 0 && (n - 4) < TH && e >= 4 && e < TW + 4;
+        unsigned int sbits = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool smp_ok = !isnan(yv[j]);
+            ev[j] = smp_ok ? zz[j] - yv[j] : 0.f;
+            sbits |= (smp_ok ? 1u : 0u) << (8 * j);
+        }
+        if (own) {
+            *reinterpret_cast<unsigned int *>(smp + (n - 4) * TW + e - 4) = sbits;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) A.jd = fmaf(ev[j], ev[j], A.jd);
+        }
+        st4v(YB + n * EW + e, ev);
+    };
+    // C1: adjoint horizontal blur of E on (E rows) x (G cols)
+    auto item_C1 = [&](int it) {
         const int n = it / (GW / 4), g = 4 * (it - n * (GW / 4));
         float in[8];
         ld8(YB + n * EW + g, in);   // E at G cols g-2 .. g+5
@@ -326,272 +372,352 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 + b];
                 if (BORDER && !adj_tap_ok(x0 - 2 + g + j, b, f)) v = 0.f;
-                s = fmaf(hx[b + 2], v, s);
+                s = fmaf(cs[C_HX + b + 2], v, s);
             }
             out[j] = s;
         }
-        st4v(H2 + n * GW + g, out);
-    }
-    __syncthreads();
-
-    // --- C2: adjoint vertical blur -> GB = 2 B^T E
-    for (int it = tid; it < (GH / 2) * (GW / 4); it += NT) {
-        const int m = it / (GW / 4), g = 4 * (it - m * (GW / 4)), n = 2 * m;
-        float rows[6][4];
+        st4v(HS + n * GW + g, out);
+    };
+    // C2: adjoint vertical blur -> GB = 2 B^T E
+    auto item_C2 = [&](int it) {
+        const int n = it / (GW / 4), g = 4 * (it - n * (GW / 4));
+        const int u = y0 - 2 + n;
+        float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-        for (int i = 0; i < 6; ++i) ld4v(H2 + (n + i) * GW + g, rows[i]);
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int u = y0 - 2 + n + rr;
-            float out[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float s = 0.f;
-#pragma unroll
-                for (int a = -2; a <= 2; ++a) {
-                    float v = rows[rr + 2 + a][j];
-                    if (BORDER && !adj_tap_ok(u, a, f)) v = 0.f;
-                    s = fmaf(hy[a + 2], v, s);
-                }
-                out[j] = 2.f * s;
-            }
-            st4v(GB + (n + rr) * GW + g, out);
+        for (int a = -2; a <= 2; ++a) {
+            const float4 v = ld4(HS + (n + 2 + a) * GW + g);
+            const float2 h = bc2((BORDER && !adj_tap_ok(u, a, f)) ? 0.f : 2.f * cs[C_HY + a + 2]);
+            s2[0] = f2fma(h, make_float2(v.x, v.y), s2[0]);
+            s2[1] = f2fma(h, make_float2(v.z, v.w), s2[1]);
         }
-    }
-    // (no barrier needed here: D reads XB and writes the planes, which alias H2 only)
-    __syncthreads();
-
-    // --- D: BTV gradient.  Items are 4-pixel row groups of the D grid (origin (-4, -4));
-    // the forward part sum_d gamma_d psi'(x_q - x_{q+d}) accumulates in registers, the
-    // backward part sum_d gamma_d psi'(x_{q-d} - x_q) is read from psi' planes, one round
-    // per row offset dy with a plane for each dx.
-    constexpr int ND = DH * DW / 4;
-    constexpr int NDI = (ND + NT - 1) / NT;
-    float *PL = SC;   // 3 planes of DH x DW
-    float facc[NDI][4], bacc[NDI][4];
+        st4(GB + n * GW + g, make_float4(s2[0].x, s2[0].y, s2[1].x, s2[1].y));
+    };
+    // horizontal blur of p on rows [-2, TH+2) x owned cols (for the curvature forms)
+    auto item_HP = [&](int it) {
+        const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
+        float inp[8];
+        ld8_off2(PB + (n + 4) * XW + o + 6, inp);     // p at owned cols o-2 .. o+5
+        float out[4];
 #pragma unroll
-    for (int i = 0; i < NDI; ++i)
+        for (int j = 0; j < 4; ++j) {
+            float sp = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { facc[i][j] = 0.f; bacc[i][j] = 0.f; }
+            for (int b = -2; b <= 2; ++b) {
+                float vp = inp[j + 2 - b];
+                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f)) vp = 0.f;
+                sp = fmaf(cs[C_HX + b + 2], vp, sp);
+            }
+            out[j] = sp;
+        }
+        st4v(HS + n * CW + o, out);
+    };
+    // horizontal blur of r' on rows [-2, TH+2) x owned cols
+    auto item_HR = [&](int it) {
+        const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
+        float inr[8];
+        ld8(GB + n * GW + o, inr);                    // r' at owned cols o-2 .. o+5
+        float out[4];
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
+        for (int j = 0; j < 4; ++j) {
+            float sr = 0.f;
 #pragma unroll
-        for (int i = 0; i < NDI; ++i) {
-            const int it = tid + i * NT;
-            if (it >= ND) break;
-            const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
-            float xq[4], xp[8];
-            ld4v(XB + (n + 2) * XW + e + 4, xq);
-            ld8(XB + (n + 2 + dy) * XW + e + 4, xp);
-            const int qy = y0 - 4 + n;
-            const bool own_row = (n - 4) >= 0 && (n - 4) < TH;
+            for (int b = -2; b <= 2; ++b) {
+                float vr = inr[j + 2 - b];
+                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f)) vr = 0.f;
+                sr = fmaf(cs[C_HX + b + 2], vr, sr);
+            }
+            out[j] = sr;
+        }
+        st4v(HR + n * CW + o, out);
+    };
+    // BTV: psi'(x_q - x_{q+d}) planes for the offsets of row offset dy; forward sums in
+    // registers; the prior's value on owned pairs
+    auto item_psi = [&](auto dy_c, int i, int it) {
+        constexpr int dy = decltype(dy_c)::value;
+        const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
+        float xq[4], xp[8];
+        ld4v(XB + (n + 2) * XW + e + 4, xq);
+        ld8(XB + (n + 2 + dy) * XW + e + 4, xp);
+        const int qy = y0 - 4 + n;
+        const bool own = (n - 4) >= 0 && (n - 4) < TH && e >= 4 && e < TW + 4;
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                if (dx == 0 && dy == 0) continue;
-                const float gam = P.gamma[dy * 3 + dx];
-                float pv[4];
+        for (int dx = 0; dx < 3; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            const float2 gam = bc2(cs[C_GAM + dy * 3 + dx]);
+            float2 pv[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * h;
+                const float2 t = f2sub(make_float2(xq[j], xq[j + 1]), make_float2(xp[j + dx], xp[j + 1 + dx]));
+                const float2 sq = f2fma(t, t, bc2(eps2));
+                const float2 rs = f2rsqrt(sq);
+                float2 psi1 = f2mul(t, rs);
+                if (BORDER) {
+                    const int qx = x0 - 4 + e + j;
+                    const bool v0 = qy >= 0 && qx >= 0 && qy + dy < H && qx + dx < W;
+                    const bool v1 = qy >= 0 && qx + 1 >= 0 && qy + dy < H && qx + 1 + dx < W;
+                    psi1.x = v0 ? psi1.x : 0.f;
+                    psi1.y = v1 ? psi1.y : 0.f;
+                    if (own) {
+                        const float2 sr = f2mul(sq, rs);
+                        jb2 = f2fma(gam, make_float2(v0 ? sr.x : 0.f, v1 ? sr.y : 0.f), jb2);
+                    }
+                } else if (own) {
+                    jb2 = f2fma(gam, f2mul(sq, rs), jb2);
+                }
+                pv[h] = psi1;
+                facc[i][h] = f2fma(gam, psi1, facc[i][h]);
+            }
+            st4(PL + dx * DH * DW + n * DW + e, make_float4(pv[0].x, pv[0].y, pv[1].x, pv[1].y));
+        }
+    };
+    // BTV: backward sums gamma_d psi'(x_{q-d} - x_q) from the planes
+    auto item_gather = [&](auto dy_c, int i, int it) {
+        constexpr int dy = decltype(dy_c)::value;
+        const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
+        if (n < dy) return;   // q - d above the plane: q is outside the R region
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            const float2 gam = bc2(cs[C_GAM + dy * 3 + dx]);
+            const float *row = PL + dx * DH * DW + (n - dy) * DW;
+            float v[8];
+            if (dx == 0) ld4v(row + e, v + 4);
+            else if (e >= 4) ld8(row + e - 4, v);
+            else { ld4v(row + e, v + 4); v[0] = v[1] = v[2] = v[3] = 0.f; }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                bacc[i][h] = f2fma(gam, make_float2(v[4 + 2 * h - dx], v[5 + 2 * h - dx]), bacc[i][h]);
+        }
+    };
+    // r' = -(2 B^T E + lambda grad BTV) on the R region (origin (-2, -2)): a D item (cols
+    // e..e+3 of the D grid) covers R cols e-2 .. e+1; owned items go to HBM whole
+    auto item_r = [&](int i, int it) {
+        const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
+        const int gn = n - 2;
+        if (gn < 0 || gn >= GH) return;
+        const int gy = y0 - 4 + n;
+        float rv[4];
+        float *grow = GB + gn * GW;
+        float gsum[4] = {0.f, 0.f, 0.f, 0.f};
+        if (e >= 4) { const float2 v = ld2(grow + e - 2); gsum[0] = v.x; gsum[1] = v.y; }
+        if (e < GW) { const float2 v = ld2(grow + e); gsum[2] = v.x; gsum[3] = v.y; }
+        const float fb[4] = {facc[i][0].x - bacc[i][0].x, facc[i][0].y - bacc[i][0].y,
+                             facc[i][1].x - bacc[i][1].x, facc[i][1].y - bacc[i][1].y};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            rv[j] = -fmaf(lambda, fb[j], gsum[j]);
+            if (BORDER) {
+                const int gx = x0 - 4 + e + j;
+                if (!(gy >= 0 && gy < H && gx >= 0 && gx < W)) rv[j] = 0.f;
+            }
+        }
+        if (e >= 4) st2(grow + e - 2, make_float2(rv[0], rv[1]));
+        if (e < GW) st2(grow + e, make_float2(rv[2], rv[3]));
+        const int orow = n - 4, ocol = e - 4;
+        if (orow >= 0 && orow < TH && ocol >= 0 && ocol < TW) {
+            float rold[4], pq[4];
+            ld4v(RB + (orow + 6) * XW + ocol + 8, rold);
+            ld4v(PB + (orow + 6) * XW + ocol + 8, pq);
+            const int gx = x0 + ocol;
+            if (!BORDER || (gy < H && gx + 3 < W)) {
+                st4(Rn + (size_t)gy * pitch + gx, make_float4(rv[0], rv[1], rv[2], rv[3]));
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const float t = xq[j] - xp[j + dx];
-                    const float s = fmaf(t, t, eps2);
-                    const float rs = rsqrtf(s);
-                    float psi1 = t * rs;
-                    bool valid = true;
-                    if (BORDER) {
-                        const int qx = x0 - 4 + e + j;
-                        valid = qy >= 0 && qx >= 0 && qy + dy < H && qx + dx < W;
-                        if (!valid) psi1 = 0.f;
-                    }
-                    pv[j] = psi1;
-                    facc[i][j] = fmaf(gam, psi1, facc[i][j]);
-                    const int oc = e + j - 4;
-                    if (own_row && oc >= 0 && oc < TW && valid) A.jb = fmaf(gam, s * rs, A.jb);
+                    A.rr = fmaf(rv[j], rv[j], A.rr);
+                    A.rrx = fmaf(rv[j], rold[j], A.rrx);
+                    A.pr = fmaf(pq[j], rv[j], A.pr);
                 }
-                st4v(PL + dx * DH * DW + n * DW + e, pv);
+            } else if (gy < H) {
+                for (int j = 0; j < 4 && gx + j < W; ++j) {
+                    Rn[(size_t)gy * pitch + gx + j] = rv[j];
+                    A.rr = fmaf(rv[j], rv[j], A.rr);
+                    A.rrx = fmaf(rv[j], rold[j], A.rrx);
+                    A.pr = fmaf(pq[j], rv[j], A.pr);
+                }
             }
         }
-        __syncthreads();
+    };
+    // curvature forms on one owned row x four columns
+    auto item_E = [&](int it) {
+        const int n = it / (TW / 4), o = 4 * (it - n * (TW / 4));
+        const int gy = y0 + n;
+        // data part 2 (B v)(c) (B w)(c) at sampled c, and J_data(x') - J_data(x)
+        {
+            float2 zr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float2 zp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-        for (int i = 0; i < NDI; ++i) {
-            const int it = tid + i * NT;
-            if (it >= ND) break;
-            const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
-            if (n < dy) continue;   // q - d above the plane: q is outside the R region
+            for (int a = -2; a <= 2; ++a) {
+                const float4 vr = ld4(HR + (n + 2 - a) * CW + o);
+                const float4 vp = ld4(HS + (n + 2 - a) * CW + o);
+                const float2 h = bc2((BORDER && !fwd_tap_ok(gy, a, f)) ? 0.f : cs[C_HY + a + 2]);
+                zr[0] = f2fma(h, make_float2(vr.x, vr.y), zr[0]);
+                zr[1] = f2fma(h, make_float2(vr.z, vr.w), zr[1]);
+                zp[0] = f2fma(h, make_float2(vp.x, vp.y), zp[0]);
+                zp[1] = f2fma(h, make_float2(vp.z, vp.w), zp[1]);
+            }
+            const float4 ev = ld4(YB + (n + 4) * EW + o + 4);
+            const unsigned int sbits = *reinterpret_cast<const unsigned int *>(smp + n * TW + o);
+            const float2 msk[2] = {make_float2((sbits & 0xffu) ? 1.f : 0.f, (sbits & 0xff00u) ? 1.f : 0.f),
+                                   make_float2((sbits & 0xff0000u) ? 1.f : 0.f, (sbits & 0xff000000u) ? 1.f : 0.f)};
+            const float2 e2[2] = {make_float2(ev.x, ev.y), make_float2(ev.z, ev.w)};
+            float2 a2 = make_float2(0.f, 0.f), b2 = a2, c2 = a2, d2 = a2;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 zrm = f2mul(zr[h], msk[h]), zpm = f2mul(zp[h], msk[h]);
+                a2 = f2fma(zrm, zrm, a2);
+                b2 = f2fma(zrm, zpm, b2);
+                c2 = f2fma(zpm, zpm, c2);
+                const float2 azp = f2mul(bc2(alpha), zpm);
+                d2 = f2fma(azp, f2sub(f2mul(bc2(2.f), e2[h]), azp), d2);
+            }
+            A.a += 2.f * (a2.x + a2.y);
+            A.b += 2.f * (b2.x + b2.y);
+            A.c += 2.f * (c2.x + c2.y);
+            A.dj += d2.x + d2.y;
+        }
+        // prior part: lambda sum_d gamma_d psi''(t_d) (dv_d)(dw_d) over valid pairs, with
+        // psi''(t) = eps^2 / (t^2 + eps^2)^(3/2); lambda eps^2 gamma_d is folded into cw
+        float2 xq[2], pq[2], rq[2];
+        {
+            const float4 a = ld4(XB + (n + 6) * XW + o + 8);
+            const float4 b = ld4(PB + (n + 6) * XW + o + 8);
+            float tmp[8];
+            ld8(GB + (n + 2) * GW + o, tmp);
+            xq[0] = make_float2(a.x, a.y); xq[1] = make_float2(a.z, a.w);
+            pq[0] = make_float2(b.x, b.y); pq[1] = make_float2(b.z, b.w);
+            rq[0] = make_float2(tmp[2], tmp[3]); rq[1] = make_float2(tmp[4], tmp[5]);
+        }
+        float2 ca = make_float2(0.f, 0.f), cb = ca, cc = ca;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            float xr[8], rrow[8], prow[8];
+            ld8(XB + (n + dy + 6) * XW + o + 8, xr);
+            ld8(PB + (n + dy + 6) * XW + o + 8, prow);
+            ld8(GB + (n + dy + 2) * GW + o, rrow);
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
                 if (dx == 0 && dy == 0) continue;
-                const float gam = P.gamma[dy * 3 + dx];
-                const float *row = PL + dx * DH * DW + (n - dy) * DW;
-                float v[8];
-                if (e >= 4) ld8(row + e - 4, v);
-                else { ld4v(row + e, v + 4); v[0] = v[1] = v[2] = v[3] = 0.f; }
+                const float2 cw = bc2(cs[C_CW + dy * 3 + dx]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) bacc[i][j] = fmaf(gam, v[4 + j - dx], bacc[i][j]);
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * h;
+                    const float2 t = f2sub(xq[h], make_float2(xr[j + dx], xr[j + 1 + dx]));
+                    const float2 rs = f2rsqrt(f2fma(t, t, bc2(eps2)));
+                    const float2 u = f2mul(rs, f2sub(rq[h], make_float2(rrow[j + 2 + dx], rrow[j + 3 + dx])));
+                    const float2 v = f2mul(rs, f2sub(pq[h], make_float2(prow[j + dx], prow[j + 1 + dx])));
+                    float2 g = f2mul(cw, rs);
+                    if (BORDER) {
+                        const int gx = x0 + o + j;
+                        g.x = (gy + dy < H && gx + dx < W) ? g.x : 0.f;
+                        g.y = (gy + dy < H && gx + 1 + dx < W) ? g.y : 0.f;
+                    }
+                    const float2 wu = f2mul(g, u);
+                    ca = f2fma(wu, u, ca);
+                    cb = f2fma(wu, v, cb);
+                    cc = f2fma(f2mul(g, v), v, cc);
+                }
             }
         }
-        __syncthreads();
+        A.a += ca.x + ca.y;
+        A.b += cb.x + cb.y;
+        A.c += cc.x + cc.y;
+    };
+
+    // ---------------- the schedule
+    using I0 = std::integral_constant<int, 0>;
+    using I1c = std::integral_constant<int, 1>;
+    using I2c = std::integral_constant<int, 2>;
+    // BTV items k in [0, ND) first (slot i = k / NT), then the paired stage's items
+#define MISR_PAIRED(BTV_CALL, N_OTHER, OTHER_CALL)                                  \
+    _Pragma("unroll") for (int m = 0; m < (ND + (N_OTHER) + NT - 1) / NT; ++m) {    \
+        const int k = tid + m * NT;                                                  \
+        if (k < ND) {                                                                \
+            if (m < NDI) { BTV_CALL; }                                               \
+        } else if (k < ND + (N_OTHER)) {                                             \
+            const int ko = k - ND;                                                   \
+            OTHER_CALL;                                                              \
+        }                                                                            \
     }
 
-    // r' = -(2 B^T E + lambda grad BTV) on the R region (origin (-2, -2)); owned r' to HBM
+    // I1
+    for (int it = tid; it < N_A; it += NT) item_A(it);
+    __syncthreads();
+    // I2: psi(0) + B1
+    MISR_PAIRED(item_psi(I0(), m, k), N_B1, item_B1(ko))
+    __syncthreads();
+    // the Y box: a wait that runs out flags the state (results of this pass are then void)
+    if (!mbar_wait_bounded(ybar, 0, TMA_WAIT_TRIES) && tid == 0) {
+        atomicExch(&P.st->status, (int)DEV_TMA_TIMEOUT);
+        atomicExch(&P.st->done, 1);
+    }
+    // I3: gather(0) + B2
+    MISR_PAIRED(item_gather(I0(), m, k), N_B2, item_B2(ko))
+    __syncthreads();
+    // I4: psi(1) + C1
+    MISR_PAIRED(item_psi(I1c(), m, k), N_C1, item_C1(ko))
+    __syncthreads();
+    // I5: gather(1) + C2
+    MISR_PAIRED(item_gather(I1c(), m, k), N_C2, item_C2(ko))
+    __syncthreads();
+    // I6: psi(2) + horizontal blur of p
+    MISR_PAIRED(item_psi(I2c(), m, k), N_HP, item_HP(ko))
+    __syncthreads();
+    // I7: gather(2) and r'
 #pragma unroll
     for (int i = 0; i < NDI; ++i) {
         const int it = tid + i * NT;
-        if (it >= ND) break;
-        const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
-        const int gn = n - 2;           // R-region row
-        if (gn < 0 || gn >= GH) continue;
-        const int gy = y0 - 4 + n;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gc = e + j - 2;    // R-region column
-            if (gc < 0 || gc >= GW) continue;
-            const int gx = x0 - 4 + e + j;
-            float rv = -fmaf(lambda, facc[i][j] - bacc[i][j], GB[gn * GW + gc]);
-            if (BORDER && !(gy >= 0 && gy < H && gx >= 0 && gx < W)) rv = 0.f;
-            GB[gn * GW + gc] = rv;
-            const int orow = gn - 2, ocol = gc - 2;
-            if (orow >= 0 && orow < TH && ocol >= 0 && ocol < TW && (!BORDER || (gy < H && gx < W))) {
-                Rn[(size_t)gy * pitch + gx] = rv;
-                const float rold = RB[(orow + 6) * XW + ocol + 8];
-                const float pq = PB[(orow + 6) * XW + ocol + 8];
-                A.rr = fmaf(rv, rv, A.rr);
-                A.rrx = fmaf(rv, rold, A.rrx);
-                A.pr = fmaf(pq, rv, A.pr);
-            }
+        if (it < ND) {
+            item_gather(I2c(), i, it);
+            item_r(i, it);
         }
     }
+    A.jb += jb2.x + jb2.y;
     __syncthreads();
-
-    // --- E1: forward horizontal blurs of r' and p on rows [-2, TH+2) x owned cols
-    float *HR = RB;   // r is dead now
-    float *HP = SC;
-    for (int it = tid; it < CH * CW / 4; it += NT) {
-        const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
-        float inr[8], inp[8];
-        ld8(GB + n * GW + o, inr);                    // r' at owned cols o-2 .. o+5
-        ld8_off2(PB + (n + 4) * XW + o + 6, inp);     // p  at owned cols o-2 .. o+5
-        float outr[4], outp[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float sr = 0.f, sp = 0.f;
-#pragma unroll
-            for (int b = -2; b <= 2; ++b) {
-                float vr = inr[j + 2 - b], vp = inp[j + 2 - b];
-                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f)) { vr = 0.f; vp = 0.f; }
-                sr = fmaf(hx[b + 2], vr, sr);
-                sp = fmaf(hx[b + 2], vp, sp);
-            }
-            outr[j] = sr;
-            outp[j] = sp;
-        }
-        st4v(HR + n * CW + o, outr);
-        st4v(HP + n * CW + o, outp);
-    }
+    // I8: horizontal blur of r'
+    for (int it = tid; it < N_HR; it += NT) item_HR(it);
     __syncthreads();
-
-    // --- E2: curvature forms on the owned pixels, two rows x four columns per item
-    for (int it = tid; it < (TH / 2) * (TW / 4); it += NT) {
-        const int m = it / (TW / 4), o = 4 * (it - m * (TW / 4)), n = 2 * m;
-        // data part: (B r')(c), (B p)(c) at sampled c, and J_data(x') - J_data(x)
-        {
-            float hr[6][4], hp[6][4];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) { ld4v(HR + (n + i) * CW + o, hr[i]); ld4v(HP + (n + i) * CW + o, hp[i]); }
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int gy = y0 + n + rr;
-                float ev[4];
-                ld4v(YB + (n + rr + 4) * EW + o + 4, ev);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float zr = 0.f, zp = 0.f;
-#pragma unroll
-                    for (int a = -2; a <= 2; ++a) {
-                        float vr = hr[rr + 2 - a][j], vp = hp[rr + 2 - a][j];
-                        if (BORDER && !fwd_tap_ok(gy, a, f)) { vr = 0.f; vp = 0.f; }
-                        zr = fmaf(hy[a + 2], vr, zr);
-                        zp = fmaf(hy[a + 2], vp, zp);
-                    }
-                    if (smp[(n + rr) * TW + o + j]) {
-                        A.ad = fmaf(zr, zr, A.ad);
-                        A.bd = fmaf(zr, zp, A.bd);
-                        A.cd = fmaf(zp, zp, A.cd);
-                        const float azp = alpha * zp;
-                        A.dj = fmaf(azp, fmaf(2.f, ev[j], -azp), A.dj);
-                    }
-                }
-            }
-        }
-        // prior part: sum_d gamma_d psi''(t_d) (dv_d)(dw_d) over valid pairs
-        float xq[2][4], rq[2][4], pq[2][4];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            float tmp[8];
-            ld4v(XB + (n + rr + 6) * XW + o + 8, xq[rr]);
-            ld4v(PB + (n + rr + 6) * XW + o + 8, pq[rr]);
-            ld8(GB + (n + rr + 2) * GW + o, tmp);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) rq[rr][j] = tmp[j + 2];
-        }
-#pragma unroll
-        for (int pr = 0; pr < 4; ++pr) {   // partner row n + pr
-            float xr[8], rrow[8], prow[8];
-            ld8(XB + (n + pr + 6) * XW + o + 8, xr);
-            ld8(PB + (n + pr + 6) * XW + o + 8, prow);
-            ld8(GB + (n + pr + 2) * GW + o, rrow);
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int dy = pr - rr;
-                if (dy < 0 || dy > 2) continue;
-                const int gy = y0 + n + rr;
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    if (dx == 0 && dy == 0) continue;
-                    const float gam = P.gamma[dy * 3 + dx];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (BORDER) {
-                            const int gx = x0 + o + j;
-                            if (!(gy + dy < H && gx + dx < W)) continue;
-                        }
-                        const float t = xq[rr][j] - xr[j + dx];
-                        const float rs = rsqrtf(fmaf(t, t, eps2));
-                        const float wgt = gam * rs * rs * rs;
-                        const float dr = rq[rr][j] - rrow[j + 2 + dx];
-                        const float dp = pq[rr][j] - prow[j + dx];
-                        const float wdr = wgt * dr;
-                        A.ab = fmaf(wdr, dr, A.ab);
-                        A.bb = fmaf(wdr, dp, A.bb);
-                        A.cb = fmaf(wgt * dp, dp, A.cb);
-                    }
-                }
-            }
-        }
-    }
+    // I9: curvature forms
+    for (int it = tid; it < N_E; it += NT) item_E(it);
+#undef MISR_PAIRED
 }
 
-// ---------------------------------------------------------------------------------------
-// The fused SCG pass.  One CTA owns a TH x TW tile of the HR grid and, for the step
-//   p = r + beta p_old,  x' = x + alpha p,
-// computes on chip (halos recomputed, nothing but the owned pixels leaves the CTA):
-//   E = B x' - Y, the objective J(x') and J_data(x') - J_data(x),
-//   r' = -(2 B^T E + lambda grad BTV(x')),
-//   and the curvature forms r'.H(x')r', r'.H(x')p, p.H(x')p of the next direction
-//   p_next = r' + beta_next p, whose beta_next is only known after the pass:
-//   p_next.H p_next = a + 2 beta_next b + beta_next^2 c.
-// It writes x', r', p for its tile and FP64 partial sums; the last CTA of the pass runs the
-// SCG scalar tail.  Traffic: reads x, r, p_old, Y, writes x', r', p = 28 bytes per HR px.
+// Fixed-order FP64 sum of `count` records of NPART doubles at src: the records are staged in
+// shared memory, warp j sums field j over its lanes in a fixed order.
+template <int NT>
+__device__ __forceinline__ void tree_sum_npart(const double *src, int count, double *stage, double *out) {
+    static_assert(NT / 32 >= NPART, "one warp per partial");
+    const int tid = threadIdx.x;
+    for (int k = tid; k < count * NPART; k += NT) stage[k] = ld_cg(src + k);
+    __syncthreads();
+    const int j = tid >> 5, l = tid & 31;
+    if (j < NPART) {
+        double s = 0.0;
+        for (int i = l; i < count; i += 32) s += stage[i * NPART + j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (l == 0) out[j] = s;
+    }
+    __syncthreads();
+}
+
 template <int TH, int TW, int NT>
 __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__restrict__ probs,
                                                          const int2 *__restrict__ tile_map, int mode,
-                                                         double probe_alpha, double probe_beta) {
+                                                         double probe_alpha, double probe_beta,
+                                                         int prefetch_stride) {
     using Gm = Geo<TH, TW>;
     constexpr int NWARP = NT / 32;
+    static_assert(Gm::FLOATS * sizeof(float) >= 1024 * NPART * sizeof(double),
+                  "the tile buffers must hold the group sums of the reduction");
     extern __shared__ unsigned char smem_raw[];
     float *sm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     unsigned char *smp = reinterpret_cast<unsigned char *>(sm + Gm::FLOATS);
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ float red[NWARP][13];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float cs[C_N];
+    __shared__ float red[NWARP][NPART];
+    __shared__ float red_lo[NWARP];
+    __shared__ double tot[NPART];
     __shared__ int s_last, s_fail;
 
     const int2 tm = tile_map[blockIdx.x];
@@ -601,32 +727,56 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
 
     const int tid = threadIdx.x;
     const int cur = ld_cg(&st->cur), pcur = ld_cg(&st->pcur);
-    const float alpha = (float)(mode == MODE_PROBE ? probe_alpha : ld_cg(&st->alpha));
-    const float beta = (float)(mode == MODE_PROBE ? probe_beta : ld_cg(&st->beta));
+    const float alpha = mode == MODE_PROBE ? (float)probe_alpha : __ldcg(&st->alpha_f);
+    const float beta = mode == MODE_PROBE ? (float)probe_beta : __ldcg(&st->beta_f);
     const int y0 = (tm.y / P.tiles_x) * TH, x0 = (tm.y % P.tiles_x) * TW;
 
-    // tile loads: x, r, p_old boxes (zero outside the image) and the Y box (NaN outside)
+    // tile loads: x, r, p_old boxes (zero outside the image) on bar[0]; the Y box (NaN
+    // outside) on bar[1], first needed by the residual stage
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_barrier_init();
     }
+    if (tid < 5) { cs[C_HX + tid] = P.hx[tid]; cs[C_HY + tid] = P.hy[tid]; }
+    if (tid < 9) {
+        cs[C_GAM + tid] = P.gamma[tid];
+        cs[C_CW + tid] = P.lambda * P.eps2 * P.gamma[tid];
+    }
+    if (tid == 0) { cs[C_LAMBDA] = P.lambda; cs[C_EPS2] = P.eps2; }
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, (uint32_t)Gm::TMA_BYTES);
-        tma_load_2d(sm, &P.tmX[cur], x0 - 8, y0 - 6, &bar);
-        tma_load_2d(sm + Gm::XH * Gm::XW, &P.tmP[pcur], x0 - 8, y0 - 6, &bar);
-        tma_load_2d(sm + 2 * Gm::XH * Gm::XW, &P.tmR[cur], x0 - 8, y0 - 6, &bar);
-        tma_load_2d(sm + 3 * Gm::XH * Gm::XW, &P.tmY, x0 - 4, y0 - 4, &bar);
+        constexpr uint32_t box_x = sizeof(float) * Gm::XH * Gm::XW;
+        constexpr uint32_t box_y = sizeof(float) * Gm::EH * Gm::EW;
+        mbar_arrive_expect_tx(&bar[0], 3 * box_x);
+        tma_load_2d(sm, &P.tmX[cur], x0 - 8, y0 - 6, &bar[0]);
+        tma_load_2d(sm + Gm::XH * Gm::XW, &P.tmP[pcur], x0 - 8, y0 - 6, &bar[0]);
+        tma_load_2d(sm + 2 * Gm::XH * Gm::XW, &P.tmR[cur], x0 - 8, y0 - 6, &bar[0]);
+        mbar_arrive_expect_tx(&bar[1], box_y);
+        tma_load_2d(sm + 3 * Gm::XH * Gm::XW, &P.tmY, x0 - 4, y0 - 4, &bar[1]);
+        // warm L2 with the inputs of the tile one resident wave ahead (same problem only)
+        const int ahead = blockIdx.x + prefetch_stride;
+        if (prefetch_stride > 0 && ahead < (int)gridDim.x) {
+            const int2 tn = tile_map[ahead];
+            if (tn.x == tm.x) {
+                const int ny = (tn.y / P.tiles_x) * TH, nx = (tn.y % P.tiles_x) * TW;
+                tma_prefetch_l2_2d(&P.tmX[cur], nx - 8, ny - 6);
+                tma_prefetch_l2_2d(&P.tmP[pcur], nx - 8, ny - 6);
+                tma_prefetch_l2_2d(&P.tmR[cur], nx - 8, ny - 6);
+                tma_prefetch_l2_2d(&P.tmY, nx - 4, ny - 4);
+            }
+        }
     }
-    if (!mbar_wait_bounded(&bar, 0, TMA_WAIT_TRIES)) s_fail = 1;
+    if (!mbar_wait_bounded(&bar[0], 0, TMA_WAIT_TRIES)) s_fail = 1;
     __syncthreads();
     if (s_fail) {
         // the loads did not complete in time: flag the state and stop this projection
         if (tid == 0) {
             atomicExch(&st->status, (int)DEV_TMA_TIMEOUT);
             atomicExch(&st->done, 1);
-            mbar_wait_bounded(&bar, 0, TMA_WAIT_TRIES);   // let copies in flight land
+            mbar_wait_bounded(&bar[0], 0, TMA_WAIT_TRIES);   // let copies in flight land
+            mbar_wait_bounded(&bar[1], 0, TMA_WAIT_TRIES);
         }
         return;
     }
@@ -634,64 +784,75 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
     PassAcc A = {};
     float *Xn = P.X[cur ^ 1], *Rn = P.Rv[cur ^ 1], *Pn = P.Pv[pcur ^ 1];
     const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
-    if (border) pass_tile<TH, TW, NT, true>(P, sm, smp, y0, x0, alpha, beta, Xn, Rn, Pn, A);
-    else pass_tile<TH, TW, NT, false>(P, sm, smp, y0, x0, alpha, beta, Xn, Rn, Pn, A);
+    if (border) pass_tile<TH, TW, NT, true>(P, sm, smp, cs, &bar[1], y0, x0, alpha, beta, Xn, Rn, Pn, A);
+    else pass_tile<TH, TW, NT, false>(P, sm, smp, cs, &bar[1], y0, x0, alpha, beta, Xn, Rn, Pn, A);
 
-    // --- FP32 warp sums, FP64 across warps, per-tile partials; the last CTA runs the tail
-    float v[13] = {A.jd, A.dj, A.jb, A.rr, A.rrx, A.pr, A.pp, A.ad, A.bd, A.cd, A.ab, A.bb, A.cb};
+    // --- FP32 warp sums, FP64 across warps: the tile's partial sums.  The prior's value
+    // enters Moller's comparison as a difference of two passes' sums, so its warp sum is
+    // compensated (two-sum: hi + lo carries the rounding error of every addition).
+    float v[NPART] = {A.jd, A.dj, A.jb, A.rr, A.rrx, A.pr, A.pp, A.a, A.b, A.c};
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-    for (int j = 0; j < 13; ++j) {
+    for (int j = 0; j < NPART; ++j) {
+        if (j == P_JB) continue;
         float x = v[j];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
         if (lane == 0) red[warp][j] = x;
     }
-    __syncthreads();
-    if (tid < NPART) {
-        const double lam_eps2 = (double)P.lambda * (double)P.eps2;
-        double s0 = 0, s1 = 0;
-        const int j0 = tid < 7 ? tid : 7 + (tid - 7);   // data part index
-        for (int w = 0; w < NWARP; ++w) {
-            s0 += (double)red[w][j0];
-            if (tid >= 7) s1 += (double)red[w][tid + 3];
+    {
+        float hi = v[P_JB], lo = 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float h2 = __shfl_down_sync(0xffffffffu, hi, off);
+            const float l2 = __shfl_down_sync(0xffffffffu, lo, off);
+            const float s = hi + h2, bb = s - hi;
+            const float err = (hi - (s - bb)) + (h2 - bb);
+            hi = s;
+            lo = lo + l2 + err;
         }
-        const double val = tid < 7 ? s0 : 2.0 * s0 + lam_eps2 * s1;
-        P.partials[(size_t)tm.y * NPART + tid] = val;
+        if (lane == 0) { red[warp][P_JB] = hi; red_lo[warp] = lo; }
     }
-    __threadfence();
     __syncthreads();
-    if (tid == 0) {
-        const unsigned int done_tiles = atomicAdd(P.counter, 1u);
-        s_last = (done_tiles == (unsigned)(P.n_tiles - 1));
+    // two-level deterministic reduction: the last tile of each group of P.group tiles sums
+    // the group in a fixed order, the last group sums the groups and runs the SCG tail
+    const int g = tm.y / P.group;
+    const int gsize = min(P.group, P.n_tiles - g * P.group);
+    if (tid < NPART) {
+        double s;
+        if (tid == P_JB) {
+            s = 0.0;
+            for (int w = 0; w < NWARP; ++w) s += (double)red[w][tid] + (double)red_lo[w];
+        } else {
+            float sf = 0.f;
+#pragma unroll
+            for (int w = 0; w < NWARP; ++w) sf += red[w][tid];
+            s = (double)sf;
+        }
+        P.partials[(size_t)tm.y * NPART + tid] = s;
+        __threadfence();
     }
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&P.gcount[g], 1u) == (unsigned)(gsize - 1));
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // fixed-order FP64 sum over tiles: thread t sums tiles t, t+NT, ...; then a fixed tree
-    __shared__ double redd[NWARP][NPART];
-    double tot[NPART];
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) tot[j] = 0.0;
-    for (int t = tid; t < P.n_tiles; t += NT) {
-#pragma unroll
-        for (int j = 0; j < NPART; ++j) tot[j] += ld_cg(&P.partials[(size_t)t * NPART + j]);
+    double *stage = reinterpret_cast<double *>(sm);   // the tile buffers are free now
+    tree_sum_npart<NT>(P.partials + (size_t)g * P.group * NPART, gsize, stage, tot);
+    if (tid < NPART) {
+        P.gpartials[(size_t)g * NPART + tid] = tot[tid];
+        __threadfence();
     }
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) {
-        double x = tot[j];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-        if (lane == 0) redd[warp][j] = x;
-    }
+    if (tid == 0) P.gcount[g] = 0u;
     __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(P.counter, 1u) == (unsigned)(P.n_groups - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    tree_sum_npart<NT>(P.gpartials, P.n_groups, stage, tot);
     if (tid == 0) {
         double S[NPART];
-        for (int j = 0; j < NPART; ++j) {
-            double s = 0;
-            for (int w = 0; w < NWARP; ++w) s += redd[w][j];
-            S[j] = s;
-        }
+        for (int j = 0; j < NPART; ++j) S[j] = tot[j];
         scg_tail(P, st, S, mode);
         *P.counter = 0u;
         __threadfence();
@@ -713,6 +874,7 @@ __global__ void prepare_kernel(const DevProblem *__restrict__ probs, int pidx, c
         ScgState *st = P.st;
         st->cur = 0; st->pcur = 0; st->done = 0; st->iter = 0; st->accepted = 0;
         st->status = 0; st->alpha = 0.0; st->beta = 0.0; st->success = 1;
+        st->alpha_f = 0.f; st->beta_f = 0.f;
         st->lam = 1e-6; st->lam_bar = 0.0; st->iters = P.iters;
         *P.counter = 0u;
     }
