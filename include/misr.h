@@ -103,9 +103,9 @@ const char *misr_last_error(void);
 
 /* Validate the descriptor and build a plan on the current device: the separable PSF taps,
  * the phase-to-frame table and the device workspace of one solve (7 HR float32 images plus
- * O(tiles) partial sums), allocated here with cudaMalloc.  The plan stands for the paper's
- * system matrices "computed once at the beginning of the CT acquisition and shared by all
- * the rotation angles" (Sec. 3.2); no matrix is formed.
+ * O(tiles) partial sums), allocated here with cudaMalloc.  The plan plays the part of the
+ * system matrices that the paper builds once per scan and reuses for every rotation angle
+ * (Sec. 3.2); no matrix is formed.
  * Errors: MISR_EINVAL (descriptor), MISR_ENOMEM, MISR_ECUDA, MISR_ENOTIMPL. */
 misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out);
 
