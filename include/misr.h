@@ -154,6 +154,23 @@ misr_status misr_solve_host(misr_plan_t plan, const void *y_host, float *x_host,
  * Synchronises with the plan's last solve. */
 misr_status misr_get_trace(misr_plan_t plan, double *out, int32_t max_rows, int32_t *rows);
 
+/* Allocation-free objective and gradient.  The paper has no counterpart: this is an
+ * interface addition of the library.  It returns the same J(x) and grad J(x) as
+ * misr_gradient for the problem in desc, without a plan and without allocating any device
+ * memory.  It is for callers that cannot call cudaMalloc: a process whose device memory is
+ * already fully reserved by another allocator (a framework's caching pool, a detector
+ * pipeline that reserves all its buffers up front), or a time-critical acquisition loop
+ * that cannot afford the implicit device synchronisation of cudaMalloc / cudaFree.
+ * The workspace is a fixed array inside the library, sized for HR images of at most
+ * 512 x 512 pixels (about 7 MB, held on every GPU that loads the library until the process
+ * exits); larger problems return MISR_EINVAL.  The first call on a device looks up the
+ * array's device address and sets the pass kernel's attributes; make that first call before
+ * any stream capture.  Every call uses the same array, so calls that overlap on the GPU
+ * (other streams or host threads) race.  y_dev, x_dev, g_dev as for misr_gradient.
+ * Blocking: g_dev and *J_out (may be NULL) are valid on return. */
+misr_status misr_gradient_noalloc(const misr_desc *desc, const void *y_dev, const float *x_dev, float *g_dev,
+                                  double *J_out, misr_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -514,3 +515,177 @@ misr_status misr_get_trace(misr_plan_t p, double *out, int32_t max_rows, int32_t
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free objective/gradient (misr_gradient_noalloc).
+//
+// For callers that must not allocate device memory at all: a process whose device memory
+// is already reserved by another allocator (a framework's caching pool or a detector
+// pipeline that pre-reserves every byte), where cudaMalloc would fail or would force a
+// device-wide synchronisation in the middle of a time-critical acquisition loop.  The
+// workspace lives in the file-scope array below, sized for HR images up to
+// NOALLOC_MAX_H x NOALLOC_MAX_W; every GPU that loads this library holds it until the
+// process exits.  All calls share it, so calls that overlap on the GPU (other streams,
+// other host threads) race.
+namespace {
+
+constexpr size_t na_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr int NOALLOC_MAX_H = 512, NOALLOC_MAX_W = 512;
+constexpr size_t NOALLOC_IMG = na_align(size_t(NOALLOC_MAX_H) * NOALLOC_MAX_W * sizeof(float), 256);
+constexpr int NOALLOC_MAX_TILES = ((NOALLOC_MAX_H + TILE_H - 1) / TILE_H) * ((NOALLOC_MAX_W + TILE_W - 1) / TILE_W);
+constexpr int NOALLOC_GROUP = 64;
+constexpr int NOALLOC_MAX_GROUPS = (NOALLOC_MAX_TILES + NOALLOC_GROUP - 1) / NOALLOC_GROUP;
+constexpr size_t NA_O_IMG = 0;
+constexpr size_t NA_O_PART = NA_O_IMG + 7 * NOALLOC_IMG;
+constexpr size_t NA_O_GPART = NA_O_PART + na_align(size_t(NOALLOC_MAX_TILES) * NPART * sizeof(double), 256);
+constexpr size_t NA_O_GCNT = NA_O_GPART + na_align(size_t(NOALLOC_MAX_GROUPS) * NPART * sizeof(double), 256);
+constexpr size_t NA_O_CNT = NA_O_GCNT + na_align(size_t(NOALLOC_MAX_GROUPS) * sizeof(unsigned int), 256);
+constexpr size_t NA_O_ST = NA_O_CNT + 256;
+constexpr size_t NA_O_PROB = NA_O_ST + na_align(sizeof(ScgState), 256);
+constexpr size_t NA_O_TMAP = NA_O_PROB + na_align(sizeof(DevProblem), 256);
+constexpr size_t NOALLOC_BYTES = NA_O_TMAP + na_align(size_t(NOALLOC_MAX_TILES) * sizeof(int2), 256);
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;   // device address of g_noalloc_scratch on this device
+};
+constexpr int NOALLOC_MAX_DEVICES = 64;
+NoallocDevice g_noalloc_devices[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mutex;
+
+// Once per device, with that device current: the device address of the scratch array (the
+// host-side symbol is only a stand-in) and the fused pass's shared-memory attributes.
+misr_status noalloc_setup(unsigned char **base) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(MISR_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocDevice &d = g_noalloc_devices[dev];
+    if (!d.ready) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(MISR_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
+        CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
+                                cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        d.base = static_cast<unsigned char *>(ptr);
+        d.ready = true;
+    }
+    *base = d.base;
+    return MISR_OK;
+}
+
+// The problem record of the descriptor with its buffers inside the scratch array.
+misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem &hp) {
+    const int f = d.factor;
+    hp = DevProblem{};
+    hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
+    hp.H = f * d.lr_h; hp.W = f * d.lr_w;
+    hp.pitch = (hp.W + 3) & ~3;
+    hp.iters = 0;
+    for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
+    for (int k = 0; k < d.K; ++k) {
+        const double tx = (double)f * d.shifts[2 * k], ty = (double)f * d.shifts[2 * k + 1];
+        const double rx = std::floor(tx + 0.5), ry = std::floor(ty + 0.5);
+        if (std::fabs(tx - rx) > 1e-4 || std::fabs(ty - ry) > 1e-4)
+            return fail(MISR_ENOTIMPL, "frame %d: shift times factor is not an integer (subpixel HR warps not supported)", k);
+        if (rx < 0 || rx > f - 1 || ry < 0 || ry > f - 1)
+            return fail(MISR_EINVAL, "frame %d: shift must lie in [0, 1 - 1/f] LR px", k);
+        const int ph = (int)ry * f + (int)rx;
+        if (hp.frame_of_phase[ph] >= 0) return fail(MISR_EINVAL, "frames %d and %d sample the same HR phase", hp.frame_of_phase[ph], k);
+        hp.frame_of_phase[ph] = k;
+        hp.ty[k] = (int)ry; hp.tx[k] = (int)rx;
+    }
+    misr_status s = psf_taps(&d, hp.hy, hp.hx);
+    if (s != MISR_OK) return s;
+    hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
+    double eps_pairs = 0;
+    for (int dy = 0; dy < BTV_W; ++dy)
+        for (int dx = 0; dx < BTV_W; ++dx) {
+            const int dd = dy * BTV_W + dx;
+            float g = 0.f;
+            if (dd != 0 && dx < d.btv_w && dy < d.btv_w) g = (float)std::pow(d.btv_alpha, dx + dy);
+            hp.gamma[dd] = g;
+            if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
+        }
+    hp.eps_pairs = d.eps * eps_pairs;
+    hp.tiles_y = (hp.H + TILE_H - 1) / TILE_H;
+    hp.tiles_x = (hp.W + TILE_W - 1) / TILE_W;
+    hp.n_tiles = hp.tiles_y * hp.tiles_x;
+    hp.group = NOALLOC_GROUP;
+    hp.n_groups = (hp.n_tiles + hp.group - 1) / hp.group;
+    for (int i = 0; i < 2; ++i) {
+        hp.X[i] = reinterpret_cast<float *>(base + NA_O_IMG + (0 + i) * NOALLOC_IMG);
+        hp.Rv[i] = reinterpret_cast<float *>(base + NA_O_IMG + (2 + i) * NOALLOC_IMG);
+        hp.Pv[i] = reinterpret_cast<float *>(base + NA_O_IMG + (4 + i) * NOALLOC_IMG);
+    }
+    hp.Y = reinterpret_cast<float *>(base + NA_O_IMG + 6 * NOALLOC_IMG);
+    hp.partials = reinterpret_cast<double *>(base + NA_O_PART);
+    hp.gpartials = reinterpret_cast<double *>(base + NA_O_GPART);
+    hp.gcount = reinterpret_cast<unsigned int *>(base + NA_O_GCNT);
+    hp.counter = reinterpret_cast<unsigned int *>(base + NA_O_CNT);
+    hp.st = reinterpret_cast<ScgState *>(base + NA_O_ST);
+    hp.trace = nullptr;
+    s = get_encode_tiled();
+    for (int i = 0; i < 2 && s == MISR_OK; ++i) {
+        s = make_map(&hp.tmX[i], hp.X[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
+        if (s == MISR_OK) s = make_map(&hp.tmR[i], hp.Rv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
+        if (s == MISR_OK) s = make_map(&hp.tmP[i], hp.Pv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
+    }
+    if (s == MISR_OK) s = make_map(&hp.tmY, hp.Y, hp.W, hp.H, hp.pitch, PassGeo::EW, PassGeo::EH, true);
+    return s;
+}
+
+}  // namespace
+
+extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *y_dev, const float *x_dev,
+                                             float *g_dev, double *J_out, misr_stream_t stream) {
+    if (!y_dev || !x_dev || !g_dev) return fail(MISR_EINVAL, "NULL argument");
+    misr_status s = validate(desc);
+    if (s != MISR_OK) return s;
+    const int H = desc->factor * desc->lr_h, W = desc->factor * desc->lr_w;
+    if (H > NOALLOC_MAX_H || W > NOALLOC_MAX_W)
+        return fail(MISR_EINVAL, "HR image %d x %d exceeds the allocation-free limit %d x %d", H, W, NOALLOC_MAX_H,
+                    NOALLOC_MAX_W);
+    unsigned char *base = nullptr;
+    s = noalloc_setup(&base);
+    if (s != MISR_OK) return s;
+    DevProblem hp;
+    s = noalloc_problem(*desc, base, hp);
+    if (s != MISR_OK) return s;
+    int2 tiles[NOALLOC_MAX_TILES];
+    for (int t = 0; t < hp.n_tiles; ++t) tiles[t] = make_int2(0, t);
+    DevProblem *dprob = reinterpret_cast<DevProblem *>(base + NA_O_PROB);
+    int2 *dtile = reinterpret_cast<int2 *>(base + NA_O_TMAP);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(dprob, &hp, sizeof(DevProblem), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dtile, tiles, sizeof(int2) * hp.n_tiles, cudaMemcpyHostToDevice, st));
+    // the pass's group counters and pass counter must start at zero
+    CK(cudaMemsetAsync(hp.gcount, 0, sizeof(unsigned int) * hp.n_groups, st));
+    CK(cudaMemsetAsync(hp.counter, 0, sizeof(unsigned int), st));
+    const float log_i0 = desc->in_dtype == MISR_U16 ? logf(desc->flat_field) : 0.f;
+    const size_t npitched = (size_t)hp.H * hp.pitch, n = (size_t)hp.H * hp.W;
+    // x_1 = x (given), r = p_old = 0, state reset; then one pass with alpha = beta = 0
+    prepare_kernel<<<grid_for(npitched, 256), 256, 0, st>>>(dprob, 0, y_dev, desc->in_dtype, log_i0, x_dev,
+                                                           MISR_X0_GIVEN, 1 | 2 | 4);
+    CK(cudaGetLastError());
+    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<hp.n_tiles, PASS_NT, PassGeo::SMEM_BYTES, st>>>(
+        dprob, dtile, MODE_PROBE, 0.0, 0.0, resident_ctas());
+    CK(cudaGetLastError());
+    scale_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(hp.Rv[1], hp.pitch, -1.f, g_dev, hp.H, hp.W);
+    CK(cudaGetLastError());
+    ScgState hst;
+    CK(cudaMemcpyAsync(&hst, hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hst.status != DEV_OK) return fail(MISR_ETIMEOUT, "a tile load of the fused pass did not complete in time");
+    if (J_out) *J_out = hst.sums[P_JD] + (double)hp.lambda * (hst.sums[P_JB] - hp.eps_pairs);
+    return MISR_OK;
+}
