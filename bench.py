@@ -68,7 +68,7 @@ def load_traffic(kernel_tag):
 def kernel_source_tag():
     import hashlib
     h = hashlib.sha1()
-    for f in ("misr_device.cuh", "misr_api.cu"):
+    for f in ("misr_device.cuh", "tma.cuh", "misr_api.cu"):
         with open(os.path.join(ROOT, "paper_2108_04315_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -304,7 +304,7 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": load_traffic(kernel_source_tag()),
-                     "kernel": "scg_pass_kernel<32,64,256>", "peak_kind": peak_kind,
+                     "kernel": "scg_pass_kernel<32,64,512>", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": PASS_BYTES_PER_PX * H * W,
                      "ms_per_launch": pass_ms},
         "e2e": e2e,
