@@ -154,6 +154,29 @@ misr_status misr_solve_host(misr_plan_t plan, const void *y_host, float *x_host,
  * Synchronises with the plan's last solve. */
 misr_status misr_get_trace(misr_plan_t plan, double *out, int32_t max_rows, int32_t *rows);
 
+/* ---- Batched solves (many projections per launch) ---------------------------------------
+ * A batch groups plans (uneven sizes, factors and frame counts are fine; all on one device) so
+ * that every SCG step of all of them is one fused-pass launch over the tiles of all projections,
+ * replayed as a CUDA graph.  The CT setting of Sec. 3.2 produces one independent projection per
+ * rotation angle; a batch advances many of them at once.  Each projection keeps its own
+ * workspace, SCG state and fixed-order reductions, so its result equals its own misr_solve.
+ * A plan may belong to several batches but runs one solve at a time. */
+typedef struct misr_batch_s *misr_batch_t;
+
+/* Build the batch tables (problem records and the combined tile map) on the plans' device.
+ * plans: n plans (host array, copied).  Errors: MISR_EINVAL, MISR_ENOMEM, MISR_ECUDA. */
+misr_status misr_batch_create(int32_t n, const misr_plan_t *plans, misr_batch_t *out);
+
+/* Synchronise and free the batch tables (the plans stay).  NULL is accepted. */
+misr_status misr_batch_destroy(misr_batch_t batch);
+
+/* Solve every projection of the batch: y_dev[i] (K_i frames, the plan's in_dtype) to x_dev[i]
+ * (HR float32; also the start point of plans with MISR_X0_GIVEN).  Each projection runs its own
+ * plan's iteration count.  Asynchronous on stream unless stats (n entries) is non-NULL, in
+ * which case the call synchronises and fills stats[i] for plan i. */
+misr_status misr_batch_solve(misr_batch_t batch, const void *const *y_dev, float *const *x_dev,
+                             misr_stream_t stream, misr_stats *stats);
+
 /* Allocation-free objective and gradient.  The paper has no counterpart: this is an
  * interface addition of the library.  It returns the same J(x) and grad J(x) as
  * misr_gradient for the problem in desc, without a plan and without allocating any device

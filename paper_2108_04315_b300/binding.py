@@ -71,8 +71,12 @@ def lib():
         L.misr_solve.argtypes = [VP, VP, VP, VP, C.POINTER(misr_stats)]
         L.misr_solve_host.argtypes = [VP, VP, VP, C.POINTER(misr_stats)]
         L.misr_get_trace.argtypes = [VP, DP, C.c_int32, C.POINTER(C.c_int32)]
+        L.misr_batch_create.argtypes = [C.c_int32, C.POINTER(VP), C.POINTER(VP)]
+        L.misr_batch_destroy.argtypes = [VP]
+        L.misr_batch_solve.argtypes = [VP, C.POINTER(VP), C.POINTER(VP), VP, C.POINTER(misr_stats)]
         for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_forward",
-                     "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_get_trace"):
+                     "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_get_trace",
+                     "misr_batch_create", "misr_batch_destroy", "misr_batch_solve"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -146,6 +150,26 @@ def misr_get_trace(plan: int, max_rows: int):
     _check(lib().misr_get_trace(VP(plan), buf.ctypes.data_as(DP), int(max_rows), C.byref(rows)), "misr_get_trace")
     buf = buf[: rows.value]
     return {k: buf[:, i].copy() for i, k in enumerate(TRACE_FIELDS)}
+
+
+def misr_batch_create(plans) -> int:
+    arr = (VP * len(plans))(*[VP(p) for p in plans])
+    h = VP()
+    _check(lib().misr_batch_create(len(plans), arr, C.byref(h)), "misr_batch_create")
+    return h.value
+
+
+def misr_batch_destroy(batch: int) -> None:
+    _check(lib().misr_batch_destroy(VP(batch)), "misr_batch_destroy")
+
+
+def misr_batch_solve(batch: int, y_devs, x_devs, stream: int = 0, want_stats: bool = True):
+    n = len(y_devs)
+    ya = (VP * n)(*[VP(v) for v in y_devs])
+    xa = (VP * n)(*[VP(v) for v in x_devs])
+    st = (misr_stats * n)()
+    _check(lib().misr_batch_solve(VP(batch), ya, xa, VP(stream), st if want_stats else None), "misr_batch_solve")
+    return [_stats_dict(st[i]) for i in range(n)] if want_stats else None
 
 
 def _stats_dict(st: misr_stats):
@@ -244,3 +268,30 @@ class Plan:
 
     def trace(self):
         return misr_get_trace(self.handle, self.iters)
+
+
+class Batch:
+    """Plans solved together: one fused-pass launch per SCG step over all of their tiles."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self.handle = misr_batch_create([p.handle for p in self.plans])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            misr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, ys, xs=None, stream=None, stats=True):
+        import torch
+        if xs is None:
+            xs = [torch.empty((p.H, p.W), dtype=torch.float32, device=y.device) for p, y in zip(self.plans, ys)]
+        st = misr_batch_solve(self.handle, [Plan._ptr(y) for y in ys], [Plan._ptr(x, torch.float32) for x in xs],
+                              _stream_handle(stream), stats)
+        return xs, st

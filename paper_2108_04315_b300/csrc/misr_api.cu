@@ -16,14 +16,16 @@
 
 #include "misr.h"
 #include "misr_device.cuh"
+#include "misr_internal.h"
 
 using namespace misr;
+using namespace misr_host;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
-misr_status fail(misr_status s, const char *fmt, ...) {
+misr_status misr_host::fail(misr_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -33,30 +35,11 @@ misr_status fail(misr_status s, const char *fmt, ...) {
     return s;
 }
 
-#define CK(call)                                                                        \
-    do {                                                                                \
-        cudaError_t e_ = (call);                                                        \
-        if (e_ != cudaSuccess) return fail(MISR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
+namespace {
 
 // the tile shape of the fused pass
 constexpr int TILE_H = 32, TILE_W = 64, PASS_NT = 512;
 using PassGeo = Geo<TILE_H, TILE_W>;
-// passes captured per CUDA graph replay
-constexpr int GRAPH_CHUNK = 50;
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int now = -1;
-        cudaGetDevice(&now);
-        if (prev >= 0 && now != prev) cudaSetDevice(prev);
-    }
-};
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -91,25 +74,6 @@ misr_status make_map(CUtensorMap *m, float *base, int W, int H, int pitch, int b
 
 }  // namespace
 
-struct misr_plan_s {
-    int device = 0;
-    misr_desc d{};
-    DevProblem hp{};              // host mirror of the device problem record
-    DevProblem *dprob = nullptr;  // device problem record
-    int2 *dtile = nullptr;        // tile map of the fused pass
-    char *ws = nullptr;           // one allocation for everything above and below
-    size_t ws_bytes = 0;
-    size_t n = 0, m_total = 0;    // HR pixels, LR samples of all frames
-    size_t n_pitched = 0;         // H * pitch
-    cudaStream_t cap = nullptr;   // private stream used for graph capture
-    cudaGraphExec_t chunk = nullptr;
-    int chunk_len = 0;
-    cudaEvent_t done_ev = nullptr;
-    bool solved = false;
-    ScgState *st_host = nullptr;  // page-locked copy of the state
-    void *io_y = nullptr;         // device buffers of misr_solve_host
-    float *io_x = nullptr;
-};
 
 static misr_status validate(const misr_desc *d) {
     if (!d) return fail(MISR_EINVAL, "desc is NULL");
@@ -189,7 +153,7 @@ static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double bet
     return MISR_OK;
 }
 
-static int grid_for(size_t n, int threads) {
+int misr_host::grid_for(size_t n, int threads) {
     size_t b = (n + threads - 1) / threads;
     return (int)std::min<size_t>(std::max<size_t>(b, 1), 148 * 16);
 }
@@ -199,6 +163,33 @@ static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float 
     const float log_i0 = p->d.in_dtype == MISR_U16 ? logf(p->d.flat_field) : 0.f;
     prepare_kernel<<<grid_for(p->n_pitched, 256), 256, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, x_given,
                                                        p->d.x0_mode, flags);
+    CK(cudaGetLastError());
+    return MISR_OK;
+}
+
+misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, int ntiles, int mode,
+                                       double alpha, double beta, cudaStream_t s) {
+    if (ntiles <= 0) return MISR_OK;
+    misr_status r = set_pass_attrs();
+    if (r != MISR_OK) return r;
+    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<ntiles, PASS_NT, PassGeo::SMEM_BYTES, s>>>(probs, tiles, mode, alpha,
+                                                                                         beta, resident_ctas());
+    CK(cudaGetLastError());
+    return MISR_OK;
+}
+
+misr_status misr_host::launch_prepare_raw(const DevProblem *probs, int pidx, const misr_desc &d, size_t n_pitched,
+                                          const void *y_dev, const float *x_given, int x0_mode, int flags,
+                                          cudaStream_t s) {
+    const float log_i0 = d.in_dtype == MISR_U16 ? logf(d.flat_field) : 0.f;
+    prepare_kernel<<<grid_for(n_pitched, 256), 256, 0, s>>>(probs, pidx, y_dev, d.in_dtype, log_i0, x_given, x0_mode,
+                                                            flags);
+    CK(cudaGetLastError());
+    return MISR_OK;
+}
+
+misr_status misr_host::launch_finalize_raw(const DevProblem *probs, int pidx, size_t n, float *out, cudaStream_t s) {
+    finalize_kernel<<<grid_for(n, 256), 256, 0, s>>>(probs, pidx, out);
     CK(cudaGetLastError());
     return MISR_OK;
 }

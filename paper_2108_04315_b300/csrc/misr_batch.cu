@@ -1,0 +1,153 @@
+// Batched SCG solves: many independent projections (uneven sizes, magnification factors and
+// frame counts) advanced together, one fused-pass launch per SCG step over the tiles of all of
+// them, the step loop replayed as a CUDA graph.  Each projection keeps its own plan workspace,
+// SCG state and fixed-order reductions, so its result is the same alone and in a batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "misr.h"
+#include "misr_internal.h"
+
+using namespace misr;
+using namespace misr_host;
+
+struct misr_batch_s {
+    int device = 0;
+    int n = 0;
+    std::vector<misr_plan_t> plans;
+    DevProblem *dprobs = nullptr;   // n problem records (copies of the plans' records)
+    int2 *dtiles = nullptr;         // tiles of all problems, problem after problem
+    void *mem = nullptr;
+    int total_tiles = 0;
+    int max_iters = 0;
+    cudaStream_t cap = nullptr;     // private stream used for graph capture
+    cudaGraphExec_t chunk = nullptr;
+    int chunk_len = 0;
+    ScgState *st_host = nullptr;    // n page-locked states
+};
+
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+extern "C" misr_status misr_batch_destroy(misr_batch_t b) {
+    if (!b) return MISR_OK;
+    DeviceGuard g(b->device);
+    cudaDeviceSynchronize();
+    if (b->chunk) cudaGraphExecDestroy(b->chunk);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->st_host) cudaFreeHost(b->st_host);
+    if (b->mem) cudaFree(b->mem);
+    delete b;
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_batch_create(int32_t n, const misr_plan_t *plans, misr_batch_t *out) {
+    if (!out) return fail(MISR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !plans) return fail(MISR_EINVAL, "a batch needs n >= 1 plans");
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return fail(MISR_EINVAL, "plan %d is NULL", i);
+        if (plans[i]->device != plans[0]->device) return fail(MISR_EINVAL, "plans %d and 0 are on different devices", i);
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return fail(MISR_EINVAL, "plan %d appears twice (a plan holds one solve)", i);
+    }
+    misr_batch_t b = new (std::nothrow) misr_batch_s();
+    if (!b) return fail(MISR_ENOMEM, "host allocation failed");
+    b->device = plans[0]->device;
+    b->n = n;
+    b->plans.assign(plans, plans + n);
+    std::vector<DevProblem> recs(n);
+    std::vector<int2> tiles;
+    for (int i = 0; i < n; ++i) {
+        recs[i] = plans[i]->hp;
+        for (int t = 0; t < plans[i]->hp.n_tiles; ++t) tiles.push_back(make_int2(i, t));
+        b->max_iters = std::max(b->max_iters, plans[i]->d.iters);
+    }
+    b->total_tiles = (int)tiles.size();
+    DeviceGuard g(b->device);
+    const size_t rec_bytes = round_up(sizeof(DevProblem) * n, 256);
+    cudaError_t e = cudaMalloc(&b->mem, rec_bytes + sizeof(int2) * tiles.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(MISR_ENOMEM, "cudaMalloc for the batch tables failed: %s", cudaGetErrorString(e));
+    }
+    b->dprobs = static_cast<DevProblem *>(b->mem);
+    b->dtiles = reinterpret_cast<int2 *>(static_cast<char *>(b->mem) + rec_bytes);
+    do {
+        if ((e = cudaMemcpy(b->dprobs, recs.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(b->dtiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaMallocHost((void **)&b->st_host, sizeof(ScgState) * n)) != cudaSuccess) break;
+    } while (0);
+    if (e != cudaSuccess) {
+        misr_status r = fail(MISR_ECUDA, "batch setup: %s", cudaGetErrorString(e));
+        misr_batch_destroy(b);
+        return r;
+    }
+    *out = b;
+    return MISR_OK;
+}
+
+static misr_status batch_graph(misr_batch_t b) {
+    const int want = std::max(1, std::min(b->max_iters, GRAPH_CHUNK));
+    if (b->chunk && b->chunk_len == want) return MISR_OK;
+    if (b->chunk) { cudaGraphExecDestroy(b->chunk); b->chunk = nullptr; }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    misr_status r = MISR_OK;
+    for (int i = 0; i < want && r == MISR_OK; ++i)
+        r = launch_pass_raw(b->dprobs, b->dtiles, b->total_tiles, MODE_ITER, 0.0, 0.0, b->cap);
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (r != MISR_OK) { if (graph) cudaGraphDestroy(graph); return r; }
+    if (e != cudaSuccess) return fail(MISR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->chunk, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MISR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    b->chunk_len = want;
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_batch_solve(misr_batch_t b, const void *const *y_dev, float *const *x_dev,
+                                        misr_stream_t stream, misr_stats *stats) {
+    if (!b || !y_dev || !x_dev) return fail(MISR_EINVAL, "NULL argument");
+    for (int i = 0; i < b->n; ++i)
+        if (!y_dev[i] || !x_dev[i]) return fail(MISR_EINVAL, "NULL frame or image pointer for projection %d", i);
+    DeviceGuard g(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    misr_status r = batch_graph(b);
+    if (r != MISR_OK) return r;
+    for (int i = 0; i < b->n && r == MISR_OK; ++i) {
+        const misr_plan_t p = b->plans[i];
+        r = launch_prepare_raw(b->dprobs, i, p->d, p->n_pitched, y_dev[i], x_dev[i], p->d.x0_mode, 1 | 2 | 4, s);
+    }
+    if (r == MISR_OK) r = launch_pass_raw(b->dprobs, b->dtiles, b->total_tiles, MODE_INIT, 0.0, 0.0, s);
+    if (r != MISR_OK) return r;
+    for (int done = 0; done < b->max_iters; done += b->chunk_len) CK(cudaGraphLaunch(b->chunk, s));
+    for (int i = 0; i < b->n && r == MISR_OK; ++i) r = launch_finalize_raw(b->dprobs, i, b->plans[i]->n, x_dev[i], s);
+    if (r != MISR_OK) return r;
+    for (int i = 0; i < b->n; ++i) {
+        CK(cudaEventRecord(b->plans[i]->done_ev, s));
+        b->plans[i]->solved = true;
+    }
+    if (!stats) return MISR_OK;
+    for (int i = 0; i < b->n; ++i)
+        CK(cudaMemcpyAsync(&b->st_host[i], b->plans[i]->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    misr_status worst = MISR_OK;
+    for (int i = 0; i < b->n; ++i) {
+        const ScgState &h = b->st_host[i];
+        stats[i].iters_done = h.iter;
+        stats[i].accepted = h.accepted;
+        stats[i].status = h.status == DEV_OK ? MISR_OK : MISR_ETIMEOUT;
+        stats[i].reserved = 0;
+        stats[i].J_final = h.E;
+        stats[i].rnorm2 = h.rn2;
+        stats[i].lambda_scg = h.lam;
+        if (stats[i].status != MISR_OK) worst = MISR_ETIMEOUT;
+    }
+    if (worst != MISR_OK) return fail(worst, "a tile load of the fused pass did not complete in time");
+    return MISR_OK;
+}

@@ -1,21 +1,5 @@
 // Device code of the sm_103a MISR solver: the fused SCG pass, its scalar tail, and the
-// prepare / forward / finalize kernels.
-//
-// Model (Sec. 3.1 of the paper): y_k = D B M_k x (Eq. 1), J(x) = sum_k ||A_k x - y_k||^2 +
-// lambda * BTV(x) (Eq. 6, 8, 9), solved with Moller's scaled conjugate gradient (Algorithm 1).
-//
-// Layout of the data term on the HR grid.  Every frame k is shifted by an integer HR offset
-// t_k in [0, f-1]^2, so its samples sit at HR pixels c = (f i + t_y, f j + t_x), and the
-// phase (c_y mod f, c_x mod f) of a sample equals its frame's shift.  With one frame per
-// phase, the K frames interleave into one HR image Y (NaN where no frame samples) and
-//   A_k x (i, j) = (B_c x)(c),   B_c: convolution with the PSF whose taps that read x at a
-//                                row < (c_y mod f) or a column < (c_x mod f) are dropped
-// (the zero padding of B in front of the shift M_k; it only matters within f + R pixels of
-// the top/left border).  So the data term of all K frames is one HR blur, one residual image
-// E = B x - Y and one adjoint blur B^T E, whatever K is.
-//
-// HR images in the workspace are row-major with a row pitch that is a multiple of 4 floats,
-// so that every row starts on a 16-byte boundary (TMA boxes, float4 stores).
+// prepare / forward / finalize kernels.  Included by exactly one translation unit.
 #pragma once
 
 #include <cuda.h>
@@ -25,61 +9,10 @@
 
 #include <type_traits>
 
+#include "misr_types.cuh"
 #include "tma.cuh"
 
 namespace misr {
-
-constexpr int MAXK = 64;
-constexpr int MAXF = 8;
-constexpr int PSF_R = 2;   // compiled PSF radius (5x5 taps); smaller PSFs are zero-padded
-constexpr int BTV_W = 3;   // compiled BTV window; smaller windows get gamma = 0
-constexpr int NPART = 10;
-constexpr int TRACE_COLS = 10;
-constexpr uint32_t TMA_WAIT_TRIES = 1u << 24;   // bounded wait for the tile loads
-
-// per-tile partial sums of one pass (FP64)
-enum { P_JD = 0, P_DJD, P_JB, P_RR, P_RRX, P_PR, P_PP, P_A, P_B, P_C };
-enum { MODE_INIT = 0, MODE_ITER = 1, MODE_PROBE = 2 };
-// device status codes (ScgState::status)
-enum { DEV_OK = 0, DEV_TMA_TIMEOUT = 1 };
-
-// Moller's SCG scalars of one projection, kept on the device between passes.
-struct ScgState {
-    double E;         // J(x_k)
-    double E_btv;     // lambda * R(x_k)
-    double lam, lam_bar;
-    double delta;     // scaled curvature in effect for the coming step
-    double mu;        // p_k . r_k
-    double pn2;       // |p_k|^2
-    double alpha;     // step of the coming pass
-    double beta;      // p_k = r_k + beta * p_{k-1}, applied inside the coming pass
-    double rn2;       // |r_k|^2
-    double sums[NPART];
-    int cur, pcur;    // which half of the X/R and P double buffers holds x_k, r_k / p_{k-1}
-    int success, iter, accepted, done, status, iters;
-    float alpha_f, beta_f;   // alpha and beta rounded once for the FP32 pass
-};
-
-struct DevProblem {
-    CUtensorMap tmX[2], tmR[2], tmP[2], tmY;      // TMA maps of the workspace images
-    int H, W, pitch, f, h, w, K;
-    int tiles_x, tiles_y, n_tiles, iters, pad0;
-    float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];  // separable PSF, h(a, b) = hy[a+R] hx[b+R]
-    float lambda, eps, eps2, pad1;
-    float gamma[BTV_W * BTV_W];                   // gamma(dx, dy) at [dy * BTV_W + dx]
-    double eps_pairs;                             // eps * sum_d gamma_d * #pairs_d
-    float *X[2], *Rv[2], *Pv[2];                  // x, r (double buffered), p (double buffered)
-    float *Y;                                     // interleaved frames, NaN where unsampled
-    double *partials;                             // [n_tiles][NPART] per-tile sums
-    double *gpartials;                            // [n_groups][NPART] per-group sums
-    unsigned int *gcount;                         // [n_groups] tiles of the group finished
-    unsigned int *counter;                        // groups finished in the current pass
-    int group, n_groups;                          // tiles per group, number of groups
-    ScgState *st;
-    double *trace;                                // [iters][TRACE_COLS]
-    int ty[MAXK], tx[MAXK];
-    int frame_of_phase[MAXF * MAXF];              // -1: no frame samples that phase
-};
 
 __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }

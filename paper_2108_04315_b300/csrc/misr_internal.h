@@ -1,0 +1,68 @@
+// Host-side internals shared by the translation units of the library: the plan record, error
+// reporting and the launch helpers of the kernels (which live in misr_api.cu only, so that
+// every kernel has one copy and one set of attributes).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "misr.h"
+#include "misr_types.cuh"
+
+namespace misr_host {
+
+// record a thread-local error text and return s
+misr_status fail(misr_status s, const char *fmt, ...);
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return misr_host::fail(MISR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// passes captured per CUDA graph replay
+constexpr int GRAPH_CHUNK = 50;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+int grid_for(size_t n, int threads);
+// one fused SCG pass over `ntiles` tiles of the problems in `probs` (tile map `tiles`)
+misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, int ntiles, int mode, double alpha,
+                            double beta, cudaStream_t s);
+// prepare problem `pidx` of `probs`: interleave frames, start point, reset (flags as prepare_kernel)
+misr_status launch_prepare_raw(const misr::DevProblem *probs, int pidx, const misr_desc &d, size_t n_pitched,
+                               const void *y_dev, const float *x_given, int x0_mode, int flags, cudaStream_t s);
+// copy problem `pidx`'s iterate out (dense H x W)
+misr_status launch_finalize_raw(const misr::DevProblem *probs, int pidx, size_t n, float *out, cudaStream_t s);
+
+}  // namespace misr_host
+
+struct misr_plan_s {
+    int device = 0;
+    misr_desc d{};
+    misr::DevProblem hp{};              // host mirror of the device problem record
+    misr::DevProblem *dprob = nullptr;  // device problem record
+    int2 *dtile = nullptr;              // tile map of the fused pass
+    char *ws = nullptr;                 // one allocation for everything above and below
+    size_t ws_bytes = 0;
+    size_t n = 0, m_total = 0;          // HR pixels, LR samples of all frames
+    size_t n_pitched = 0;               // H * pitch
+    cudaStream_t cap = nullptr;         // private stream used for graph capture
+    cudaGraphExec_t chunk = nullptr;
+    int chunk_len = 0;
+    cudaEvent_t done_ev = nullptr;
+    bool solved = false;
+    misr::ScgState *st_host = nullptr;  // page-locked copy of the state
+    void *io_y = nullptr;               // device buffers of misr_solve_host
+    float *io_x = nullptr;
+};
