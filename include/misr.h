@@ -177,6 +177,53 @@ misr_status misr_batch_destroy(misr_batch_t batch);
 misr_status misr_batch_solve(misr_batch_t batch, const void *const *y_dev, float *const *x_dev,
                              misr_stream_t stream, misr_stats *stats);
 
+/* ---- Serving: continuous batching of projections as an acquisition produces them ----------
+ * The CT setting of Sec. 3.2 reconstructs each rotation angle while the scan goes on.  A
+ * server owns a worker thread, a private stream and a pool of slots.  A slot is a plan (its
+ * workspace and its device-resident SCG state) of one geometry class.  Requests are admitted in
+ * arrival order into free slots of their class.  A new slot is created when its workspace fits
+ * the HBM budget, and idle slots of other classes are freed to make room.  Every tick runs
+ * passes_per_tick fused-pass launches over the tiles of all live slots (one SCG iteration per
+ * launch for each), so a request that arrives while others are on the GPU joins the next
+ * launch.  Finished projections are copied out and their slots reused.  Each projection keeps
+ * its own state and fixed-order reductions: its result is the same alone and in the mix. */
+typedef struct misr_server_s *misr_server_t;
+
+typedef struct misr_server_cfg {
+    int32_t max_slots;           /* most projections resident at once, 1..4096 */
+    int32_t passes_per_tick;     /* SCG iterations between admission rounds, 0 = 4 */
+    uint64_t hbm_budget_bytes;   /* > 0: slot workspaces use at most this many bytes */
+    uint64_t hbm_reserve_bytes;  /* budget 0: admit while free device memory exceeds this */
+} misr_server_cfg;
+
+/* Start a server on the current device.  Errors: MISR_EINVAL, MISR_ENOMEM. */
+misr_status misr_server_create(const misr_server_cfg *cfg, misr_server_t *out);
+
+/* Stop the worker after its current tick, then free every slot.  Requests still queued or
+ * running are dropped (their buffers are no longer touched after this returns).  NULL is
+ * accepted. */
+misr_status misr_server_destroy(misr_server_t server);
+
+/* Queue one projection: desc (copied; checked like misr_plan_create), y_dev its frames,
+ * x_dev the HR output (and the start point for MISR_X0_GIVEN).  Both device buffers must stay
+ * valid until misr_poll reports the ticket finished.  *ticket identifies the request. */
+misr_status misr_submit(misr_server_t server, const misr_desc *desc, const void *y_dev, float *x_dev,
+                        uint64_t *ticket);
+
+/* MISR_EAGAIN while the request is queued or running.  Once it finished: its status (MISR_OK,
+ * or the failure), *stats (may be NULL), times[3] = submit, start and end on the host's steady
+ * clock in seconds (may be NULL); the ticket is then forgotten (a further poll gives
+ * MISR_EINVAL). */
+misr_status misr_poll(misr_server_t server, uint64_t ticket, misr_stats *stats, double *times);
+
+/* Wait at most timeout_s seconds for the ticket to finish (then poll it).  MISR_OK when it
+ * finished, MISR_ETIMEOUT otherwise, MISR_EINVAL for an unknown ticket. */
+misr_status misr_server_wait(misr_server_t server, uint64_t ticket, double timeout_s);
+
+/* Counters: out[0] queued requests, out[1] running, out[2] slots, out[3] slot workspace bytes,
+ * out[4] fused-pass launches so far. */
+misr_status misr_server_counters(misr_server_t server, int64_t *out);
+
 /* Allocation-free objective and gradient.  The paper has no counterpart: this is an
  * interface addition of the library.  It returns the same J(x) and grad J(x) as
  * misr_gradient for the problem in desc, without a plan and without allocating any device

@@ -41,6 +41,11 @@ class misr_stats(C.Structure):
     ]
 
 
+class misr_server_cfg(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("passes_per_tick", C.c_int32),
+                ("hbm_budget_bytes", C.c_uint64), ("hbm_reserve_bytes", C.c_uint64)]
+
+
 class MisrError(RuntimeError):
     def __init__(self, status, where):
         self.status = int(status)
@@ -74,9 +79,16 @@ def lib():
         L.misr_batch_create.argtypes = [C.c_int32, C.POINTER(VP), C.POINTER(VP)]
         L.misr_batch_destroy.argtypes = [VP]
         L.misr_batch_solve.argtypes = [VP, C.POINTER(VP), C.POINTER(VP), VP, C.POINTER(misr_stats)]
+        L.misr_server_create.argtypes = [C.POINTER(misr_server_cfg), C.POINTER(VP)]
+        L.misr_server_destroy.argtypes = [VP]
+        L.misr_submit.argtypes = [VP, C.POINTER(misr_desc), VP, VP, C.POINTER(C.c_uint64)]
+        L.misr_poll.argtypes = [VP, C.c_uint64, C.POINTER(misr_stats), DP]
+        L.misr_server_wait.argtypes = [VP, C.c_uint64, C.c_double]
+        L.misr_server_counters.argtypes = [VP, C.POINTER(C.c_int64)]
         for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_forward",
                      "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_get_trace",
-                     "misr_batch_create", "misr_batch_destroy", "misr_batch_solve"):
+                     "misr_batch_create", "misr_batch_destroy", "misr_batch_solve", "misr_server_create",
+                     "misr_server_destroy", "misr_submit", "misr_poll", "misr_server_wait", "misr_server_counters"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -170,6 +182,45 @@ def misr_batch_solve(batch: int, y_devs, x_devs, stream: int = 0, want_stats: bo
     st = (misr_stats * n)()
     _check(lib().misr_batch_solve(VP(batch), ya, xa, VP(stream), st if want_stats else None), "misr_batch_solve")
     return [_stats_dict(st[i]) for i in range(n)] if want_stats else None
+
+
+def misr_server_create(max_slots: int, passes_per_tick: int = 0, hbm_budget_bytes: int = 0,
+                       hbm_reserve_bytes: int = 0) -> int:
+    cfg = misr_server_cfg(int(max_slots), int(passes_per_tick), int(hbm_budget_bytes), int(hbm_reserve_bytes))
+    h = VP()
+    _check(lib().misr_server_create(C.byref(cfg), C.byref(h)), "misr_server_create")
+    return h.value
+
+
+def misr_server_destroy(server: int) -> None:
+    _check(lib().misr_server_destroy(VP(server)), "misr_server_destroy")
+
+
+def misr_submit(server: int, desc: misr_desc, y_dev: int, x_dev: int) -> int:
+    t = C.c_uint64()
+    _check(lib().misr_submit(VP(server), C.byref(desc), VP(y_dev), VP(x_dev), C.byref(t)), "misr_submit")
+    return t.value
+
+
+def misr_poll(server: int, ticket: int):
+    """None while the request is pending; else (stats dict, (t_submit, t_start, t_end))."""
+    st = misr_stats()
+    times = np.zeros(3, dtype=np.float64)
+    rc = lib().misr_poll(VP(server), C.c_uint64(ticket), C.byref(st), times.ctypes.data_as(DP))
+    if rc == MISR_EAGAIN:
+        return None
+    _check(rc, "misr_poll")
+    return _stats_dict(st), tuple(float(v) for v in times)
+
+
+def misr_server_wait(server: int, ticket: int, timeout_s: float) -> None:
+    _check(lib().misr_server_wait(VP(server), C.c_uint64(ticket), float(timeout_s)), "misr_server_wait")
+
+
+def misr_server_counters(server: int) -> dict:
+    out = (C.c_int64 * 5)()
+    _check(lib().misr_server_counters(VP(server), out), "misr_server_counters")
+    return dict(zip(("queued", "running", "slots", "slot_bytes", "passes_launched"), list(out)))
 
 
 def _stats_dict(st: misr_stats):
@@ -295,3 +346,53 @@ class Batch:
         st = misr_batch_solve(self.handle, [Plan._ptr(y) for y in ys], [Plan._ptr(x, torch.float32) for x in xs],
                               _stream_handle(stream), stats)
         return xs, st
+
+
+class Server:
+    """Continuous-batching solver: submit projections as they arrive, poll or wait for results.
+    Frames and outputs are CUDA tensors that must stay alive until their ticket finishes."""
+
+    def __init__(self, max_slots=64, passes_per_tick=0, hbm_budget_bytes=0, hbm_reserve_bytes=0):
+        self.handle = misr_server_create(max_slots, passes_per_tick, hbm_budget_bytes, hbm_reserve_bytes)
+        self._live = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            misr_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, y, lr_h, lr_w, factor, shifts, psf, x_out=None, **kw):
+        import torch
+        desc = make_desc(lr_h, lr_w, factor, shifts, psf, **kw)
+        if x_out is None:
+            x_out = torch.empty((factor * lr_h, factor * lr_w), dtype=torch.float32, device=y.device)
+        # work queued on the caller's stream (e.g. the frames' upload) must be done first
+        torch.cuda.current_stream(y.device).synchronize()
+        t = misr_submit(self.handle, desc, Plan._ptr(y), Plan._ptr(x_out, torch.float32))
+        self._live[t] = (y, x_out)
+        return t
+
+    def poll(self, ticket):
+        try:
+            r = misr_poll(self.handle, ticket)
+        except MisrError:
+            self._live.pop(ticket, None)
+            raise
+        if r is None:
+            return None
+        y, x = self._live.pop(ticket)
+        return x, r[0], r[1]
+
+    def wait(self, ticket, timeout_s=60.0):
+        misr_server_wait(self.handle, ticket, timeout_s)
+        return self.poll(ticket)
+
+    def counters(self):
+        return misr_server_counters(self.handle)

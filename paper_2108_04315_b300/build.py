@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libmisr.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("misr_api.cu", "misr_batch.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("misr_api.cu", "misr_batch.cu", "misr_server.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h", ".cu"))] + \
     [os.path.join(INCLUDE, "misr.h")]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

@@ -194,6 +194,28 @@ misr_status misr_host::launch_finalize_raw(const DevProblem *probs, int pidx, si
     return MISR_OK;
 }
 
+// Every check misr_plan_create makes before allocating (descriptor, shifts, PSF).
+misr_status misr_host::check_desc(const misr_desc &d) {
+    misr_status s = validate(&d);
+    if (s != MISR_OK) return s;
+    const int f = d.factor;
+    int seen[MAXF * MAXF];
+    for (int i = 0; i < MAXF * MAXF; ++i) seen[i] = -1;
+    for (int k = 0; k < d.K; ++k) {
+        const double tx = (double)f * d.shifts[2 * k], ty = (double)f * d.shifts[2 * k + 1];
+        const double rx = std::floor(tx + 0.5), ry = std::floor(ty + 0.5);
+        if (std::fabs(tx - rx) > 1e-4 || std::fabs(ty - ry) > 1e-4)
+            return fail(MISR_ENOTIMPL, "frame %d: shift times factor is not an integer (subpixel HR warps not supported)", k);
+        if (rx < 0 || rx > f - 1 || ry < 0 || ry > f - 1)
+            return fail(MISR_EINVAL, "frame %d: shift must lie in [0, 1 - 1/f] LR px", k);
+        const int ph = (int)ry * f + (int)rx;
+        if (seen[ph] >= 0) return fail(MISR_EINVAL, "frames %d and %d sample the same HR phase", seen[ph], k);
+        seen[ph] = k;
+    }
+    float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];
+    return psf_taps(&d, hy, hx);
+}
+
 extern "C" {
 
 const char *misr_version(void) { return "misr-b300 0.2 (sm_103a, TMA-fed fused SCG pass 32x64)"; }

@@ -36,6 +36,8 @@ struct DeviceGuard {
 };
 
 int grid_for(size_t n, int threads);
+// every check misr_plan_create makes before allocating
+misr_status check_desc(const misr_desc &d);
 // one fused SCG pass over `ntiles` tiles of the problems in `probs` (tile map `tiles`)
 misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, int ntiles, int mode, double alpha,
                             double beta, cudaStream_t s);

@@ -1,0 +1,466 @@
+// Serving: a request loop that super-resolves projections as an acquisition produces them
+// (Sec. 3.2: each rotation angle's frames are reconstructed while the scan goes on).
+//
+// Continuous batching.  A worker thread owns a private stream and a pool of slots; a slot is a
+// plan (workspace + device-resident SCG state) of one geometry class.  Requests queue in
+// arrival order and are admitted into free slots; a slot is created when a request's class has
+// none free and the slot's workspace fits the HBM budget (free device memory minus a reserve,
+// or an explicit budget).  Every tick runs a few fused-pass launches over the tiles of all live
+// slots at once (one SCG iteration each per launch), so requests that arrive while others are on
+// the GPU join the next launch; a finished projection is copied out and its slot freed.  Each
+// projection keeps its own state and fixed-order reductions: the result is the same alone and in
+// the mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "misr.h"
+#include "misr_internal.h"
+
+using namespace misr;
+using namespace misr_host;
+
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// owned copy of a descriptor (its shift and PSF arrays included)
+struct DescCopy {
+    misr_desc d{};
+    std::vector<float> shifts, psf;
+    void set(const misr_desc &src) {
+        d = src;
+        shifts.assign(src.shifts, src.shifts + 2 * src.K);
+        psf.assign(src.psf, src.psf + src.psf_size * src.psf_size);
+        d.shifts = shifts.data();
+        d.psf = psf.data();
+    }
+    bool same_class(const DescCopy &o) const {
+        const misr_desc &a = d, &b = o.d;
+        return a.lr_h == b.lr_h && a.lr_w == b.lr_w && a.K == b.K && a.factor == b.factor &&
+               a.psf_size == b.psf_size && a.lambda == b.lambda && a.btv_alpha == b.btv_alpha &&
+               a.btv_w == b.btv_w && a.eps == b.eps && a.iters == b.iters && a.x0_mode == b.x0_mode &&
+               a.in_dtype == b.in_dtype && a.flat_field == b.flat_field && a.iterate_dtype == b.iterate_dtype &&
+               shifts == o.shifts && psf == o.psf;
+    }
+};
+
+enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2, RQ_FAILED = 3 };
+
+struct Request {
+    uint64_t ticket = 0;
+    DescCopy desc;
+    const void *y = nullptr;
+    float *x = nullptr;
+    ReqState state = RQ_QUEUED;
+    misr_status status = MISR_OK;
+    misr_stats stats{};
+    double t_submit = 0, t_start = 0, t_end = 0;
+    int slot = -1;
+};
+
+struct Slot {
+    misr_plan_t plan = nullptr;
+    DescCopy desc;
+    bool busy = false;
+    uint64_t ticket = 0;
+    int passes = 0;        // fused passes run since admission
+    int2 *tiles = nullptr;  // device tile map of this slot alone (for its init pass)
+};
+
+size_t plan_bytes_estimate(const misr_desc &d) {
+    const size_t H = (size_t)d.factor * d.lr_h, W = (size_t)d.factor * d.lr_w, pitch = (W + 3) & ~size_t(3);
+    const size_t tiles = ((H + 31) / 32) * ((W + 63) / 64);
+    return 7 * ((H * pitch * 4 + 255) / 256 * 256) + tiles * 100 + (size_t)std::max(d.iters, 1) * 80 + (1 << 16);
+}
+
+}  // namespace
+
+struct misr_server_s {
+    misr_server_cfg cfg{};
+    int device = 0;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, Request> reqs;
+    // worker-owned state
+    std::vector<Slot> slots;
+    size_t slot_bytes = 0;
+    cudaStream_t stream = nullptr;
+    DevProblem *dprobs = nullptr;   // one record per slot (capacity cfg.max_slots)
+    int2 *dtiles = nullptr;         // tile map of the live slots
+    size_t dtiles_cap = 0;
+    ScgState *st_host = nullptr;    // page-locked states, one per slot
+    std::vector<int2> h_tiles;
+    bool tiles_dirty = true;
+    misr_status worker_error = MISR_OK;
+    uint64_t passes_launched = 0;
+};
+
+namespace {
+
+misr_status grow_tiles(misr_server_t s, size_t need) {
+    if (need <= s->dtiles_cap) return MISR_OK;
+    size_t cap = std::max<size_t>(need, 2 * s->dtiles_cap);
+    if (s->dtiles) {
+        CK(cudaStreamSynchronize(s->stream));
+        cudaFree(s->dtiles);
+        s->dtiles = nullptr;
+    }
+    cudaError_t e = cudaMalloc(&s->dtiles, cap * sizeof(int2));
+    if (e != cudaSuccess) { cudaGetLastError(); s->dtiles_cap = 0; return fail(MISR_ENOMEM, "tile map: %s", cudaGetErrorString(e)); }
+    s->dtiles_cap = cap;
+    return MISR_OK;
+}
+
+// Can a new slot for `d` be created?  (slot count, explicit budget, free device memory)
+bool can_create(misr_server_t s, const misr_desc &d) {
+    if ((int)s->slots.size() >= s->cfg.max_slots) return false;
+    const size_t need = plan_bytes_estimate(d);
+    if (s->cfg.hbm_budget_bytes > 0) return s->slot_bytes + need <= s->cfg.hbm_budget_bytes;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); return false; }
+    return free_b > need + s->cfg.hbm_reserve_bytes;
+}
+
+// Free one idle slot of another class (when memory or the slot count blocks a request).
+bool evict_idle(misr_server_t s, const DescCopy &want) {
+    for (size_t i = 0; i < s->slots.size(); ++i) {
+        Slot &sl = s->slots[i];
+        if (!sl.busy && sl.plan && !sl.desc.same_class(want)) {
+            cudaStreamSynchronize(s->stream);
+            s->slot_bytes -= plan_bytes_estimate(sl.desc.d);
+            misr_plan_destroy(sl.plan);
+            cudaFree(sl.tiles);
+            sl.plan = nullptr;
+            sl.tiles = nullptr;
+            // keep the slot index (records are per index); mark it empty
+            return true;
+        }
+    }
+    return false;
+}
+
+// Assign queued requests to slots; returns the slots admitted this tick.
+std::vector<int> admit(misr_server_t s) {
+    std::vector<int> started;
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+        Request &rq = s->reqs[*it];
+        int use = -1;
+        for (size_t i = 0; i < s->slots.size(); ++i)
+            if (s->slots[i].plan && !s->slots[i].busy && s->slots[i].desc.same_class(rq.desc)) { use = (int)i; break; }
+        if (use < 0) {
+            bool ok = can_create(s, rq.desc.d);
+            while (!ok && evict_idle(s, rq.desc)) ok = can_create(s, rq.desc.d);
+            if (ok) {
+                int idx = -1;   // reuse an empty index first
+                for (size_t i = 0; i < s->slots.size(); ++i)
+                    if (!s->slots[i].plan) { idx = (int)i; break; }
+                if (idx < 0 && (int)s->slots.size() < s->cfg.max_slots) { s->slots.emplace_back(); idx = (int)s->slots.size() - 1; }
+                misr_plan_t p = nullptr;
+                const misr_status pc = idx >= 0 ? misr_plan_create(&rq.desc.d, &p) : MISR_EAGAIN;
+                if (pc != MISR_OK && pc != MISR_ENOMEM && pc != MISR_ECUDA && pc != MISR_EAGAIN) {
+                    rq.state = RQ_FAILED;
+                    rq.status = pc;
+                    rq.t_end = now_s();
+                    it = s->queue.erase(it);
+                    s->cv_done.notify_all();
+                    continue;
+                }
+                if (pc == MISR_OK) {
+                    Slot &sl = s->slots[idx];
+                    sl.plan = p;
+                    sl.desc.set(rq.desc.d);
+                    s->slot_bytes += plan_bytes_estimate(rq.desc.d);
+                    std::vector<int2> t(p->hp.n_tiles);
+                    for (int k = 0; k < p->hp.n_tiles; ++k) t[k] = make_int2(idx, k);
+                    bool ok2 = cudaMalloc(&sl.tiles, sizeof(int2) * t.size()) == cudaSuccess &&
+                               cudaMemcpy(sl.tiles, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                               cudaMemcpy(&s->dprobs[idx], &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice) == cudaSuccess;
+                    if (!ok2) {
+                        cudaGetLastError();
+                        misr_plan_destroy(p);
+                        if (sl.tiles) cudaFree(sl.tiles);
+                        sl.plan = nullptr;
+                        sl.tiles = nullptr;
+                        s->slot_bytes -= plan_bytes_estimate(rq.desc.d);
+                    } else {
+                        use = idx;
+                    }
+                } else {
+                    cudaGetLastError();
+                }
+            }
+        }
+        if (use < 0) {
+            bool any_busy = false;
+            for (auto &sl : s->slots) any_busy |= sl.busy;
+            if (any_busy) { ++it; continue; }   // stays queued until a running projection frees room
+            // nothing running will ever free room for it
+            rq.state = RQ_FAILED;
+            rq.status = fail(MISR_ENOMEM, "a %dx%d x%d projection does not fit the server's HBM budget",
+                             rq.desc.d.lr_h, rq.desc.d.lr_w, rq.desc.d.factor);
+            rq.t_end = now_s();
+            it = s->queue.erase(it);
+            s->cv_done.notify_all();
+            continue;
+        }
+        Slot &sl = s->slots[use];
+        sl.busy = true;
+        sl.ticket = rq.ticket;
+        sl.passes = 0;
+        rq.state = RQ_RUNNING;
+        rq.slot = use;
+        rq.t_start = now_s();
+        started.push_back(use);
+        it = s->queue.erase(it);
+        s->tiles_dirty = true;
+    }
+    return started;
+}
+
+void finish(misr_server_t s, int idx, misr_status st_code) {
+    Slot &sl = s->slots[idx];
+    std::lock_guard<std::mutex> lock(s->mu);
+    Request &rq = s->reqs[sl.ticket];
+    const ScgState &h = s->st_host[idx];
+    rq.stats.iters_done = h.iter;
+    rq.stats.accepted = h.accepted;
+    rq.stats.status = st_code;
+    rq.stats.reserved = 0;
+    rq.stats.J_final = h.E;
+    rq.stats.rnorm2 = h.rn2;
+    rq.stats.lambda_scg = h.lam;
+    rq.status = st_code;
+    rq.state = st_code == MISR_OK ? RQ_DONE : RQ_FAILED;
+    rq.t_end = now_s();
+    sl.busy = false;
+    s->tiles_dirty = true;
+}
+
+void worker_main(misr_server_t s) {
+    cudaSetDevice(s->device);
+    const int k_passes = std::max(1, s->cfg.passes_per_tick);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            s->cv_work.wait(lock, [&] {
+                if (s->stop || !s->queue.empty()) return true;
+                for (auto &sl : s->slots)
+                    if (sl.busy) return true;
+                return false;
+            });
+            if (s->stop) break;
+        }
+        // 1. admission: prepare + initial pass of each newly admitted projection
+        std::vector<int> started = admit(s);
+        misr_status r = MISR_OK;
+        for (int idx : started) {
+            Slot &sl = s->slots[idx];
+            const Request *rq;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                rq = &s->reqs[sl.ticket];
+            }
+            misr_plan_t p = sl.plan;
+            if (r == MISR_OK)
+                r = launch_prepare_raw(s->dprobs, idx, p->d, p->n_pitched, rq->y, rq->x, p->d.x0_mode, 1 | 2 | 4, s->stream);
+            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.tiles, p->hp.n_tiles, MODE_INIT, 0.0, 0.0, s->stream);
+        }
+        // 2. the live slots' tile map
+        if (r == MISR_OK && s->tiles_dirty) {
+            s->h_tiles.clear();
+            for (size_t i = 0; i < s->slots.size(); ++i)
+                if (s->slots[i].busy)
+                    for (int k = 0; k < s->slots[i].plan->hp.n_tiles; ++k) s->h_tiles.push_back(make_int2((int)i, k));
+            r = grow_tiles(s, std::max<size_t>(s->h_tiles.size(), 1));
+            if (r == MISR_OK && !s->h_tiles.empty() &&
+                cudaMemcpyAsync(s->dtiles, s->h_tiles.data(), sizeof(int2) * s->h_tiles.size(), cudaMemcpyHostToDevice,
+                                s->stream) != cudaSuccess)
+                r = fail(MISR_ECUDA, "tile map upload failed");
+            s->tiles_dirty = false;
+        }
+        // 3. k SCG iterations of every live projection, one launch each
+        const int nt = (int)s->h_tiles.size();
+        for (int it = 0; it < k_passes && r == MISR_OK && nt > 0; ++it) {
+            r = launch_pass_raw(s->dprobs, s->dtiles, nt, MODE_ITER, 0.0, 0.0, s->stream);
+            ++s->passes_launched;
+        }
+        // 4. completion: read the live states, copy finished projections out
+        for (size_t i = 0; i < s->slots.size() && r == MISR_OK; ++i)
+            if (s->slots[i].busy &&
+                cudaMemcpyAsync(&s->st_host[i], s->slots[i].plan->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost,
+                                s->stream) != cudaSuccess)
+                r = fail(MISR_ECUDA, "state copy failed");
+        if (r == MISR_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) r = fail(MISR_ECUDA, "server stream failed");
+        std::vector<int> done;
+        for (size_t i = 0; i < s->slots.size(); ++i) {
+            Slot &sl = s->slots[i];
+            if (!sl.busy) continue;
+            sl.passes += k_passes;
+            if (r != MISR_OK || s->st_host[i].done) done.push_back((int)i);
+        }
+        for (int idx : done) {
+            Slot &sl = s->slots[idx];
+            misr_status code = r;
+            if (code == MISR_OK && s->st_host[idx].status != DEV_OK) code = MISR_ETIMEOUT;
+            if (code == MISR_OK) {
+                const Request *rq;
+                {
+                    std::lock_guard<std::mutex> lock(s->mu);
+                    rq = &s->reqs[sl.ticket];
+                }
+                code = launch_finalize_raw(s->dprobs, idx, sl.plan->n, rq->x, s->stream);
+                if (code == MISR_OK && cudaStreamSynchronize(s->stream) != cudaSuccess)
+                    code = fail(MISR_ECUDA, "server stream failed");
+            }
+            finish(s, idx, code);
+        }
+        if (!done.empty()) s->cv_done.notify_all();
+        if (r != MISR_OK) {   // the stream is unusable: fail what is queued and stop serving
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->worker_error = r;
+            for (uint64_t t : s->queue) {
+                Request &rq = s->reqs[t];
+                rq.state = RQ_FAILED;
+                rq.status = r;
+                rq.t_end = now_s();
+            }
+            s->queue.clear();
+            s->cv_done.notify_all();
+            break;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" misr_status misr_server_create(const misr_server_cfg *cfg, misr_server_t *out) {
+    if (!out || !cfg) return fail(MISR_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (cfg->max_slots < 1 || cfg->max_slots > 4096) return fail(MISR_EINVAL, "max_slots must be in [1, 4096]");
+    if (cfg->passes_per_tick < 0 || cfg->passes_per_tick > 1000) return fail(MISR_EINVAL, "passes_per_tick must be in [0, 1000]");
+    misr_server_t s = new (std::nothrow) misr_server_s();
+    if (!s) return fail(MISR_ENOMEM, "host allocation failed");
+    s->cfg = *cfg;
+    if (s->cfg.passes_per_tick == 0) s->cfg.passes_per_tick = 4;
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dprobs, sizeof(DevProblem) * cfg->max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->st_host, sizeof(ScgState) * cfg->max_slots);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        misr_status r = fail(MISR_ENOMEM, "server setup: %s", cudaGetErrorString(e));
+        if (s->stream) cudaStreamDestroy(s->stream);
+        if (s->dprobs) cudaFree(s->dprobs);
+        delete s;
+        return r;
+    }
+    s->slots.reserve(cfg->max_slots);
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_server_destroy(misr_server_t s) {
+    if (!s) return MISR_OK;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    DeviceGuard g(s->device);
+    cudaStreamSynchronize(s->stream);
+    for (auto &sl : s->slots) {
+        if (sl.plan) misr_plan_destroy(sl.plan);
+        if (sl.tiles) cudaFree(sl.tiles);
+    }
+    if (s->dtiles) cudaFree(s->dtiles);
+    if (s->dprobs) cudaFree(s->dprobs);
+    if (s->st_host) cudaFreeHost(s->st_host);
+    cudaStreamDestroy(s->stream);
+    delete s;
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_submit(misr_server_t s, const misr_desc *desc, const void *y_dev, float *x_dev,
+                                   uint64_t *ticket) {
+    if (!s || !desc || !y_dev || !x_dev || !ticket) return fail(MISR_EINVAL, "NULL argument");
+    const misr_status chk = check_desc(*desc);
+    if (chk != MISR_OK) return chk;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->worker_error != MISR_OK) return fail(s->worker_error, "the server stopped after an error");
+    const uint64_t t = s->next_ticket++;
+    Request &rq = s->reqs[t];
+    rq.ticket = t;
+    rq.desc.set(*desc);
+    rq.y = y_dev;
+    rq.x = x_dev;
+    rq.t_submit = now_s();
+    s->queue.push_back(t);
+    *ticket = t;
+    s->cv_work.notify_all();
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_poll(misr_server_t s, uint64_t ticket, misr_stats *stats, double *times) {
+    if (!s) return fail(MISR_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(MISR_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    const Request &rq = it->second;
+    if (rq.state == RQ_QUEUED || rq.state == RQ_RUNNING) return MISR_EAGAIN;
+    if (stats) *stats = rq.stats;
+    if (times) { times[0] = rq.t_submit; times[1] = rq.t_start; times[2] = rq.t_end; }
+    const misr_status st = rq.status;
+    s->reqs.erase(it);
+    if (st != MISR_OK) return fail(st, "request %llu failed", (unsigned long long)ticket);
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_server_wait(misr_server_t s, uint64_t ticket, double timeout_s) {
+    if (!s) return fail(MISR_EINVAL, "NULL server");
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto done = [&] {
+        auto it = s->reqs.find(ticket);
+        return it == s->reqs.end() || (it->second.state != RQ_QUEUED && it->second.state != RQ_RUNNING) ||
+               s->worker_error != MISR_OK;
+    };
+    if (s->reqs.find(ticket) == s->reqs.end()) return fail(MISR_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    if (!s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), done))
+        return fail(MISR_ETIMEOUT, "ticket %llu not finished within %.3f s", (unsigned long long)ticket, timeout_s);
+    auto it = s->reqs.find(ticket);
+    if (it != s->reqs.end() && (it->second.state == RQ_QUEUED || it->second.state == RQ_RUNNING))
+        return fail(s->worker_error, "the server stopped after an error");
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_server_counters(misr_server_t s, int64_t *out) {
+    if (!s || !out) return fail(MISR_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    int64_t live = 0, slots = 0;
+    for (auto &sl : s->slots) { live += sl.busy; slots += sl.plan != nullptr; }
+    out[0] = (int64_t)s->queue.size();
+    out[1] = live;
+    out[2] = slots;
+    out[3] = (int64_t)s->slot_bytes;
+    out[4] = (int64_t)s->passes_launched;
+    return MISR_OK;
+}
