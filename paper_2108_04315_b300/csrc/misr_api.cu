@@ -132,7 +132,7 @@ static misr_status set_pass_attrs() {
     return MISR_OK;
 }
 
-// CTAs of the fused pass resident on the whole GPU (the L2 prefetch distance)
+// CTAs of the fused pass resident on the whole GPU
 static int resident_ctas() {
     static int cached = -1;
     if (cached >= 0) return cached;
@@ -146,11 +146,22 @@ static int resident_ctas() {
     return cached;
 }
 
+// persistent grid: one CTA per resident slot, at most one per work item
+static int pass_grid(int n_items) { return std::max(1, std::min(n_items, resident_ctas())); }
+
 static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double beta, cudaStream_t s) {
-    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<p->hp.n_tiles, PASS_NT, PassGeo::SMEM_BYTES, s>>>(
-        p->dprob, p->dtile, mode, alpha, beta, resident_ctas());
+    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<pass_grid(p->hp.n_tiles), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
+        p->dprob, p->dtile, p->hp.n_tiles, p->work, mode, alpha, beta);
     CK(cudaGetLastError());
     return MISR_OK;
+}
+
+// Groups of the pass reduction: at least 64 tiles, at most 128 groups (the last group's
+// warp sums all groups).
+static void set_groups(DevProblem &hp) {
+    hp.group = 64;
+    while ((hp.n_tiles + hp.group - 1) / hp.group > 128) hp.group *= 2;
+    hp.n_groups = (hp.n_tiles + hp.group - 1) / hp.group;
 }
 
 int misr_host::grid_for(size_t n, int threads) {
@@ -167,13 +178,13 @@ static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float 
     return MISR_OK;
 }
 
-misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, int ntiles, int mode,
-                                       double alpha, double beta, cudaStream_t s) {
-    if (ntiles <= 0) return MISR_OK;
+misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, int n_tiles, unsigned *work,
+                                       int mode, double alpha, double beta, cudaStream_t s) {
+    if (n_tiles <= 0) return MISR_OK;
     misr_status r = set_pass_attrs();
     if (r != MISR_OK) return r;
-    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<ntiles, PASS_NT, PassGeo::SMEM_BYTES, s>>>(probs, tiles, mode, alpha,
-                                                                                         beta, resident_ctas());
+    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<pass_grid(n_tiles), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
+        probs, tiles, n_tiles, work, mode, alpha, beta);
     CK(cudaGetLastError());
     return MISR_OK;
 }
@@ -263,11 +274,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     hp.tiles_y = (hp.H + TILE_H - 1) / TILE_H;
     hp.tiles_x = (hp.W + TILE_W - 1) / TILE_W;
     hp.n_tiles = hp.tiles_y * hp.tiles_x;
-    // two-level reduction: groups of at least 64 tiles, at most 1024 groups (their sums are
-    // staged in the freed tile buffers of the last CTA)
-    hp.group = 64;
-    while ((hp.n_tiles + hp.group - 1) / hp.group > 1024) hp.group *= 2;
-    hp.n_groups = (hp.n_tiles + hp.group - 1) / hp.group;
+    set_groups(hp);
 
     misr_plan_t p = new (std::nothrow) misr_plan_s();
     if (!p) return fail(MISR_ENOMEM, "host allocation failed");
@@ -279,7 +286,8 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     p->n_pitched = (size_t)hp.H * hp.pitch;
     p->m_total = (size_t)d.K * d.lr_h * d.lr_w;
 
-    // workspace: X[2], R[2], P[2], Y | partials | counter | state | trace | problem | tile map
+    // workspace: X[2], R[2], P[2], Y | tile and group sums, group counters, pass counter,
+    // launch tile counter | state | trace | problem | tile list
     const size_t img = align_up(p->n_pitched * sizeof(float), 256);
     size_t off = 0;
     const size_t o_img = off; off += 7 * img;
@@ -287,6 +295,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     const size_t o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(double), 256);
     const size_t o_gcnt = off; off += align_up((size_t)hp.n_groups * sizeof(unsigned int), 256);
     const size_t o_cnt = off; off += 256;
+    const size_t o_work = off; off += 256;
     const size_t o_st = off; off += align_up(sizeof(ScgState), 256);
     const size_t o_tr = off; off += align_up((size_t)std::max(d.iters, 1) * TRACE_COLS * sizeof(double), 256);
     const size_t o_pr = off; off += align_up(sizeof(DevProblem), 256);
@@ -306,9 +315,10 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     }
     hp.Y = (float *)(b + o_img + 6 * img);
     hp.partials = (double *)(b + o_part);
-    hp.counter = (unsigned int *)(b + o_cnt);
     hp.gpartials = (double *)(b + o_gpart);
     hp.gcount = (unsigned int *)(b + o_gcnt);
+    hp.counter = (unsigned int *)(b + o_cnt);
+    p->work = (unsigned int *)(b + o_work);
     hp.st = (ScgState *)(b + o_st);
     hp.trace = (double *)(b + o_tr);
     p->dprob = (DevProblem *)(b + o_pr);
@@ -546,14 +556,14 @@ constexpr size_t na_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 constexpr int NOALLOC_MAX_H = 512, NOALLOC_MAX_W = 512;
 constexpr size_t NOALLOC_IMG = na_align(size_t(NOALLOC_MAX_H) * NOALLOC_MAX_W * sizeof(float), 256);
 constexpr int NOALLOC_MAX_TILES = ((NOALLOC_MAX_H + TILE_H - 1) / TILE_H) * ((NOALLOC_MAX_W + TILE_W - 1) / TILE_W);
-constexpr int NOALLOC_GROUP = 64;
-constexpr int NOALLOC_MAX_GROUPS = (NOALLOC_MAX_TILES + NOALLOC_GROUP - 1) / NOALLOC_GROUP;
+constexpr int NOALLOC_MAX_GROUPS = 128;
 constexpr size_t NA_O_IMG = 0;
 constexpr size_t NA_O_PART = NA_O_IMG + 7 * NOALLOC_IMG;
 constexpr size_t NA_O_GPART = NA_O_PART + na_align(size_t(NOALLOC_MAX_TILES) * NPART * sizeof(double), 256);
 constexpr size_t NA_O_GCNT = NA_O_GPART + na_align(size_t(NOALLOC_MAX_GROUPS) * NPART * sizeof(double), 256);
 constexpr size_t NA_O_CNT = NA_O_GCNT + na_align(size_t(NOALLOC_MAX_GROUPS) * sizeof(unsigned int), 256);
-constexpr size_t NA_O_ST = NA_O_CNT + 256;
+constexpr size_t NA_O_WORK = NA_O_CNT + 256;
+constexpr size_t NA_O_ST = NA_O_WORK + 256;
 constexpr size_t NA_O_PROB = NA_O_ST + na_align(sizeof(ScgState), 256);
 constexpr size_t NA_O_TMAP = NA_O_PROB + na_align(sizeof(DevProblem), 256);
 constexpr size_t NOALLOC_BYTES = NA_O_TMAP + na_align(size_t(NOALLOC_MAX_TILES) * sizeof(int2), 256);
@@ -633,8 +643,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
     hp.tiles_y = (hp.H + TILE_H - 1) / TILE_H;
     hp.tiles_x = (hp.W + TILE_W - 1) / TILE_W;
     hp.n_tiles = hp.tiles_y * hp.tiles_x;
-    hp.group = NOALLOC_GROUP;
-    hp.n_groups = (hp.n_tiles + hp.group - 1) / hp.group;
+    set_groups(hp);
     for (int i = 0; i < 2; ++i) {
         hp.X[i] = reinterpret_cast<float *>(base + NA_O_IMG + (0 + i) * NOALLOC_IMG);
         hp.Rv[i] = reinterpret_cast<float *>(base + NA_O_IMG + (2 + i) * NOALLOC_IMG);
@@ -678,20 +687,20 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     for (int t = 0; t < hp.n_tiles; ++t) tiles[t] = make_int2(0, t);
     DevProblem *dprob = reinterpret_cast<DevProblem *>(base + NA_O_PROB);
     int2 *dtile = reinterpret_cast<int2 *>(base + NA_O_TMAP);
+    unsigned int *work = reinterpret_cast<unsigned int *>(base + NA_O_WORK);
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(dprob, &hp, sizeof(DevProblem), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dtile, tiles, sizeof(int2) * hp.n_tiles, cudaMemcpyHostToDevice, st));
-    // the pass's group counters and pass counter must start at zero
-    CK(cudaMemsetAsync(hp.gcount, 0, sizeof(unsigned int) * hp.n_groups, st));
-    CK(cudaMemsetAsync(hp.counter, 0, sizeof(unsigned int), st));
+    // (prepare's state reset zeroes the group counters and the pass counter; the tile counter
+    // is zero in a fresh scratch array and zeroed again by every pass)
     const float log_i0 = desc->in_dtype == MISR_U16 ? logf(desc->flat_field) : 0.f;
     const size_t npitched = (size_t)hp.H * hp.pitch, n = (size_t)hp.H * hp.W;
     // x_1 = x (given), r = p_old = 0, state reset; then one pass with alpha = beta = 0
     prepare_kernel<<<grid_for(npitched, 256), 256, 0, st>>>(dprob, 0, y_dev, desc->in_dtype, log_i0, x_dev,
                                                            MISR_X0_GIVEN, 1 | 2 | 4);
     CK(cudaGetLastError());
-    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<hp.n_tiles, PASS_NT, PassGeo::SMEM_BYTES, st>>>(
-        dprob, dtile, MODE_PROBE, 0.0, 0.0, resident_ctas());
+    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<pass_grid(hp.n_tiles), PASS_NT, PassGeo::SMEM_BYTES, st>>>(
+        dprob, dtile, hp.n_tiles, work, MODE_PROBE, 0.0, 0.0);
     CK(cudaGetLastError());
     scale_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(hp.Rv[1], hp.pitch, -1.f, g_dev, hp.H, hp.W);
     CK(cudaGetLastError());

@@ -19,9 +19,10 @@ struct misr_batch_s {
     int n = 0;
     std::vector<misr_plan_t> plans;
     DevProblem *dprobs = nullptr;   // n problem records (copies of the plans' records)
-    int2 *dtiles = nullptr;         // tiles of all problems, problem after problem
+    int2 *ditems = nullptr;         // tiles of all problems, problem after problem
+    unsigned int *work = nullptr;   // the fused pass's tile counter
     void *mem = nullptr;
-    int total_tiles = 0;
+    int total_items = 0;
     int max_iters = 0;
     cudaStream_t cap = nullptr;     // private stream used for graph capture
     cudaGraphExec_t chunk = nullptr;
@@ -59,26 +60,29 @@ extern "C" misr_status misr_batch_create(int32_t n, const misr_plan_t *plans, mi
     b->n = n;
     b->plans.assign(plans, plans + n);
     std::vector<DevProblem> recs(n);
-    std::vector<int2> tiles;
+    std::vector<int2> items;
     for (int i = 0; i < n; ++i) {
         recs[i] = plans[i]->hp;
-        for (int t = 0; t < plans[i]->hp.n_tiles; ++t) tiles.push_back(make_int2(i, t));
+        for (int t = 0; t < plans[i]->hp.n_tiles; ++t) items.push_back(make_int2(i, t));
         b->max_iters = std::max(b->max_iters, plans[i]->d.iters);
     }
-    b->total_tiles = (int)tiles.size();
+    b->total_items = (int)items.size();
     DeviceGuard g(b->device);
     const size_t rec_bytes = round_up(sizeof(DevProblem) * n, 256);
-    cudaError_t e = cudaMalloc(&b->mem, rec_bytes + sizeof(int2) * tiles.size());
+    const size_t list_bytes = round_up(sizeof(int2) * items.size(), 256);
+    cudaError_t e = cudaMalloc(&b->mem, rec_bytes + list_bytes + 256);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete b;
         return fail(MISR_ENOMEM, "cudaMalloc for the batch tables failed: %s", cudaGetErrorString(e));
     }
     b->dprobs = static_cast<DevProblem *>(b->mem);
-    b->dtiles = reinterpret_cast<int2 *>(static_cast<char *>(b->mem) + rec_bytes);
+    b->ditems = reinterpret_cast<int2 *>(static_cast<char *>(b->mem) + rec_bytes);
+    b->work = reinterpret_cast<unsigned int *>(static_cast<char *>(b->mem) + rec_bytes + list_bytes);
     do {
         if ((e = cudaMemcpy(b->dprobs, recs.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice)) != cudaSuccess) break;
-        if ((e = cudaMemcpy(b->dtiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(b->ditems, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemset(b->work, 0, 256)) != cudaSuccess) break;
         if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaMallocHost((void **)&b->st_host, sizeof(ScgState) * n)) != cudaSuccess) break;
     } while (0);
@@ -99,7 +103,7 @@ static misr_status batch_graph(misr_batch_t b) {
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     misr_status r = MISR_OK;
     for (int i = 0; i < want && r == MISR_OK; ++i)
-        r = launch_pass_raw(b->dprobs, b->dtiles, b->total_tiles, MODE_ITER, 0.0, 0.0, b->cap);
+        r = launch_pass_raw(b->dprobs, b->ditems, b->total_items, b->work, MODE_ITER, 0.0, 0.0, b->cap);
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (r != MISR_OK) { if (graph) cudaGraphDestroy(graph); return r; }
     if (e != cudaSuccess) return fail(MISR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
@@ -123,7 +127,7 @@ extern "C" misr_status misr_batch_solve(misr_batch_t b, const void *const *y_dev
         const misr_plan_t p = b->plans[i];
         r = launch_prepare_raw(b->dprobs, i, p->d, p->n_pitched, y_dev[i], x_dev[i], p->d.x0_mode, 1 | 2 | 4, s);
     }
-    if (r == MISR_OK) r = launch_pass_raw(b->dprobs, b->dtiles, b->total_tiles, MODE_INIT, 0.0, 0.0, s);
+    if (r == MISR_OK) r = launch_pass_raw(b->dprobs, b->ditems, b->total_items, b->work, MODE_INIT, 0.0, 0.0, s);
     if (r != MISR_OK) return r;
     for (int done = 0; done < b->max_iters; done += b->chunk_len) CK(cudaGraphLaunch(b->chunk, s));
     for (int i = 0; i < b->n && r == MISR_OK; ++i) r = launch_finalize_raw(b->dprobs, i, b->plans[i]->n, x_dev[i], s);

@@ -91,10 +91,9 @@ __device__ inline void scg_tail(const DevProblem &P, ScgState *st, const double 
 //   XB, PB, RB  x' / p / r     origin (-6, -8)  (TH+12) x (TW+16)   TMA boxes (x first col
 //                                                                    16-byte aligned)
 //   YB          Y, then E      origin (-4, -4)  (TH+8)  x (TW+8)    TMA box, NaN outside
-//   GB          2 B^T E, r'    origin (-2, -2)  (TH+4)  x (TW+4)
-//   SC scratch: forward horizontal blur (TH+12) x (TW+8), adjoint horizontal blur
-//               (TH+8) x (TW+4), three psi'(t_d) planes on origin (-4, -4) (TH+6) x (TW+8),
-//               and the horizontal blurs of p for the curvature (TH+4) x TW
+//   GB          lambda-free BTV gradient, then r'   origin (-2, -2)  (TH+4) x (TW+4)
+//   HS scratch: forward horizontal blur of x' (TH+12) x (TW+8), adjoint horizontal blur of E
+//               (TH+8) x (TW+4), horizontal blur of p (TH+4) x TW
 //   SMP         sampled flags of the owned pixels
 template <int TH, int TW>
 struct Geo {
@@ -103,13 +102,11 @@ struct Geo {
     static constexpr int XH = TH + 12, XW = TW + 16;
     static constexpr int EH = TH + 8, EW = TW + 8;
     static constexpr int GH = TH + 4, GW = TW + 4;
-    static constexpr int DH = TH + 6, DW = TW + 8;
     static constexpr int CH = TH + 4, CW = TW;
     static constexpr int HS1 = XH * EW, HS2 = EH * GW, HS3 = CH * CW;
     static constexpr int HS12 = HS1 > HS2 ? HS1 : HS2;
     static constexpr int HS = HS12 > HS3 ? HS12 : HS3;
-    static constexpr int SC = 3 * DH * DW + HS;          // psi' planes + one horizontal blur
-    static constexpr int FLOATS = 3 * XH * XW + EH * EW + GH * GW + SC;
+    static constexpr int FLOATS = 3 * XH * XW + EH * EW + GH * GW + HS;
     static constexpr size_t TMA_BYTES = sizeof(float) * (3 * XH * XW + EH * EW);
     static constexpr size_t SMEM_BYTES = 128 /*align slack*/ + sizeof(float) * FLOATS + TH * TW + 64;
 };
@@ -151,15 +148,30 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {   // a *
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
     return u2f(r);
 }
-__device__ __forceinline__ float2 f2rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+// reciprocal square root on the SFU, denormal inputs flushed (every argument here is at least
+// eps^2, so no input is denormal and the result equals the non-flushing form)
+__device__ __forceinline__ float rsqrt_ftz(float a) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float2 f2rsqrt(float2 a) { return make_float2(rsqrt_ftz(a.x), rsqrt_ftz(a.y)); }
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
 // Frame mask of the forward blur at sample coordinate c (one axis) for tap offset a:
 // the tap reads coordinate c - a, dropped when c - a < (c mod f).
-__device__ __forceinline__ bool fwd_tap_ok(int c, int a, int f) { return c < 0 || (c - a) >= (c % f); }
+// c mod f for 0 <= c < 2^29, 1 <= f <= 8: floor(c / f) = floor(c * m / 2^32) with
+// m = ceil(2^32 / f) is exact in that range (the rounding excess c (m f - 2^32) / 2^32 < 1);
+// m = 0 stands for f = 1.
+__device__ __forceinline__ int mod_f(int c, int f, unsigned m) {
+    return m ? c - f * (int)__umulhi((unsigned)c, m) : 0;
+}
+__device__ __forceinline__ bool fwd_tap_ok(int c, int a, int f, unsigned m) { return c < 0 || (c - a) >= mod_f(c, f, m); }
 // Frame mask of the adjoint blur at output coordinate u for tap offset a: the sample read
 // sits at u + a; the tap exists when u >= ((u + a) mod f).
-__device__ __forceinline__ bool adj_tap_ok(int u, int a, int f) { return (u + a) < 0 || u >= ((u + a) % f); }
+__device__ __forceinline__ bool adj_tap_ok(int u, int a, int f, unsigned m) {
+    return (u + a) < 0 || u >= mod_f(u + a, f, m);
+}
 
 
 // per-thread partial sums of a pass (FP32; combined across the CTA in FP64).  a, b, c hold
@@ -169,48 +181,47 @@ struct PassAcc {
 };
 
 // per-problem constants staged in shared memory at CTA start
-enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_N = 32 };
+enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_FMAG = 30, C_N = 32 };
 
 // ---------------------------------------------------------------------------------------
 // Body of the fused pass on one tile.  BORDER: the tile's halo reaches outside the image, so
 // frame masks, BTV pair validity and image bounds are checked; interior tiles skip them.
 //
-// Work is split into 4-pixel row items and scheduled in nine barrier intervals.  The BTV
-// gradient rounds (psi' planes, backward gather) depend only on x', so each is paired with a
-// data-term stage in one combined item loop; BTV items come first in the index space so a
-// thread's BTV items (and their register accumulators) are the same in every interval.
-//   I1 A: p, x'                I2 psi(dy=0) + B1          I3 gather(0) + B2 (residual)
-//   I4 psi(1) + C1             I5 gather(1) + C2          I6 psi(2) + horizontal blur of p
-//   I7 gather(2) + r'          I8 horizontal blur of r'   I9 curvature forms (owned)
+// Work is split into 4-pixel row items and scheduled in seven barrier intervals.  The BTV
+// gradient depends only on x' and is the heaviest stage (16 psi' evaluations per pixel, each
+// pair evaluated from both ends instead of staged in shared memory); its items are split over
+// I2 and I3, one per thread on the first threads, with the light data-term items of the same
+// interval spread over the other threads.
+//   I1 A: p, x'                        I2 BTV (first half) + B1 (forward horizontal blur)
+//   I3 BTV (second half) + B2          I4 C1 (adjoint horizontal blur)
+//   I5 C2 + r'                         I6 horizontal blurs of r' and p
+//   I7 curvature forms (owned)
 template <int TH, int TW, int NT, bool BORDER>
-__device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsigned char *smp, const float *cs,
-                                          uint64_t *ybar, int y0, int x0, float alpha, float beta, float *Xn,
+__device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsigned char *smp, const float *cs,
+                                          uint64_t *ybar, uint32_t yphase, int y0, int x0, float alpha,
+                                          float beta, float *Xn,
                                           float *Rn, float *Pn, PassAcc &A) {
     using G = Geo<TH, TW>;
     constexpr int XH = G::XH, XW = G::XW, EH = G::EH, EW = G::EW, GH = G::GH, GW = G::GW;
-    constexpr int DH = G::DH, DW = G::DW, CH = G::CH, CW = G::CW;
+    constexpr int CH = G::CH, CW = G::CW;
     float *XB = sm;
     float *PB = XB + XH * XW;
     float *RB = PB + XH * XW;
     float *YB = RB + XH * XW;
     float *GB = YB + EH * EW;
-    float *PL = GB + GH * GW;           // 3 psi' planes of DH x DW
-    float *HS = PL + 3 * DH * DW;       // horizontal blurs: x' (B1), E (C1), p (E)
+    float *HS = GB + GH * GW;           // horizontal blurs: x' (B1), E (C1), p (HP)
     float *HR = RB;                     // horizontal blur of r' (r is dead by then)
     const int tid = threadIdx.x;
     const int H = P.H, W = P.W, f = P.f, pitch = P.pitch;
     const float eps2 = cs[C_EPS2], lambda = cs[C_LAMBDA];
+    const unsigned fmag = __float_as_uint(cs[C_FMAG]);
 
-    constexpr int ND = DH * DW / 4;                  // BTV items (D grid, origin (-4, -4))
-    constexpr int NDI = (ND + NT - 1) / NT;
     constexpr int N_A = XH * XW / 4, N_B1 = XH * EW / 4, N_B2 = EH * EW / 4, N_C1 = EH * GW / 4;
     constexpr int N_C2 = GH * GW / 4, N_HP = CH * CW / 4, N_HR = CH * CW / 4, N_E = TH * TW / 4;
-    float2 facc[NDI][2], bacc[NDI][2];
+    constexpr int N_BTV = GH * GW / 4;                       // BTV items on the G grid
+    constexpr int N_BTV1 = N_BTV / 2, N_BTV2 = N_BTV - N_BTV1;
+    static_assert(N_BTV2 < NT, "one BTV item per thread and interval");
     float2 jb2 = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < NDI; ++i)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) { facc[i][h] = make_float2(0.f, 0.f); bacc[i][h] = make_float2(0.f, 0.f); }
 
     // ---------------- item bodies
     // A: p = r + beta p_old, x' = x + alpha p on the X box; owned pixels go to HBM
@@ -255,7 +266,7 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 - b];
-                if (BORDER && !fwd_tap_ok(x0 - 4 + e + j, b, f)) v = 0.f;
+                if (BORDER && !fwd_tap_ok(x0 - 4 + e + j, b, f, fmag)) v = 0.f;
                 s = fmaf(cs[C_HX + b + 2], v, s);
             }
             out[j] = s;
@@ -270,7 +281,7 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
         for (int a = -2; a <= 2; ++a) {
             const float4 v = ld4(HS + (n + 2 - a) * EW + e);
-            const float2 h = bc2((BORDER && !fwd_tap_ok(gy, a, f)) ? 0.f : cs[C_HY + a + 2]);
+            const float2 h = bc2((BORDER && !fwd_tap_ok(gy, a, f, fmag)) ? 0.f : cs[C_HY + a + 2]);
             z[0] = f2fma(h, make_float2(v.x, v.y), z[0]);
             z[1] = f2fma(h, make_float2(v.z, v.w), z[1]);
         }
@@ -304,26 +315,12 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 + b];
-                if (BORDER && !adj_tap_ok(x0 - 2 + g + j, b, f)) v = 0.f;
+                if (BORDER && !adj_tap_ok(x0 - 2 + g + j, b, f, fmag)) v = 0.f;
                 s = fmaf(cs[C_HX + b + 2], v, s);
             }
             out[j] = s;
         }
         st4v(HS + n * GW + g, out);
-    };
-    // C2: adjoint vertical blur -> GB = 2 B^T E
-    auto item_C2 = [&](int it) {
-        const int n = it / (GW / 4), g = 4 * (it - n * (GW / 4));
-        const int u = y0 - 2 + n;
-        float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-        for (int a = -2; a <= 2; ++a) {
-            const float4 v = ld4(HS + (n + 2 + a) * GW + g);
-            const float2 h = bc2((BORDER && !adj_tap_ok(u, a, f)) ? 0.f : 2.f * cs[C_HY + a + 2]);
-            s2[0] = f2fma(h, make_float2(v.x, v.y), s2[0]);
-            s2[1] = f2fma(h, make_float2(v.z, v.w), s2[1]);
-        }
-        st4(GB + n * GW + g, make_float4(s2[0].x, s2[0].y, s2[1].x, s2[1].y));
     };
     // horizontal blur of p on rows [-2, TH+2) x owned cols (for the curvature forms)
     auto item_HP = [&](int it) {
@@ -337,12 +334,142 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float vp = inp[j + 2 - b];
-                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f)) vp = 0.f;
+                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f, fmag)) vp = 0.f;
                 sp = fmaf(cs[C_HX + b + 2], vp, sp);
             }
             out[j] = sp;
         }
         st4v(HS + n * CW + o, out);
+    };
+    // BTV gradient (without lambda) of the prior at x' on the G grid (origin (-2, -2)):
+    // g(q) = sum_d gamma_d [psi'(x_q - x_{q+d}) - psi'(x_{q-d} - x_q)] over pairs inside the
+    // image; the prior's value gamma_d psi(x_q - x_{q+d}) + eps is summed over owned q.
+    auto item_btv = [&](int it) {
+        const int n = it / (GW / 4), g = 4 * (it - n * (GW / 4));
+        const int qy = y0 - 2 + n, qx = x0 - 2 + g;          // image coords of the first pixel
+        // x' rows n-2 .. n+2 of the G grid are XB rows n+2 .. n+6; cols g-4 .. g+3 of the G
+        // grid (8 values, 16-byte aligned) are XB cols g+4 .. g+11
+        const float *xrow = XB + (n + 4) * XW + g + 4;
+        float c[8];
+        ld8(xrow, c);                                        // c[2 + j] = x'(q_j)
+        const float2 cq[2] = {make_float2(c[2], c[3]), make_float2(c[4], c[5])};
+        const bool own_row = (n - 2) >= 0 && (n - 2) < TH;
+        float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        // forward pairs (q, q + d), d = (dy, dx), given the row of q + d: gradient and value
+        auto fwd_terms = [&](const float *fr, int dy, int dx) {
+            const float2 gam = bc2(cs[C_GAM + dy * 3 + dx]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * h;
+                const float2 t = f2sub(cq[h], make_float2(fr[2 + j + dx], fr[3 + j + dx]));
+                const float2 sq = f2fma(t, t, bc2(eps2));
+                const float2 rs = f2rsqrt(sq);
+                float2 ps = f2mul(t, rs);
+                float2 sr = f2mul(sq, rs);
+                if (BORDER) {
+                    const int x = qx + j;
+                    const bool f0 = qy >= 0 && qy + dy < H && x >= 0 && x + dx < W;
+                    const bool f1 = qy >= 0 && qy + dy < H && x + 1 >= 0 && x + 1 + dx < W;
+                    ps.x = f0 ? ps.x : 0.f; ps.y = f1 ? ps.y : 0.f;
+                    sr.x = f0 ? sr.x : 0.f; sr.y = f1 ? sr.y : 0.f;
+                }
+                acc[h] = f2fma(gam, ps, acc[h]);
+                if (own_row) {
+                    const int oc = g - 2 + j;                   // tile column of q_j
+                    sr.x = (oc >= 0 && oc < TW) ? sr.x : 0.f;
+                    sr.y = (oc + 1 >= 0 && oc + 1 < TW) ? sr.y : 0.f;
+                    jb2 = f2fma(gam, sr, jb2);
+                }
+            }
+        };
+        // backward pairs (q - d, q) given the row of q - d
+        auto bwd_terms = [&](const float *br, int dy, int dx) {
+            const float2 ngam = bc2(-cs[C_GAM + dy * 3 + dx]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * h;
+                const float2 t = f2sub(make_float2(br[2 + j - dx], br[3 + j - dx]), cq[h]);
+                const float2 rs = f2rsqrt(f2fma(t, t, bc2(eps2)));
+                float2 ps = f2mul(t, rs);
+                if (BORDER) {
+                    const int x = qx + j;
+                    const bool b0 = qy < H && qy - dy >= 0 && x < W && x - dx >= 0;
+                    const bool b1 = qy < H && qy - dy >= 0 && x + 1 < W && x + 1 - dx >= 0;
+                    ps.x = b0 ? ps.x : 0.f; ps.y = b1 ? ps.y : 0.f;
+                }
+                acc[h] = f2fma(ngam, ps, acc[h]);
+            }
+        };
+        fwd_terms(c, 0, 1);
+        fwd_terms(c, 0, 2);
+        bwd_terms(c, 0, 1);
+        bwd_terms(c, 0, 2);
+#pragma unroll
+        for (int dy = 1; dy <= 2; ++dy) {
+            float rowv[8];
+            ld8(xrow + dy * XW, rowv);
+            fwd_terms(rowv, dy, 0);
+            fwd_terms(rowv, dy, 1);
+            fwd_terms(rowv, dy, 2);
+            ld8(xrow - dy * XW, rowv);
+            bwd_terms(rowv, dy, 0);
+            bwd_terms(rowv, dy, 1);
+            bwd_terms(rowv, dy, 2);
+        }
+        st4(GB + n * GW + g, make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y));
+    };
+    // C2 + r': adjoint vertical blur 2 B^T E, then r' = -(2 B^T E + lambda g_BTV) in place of
+    // the BTV gradient; zero outside the image; owned pixels go to HBM with their sums
+    auto item_C2r = [&](int it) {
+        const int n = it / (GW / 4), g = 4 * (it - n * (GW / 4));
+        const int u = y0 - 2 + n;
+        float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+        for (int a = -2; a <= 2; ++a) {
+            const float4 v = ld4(HS + (n + 2 + a) * GW + g);
+            const float2 h = bc2((BORDER && !adj_tap_ok(u, a, f, fmag)) ? 0.f : 2.f * cs[C_HY + a + 2]);
+            s2[0] = f2fma(h, make_float2(v.x, v.y), s2[0]);
+            s2[1] = f2fma(h, make_float2(v.z, v.w), s2[1]);
+        }
+        const float4 gb = ld4(GB + n * GW + g);
+        float rv[4];
+        rv[0] = -fmaf(lambda, gb.x, s2[0].x);
+        rv[1] = -fmaf(lambda, gb.y, s2[0].y);
+        rv[2] = -fmaf(lambda, gb.z, s2[1].x);
+        rv[3] = -fmaf(lambda, gb.w, s2[1].y);
+        if (BORDER) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gx = x0 - 2 + g + j;
+                if (!(u >= 0 && u < H && gx >= 0 && gx < W)) rv[j] = 0.f;
+            }
+        }
+        st4(GB + n * GW + g, make_float4(rv[0], rv[1], rv[2], rv[3]));
+        const int orow = n - 2;
+        if (orow >= 0 && orow < TH) {
+            // owned columns of the item: tile cols g-2 .. g+1 inside [0, TW), as two pairs
+            // (8-byte aligned in the workspace images and in XB)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int oc = g - 2 + 2 * h;
+                if (oc < 0 || oc >= TW) continue;
+                const int gx = x0 + oc;
+                const float2 ro = ld2(RB + (orow + 6) * XW + oc + 8);
+                const float2 pq = ld2(PB + (orow + 6) * XW + oc + 8);
+                const float r0 = rv[2 * h], r1 = rv[2 * h + 1];
+                if (!BORDER || (u < H && gx + 1 < W)) {
+                    st2(Rn + (size_t)u * pitch + gx, make_float2(r0, r1));
+                    A.rr = fmaf(r0, r0, fmaf(r1, r1, A.rr));
+                    A.rrx = fmaf(r0, ro.x, fmaf(r1, ro.y, A.rrx));
+                    A.pr = fmaf(pq.x, r0, fmaf(pq.y, r1, A.pr));
+                } else if (u < H && gx < W) {
+                    Rn[(size_t)u * pitch + gx] = r0;
+                    A.rr = fmaf(r0, r0, A.rr);
+                    A.rrx = fmaf(r0, ro.x, A.rrx);
+                    A.pr = fmaf(pq.x, r0, A.pr);
+                }
+            }
+        }
     };
     // horizontal blur of r' on rows [-2, TH+2) x owned cols
     auto item_HR = [&](int it) {
@@ -356,120 +483,12 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float vr = inr[j + 2 - b];
-                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f)) vr = 0.f;
+                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f, fmag)) vr = 0.f;
                 sr = fmaf(cs[C_HX + b + 2], vr, sr);
             }
             out[j] = sr;
         }
         st4v(HR + n * CW + o, out);
-    };
-    // BTV: psi'(x_q - x_{q+d}) planes for the offsets of row offset dy; forward sums in
-    // registers; the prior's value on owned pairs
-    auto item_psi = [&](auto dy_c, int i, int it) {
-        constexpr int dy = decltype(dy_c)::value;
-        const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
-        float xq[4], xp[8];
-        ld4v(XB + (n + 2) * XW + e + 4, xq);
-        ld8(XB + (n + 2 + dy) * XW + e + 4, xp);
-        const int qy = y0 - 4 + n;
-        const bool own = (n - 4) >= 0 && (n - 4) < TH && e >= 4 && e < TW + 4;
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-            if (dx == 0 && dy == 0) continue;
-            const float2 gam = bc2(cs[C_GAM + dy * 3 + dx]);
-            float2 pv[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = 2 * h;
-                const float2 t = f2sub(make_float2(xq[j], xq[j + 1]), make_float2(xp[j + dx], xp[j + 1 + dx]));
-                const float2 sq = f2fma(t, t, bc2(eps2));
-                const float2 rs = f2rsqrt(sq);
-                float2 psi1 = f2mul(t, rs);
-                if (BORDER) {
-                    const int qx = x0 - 4 + e + j;
-                    const bool v0 = qy >= 0 && qx >= 0 && qy + dy < H && qx + dx < W;
-                    const bool v1 = qy >= 0 && qx + 1 >= 0 && qy + dy < H && qx + 1 + dx < W;
-                    psi1.x = v0 ? psi1.x : 0.f;
-                    psi1.y = v1 ? psi1.y : 0.f;
-                    if (own) {
-                        const float2 sr = f2mul(sq, rs);
-                        jb2 = f2fma(gam, make_float2(v0 ? sr.x : 0.f, v1 ? sr.y : 0.f), jb2);
-                    }
-                } else if (own) {
-                    jb2 = f2fma(gam, f2mul(sq, rs), jb2);
-                }
-                pv[h] = psi1;
-                facc[i][h] = f2fma(gam, psi1, facc[i][h]);
-            }
-            st4(PL + dx * DH * DW + n * DW + e, make_float4(pv[0].x, pv[0].y, pv[1].x, pv[1].y));
-        }
-    };
-    // BTV: backward sums gamma_d psi'(x_{q-d} - x_q) from the planes
-    auto item_gather = [&](auto dy_c, int i, int it) {
-        constexpr int dy = decltype(dy_c)::value;
-        const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
-        if (n < dy) return;   // q - d above the plane: q is outside the R region
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-            if (dx == 0 && dy == 0) continue;
-            const float2 gam = bc2(cs[C_GAM + dy * 3 + dx]);
-            const float *row = PL + dx * DH * DW + (n - dy) * DW;
-            float v[8];
-            if (dx == 0) ld4v(row + e, v + 4);
-            else if (e >= 4) ld8(row + e - 4, v);
-            else { ld4v(row + e, v + 4); v[0] = v[1] = v[2] = v[3] = 0.f; }
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                bacc[i][h] = f2fma(gam, make_float2(v[4 + 2 * h - dx], v[5 + 2 * h - dx]), bacc[i][h]);
-        }
-    };
-    // r' = -(2 B^T E + lambda grad BTV) on the R region (origin (-2, -2)): a D item (cols
-    // e..e+3 of the D grid) covers R cols e-2 .. e+1; owned items go to HBM whole
-    auto item_r = [&](int i, int it) {
-        const int n = it / (DW / 4), e = 4 * (it - n * (DW / 4));
-        const int gn = n - 2;
-        if (gn < 0 || gn >= GH) return;
-        const int gy = y0 - 4 + n;
-        float rv[4];
-        float *grow = GB + gn * GW;
-        float gsum[4] = {0.f, 0.f, 0.f, 0.f};
-        if (e >= 4) { const float2 v = ld2(grow + e - 2); gsum[0] = v.x; gsum[1] = v.y; }
-        if (e < GW) { const float2 v = ld2(grow + e); gsum[2] = v.x; gsum[3] = v.y; }
-        const float fb[4] = {facc[i][0].x - bacc[i][0].x, facc[i][0].y - bacc[i][0].y,
-                             facc[i][1].x - bacc[i][1].x, facc[i][1].y - bacc[i][1].y};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            rv[j] = -fmaf(lambda, fb[j], gsum[j]);
-            if (BORDER) {
-                const int gx = x0 - 4 + e + j;
-                if (!(gy >= 0 && gy < H && gx >= 0 && gx < W)) rv[j] = 0.f;
-            }
-        }
-        if (e >= 4) st2(grow + e - 2, make_float2(rv[0], rv[1]));
-        if (e < GW) st2(grow + e, make_float2(rv[2], rv[3]));
-        const int orow = n - 4, ocol = e - 4;
-        if (orow >= 0 && orow < TH && ocol >= 0 && ocol < TW) {
-            float rold[4], pq[4];
-            ld4v(RB + (orow + 6) * XW + ocol + 8, rold);
-            ld4v(PB + (orow + 6) * XW + ocol + 8, pq);
-            const int gx = x0 + ocol;
-            if (!BORDER || (gy < H && gx + 3 < W)) {
-                st4(Rn + (size_t)gy * pitch + gx, make_float4(rv[0], rv[1], rv[2], rv[3]));
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    A.rr = fmaf(rv[j], rv[j], A.rr);
-                    A.rrx = fmaf(rv[j], rold[j], A.rrx);
-                    A.pr = fmaf(pq[j], rv[j], A.pr);
-                }
-            } else if (gy < H) {
-                for (int j = 0; j < 4 && gx + j < W; ++j) {
-                    Rn[(size_t)gy * pitch + gx + j] = rv[j];
-                    A.rr = fmaf(rv[j], rv[j], A.rr);
-                    A.rrx = fmaf(rv[j], rold[j], A.rrx);
-                    A.pr = fmaf(pq[j], rv[j], A.pr);
-                }
-            }
-        }
     };
     // curvature forms on one owned row x four columns
     auto item_E = [&](int it) {
@@ -483,7 +502,7 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
             for (int a = -2; a <= 2; ++a) {
                 const float4 vr = ld4(HR + (n + 2 - a) * CW + o);
                 const float4 vp = ld4(HS + (n + 2 - a) * CW + o);
-                const float2 h = bc2((BORDER && !fwd_tap_ok(gy, a, f)) ? 0.f : cs[C_HY + a + 2]);
+                const float2 h = bc2((BORDER && !fwd_tap_ok(gy, a, f, fmag)) ? 0.f : cs[C_HY + a + 2]);
                 zr[0] = f2fma(h, make_float2(vr.x, vr.y), zr[0]);
                 zr[1] = f2fma(h, make_float2(vr.z, vr.w), zr[1]);
                 zp[0] = f2fma(h, make_float2(vp.x, vp.y), zp[0]);
@@ -558,237 +577,331 @@ __device__ __forceinline__ void pass_tile(const DevProblem &P, float *sm, unsign
     };
 
     // ---------------- the schedule
-    using I0 = std::integral_constant<int, 0>;
-    using I1c = std::integral_constant<int, 1>;
-    using I2c = std::integral_constant<int, 2>;
-    // BTV items k in [0, ND) first (slot i = k / NT), then the paired stage's items
-#define MISR_PAIRED(BTV_CALL, N_OTHER, OTHER_CALL)                                  \
-    _Pragma("unroll") for (int m = 0; m < (ND + (N_OTHER) + NT - 1) / NT; ++m) {    \
-        const int k = tid + m * NT;                                                  \
-        if (k < ND) {                                                                \
-            if (m < NDI) { BTV_CALL; }                                               \
-        } else if (k < ND + (N_OTHER)) {                                             \
-            const int ko = k - ND;                                                   \
-            OTHER_CALL;                                                              \
-        }                                                                            \
-    }
-
     // I1
     for (int it = tid; it < N_A; it += NT) item_A(it);
     __syncthreads();
-    // I2: psi(0) + B1
-    MISR_PAIRED(item_psi(I0(), m, k), N_B1, item_B1(ko))
+    // I2: BTV items [0, N_BTV1) on the first threads, B1 on the others
+    if (tid < N_BTV1) item_btv(tid);
+    else
+        for (int it = tid - N_BTV1; it < N_B1; it += NT - N_BTV1) item_B1(it);
     __syncthreads();
-    // the Y box: a wait that runs out flags the state (results of this pass are then void)
-    if (!mbar_wait_bounded(ybar, 0, TMA_WAIT_TRIES) && tid == 0) {
-        atomicExch(&P.st->status, (int)DEV_TMA_TIMEOUT);
-        atomicExch(&P.st->done, 1);
-    }
-    // I3: gather(0) + B2
-    MISR_PAIRED(item_gather(I0(), m, k), N_B2, item_B2(ko))
+    // the Y box: a wait that runs out is reported to the caller (the tile's results are void)
+    const bool y_late = !mbar_wait_bounded(ybar, yphase, TMA_WAIT_TRIES);
+    // I3: BTV items [N_BTV1, N_BTV) on the first threads, B2 on the others
+    if (tid < N_BTV2) item_btv(N_BTV1 + tid);
+    else
+        for (int it = tid - N_BTV2; it < N_B2; it += NT - N_BTV2) item_B2(it);
     __syncthreads();
-    // I4: psi(1) + C1
-    MISR_PAIRED(item_psi(I1c(), m, k), N_C1, item_C1(ko))
+    // I4: adjoint horizontal blur
+    for (int it = tid; it < N_C1; it += NT) item_C1(it);
     __syncthreads();
-    // I5: gather(1) + C2
-    MISR_PAIRED(item_gather(I1c(), m, k), N_C2, item_C2(ko))
-    __syncthreads();
-    // I6: psi(2) + horizontal blur of p
-    MISR_PAIRED(item_psi(I2c(), m, k), N_HP, item_HP(ko))
-    __syncthreads();
-    // I7: gather(2) and r'
-#pragma unroll
-    for (int i = 0; i < NDI; ++i) {
-        const int it = tid + i * NT;
-        if (it < ND) {
-            item_gather(I2c(), i, it);
-            item_r(i, it);
-        }
-    }
+    // I5: adjoint vertical blur and r'
+    for (int it = tid; it < N_C2; it += NT) item_C2r(it);
     A.jb += jb2.x + jb2.y;
     __syncthreads();
-    // I8: horizontal blur of r'
-    for (int it = tid; it < N_HR; it += NT) item_HR(it);
-    __syncthreads();
-    // I9: curvature forms
-    for (int it = tid; it < N_E; it += NT) item_E(it);
-#undef MISR_PAIRED
-}
-
-// Fixed-order FP64 sum of `count` records of NPART doubles at src: the records are staged in
-// shared memory, warp j sums field j over its lanes in a fixed order.
-template <int NT>
-__device__ __forceinline__ void tree_sum_npart(const double *src, int count, double *stage, double *out) {
-    static_assert(NT / 32 >= NPART, "one warp per partial");
-    const int tid = threadIdx.x;
-    for (int k = tid; k < count * NPART; k += NT) stage[k] = ld_cg(src + k);
-    __syncthreads();
-    const int j = tid >> 5, l = tid & 31;
-    if (j < NPART) {
-        double s = 0.0;
-        for (int i = l; i < count; i += 32) s += stage[i * NPART + j];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (l == 0) out[j] = s;
+    // I6: horizontal blurs of r' and p (HS is free once C2 has read it)
+    for (int it = tid; it < N_HR + N_HP; it += NT) {
+        if (it < N_HR) item_HR(it);
+        else item_HP(it - N_HR);
     }
     __syncthreads();
+    // I7: curvature forms
+    for (int it = tid; it < N_E; it += NT) item_E(it);
+    return y_late;
 }
 
+// Sum of `count` field-major records (`stride` apart) by one warp in a fixed order (a lane
+// sums its strided share in order, then a fixed butterfly); every lane gets the totals.
+__device__ __forceinline__ void warp_sum_fields(const double *src, size_t stride, int count, double *v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NPART; ++j) {
+        double a = 0.0;
+        for (int i = lane; i < count; i += 32) a += ld_cg(src + (size_t)j * stride + i);
+        v[j] = a;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int j = 0; j < NPART; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+}
+
+// Warp 0's share of the pass reduction after tile t of problem P (lanes < NPART hold the
+// tile's sums): write them; the warp that completes a group of P.group tiles sums the group;
+// the warp that completes the last group sums the groups and runs the SCG tail.  Every sum has
+// a fixed order whichever CTA does it, so a projection's totals do not depend on what else
+// shares the launch or on the order the tiles were run in.
+__device__ __noinline__ void tile_done(const DevProblem &P, int t, double tv, int mode) {
+    const int lane = threadIdx.x & 31;
+    if (lane < NPART) P.partials[(size_t)lane * P.n_tiles + t] = tv;
+    __syncwarp();
+    const int g = t / P.group;
+    const int gsize = min(P.group, P.n_tiles - g * P.group);
+    unsigned old = 0;
+    if (lane == 0) {
+        __threadfence();
+        old = atomicAdd(&P.gcount[g], 1u);
+    }
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != (unsigned)(gsize - 1)) return;
+    __threadfence();
+    double v[NPART];
+    warp_sum_fields(P.partials + (size_t)g * P.group, P.n_tiles, gsize, v);
+    if (lane < NPART) {
+        double mine = v[0];
+#pragma unroll
+        for (int j = 1; j < NPART; ++j) mine = lane == j ? v[j] : mine;
+        P.gpartials[(size_t)lane * P.n_groups + g] = mine;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        P.gcount[g] = 0u;
+        __threadfence();
+        old = atomicAdd(P.counter, 1u);
+    }
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != (unsigned)(P.n_groups - 1)) return;
+    __threadfence();
+    warp_sum_fields(P.gpartials, P.n_groups, P.n_groups, v);
+    if (lane == 0) {
+        scg_tail(P, P.st, v, mode);
+        *P.counter = 0u;
+        __threadfence();
+    }
+}
+
+// Launch-wide failure: a tile load of this CTA did not land in time.  The projection of the
+// tile is flagged (its sums of this pass are incomplete) and stops; the CTA stops taking tiles.
+__device__ __noinline__ void flag_timeout(const DevProblem &P) {
+    atomicExch(&P.st->status, (int)DEV_TMA_TIMEOUT);
+    atomicExch(&P.st->done, 1);
+}
+
+// Per-tile context of the persistent pass, in shared memory: written by the scheduling thread
+// at the top of each tile, read by every thread after the barrier that follows.  Keeping the
+// loop state here (not in registers) leaves the fused pass its registers.
+struct PassCtx {
+    const DevProblem *P;
+    float *Xn, *Rn, *Pn;
+    float alpha, beta;
+    int y0, x0, t, end;
+    uint32_t phase;
+    int restage;
+    // scheduler state
+    int next, cached, ntile, cur, pcur;
+};
+
+// The scheduling thread: take the CTA's next tile (the first one is blockIdx.x, later ones come
+// from the launch's tile counter), skipping problems that are done; publish it in c, issue its
+// TMA loads and warm L2 with the tile one resident wave ahead (the tile counter hands out
+// tiles in order, so that is about when another CTA will need it).
+template <int TH, int TW>
+__device__ __forceinline__ unsigned schedule_tile(PassCtx &c, const DevProblem *__restrict__ probs,
+                                              const int2 *__restrict__ tiles, int n_tiles, unsigned *work, int mode,
+                                              double probe_alpha, double probe_beta, float *sm, uint64_t *bar) {
+    using Gm = Geo<TH, TW>;
+    int k = c.next;
+    int2 wt = make_int2(0, 0);
+    const DevProblem *P = c.P;
+    for (;; k = (int)atomicAdd(&work[0], 1u) + (int)gridDim.x) {
+        if (k >= n_tiles) {
+            c.end = 1;
+            return 0u;
+        }
+        wt = tiles[k];
+        if (wt.x != c.cached) {
+            P = &probs[wt.x];
+            const ScgState *st = P->st;
+            c.cached = wt.x;
+            c.P = P;
+            c.restage = 1;
+            c.cur = ld_cg(&st->cur);
+            c.pcur = ld_cg(&st->pcur);
+            c.alpha = mode == MODE_PROBE ? (float)probe_alpha : __ldcg(&st->alpha_f);
+            c.beta = mode == MODE_PROBE ? (float)probe_beta : __ldcg(&st->beta_f);
+            c.Xn = P->X[c.cur ^ 1];
+            c.Rn = P->Rv[c.cur ^ 1];
+            c.Pn = P->Pv[c.pcur ^ 1];
+        }
+        if (!ld_cg(&P->st->done)) break;
+    }
+    // the CTA's following tile; the caller stores it once the loads are in flight
+    const unsigned nxt = atomicAdd(&work[0], 1u);
+    c.t = wt.y;
+    c.y0 = (wt.y / P->tiles_x) * TH;
+    c.x0 = (wt.y % P->tiles_x) * TW;
+    c.phase = (uint32_t)(c.ntile & 1);
+    ++c.ntile;
+    const int cur = c.cur, pcur = c.pcur;
+    // generic-proxy accesses of the previous tile are ordered before these async writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    constexpr uint32_t box_x = sizeof(float) * Gm::XH * Gm::XW;
+    constexpr uint32_t box_y = sizeof(float) * Gm::EH * Gm::EW;
+    mbar_arrive_expect_tx(&bar[0], 3 * box_x);
+    tma_load_2d(sm, &P->tmX[cur], c.x0 - 8, c.y0 - 6, &bar[0]);
+    tma_load_2d(sm + Gm::XH * Gm::XW, &P->tmP[pcur], c.x0 - 8, c.y0 - 6, &bar[0]);
+    tma_load_2d(sm + 2 * Gm::XH * Gm::XW, &P->tmR[cur], c.x0 - 8, c.y0 - 6, &bar[0]);
+    mbar_arrive_expect_tx(&bar[1], box_y);
+    tma_load_2d(sm + 3 * Gm::XH * Gm::XW, &P->tmY, c.x0 - 4, c.y0 - 4, &bar[1]);
+    const int ka = k + (int)gridDim.x;
+    if (ka < n_tiles) {
+        const int2 wa = tiles[ka];
+        if (wa.x == wt.x) {
+            const int ny = (wa.y / P->tiles_x) * TH, nx = (wa.y % P->tiles_x) * TW;
+            tma_prefetch_l2_2d(&P->tmX[cur], nx - 8, ny - 6);
+            tma_prefetch_l2_2d(&P->tmP[pcur], nx - 8, ny - 6);
+            tma_prefetch_l2_2d(&P->tmR[cur], nx - 8, ny - 6);
+            tma_prefetch_l2_2d(&P->tmY, nx - 4, ny - 4);
+        }
+    }
+    return nxt;
+}
+
+// The fused SCG pass, persistent: one CTA per resident slot takes tiles (problem, tile) from
+// the launch's tile list until it runs out.  Thread 32 schedules the tiles and issues their
+// loads; warp 0 reduces each tile's sums while the next tile loads.  `work` (two counters,
+// zero at launch) is the launch's tile counter; the last CTA to finish zeroes it again.
 template <int TH, int TW, int NT>
 __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__restrict__ probs,
-                                                         const int2 *__restrict__ tile_map, int mode,
-                                                         double probe_alpha, double probe_beta,
-                                                         int prefetch_stride) {
+                                                         const int2 *__restrict__ tiles, int n_tiles,
+                                                         unsigned *work, int mode, double probe_alpha,
+                                                         double probe_beta) {
     using Gm = Geo<TH, TW>;
     constexpr int NWARP = NT / 32;
-    static_assert(Gm::FLOATS * sizeof(float) >= 1024 * NPART * sizeof(double),
-                  "the tile buffers must hold the group sums of the reduction");
-    extern __shared__ unsigned char smem_raw[];
-    float *sm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned tile buffers (TMA destinations), derived from the shared array by
+    // pointer arithmetic so that the accesses stay shared-memory accesses
+    float *sm = reinterpret_cast<float *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
     unsigned char *smp = reinterpret_cast<unsigned char *>(sm + Gm::FLOATS);
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float cs[C_N];
     __shared__ float red[NWARP][NPART];
     __shared__ float red_lo[NWARP];
-    __shared__ double tot[NPART];
-    __shared__ int s_last, s_fail;
+    __shared__ PassCtx ctx;
 
-    const int2 tm = tile_map[blockIdx.x];
-    const DevProblem &P = probs[tm.x];
-    ScgState *st = P.st;
-    if (ld_cg(&st->done)) return;
-
-    const int tid = threadIdx.x;
-    const int cur = ld_cg(&st->cur), pcur = ld_cg(&st->pcur);
-    const float alpha = mode == MODE_PROBE ? (float)probe_alpha : __ldcg(&st->alpha_f);
-    const float beta = mode == MODE_PROBE ? (float)probe_beta : __ldcg(&st->beta_f);
-    const int y0 = (tm.y / P.tiles_x) * TH, x0 = (tm.y % P.tiles_x) * TW;
-
-    // tile loads: x, r, p_old boxes (zero outside the image) on bar[0]; the Y box (NaN
-    // outside) on bar[1], first needed by the residual stage
-    if (tid == 0) {
-        s_fail = 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int SCHED_TID = 32;
+    if (tid == SCHED_TID) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_barrier_init();
+        ctx.P = nullptr;
+        ctx.next = blockIdx.x;
+        ctx.cached = -1;
+        ctx.ntile = 0;
+        ctx.end = 0;
     }
-    if (tid < 5) { cs[C_HX + tid] = P.hx[tid]; cs[C_HY + tid] = P.hy[tid]; }
-    if (tid < 9) {
-        cs[C_GAM + tid] = P.gamma[tid];
-        cs[C_CW + tid] = P.lambda * P.eps2 * P.gamma[tid];
-    }
-    if (tid == 0) { cs[C_LAMBDA] = P.lambda; cs[C_EPS2] = P.eps2; }
     __syncthreads();
-    if (tid == 0) {
-        constexpr uint32_t box_x = sizeof(float) * Gm::XH * Gm::XW;
-        constexpr uint32_t box_y = sizeof(float) * Gm::EH * Gm::EW;
-        mbar_arrive_expect_tx(&bar[0], 3 * box_x);
-        tma_load_2d(sm, &P.tmX[cur], x0 - 8, y0 - 6, &bar[0]);
-        tma_load_2d(sm + Gm::XH * Gm::XW, &P.tmP[pcur], x0 - 8, y0 - 6, &bar[0]);
-        tma_load_2d(sm + 2 * Gm::XH * Gm::XW, &P.tmR[cur], x0 - 8, y0 - 6, &bar[0]);
-        mbar_arrive_expect_tx(&bar[1], box_y);
-        tma_load_2d(sm + 3 * Gm::XH * Gm::XW, &P.tmY, x0 - 4, y0 - 4, &bar[1]);
-        // warm L2 with the inputs of the tile one resident wave ahead (same problem only)
-        const int ahead = blockIdx.x + prefetch_stride;
-        if (prefetch_stride > 0 && ahead < (int)gridDim.x) {
-            const int2 tn = tile_map[ahead];
-            if (tn.x == tm.x) {
-                const int ny = (tn.y / P.tiles_x) * TH, nx = (tn.y % P.tiles_x) * TW;
-                tma_prefetch_l2_2d(&P.tmX[cur], nx - 8, ny - 6);
-                tma_prefetch_l2_2d(&P.tmP[pcur], nx - 8, ny - 6);
-                tma_prefetch_l2_2d(&P.tmR[cur], nx - 8, ny - 6);
-                tma_prefetch_l2_2d(&P.tmY, nx - 4, ny - 4);
+    for (;;) {
+        unsigned nxt = 0;
+        if (tid == SCHED_TID)
+            nxt = schedule_tile<TH, TW>(ctx, probs, tiles, n_tiles, work, mode, probe_alpha, probe_beta, sm, bar);
+        __syncthreads();
+        if (ctx.end) break;
+        const DevProblem &P = *ctx.P;
+        if (ctx.restage) {
+            if (tid < 5) { cs[C_HX + tid] = P.hx[tid]; cs[C_HY + tid] = P.hy[tid]; }
+            if (tid < 9) {
+                cs[C_GAM + tid] = P.gamma[tid];
+                cs[C_CW + tid] = P.lambda * P.eps2 * P.gamma[tid];
+            }
+            if (tid == 0) {
+                cs[C_LAMBDA] = P.lambda;
+                cs[C_EPS2] = P.eps2;
+                cs[C_FMAG] = __uint_as_float(P.f > 1 ? (unsigned)((0x100000000ull + P.f - 1) / P.f) : 0u);
             }
         }
-    }
-    if (!mbar_wait_bounded(&bar[0], 0, TMA_WAIT_TRIES)) s_fail = 1;
-    __syncthreads();
-    if (s_fail) {
-        // the loads did not complete in time: flag the state and stop this projection
-        if (tid == 0) {
-            atomicExch(&st->status, (int)DEV_TMA_TIMEOUT);
-            atomicExch(&st->done, 1);
-            mbar_wait_bounded(&bar[0], 0, TMA_WAIT_TRIES);   // let copies in flight land
-            mbar_wait_bounded(&bar[1], 0, TMA_WAIT_TRIES);
+        const uint32_t phase = ctx.phase;
+        const bool landed = mbar_wait_bounded(&bar[0], phase, TMA_WAIT_TRIES);
+        if (__syncthreads_or(!landed)) {
+            // the loads did not land in time: flag the projection, let the copies in flight
+            // land, and stop taking tiles
+            if (tid == SCHED_TID) {
+                flag_timeout(P);
+                mbar_wait_bounded(&bar[0], phase, TMA_WAIT_TRIES);
+                mbar_wait_bounded(&bar[1], phase, TMA_WAIT_TRIES);
+            }
+            break;
         }
-        return;
-    }
+        if (tid == SCHED_TID) {
+            ctx.restage = 0;
+            ctx.next = (int)nxt + (int)gridDim.x;
+        }
 
-    PassAcc A = {};
-    float *Xn = P.X[cur ^ 1], *Rn = P.Rv[cur ^ 1], *Pn = P.Pv[pcur ^ 1];
-    const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
-    if (border) pass_tile<TH, TW, NT, true>(P, sm, smp, cs, &bar[1], y0, x0, alpha, beta, Xn, Rn, Pn, A);
-    else pass_tile<TH, TW, NT, false>(P, sm, smp, cs, &bar[1], y0, x0, alpha, beta, Xn, Rn, Pn, A);
+        PassAcc A = {};
+        bool y_late;
+        {
+            const int y0 = ctx.y0, x0 = ctx.x0;
+            const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
+            if (border)
+                y_late = pass_tile<TH, TW, NT, true>(P, sm, smp, cs, &bar[1], phase, y0, x0, ctx.alpha, ctx.beta,
+                                                     ctx.Xn, ctx.Rn, ctx.Pn, A);
+            else
+                y_late = pass_tile<TH, TW, NT, false>(P, sm, smp, cs, &bar[1], phase, y0, x0, ctx.alpha, ctx.beta,
+                                                      ctx.Xn, ctx.Rn, ctx.Pn, A);
+        }
 
-    // --- FP32 warp sums, FP64 across warps: the tile's partial sums.  The prior's value
-    // enters Moller's comparison as a difference of two passes' sums, so its warp sum is
-    // compensated (two-sum: hi + lo carries the rounding error of every addition).
-    float v[NPART] = {A.jd, A.dj, A.jb, A.rr, A.rrx, A.pr, A.pp, A.a, A.b, A.c};
-    const int lane = tid & 31, warp = tid >> 5;
+        // FP32 warp sums.  The prior's value enters Moller's comparison as a difference of
+        // two passes' sums, so its sums are compensated (two-sum: hi + lo carries the
+        // rounding error of every addition).
+        float v[NPART] = {A.jd, A.dj, A.jb, A.rr, A.rrx, A.pr, A.pp, A.a, A.b, A.c};
 #pragma unroll
-    for (int j = 0; j < NPART; ++j) {
-        if (j == P_JB) continue;
-        float x = v[j];
+        for (int j = 0; j < NPART; ++j) {
+            if (j == P_JB) continue;
+            float x = v[j];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-        if (lane == 0) red[warp][j] = x;
-    }
-    {
-        float hi = v[P_JB], lo = 0.f;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float h2 = __shfl_down_sync(0xffffffffu, hi, off);
-            const float l2 = __shfl_down_sync(0xffffffffu, lo, off);
-            const float s = hi + h2, bb = s - hi;
-            const float err = (hi - (s - bb)) + (h2 - bb);
-            hi = s;
-            lo = lo + l2 + err;
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+            if (lane == 0) red[warp][j] = x;
         }
-        if (lane == 0) { red[warp][P_JB] = hi; red_lo[warp] = lo; }
-    }
-    __syncthreads();
-    // two-level deterministic reduction: the last tile of each group of P.group tiles sums
-    // the group in a fixed order, the last group sums the groups and runs the SCG tail
-    const int g = tm.y / P.group;
-    const int gsize = min(P.group, P.n_tiles - g * P.group);
-    if (tid < NPART) {
-        double s;
-        if (tid == P_JB) {
-            s = 0.0;
-            for (int w = 0; w < NWARP; ++w) s += (double)red[w][tid] + (double)red_lo[w];
-        } else {
-            float sf = 0.f;
+        {
+            float hi = v[P_JB], lo = 0.f;
 #pragma unroll
-            for (int w = 0; w < NWARP; ++w) sf += red[w][tid];
-            s = (double)sf;
+            for (int off = 16; off > 0; off >>= 1) {
+                const float h2 = __shfl_down_sync(0xffffffffu, hi, off);
+                const float l2 = __shfl_down_sync(0xffffffffu, lo, off);
+                const float s = hi + h2, bb = s - hi;
+                const float err = (hi - (s - bb)) + (h2 - bb);
+                hi = s;
+                lo = lo + l2 + err;
+            }
+            if (lane == 0) { red[warp][P_JB] = hi; red_lo[warp] = lo; }
         }
-        P.partials[(size_t)tm.y * NPART + tid] = s;
-        __threadfence();
+        // warp 0 takes what it needs of the context before the scheduler moves on
+        const DevProblem *Pt = ctx.P;
+        const int t = ctx.t;
+        // also: every thread is done with the tile buffers and the context
+        if (__syncthreads_or(y_late)) {
+            if (tid == SCHED_TID) {
+                flag_timeout(P);
+                mbar_wait_bounded(&bar[1], phase, TMA_WAIT_TRIES);
+            }
+            break;
+        }
+        if (warp == 0) {
+            double tv = 0.0;
+            if (lane < NPART) {
+                float hi = 0.f, lo = 0.f;
+#pragma unroll
+                for (int w = 0; w < NWARP; ++w) {
+                    const float x = red[w][lane];
+                    const float s = hi + x, bb = s - hi;
+                    lo += ((hi - (s - bb)) + (x - bb)) + (lane == P_JB ? red_lo[w] : 0.f);
+                    hi = s;
+                }
+                tv = lane == P_JB ? (double)hi + (double)lo : (double)hi;
+            }
+            tile_done(*Pt, t, tv, mode);
+        }
     }
+    // the last CTA to stop zeroes the launch's tile counter for the next launch
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&P.gcount[g], 1u) == (unsigned)(gsize - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double *stage = reinterpret_cast<double *>(sm);   // the tile buffers are free now
-    tree_sum_npart<NT>(P.partials + (size_t)g * P.group * NPART, gsize, stage, tot);
-    if (tid < NPART) {
-        P.gpartials[(size_t)g * NPART + tid] = tot[tid];
-        __threadfence();
-    }
-    if (tid == 0) P.gcount[g] = 0u;
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(P.counter, 1u) == (unsigned)(P.n_groups - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    tree_sum_npart<NT>(P.gpartials, P.n_groups, stage, tot);
     if (tid == 0) {
-        double S[NPART];
-        for (int j = 0; j < NPART; ++j) S[j] = tot[j];
-        scg_tail(P, st, S, mode);
-        *P.counter = 0u;
         __threadfence();
+        if (atomicAdd(&work[1], 1u) == gridDim.x - 1) {
+            work[0] = 0u;
+            work[1] = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -811,6 +924,9 @@ __global__ void prepare_kernel(const DevProblem *__restrict__ probs, int pidx, c
         st->lam = 1e-6; st->lam_bar = 0.0; st->iters = P.iters;
         *P.counter = 0u;
     }
+    if (flags & 4)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n_groups; i += gridDim.x * blockDim.x)
+            P.gcount[i] = 0u;
     for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         const int cy = (int)(o / pitch), cx = (int)(o - (size_t)cy * pitch);
         float yv = __int_as_float(0x7fc00000);  // NaN: no frame samples this pixel

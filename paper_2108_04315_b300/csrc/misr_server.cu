@@ -77,12 +77,12 @@ struct Slot {
     bool busy = false;
     uint64_t ticket = 0;
     int passes = 0;        // fused passes run since admission
-    int2 *tiles = nullptr;  // device tile map of this slot alone (for its init pass)
+    int2 *items = nullptr;  // device tile list of this slot alone (for its init pass)
 };
 
 size_t plan_bytes_estimate(const misr_desc &d) {
     const size_t H = (size_t)d.factor * d.lr_h, W = (size_t)d.factor * d.lr_w, pitch = (W + 3) & ~size_t(3);
-    const size_t tiles = ((H + 31) / 32) * ((W + 63) / 64);
+    const size_t tiles = ((H + 31) / 32) * ((W + 63) / 64);   // groups and blocks are at most this
     return 7 * ((H * pitch * 4 + 255) / 256 * 256) + tiles * 100 + (size_t)std::max(d.iters, 1) * 80 + (1 << 16);
 }
 
@@ -103,28 +103,29 @@ struct misr_server_s {
     size_t slot_bytes = 0;
     cudaStream_t stream = nullptr;
     DevProblem *dprobs = nullptr;   // one record per slot (capacity cfg.max_slots)
-    int2 *dtiles = nullptr;         // tile map of the live slots
-    size_t dtiles_cap = 0;
+    int2 *ditems = nullptr;         // tile list of the live slots
+    unsigned int *work = nullptr;   // the fused pass's tile counter
+    size_t ditems_cap = 0;
     ScgState *st_host = nullptr;    // page-locked states, one per slot
-    std::vector<int2> h_tiles;
-    bool tiles_dirty = true;
+    std::vector<int2> h_items;
+    bool items_dirty = true;
     misr_status worker_error = MISR_OK;
     uint64_t passes_launched = 0;
 };
 
 namespace {
 
-misr_status grow_tiles(misr_server_t s, size_t need) {
-    if (need <= s->dtiles_cap) return MISR_OK;
-    size_t cap = std::max<size_t>(need, 2 * s->dtiles_cap);
-    if (s->dtiles) {
+misr_status grow_items(misr_server_t s, size_t need) {
+    if (need <= s->ditems_cap) return MISR_OK;
+    size_t cap = std::max<size_t>(need, 2 * s->ditems_cap);
+    if (s->ditems) {
         CK(cudaStreamSynchronize(s->stream));
-        cudaFree(s->dtiles);
-        s->dtiles = nullptr;
+        cudaFree(s->ditems);
+        s->ditems = nullptr;
     }
-    cudaError_t e = cudaMalloc(&s->dtiles, cap * sizeof(int2));
-    if (e != cudaSuccess) { cudaGetLastError(); s->dtiles_cap = 0; return fail(MISR_ENOMEM, "tile map: %s", cudaGetErrorString(e)); }
-    s->dtiles_cap = cap;
+    cudaError_t e = cudaMalloc(&s->ditems, cap * sizeof(int2));
+    if (e != cudaSuccess) { cudaGetLastError(); s->ditems_cap = 0; return fail(MISR_ENOMEM, "work items: %s", cudaGetErrorString(e)); }
+    s->ditems_cap = cap;
     return MISR_OK;
 }
 
@@ -146,9 +147,9 @@ bool evict_idle(misr_server_t s, const DescCopy &want) {
             cudaStreamSynchronize(s->stream);
             s->slot_bytes -= plan_bytes_estimate(sl.desc.d);
             misr_plan_destroy(sl.plan);
-            cudaFree(sl.tiles);
+            cudaFree(sl.items);
             sl.plan = nullptr;
-            sl.tiles = nullptr;
+            sl.items = nullptr;
             // keep the slot index (records are per index); mark it empty
             return true;
         }
@@ -190,15 +191,15 @@ std::vector<int> admit(misr_server_t s) {
                     s->slot_bytes += plan_bytes_estimate(rq.desc.d);
                     std::vector<int2> t(p->hp.n_tiles);
                     for (int k = 0; k < p->hp.n_tiles; ++k) t[k] = make_int2(idx, k);
-                    bool ok2 = cudaMalloc(&sl.tiles, sizeof(int2) * t.size()) == cudaSuccess &&
-                               cudaMemcpy(sl.tiles, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                    bool ok2 = cudaMalloc(&sl.items, sizeof(int2) * t.size()) == cudaSuccess &&
+                               cudaMemcpy(sl.items, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                                cudaMemcpy(&s->dprobs[idx], &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice) == cudaSuccess;
                     if (!ok2) {
                         cudaGetLastError();
                         misr_plan_destroy(p);
-                        if (sl.tiles) cudaFree(sl.tiles);
+                        if (sl.items) cudaFree(sl.items);
                         sl.plan = nullptr;
-                        sl.tiles = nullptr;
+                        sl.items = nullptr;
                         s->slot_bytes -= plan_bytes_estimate(rq.desc.d);
                     } else {
                         use = idx;
@@ -230,7 +231,7 @@ std::vector<int> admit(misr_server_t s) {
         rq.t_start = now_s();
         started.push_back(use);
         it = s->queue.erase(it);
-        s->tiles_dirty = true;
+        s->items_dirty = true;
     }
     return started;
 }
@@ -251,7 +252,7 @@ void finish(misr_server_t s, int idx, misr_status st_code) {
     rq.state = st_code == MISR_OK ? RQ_DONE : RQ_FAILED;
     rq.t_end = now_s();
     sl.busy = false;
-    s->tiles_dirty = true;
+    s->items_dirty = true;
 }
 
 void worker_main(misr_server_t s) {
@@ -281,25 +282,25 @@ void worker_main(misr_server_t s) {
             misr_plan_t p = sl.plan;
             if (r == MISR_OK)
                 r = launch_prepare_raw(s->dprobs, idx, p->d, p->n_pitched, rq->y, rq->x, p->d.x0_mode, 1 | 2 | 4, s->stream);
-            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.tiles, p->hp.n_tiles, MODE_INIT, 0.0, 0.0, s->stream);
+            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, p->hp.n_tiles, s->work, MODE_INIT, 0.0, 0.0, s->stream);
         }
         // 2. the live slots' tile map
-        if (r == MISR_OK && s->tiles_dirty) {
-            s->h_tiles.clear();
+        if (r == MISR_OK && s->items_dirty) {
+            s->h_items.clear();
             for (size_t i = 0; i < s->slots.size(); ++i)
                 if (s->slots[i].busy)
-                    for (int k = 0; k < s->slots[i].plan->hp.n_tiles; ++k) s->h_tiles.push_back(make_int2((int)i, k));
-            r = grow_tiles(s, std::max<size_t>(s->h_tiles.size(), 1));
-            if (r == MISR_OK && !s->h_tiles.empty() &&
-                cudaMemcpyAsync(s->dtiles, s->h_tiles.data(), sizeof(int2) * s->h_tiles.size(), cudaMemcpyHostToDevice,
+                    for (int k = 0; k < s->slots[i].plan->hp.n_tiles; ++k) s->h_items.push_back(make_int2((int)i, k));
+            r = grow_items(s, std::max<size_t>(s->h_items.size(), 1));
+            if (r == MISR_OK && !s->h_items.empty() &&
+                cudaMemcpyAsync(s->ditems, s->h_items.data(), sizeof(int2) * s->h_items.size(), cudaMemcpyHostToDevice,
                                 s->stream) != cudaSuccess)
                 r = fail(MISR_ECUDA, "tile map upload failed");
-            s->tiles_dirty = false;
+            s->items_dirty = false;
         }
         // 3. k SCG iterations of every live projection, one launch each
-        const int nt = (int)s->h_tiles.size();
+        const int nt = (int)s->h_items.size();
         for (int it = 0; it < k_passes && r == MISR_OK && nt > 0; ++it) {
-            r = launch_pass_raw(s->dprobs, s->dtiles, nt, MODE_ITER, 0.0, 0.0, s->stream);
+            r = launch_pass_raw(s->dprobs, s->ditems, nt, s->work, MODE_ITER, 0.0, 0.0, s->stream);
             ++s->passes_launched;
         }
         // 4. completion: read the live states, copy finished projections out
@@ -363,12 +364,15 @@ extern "C" misr_status misr_server_create(const misr_server_cfg *cfg, misr_serve
     cudaGetDevice(&s->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->dprobs, sizeof(DevProblem) * cfg->max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->work, 256);
+    if (e == cudaSuccess) e = cudaMemset(s->work, 0, 256);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->st_host, sizeof(ScgState) * cfg->max_slots);
     if (e != cudaSuccess) {
         cudaGetLastError();
         misr_status r = fail(MISR_ENOMEM, "server setup: %s", cudaGetErrorString(e));
         if (s->stream) cudaStreamDestroy(s->stream);
         if (s->dprobs) cudaFree(s->dprobs);
+        if (s->work) cudaFree(s->work);
         delete s;
         return r;
     }
@@ -390,10 +394,11 @@ extern "C" misr_status misr_server_destroy(misr_server_t s) {
     cudaStreamSynchronize(s->stream);
     for (auto &sl : s->slots) {
         if (sl.plan) misr_plan_destroy(sl.plan);
-        if (sl.tiles) cudaFree(sl.tiles);
+        if (sl.items) cudaFree(sl.items);
     }
-    if (s->dtiles) cudaFree(s->dtiles);
+    if (s->ditems) cudaFree(s->ditems);
     if (s->dprobs) cudaFree(s->dprobs);
+    if (s->work) cudaFree(s->work);
     if (s->st_host) cudaFreeHost(s->st_host);
     cudaStreamDestroy(s->stream);
     delete s;

@@ -32,7 +32,7 @@ constexpr int NPART = 10;
 constexpr int TRACE_COLS = 10;
 constexpr uint32_t TMA_WAIT_TRIES = 1u << 24;   // bounded wait for the tile loads
 
-// per-tile partial sums of one pass (FP64)
+// partial sums of one pass (FP64)
 enum { P_JD = 0, P_DJD, P_JB, P_RR, P_RRX, P_PR, P_PP, P_A, P_B, P_C };
 enum { MODE_INIT = 0, MODE_ITER = 1, MODE_PROBE = 2 };
 // device status codes (ScgState::status)
@@ -65,11 +65,14 @@ struct DevProblem {
     double eps_pairs;                             // eps * sum_d gamma_d * #pairs_d
     float *X[2], *Rv[2], *Pv[2];                  // x, r (double buffered), p (double buffered)
     float *Y;                                     // interleaved frames, NaN where unsampled
-    double *partials;                             // [n_tiles][NPART] per-tile sums
-    double *gpartials;                            // [n_groups][NPART] per-group sums
+    // Fixed-order reduction of a pass's sums: every tile writes its sums; whoever finishes the
+    // last tile of a group of `group` tiles sums the group in tile order; whoever finishes the
+    // last group sums the groups in order and runs the SCG tail.  Field-major arrays.
+    double *partials;                             // [NPART][n_tiles] tile sums
+    double *gpartials;                            // [NPART][n_groups] group sums
     unsigned int *gcount;                         // [n_groups] tiles of the group finished
     unsigned int *counter;                        // groups finished in the current pass
-    int group, n_groups;                          // tiles per group, number of groups
+    int group, n_groups;                          // tiles per group, groups
     ScgState *st;
     double *trace;                                // [iters][TRACE_COLS]
     int ty[MAXK], tx[MAXK];
