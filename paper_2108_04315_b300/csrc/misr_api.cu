@@ -150,14 +150,25 @@ static int resident_ctas() {
 static int pass_grid(int n_items) { return std::max(1, std::min(n_items, resident_ctas())); }
 
 static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double beta, cudaStream_t s) {
-    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<pass_grid(p->hp.n_tiles), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
-        p->dprob, p->dtile, p->hp.n_tiles, p->work, mode, alpha, beta);
-    CK(cudaGetLastError());
-    return MISR_OK;
+    return launch_pass_raw(p->dprob, p->dtile, p->hp.n_tiles, p->dgroup, p->hp.n_groups, p->work, mode, alpha, beta, s);
 }
 
 // Groups of the pass reduction: at least 64 tiles, at most 128 groups (the last group's
 // warp sums all groups).
+// The tile list (border tiles first: they cost more, so the pass ends on interior tiles)
+// and the group list of problem `pi`, appended to the launch's lists.
+void misr_host::append_tiles(const DevProblem &hp, int pi, std::vector<int2> &tiles, std::vector<int2> &groups) {
+    const int ty = hp.tiles_y, tx = hp.tiles_x;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int t = 0; t < hp.n_tiles; ++t) {
+            const int y0 = (t / tx) * TILE_H, x0 = (t % tx) * TILE_W;
+            const bool border = y0 - 6 < 0 || x0 - 8 < 0 || y0 + TILE_H + 6 > hp.H || x0 + TILE_W + 8 > hp.W;
+            if (border == (pass == 0)) tiles.push_back(make_int2(pi, t));
+        }
+    (void)ty;
+    for (int g = 0; g < hp.n_groups; ++g) groups.push_back(make_int2(pi, g));
+}
+
 static void set_groups(DevProblem &hp) {
     hp.group = 64;
     while ((hp.n_tiles + hp.group - 1) / hp.group > 128) hp.group *= 2;
@@ -178,13 +189,16 @@ static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float 
     return MISR_OK;
 }
 
-misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, int n_tiles, unsigned *work,
-                                       int mode, double alpha, double beta, cudaStream_t s) {
+misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, int n_tiles, const int2 *groups,
+                                       int n_groups, unsigned *work, int mode, double alpha, double beta,
+                                       cudaStream_t s) {
     if (n_tiles <= 0) return MISR_OK;
     misr_status r = set_pass_attrs();
     if (r != MISR_OK) return r;
     scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<pass_grid(n_tiles), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
         probs, tiles, n_tiles, work, mode, alpha, beta);
+    CK(cudaGetLastError());
+    reduce_kernel<<<n_groups, 32, 0, s>>>(probs, groups, mode);
     CK(cudaGetLastError());
     return MISR_OK;
 }
@@ -300,6 +314,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     const size_t o_tr = off; off += align_up((size_t)std::max(d.iters, 1) * TRACE_COLS * sizeof(double), 256);
     const size_t o_pr = off; off += align_up(sizeof(DevProblem), 256);
     const size_t o_tm = off; off += align_up((size_t)hp.n_tiles * sizeof(int2), 256);
+    const size_t o_gl = off; off += align_up((size_t)hp.n_groups * sizeof(int2), 256);
     p->ws_bytes = off;
     cudaError_t e = cudaMalloc((void **)&p->ws, off);
     if (e != cudaSuccess) {
@@ -323,6 +338,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     hp.trace = (double *)(b + o_tr);
     p->dprob = (DevProblem *)(b + o_pr);
     p->dtile = (int2 *)(b + o_tm);
+    p->dgroup = (int2 *)(b + o_gl);
     {
         misr_status ms = get_encode_tiled();
         for (int i = 0; i < 2 && ms == MISR_OK; ++i) {
@@ -339,13 +355,14 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     }
     p->hp = hp;
 
-    std::vector<int2> tiles(hp.n_tiles);
-    for (int t = 0; t < hp.n_tiles; ++t) tiles[t] = make_int2(0, t);
+    std::vector<int2> tiles, groups;
+    append_tiles(hp, 0, tiles, groups);
     misr_status rs = MISR_OK;
     do {
         if ((e = cudaMemset(p->ws, 0, off)) != cudaSuccess) break;
         if ((e = cudaMemcpy(p->dprob, &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice)) != cudaSuccess) break;
         if ((e = cudaMemcpy(p->dtile, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(p->dgroup, groups.data(), groups.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) break;
         if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming)) != cudaSuccess) break;
         if ((e = cudaMallocHost((void **)&p->st_host, sizeof(ScgState))) != cudaSuccess) break;
@@ -566,7 +583,8 @@ constexpr size_t NA_O_WORK = NA_O_CNT + 256;
 constexpr size_t NA_O_ST = NA_O_WORK + 256;
 constexpr size_t NA_O_PROB = NA_O_ST + na_align(sizeof(ScgState), 256);
 constexpr size_t NA_O_TMAP = NA_O_PROB + na_align(sizeof(DevProblem), 256);
-constexpr size_t NOALLOC_BYTES = NA_O_TMAP + na_align(size_t(NOALLOC_MAX_TILES) * sizeof(int2), 256);
+constexpr size_t NA_O_GLIST = NA_O_TMAP + na_align(size_t(NOALLOC_MAX_TILES) * sizeof(int2), 256);
+constexpr size_t NOALLOC_BYTES = NA_O_GLIST + na_align(size_t(NOALLOC_MAX_GROUPS) * sizeof(int2), 256);
 
 }  // namespace
 
@@ -683,14 +701,25 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     DevProblem hp;
     s = noalloc_problem(*desc, base, hp);
     if (s != MISR_OK) return s;
-    int2 tiles[NOALLOC_MAX_TILES];
-    for (int t = 0; t < hp.n_tiles; ++t) tiles[t] = make_int2(0, t);
+    int2 tiles[NOALLOC_MAX_TILES], groups[NOALLOC_MAX_GROUPS];
+    {
+        int nt = 0;
+        for (int pass = 0; pass < 2; ++pass)   // border tiles first, as append_tiles orders them
+            for (int t = 0; t < hp.n_tiles; ++t) {
+                const int y0 = (t / hp.tiles_x) * TILE_H, x0 = (t % hp.tiles_x) * TILE_W;
+                const bool border = y0 - 6 < 0 || x0 - 8 < 0 || y0 + TILE_H + 6 > hp.H || x0 + TILE_W + 8 > hp.W;
+                if (border == (pass == 0)) tiles[nt++] = make_int2(0, t);
+            }
+        for (int g = 0; g < hp.n_groups; ++g) groups[g] = make_int2(0, g);
+    }
     DevProblem *dprob = reinterpret_cast<DevProblem *>(base + NA_O_PROB);
     int2 *dtile = reinterpret_cast<int2 *>(base + NA_O_TMAP);
+    int2 *dgroup = reinterpret_cast<int2 *>(base + NA_O_GLIST);
     unsigned int *work = reinterpret_cast<unsigned int *>(base + NA_O_WORK);
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(dprob, &hp, sizeof(DevProblem), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dtile, tiles, sizeof(int2) * hp.n_tiles, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dgroup, groups, sizeof(int2) * hp.n_groups, cudaMemcpyHostToDevice, st));
     // (prepare's state reset zeroes the group counters and the pass counter; the tile counter
     // is zero in a fresh scratch array and zeroed again by every pass)
     const float log_i0 = desc->in_dtype == MISR_U16 ? logf(desc->flat_field) : 0.f;
@@ -699,9 +728,8 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     prepare_kernel<<<grid_for(npitched, 256), 256, 0, st>>>(dprob, 0, y_dev, desc->in_dtype, log_i0, x_dev,
                                                            MISR_X0_GIVEN, 1 | 2 | 4);
     CK(cudaGetLastError());
-    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<pass_grid(hp.n_tiles), PASS_NT, PassGeo::SMEM_BYTES, st>>>(
-        dprob, dtile, hp.n_tiles, work, MODE_PROBE, 0.0, 0.0);
-    CK(cudaGetLastError());
+    s = launch_pass_raw(dprob, dtile, hp.n_tiles, dgroup, hp.n_groups, work, MODE_PROBE, 0.0, 0.0, st);
+    if (s != MISR_OK) return s;
     scale_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(hp.Rv[1], hp.pitch, -1.f, g_dev, hp.H, hp.W);
     CK(cudaGetLastError());
     ScgState hst;

@@ -22,7 +22,14 @@ __device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
 // Steps follow Moller's algorithm (the same order as Algorithm 1's loop body):
 // comparison parameter, accept/reject, lambda updates, beta, then the scaling of the next
 // curvature and the next step size.
-__device__ inline void scg_tail(const DevProblem &P, ScgState *st, const double *S, int mode) {
+__device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const double *S, int mode);
+// (the state is read once, updated in registers and written back once)
+__device__ inline void scg_tail(const DevProblem &P, ScgState *gst, const double *S, int mode) {
+    ScgState L = *gst;
+    scg_tail_local(P, &L, S, mode);
+    *gst = L;
+}
+__device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const double *S, int mode) {
     for (int i = 0; i < NPART; ++i) st->sums[i] = S[i];
     if (mode == MODE_PROBE) return;
     const double lambda = (double)P.lambda;
@@ -610,15 +617,26 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     return y_late;
 }
 
-// Sum of `count` field-major records (`stride` apart) by one warp in a fixed order (a lane
-// sums its strided share in order, then a fixed butterfly); every lane gets the totals.
+// Sum of `count` field-major records (`stride` apart) by one warp in a fixed order (lane l
+// sums elements l, l + 32, l + 64, ... in that order, then a fixed butterfly); every lane gets
+// the totals.  The loads of each chunk of 128 elements are issued together.
 __device__ __forceinline__ void warp_sum_fields(const double *src, size_t stride, int count, double *v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int j = 0; j < NPART; ++j) {
-        double a = 0.0;
-        for (int i = lane; i < count; i += 32) a += ld_cg(src + (size_t)j * stride + i);
-        v[j] = a;
+    for (int j = 0; j < NPART; ++j) v[j] = 0.0;
+    for (int base = 0; base < count; base += 128) {
+        double t[NPART][4];
+#pragma unroll
+        for (int j = 0; j < NPART; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = base + lane + 32 * k;
+                t[j][k] = i < count ? ld_cg(src + (size_t)j * stride + i) : 0.0;
+            }
+#pragma unroll
+        for (int j = 0; j < NPART; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[j] += t[j][k];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
@@ -626,25 +644,18 @@ __device__ __forceinline__ void warp_sum_fields(const double *src, size_t stride
         for (int j = 0; j < NPART; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
 }
 
-// Warp 0's share of the pass reduction after tile t of problem P (lanes < NPART hold the
-// tile's sums): write them; the warp that completes a group of P.group tiles sums the group;
-// the warp that completes the last group sums the groups and runs the SCG tail.  Every sum has
-// a fixed order whichever CTA does it, so a projection's totals do not depend on what else
-// shares the launch or on the order the tiles were run in.
-__device__ __noinline__ void tile_done(const DevProblem &P, int t, double tv, int mode) {
-    const int lane = threadIdx.x & 31;
-    if (lane < NPART) P.partials[(size_t)lane * P.n_tiles + t] = tv;
-    __syncwarp();
-    const int g = t / P.group;
+// The reduction of a pass, one warp per (problem, group): sum the group's tile sums in tile
+// order; the warp that completes the last group of its problem sums the groups in order and
+// runs the SCG tail.  Every sum has a fixed order whichever warp does it and whatever else
+// shares the launch.  Problems that are done are skipped (the pass skipped them too).
+__global__ void __launch_bounds__(32) reduce_kernel(const DevProblem *__restrict__ probs,
+                                                    const int2 *__restrict__ groups, int mode) {
+    const int lane = threadIdx.x;
+    const int2 gi = groups[blockIdx.x];
+    const DevProblem &P = probs[gi.x];
+    if (ld_cg(&P.st->done)) return;
+    const int g = gi.y;
     const int gsize = min(P.group, P.n_tiles - g * P.group);
-    unsigned old = 0;
-    if (lane == 0) {
-        __threadfence();
-        old = atomicAdd(&P.gcount[g], 1u);
-    }
-    old = __shfl_sync(0xffffffffu, old, 0);
-    if (old != (unsigned)(gsize - 1)) return;
-    __threadfence();
     double v[NPART];
     warp_sum_fields(P.partials + (size_t)g * P.group, P.n_tiles, gsize, v);
     if (lane < NPART) {
@@ -654,8 +665,8 @@ __device__ __noinline__ void tile_done(const DevProblem &P, int t, double tv, in
         P.gpartials[(size_t)lane * P.n_groups + g] = mine;
     }
     __syncwarp();
+    unsigned old = 0;
     if (lane == 0) {
-        P.gcount[g] = 0u;
         __threadfence();
         old = atomicAdd(P.counter, 1u);
     }
@@ -759,7 +770,7 @@ __device__ __forceinline__ unsigned schedule_tile(PassCtx &c, const DevProblem *
 
 // The fused SCG pass, persistent: one CTA per resident slot takes tiles (problem, tile) from
 // the launch's tile list until it runs out.  Thread 32 schedules the tiles and issues their
-// loads; warp 0 reduces each tile's sums while the next tile loads.  `work` (two counters,
+// loads; warp 0 writes each tile's sums, which reduce_kernel combines after the pass.  `work` (two counters,
 // zero at launch) is the launch's tile counter; the last CTA to finish zeroes it again.
 template <int TH, int TW, int NT>
 __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__restrict__ probs,
@@ -867,8 +878,8 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
             if (lane == 0) { red[warp][P_JB] = hi; red_lo[warp] = lo; }
         }
         // warp 0 takes what it needs of the context before the scheduler moves on
-        const DevProblem *Pt = ctx.P;
-        const int t = ctx.t;
+        double *tile_sums = ctx.P->partials + ctx.t;
+        const int n_tiles_p = ctx.P->n_tiles;
         // also: every thread is done with the tile buffers and the context
         if (__syncthreads_or(y_late)) {
             if (tid == SCHED_TID) {
@@ -877,20 +888,18 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
             }
             break;
         }
-        if (warp == 0) {
-            double tv = 0.0;
-            if (lane < NPART) {
-                float hi = 0.f, lo = 0.f;
+        // the tile's sums (FP32 across warps in a fixed order, compensated for the prior's
+        // value); the reduction kernel that follows the pass sums the tiles
+        if (warp == 0 && lane < NPART) {
+            float hi = 0.f, lo = 0.f;
 #pragma unroll
-                for (int w = 0; w < NWARP; ++w) {
-                    const float x = red[w][lane];
-                    const float s = hi + x, bb = s - hi;
-                    lo += ((hi - (s - bb)) + (x - bb)) + (lane == P_JB ? red_lo[w] : 0.f);
-                    hi = s;
-                }
-                tv = lane == P_JB ? (double)hi + (double)lo : (double)hi;
+            for (int w = 0; w < NWARP; ++w) {
+                const float x = red[w][lane];
+                const float s = hi + x, bb = s - hi;
+                lo += ((hi - (s - bb)) + (x - bb)) + (lane == P_JB ? red_lo[w] : 0.f);
+                hi = s;
             }
-            tile_done(*Pt, t, tv, mode);
+            tile_sums[(size_t)lane * n_tiles_p] = lane == P_JB ? (double)hi + (double)lo : (double)hi;
         }
     }
     // the last CTA to stop zeroes the launch's tile counter for the next launch

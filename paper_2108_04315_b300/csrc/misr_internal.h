@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "misr.h"
 #include "misr_types.cuh"
 
@@ -38,12 +40,15 @@ struct DeviceGuard {
 int grid_for(size_t n, int threads);
 // every check misr_plan_create makes before allocating
 misr_status check_desc(const misr_desc &d);
-// one fused SCG pass over the tiles (problem index, tile) of the problems in `probs`; every
-// tile of every problem named must be listed exactly once.  `work`: the launch's tile counter
-// (two unsigned ints, zero before the first launch; every launch leaves them zero).  Launches
-// that share a `work` must be stream-ordered.
-misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, int n_tiles, unsigned *work, int mode,
-                            double alpha, double beta, cudaStream_t s);
+// one fused SCG pass (the pass kernel, then its reduction) over the tiles (problem index, tile)
+// and the groups (problem index, group) of the problems in `probs`; every tile and every group
+// of every problem named must be listed exactly once.  `work`: the launch's tile counter (two
+// unsigned ints, zero before the first launch; every launch leaves them zero).  Launches that
+// share a `work` must be stream-ordered.
+misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, int n_tiles, const int2 *groups,
+                            int n_groups, unsigned *work, int mode, double alpha, double beta, cudaStream_t s);
+// append problem `pi`'s tiles (border tiles first) and groups to a launch's lists
+void append_tiles(const misr::DevProblem &hp, int pi, std::vector<int2> &tiles, std::vector<int2> &groups);
 // prepare problem `pidx` of `probs`: interleave frames, start point, reset (flags as prepare_kernel)
 misr_status launch_prepare_raw(const misr::DevProblem *probs, int pidx, const misr_desc &d, size_t n_pitched,
                                const void *y_dev, const float *x_given, int x0_mode, int flags, cudaStream_t s);
@@ -58,6 +63,7 @@ struct misr_plan_s {
     misr::DevProblem hp{};              // host mirror of the device problem record
     misr::DevProblem *dprob = nullptr;  // device problem record
     int2 *dtile = nullptr;              // tile list of the fused pass (0, tile)
+    int2 *dgroup = nullptr;             // group list of its reduction (0, group)
     unsigned int *work = nullptr;       // the fused pass's tile counter
     char *ws = nullptr;                 // one allocation for everything above and below
     size_t ws_bytes = 0;

@@ -77,7 +77,7 @@ struct Slot {
     bool busy = false;
     uint64_t ticket = 0;
     int passes = 0;        // fused passes run since admission
-    int2 *items = nullptr;  // device tile list of this slot alone (for its init pass)
+    int2 *items = nullptr;  // device tile and group lists of this slot alone (for its init pass)
 };
 
 size_t plan_bytes_estimate(const misr_desc &d) {
@@ -103,7 +103,8 @@ struct misr_server_s {
     size_t slot_bytes = 0;
     cudaStream_t stream = nullptr;
     DevProblem *dprobs = nullptr;   // one record per slot (capacity cfg.max_slots)
-    int2 *ditems = nullptr;         // tile list of the live slots
+    int2 *ditems = nullptr;         // tile list of the live slots, then their group list
+    int live_tiles = 0, live_groups = 0;
     unsigned int *work = nullptr;   // the fused pass's tile counter
     size_t ditems_cap = 0;
     ScgState *st_host = nullptr;    // page-locked states, one per slot
@@ -189,8 +190,9 @@ std::vector<int> admit(misr_server_t s) {
                     sl.plan = p;
                     sl.desc.set(rq.desc.d);
                     s->slot_bytes += plan_bytes_estimate(rq.desc.d);
-                    std::vector<int2> t(p->hp.n_tiles);
-                    for (int k = 0; k < p->hp.n_tiles; ++k) t[k] = make_int2(idx, k);
+                    std::vector<int2> t, gl;
+                    append_tiles(p->hp, idx, t, gl);
+                    t.insert(t.end(), gl.begin(), gl.end());
                     bool ok2 = cudaMalloc(&sl.items, sizeof(int2) * t.size()) == cudaSuccess &&
                                cudaMemcpy(sl.items, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                                cudaMemcpy(&s->dprobs[idx], &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -282,14 +284,19 @@ void worker_main(misr_server_t s) {
             misr_plan_t p = sl.plan;
             if (r == MISR_OK)
                 r = launch_prepare_raw(s->dprobs, idx, p->d, p->n_pitched, rq->y, rq->x, p->d.x0_mode, 1 | 2 | 4, s->stream);
-            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, p->hp.n_tiles, s->work, MODE_INIT, 0.0, 0.0, s->stream);
+            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, p->hp.n_tiles, sl.items + p->hp.n_tiles,
+                                                  p->hp.n_groups, s->work, MODE_INIT, 0.0, 0.0, s->stream);
         }
         // 2. the live slots' tile map
         if (r == MISR_OK && s->items_dirty) {
             s->h_items.clear();
+            std::vector<int2> gl;
             for (size_t i = 0; i < s->slots.size(); ++i)
                 if (s->slots[i].busy)
-                    for (int k = 0; k < s->slots[i].plan->hp.n_tiles; ++k) s->h_items.push_back(make_int2((int)i, k));
+                    append_tiles(s->slots[i].plan->hp, (int)i, s->h_items, gl);
+            s->live_tiles = (int)s->h_items.size();
+            s->live_groups = (int)gl.size();
+            s->h_items.insert(s->h_items.end(), gl.begin(), gl.end());
             r = grow_items(s, std::max<size_t>(s->h_items.size(), 1));
             if (r == MISR_OK && !s->h_items.empty() &&
                 cudaMemcpyAsync(s->ditems, s->h_items.data(), sizeof(int2) * s->h_items.size(), cudaMemcpyHostToDevice,
@@ -298,9 +305,10 @@ void worker_main(misr_server_t s) {
             s->items_dirty = false;
         }
         // 3. k SCG iterations of every live projection, one launch each
-        const int nt = (int)s->h_items.size();
+        const int nt = s->live_tiles;
         for (int it = 0; it < k_passes && r == MISR_OK && nt > 0; ++it) {
-            r = launch_pass_raw(s->dprobs, s->ditems, nt, s->work, MODE_ITER, 0.0, 0.0, s->stream);
+            r = launch_pass_raw(s->dprobs, s->ditems, nt, s->ditems + nt, s->live_groups, s->work, MODE_ITER, 0.0, 0.0,
+                                s->stream);
             ++s->passes_launched;
         }
         // 4. completion: read the live states, copy finished projections out
