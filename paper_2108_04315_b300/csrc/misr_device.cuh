@@ -203,11 +203,11 @@ enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_
 //   I3 BTV (second half) + B2          I4 C1 (adjoint horizontal blur)
 //   I5 C2 + r'                         I6 horizontal blurs of r' and p
 //   I7 curvature forms (owned)
-template <int TH, int TW, int NT, bool BORDER>
+template <int TH, int TW, int NT, bool BORDER, typename Hook>
 __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsigned char *smp, const float *cs,
                                           uint64_t *ybar, uint32_t yphase, int y0, int x0, float alpha,
                                           float beta, float *Xn,
-                                          float *Rn, float *Pn, PassAcc &A) {
+                                          float *Rn, float *Pn, PassAcc &A, Hook &&hook) {
     using G = Geo<TH, TW>;
     constexpr int XH = G::XH, XW = G::XW, EH = G::EH, EW = G::EW, GH = G::GH, GW = G::GW;
     constexpr int CH = G::CH, CW = G::CW;
@@ -591,6 +591,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     if (tid < N_BTV1) item_btv(tid);
     else
         for (int it = tid - N_BTV1; it < N_B1; it += NT - N_BTV1) item_B1(it);
+    hook(2);
     __syncthreads();
     // the Y box: a wait that runs out is reported to the caller (the tile's results are void)
     const bool y_late = !mbar_wait_bounded(ybar, yphase, TMA_WAIT_TRIES);
@@ -598,6 +599,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     if (tid < N_BTV2) item_btv(N_BTV1 + tid);
     else
         for (int it = tid - N_BTV2; it < N_B2; it += NT - N_BTV2) item_B2(it);
+    hook(3);
     __syncthreads();
     // I4: adjoint horizontal blur
     for (int it = tid; it < N_C1; it += NT) item_C1(it);
@@ -688,44 +690,45 @@ __device__ __noinline__ void flag_timeout(const DevProblem &P) {
     atomicExch(&P.st->done, 1);
 }
 
-// Per-tile context of the persistent pass, in shared memory: written by the scheduling thread
-// at the top of each tile, read by every thread after the barrier that follows.  Keeping the
-// loop state here (not in registers) leaves the fused pass its registers.
-struct PassCtx {
+// A tile of the persistent pass as the scheduling thread prepares it, in shared memory (two
+// of them, by the parity of the CTA's tile count): read by every thread after the barrier at
+// the top of its tile.  Keeping this state here, not in registers, leaves the fused pass its
+// registers.
+struct TileInfo {
     const DevProblem *P;
     float *Xn, *Rn, *Pn;
     float alpha, beta;
-    int y0, x0, t, end;
-    uint32_t phase;
-    int restage;
-    // scheduler state
-    int next, cached, ntile, cur, pcur;
+    int y0, x0, t, cur, pcur, end, restage;
+};
+// The scheduling thread's own state: the CTA's next claimed tile and the fields of the problem
+// it last prepared a tile of.
+struct SchedState {
+    int next, cached, done;
+    TileInfo cache;
 };
 
-// The scheduling thread: take the CTA's next tile (the first one is blockIdx.x, later ones come
-// from the launch's tile counter), skipping problems that are done; publish it in c, issue its
-// TMA loads and warm L2 with the tile one resident wave ahead (the tile counter hands out
-// tiles in order, so that is about when another CTA will need it).
+// Prepare list entry k (or the end of the list) as the CTA's tile in `ti`: skip problems that
+// are done, take the problem's fields from the cache (loaded when the problem changes), and
+// warm L2 with the tile's boxes (it is loaded one tile later).
 template <int TH, int TW>
-__device__ __forceinline__ unsigned schedule_tile(PassCtx &c, const DevProblem *__restrict__ probs,
-                                              const int2 *__restrict__ tiles, int n_tiles, unsigned *work, int mode,
-                                              double probe_alpha, double probe_beta, float *sm, uint64_t *bar) {
-    using Gm = Geo<TH, TW>;
-    int k = c.next;
+__device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k, const DevProblem *__restrict__ probs,
+                                             const int2 *__restrict__ tiles, int n_tiles, unsigned *work, int mode,
+                                             double probe_alpha, double probe_beta) {
     int2 wt = make_int2(0, 0);
-    const DevProblem *P = c.P;
+    int restage = 0;
     for (;; k = (int)atomicAdd(&work[0], 1u) + (int)gridDim.x) {
         if (k >= n_tiles) {
-            c.end = 1;
-            return 0u;
+            ti.end = 1;
+            return;
         }
         wt = tiles[k];
-        if (wt.x != c.cached) {
-            P = &probs[wt.x];
+        if (wt.x != sc.cached) {
+            const DevProblem *P = &probs[wt.x];
             const ScgState *st = P->st;
-            c.cached = wt.x;
+            TileInfo &c = sc.cache;
+            sc.cached = wt.x;
+            restage = 1;
             c.P = P;
-            c.restage = 1;
             c.cur = ld_cg(&st->cur);
             c.pcur = ld_cg(&st->pcur);
             c.alpha = mode == MODE_PROBE ? (float)probe_alpha : __ldcg(&st->alpha_f);
@@ -733,44 +736,43 @@ __device__ __forceinline__ unsigned schedule_tile(PassCtx &c, const DevProblem *
             c.Xn = P->X[c.cur ^ 1];
             c.Rn = P->Rv[c.cur ^ 1];
             c.Pn = P->Pv[c.pcur ^ 1];
+            sc.done = ld_cg(&st->done);
         }
-        if (!ld_cg(&P->st->done)) break;
+        if (!sc.done) break;
     }
-    // the CTA's following tile; the caller stores it once the loads are in flight
-    const unsigned nxt = atomicAdd(&work[0], 1u);
-    c.t = wt.y;
-    c.y0 = (wt.y / P->tiles_x) * TH;
-    c.x0 = (wt.y % P->tiles_x) * TW;
-    c.phase = (uint32_t)(c.ntile & 1);
-    ++c.ntile;
-    const int cur = c.cur, pcur = c.pcur;
+    ti = sc.cache;
+    const DevProblem *P = ti.P;
+    ti.t = wt.y;
+    ti.y0 = (wt.y / P->tiles_x) * TH;
+    ti.x0 = (wt.y % P->tiles_x) * TW;
+    ti.end = 0;
+    ti.restage = restage;
+    tma_prefetch_l2_2d(&P->tmX[ti.cur], ti.x0 - 8, ti.y0 - 6);
+    tma_prefetch_l2_2d(&P->tmP[ti.pcur], ti.x0 - 8, ti.y0 - 6);
+    tma_prefetch_l2_2d(&P->tmR[ti.cur], ti.x0 - 8, ti.y0 - 6);
+    tma_prefetch_l2_2d(&P->tmY, ti.x0 - 4, ti.y0 - 4);
+}
+
+// Issue the TMA loads of a prepared tile (x, p_old, r boxes on bar[0]; the Y box on bar[1]).
+template <int TH, int TW>
+__device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_t *bar) {
+    using Gm = Geo<TH, TW>;
+    const DevProblem *P = ti.P;
     // generic-proxy accesses of the previous tile are ordered before these async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     constexpr uint32_t box_x = sizeof(float) * Gm::XH * Gm::XW;
     constexpr uint32_t box_y = sizeof(float) * Gm::EH * Gm::EW;
     mbar_arrive_expect_tx(&bar[0], 3 * box_x);
-    tma_load_2d(sm, &P->tmX[cur], c.x0 - 8, c.y0 - 6, &bar[0]);
-    tma_load_2d(sm + Gm::XH * Gm::XW, &P->tmP[pcur], c.x0 - 8, c.y0 - 6, &bar[0]);
-    tma_load_2d(sm + 2 * Gm::XH * Gm::XW, &P->tmR[cur], c.x0 - 8, c.y0 - 6, &bar[0]);
+    tma_load_2d(sm, &P->tmX[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
+    tma_load_2d(sm + Gm::XH * Gm::XW, &P->tmP[ti.pcur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
+    tma_load_2d(sm + 2 * Gm::XH * Gm::XW, &P->tmR[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
     mbar_arrive_expect_tx(&bar[1], box_y);
-    tma_load_2d(sm + 3 * Gm::XH * Gm::XW, &P->tmY, c.x0 - 4, c.y0 - 4, &bar[1]);
-    const int ka = k + (int)gridDim.x;
-    if (ka < n_tiles) {
-        const int2 wa = tiles[ka];
-        if (wa.x == wt.x) {
-            const int ny = (wa.y / P->tiles_x) * TH, nx = (wa.y % P->tiles_x) * TW;
-            tma_prefetch_l2_2d(&P->tmX[cur], nx - 8, ny - 6);
-            tma_prefetch_l2_2d(&P->tmP[pcur], nx - 8, ny - 6);
-            tma_prefetch_l2_2d(&P->tmR[cur], nx - 8, ny - 6);
-            tma_prefetch_l2_2d(&P->tmY, nx - 4, ny - 4);
-        }
-    }
-    return nxt;
+    tma_load_2d(sm + 3 * Gm::XH * Gm::XW, &P->tmY, ti.x0 - 4, ti.y0 - 4, &bar[1]);
 }
 
 // The fused SCG pass, persistent: one CTA per resident slot takes tiles (problem, tile) from
-// the launch's tile list until it runs out.  Thread 32 schedules the tiles and issues their
-// loads; warp 0 writes each tile's sums, which reduce_kernel combines after the pass.  `work` (two counters,
+// the launch's tile list until it runs out.  The last thread schedules the tiles and issues
+// their loads; warp 0 writes each tile's sums, which reduce_kernel combines after the pass.  `work` (two counters,
 // zero at launch) is the launch's tile counter; the last CTA to finish zeroes it again.
 template <int TH, int TW, int NT>
 __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__restrict__ probs,
@@ -788,29 +790,32 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
     __shared__ float cs[C_N];
     __shared__ float red[NWARP][NPART];
     __shared__ float red_lo[NWARP];
-    __shared__ PassCtx ctx;
+    __shared__ TileInfo tinfo[2];
+    __shared__ SchedState sched;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int SCHED_TID = 32;
+    // the scheduling thread: the last thread, whose warp takes light items in the intervals
+    // where it also prepares the CTA's next tile
+    constexpr int SCHED_TID = NT - 1;
     if (tid == SCHED_TID) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_barrier_init();
-        ctx.P = nullptr;
-        ctx.next = blockIdx.x;
-        ctx.cached = -1;
-        ctx.ntile = 0;
-        ctx.end = 0;
+        sched.cached = -1;
+        sched.done = 0;
+        prepare_tile<TH, TW>(tinfo[0], sched, blockIdx.x, probs, tiles, n_tiles, work, mode, probe_alpha, probe_beta);
+        sched.next = (int)atomicAdd(&work[0], 1u) + (int)gridDim.x;
     }
     __syncthreads();
-    for (;;) {
-        unsigned nxt = 0;
-        if (tid == SCHED_TID)
-            nxt = schedule_tile<TH, TW>(ctx, probs, tiles, n_tiles, work, mode, probe_alpha, probe_beta, sm, bar);
+    unsigned pending = 0;   // the scheduling thread's claim of the tile after next
+    for (uint32_t n = 0;; ++n) {
+        const int slot = n & 1;
+        const TileInfo &ti = tinfo[slot];
+        if (tid == SCHED_TID && !ti.end) load_tile<TH, TW>(ti, sm, bar);
         __syncthreads();
-        if (ctx.end) break;
-        const DevProblem &P = *ctx.P;
-        if (ctx.restage) {
+        if (ti.end) break;
+        const DevProblem &P = *ti.P;
+        if (ti.restage) {
             if (tid < 5) { cs[C_HX + tid] = P.hx[tid]; cs[C_HY + tid] = P.hy[tid]; }
             if (tid < 9) {
                 cs[C_GAM + tid] = P.gamma[tid];
@@ -822,7 +827,7 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
                 cs[C_FMAG] = __uint_as_float(P.f > 1 ? (unsigned)((0x100000000ull + P.f - 1) / P.f) : 0u);
             }
         }
-        const uint32_t phase = ctx.phase;
+        const uint32_t phase = n & 1;
         const bool landed = mbar_wait_bounded(&bar[0], phase, TMA_WAIT_TRIES);
         if (__syncthreads_or(!landed)) {
             // the loads did not land in time: flag the projection, let the copies in flight
@@ -834,22 +839,30 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
             }
             break;
         }
-        if (tid == SCHED_TID) {
-            ctx.restage = 0;
-            ctx.next = (int)nxt + (int)gridDim.x;
-        }
+        // the scheduling thread's share of the tile's light intervals: prepare the next tile
+        // (after I2's items), then record the claim made for the tile after it (after I3's)
+        auto hook = [&](int at) {
+            if (tid != SCHED_TID) return;
+            if (at == 2) {
+                prepare_tile<TH, TW>(tinfo[slot ^ 1], sched, sched.next, probs, tiles, n_tiles, work, mode,
+                                     probe_alpha, probe_beta);
+                pending = atomicAdd(&work[0], 1u);
+            } else {
+                sched.next = (int)pending + (int)gridDim.x;
+            }
+        };
 
         PassAcc A = {};
         bool y_late;
         {
-            const int y0 = ctx.y0, x0 = ctx.x0;
+            const int y0 = ti.y0, x0 = ti.x0;
             const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
             if (border)
-                y_late = pass_tile<TH, TW, NT, true>(P, sm, smp, cs, &bar[1], phase, y0, x0, ctx.alpha, ctx.beta,
-                                                     ctx.Xn, ctx.Rn, ctx.Pn, A);
+                y_late = pass_tile<TH, TW, NT, true>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
+                                                     ti.Rn, ti.Pn, A, hook);
             else
-                y_late = pass_tile<TH, TW, NT, false>(P, sm, smp, cs, &bar[1], phase, y0, x0, ctx.alpha, ctx.beta,
-                                                      ctx.Xn, ctx.Rn, ctx.Pn, A);
+                y_late = pass_tile<TH, TW, NT, false>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
+                                                      ti.Xn, ti.Rn, ti.Pn, A, hook);
         }
 
         // FP32 warp sums.  The prior's value enters Moller's comparison as a difference of
@@ -877,9 +890,8 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
             }
             if (lane == 0) { red[warp][P_JB] = hi; red_lo[warp] = lo; }
         }
-        // warp 0 takes what it needs of the context before the scheduler moves on
-        double *tile_sums = ctx.P->partials + ctx.t;
-        const int n_tiles_p = ctx.P->n_tiles;
+        double *tile_sums = P.partials + ti.t;
+        const int n_tiles_p = P.n_tiles;
         // also: every thread is done with the tile buffers and the context
         if (__syncthreads_or(y_late)) {
             if (tid == SCHED_TID) {
