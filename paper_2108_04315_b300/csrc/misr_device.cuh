@@ -599,7 +599,6 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     if (tid < N_BTV2) item_btv(N_BTV1 + tid);
     else
         for (int it = tid - N_BTV2; it < N_B2; it += NT - N_BTV2) item_B2(it);
-    hook(3);
     __syncthreads();
     // I4: adjoint horizontal blur
     for (int it = tid; it < N_C1; it += NT) item_C1(it);
@@ -839,16 +838,14 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
             }
             break;
         }
-        // the scheduling thread's share of the tile's light intervals: prepare the next tile
-        // (after I2's items), then record the claim made for the tile after it (after I3's)
+        // the scheduling thread's share of the tile's light interval I2: prepare the next tile
+        // and claim the one after it (recorded once the tile's intervals are done)
         auto hook = [&](int at) {
             if (tid != SCHED_TID) return;
             if (at == 2) {
                 prepare_tile<TH, TW>(tinfo[slot ^ 1], sched, sched.next, probs, tiles, n_tiles, work, mode,
                                      probe_alpha, probe_beta);
                 pending = atomicAdd(&work[0], 1u);
-            } else {
-                sched.next = (int)pending + (int)gridDim.x;
             }
         };
 
@@ -865,6 +862,7 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
                                                       ti.Xn, ti.Rn, ti.Pn, A, hook);
         }
 
+        if (tid == SCHED_TID) sched.next = (int)pending + (int)gridDim.x;
         // FP32 warp sums.  The prior's value enters Moller's comparison as a difference of
         // two passes' sums, so its sums are compensated (two-sum: hi + lo carries the
         // rounding error of every addition).
