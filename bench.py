@@ -519,9 +519,13 @@ def main():
                      "frac": achieved / peak, "traffic": load_traffic(kernel_source_tag()),
                      "kernel": "scg_pass_kernel<32,64,512>", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": PASS_BYTES_PER_PX * H * W,
-                     "ms_per_launch": pass_ms},
+                     "ms_per_launch": pass_ms,
+                     "timed_as": "one SCG pass: the fused pass kernel and its reduction kernel, "
+                                 "(T(100 it) - T(0 it)) / 100 with CUDA events on the solve's stream"},
         "e2e": e2e,
-        "gpu_launches": args.steps * (wl["iters"] + 3),
+        # per solve: prepare, the initial pass and every SCG pass (the fused pass kernel and its
+        # reduction kernel), finalize
+        "gpu_launches": args.steps * (2 * wl["iters"] + 4),
         "clocks": clocks,
         "solve": {"J_final": st["J_final"], "accepted": st["accepted"], "iters_done": st["iters_done"]},
     }
