@@ -276,6 +276,61 @@ def run_batch(args):
         p.close()
 
 
+def run_precision(args):
+    """The precision form at full size: 4 x 3072^2 uint16 counts (Poisson, I0 40000) of a
+    seeded phantom, log-converted on the device, 6144^2 HR, 100 SCG iterations; r and p stored
+    in bf16 with the float master x, against the all-float solve on the same GPU."""
+    import torch
+    from paper_2108_04315_b300.binding import MISR_BF16, MISR_F32, MISR_U16, Plan
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    h = w = 3072
+    f, iters, seed = 2, 100, gen.CONFIG_SEEDS["precision"]
+    sh, psf = gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)
+    plans = {name: Plan(h, w, f, sh, psf, lam=0.01, iters=iters, in_dtype=MISR_U16, flat_field=FLAT_FIELD,
+                        iterate_dtype=dt) for name, dt in (("f32", MISR_F32), ("bf16", MISR_BF16))}
+    xt = torch.from_numpy(gen.phantom(f * h, f * w, seed).astype(np.float32)).to(device)
+    m = plans["f32"].forward(xt)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    c = torch.poisson(FLAT_FIELD * torch.exp(-m), generator=g).clamp_(1, 65535).to(torch.int32)
+    y = torch.where(c > 32767, c - 65536, c).to(torch.int16).contiguous()
+    xs = {k: torch.empty((f * h, f * w), dtype=torch.float32, device=device) for k in plans}
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        for k, p in plans.items():
+            p.solve(y, xs[k], stats=False)
+    torch.cuda.synchronize()
+    res = {}
+    with ClockSampler(0) as clk:
+        for k, p in plans.items():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                p.solve(y, xs[k], stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            res[k] = e0.elapsed_time(e1) / args.steps
+    st = {k: p.solve(y, xs[k])[1] for k, p in plans.items()}
+    diff = float(torch.linalg.vector_norm(xs["bf16"] - xs["f32"]) / torch.linalg.vector_norm(xs["f32"]))
+    out = {"metric": "SR projections/s (3072^2 u16 -> 6144^2, 100 SCG it, bf16 r and p)", "value": 1e3 / res["bf16"],
+           "unit": "projections/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+           "ms_per_step": res["bf16"], "higher_is_better": True, "dtype": "f32 (x) + bf16 (r, p)",
+           "data": "synthetic", "impl": "misr-precision",
+           "config": {"workload": "4 x 3072^2 u16 counts (Poisson, I0 40000) -> 6144^2 HR, f=2, half-pixel shifts, "
+                                  "lambda 0.01, 100 SCG iterations", "hr_pixels": f * h * f * w},
+           "f32": {"value": 1e3 / res["f32"], "unit": "projections/s", "ms_per_step": res["f32"],
+                   "workspace_bytes": plans["f32"].workspace_bytes()},
+           "bf16_workspace_bytes": plans["bf16"].workspace_bytes(),
+           "bf16_vs_f32_image_rel_l2": diff,
+           "J_final": {k: v["J_final"] for k, v in st.items()},
+           "accepted": {k: v["accepted"] for k, v in st.items()},
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+    for p in plans.values():
+        p.close()
+
+
 SERVE_SCANS = {
     # scan A: full detector, f=2, K=4 half-pixel shifts; scan B: ROIs at f=3, K=9 third-pixel shifts
     "A": dict(h=1536, w=1920, f=2, shifts=gen.half_pixel_shifts()),
@@ -414,7 +469,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="misr", choices=["misr", "reference"])
-    ap.add_argument("--workload", default="detector", choices=sorted(WORKLOADS) + ["batch", "serving"])
+    ap.add_argument("--workload", default="detector", choices=sorted(WORKLOADS) + ["batch", "serving", "precision"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--serve-n", type=int, default=240)
@@ -426,6 +481,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
         return
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))

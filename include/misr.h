@@ -72,7 +72,11 @@ typedef struct misr_desc {
     int32_t in_dtype;        /* MISR_F32 frames, or MISR_U16 detector counts c converted on the
                                 device to line integrals y = ln(flat_field) - ln(max(c, 1)) */
     float flat_field;        /* I0 for MISR_U16 (> 0) */
-    int32_t iterate_dtype;   /* MISR_F32 */
+    int32_t iterate_dtype;   /* MISR_F32: x, r, p in float.  MISR_BF16: r and p (the gradient and
+                                the search direction) stored in bf16, x kept in float as the master
+                                copy (an alpha p update below the bf16 step of x is not lost);
+                                stencils accumulate in float and the SCG scalars stay FP64 either
+                                way.  misr_pass_probe needs MISR_F32. */
 } misr_desc;
 
 /* Solve summary.  J_final, rnorm2 are FP64 reductions computed on the device. */

@@ -58,12 +58,15 @@ misr_status get_encode_tiled() {
 
 // 2-D float32 tensor map over an H x W image with the given row pitch (floats); box of
 // box_w x box_h elements; out-of-bounds elements read as 0 or as NaN.
-misr_status make_map(CUtensorMap *m, float *base, int W, int H, int pitch, int box_w, int box_h, bool nan_fill) {
+misr_status make_map(CUtensorMap *m, void *base, int W, int H, int pitch, int box_w, int box_h, bool nan_fill,
+                     bool bf16 = false) {
+    const size_t esz = bf16 ? 2 : sizeof(float);
     const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
-    const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * esz};
     const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+    CUresult r = g_encode_tiled(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
+                                dims, strides, box, estr,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                 nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA
@@ -95,8 +98,8 @@ static misr_status validate(const misr_desc *d) {
     if (d->x0_mode < 0 || d->x0_mode > 2) return fail(MISR_EINVAL, "bad x0_mode");
     if (d->in_dtype != MISR_F32 && d->in_dtype != MISR_U16) return fail(MISR_EINVAL, "in_dtype must be MISR_F32 or MISR_U16");
     if (d->in_dtype == MISR_U16 && !(d->flat_field > 0)) return fail(MISR_EINVAL, "flat_field must be > 0");
-    if (d->iterate_dtype == MISR_BF16) return fail(MISR_ENOTIMPL, "BF16 iterate not available in this build");
-    if (d->iterate_dtype != MISR_F32) return fail(MISR_EINVAL, "iterate_dtype must be MISR_F32");
+    if (d->iterate_dtype != MISR_F32 && d->iterate_dtype != MISR_BF16)
+        return fail(MISR_EINVAL, "iterate_dtype must be MISR_F32 or MISR_BF16");
     return MISR_OK;
 }
 
@@ -257,7 +260,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     DevProblem hp{};
     hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
     hp.H = f * d.lr_h; hp.W = f * d.lr_w;
-    hp.pitch = (hp.W + 3) & ~3;
+    hp.pitch = (hp.W + 7) & ~7;   // 16-byte rows for float and bf16 planes
     hp.iters = d.iters;
     for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
     for (int k = 0; k < d.K; ++k) {
@@ -303,8 +306,9 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     // workspace: X[2], R[2], P[2], Y | tile and group sums, group counters, pass counter,
     // launch tile counter | state | trace | problem | tile list
     const size_t img = align_up(p->n_pitched * sizeof(float), 256);
+    const size_t rp_img = d.iterate_dtype == MISR_BF16 ? align_up(p->n_pitched * 2, 256) : img;
     size_t off = 0;
-    const size_t o_img = off; off += 7 * img;
+    const size_t o_img = off; off += 3 * img + 4 * rp_img;   // X[2], Y (float); R[2], P[2]
     const size_t o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(double), 256);
     const size_t o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(double), 256);
     const size_t o_gcnt = off; off += align_up((size_t)hp.n_groups * sizeof(unsigned int), 256);
@@ -325,10 +329,11 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     char *b = p->ws;
     for (int i = 0; i < 2; ++i) {
         hp.X[i] = (float *)(b + o_img + (0 + i) * img);
-        hp.Rv[i] = (float *)(b + o_img + (2 + i) * img);
-        hp.Pv[i] = (float *)(b + o_img + (4 + i) * img);
+        hp.Rv[i] = (float *)(b + o_img + 3 * img + (0 + i) * rp_img);
+        hp.Pv[i] = (float *)(b + o_img + 3 * img + (2 + i) * rp_img);
     }
-    hp.Y = (float *)(b + o_img + 6 * img);
+    hp.Y = (float *)(b + o_img + 2 * img);
+    hp.rp_bf16 = d.iterate_dtype == MISR_BF16;
     hp.partials = (double *)(b + o_part);
     hp.gpartials = (double *)(b + o_gpart);
     hp.gcount = (unsigned int *)(b + o_gcnt);
@@ -343,8 +348,10 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
         misr_status ms = get_encode_tiled();
         for (int i = 0; i < 2 && ms == MISR_OK; ++i) {
             ms = make_map(&hp.tmX[i], hp.X[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
-            if (ms == MISR_OK) ms = make_map(&hp.tmR[i], hp.Rv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
-            if (ms == MISR_OK) ms = make_map(&hp.tmP[i], hp.Pv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
+            if (ms == MISR_OK)
+                ms = make_map(&hp.tmR[i], hp.Rv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false, hp.rp_bf16);
+            if (ms == MISR_OK)
+                ms = make_map(&hp.tmP[i], hp.Pv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false, hp.rp_bf16);
         }
         if (ms == MISR_OK) ms = make_map(&hp.tmY, hp.Y, hp.W, hp.H, hp.pitch, PassGeo::EW, PassGeo::EH, true);
         if (ms != MISR_OK) {
@@ -411,6 +418,7 @@ misr_status misr_pass_probe(misr_plan_t p, const void *y_dev, const float *x_dev
                             float *r_out_dev, float *p_out_dev, double *sums, misr_stream_t stream) {
     if (!p || !y_dev || !x_dev || !r_dev || !p_old_dev || !sums) return fail(MISR_EINVAL, "NULL argument");
     if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(MISR_EINVAL, "alpha, beta must be finite");
+    if (p->hp.rp_bf16) return fail(MISR_ENOTIMPL, "misr_pass_probe takes float r and p: use a MISR_F32 iterate plan");
     DeviceGuard g(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t wb = (size_t)p->hp.W * sizeof(float), pb = (size_t)p->hp.pitch * sizeof(float);
@@ -445,7 +453,11 @@ misr_status misr_gradient(misr_plan_t p, const void *y_dev, const float *x_dev, 
     if (r != MISR_OK) return r;
     r = launch_pass(p, MODE_PROBE, 0.0, 0.0, s);
     if (r != MISR_OK) return r;
-    scale_copy_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->hp.Rv[1], p->hp.pitch, -1.f, g_dev, p->hp.H, p->hp.W);
+    if (p->hp.rp_bf16)
+        scale_copy_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(p->hp.Rv[1]),
+                                                              p->hp.pitch, -1.f, g_dev, p->hp.H, p->hp.W);
+    else
+        scale_copy_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->hp.Rv[1], p->hp.pitch, -1.f, g_dev, p->hp.H, p->hp.W);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(p->st_host, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -630,7 +642,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
     hp = DevProblem{};
     hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
     hp.H = f * d.lr_h; hp.W = f * d.lr_w;
-    hp.pitch = (hp.W + 3) & ~3;
+    hp.pitch = (hp.W + 7) & ~7;   // 16-byte rows for float and bf16 planes
     hp.iters = 0;
     for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
     for (int k = 0; k < d.K; ++k) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -101,6 +102,8 @@ __device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const d
 //   GB          lambda-free BTV gradient, then r'   origin (-2, -2)  (TH+4) x (TW+4)
 //   HS scratch: forward horizontal blur of x' (TH+12) x (TW+8), adjoint horizontal blur of E
 //               (TH+8) x (TW+4), horizontal blur of p (TH+4) x TW
+//   RS, PS      the bf16 r and p_old boxes of a bf16-direction problem (converted in I1),
+//               after YB
 //   SMP         sampled flags of the owned pixels
 template <int TH, int TW>
 struct Geo {
@@ -113,7 +116,11 @@ struct Geo {
     static constexpr int HS1 = XH * EW, HS2 = EH * GW, HS3 = CH * CW;
     static constexpr int HS12 = HS1 > HS2 ? HS1 : HS2;
     static constexpr int HS = HS12 > HS3 ? HS12 : HS3;
-    static constexpr int FLOATS = 3 * XH * XW + EH * EW + GH * GW + HS;
+    static constexpr int RPS = XH * XW;                  // bf16 r and p boxes (two halves)
+    static constexpr int FLOATS = 3 * XH * XW + EH * EW + RPS + GH * GW + HS;
+    static_assert(((3 * XH * XW + EH * EW) * 4) % 128 == 0 && (3 * XH * XW * 4) % 128 == 0 &&
+                      (XH * XW * 4) % 128 == 0 && (XH * XW * 2) % 128 == 0,
+                  "TMA destinations must stay 128-byte aligned");
     static constexpr size_t TMA_BYTES = sizeof(float) * (3 * XH * XW + EH * EW);
     static constexpr size_t SMEM_BYTES = 128 /*align slack*/ + sizeof(float) * FLOATS + TH * TW + 64;
 };
@@ -136,6 +143,24 @@ __device__ __forceinline__ void ld4v(const float *p, float *v) {
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
 }
 __device__ __forceinline__ void st4v(float *p, const float *v) { st4(p, make_float4(v[0], v[1], v[2], v[3])); }
+// four bf16 values (8-byte aligned) as floats, and back (round to nearest even)
+__device__ __forceinline__ float4 bf4(const __nv_bfloat16 *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_bf4(__nv_bfloat16 *p, float4 v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned *>(&a);
+    u.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+__device__ __forceinline__ float4 round_bf4(float4 v) {
+    return make_float4(__bfloat162float(__float2bfloat16_rn(v.x)), __bfloat162float(__float2bfloat16_rn(v.y)),
+                       __bfloat162float(__float2bfloat16_rn(v.z)), __bfloat162float(__float2bfloat16_rn(v.w)));
+}
 
 // packed two-lane FP32 arithmetic (one instruction for two values)
 __device__ __forceinline__ unsigned long long f2u(float2 a) { return *reinterpret_cast<unsigned long long *>(&a); }
@@ -215,8 +240,11 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     float *PB = XB + XH * XW;
     float *RB = PB + XH * XW;
     float *YB = RB + XH * XW;
-    float *GB = YB + EH * EW;
+    const __nv_bfloat16 *RS = reinterpret_cast<const __nv_bfloat16 *>(YB + EH * EW);   // bf16 r box
+    const __nv_bfloat16 *PS = RS + XH * XW;                                            // bf16 p_old box
+    float *GB = YB + EH * EW + G::RPS;
     float *HS = GB + GH * GW;           // horizontal blurs: x' (B1), E (C1), p (HP)
+    const bool rpb = P.rp_bf16 != 0;
     float *HR = RB;                     // horizontal blur of r' (r is dead by then)
     const int tid = threadIdx.x;
     const int H = P.H, W = P.W, f = P.f, pitch = P.pitch;
@@ -232,12 +260,24 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
 
     // ---------------- item bodies
     // A: p = r + beta p_old, x' = x + alpha p on the X box; owned pixels go to HBM
+    // (bf16 directions: r and p_old come from the bf16 boxes, p is rounded to bf16 before x' uses
+    // it, so the tile works with exactly the p the next pass reads back)
     auto item_A = [&](int it) {
         const int r = it / (XW / 4), c4 = it - r * (XW / 4);
-        const float4 rv = ld4(RB + 4 * it), pov = ld4(PB + 4 * it), xv = ld4(XB + 4 * it);
+        float4 rv, pov;
+        if (rpb) {
+            rv = bf4(RS + 4 * it);
+            pov = bf4(PS + 4 * it);
+            st4(RB + 4 * it, rv);
+        } else {
+            rv = ld4(RB + 4 * it);
+            pov = ld4(PB + 4 * it);
+        }
+        const float4 xv = ld4(XB + 4 * it);
         float4 pv, xn;
         pv.x = fmaf(beta, pov.x, rv.x); pv.y = fmaf(beta, pov.y, rv.y);
         pv.z = fmaf(beta, pov.z, rv.z); pv.w = fmaf(beta, pov.w, rv.w);
+        if (rpb) pv = round_bf4(pv);
         xn.x = fmaf(alpha, pv.x, xv.x); xn.y = fmaf(alpha, pv.y, xv.y);
         xn.z = fmaf(alpha, pv.z, xv.z); xn.w = fmaf(alpha, pv.w, xv.w);
         st4(PB + 4 * it, pv);
@@ -248,14 +288,16 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
             if (!BORDER || (gy < H && gx + 3 < W)) {
                 const size_t o = (size_t)gy * pitch + gx;
                 st4(Xn + o, xn);
-                st4(Pn + o, pv);
+                if (rpb) st_bf4(reinterpret_cast<__nv_bfloat16 *>(Pn) + o, pv);
+                else st4(Pn + o, pv);
                 A.pp += pv.x * pv.x + pv.y * pv.y + pv.z * pv.z + pv.w * pv.w;
             } else if (gy < H) {
                 const float xs[4] = {xn.x, xn.y, xn.z, xn.w}, ps[4] = {pv.x, pv.y, pv.z, pv.w};
                 for (int j = 0; j < 4 && gx + j < W; ++j) {
                     const size_t o = (size_t)gy * pitch + gx + j;
                     Xn[o] = xs[j];
-                    Pn[o] = ps[j];
+                    if (rpb) reinterpret_cast<__nv_bfloat16 *>(Pn)[o] = __float2bfloat16_rn(ps[j]);
+                    else Pn[o] = ps[j];
                     A.pp += ps[j] * ps[j];
                 }
             }
@@ -451,6 +493,10 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
                 if (!(u >= 0 && u < H && gx >= 0 && gx < W)) rv[j] = 0.f;
             }
         }
+        if (rpb) {   // the tile continues with the r' the next pass reads back
+#pragma unroll
+            for (int j = 0; j < 4; ++j) rv[j] = __bfloat162float(__float2bfloat16_rn(rv[j]));
+        }
         st4(GB + n * GW + g, make_float4(rv[0], rv[1], rv[2], rv[3]));
         const int orow = n - 2;
         if (orow >= 0 && orow < TH) {
@@ -465,12 +511,17 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
                 const float2 pq = ld2(PB + (orow + 6) * XW + oc + 8);
                 const float r0 = rv[2 * h], r1 = rv[2 * h + 1];
                 if (!BORDER || (u < H && gx + 1 < W)) {
-                    st2(Rn + (size_t)u * pitch + gx, make_float2(r0, r1));
+                    if (rpb)
+                        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(Rn) + (size_t)u * pitch + gx) =
+                            __floats2bfloat162_rn(r0, r1);
+                    else
+                        st2(Rn + (size_t)u * pitch + gx, make_float2(r0, r1));
                     A.rr = fmaf(r0, r0, fmaf(r1, r1, A.rr));
                     A.rrx = fmaf(r0, ro.x, fmaf(r1, ro.y, A.rrx));
                     A.pr = fmaf(pq.x, r0, fmaf(pq.y, r1, A.pr));
                 } else if (u < H && gx < W) {
-                    Rn[(size_t)u * pitch + gx] = r0;
+                    if (rpb) reinterpret_cast<__nv_bfloat16 *>(Rn)[(size_t)u * pitch + gx] = __float2bfloat16_rn(r0);
+                    else Rn[(size_t)u * pitch + gx] = r0;
                     A.rr = fmaf(r0, r0, A.rr);
                     A.rrx = fmaf(r0, ro.x, A.rrx);
                     A.pr = fmaf(pq.x, r0, A.pr);
@@ -761,10 +812,19 @@ __device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     constexpr uint32_t box_x = sizeof(float) * Gm::XH * Gm::XW;
     constexpr uint32_t box_y = sizeof(float) * Gm::EH * Gm::EW;
-    mbar_arrive_expect_tx(&bar[0], 3 * box_x);
-    tma_load_2d(sm, &P->tmX[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
-    tma_load_2d(sm + Gm::XH * Gm::XW, &P->tmP[ti.pcur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
-    tma_load_2d(sm + 2 * Gm::XH * Gm::XW, &P->tmR[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
+    if (P->rp_bf16) {   // r and p_old as bf16 boxes into their staging halves
+        float *rps = sm + 3 * Gm::XH * Gm::XW + Gm::EH * Gm::EW;   // 128-byte aligned
+        mbar_arrive_expect_tx(&bar[0], box_x + box_x);   // one float box + two bf16 boxes
+        tma_load_2d(sm, &P->tmX[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
+        tma_load_2d(rps, &P->tmR[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
+        tma_load_2d(reinterpret_cast<__nv_bfloat16 *>(rps) + Gm::XH * Gm::XW, &P->tmP[ti.pcur], ti.x0 - 8,
+                    ti.y0 - 6, &bar[0]);
+    } else {
+        mbar_arrive_expect_tx(&bar[0], 3 * box_x);
+        tma_load_2d(sm, &P->tmX[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
+        tma_load_2d(sm + Gm::XH * Gm::XW, &P->tmP[ti.pcur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
+        tma_load_2d(sm + 2 * Gm::XH * Gm::XW, &P->tmR[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
+    }
     mbar_arrive_expect_tx(&bar[1], box_y);
     tma_load_2d(sm + 3 * Gm::XH * Gm::XW, &P->tmY, ti.x0 - 4, ti.y0 - 4, &bar[1]);
 }
@@ -967,8 +1027,13 @@ __global__ void prepare_kernel(const DevProblem *__restrict__ probs, int pidx, c
         P.Y[o] = yv;
         if (flags & 1) P.X[0][o] = x0;
         if (flags & 2) {
-            P.Rv[0][o] = 0.f;
-            P.Pv[0][o] = 0.f;
+            if (P.rp_bf16) {
+                reinterpret_cast<__nv_bfloat16 *>(P.Rv[0])[o] = __float2bfloat16_rn(0.f);
+                reinterpret_cast<__nv_bfloat16 *>(P.Pv[0])[o] = __float2bfloat16_rn(0.f);
+            } else {
+                P.Rv[0][o] = 0.f;
+                P.Pv[0][o] = 0.f;
+            }
         }
     }
 }
@@ -1013,12 +1078,15 @@ __global__ void finalize_kernel(const DevProblem *__restrict__ probs, int pidx, 
 }
 
 // out (dense, row pitch W) = sign * src (row pitch `pitch`)
-__global__ void scale_copy_kernel(const float *__restrict__ src, int pitch, float sign, float *__restrict__ out,
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T>
+__global__ void scale_copy_kernel(const T *__restrict__ src, int pitch, float sign, float *__restrict__ out,
                                   int H, int W) {
     const size_t n = (size_t)H * W;
     for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         const int y = (int)(o / W), x = (int)(o - (size_t)y * W);
-        out[o] = sign * src[(size_t)y * pitch + x];
+        out[o] = sign * to_f(src[(size_t)y * pitch + x]);
     }
 }
 

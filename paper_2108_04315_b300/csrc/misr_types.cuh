@@ -58,12 +58,14 @@ struct ScgState {
 struct DevProblem {
     CUtensorMap tmX[2], tmR[2], tmP[2], tmY;      // TMA maps of the workspace images
     int H, W, pitch, f, h, w, K;
-    int tiles_x, tiles_y, n_tiles, iters, pad0;
+    int tiles_x, tiles_y, n_tiles, iters;
+    int rp_bf16;                                  // r and p stored as bf16 (x stays float)
     float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];  // separable PSF, h(a, b) = hy[a+R] hx[b+R]
     float lambda, eps, eps2, pad1;
     float gamma[BTV_W * BTV_W];                   // gamma(dx, dy) at [dy * BTV_W + dx]
     double eps_pairs;                             // eps * sum_d gamma_d * #pairs_d
-    float *X[2], *Rv[2], *Pv[2];                  // x, r (double buffered), p (double buffered)
+    float *X[2], *Rv[2], *Pv[2];                  // x, r (double buffered), p (double buffered);
+                                                  // Rv, Pv hold __nv_bfloat16 when rp_bf16
     float *Y;                                     // interleaved frames, NaN where unsampled
     // Fixed-order reduction of a pass's sums: every tile writes its sums; whoever finishes the
     // last tile of a group of `group` tiles sums the group in tile order; whoever finishes the

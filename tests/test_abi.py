@@ -68,7 +68,7 @@ def _desc(**kw):
     (dict(lam=-1.0), "EINVAL"),
     (dict(iters=-1), "EINVAL"),
     (dict(in_dtype=7), "EINVAL"),
-    (dict(iterate_dtype=2), "ENOTIMPL"),
+    (dict(iterate_dtype=1), "EINVAL"),                            # u16 is an input type only
 ])
 def test_invalid_descriptor_rejected_on_host(L, kw, status):
     from paper_2108_04315_b300 import binding
