@@ -127,9 +127,13 @@ static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
 static misr_status set_pass_attrs() {
     static bool done = false;
     if (done) return MISR_OK;
-    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
+    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>,
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
-    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
+    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>,
+                            cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, true>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
+    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, true>,
                             cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     done = true;
     return MISR_OK;
@@ -142,7 +146,7 @@ static int resident_ctas() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scg_pass_kernel<TILE_H, TILE_W, PASS_NT>, PASS_NT,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>, PASS_NT,
                                                   PassGeo::SMEM_BYTES);
     cudaGetLastError();
     cached = sms * per_sm;
@@ -153,7 +157,9 @@ static int resident_ctas() {
 static int pass_grid(int n_items) { return std::max(1, std::min(n_items, resident_ctas())); }
 
 static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double beta, cudaStream_t s) {
-    return launch_pass_raw(p->dprob, p->dtile, p->hp.n_tiles, p->dgroup, p->hp.n_groups, p->work, mode, alpha, beta, s);
+    const int n = p->hp.n_tiles;
+    return launch_pass_raw(p->dprob, p->dtile, p->hp.rp_bf16 ? 0 : n, p->hp.rp_bf16 ? n : 0, p->dgroup,
+                           p->hp.n_groups, p->work, mode, alpha, beta, s);
 }
 
 // Groups of the pass reduction: at least 64 tiles, at most 128 groups (the last group's
@@ -192,15 +198,22 @@ static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float 
     return MISR_OK;
 }
 
-misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, int n_tiles, const int2 *groups,
-                                       int n_groups, unsigned *work, int mode, double alpha, double beta,
-                                       cudaStream_t s) {
-    if (n_tiles <= 0) return MISR_OK;
+misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, int n_f32, int n_bf16,
+                                       const int2 *groups, int n_groups, unsigned *work, int mode, double alpha,
+                                       double beta, cudaStream_t s) {
+    if (n_f32 + n_bf16 <= 0) return MISR_OK;
     misr_status r = set_pass_attrs();
     if (r != MISR_OK) return r;
-    scg_pass_kernel<TILE_H, TILE_W, PASS_NT><<<pass_grid(n_tiles), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
-        probs, tiles, n_tiles, work, mode, alpha, beta);
-    CK(cudaGetLastError());
+    if (n_f32 > 0) {
+        scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false><<<pass_grid(n_f32), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
+            probs, tiles, n_f32, work, mode, alpha, beta);
+        CK(cudaGetLastError());
+    }
+    if (n_bf16 > 0) {
+        scg_pass_kernel<TILE_H, TILE_W, PASS_NT, true><<<pass_grid(n_bf16), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
+            probs, tiles + n_f32, n_bf16, work, mode, alpha, beta);
+        CK(cudaGetLastError());
+    }
     reduce_kernel<<<n_groups, 32, 0, s>>>(probs, groups, mode);
     CK(cudaGetLastError());
     return MISR_OK;
@@ -625,9 +638,9 @@ misr_status noalloc_setup(unsigned char **base) {
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr)
             return fail(MISR_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-        CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
+        CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
-        CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT>,
+        CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>,
                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         d.base = static_cast<unsigned char *>(ptr);
         d.ready = true;
@@ -740,7 +753,7 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     prepare_kernel<<<grid_for(npitched, 256), 256, 0, st>>>(dprob, 0, y_dev, desc->in_dtype, log_i0, x_dev,
                                                            MISR_X0_GIVEN, 1 | 2 | 4);
     CK(cudaGetLastError());
-    s = launch_pass_raw(dprob, dtile, hp.n_tiles, dgroup, hp.n_groups, work, MODE_PROBE, 0.0, 0.0, st);
+    s = launch_pass_raw(dprob, dtile, hp.n_tiles, 0, dgroup, hp.n_groups, work, MODE_PROBE, 0.0, 0.0, st);
     if (s != MISR_OK) return s;
     scale_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(hp.Rv[1], hp.pitch, -1.f, g_dev, hp.H, hp.W);
     CK(cudaGetLastError());

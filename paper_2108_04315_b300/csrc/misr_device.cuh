@@ -102,8 +102,8 @@ __device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const d
 //   GB          lambda-free BTV gradient, then r'   origin (-2, -2)  (TH+4) x (TW+4)
 //   HS scratch: forward horizontal blur of x' (TH+12) x (TW+8), adjoint horizontal blur of E
 //               (TH+8) x (TW+4), horizontal blur of p (TH+4) x TW
-//   RS, PS      the bf16 r and p_old boxes of a bf16-direction problem (converted in I1),
-//               after YB
+//   RS, PS      the bf16 r and p_old boxes of a bf16-direction problem, staged over GB and HS
+//               (converted in I1, before GB and HS are first written)
 //   SMP         sampled flags of the owned pixels
 template <int TH, int TW>
 struct Geo {
@@ -117,7 +117,8 @@ struct Geo {
     static constexpr int HS12 = HS1 > HS2 ? HS1 : HS2;
     static constexpr int HS = HS12 > HS3 ? HS12 : HS3;
     static constexpr int RPS = XH * XW;                  // bf16 r and p boxes (two halves)
-    static constexpr int FLOATS = 3 * XH * XW + EH * EW + RPS + GH * GW + HS;
+    static constexpr int FLOATS = 3 * XH * XW + EH * EW + GH * GW + HS;
+    static_assert(RPS <= GH * GW + HS, "the bf16 boxes are staged in the GB and HS area");
     static_assert(((3 * XH * XW + EH * EW) * 4) % 128 == 0 && (3 * XH * XW * 4) % 128 == 0 &&
                       (XH * XW * 4) % 128 == 0 && (XH * XW * 2) % 128 == 0,
                   "TMA destinations must stay 128-byte aligned");
@@ -228,7 +229,7 @@ enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_
 //   I3 BTV (second half) + B2          I4 C1 (adjoint horizontal blur)
 //   I5 C2 + r'                         I6 horizontal blurs of r' and p
 //   I7 curvature forms (owned)
-template <int TH, int TW, int NT, bool BORDER, typename Hook>
+template <int TH, int TW, int NT, bool BORDER, bool RPB, typename Hook>
 __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsigned char *smp, const float *cs,
                                           uint64_t *ybar, uint32_t yphase, int y0, int x0, float alpha,
                                           float beta, float *Xn,
@@ -240,11 +241,13 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     float *PB = XB + XH * XW;
     float *RB = PB + XH * XW;
     float *YB = RB + XH * XW;
-    const __nv_bfloat16 *RS = reinterpret_cast<const __nv_bfloat16 *>(YB + EH * EW);   // bf16 r box
-    const __nv_bfloat16 *PS = RS + XH * XW;                                            // bf16 p_old box
-    float *GB = YB + EH * EW + G::RPS;
+    float *GB = YB + EH * EW;
+    // bf16 r and p_old boxes, staged in the GB and HS area (read in I1; GB and HS are first
+    // written in I2)
+    const __nv_bfloat16 *RS = reinterpret_cast<const __nv_bfloat16 *>(GB);
+    const __nv_bfloat16 *PS = RS + XH * XW;
     float *HS = GB + GH * GW;           // horizontal blurs: x' (B1), E (C1), p (HP)
-    const bool rpb = P.rp_bf16 != 0;
+    constexpr bool rpb = RPB;           // r and p stored as bf16 (compiled per storage type)
     float *HR = RB;                     // horizontal blur of r' (r is dead by then)
     const int tid = threadIdx.x;
     const int H = P.H, W = P.W, f = P.f, pitch = P.pitch;
@@ -265,7 +268,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     auto item_A = [&](int it) {
         const int r = it / (XW / 4), c4 = it - r * (XW / 4);
         float4 rv, pov;
-        if (rpb) {
+        if constexpr (rpb) {
             rv = bf4(RS + 4 * it);
             pov = bf4(PS + 4 * it);
             st4(RB + 4 * it, rv);
@@ -277,7 +280,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         float4 pv, xn;
         pv.x = fmaf(beta, pov.x, rv.x); pv.y = fmaf(beta, pov.y, rv.y);
         pv.z = fmaf(beta, pov.z, rv.z); pv.w = fmaf(beta, pov.w, rv.w);
-        if (rpb) pv = round_bf4(pv);
+        if constexpr (rpb) pv = round_bf4(pv);
         xn.x = fmaf(alpha, pv.x, xv.x); xn.y = fmaf(alpha, pv.y, xv.y);
         xn.z = fmaf(alpha, pv.z, xv.z); xn.w = fmaf(alpha, pv.w, xv.w);
         st4(PB + 4 * it, pv);
@@ -493,7 +496,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
                 if (!(u >= 0 && u < H && gx >= 0 && gx < W)) rv[j] = 0.f;
             }
         }
-        if (rpb) {   // the tile continues with the r' the next pass reads back
+        if constexpr (rpb) {   // the tile continues with the r' the next pass reads back
 #pragma unroll
             for (int j = 0; j < 4; ++j) rv[j] = __bfloat162float(__float2bfloat16_rn(rv[j]));
         }
@@ -804,7 +807,7 @@ __device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k
 }
 
 // Issue the TMA loads of a prepared tile (x, p_old, r boxes on bar[0]; the Y box on bar[1]).
-template <int TH, int TW>
+template <int TH, int TW, bool RPB>
 __device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_t *bar) {
     using Gm = Geo<TH, TW>;
     const DevProblem *P = ti.P;
@@ -812,8 +815,8 @@ __device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     constexpr uint32_t box_x = sizeof(float) * Gm::XH * Gm::XW;
     constexpr uint32_t box_y = sizeof(float) * Gm::EH * Gm::EW;
-    if (P->rp_bf16) {   // r and p_old as bf16 boxes into their staging halves
-        float *rps = sm + 3 * Gm::XH * Gm::XW + Gm::EH * Gm::EW;   // 128-byte aligned
+    if constexpr (RPB) {   // r and p_old as bf16 boxes into their staging halves
+        float *rps = sm + 3 * Gm::XH * Gm::XW + Gm::EH * Gm::EW;   // the GB area, 128-byte aligned
         mbar_arrive_expect_tx(&bar[0], box_x + box_x);   // one float box + two bf16 boxes
         tma_load_2d(sm, &P->tmX[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
         tma_load_2d(rps, &P->tmR[ti.cur], ti.x0 - 8, ti.y0 - 6, &bar[0]);
@@ -830,10 +833,11 @@ __device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_
 }
 
 // The fused SCG pass, persistent: one CTA per resident slot takes tiles (problem, tile) from
-// the launch's tile list until it runs out.  The last thread schedules the tiles and issues
-// their loads; warp 0 writes each tile's sums, which reduce_kernel combines after the pass.  `work` (two counters,
+// the launch's tile list until it runs out; the problems of one launch share the storage type
+// of r and p (RPB: bf16).  The last thread schedules the tiles and issues their loads; warp 0
+// writes each tile's sums, which reduce_kernel combines after the pass.  `work` (two counters,
 // zero at launch) is the launch's tile counter; the last CTA to finish zeroes it again.
-template <int TH, int TW, int NT>
+template <int TH, int TW, int NT, bool RPB>
 __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__restrict__ probs,
                                                          const int2 *__restrict__ tiles, int n_tiles,
                                                          unsigned *work, int mode, double probe_alpha,
@@ -870,7 +874,7 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
     for (uint32_t n = 0;; ++n) {
         const int slot = n & 1;
         const TileInfo &ti = tinfo[slot];
-        if (tid == SCHED_TID && !ti.end) load_tile<TH, TW>(ti, sm, bar);
+        if (tid == SCHED_TID && !ti.end) load_tile<TH, TW, RPB>(ti, sm, bar);
         __syncthreads();
         if (ti.end) break;
         const DevProblem &P = *ti.P;
@@ -915,10 +919,10 @@ __global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__res
             const int y0 = ti.y0, x0 = ti.x0;
             const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
             if (border)
-                y_late = pass_tile<TH, TW, NT, true>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
+                y_late = pass_tile<TH, TW, NT, true, RPB>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
                                                      ti.Rn, ti.Pn, A, hook);
             else
-                y_late = pass_tile<TH, TW, NT, false>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
+                y_late = pass_tile<TH, TW, NT, false, RPB>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
                                                       ti.Xn, ti.Rn, ti.Pn, A, hook);
         }
 

@@ -45,8 +45,11 @@ misr_status check_desc(const misr_desc &d);
 // of every problem named must be listed exactly once.  `work`: the launch's tile counter (two
 // unsigned ints, zero before the first launch; every launch leaves them zero).  Launches that
 // share a `work` must be stream-ordered.
-misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, int n_tiles, const int2 *groups,
-                            int n_groups, unsigned *work, int mode, double alpha, double beta, cudaStream_t s);
+// The tile list holds the n_f32 tiles of float-direction problems first, then the n_bf16 tiles
+// of bf16-direction problems (one pass launch each).
+misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, int n_f32, int n_bf16,
+                            const int2 *groups, int n_groups, unsigned *work, int mode, double alpha, double beta,
+                            cudaStream_t s);
 // append problem `pi`'s tiles (border tiles first) and groups to a launch's lists
 void append_tiles(const misr::DevProblem &hp, int pi, std::vector<int2> &tiles, std::vector<int2> &groups);
 // prepare problem `pidx` of `probs`: interleave frames, start point, reset (flags as prepare_kernel)
