@@ -77,7 +77,13 @@ typedef struct misr_desc {
                                 copy (an alpha p update below the bf16 step of x is not lost);
                                 stencils accumulate in float and the SCG scalars stay FP64 either
                                 way.  misr_pass_probe needs MISR_F32. */
+    int32_t tile_shape;      /* MISR_TILE_AUTO (0): the shape misr_autotune chose for this HR size
+                                in this process, else the default; or one of MISR_TILE_* */
 } misr_desc;
+
+/* Tile shapes of the fused pass (HR pixels per CTA tile; threads per CTA).  The paper has no
+ * counterpart: its partitions are whole sub-images per GPU (Sec. 3.1). */
+enum { MISR_TILE_AUTO = 0, MISR_TILE_32x64 = 1, MISR_TILE_32x32 = 2, MISR_TILE_16x64 = 3, MISR_N_TILE_SHAPES = 3 };
 
 /* Solve summary.  J_final, rnorm2 are FP64 reductions computed on the device. */
 typedef struct misr_stats {
@@ -227,6 +233,14 @@ misr_status misr_server_wait(misr_server_t server, uint64_t ticket, double timeo
 /* Counters: out[0] queued requests, out[1] running, out[2] slots, out[3] slot workspace bytes,
  * out[4] fused-pass launches so far. */
 misr_status misr_server_counters(misr_server_t server, int64_t *out);
+
+/* Autotuner of the tile shape.  Times `passes` fused passes of every compiled tile shape on the
+ * geometry of `desc` (on zeroed device buffers it allocates and frees), and remembers the
+ * fastest for plans of the same HR size created with tile_shape = MISR_TILE_AUTO in this
+ * process.  shape_out (may be NULL): the chosen MISR_TILE_*; ms_out (may be NULL): the time per
+ * pass of each shape, MISR_N_TILE_SHAPES values in MISR_TILE_* order.  passes: 1..1000.
+ * Errors: MISR_EINVAL (descriptor, passes), MISR_ENOMEM, MISR_ECUDA. */
+misr_status misr_autotune(const misr_desc *desc, int32_t passes, int32_t *shape_out, double *ms_out);
 
 /* Allocation-free objective and gradient.  The paper has no counterpart: this is an
  * interface addition of the library.  It returns the same J(x) and grad J(x) as

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(PKG, "libmisr.so")
 MISR_OK, MISR_EINVAL, MISR_ENOMEM, MISR_ECUDA, MISR_EAGAIN, MISR_ETIMEOUT, MISR_ENOTIMPL = range(7)
 MISR_F32, MISR_U16, MISR_BF16 = 0, 1, 2
 MISR_X0_ZERO, MISR_X0_SHIFT_ADD, MISR_X0_GIVEN = 0, 1, 2
+MISR_TILE_AUTO, MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64 = 0, 1, 2, 3
+MISR_N_TILE_SHAPES = 3
 MISR_TRACE_COLS = 10
 MISR_PASS_SUMS = 10
 TRACE_FIELDS = ("E", "J_trial", "alpha", "delta", "mu", "lam", "Delta", "pn2", "rn2", "accept")
@@ -30,6 +32,7 @@ class misr_desc(C.Structure):
         ("lambda_", C.c_double), ("btv_alpha", C.c_double), ("btv_w", C.c_int32),
         ("eps", C.c_double), ("iters", C.c_int32), ("x0_mode", C.c_int32),
         ("in_dtype", C.c_int32), ("flat_field", C.c_float), ("iterate_dtype", C.c_int32),
+        ("tile_shape", C.c_int32),
     ]
 
 
@@ -79,6 +82,7 @@ def lib():
         L.misr_batch_create.argtypes = [C.c_int32, C.POINTER(VP), C.POINTER(VP)]
         L.misr_batch_destroy.argtypes = [VP]
         L.misr_batch_solve.argtypes = [VP, C.POINTER(VP), C.POINTER(VP), VP, C.POINTER(misr_stats)]
+        L.misr_autotune.argtypes = [C.POINTER(misr_desc), C.c_int32, C.POINTER(C.c_int32), DP]
         L.misr_server_create.argtypes = [C.POINTER(misr_server_cfg), C.POINTER(VP)]
         L.misr_server_destroy.argtypes = [VP]
         L.misr_submit.argtypes = [VP, C.POINTER(misr_desc), VP, VP, C.POINTER(C.c_uint64)]
@@ -88,7 +92,8 @@ def lib():
         for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_forward",
                      "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_get_trace",
                      "misr_batch_create", "misr_batch_destroy", "misr_batch_solve", "misr_server_create",
-                     "misr_server_destroy", "misr_submit", "misr_poll", "misr_server_wait", "misr_server_counters"):
+                     "misr_server_destroy", "misr_submit", "misr_poll", "misr_server_wait", "misr_server_counters",
+                     "misr_autotune"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -223,6 +228,15 @@ def misr_server_counters(server: int) -> dict:
     return dict(zip(("queued", "running", "slots", "slot_bytes", "passes_launched"), list(out)))
 
 
+def misr_autotune(desc: misr_desc, passes: int = 10):
+    """Time every tile shape on this geometry; the fastest becomes the default of later plans of
+    the same HR size.  Returns (chosen MISR_TILE_*, ms per pass of each shape)."""
+    shape = C.c_int32()
+    ms = np.zeros(MISR_N_TILE_SHAPES, dtype=np.float64)
+    _check(lib().misr_autotune(C.byref(desc), int(passes), C.byref(shape), ms.ctypes.data_as(DP)), "misr_autotune")
+    return shape.value, ms
+
+
 def _stats_dict(st: misr_stats):
     return {"iters_done": st.iters_done, "accepted": st.accepted, "status": st.status,
             "J_final": st.J_final, "rnorm2": st.rnorm2, "lambda_scg": st.lambda_scg}
@@ -230,7 +244,8 @@ def _stats_dict(st: misr_stats):
 
 # ---------------------------------------------------------------- torch convenience layer
 def make_desc(lr_h, lr_w, factor, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, iters=100,
-              x0_mode=MISR_X0_SHIFT_ADD, in_dtype=MISR_F32, flat_field=40000.0, iterate_dtype=MISR_F32):
+              x0_mode=MISR_X0_SHIFT_ADD, in_dtype=MISR_F32, flat_field=40000.0, iterate_dtype=MISR_F32,
+              tile_shape=MISR_TILE_AUTO):
     sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float32).reshape(-1))
     ps = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
     d = misr_desc()
@@ -241,6 +256,7 @@ def make_desc(lr_h, lr_w, factor, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3,
     d.lambda_, d.btv_alpha, d.btv_w, d.eps = float(lam), float(btv_alpha), int(btv_w), float(eps)
     d.iters, d.x0_mode, d.in_dtype = int(iters), int(x0_mode), int(in_dtype)
     d.flat_field, d.iterate_dtype = float(flat_field), int(iterate_dtype)
+    d.tile_shape = int(tile_shape)
     d._keep = (sh, ps)  # keep the host arrays alive while the descriptor is used
     return d
 

@@ -37,9 +37,20 @@ misr_status misr_host::fail(misr_status s, const char *fmt, ...) {
 
 namespace {
 
-// the tile shape of the fused pass
-constexpr int TILE_H = 32, TILE_W = 64, PASS_NT = 512;
-using PassGeo = Geo<TILE_H, TILE_W>;
+// The compiled tile shapes of the fused pass (SHAPE_* in misr_types.cuh), dispatched at run time.
+template <int S>
+using ShapeGeo = Geo<SHAPE_TH[S], SHAPE_TW[S]>;
+template <typename F>
+auto with_shape(int s, F &&f) {
+    static_assert(N_SHAPES == 3 && MISR_N_TILE_SHAPES == N_SHAPES, "one case per compiled shape");
+    switch (s) {
+    case 0: return f(std::integral_constant<int, 0>());
+    case 1: return f(std::integral_constant<int, 1>());
+    default: return f(std::integral_constant<int, 2>());
+    }
+}
+// the shape untuned geometries get (fastest on the B300 at 4096^2 and 768^2 HR)
+constexpr int DEFAULT_SHAPE = 1;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -100,6 +111,8 @@ static misr_status validate(const misr_desc *d) {
     if (d->in_dtype == MISR_U16 && !(d->flat_field > 0)) return fail(MISR_EINVAL, "flat_field must be > 0");
     if (d->iterate_dtype != MISR_F32 && d->iterate_dtype != MISR_BF16)
         return fail(MISR_EINVAL, "iterate_dtype must be MISR_F32 or MISR_BF16");
+    if (d->tile_shape < MISR_TILE_AUTO || d->tile_shape > MISR_N_TILE_SHAPES)
+        return fail(MISR_EINVAL, "tile_shape must be MISR_TILE_AUTO or a MISR_TILE_* shape");
     return MISR_OK;
 }
 
@@ -124,60 +137,121 @@ static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
     return MISR_OK;
 }
 
+template <int S, bool B>
+static misr_status set_attrs_one() {
+    auto *k = scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], B>;
+    CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ShapeGeo<S>::SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    return MISR_OK;
+}
+
 static misr_status set_pass_attrs() {
     static bool done = false;
     if (done) return MISR_OK;
-    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>,
-                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
-    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>,
-                            cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, true>,
-                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
-    CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, true>,
-                            cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    for (int sh = 0; sh < N_SHAPES; ++sh) {
+        misr_status r = with_shape(sh, [](auto S) {
+            misr_status q = set_attrs_one<decltype(S)::value, false>();
+            return q != MISR_OK ? q : set_attrs_one<decltype(S)::value, true>();
+        });
+        if (r != MISR_OK) return r;
+    }
     done = true;
     return MISR_OK;
 }
 
-// CTAs of the fused pass resident on the whole GPU
-static int resident_ctas() {
-    static int cached = -1;
-    if (cached >= 0) return cached;
+// CTAs of the fused pass resident on the whole GPU, per shape
+static int resident_ctas(int shape) {
+    static int cached[N_SHAPES] = {-1, -1, -1};
+    if (cached[shape] >= 0) return cached[shape];
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>, PASS_NT,
-                                                  PassGeo::SMEM_BYTES);
+    with_shape(shape, [&](auto S) {
+        constexpr int s = decltype(S)::value;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scg_pass_kernel<SHAPE_TH[s], SHAPE_TW[s], SHAPE_NT[s], false>,
+                                                      SHAPE_NT[s], ShapeGeo<s>::SMEM_BYTES);
+        return 0;
+    });
     cudaGetLastError();
-    cached = sms * per_sm;
-    return cached;
+    cached[shape] = sms * per_sm;
+    return cached[shape];
 }
 
-// persistent grid: one CTA per resident slot, at most one per work item
-static int pass_grid(int n_items) { return std::max(1, std::min(n_items, resident_ctas())); }
+// persistent grid: one CTA per resident slot, at most one per tile
+static int pass_grid(int shape, int n_tiles) { return std::max(1, std::min(n_tiles, resident_ctas(shape))); }
 
 static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double beta, cudaStream_t s) {
-    const int n = p->hp.n_tiles;
-    return launch_pass_raw(p->dprob, p->dtile, p->hp.rp_bf16 ? 0 : n, p->hp.rp_bf16 ? n : 0, p->dgroup,
-                           p->hp.n_groups, p->work, mode, alpha, beta, s);
+    return launch_pass_raw(p->dprob, p->dtile, p->segs, p->dgroup, p->hp.n_groups, p->work, mode, alpha, beta, s);
+}
+
+// The tile list of problem `pi` (border tiles first: they cost more, so a pass ends on
+// interior tiles).
+static void append_tiles(const DevProblem &hp, int pi, std::vector<int2> &tiles) {
+    const int tx = hp.tiles_x, TH = hp.tile_h, TW = hp.tile_w;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int t = 0; t < hp.n_tiles; ++t) {
+            const int y0 = (t / tx) * TH, x0 = (t % tx) * TW;
+            const bool border = y0 - 6 < 0 || x0 - 8 < 0 || y0 + TH + 6 > hp.H || x0 + TW + 8 > hp.W;
+            if (border == (pass == 0)) tiles.push_back(make_int2(pi, t));
+        }
+}
+
+void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, const std::vector<int> &idx,
+                                 std::vector<int2> &tiles, std::vector<int2> &groups, PassSegs &segs) {
+    segs = PassSegs{};
+    for (int sh = 0; sh < N_SHAPES; ++sh)
+        for (int b = 0; b < 2; ++b)
+            for (size_t i = 0; i < recs.size(); ++i)
+                if (recs[i]->shape == sh && (recs[i]->rp_bf16 != 0) == (b == 1)) {
+                    append_tiles(*recs[i], idx[i], tiles);
+                    segs.n[sh][b] += recs[i]->n_tiles;
+                }
+    for (size_t i = 0; i < recs.size(); ++i)
+        for (int g = 0; g < recs[i]->n_groups; ++g) groups.push_back(make_int2(idx[i], g));
+}
+
+// The process's tuned shapes: HR image size -> the fastest shape misr_autotune measured.
+std::mutex g_tuned_mu;
+std::vector<std::pair<std::pair<int, int>, int>> g_tuned;
+
+// The shape of a plan: the descriptor's, else the tuned one for its HR size, else the default.
+static int pick_shape(const misr_desc &d) {
+    if (d.tile_shape >= 1 && d.tile_shape <= N_SHAPES) return d.tile_shape - 1;
+    const int H = d.factor * d.lr_h, W = d.factor * d.lr_w;
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    for (auto &e : g_tuned)
+        if (e.first.first == H && e.first.second == W) return e.second;
+    return DEFAULT_SHAPE;
+}
+
+// Tile grid of a shape; the TMA maps of the workspace images with that shape's boxes.
+static void set_shape(DevProblem &hp, int shape) {
+    hp.shape = shape;
+    hp.tile_h = SHAPE_TH[shape];
+    hp.tile_w = SHAPE_TW[shape];
+    hp.tiles_y = (hp.H + hp.tile_h - 1) / hp.tile_h;
+    hp.tiles_x = (hp.W + hp.tile_w - 1) / hp.tile_w;
+    hp.n_tiles = hp.tiles_y * hp.tiles_x;
+}
+static misr_status make_maps(DevProblem &hp) {
+    int xw = 0, xh = 0, ew = 0, eh = 0;
+    with_shape(hp.shape, [&](auto S) {
+        using G = ShapeGeo<decltype(S)::value>;
+        xw = G::XW; xh = G::XH; ew = G::EW; eh = G::EH;
+        return 0;
+    });
+    misr_status ms = get_encode_tiled();
+    for (int i = 0; i < 2 && ms == MISR_OK; ++i) {
+        ms = make_map(&hp.tmX[i], hp.X[i], hp.W, hp.H, hp.pitch, xw, xh, false);
+        if (ms == MISR_OK) ms = make_map(&hp.tmR[i], hp.Rv[i], hp.W, hp.H, hp.pitch, xw, xh, false, hp.rp_bf16);
+        if (ms == MISR_OK) ms = make_map(&hp.tmP[i], hp.Pv[i], hp.W, hp.H, hp.pitch, xw, xh, false, hp.rp_bf16);
+    }
+    if (ms == MISR_OK) ms = make_map(&hp.tmY, hp.Y, hp.W, hp.H, hp.pitch, ew, eh, true);
+    return ms;
 }
 
 // Groups of the pass reduction: at least 64 tiles, at most 128 groups (the last group's
 // warp sums all groups).
-// The tile list (border tiles first: they cost more, so the pass ends on interior tiles)
-// and the group list of problem `pi`, appended to the launch's lists.
-void misr_host::append_tiles(const DevProblem &hp, int pi, std::vector<int2> &tiles, std::vector<int2> &groups) {
-    const int ty = hp.tiles_y, tx = hp.tiles_x;
-    for (int pass = 0; pass < 2; ++pass)
-        for (int t = 0; t < hp.n_tiles; ++t) {
-            const int y0 = (t / tx) * TILE_H, x0 = (t % tx) * TILE_W;
-            const bool border = y0 - 6 < 0 || x0 - 8 < 0 || y0 + TILE_H + 6 > hp.H || x0 + TILE_W + 8 > hp.W;
-            if (border == (pass == 0)) tiles.push_back(make_int2(pi, t));
-        }
-    (void)ty;
-    for (int g = 0; g < hp.n_groups; ++g) groups.push_back(make_int2(pi, g));
-}
-
 static void set_groups(DevProblem &hp) {
     hp.group = 64;
     while ((hp.n_tiles + hp.group - 1) / hp.group > 128) hp.group *= 2;
@@ -198,22 +272,29 @@ static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float 
     return MISR_OK;
 }
 
-misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, int n_f32, int n_bf16,
+misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, const PassSegs &segs,
                                        const int2 *groups, int n_groups, unsigned *work, int mode, double alpha,
                                        double beta, cudaStream_t s) {
-    if (n_f32 + n_bf16 <= 0) return MISR_OK;
+    if (segs.total() <= 0) return MISR_OK;
     misr_status r = set_pass_attrs();
     if (r != MISR_OK) return r;
-    if (n_f32 > 0) {
-        scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false><<<pass_grid(n_f32), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
-            probs, tiles, n_f32, work, mode, alpha, beta);
-        CK(cudaGetLastError());
-    }
-    if (n_bf16 > 0) {
-        scg_pass_kernel<TILE_H, TILE_W, PASS_NT, true><<<pass_grid(n_bf16), PASS_NT, PassGeo::SMEM_BYTES, s>>>(
-            probs, tiles + n_f32, n_bf16, work, mode, alpha, beta);
-        CK(cudaGetLastError());
-    }
+    int off = 0;
+    for (int sh = 0; sh < N_SHAPES; ++sh)
+        for (int b = 0; b < 2; ++b) {
+            const int n = segs.n[sh][b];
+            if (n <= 0) continue;
+            const int2 *t = tiles + off;
+            off += n;
+            with_shape(sh, [&](auto S) {
+                constexpr int k = decltype(S)::value;
+                constexpr int TH = SHAPE_TH[k], TW = SHAPE_TW[k], NT = SHAPE_NT[k];
+                const size_t smem = ShapeGeo<k>::SMEM_BYTES;
+                if (b) scg_pass_kernel<TH, TW, NT, true><<<pass_grid(k, n), NT, smem, s>>>(probs, t, n, work, mode, alpha, beta);
+                else scg_pass_kernel<TH, TW, NT, false><<<pass_grid(k, n), NT, smem, s>>>(probs, t, n, work, mode, alpha, beta);
+                return 0;
+            });
+            CK(cudaGetLastError());
+        }
     reduce_kernel<<<n_groups, 32, 0, s>>>(probs, groups, mode);
     CK(cudaGetLastError());
     return MISR_OK;
@@ -301,9 +382,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
             if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
         }
     hp.eps_pairs = d.eps * eps_pairs;
-    hp.tiles_y = (hp.H + TILE_H - 1) / TILE_H;
-    hp.tiles_x = (hp.W + TILE_W - 1) / TILE_W;
-    hp.n_tiles = hp.tiles_y * hp.tiles_x;
+    set_shape(hp, pick_shape(d));
     set_groups(hp);
 
     misr_plan_t p = new (std::nothrow) misr_plan_s();
@@ -358,15 +437,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     p->dtile = (int2 *)(b + o_tm);
     p->dgroup = (int2 *)(b + o_gl);
     {
-        misr_status ms = get_encode_tiled();
-        for (int i = 0; i < 2 && ms == MISR_OK; ++i) {
-            ms = make_map(&hp.tmX[i], hp.X[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
-            if (ms == MISR_OK)
-                ms = make_map(&hp.tmR[i], hp.Rv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false, hp.rp_bf16);
-            if (ms == MISR_OK)
-                ms = make_map(&hp.tmP[i], hp.Pv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false, hp.rp_bf16);
-        }
-        if (ms == MISR_OK) ms = make_map(&hp.tmY, hp.Y, hp.W, hp.H, hp.pitch, PassGeo::EW, PassGeo::EH, true);
+        const misr_status ms = make_maps(hp);
         if (ms != MISR_OK) {
             cudaFree(p->ws);
             delete p;
@@ -376,7 +447,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     p->hp = hp;
 
     std::vector<int2> tiles, groups;
-    append_tiles(hp, 0, tiles, groups);
+    build_pass_lists({&p->hp}, {0}, tiles, groups, p->segs);
     misr_status rs = MISR_OK;
     do {
         if ((e = cudaMemset(p->ws, 0, off)) != cudaSuccess) break;
@@ -597,7 +668,9 @@ namespace {
 constexpr size_t na_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 constexpr int NOALLOC_MAX_H = 512, NOALLOC_MAX_W = 512;
 constexpr size_t NOALLOC_IMG = na_align(size_t(NOALLOC_MAX_H) * NOALLOC_MAX_W * sizeof(float), 256);
-constexpr int NOALLOC_MAX_TILES = ((NOALLOC_MAX_H + TILE_H - 1) / TILE_H) * ((NOALLOC_MAX_W + TILE_W - 1) / TILE_W);
+// (the allocation-free gradient runs the default shape)
+constexpr int NOALLOC_MAX_TILES = ((NOALLOC_MAX_H + SHAPE_TH[DEFAULT_SHAPE] - 1) / SHAPE_TH[DEFAULT_SHAPE]) *
+                                  ((NOALLOC_MAX_W + SHAPE_TW[DEFAULT_SHAPE] - 1) / SHAPE_TW[DEFAULT_SHAPE]);
 constexpr int NOALLOC_MAX_GROUPS = 128;
 constexpr size_t NA_O_IMG = 0;
 constexpr size_t NA_O_PART = NA_O_IMG + 7 * NOALLOC_IMG;
@@ -638,10 +711,8 @@ misr_status noalloc_setup(unsigned char **base) {
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr)
             return fail(MISR_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-        CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeo::SMEM_BYTES));
-        CK(cudaFuncSetAttribute(scg_pass_kernel<TILE_H, TILE_W, PASS_NT, false>,
-                                cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        const misr_status r = set_pass_attrs();
+        if (r != MISR_OK) return r;
         d.base = static_cast<unsigned char *>(ptr);
         d.ready = true;
     }
@@ -683,9 +754,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
             if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
         }
     hp.eps_pairs = d.eps * eps_pairs;
-    hp.tiles_y = (hp.H + TILE_H - 1) / TILE_H;
-    hp.tiles_x = (hp.W + TILE_W - 1) / TILE_W;
-    hp.n_tiles = hp.tiles_y * hp.tiles_x;
+    set_shape(hp, DEFAULT_SHAPE);
     set_groups(hp);
     for (int i = 0; i < 2; ++i) {
         hp.X[i] = reinterpret_cast<float *>(base + NA_O_IMG + (0 + i) * NOALLOC_IMG);
@@ -699,14 +768,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
     hp.counter = reinterpret_cast<unsigned int *>(base + NA_O_CNT);
     hp.st = reinterpret_cast<ScgState *>(base + NA_O_ST);
     hp.trace = nullptr;
-    s = get_encode_tiled();
-    for (int i = 0; i < 2 && s == MISR_OK; ++i) {
-        s = make_map(&hp.tmX[i], hp.X[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
-        if (s == MISR_OK) s = make_map(&hp.tmR[i], hp.Rv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
-        if (s == MISR_OK) s = make_map(&hp.tmP[i], hp.Pv[i], hp.W, hp.H, hp.pitch, PassGeo::XW, PassGeo::XH, false);
-    }
-    if (s == MISR_OK) s = make_map(&hp.tmY, hp.Y, hp.W, hp.H, hp.pitch, PassGeo::EW, PassGeo::EH, true);
-    return s;
+    return make_maps(hp);
 }
 
 }  // namespace
@@ -726,25 +788,17 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     DevProblem hp;
     s = noalloc_problem(*desc, base, hp);
     if (s != MISR_OK) return s;
-    int2 tiles[NOALLOC_MAX_TILES], groups[NOALLOC_MAX_GROUPS];
-    {
-        int nt = 0;
-        for (int pass = 0; pass < 2; ++pass)   // border tiles first, as append_tiles orders them
-            for (int t = 0; t < hp.n_tiles; ++t) {
-                const int y0 = (t / hp.tiles_x) * TILE_H, x0 = (t % hp.tiles_x) * TILE_W;
-                const bool border = y0 - 6 < 0 || x0 - 8 < 0 || y0 + TILE_H + 6 > hp.H || x0 + TILE_W + 8 > hp.W;
-                if (border == (pass == 0)) tiles[nt++] = make_int2(0, t);
-            }
-        for (int g = 0; g < hp.n_groups; ++g) groups[g] = make_int2(0, g);
-    }
+    std::vector<int2> tiles, groups;   // host lists (no device allocation)
+    PassSegs segs;
+    build_pass_lists({&hp}, {0}, tiles, groups, segs);
     DevProblem *dprob = reinterpret_cast<DevProblem *>(base + NA_O_PROB);
     int2 *dtile = reinterpret_cast<int2 *>(base + NA_O_TMAP);
     int2 *dgroup = reinterpret_cast<int2 *>(base + NA_O_GLIST);
     unsigned int *work = reinterpret_cast<unsigned int *>(base + NA_O_WORK);
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(dprob, &hp, sizeof(DevProblem), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(dtile, tiles, sizeof(int2) * hp.n_tiles, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(dgroup, groups, sizeof(int2) * hp.n_groups, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dtile, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dgroup, groups.data(), sizeof(int2) * groups.size(), cudaMemcpyHostToDevice, st));
     // (prepare's state reset zeroes the group counters and the pass counter; the tile counter
     // is zero in a fresh scratch array and zeroed again by every pass)
     const float log_i0 = desc->in_dtype == MISR_U16 ? logf(desc->flat_field) : 0.f;
@@ -753,7 +807,7 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     prepare_kernel<<<grid_for(npitched, 256), 256, 0, st>>>(dprob, 0, y_dev, desc->in_dtype, log_i0, x_dev,
                                                            MISR_X0_GIVEN, 1 | 2 | 4);
     CK(cudaGetLastError());
-    s = launch_pass_raw(dprob, dtile, hp.n_tiles, 0, dgroup, hp.n_groups, work, MODE_PROBE, 0.0, 0.0, st);
+    s = launch_pass_raw(dprob, dtile, segs, dgroup, hp.n_groups, work, MODE_PROBE, 0.0, 0.0, st);
     if (s != MISR_OK) return s;
     scale_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(hp.Rv[1], hp.pitch, -1.f, g_dev, hp.H, hp.W);
     CK(cudaGetLastError());
@@ -762,5 +816,70 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     CK(cudaStreamSynchronize(st));
     if (hst.status != DEV_OK) return fail(MISR_ETIMEOUT, "a tile load of the fused pass did not complete in time");
     if (J_out) *J_out = hst.sums[P_JD] + (double)hp.lambda * (hst.sums[P_JB] - hp.eps_pairs);
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_autotune(const misr_desc *desc, int32_t passes, int32_t *shape_out, double *ms_out) {
+    if (!desc) return fail(MISR_EINVAL, "desc is NULL");
+    if (passes < 1 || passes > 1000) return fail(MISR_EINVAL, "passes must be in [1, 1000]");
+    misr_status st = check_desc(*desc);
+    if (st != MISR_OK) return st;
+    const size_t in_bytes = (size_t)desc->K * desc->lr_h * desc->lr_w * (desc->in_dtype == MISR_U16 ? 2 : 4);
+    void *y = nullptr;
+    cudaError_t e = cudaMalloc(&y, in_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MISR_ENOMEM, "autotune frames: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double ms[N_SHAPES];
+    int best = DEFAULT_SHAPE;
+    do {
+        if ((e = cudaMemset(y, 0, in_bytes)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) break;
+        if ((e = cudaEventCreate(&e0)) != cudaSuccess) break;
+        if ((e = cudaEventCreate(&e1)) != cudaSuccess) break;
+        for (int sh = 0; sh < N_SHAPES && st == MISR_OK; ++sh) {
+            misr_desc d = *desc;
+            d.tile_shape = sh + 1;
+            d.iters = 1;
+            d.x0_mode = MISR_X0_ZERO;
+            misr_plan_t p = nullptr;
+            st = misr_plan_create(&d, &p);
+            if (st != MISR_OK) break;
+            // passes of the probe mode leave the state alone, so every launch is the same pass
+            st = launch_prepare(p, y, nullptr, 1 | 2 | 4, s);
+            for (int i = 0; i < 2 && st == MISR_OK; ++i) st = launch_pass(p, MODE_PROBE, 0.5, 0.5, s);
+            if (st == MISR_OK && (e = cudaEventRecord(e0, s)) != cudaSuccess) st = fail(MISR_ECUDA, "event");
+            for (int i = 0; i < passes && st == MISR_OK; ++i) st = launch_pass(p, MODE_PROBE, 0.5, 0.5, s);
+            if (st == MISR_OK && (e = cudaEventRecord(e1, s)) != cudaSuccess) st = fail(MISR_ECUDA, "event");
+            if (st == MISR_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) st = fail(MISR_ECUDA, "autotune run failed");
+            float t = 0.f;
+            if (st == MISR_OK) cudaEventElapsedTime(&t, e0, e1);
+            ms[sh] = (double)t / passes;
+            misr_plan_destroy(p);
+        }
+        if (st != MISR_OK) break;
+        for (int sh = 0; sh < N_SHAPES; ++sh)
+            if (ms[sh] < ms[best]) best = sh;
+    } while (0);
+    if (e1) cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(y);
+    if (st != MISR_OK) return st;
+    if (e != cudaSuccess) return fail(MISR_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    {
+        const int H = desc->factor * desc->lr_h, W = desc->factor * desc->lr_w;
+        std::lock_guard<std::mutex> lock(g_tuned_mu);
+        bool found = false;
+        for (auto &en : g_tuned)
+            if (en.first.first == H && en.first.second == W) { en.second = best; found = true; }
+        if (!found) g_tuned.push_back({{H, W}, best});
+    }
+    if (shape_out) *shape_out = best + 1;
+    if (ms_out)
+        for (int sh = 0; sh < N_SHAPES; ++sh) ms_out[sh] = ms[sh];
     return MISR_OK;
 }

@@ -22,8 +22,8 @@ struct misr_batch_s {
     int2 *ditems = nullptr;         // tiles of all problems, problem after problem
     unsigned int *work = nullptr;   // the fused pass's tile counter
     void *mem = nullptr;
-    int total_items = 0;            // tiles (float-direction problems' first)
-    int n_f32 = 0;                  // tiles of float-direction problems
+    int total_items = 0;            // tiles, by segment
+    PassSegs segs;
     int total_groups = 0;           // groups (listed after the tiles in ditems)
     int max_iters = 0;
     cudaStream_t cap = nullptr;     // private stream used for graph capture
@@ -63,15 +63,16 @@ extern "C" misr_status misr_batch_create(int32_t n, const misr_plan_t *plans, mi
     b->plans.assign(plans, plans + n);
     std::vector<DevProblem> recs(n);
     std::vector<int2> items, groups;
-    for (int pass = 0; pass < 2; ++pass)   // float-direction problems' tiles first, then bf16
-        for (int i = 0; i < n; ++i)
-            if ((plans[i]->hp.rp_bf16 != 0) == (pass == 1)) append_tiles(plans[i]->hp, i, items, groups);
-    b->n_f32 = 0;
+    std::vector<const DevProblem *> rp(n);
+    std::vector<int> idx(n);
     for (int i = 0; i < n; ++i) {
         recs[i] = plans[i]->hp;
-        if (!plans[i]->hp.rp_bf16) b->n_f32 += plans[i]->hp.n_tiles;
+        rp[i] = &plans[i]->hp;
+        idx[i] = i;
         b->max_iters = std::max(b->max_iters, plans[i]->d.iters);
     }
+    // one pass launch per (tile shape, storage type of r and p) present in the batch
+    build_pass_lists(rp, idx, items, groups, b->segs);
     b->total_items = (int)items.size();
     b->total_groups = (int)groups.size();
     items.insert(items.end(), groups.begin(), groups.end());   // tiles, then groups
@@ -111,7 +112,7 @@ static misr_status batch_graph(misr_batch_t b) {
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     misr_status r = MISR_OK;
     for (int i = 0; i < want && r == MISR_OK; ++i)
-        r = launch_pass_raw(b->dprobs, b->ditems, b->n_f32, b->total_items - b->n_f32, b->ditems + b->total_items,
+        r = launch_pass_raw(b->dprobs, b->ditems, b->segs, b->ditems + b->total_items,
                             b->total_groups, b->work, MODE_ITER, 0.0, 0.0, b->cap);
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (r != MISR_OK) { if (graph) cudaGraphDestroy(graph); return r; }
@@ -137,7 +138,7 @@ extern "C" misr_status misr_batch_solve(misr_batch_t b, const void *const *y_dev
         r = launch_prepare_raw(b->dprobs, i, p->d, p->n_pitched, y_dev[i], x_dev[i], p->d.x0_mode, 1 | 2 | 4, s);
     }
     if (r == MISR_OK)
-        r = launch_pass_raw(b->dprobs, b->ditems, b->n_f32, b->total_items - b->n_f32, b->ditems + b->total_items,
+        r = launch_pass_raw(b->dprobs, b->ditems, b->segs, b->ditems + b->total_items,
                             b->total_groups, b->work, MODE_INIT, 0.0, 0.0, s);
     if (r != MISR_OK) return r;
     for (int done = 0; done < b->max_iters; done += b->chunk_len) CK(cudaGraphLaunch(b->chunk, s));

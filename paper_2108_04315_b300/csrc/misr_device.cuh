@@ -838,7 +838,7 @@ __device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_
 // writes each tile's sums, which reduce_kernel combines after the pass.  `work` (two counters,
 // zero at launch) is the launch's tile counter; the last CTA to finish zeroes it again.
 template <int TH, int TW, int NT, bool RPB>
-__global__ void __launch_bounds__(NT, 2) scg_pass_kernel(const DevProblem *__restrict__ probs,
+__global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProblem *__restrict__ probs,
                                                          const int2 *__restrict__ tiles, int n_tiles,
                                                          unsigned *work, int mode, double probe_alpha,
                                                          double probe_beta) {

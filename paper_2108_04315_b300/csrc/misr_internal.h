@@ -45,13 +45,24 @@ misr_status check_desc(const misr_desc &d);
 // of every problem named must be listed exactly once.  `work`: the launch's tile counter (two
 // unsigned ints, zero before the first launch; every launch leaves them zero).  Launches that
 // share a `work` must be stream-ordered.
-// The tile list holds the n_f32 tiles of float-direction problems first, then the n_bf16 tiles
-// of bf16-direction problems (one pass launch each).
-misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, int n_f32, int n_bf16,
+// Tiles per pass kernel instantiation: the tile list holds segment (shape 0, float r/p),
+// (shape 0, bf16 r/p), (shape 1, float), ... in that order, n[shape][bf16] tiles each; one pass
+// launch per non-empty segment.
+struct PassSegs {
+    int n[misr::N_SHAPES][2] = {};
+    int total() const {
+        int t = 0;
+        for (auto &a : n) t += a[0] + a[1];
+        return t;
+    }
+};
+misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, const PassSegs &segs,
                             const int2 *groups, int n_groups, unsigned *work, int mode, double alpha, double beta,
                             cudaStream_t s);
-// append problem `pi`'s tiles (border tiles first) and groups to a launch's lists
-void append_tiles(const misr::DevProblem &hp, int pi, std::vector<int2> &tiles, std::vector<int2> &groups);
+// The tile and group lists of a launch over problems recs[i] (problem index idx[i] in the
+// launch's record array), ordered by segment, each problem's border tiles first.
+void build_pass_lists(const std::vector<const misr::DevProblem *> &recs, const std::vector<int> &idx,
+                      std::vector<int2> &tiles, std::vector<int2> &groups, PassSegs &segs);
 // prepare problem `pidx` of `probs`: interleave frames, start point, reset (flags as prepare_kernel)
 misr_status launch_prepare_raw(const misr::DevProblem *probs, int pidx, const misr_desc &d, size_t n_pitched,
                                const void *y_dev, const float *x_given, int x0_mode, int flags, cudaStream_t s);
@@ -66,6 +77,7 @@ struct misr_plan_s {
     misr::DevProblem hp{};              // host mirror of the device problem record
     misr::DevProblem *dprob = nullptr;  // device problem record
     int2 *dtile = nullptr;              // tile list of the fused pass (0, tile)
+    misr_host::PassSegs segs;           // its one segment
     int2 *dgroup = nullptr;             // group list of its reduction (0, group)
     unsigned int *work = nullptr;       // the fused pass's tile counter
     char *ws = nullptr;                 // one allocation for everything above and below

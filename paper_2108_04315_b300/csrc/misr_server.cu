@@ -53,6 +53,7 @@ struct DescCopy {
                a.psf_size == b.psf_size && a.lambda == b.lambda && a.btv_alpha == b.btv_alpha &&
                a.btv_w == b.btv_w && a.eps == b.eps && a.iters == b.iters && a.x0_mode == b.x0_mode &&
                a.in_dtype == b.in_dtype && a.flat_field == b.flat_field && a.iterate_dtype == b.iterate_dtype &&
+               a.tile_shape == b.tile_shape &&
                shifts == o.shifts && psf == o.psf;
     }
 };
@@ -78,6 +79,7 @@ struct Slot {
     uint64_t ticket = 0;
     int passes = 0;        // fused passes run since admission
     int2 *items = nullptr;  // device tile and group lists of this slot alone (for its init pass)
+    PassSegs segs;
 };
 
 size_t plan_bytes_estimate(const misr_desc &d) {
@@ -104,7 +106,8 @@ struct misr_server_s {
     cudaStream_t stream = nullptr;
     DevProblem *dprobs = nullptr;   // one record per slot (capacity cfg.max_slots)
     int2 *ditems = nullptr;         // tile list of the live slots, then their group list
-    int live_tiles = 0, live_groups = 0, live_f32 = 0;
+    int live_tiles = 0, live_groups = 0;
+    PassSegs live_segs;
     unsigned int *work = nullptr;   // the fused pass's tile counter
     size_t ditems_cap = 0;
     ScgState *st_host = nullptr;    // page-locked states, one per slot
@@ -191,7 +194,7 @@ std::vector<int> admit(misr_server_t s) {
                     sl.desc.set(rq.desc.d);
                     s->slot_bytes += plan_bytes_estimate(rq.desc.d);
                     std::vector<int2> t, gl;
-                    append_tiles(p->hp, idx, t, gl);
+                    build_pass_lists({&p->hp}, {idx}, t, gl, sl.segs);
                     t.insert(t.end(), gl.begin(), gl.end());
                     bool ok2 = cudaMalloc(&sl.items, sizeof(int2) * t.size()) == cudaSuccess &&
                                cudaMemcpy(sl.items, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -284,21 +287,21 @@ void worker_main(misr_server_t s) {
             misr_plan_t p = sl.plan;
             if (r == MISR_OK)
                 r = launch_prepare_raw(s->dprobs, idx, p->d, p->n_pitched, rq->y, rq->x, p->d.x0_mode, 1 | 2 | 4, s->stream);
-            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, p->hp.rp_bf16 ? 0 : p->hp.n_tiles,
-                                                  p->hp.rp_bf16 ? p->hp.n_tiles : 0, sl.items + p->hp.n_tiles,
-                                                  p->hp.n_groups, s->work, MODE_INIT, 0.0, 0.0, s->stream);
+            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, sl.segs, sl.items + p->hp.n_tiles, p->hp.n_groups,
+                                                  s->work, MODE_INIT, 0.0, 0.0, s->stream);
         }
         // 2. the live slots' tile map
         if (r == MISR_OK && s->items_dirty) {
             s->h_items.clear();
             std::vector<int2> gl;
-            s->live_f32 = 0;
-            for (int pass = 0; pass < 2; ++pass) {   // float-direction slots' tiles first, then bf16
-                for (size_t i = 0; i < s->slots.size(); ++i)
-                    if (s->slots[i].busy && (s->slots[i].plan->hp.rp_bf16 != 0) == (pass == 1))
-                        append_tiles(s->slots[i].plan->hp, (int)i, s->h_items, gl);
-                if (pass == 0) s->live_f32 = (int)s->h_items.size();
-            }
+            std::vector<const DevProblem *> rp;
+            std::vector<int> idx;
+            for (size_t i = 0; i < s->slots.size(); ++i)
+                if (s->slots[i].busy) {
+                    rp.push_back(&s->slots[i].plan->hp);
+                    idx.push_back((int)i);
+                }
+            build_pass_lists(rp, idx, s->h_items, gl, s->live_segs);
             s->live_tiles = (int)s->h_items.size();
             s->live_groups = (int)gl.size();
             s->h_items.insert(s->h_items.end(), gl.begin(), gl.end());
@@ -312,8 +315,8 @@ void worker_main(misr_server_t s) {
         // 3. k SCG iterations of every live projection, one launch each
         const int nt = s->live_tiles;
         for (int it = 0; it < k_passes && r == MISR_OK && nt > 0; ++it) {
-            r = launch_pass_raw(s->dprobs, s->ditems, s->live_f32, nt - s->live_f32, s->ditems + nt, s->live_groups,
-                                s->work, MODE_ITER, 0.0, 0.0, s->stream);
+            r = launch_pass_raw(s->dprobs, s->ditems, s->live_segs, s->ditems + nt, s->live_groups, s->work, MODE_ITER,
+                                0.0, 0.0, s->stream);
             ++s->passes_launched;
         }
         // 4. completion: read the live states, copy finished projections out

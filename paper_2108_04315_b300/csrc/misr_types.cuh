@@ -32,6 +32,13 @@ constexpr int NPART = 10;
 constexpr int TRACE_COLS = 10;
 constexpr uint32_t TMA_WAIT_TRIES = 1u << 24;   // bounded wait for the tile loads
 
+// Tile shapes of the fused pass: TH x TW HR pixels per tile, NT threads per CTA (1024 / NT
+// CTAs resident per SM).  The autotuner picks one per HR image size.
+constexpr int N_SHAPES = 3;
+constexpr int SHAPE_TH[N_SHAPES] = {32, 32, 16};
+constexpr int SHAPE_TW[N_SHAPES] = {64, 32, 64};
+constexpr int SHAPE_NT[N_SHAPES] = {512, 256, 256};
+
 // partial sums of one pass (FP64)
 enum { P_JD = 0, P_DJD, P_JB, P_RR, P_RRX, P_PR, P_PP, P_A, P_B, P_C };
 enum { MODE_INIT = 0, MODE_ITER = 1, MODE_PROBE = 2 };
@@ -60,6 +67,7 @@ struct DevProblem {
     int H, W, pitch, f, h, w, K;
     int tiles_x, tiles_y, n_tiles, iters;
     int rp_bf16;                                  // r and p stored as bf16 (x stays float)
+    int shape, tile_h, tile_w, pad0;              // tile shape (index into SHAPE_*) and its size
     float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];  // separable PSF, h(a, b) = hy[a+R] hx[b+R]
     float lambda, eps, eps2, pad1;
     float gamma[BTV_W * BTV_W];                   // gamma(dx, dy) at [dy * BTV_W + dx]

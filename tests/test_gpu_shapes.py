@@ -1,0 +1,71 @@
+"""Tile shapes of the fused pass and their autotuner.  Every compiled shape must give the
+oracle's gradient and solve (the tiling changes only the order of the pass's sums); a batch
+mixing shapes must give each projection its own solve bit for bit; misr_autotune must time
+every shape and make the fastest the default of later plans of that HR size."""
+import numpy as np
+import pytest
+
+import gen
+from tests.gpu_common import RTOL_OP, RTOL_X, asym_separable_psf, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SHAPES = (1, 2, 3)   # MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_every_shape_matches_the_oracle(orc, shape):
+    from paper_2108_04315_b300 import binding as B
+    h, w, f = 45, 71, 3
+    sh, psf = gen.third_pixel_shifts(), asym_separable_psf(31)
+    P = orc.Problem(h, w, f, sh, psf, lam=0.01)
+    xt = gen.phantom(f * h, f * w, 32)
+    y = (P.forward_all(xt) + gen.gaussian_noise((len(sh), h, w), 0.01, 33)).astype(np.float32)
+    y64 = y.astype(np.float64)
+    plan = B.Plan(h, w, f, sh, psf, lam=0.01, iters=12, tile_shape=shape)
+    x = gen.smooth_field(f * h, f * w, 34).astype(np.float32)
+    J, g = plan.gradient(to_dev(y), to_dev(x))
+    Jr, gr = P.gradient(x.astype(np.float64), y64)
+    assert rel_l2(g.cpu().numpy(), gr) <= RTOL_OP
+    assert J == pytest.approx(Jr, rel=RTOL_OP)
+    xs, st = plan.solve(to_dev(y))
+    xr, _ = P.scg(y64, P.shift_add(y64), 12)
+    assert rel_l2(xs.cpu().numpy(), xr) <= RTOL_X
+    plan.close()
+
+
+def test_batch_mixing_shapes_equals_each_alone(orc):
+    from paper_2108_04315_b300 import binding as B
+    psf = gen.gaussian_psf(5, 0.5)
+    plans, ys = [], []
+    for i, shape in enumerate((1, 2, 3, 2)):
+        h, w = 30 + 6 * i, 50 - 4 * i
+        P = orc.Problem(h, w, 2, gen.half_pixel_shifts(), psf, lam=0.01)
+        y = (P.forward_all(gen.phantom(2 * h, 2 * w, 40 + i)) + gen.gaussian_noise((4, h, w), 0.01, 50 + i))
+        plans.append(B.Plan(h, w, 2, gen.half_pixel_shifts(), psf, lam=0.01, iters=10, tile_shape=shape))
+        ys.append(to_dev(y.astype(np.float32)))
+    alone = [p.solve(y)[0].clone() for p, y in zip(plans, ys)]
+    batch = B.Batch(plans)
+    xs, _ = batch.solve(ys)
+    for a, b in zip(alone, xs):
+        assert torch.equal(a, b)
+    batch.close()
+
+
+def test_autotune_picks_a_shape_that_later_plans_use(orc):
+    from paper_2108_04315_b300 import binding as B
+    h, w, f = 96, 128, 2
+    sh, psf = gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)
+    shape, ms = B.misr_autotune(B.make_desc(h, w, f, sh, psf, iters=1), passes=5)
+    assert shape in SHAPES
+    assert np.all(ms > 0) and ms[shape - 1] == ms.min()
+    P = orc.Problem(h, w, f, sh, psf, lam=0.01)
+    y = to_dev((P.forward_all(gen.phantom(f * h, f * w, 60)) + gen.gaussian_noise((4, h, w), 0.01, 61))
+               .astype(np.float32))
+    auto = B.Plan(h, w, f, sh, psf, lam=0.01, iters=8)
+    explicit = B.Plan(h, w, f, sh, psf, lam=0.01, iters=8, tile_shape=shape)
+    assert torch.equal(auto.solve(y)[0], explicit.solve(y)[0])
+    with pytest.raises(B.MisrError) as e:
+        B.misr_autotune(B.make_desc(h, w, f, sh, psf), passes=0)
+    assert e.value.status == B.MISR_EINVAL
