@@ -52,13 +52,13 @@ def load_peaks():
         return 6400.0, "fallback"
 
 
-def load_traffic(kernel_tag):
+def load_traffic(kernel_tag, shape_name):
     """Per-launch DRAM bytes of the fused pass from the committed ncu summary, if it was
-    taken on the current kernel source."""
+    taken on the current kernel source and tile shape."""
     try:
         with open(os.path.join(ROOT, "profiles", "scg_pass_traffic.json")) as fh:
             d = json.load(fh)
-        if d.get("kernel_source_sha1") == kernel_tag:
+        if d.get("kernel_source_sha1") == kernel_tag and d.get("tile_shape") == shape_name:
             return float(d["dram_bytes_per_launch_4096"])
     except Exception:
         pass
@@ -66,16 +66,18 @@ def load_traffic(kernel_tag):
 
 
 def kernel_source_tag():
-    """Hash of the fused pass's device code and its launch shape (tile and block size)."""
+    """Hash of the fused pass's device code (its tile shapes included)."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2108_04315_b300", "csrc")
     for f in ("misr_types.cuh", "misr_device.cuh", "tma.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
-    with open(os.path.join(csrc, "misr_api.cu"), "rb") as fh:
-        h.update(b"".join(l for l in fh if l.lstrip().startswith(b"constexpr int TILE_H")))
     return h.hexdigest()
+
+
+# MISR_TILE_* -> (tile rows, tile columns, threads per CTA)
+TILE_SHAPES = {1: (32, 64, 512), 2: (32, 32, 256), 3: (16, 64, 256)}
 
 
 class ClockSampler:
@@ -475,6 +477,8 @@ def main():
     ap.add_argument("--serve-n", type=int, default=240)
     ap.add_argument("--serve-slots", type=int, default=32)
     ap.add_argument("--serve-tick", type=int, default=8)
+    ap.add_argument("--tile-shape", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0: autotune (default); 1: 32x64, 2: 32x32, 3: 16x64")
     args = ap.parse_args()
     if args.workload == "batch":
         run_batch(args)
@@ -507,9 +511,19 @@ def main():
     stream = torch.cuda.current_stream()
     H, W = wl["f"] * wl["h"], wl["f"] * wl["w"]
     shifts, psf = gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)
+    # the autotuner times each tile shape on this geometry; the plans below get the fastest
+    # (--tile-shape fixes one instead, e.g. for profiling runs where timings are distorted)
+    from paper_2108_04315_b300.binding import make_desc, misr_autotune
+    if args.tile_shape:
+        tuned, tune_ms = args.tile_shape, [None] * len(TILE_SHAPES)
+    else:
+        tuned, tune_ms = misr_autotune(make_desc(wl["h"], wl["w"], wl["f"], shifts, psf, iters=1), passes=10)
+    th, tw, nt = TILE_SHAPES[tuned]
+    shape_name = f"{th}x{tw}"
     plan = Plan(wl["h"], wl["w"], wl["f"], shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3,
-                iters=wl["iters"])
-    plan0 = Plan(wl["h"], wl["w"], wl["f"], shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, iters=0)
+                iters=wl["iters"], tile_shape=tuned)
+    plan0 = Plan(wl["h"], wl["w"], wl["f"], shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, iters=0,
+                 tile_shape=tuned)
     xt, y = make_inputs(plan, wl, device)
     x = torch.empty((H, W), dtype=torch.float32, device=device)
 
@@ -574,8 +588,8 @@ def main():
                          % (7 * H * W * 4 // 2**20),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": load_traffic(kernel_source_tag()),
-                     "kernel": "scg_pass_kernel<32,64,512>", "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": load_traffic(kernel_source_tag(), shape_name),
+                     "kernel": f"scg_pass_kernel<{th},{tw},{nt}>", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": PASS_BYTES_PER_PX * H * W,
                      "ms_per_launch": pass_ms,
                      "timed_as": "one SCG pass: the fused pass kernel and its reduction kernel, "
@@ -584,6 +598,9 @@ def main():
         # per solve: prepare, the initial pass and every SCG pass (the fused pass kernel and its
         # reduction kernel), finalize
         "gpu_launches": args.steps * (2 * wl["iters"] + 4),
+        "tile_shape": {"tuned": shape_name, "threads": nt,
+                       "ms_per_pass_by_shape": {"x".join(map(str, TILE_SHAPES[k][:2])): (None if v is None else round(float(v), 5))
+                                                for k, v in zip(sorted(TILE_SHAPES), tune_ms)}},
         "clocks": clocks,
         "solve": {"J_final": st["J_final"], "accepted": st["accepted"], "iters_done": st["iters_done"]},
     }
