@@ -137,6 +137,25 @@ static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
     return MISR_OK;
 }
 
+// Launch with programmatic stream serialization: the kernel may begin launching while the
+// previous kernel on the stream finishes; it waits for it (griddepcontrol.wait) before reading
+// what that kernel produced.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <int S, bool B>
 static misr_status set_attrs_one() {
     auto *k = scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], B>;
@@ -285,18 +304,18 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
             if (n <= 0) continue;
             const int2 *t = tiles + off;
             off += n;
-            with_shape(sh, [&](auto S) {
+            CK(with_shape(sh, [&](auto S) {
                 constexpr int k = decltype(S)::value;
                 constexpr int TH = SHAPE_TH[k], TW = SHAPE_TW[k], NT = SHAPE_NT[k];
                 const size_t smem = ShapeGeo<k>::SMEM_BYTES;
-                if (b) scg_pass_kernel<TH, TW, NT, true><<<pass_grid(k, n), NT, smem, s>>>(probs, t, n, work, mode, alpha, beta);
-                else scg_pass_kernel<TH, TW, NT, false><<<pass_grid(k, n), NT, smem, s>>>(probs, t, n, work, mode, alpha, beta);
-                return 0;
-            });
-            CK(cudaGetLastError());
+                if (b)
+                    return launch_pdl(scg_pass_kernel<TH, TW, NT, true>, pass_grid(k, n), NT, smem, s, probs, t, n,
+                                      work, mode, alpha, beta);
+                return launch_pdl(scg_pass_kernel<TH, TW, NT, false>, pass_grid(k, n), NT, smem, s, probs, t, n, work,
+                                  mode, alpha, beta);
+            }));
         }
-    reduce_kernel<<<n_groups, 32, 0, s>>>(probs, groups, mode);
-    CK(cudaGetLastError());
+    CK(launch_pdl(reduce_kernel, n_groups, 32, 0, s, probs, groups, mode));
     return MISR_OK;
 }
 

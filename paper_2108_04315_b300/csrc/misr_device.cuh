@@ -706,6 +706,10 @@ __device__ __forceinline__ void warp_sum_fields(const double *src, size_t stride
 __global__ void __launch_bounds__(32) reduce_kernel(const DevProblem *__restrict__ probs,
                                                     const int2 *__restrict__ groups, int mode) {
     const int lane = threadIdx.x;
+    // programmatic dependent launch: the next pass may start launching now (its CTAs wait for
+    // this grid to finish before they read the state); this grid waits for the pass
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int2 gi = groups[blockIdx.x];
     const DevProblem &P = probs[gi.x];
     if (ld_cg(&P.st->done)) return;
@@ -857,6 +861,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
     __shared__ SchedState sched;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // launched as a programmatic dependent of the previous kernel: wait for it to finish (and
+    // its writes to be visible) before anything it produced is read
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // the scheduling thread: the last thread, whose warp takes light items in the intervals
     // where it also prepares the CTA's next tile
     constexpr int SCHED_TID = NT - 1;
@@ -976,6 +983,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
             tile_sums[(size_t)lane * n_tiles_p] = lane == P_JB ? (double)hi + (double)lo : (double)hi;
         }
     }
+    // this CTA takes no more tiles: the reduction kernel may start launching
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // the last CTA to stop zeroes the launch's tile counter for the next launch
     __syncthreads();
     if (tid == 0) {
