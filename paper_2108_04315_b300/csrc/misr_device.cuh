@@ -19,7 +19,7 @@ __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
 
 // ---------------------------------------------------------------------------------------
-// SCG scalar tail, run by thread 0 of the last CTA of a pass with the pass totals S.
+// SCG scalar tail, run by lane 0 of the reduction warp that completes a pass's sums S.
 // Steps follow Moller's algorithm (the same order as Algorithm 1's loop body):
 // comparison parameter, accept/reject, lambda updates, beta, then the scaling of the next
 // curvature and the next step size.

@@ -290,7 +290,7 @@ void worker_main(misr_server_t s) {
             if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, sl.segs, sl.items + p->hp.n_tiles, p->hp.n_groups,
                                                   s->work, MODE_INIT, 0.0, 0.0, s->stream);
         }
-        // 2. the live slots' tile map
+        // 2. the live slots' tile and group lists
         if (r == MISR_OK && s->items_dirty) {
             s->h_items.clear();
             std::vector<int2> gl;
@@ -309,7 +309,7 @@ void worker_main(misr_server_t s) {
             if (r == MISR_OK && !s->h_items.empty() &&
                 cudaMemcpyAsync(s->ditems, s->h_items.data(), sizeof(int2) * s->h_items.size(), cudaMemcpyHostToDevice,
                                 s->stream) != cudaSuccess)
-                r = fail(MISR_ECUDA, "tile map upload failed");
+                r = fail(MISR_ECUDA, "tile list upload failed");
             s->items_dirty = false;
         }
         // 3. k SCG iterations of every live projection, one launch each
