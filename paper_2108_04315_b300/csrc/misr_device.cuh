@@ -397,7 +397,19 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     // g(q) = sum_d gamma_d [psi'(x_q - x_{q+d}) - psi'(x_{q-d} - x_q)] over pairs inside the
     // image; the prior's value gamma_d psi(x_q - x_{q+d}) + eps is summed over owned q.
     auto item_btv = [&](int it) {
-        const int n = it / (GW / 4), g = 4 * (it - n * (GW / 4));
+        // items of the first WA columns of each row come first, so that 8 consecutive threads
+        // (one shared-memory phase of 16-byte loads) stay in one row; the remaining columns
+        // follow
+        constexpr int W4 = GW / 4, WA = W4 & ~7, WB = W4 - WA;
+        int n, g;
+        if (it < GH * WA) {
+            n = it / WA;
+            g = 4 * (it - n * WA);
+        } else {
+            const int k = it - GH * WA;
+            n = k / WB;
+            g = 4 * (WA + k - n * WB);
+        }
         const int qy = y0 - 2 + n, qx = x0 - 2 + g;          // image coords of the first pixel
         // x' rows n-2 .. n+2 of the G grid are XB rows n+2 .. n+6; cols g-4 .. g+3 of the G
         // grid (8 values, 16-byte aligned) are XB cols g+4 .. g+11
