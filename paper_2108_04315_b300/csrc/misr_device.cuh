@@ -949,17 +949,40 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
         // FP32 warp sums.  The prior's value enters Moller's comparison as a difference of
         // two passes' sums, so its sums are compensated (two-sum: hi + lo carries the
         // rounding error of every addition).
-        float v[NPART] = {A.jd, A.dj, A.jb, A.rr, A.rrx, A.pr, A.pp, A.a, A.b, A.c};
+        // Eight of the plain sums by a transposing butterfly: at offsets 16, 8 and 4 each lane
+        // keeps half of its values and adds its partner's half (lane bits 4, 3, 2 choose which
+        // half), so lane l ends with value ((l>>4)&1)*4 + ((l>>3)&1)*2 + ((l>>2)&1) summed over
+        // its group of four lanes; offsets 2 and 1 finish it.  Nine shuffles instead of forty.
+        {
+            float t8[8] = {A.jd, A.dj, A.rr, A.rrx, A.pr, A.pp, A.a, A.b};
+            const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+            float t4[4], t2[2];
 #pragma unroll
-        for (int j = 0; j < NPART; ++j) {
-            if (j == P_JB) continue;
-            float x = v[j];
+            for (int k = 0; k < 4; ++k) {
+                const float keep = b4 ? t8[4 + k] : t8[k], send = b4 ? t8[k] : t8[4 + k];
+                t4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-            if (lane == 0) red[warp][j] = x;
+            for (int k = 0; k < 2; ++k) {
+                const float keep = b3 ? t4[2 + k] : t4[k], send = b3 ? t4[k] : t4[2 + k];
+                t2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+            float t1;
+            {
+                const float keep = b2 ? t2[1] : t2[0], send = b2 ? t2[0] : t2[1];
+                t1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            t1 += __shfl_xor_sync(0xffffffffu, t1, 2);
+            t1 += __shfl_xor_sync(0xffffffffu, t1, 1);
+            constexpr int slot[8] = {P_JD, P_DJD, P_RR, P_RRX, P_PR, P_PP, P_A, P_B};
+            if ((lane & 3) == 0) red[warp][slot[(b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0)]] = t1;
+            float c = A.c;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+            if (lane == 0) red[warp][P_C] = c;
         }
         {
-            float hi = v[P_JB], lo = 0.f;
+            float hi = A.jb, lo = 0.f;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const float h2 = __shfl_down_sync(0xffffffffu, hi, off);

@@ -191,9 +191,14 @@ def test_uint16_counts_log_converted_on_device(orc):
     xt = gen.phantom(f * h, f * w, 600)
     counts = gen.poisson_counts(P.forward_all(xt), 40000.0, 601)
     y64 = orc.log_convert(counts, 40000.0)
-    plan = B.Plan(h, w, f, shifts, psf, lam=0.01, iters=20, in_dtype=B.MISR_U16, flat_field=40000.0)
+    # 10 iterations: the 12th step of this problem lowers J by 2.6e-10 of J, below the FP32
+    # evaluation floor of the objective (~1e-9 J), so its accept decision is not determined in
+    # FP32 and later iterates may follow either branch
+    iters = 10
+    plan = B.Plan(h, w, f, shifts, psf, lam=0.01, iters=iters, in_dtype=B.MISR_U16, flat_field=40000.0)
     xg, st = plan.solve(to_dev(counts.view(np.int16)))
-    xr, tr = P.scg(y64, P.shift_add(y64), 20)
+    xr, tr = P.scg(y64, P.shift_add(y64), iters)
+    _check_decisions(plan.trace(), tr)
     assert rel_l2(xg.cpu().numpy(), xr) <= RTOL_X
     assert st["J_final"] == pytest.approx(P.objective(xr, y64), rel=RTOL_J)
 
