@@ -214,7 +214,7 @@ struct PassAcc {
 };
 
 // per-problem constants staged in shared memory at CTA start
-enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_FMAG = 30, C_N = 32 };
+enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_FMAG = 30, C_IEPS2 = 31, C_N = 32 };
 
 // ---------------------------------------------------------------------------------------
 // Body of the fused pass on one tile.  BORDER: the tile's halo reaches outside the image, so
@@ -225,8 +225,8 @@ enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_
 // pair evaluated from both ends instead of staged in shared memory); its items are split over
 // I2 and I3, one per thread on the first threads, with the light data-term items of the same
 // interval spread over the other threads.
-//   I1 A: p, x'                        I2 BTV (first half) + B1 (forward horizontal blur)
-//   I3 BTV (second half) + B2          I4 C1 (adjoint horizontal blur)
+//   I1 A: p, x'                        I2 BTV (part) + B1 (forward horizontal blur)
+//   I3 BTV (the rest) + B2             I4 C1 (adjoint horizontal blur)
 //   I5 C2 + r'                         I6 horizontal blurs of r' and p
 //   I7 curvature forms (owned)
 template <int TH, int TW, int NT, bool BORDER, bool RPB, typename Hook>
@@ -256,10 +256,13 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
 
     constexpr int N_A = XH * XW / 4, N_B1 = XH * EW / 4, N_B2 = EH * EW / 4, N_C1 = EH * GW / 4;
     constexpr int N_C2 = GH * GW / 4, N_HP = CH * CW / 4, N_HR = CH * CW / 4, N_E = TH * TW / 4;
-    constexpr int N_BTV = GH * GW / 4;                       // BTV items on the G grid
-    constexpr int N_BTV1 = N_BTV / 2, N_BTV2 = N_BTV - N_BTV1;
-    static_assert(N_BTV2 < NT, "one BTV item per thread and interval");
-    float2 jb2 = make_float2(0.f, 0.f);
+    // BTV items on the G grid, one per thread, over I2 and I3 on whole warps (a warp that took
+    // both a BTV item and light items would run the two one after the other): I3 takes whole
+    // warps' worth, I2 the rest, its last BTV warp possibly partial with its other lanes idle
+    constexpr int N_BTV = GH * GW / 4;
+    constexpr int N_BTV3 = (N_BTV / 2) / 32 * 32, N_BTV2 = N_BTV - N_BTV3;
+    constexpr int T_BTV2 = (N_BTV2 + 31) / 32 * 32;          // threads given to BTV in I2
+    static_assert(T_BTV2 < NT - 32 && N_BTV3 < NT - 32, "light items keep at least one warp");
 
     // ---------------- item bodies
     // A: p = r + beta p_old, x' = x + alpha p on the X box; owned pixels go to HBM
@@ -395,7 +398,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     };
     // BTV gradient (without lambda) of the prior at x' on the G grid (origin (-2, -2)):
     // g(q) = sum_d gamma_d [psi'(x_q - x_{q+d}) - psi'(x_{q-d} - x_q)] over pairs inside the
-    // image; the prior's value gamma_d psi(x_q - x_{q+d}) + eps is summed over owned q.
+    // image (the prior's value is summed with the curvature forms, over owned q only)
     auto item_btv = [&](int it) {
         // items of the first WA columns of each row come first, so that 8 consecutive threads
         // (one shared-memory phase of 16-byte loads) stay in one row; the remaining columns
@@ -417,38 +420,30 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         float c[8];
         ld8(xrow, c);                                        // c[2 + j] = x'(q_j)
         const float2 cq[2] = {make_float2(c[2], c[3]), make_float2(c[4], c[5])};
-        const bool own_row = (n - 2) >= 0 && (n - 2) < TH;
+        // forward and backward terms in separate accumulators (two independent chains each)
         float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        // forward pairs (q, q + d), d = (dy, dx), given the row of q + d: gradient and value
+        float2 acb[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        // forward pairs (q, q + d), d = (dy, dx), given the row of q + d
         auto fwd_terms = [&](const float *fr, int dy, int dx) {
             const float2 gam = bc2(cs[C_GAM + dy * 3 + dx]);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = 2 * h;
                 const float2 t = f2sub(cq[h], make_float2(fr[2 + j + dx], fr[3 + j + dx]));
-                const float2 sq = f2fma(t, t, bc2(eps2));
-                const float2 rs = f2rsqrt(sq);
+                const float2 rs = f2rsqrt(f2fma(t, t, bc2(eps2)));
                 float2 ps = f2mul(t, rs);
-                float2 sr = f2mul(sq, rs);
                 if (BORDER) {
                     const int x = qx + j;
                     const bool f0 = qy >= 0 && qy + dy < H && x >= 0 && x + dx < W;
                     const bool f1 = qy >= 0 && qy + dy < H && x + 1 >= 0 && x + 1 + dx < W;
                     ps.x = f0 ? ps.x : 0.f; ps.y = f1 ? ps.y : 0.f;
-                    sr.x = f0 ? sr.x : 0.f; sr.y = f1 ? sr.y : 0.f;
                 }
                 acc[h] = f2fma(gam, ps, acc[h]);
-                if (own_row) {
-                    const int oc = g - 2 + j;                   // tile column of q_j
-                    sr.x = (oc >= 0 && oc < TW) ? sr.x : 0.f;
-                    sr.y = (oc + 1 >= 0 && oc + 1 < TW) ? sr.y : 0.f;
-                    jb2 = f2fma(gam, sr, jb2);
-                }
             }
         };
         // backward pairs (q - d, q) given the row of q - d
         auto bwd_terms = [&](const float *br, int dy, int dx) {
-            const float2 ngam = bc2(-cs[C_GAM + dy * 3 + dx]);
+            const float2 gam = bc2(cs[C_GAM + dy * 3 + dx]);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = 2 * h;
@@ -461,7 +456,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
                     const bool b1 = qy < H && qy - dy >= 0 && x + 1 < W && x + 1 - dx >= 0;
                     ps.x = b0 ? ps.x : 0.f; ps.y = b1 ? ps.y : 0.f;
                 }
-                acc[h] = f2fma(ngam, ps, acc[h]);
+                acb[h] = f2fma(gam, ps, acb[h]);
             }
         };
         fwd_terms(c, 0, 1);
@@ -480,7 +475,8 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
             bwd_terms(rowv, dy, 1);
             bwd_terms(rowv, dy, 2);
         }
-        st4(GB + n * GW + g, make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y));
+        const float2 g0 = f2sub(acc[0], acb[0]), g1 = f2sub(acc[1], acb[1]);
+        st4(GB + n * GW + g, make_float4(g0.x, g0.y, g1.x, g1.y));
     };
     // C2 + r': adjoint vertical blur 2 B^T E, then r' = -(2 B^T E + lambda g_BTV) in place of
     // the BTV gradient; zero outside the image; owned pixels go to HBM with their sums
@@ -602,7 +598,9 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
             A.dj += d2.x + d2.y;
         }
         // prior part: lambda sum_d gamma_d psi''(t_d) (dv_d)(dw_d) over valid pairs, with
-        // psi''(t) = eps^2 / (t^2 + eps^2)^(3/2); lambda eps^2 gamma_d is folded into cw
+        // psi''(t) = eps^2 / (t^2 + eps^2)^(3/2) (eps^2 gamma_d is folded into cw, lambda applied
+        // to the sums); and the prior's value sum_d gamma_d psi(t_d), psi(t) = sqrt(t^2 + eps^2),
+        // over the forward pairs of owned q, as (cw / sqrt(t^2 + eps^2)) (t^2 + eps^2) / eps^2
         float2 xq[2], pq[2], rq[2];
         {
             const float4 a = ld4(XB + (n + 6) * XW + o + 8);
@@ -613,7 +611,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
             pq[0] = make_float2(b.x, b.y); pq[1] = make_float2(b.z, b.w);
             rq[0] = make_float2(tmp[2], tmp[3]); rq[1] = make_float2(tmp[4], tmp[5]);
         }
-        float2 ca = make_float2(0.f, 0.f), cb = ca, cc = ca;
+        float2 ca = make_float2(0.f, 0.f), cb = ca, cc = ca, cv = ca;
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy) {
             float xr[8], rrow[8], prow[8];
@@ -628,7 +626,8 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
                 for (int h = 0; h < 2; ++h) {
                     const int j = 2 * h;
                     const float2 t = f2sub(xq[h], make_float2(xr[j + dx], xr[j + 1 + dx]));
-                    const float2 rs = f2rsqrt(f2fma(t, t, bc2(eps2)));
+                    const float2 sq = f2fma(t, t, bc2(eps2));
+                    const float2 rs = f2rsqrt(sq);
                     const float2 u = f2mul(rs, f2sub(rq[h], make_float2(rrow[j + 2 + dx], rrow[j + 3 + dx])));
                     const float2 v = f2mul(rs, f2sub(pq[h], make_float2(prow[j + dx], prow[j + 1 + dx])));
                     float2 g = f2mul(cw, rs);
@@ -641,37 +640,40 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
                     ca = f2fma(wu, u, ca);
                     cb = f2fma(wu, v, cb);
                     cc = f2fma(f2mul(g, v), v, cc);
+                    cv = f2fma(g, sq, cv);
                 }
             }
         }
-        A.a += ca.x + ca.y;
-        A.b += cb.x + cb.y;
-        A.c += cc.x + cc.y;
+        A.a = fmaf(lambda, ca.x + ca.y, A.a);
+        A.b = fmaf(lambda, cb.x + cb.y, A.b);
+        A.c = fmaf(lambda, cc.x + cc.y, A.c);
+        A.jb = fmaf(cs[C_IEPS2], cv.x + cv.y, A.jb);
     };
 
     // ---------------- the schedule
     // I1
     for (int it = tid; it < N_A; it += NT) item_A(it);
     __syncthreads();
-    // I2: BTV items [0, N_BTV1) on the first threads, B1 on the others
-    if (tid < N_BTV1) item_btv(tid);
-    else
-        for (int it = tid - N_BTV1; it < N_B1; it += NT - N_BTV1) item_B1(it);
+    // I2: BTV items [0, N_BTV2) on the first warps, B1 on the others
+    if (tid < T_BTV2) {
+        if (tid < N_BTV2) item_btv(tid);
+    } else {
+        for (int it = tid - T_BTV2; it < N_B1; it += NT - T_BTV2) item_B1(it);
+    }
     hook(2);
     __syncthreads();
     // the Y box: a wait that runs out is reported to the caller (the tile's results are void)
     const bool y_late = !mbar_wait_bounded(ybar, yphase, TMA_WAIT_TRIES);
-    // I3: BTV items [N_BTV1, N_BTV) on the first threads, B2 on the others
-    if (tid < N_BTV2) item_btv(N_BTV1 + tid);
+    // I3: BTV items [N_BTV2, N_BTV) on the first warps, B2 on the others
+    if (tid < N_BTV3) item_btv(N_BTV2 + tid);
     else
-        for (int it = tid - N_BTV2; it < N_B2; it += NT - N_BTV2) item_B2(it);
+        for (int it = tid - N_BTV3; it < N_B2; it += NT - N_BTV3) item_B2(it);
     __syncthreads();
     // I4: adjoint horizontal blur
     for (int it = tid; it < N_C1; it += NT) item_C1(it);
     __syncthreads();
     // I5: adjoint vertical blur and r'
     for (int it = tid; it < N_C2; it += NT) item_C2r(it);
-    A.jb += jb2.x + jb2.y;
     __syncthreads();
     // I6: horizontal blurs of r' and p (HS is free once C2 has read it)
     for (int it = tid; it < N_HR + N_HP; it += NT) {
@@ -901,11 +903,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
             if (tid < 5) { cs[C_HX + tid] = P.hx[tid]; cs[C_HY + tid] = P.hy[tid]; }
             if (tid < 9) {
                 cs[C_GAM + tid] = P.gamma[tid];
-                cs[C_CW + tid] = P.lambda * P.eps2 * P.gamma[tid];
+                cs[C_CW + tid] = P.eps2 * P.gamma[tid];
             }
             if (tid == 0) {
                 cs[C_LAMBDA] = P.lambda;
                 cs[C_EPS2] = P.eps2;
+                cs[C_IEPS2] = 1.f / P.eps2;
                 cs[C_FMAG] = __uint_as_float(P.f > 1 ? (unsigned)((0x100000000ull + P.f - 1) / P.f) : 0u);
             }
         }
