@@ -204,14 +204,15 @@ static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double bet
 }
 
 // The tile list of problem `pi` (border tiles first: they cost more, so a pass ends on
-// interior tiles).
+// interior tiles).  An entry is (problem, ty << 16 | tx); an HR side of at most 2^20 pixels
+// keeps both tile coordinates below 2^16.
 static void append_tiles(const DevProblem &hp, int pi, std::vector<int2> &tiles) {
     const int tx = hp.tiles_x, TH = hp.tile_h, TW = hp.tile_w;
     for (int pass = 0; pass < 2; ++pass)
         for (int t = 0; t < hp.n_tiles; ++t) {
-            const int y0 = (t / tx) * TH, x0 = (t % tx) * TW;
+            const int ty = t / tx, tc = t % tx, y0 = ty * TH, x0 = tc * TW;
             const bool border = y0 - 6 < 0 || x0 - 8 < 0 || y0 + TH + 6 > hp.H || x0 + TW + 8 > hp.W;
-            if (border == (pass == 0)) tiles.push_back(make_int2(pi, t));
+            if (border == (pass == 0)) tiles.push_back(make_int2(pi, (int)(((unsigned)ty << 16) | (unsigned)tc)));
         }
 }
 
@@ -359,7 +360,7 @@ misr_status misr_host::check_desc(const misr_desc &d) {
 
 extern "C" {
 
-const char *misr_version(void) { return "misr-b300 0.2 (sm_103a, TMA-fed fused SCG pass 32x64)"; }
+const char *misr_version(void) { return "misr-b300 0.3 (sm_103a, persistent TMA-fed fused SCG pass; tiles 32x64, 32x32, 16x64)"; }
 
 const char *misr_last_error(void) { return g_err.c_str(); }
 

@@ -674,6 +674,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     __syncthreads();
     // I5: adjoint vertical blur and r'
     for (int it = tid; it < N_C2; it += NT) item_C2r(it);
+    hook(5);
     __syncthreads();
     // I6: horizontal blurs of r' and p (HS is free once C2 has read it)
     for (int it = tid; it < N_HR + N_HP; it += NT) {
@@ -769,30 +770,34 @@ struct TileInfo {
     const DevProblem *P;
     float *Xn, *Rn, *Pn;
     float alpha, beta;
-    int y0, x0, t, cur, pcur, end, restage;
+    int cur, pcur, prob;                 // the problem's fields (rewritten when it changes)
+    int y0, x0, t, end, restage;         // the tile's
 };
-// The scheduling thread's own state: the CTA's next claimed tile and the fields of the problem
-// it last prepared a tile of.
+// The scheduling thread's own state: the CTA's next claimed tile, its list entry (copied
+// ahead by cp.async), and the fields of the problem it last prepared a tile of.
 struct SchedState {
-    int next, cached, done;
+    int2 wt_pre;
+    int next, cached, done, tiles_x;
     TileInfo cache;
 };
 
 // Prepare list entry k (or the end of the list) as the CTA's tile in `ti`: skip problems that
-// are done, take the problem's fields from the cache (loaded when the problem changes), and
-// warm L2 with the tile's boxes (it is loaded one tile later).
+// are done, take the problem's fields from the cache (loaded when the problem changes, copied
+// when `ti` holds another problem's), and warm L2 with the tile's boxes (it is loaded one tile
+// later).  k_pre: entry k is already in sc.wt_pre.  A list entry is (problem, ty << 16 | tx).
 template <int TH, int TW>
-__device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k, const DevProblem *__restrict__ probs,
-                                             const int2 *__restrict__ tiles, int n_tiles, unsigned *work, int mode,
-                                             double probe_alpha, double probe_beta) {
+__device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k, bool k_pre,
+                                             const DevProblem *__restrict__ probs, const int2 *__restrict__ tiles,
+                                             int n_tiles, unsigned *work, int mode, double probe_alpha,
+                                             double probe_beta) {
     int2 wt = make_int2(0, 0);
     int restage = 0;
-    for (;; k = (int)atomicAdd(&work[0], 1u) + (int)gridDim.x) {
+    for (;; k = (int)atomicAdd(&work[0], 1u) + (int)gridDim.x, k_pre = false) {
         if (k >= n_tiles) {
             ti.end = 1;
             return;
         }
-        wt = tiles[k];
+        wt = k_pre ? sc.wt_pre : tiles[k];
         if (wt.x != sc.cached) {
             const DevProblem *P = &probs[wt.x];
             const ScgState *st = P->st;
@@ -800,6 +805,7 @@ __device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k
             sc.cached = wt.x;
             restage = 1;
             c.P = P;
+            c.prob = wt.x;
             c.cur = ld_cg(&st->cur);
             c.pcur = ld_cg(&st->pcur);
             c.alpha = mode == MODE_PROBE ? (float)probe_alpha : __ldcg(&st->alpha_f);
@@ -807,21 +813,22 @@ __device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k
             c.Xn = P->X[c.cur ^ 1];
             c.Rn = P->Rv[c.cur ^ 1];
             c.Pn = P->Pv[c.pcur ^ 1];
+            sc.tiles_x = P->tiles_x;
             sc.done = ld_cg(&st->done);
         }
         if (!sc.done) break;
     }
-    ti = sc.cache;
-    const DevProblem *P = ti.P;
-    ti.t = wt.y;
-    ti.y0 = (wt.y / P->tiles_x) * TH;
-    ti.x0 = (wt.y % P->tiles_x) * TW;
+    const TileInfo &c = sc.cache;
+    if (ti.prob != c.prob) {
+        ti.P = c.P; ti.Xn = c.Xn; ti.Rn = c.Rn; ti.Pn = c.Pn;
+        ti.alpha = c.alpha; ti.beta = c.beta; ti.cur = c.cur; ti.pcur = c.pcur; ti.prob = c.prob;
+    }
+    const unsigned ty = (unsigned)wt.y >> 16, tx = (unsigned)wt.y & 0xffffu;
+    ti.t = (int)(ty * (unsigned)sc.tiles_x + tx);
+    ti.y0 = (int)ty * TH;
+    ti.x0 = (int)tx * TW;
     ti.end = 0;
     ti.restage = restage;
-    tma_prefetch_l2_2d(&P->tmX[ti.cur], ti.x0 - 8, ti.y0 - 6);
-    tma_prefetch_l2_2d(&P->tmP[ti.pcur], ti.x0 - 8, ti.y0 - 6);
-    tma_prefetch_l2_2d(&P->tmR[ti.cur], ti.x0 - 8, ti.y0 - 6);
-    tma_prefetch_l2_2d(&P->tmY, ti.x0 - 4, ti.y0 - 4);
 }
 
 // Issue the TMA loads of a prepared tile (x, p_old, r boxes on bar[0]; the Y box on bar[1]).
@@ -887,7 +894,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
         fence_barrier_init();
         sched.cached = -1;
         sched.done = 0;
-        prepare_tile<TH, TW>(tinfo[0], sched, blockIdx.x, probs, tiles, n_tiles, work, mode, probe_alpha, probe_beta);
+        tinfo[0].prob = tinfo[1].prob = -1;
+        prepare_tile<TH, TW>(tinfo[0], sched, blockIdx.x, false, probs, tiles, n_tiles, work, mode, probe_alpha, probe_beta);
         sched.next = (int)atomicAdd(&work[0], 1u) + (int)gridDim.x;
     }
     __syncthreads();
@@ -912,6 +920,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
                 cs[C_FMAG] = __uint_as_float(P.f > 1 ? (unsigned)((0x100000000ull + P.f - 1) / P.f) : 0u);
             }
         }
+        if (tid == SCHED_TID && sched.next < n_tiles) cp_async_8(&sched.wt_pre, tiles + sched.next);
         const uint32_t phase = n & 1;
         const bool landed = mbar_wait_bounded(&bar[0], phase, TMA_WAIT_TRIES);
         if (__syncthreads_or(!landed)) {
@@ -921,6 +930,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
                 flag_timeout(P);
                 mbar_wait_bounded(&bar[0], phase, TMA_WAIT_TRIES);
                 mbar_wait_bounded(&bar[1], phase, TMA_WAIT_TRIES);
+                cp_async_wait_all();
             }
             break;
         }
@@ -929,9 +939,21 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
         auto hook = [&](int at) {
             if (tid != SCHED_TID) return;
             if (at == 2) {
-                prepare_tile<TH, TW>(tinfo[slot ^ 1], sched, sched.next, probs, tiles, n_tiles, work, mode,
-                                     probe_alpha, probe_beta);
+                // the claim first: its round trip overlaps the preparation
                 pending = atomicAdd(&work[0], 1u);
+                cp_async_wait_all();
+                prepare_tile<TH, TW>(tinfo[slot ^ 1], sched, sched.next, true, probs, tiles, n_tiles, work, mode,
+                                     probe_alpha, probe_beta);
+            }
+            if (at == 5) {   // warm L2 with the next tile's boxes
+                const TileInfo &nx = tinfo[slot ^ 1];
+                if (!nx.end) {
+                    const DevProblem *Q = nx.P;
+                    tma_prefetch_l2_2d(&Q->tmX[nx.cur], nx.x0 - 8, nx.y0 - 6);
+                    tma_prefetch_l2_2d(&Q->tmP[nx.pcur], nx.x0 - 8, nx.y0 - 6);
+                    tma_prefetch_l2_2d(&Q->tmR[nx.cur], nx.x0 - 8, nx.y0 - 6);
+                    tma_prefetch_l2_2d(&Q->tmY, nx.x0 - 4, nx.y0 - 4);
+                }
             }
         };
 
