@@ -159,6 +159,23 @@ misr_status misr_solve(misr_plan_t plan, const void *y_dev, float *x_dev, misr_s
  * plan allocates the device copies on first use. */
 misr_status misr_solve_host(misr_plan_t plan, const void *y_host, float *x_host, misr_stats *stats);
 
+/* A stream of projections from host memory through one plan: solves projection k while the
+ * frames of projection k+1 go to the device and the image of projection k-1 comes back, on a
+ * copy stream beside the plan's stream, through two device buffer pairs the plan allocates on
+ * first use and keeps.  The projections are solved one after another (same results as n calls
+ * of misr_solve_host); only the copies overlap.  The CT setting of Sec. 3.2 reconstructs one
+ * projection per rotation angle as they are acquired.
+ * y_host[k]: frames of projection k (K x lr_h x lr_w, in_dtype, dense); x_host[k]: its HR image
+ * (H x W float32, dense; also read as the start point under MISR_X0_GIVEN).  Page-locked host
+ * buffers let the copies overlap the solves; pageable ones work but serialise.  The host
+ * buffers must stay valid and unchanged until the call returns; it returns when every image
+ * is in host memory.  stats: NULL or n records (projection k's in stats[k]).
+ * Errors: MISR_EINVAL (NULL plan or arrays or entries, n < 0), MISR_ENOMEM, MISR_ECUDA,
+ * MISR_ETIMEOUT (a tile load timed out in at least one projection: its record carries the
+ * status, the others are complete). */
+misr_status misr_solve_host_many(misr_plan_t plan, int32_t n, const void *const *y_host, float *const *x_host,
+                                 misr_stats *stats);
+
 /* Copy the per-iteration trace of the plan's last completed solve (MISR_TRACE_COLS doubles
  * per iteration) into out (host, max_rows rows); *rows receives the number written.
  * Synchronises with the plan's last solve. */

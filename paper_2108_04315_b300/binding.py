@@ -78,6 +78,7 @@ def lib():
         L.misr_pass_probe.argtypes = [VP, VP, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, DP, VP]
         L.misr_solve.argtypes = [VP, VP, VP, VP, C.POINTER(misr_stats)]
         L.misr_solve_host.argtypes = [VP, VP, VP, C.POINTER(misr_stats)]
+        L.misr_solve_host_many.argtypes = [VP, C.c_int32, C.POINTER(VP), C.POINTER(VP), C.POINTER(misr_stats)]
         L.misr_get_trace.argtypes = [VP, DP, C.c_int32, C.POINTER(C.c_int32)]
         L.misr_batch_create.argtypes = [C.c_int32, C.POINTER(VP), C.POINTER(VP)]
         L.misr_batch_destroy.argtypes = [VP]
@@ -90,7 +91,8 @@ def lib():
         L.misr_server_wait.argtypes = [VP, C.c_uint64, C.c_double]
         L.misr_server_counters.argtypes = [VP, C.POINTER(C.c_int64)]
         for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_forward",
-                     "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_get_trace",
+                     "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_solve_host_many",
+                     "misr_get_trace",
                      "misr_batch_create", "misr_batch_destroy", "misr_batch_solve", "misr_server_create",
                      "misr_server_destroy", "misr_submit", "misr_poll", "misr_server_wait", "misr_server_counters",
                      "misr_autotune"):
@@ -159,6 +161,18 @@ def misr_solve_host(plan: int, y_host: int, x_host: int):
     st = misr_stats()
     _check(lib().misr_solve_host(VP(plan), VP(y_host), VP(x_host), C.byref(st)), "misr_solve_host")
     return _stats_dict(st)
+
+
+def misr_solve_host_many(plan: int, y_hosts, x_hosts, want_stats: bool = True):
+    """Solve len(y_hosts) projections from host buffers (addresses) with overlapped copies."""
+    n = len(y_hosts)
+    if len(x_hosts) != n:
+        raise ValueError("y_hosts and x_hosts differ in length")
+    ya = (VP * max(1, n))(*[VP(a) for a in y_hosts])
+    xa = (VP * max(1, n))(*[VP(a) for a in x_hosts])
+    st = (misr_stats * max(1, n))()
+    _check(lib().misr_solve_host_many(VP(plan), n, ya, xa, st if want_stats else None), "misr_solve_host_many")
+    return [_stats_dict(st[k]) for k in range(n)] if want_stats else None
 
 
 def misr_get_trace(plan: int, max_rows: int):
@@ -332,6 +346,15 @@ class Plan:
     def solve_host(self, y_host: np.ndarray, x_host: np.ndarray):
         assert y_host.flags.c_contiguous and x_host.flags.c_contiguous and x_host.dtype == np.float32
         return misr_solve_host(self.handle, y_host.ctypes.data, x_host.ctypes.data)
+
+    def solve_host_many(self, y_hosts, x_hosts, stats=True):
+        """Projections y_hosts[k] -> x_hosts[k] (C-contiguous host arrays), the copies of one
+        overlapped with the solve of another (page-locked arrays overlap; others serialise)."""
+        for a in list(y_hosts) + list(x_hosts):
+            assert a.flags.c_contiguous
+        assert all(x.dtype == np.float32 for x in x_hosts)
+        return misr_solve_host_many(self.handle, [a.ctypes.data for a in y_hosts], [a.ctypes.data for a in x_hosts],
+                                    stats)
 
     def trace(self):
         return misr_get_trace(self.handle, self.iters)

@@ -498,6 +498,15 @@ misr_status misr_plan_destroy(misr_plan_t p) {
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->io_y) cudaFree(p->io_y);
     if (p->io_x) cudaFree(p->io_x);
+    for (int b = 0; b < 2; ++b) {
+        if (p->pio_y[b]) cudaFree(p->pio_y[b]);
+        if (p->pio_x[b]) cudaFree(p->pio_x[b]);
+        if (p->ev_in[b]) cudaEventDestroy(p->ev_in[b]);
+        if (p->ev_done[b]) cudaEventDestroy(p->ev_done[b]);
+        if (p->ev_out[b]) cudaEventDestroy(p->ev_out[b]);
+    }
+    if (p->cpy) cudaStreamDestroy(p->cpy);
+    if (p->st_ring) cudaFree(p->st_ring);
     if (p->ws) cudaFree(p->ws);
     delete p;
     return MISR_OK;
@@ -591,8 +600,7 @@ static misr_status ensure_graph(misr_plan_t p) {
     return MISR_OK;
 }
 
-static misr_status fill_stats(misr_plan_t p, misr_stats *st) {
-    const ScgState &h = *p->st_host;
+static misr_status fill_stats_from(const ScgState &h, misr_stats *st) {
     if (h.status == DEV_TMA_TIMEOUT) {
         st->status = MISR_ETIMEOUT;
         return fail(MISR_ETIMEOUT, "a tile load of the fused pass did not complete in time; the solve stopped");
@@ -606,6 +614,7 @@ static misr_status fill_stats(misr_plan_t p, misr_stats *st) {
     st->lambda_scg = h.lam;
     return MISR_OK;
 }
+static misr_status fill_stats(misr_plan_t p, misr_stats *st) { return fill_stats_from(*p->st_host, st); }
 
 misr_status misr_solve(misr_plan_t p, const void *y_dev, float *x_dev, misr_stream_t stream, misr_stats *stats) {
     if (!p || !y_dev || !x_dev) return fail(MISR_EINVAL, "NULL argument");
@@ -655,6 +664,90 @@ misr_status misr_solve_host(misr_plan_t p, const void *y_host, float *x_host, mi
     CK(cudaStreamSynchronize(s));
     if (stats) return fill_stats(p, stats);
     return MISR_OK;
+}
+
+// The buffers, stream and events of misr_solve_host_many (kept with the plan).
+static misr_status ensure_stream_io(misr_plan_t p, size_t ybytes, size_t xbytes, int n_states) {
+    for (int b = 0; b < 2; ++b) {
+        if (!p->pio_y[b] && cudaMalloc(&p->pio_y[b], ybytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MISR_ENOMEM, "cudaMalloc of the frame buffers of misr_solve_host_many");
+        }
+        if (!p->pio_x[b] && cudaMalloc((void **)&p->pio_x[b], xbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MISR_ENOMEM, "cudaMalloc of the image buffers of misr_solve_host_many");
+        }
+        if (!p->ev_in[b]) CK(cudaEventCreateWithFlags(&p->ev_in[b], cudaEventDisableTiming));
+        if (!p->ev_done[b]) CK(cudaEventCreateWithFlags(&p->ev_done[b], cudaEventDisableTiming));
+        if (!p->ev_out[b]) CK(cudaEventCreateWithFlags(&p->ev_out[b], cudaEventDisableTiming));
+    }
+    if (!p->cpy) CK(cudaStreamCreateWithFlags(&p->cpy, cudaStreamNonBlocking));
+    if (n_states > p->st_ring_cap) {
+        if (p->st_ring) { cudaFree(p->st_ring); p->st_ring = nullptr; p->st_ring_cap = 0; }
+        if (cudaMalloc((void **)&p->st_ring, sizeof(ScgState) * (size_t)n_states) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MISR_ENOMEM, "cudaMalloc of the state records of misr_solve_host_many");
+        }
+        p->st_ring_cap = n_states;
+    }
+    return MISR_OK;
+}
+
+misr_status misr_solve_host_many(misr_plan_t p, int32_t n, const void *const *y_host, float *const *x_host,
+                                 misr_stats *stats) {
+    if (!p || n < 0 || (n > 0 && (!y_host || !x_host))) return fail(MISR_EINVAL, "NULL plan or arrays, or n < 0");
+    for (int32_t k = 0; k < n; ++k)
+        if (!y_host[k] || !x_host[k]) return fail(MISR_EINVAL, "projection %d: NULL host buffer", (int)k);
+    if (n == 0) return MISR_OK;
+    DeviceGuard g(p->device);
+    misr_status r = ensure_graph(p);   // captured on the plan's stream before work is queued on it
+    if (r != MISR_OK) return r;
+    const size_t ybytes = p->m_total * (p->d.in_dtype == MISR_U16 ? 2 : 4);
+    const size_t xbytes = p->n * sizeof(float);
+    r = ensure_stream_io(p, ybytes, xbytes, stats ? n : 0);
+    if (r != MISR_OK) return r;
+    cudaStream_t s = p->cap, c = p->cpy;
+    const bool x_in = p->d.x0_mode == MISR_X0_GIVEN;
+    // projection k uses buffer pair k & 1.  Copy stream: in(0), then for each k: in(k+1) once
+    // solve k-1 has read pair (k+1) & 1, out(k) once solve k is done.  Plan stream: solve k
+    // once in(k) has landed and out(k-2) has left pair k & 1.
+    auto copy_in = [&](int32_t k) -> misr_status {
+        const int b = k & 1;
+        if (k >= 2) CK(cudaStreamWaitEvent(c, p->ev_done[b], 0));
+        CK(cudaMemcpyAsync(p->pio_y[b], y_host[k], ybytes, cudaMemcpyHostToDevice, c));
+        if (x_in) CK(cudaMemcpyAsync(p->pio_x[b], x_host[k], xbytes, cudaMemcpyHostToDevice, c));
+        CK(cudaEventRecord(p->ev_in[b], c));
+        return MISR_OK;
+    };
+    r = copy_in(0);
+    for (int32_t k = 0; k < n && r == MISR_OK; ++k) {
+        const int b = k & 1;
+        CK(cudaStreamWaitEvent(s, p->ev_in[b], 0));
+        if (k >= 2) CK(cudaStreamWaitEvent(s, p->ev_out[b], 0));
+        r = misr_solve(p, p->pio_y[b], p->pio_x[b], (misr_stream_t)s, nullptr);
+        if (r != MISR_OK) break;
+        if (stats) CK(cudaMemcpyAsync(p->st_ring + k, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToDevice, s));
+        CK(cudaEventRecord(p->ev_done[b], s));
+        if (k + 1 < n) r = copy_in(k + 1);
+        if (r != MISR_OK) break;
+        CK(cudaStreamWaitEvent(c, p->ev_done[b], 0));
+        CK(cudaMemcpyAsync(x_host[k], p->pio_x[b], xbytes, cudaMemcpyDeviceToHost, c));
+        CK(cudaEventRecord(p->ev_out[b], c));
+    }
+    const cudaError_t e1 = cudaStreamSynchronize(s), e2 = cudaStreamSynchronize(c);
+    if (r != MISR_OK) return r;
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return fail(MISR_ECUDA, "misr_solve_host_many: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    if (!stats) return MISR_OK;
+    std::vector<ScgState> h((size_t)n);
+    CK(cudaMemcpy(h.data(), p->st_ring, sizeof(ScgState) * (size_t)n, cudaMemcpyDeviceToHost));
+    *p->st_host = h[(size_t)n - 1];
+    misr_status worst = MISR_OK;
+    for (int32_t k = 0; k < n; ++k) {
+        const misr_status sk = fill_stats_from(h[(size_t)k], &stats[k]);
+        if (sk != MISR_OK) worst = sk;
+    }
+    return worst;
 }
 
 misr_status misr_get_trace(misr_plan_t p, double *out, int32_t max_rows, int32_t *rows) {

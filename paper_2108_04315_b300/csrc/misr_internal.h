@@ -92,4 +92,12 @@ struct misr_plan_s {
     misr::ScgState *st_host = nullptr;  // page-locked copy of the state
     void *io_y = nullptr;               // device buffers of misr_solve_host
     float *io_x = nullptr;
+    // misr_solve_host_many: two device buffer pairs, a copy stream and its events, and the
+    // device copies of each projection's final state
+    void *pio_y[2] = {nullptr, nullptr};
+    float *pio_x[2] = {nullptr, nullptr};
+    cudaStream_t cpy = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    misr::ScgState *st_ring = nullptr;
+    int st_ring_cap = 0;
 };

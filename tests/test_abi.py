@@ -30,7 +30,8 @@ def L():
 
 def test_header_declares_entry_points():
     names = declared_functions()
-    for want in ("misr_plan_create", "misr_plan_destroy", "misr_solve", "misr_solve_host", "misr_forward",
+    for want in ("misr_plan_create", "misr_plan_destroy", "misr_solve", "misr_solve_host", "misr_solve_host_many",
+                 "misr_forward",
                  "misr_gradient", "misr_pass_probe", "misr_get_trace", "misr_last_error", "misr_version"):
         assert want in names
 
@@ -84,4 +85,5 @@ def test_null_arguments_rejected(L):
     from paper_2108_04315_b300 import binding
     assert L.misr_plan_create(None, None) == binding.MISR_EINVAL
     assert L.misr_solve(None, None, None, None, None) == binding.MISR_EINVAL
+    assert L.misr_solve_host_many(None, 1, None, None, None) == binding.MISR_EINVAL
     assert L.misr_plan_destroy(None) == binding.MISR_OK
