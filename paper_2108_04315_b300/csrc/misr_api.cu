@@ -421,8 +421,8 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     const size_t rp_img = d.iterate_dtype == MISR_BF16 ? align_up(p->n_pitched * 2, 256) : img;
     size_t off = 0;
     const size_t o_img = off; off += 3 * img + 4 * rp_img;   // X[2], Y (float); R[2], P[2]
-    const size_t o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(double), 256);
-    const size_t o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(double), 256);
+    const size_t o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(float2), 256);
+    const size_t o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(float2), 256);
     const size_t o_gcnt = off; off += align_up((size_t)hp.n_groups * sizeof(unsigned int), 256);
     const size_t o_cnt = off; off += 256;
     const size_t o_work = off; off += 256;
@@ -446,8 +446,8 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     }
     hp.Y = (float *)(b + o_img + 2 * img);
     hp.rp_bf16 = d.iterate_dtype == MISR_BF16;
-    hp.partials = (double *)(b + o_part);
-    hp.gpartials = (double *)(b + o_gpart);
+    hp.partials = (float2 *)(b + o_part);
+    hp.gpartials = (float2 *)(b + o_gpart);
     hp.gcount = (unsigned int *)(b + o_gcnt);
     hp.counter = (unsigned int *)(b + o_cnt);
     p->work = (unsigned int *)(b + o_work);
@@ -787,8 +787,8 @@ constexpr int NOALLOC_MAX_TILES = ((NOALLOC_MAX_H + SHAPE_TH[DEFAULT_SHAPE] - 1)
 constexpr int NOALLOC_MAX_GROUPS = 128;
 constexpr size_t NA_O_IMG = 0;
 constexpr size_t NA_O_PART = NA_O_IMG + 7 * NOALLOC_IMG;
-constexpr size_t NA_O_GPART = NA_O_PART + na_align(size_t(NOALLOC_MAX_TILES) * NPART * sizeof(double), 256);
-constexpr size_t NA_O_GCNT = NA_O_GPART + na_align(size_t(NOALLOC_MAX_GROUPS) * NPART * sizeof(double), 256);
+constexpr size_t NA_O_GPART = NA_O_PART + na_align(size_t(NOALLOC_MAX_TILES) * NPART * sizeof(float2), 256);
+constexpr size_t NA_O_GCNT = NA_O_GPART + na_align(size_t(NOALLOC_MAX_GROUPS) * NPART * sizeof(float2), 256);
 constexpr size_t NA_O_CNT = NA_O_GCNT + na_align(size_t(NOALLOC_MAX_GROUPS) * sizeof(unsigned int), 256);
 constexpr size_t NA_O_WORK = NA_O_CNT + 256;
 constexpr size_t NA_O_ST = NA_O_WORK + 256;
@@ -875,8 +875,8 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
         hp.Pv[i] = reinterpret_cast<float *>(base + NA_O_IMG + (4 + i) * NOALLOC_IMG);
     }
     hp.Y = reinterpret_cast<float *>(base + NA_O_IMG + 6 * NOALLOC_IMG);
-    hp.partials = reinterpret_cast<double *>(base + NA_O_PART);
-    hp.gpartials = reinterpret_cast<double *>(base + NA_O_GPART);
+    hp.partials = reinterpret_cast<float2 *>(base + NA_O_PART);
+    hp.gpartials = reinterpret_cast<float2 *>(base + NA_O_GPART);
     hp.gcount = reinterpret_cast<unsigned int *>(base + NA_O_GCNT);
     hp.counter = reinterpret_cast<unsigned int *>(base + NA_O_CNT);
     hp.st = reinterpret_cast<ScgState *>(base + NA_O_ST);

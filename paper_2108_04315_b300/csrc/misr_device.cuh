@@ -687,31 +687,57 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     return y_late;
 }
 
-// Sum of `count` field-major records (`stride` apart) by one warp in a fixed order (lane l
-// sums elements l, l + 32, l + 64, ... in that order, then a fixed butterfly); every lane gets
-// the totals.  The loads of each chunk of 128 elements are issued together.
-__device__ __forceinline__ void warp_sum_fields(const double *src, size_t stride, int count, double *v) {
+// Double-float sum of two (hi, lo) pairs: two-sum of the high parts, the low parts added to
+// its error, then a fast two-sum that renormalises.  About 48 significant bits, in FP32
+// arithmetic (the FP64 pipe of this GPU is a small fraction of the FP32 one).
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x, bb = s - a.x;
+    const float e = ((a.x - (s - bb)) + (b.x - bb)) + (a.y + b.y);
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ float2 shfl_xor_f2(float2 v, int off) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
+}
+
+// Sum of `count` field-major records of NPART (hi, lo) fields (`stride` apart) by one warp in
+// a fixed order: lane l sums elements l, l + 32, l + 64, ... of every field in that order; then
+// a transposing butterfly over 16 field slots (the fields, then zeros): at offsets 16, 8, 4
+// and 2 each lane keeps half of its slots and adds its partner's half (lane bits 4, 3, 2, 1
+// choose which), and offset 1 finishes, so lanes 2s and 2s + 1 end with the total of field s.
+// The loads of each chunk of 128 records are issued together.
+__device__ __forceinline__ float2 warp_sum_fields(const float2 *src, size_t stride, int count) {
+    static_assert(NPART <= 16, "field slots");
     const int lane = threadIdx.x & 31;
+    float2 v[16];
 #pragma unroll
-    for (int j = 0; j < NPART; ++j) v[j] = 0.0;
+    for (int j = 0; j < 16; ++j) v[j] = make_float2(0.f, 0.f);
     for (int base = 0; base < count; base += 128) {
-        double t[NPART][4];
+        float2 t[NPART][4];
 #pragma unroll
         for (int j = 0; j < NPART; ++j)
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int i = base + lane + 32 * k;
-                t[j][k] = i < count ? ld_cg(src + (size_t)j * stride + i) : 0.0;
+                t[j][k] = i < count ? __ldcg(src + (size_t)j * stride + i) : make_float2(0.f, 0.f);
             }
 #pragma unroll
         for (int j = 0; j < NPART; ++j)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[j] += t[j][k];
+            for (int k = 0; k < 4; ++k) v[j] = df_add(v[j], t[j][k]);
     }
+    int m = 16;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
+    for (int off = 16; off >= 2; off >>= 1) {
+        const bool upper = lane & off;
+        m >>= 1;
 #pragma unroll
-        for (int j = 0; j < NPART; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+        for (int k = 0; k < m; ++k) {
+            const float2 keep = upper ? v[m + k] : v[k], send = upper ? v[k] : v[m + k];
+            v[k] = df_add(keep, shfl_xor_f2(send, off));
+        }
+    }
+    return df_add(v[0], shfl_xor_f2(v[0], 1));
 }
 
 // The reduction of a pass, one warp per (problem, group): sum the group's tile sums in tile
@@ -730,14 +756,9 @@ __global__ void __launch_bounds__(32) reduce_kernel(const DevProblem *__restrict
     if (ld_cg(&P.st->done)) return;
     const int g = gi.y;
     const int gsize = min(P.group, P.n_tiles - g * P.group);
-    double v[NPART];
-    warp_sum_fields(P.partials + (size_t)g * P.group, P.n_tiles, gsize, v);
-    if (lane < NPART) {
-        double mine = v[0];
-#pragma unroll
-        for (int j = 1; j < NPART; ++j) mine = lane == j ? v[j] : mine;
-        P.gpartials[(size_t)lane * P.n_groups + g] = mine;
-    }
+    const float2 v = warp_sum_fields(P.partials + (size_t)g * P.group, P.n_tiles, gsize);
+    const int slot = lane >> 1;
+    if ((lane & 1) == 0 && slot < NPART) P.gpartials[(size_t)slot * P.n_groups + g] = v;
     __syncwarp();
     unsigned old = 0;
     if (lane == 0) {
@@ -747,9 +768,15 @@ __global__ void __launch_bounds__(32) reduce_kernel(const DevProblem *__restrict
     old = __shfl_sync(0xffffffffu, old, 0);
     if (old != (unsigned)(P.n_groups - 1)) return;
     __threadfence();
-    warp_sum_fields(P.gpartials, P.n_groups, P.n_groups, v);
+    const float2 w = warp_sum_fields(P.gpartials, P.n_groups, P.n_groups);
+    double S[NPART];
+#pragma unroll
+    for (int j = 0; j < NPART; ++j) {
+        const float hi = __shfl_sync(0xffffffffu, w.x, 2 * j), lo = __shfl_sync(0xffffffffu, w.y, 2 * j);
+        S[j] = (double)hi + (double)lo;
+    }
     if (lane == 0) {
-        scg_tail(P, P.st, v, mode);
+        scg_tail(P, P.st, S, mode);
         *P.counter = 0u;
         __threadfence();
     }
@@ -1019,7 +1046,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
             }
             if (lane == 0) { red[warp][P_JB] = hi; red_lo[warp] = lo; }
         }
-        double *tile_sums = P.partials + ti.t;
+        float2 *tile_sums = P.partials + ti.t;
         const int n_tiles_p = P.n_tiles;
         // also: every thread is done with the tile buffers and the context
         if (__syncthreads_or(y_late)) {
@@ -1029,8 +1056,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
             }
             break;
         }
-        // the tile's sums (FP32 across warps in a fixed order, compensated for the prior's
-        // value); the reduction kernel that follows the pass sums the tiles
+        // the tile's sums as (hi, lo) pairs (FP32 across warps in a fixed order, compensated);
+        // the reduction kernel that follows the pass sums the tiles
         if (warp == 0 && lane < NPART) {
             float hi = 0.f, lo = 0.f;
 #pragma unroll
@@ -1040,7 +1067,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
                 lo += ((hi - (s - bb)) + (x - bb)) + (lane == P_JB ? red_lo[w] : 0.f);
                 hi = s;
             }
-            tile_sums[(size_t)lane * n_tiles_p] = lane == P_JB ? (double)hi + (double)lo : (double)hi;
+            tile_sums[(size_t)lane * n_tiles_p] = make_float2(hi, lo);
         }
     }
     // this CTA takes no more tiles: the reduction kernel may start launching

@@ -78,8 +78,8 @@ struct DevProblem {
     // Fixed-order reduction of a pass's sums: every tile writes its sums; whoever finishes the
     // last tile of a group of `group` tiles sums the group in tile order; whoever finishes the
     // last group sums the groups in order and runs the SCG tail.  Field-major arrays.
-    double *partials;                             // [NPART][n_tiles] tile sums
-    double *gpartials;                            // [NPART][n_groups] group sums
+    float2 *partials;                             // [NPART][n_tiles] tile sums (hi, lo)
+    float2 *gpartials;                            // [NPART][n_groups] group sums (hi, lo)
     unsigned int *gcount;                         // [n_groups] tiles of the group finished
     unsigned int *counter;                        // groups finished in the current pass
     int group, n_groups;                          // tiles per group, groups
