@@ -199,11 +199,14 @@ __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ int mod_f(int c, int f, unsigned m) {
     return m ? c - f * (int)__umulhi((unsigned)c, m) : 0;
 }
-__device__ __forceinline__ bool fwd_tap_ok(int c, int a, int f, unsigned m) { return c < 0 || (c - a) >= mod_f(c, f, m); }
+// As a bound on the tap offset (one c mod f per coordinate): the tap exists when
+// a <= fwd_lim(c) = c - (c mod f), and for every a when c < 0.
+__device__ __forceinline__ int fwd_lim(int c, int f, unsigned m) { return c < 0 ? 0x7fffffff : c - mod_f(c, f, m); }
 // Frame mask of the adjoint blur at output coordinate u for tap offset a: the sample read
 // sits at u + a; the tap exists when u >= ((u + a) mod f).
 __device__ __forceinline__ bool adj_tap_ok(int u, int a, int f, unsigned m) {
-    return (u + a) < 0 || u >= mod_f(u + a, f, m);
+    // (u + a) mod f <= f - 1, so every u >= f - 1 keeps the tap without the modulo
+    return u >= f - 1 || (u + a) < 0 || u >= mod_f(u + a, f, m);
 }
 
 
@@ -318,10 +321,11 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float s = 0.f;
+            const int lim = BORDER ? fwd_lim(x0 - 4 + e + j, f, fmag) : 2;
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 - b];
-                if (BORDER && !fwd_tap_ok(x0 - 4 + e + j, b, f, fmag)) v = 0.f;
+                if (BORDER && b > lim) v = 0.f;
                 s = fmaf(cs[C_HX + b + 2], v, s);
             }
             out[j] = s;
@@ -333,10 +337,11 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         const int n = it / (EW / 4), e = 4 * (it - n * (EW / 4));
         const int gy = y0 - 4 + n;
         float2 z[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        const int lim = BORDER ? fwd_lim(gy, f, fmag) : 2;
 #pragma unroll
         for (int a = -2; a <= 2; ++a) {
             const float4 v = ld4(HS + (n + 2 - a) * EW + e);
-            const float2 h = bc2((BORDER && !fwd_tap_ok(gy, a, f, fmag)) ? 0.f : cs[C_HY + a + 2]);
+            const float2 h = bc2((BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
             z[0] = f2fma(h, make_float2(v.x, v.y), z[0]);
             z[1] = f2fma(h, make_float2(v.z, v.w), z[1]);
         }
@@ -386,10 +391,11 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float sp = 0.f;
+            const int lim = BORDER ? fwd_lim(x0 + o + j, f, fmag) : 2;
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float vp = inp[j + 2 - b];
-                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f, fmag)) vp = 0.f;
+                if (BORDER && b > lim) vp = 0.f;
                 sp = fmaf(cs[C_HX + b + 2], vp, sp);
             }
             out[j] = sp;
@@ -549,10 +555,11 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float sr = 0.f;
+            const int lim = BORDER ? fwd_lim(x0 + o + j, f, fmag) : 2;
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float vr = inr[j + 2 - b];
-                if (BORDER && !fwd_tap_ok(x0 + o + j, b, f, fmag)) vr = 0.f;
+                if (BORDER && b > lim) vr = 0.f;
                 sr = fmaf(cs[C_HX + b + 2], vr, sr);
             }
             out[j] = sr;
@@ -567,11 +574,12 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         {
             float2 zr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             float2 zp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            const int lim = BORDER ? fwd_lim(gy, f, fmag) : 2;
 #pragma unroll
             for (int a = -2; a <= 2; ++a) {
                 const float4 vr = ld4(HR + (n + 2 - a) * CW + o);
                 const float4 vp = ld4(HS + (n + 2 - a) * CW + o);
-                const float2 h = bc2((BORDER && !fwd_tap_ok(gy, a, f, fmag)) ? 0.f : cs[C_HY + a + 2]);
+                const float2 h = bc2((BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
                 zr[0] = f2fma(h, make_float2(vr.x, vr.y), zr[0]);
                 zr[1] = f2fma(h, make_float2(vr.z, vr.w), zr[1]);
                 zp[0] = f2fma(h, make_float2(vp.x, vp.y), zp[0]);
