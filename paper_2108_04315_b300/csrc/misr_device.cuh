@@ -134,11 +134,6 @@ __device__ __forceinline__ void ld8(const float *p, float *v) {   // p 16-byte a
     const float4 a = ld4(p), b = ld4(p + 4);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
-__device__ __forceinline__ void ld8_off2(const float *p, float *v) {   // p 8-byte aligned
-    const float2 a = ld2(p), c = ld2(p + 6);
-    const float4 b = ld4(p + 2);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = b.z; v[5] = b.w; v[6] = c.x; v[7] = c.y;
-}
 __device__ __forceinline__ void ld4v(const float *p, float *v) {
     const float4 a = ld4(p);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -209,6 +204,25 @@ __device__ __forceinline__ bool adj_tap_ok(int u, int a, int f, unsigned m) {
     return u >= f - 1 || (u + a) < 0 || u >= mod_f(u + a, f, m);
 }
 
+
+// Row and first column of item `it` of a grid of ROWS x W4 four-pixel items: the items of
+// the first W4 & ~7 columns of every row come first, so that the 8 threads of a shared-memory
+// phase of 16-byte accesses stay in one row; the remaining columns follow, row by row.
+template <int ROWS, int W4>
+__device__ __forceinline__ void item_rc(int it, int &r, int &c) {
+    constexpr int WA = W4 & ~7, WB = W4 - WA;
+    if constexpr (WA == 0 || WB == 0) {
+        r = it / W4;
+        c = 4 * (it - r * W4);
+    } else if (it < ROWS * WA) {
+        r = it / WA;
+        c = 4 * (it - r * WA);
+    } else {
+        const int k = it - ROWS * WA;
+        r = k / WB;
+        c = 4 * (WA + k - r * WB);
+    }
+}
 
 // per-thread partial sums of a pass (FP32; combined across the CTA in FP64).  a, b, c hold
 // the full curvature forms: 2 sum (B v)(B w) over sampled pixels + lambda * prior part.
@@ -314,9 +328,12 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     };
     // B1: forward horizontal blur of x' on (X rows) x (E cols)
     auto item_B1 = [&](int it) {
-        const int r = it / (EW / 4), e = 4 * (it - r * (EW / 4));
-        float in[8];
-        ld8_off2(XB + r * XW + e + 2, in);   // x' at E cols e-2 .. e+5
+        int r, e;
+        item_rc<XH, EW / 4>(it, r, e);
+        float in12[12];
+        ld8(XB + r * XW + e, in12);          // x' at E cols e-4 .. e+7 (three 16-byte loads)
+        ld4v(XB + r * XW + e + 8, in12 + 8);
+        const float *in = in12 + 2;          // x' at E cols e-2 .. e+5
         float out[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -365,7 +382,8 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     };
     // C1: adjoint horizontal blur of E on (E rows) x (G cols)
     auto item_C1 = [&](int it) {
-        const int n = it / (GW / 4), g = 4 * (it - n * (GW / 4));
+        int n, g;
+        item_rc<EH, GW / 4>(it, n, g);
         float in[8];
         ld8(YB + n * EW + g, in);   // E at G cols g-2 .. g+5
         float out[4];
@@ -385,8 +403,10 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     // horizontal blur of p on rows [-2, TH+2) x owned cols (for the curvature forms)
     auto item_HP = [&](int it) {
         const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
-        float inp[8];
-        ld8_off2(PB + (n + 4) * XW + o + 6, inp);     // p at owned cols o-2 .. o+5
+        float in12[12];
+        ld8(PB + (n + 4) * XW + o + 4, in12);         // p at owned cols o-4 .. o+7
+        ld4v(PB + (n + 4) * XW + o + 12, in12 + 8);
+        const float *inp = in12 + 2;                  // p at owned cols o-2 .. o+5
         float out[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -487,7 +507,8 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     // C2 + r': adjoint vertical blur 2 B^T E, then r' = -(2 B^T E + lambda g_BTV) in place of
     // the BTV gradient; zero outside the image; owned pixels go to HBM with their sums
     auto item_C2r = [&](int it) {
-        const int n = it / (GW / 4), g = 4 * (it - n * (GW / 4));
+        int n, g;
+        item_rc<GH, GW / 4>(it, n, g);
         const int u = y0 - 2 + n;
         float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
@@ -518,14 +539,17 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         const int orow = n - 2;
         if (orow >= 0 && orow < TH) {
             // owned columns of the item: tile cols g-2 .. g+1 inside [0, TW), as two pairs
-            // (8-byte aligned in the workspace images and in XB)
+            // (8-byte aligned in the workspace images); r and p_old read as 16-byte groups
+            // (tile cols g-4 .. g-1 and g .. g+3 are XB cols g+4 .. g+11)
+            const float *rrow_o = RB + (orow + 6) * XW + g + 4, *prow_o = PB + (orow + 6) * XW + g + 4;
+            const float4 ra = ld4(rrow_o), rb = ld4(rrow_o + 4), pa = ld4(prow_o), pb4 = ld4(prow_o + 4);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int oc = g - 2 + 2 * h;
                 if (oc < 0 || oc >= TW) continue;
                 const int gx = x0 + oc;
-                const float2 ro = ld2(RB + (orow + 6) * XW + oc + 8);
-                const float2 pq = ld2(PB + (orow + 6) * XW + oc + 8);
+                const float2 ro = h == 0 ? make_float2(ra.z, ra.w) : make_float2(rb.x, rb.y);
+                const float2 pq = h == 0 ? make_float2(pa.z, pa.w) : make_float2(pb4.x, pb4.y);
                 const float r0 = rv[2 * h], r1 = rv[2 * h + 1];
                 if (!BORDER || (u < H && gx + 1 < W)) {
                     if (rpb)
