@@ -23,13 +23,16 @@ __device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
 // Steps follow Moller's algorithm (the same order as Algorithm 1's loop body):
 // comparison parameter, accept/reject, lambda updates, beta, then the scaling of the next
 // curvature and the next step size.
-__device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const double *S, int mode);
-// (the state is read once, updated in registers and written back once)
-__device__ inline void scg_tail(const DevProblem &P, ScgState *gst, const double *S, int mode) {
-    ScgState L = *gst;
-    scg_tail_local(P, &L, S, mode);
-    *gst = L;
+// The state read with L2-coherent 8-byte loads (the previous kernel wrote it).
+__device__ __forceinline__ void load_state(ScgState &L, const ScgState *g) {
+    static_assert(sizeof(ScgState) % 8 == 0, "8-byte words");
+    const unsigned long long *s = reinterpret_cast<const unsigned long long *>(g);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(&L);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(ScgState) / 8); ++i) d[i] = __ldcg(s + i);
 }
+// The tail on a copy of the state held by the caller (read before the sums were known, written
+// back once).
 __device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const double *S, int mode) {
     for (int i = 0; i < NPART; ++i) st->sums[i] = S[i];
     if (mode == MODE_PROBE) return;
@@ -48,14 +51,16 @@ __device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const d
         if (rr == 0.0 || st->iters <= 0) st->done = 1;
     } else {
         const double delta = st->delta, mu = st->mu, pn2 = st->pn2;
+        // reciprocals of the state's mu and |p|^2: they do not depend on the pass's sums
+        const double inv_mu = 1.0 / mu, inv_pn2 = 1.0 / pn2;
         // J(x') - J(x): data part from the per-pixel difference (accurate in FP32),
         // prior part from its two direct evaluations
         const double dE = S[P_DJD] + (Jb - st->E_btv);
-        const double Delta = 2.0 * delta * (-dE) / (mu * mu);
+        const double Delta = 2.0 * delta * (-dE) * (inv_mu * inv_mu);
         const double E_before = st->E;
         const int accept = Delta >= 0.0;
         if (accept) {
-            const double beta = (rr - rrx) / mu;
+            const double beta = (rr - rrx) * inv_mu;
             st->E = Jt; st->E_btv = Jb; st->rn2 = rr;
             delta_raw = S[P_A] + 2.0 * beta * S[P_B] + beta * beta * S[P_C];
             mu_next = rr + beta * pr;
@@ -69,7 +74,7 @@ __device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const d
             st->lam_bar = st->lam;
             st->success = 0;
         }
-        if (Delta < 0.25) st->lam = st->lam + delta * (1.0 - Delta) / pn2;
+        if (Delta < 0.25) st->lam = st->lam + delta * (1.0 - Delta) * inv_pn2;
         if (P.trace) {
             double *t = P.trace + (size_t)st->iter * TRACE_COLS;
             t[0] = E_before; t[1] = Jt; t[2] = st->alpha; t[3] = delta; t[4] = mu;
@@ -785,7 +790,11 @@ __global__ void __launch_bounds__(32) reduce_kernel(const DevProblem *__restrict
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int2 gi = groups[blockIdx.x];
     const DevProblem &P = probs[gi.x];
-    if (ld_cg(&P.st->done)) return;
+    // the state: its done flag now, and the tail's input if this warp completes the problem
+    // (read before the sums, so that the tail does not wait for it)
+    ScgState L;
+    load_state(L, P.st);
+    if (L.done) return;
     const int g = gi.y;
     const int gsize = min(P.group, P.n_tiles - g * P.group);
     const float2 v = warp_sum_fields(P.partials + (size_t)g * P.group, P.n_tiles, gsize);
@@ -808,7 +817,8 @@ __global__ void __launch_bounds__(32) reduce_kernel(const DevProblem *__restrict
         S[j] = (double)hi + (double)lo;
     }
     if (lane == 0) {
-        scg_tail(P, P.st, S, mode);
+        scg_tail_local(P, &L, S, mode);
+        *P.st = L;
         *P.counter = 0u;
         __threadfence();
     }
