@@ -15,15 +15,9 @@
 
 namespace misr {
 
-__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
 
-// ---------------------------------------------------------------------------------------
-// SCG scalar tail, run by lane 0 of the reduction warp that completes a pass's sums S.
-// Steps follow Moller's algorithm (the same order as Algorithm 1's loop body):
-// comparison parameter, accept/reject, lambda updates, beta, then the scaling of the next
-// curvature and the next step size.
-// The state read with L2-coherent 8-byte loads (the previous kernel wrote it).
+// The SCG state read with L2-coherent 8-byte loads (the previous kernel wrote it).
 __device__ __forceinline__ void load_state(ScgState &L, const ScgState *g) {
     static_assert(sizeof(ScgState) % 8 == 0, "8-byte words");
     const unsigned long long *s = reinterpret_cast<const unsigned long long *>(g);
@@ -31,8 +25,13 @@ __device__ __forceinline__ void load_state(ScgState &L, const ScgState *g) {
 #pragma unroll
     for (int i = 0; i < (int)(sizeof(ScgState) / 8); ++i) d[i] = __ldcg(s + i);
 }
-// The tail on a copy of the state held by the caller (read before the sums were known, written
-// back once).
+
+// ---------------------------------------------------------------------------------------
+// SCG scalar tail, run by lane 0 of the reduction warp that completes a pass's sums S, on a
+// copy of the state the caller read before the sums were known (written back once).
+// Steps follow Moller's algorithm (the same order as Algorithm 1's loop body):
+// comparison parameter, accept/reject, lambda updates, beta, then the scaling of the next
+// curvature and the next step size.
 __device__ inline void scg_tail_local(const DevProblem &P, ScgState *st, const double *S, int mode) {
     for (int i = 0; i < NPART; ++i) st->sums[i] = S[i];
     if (mode == MODE_PROBE) return;
@@ -132,7 +131,6 @@ struct Geo {
 };
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 __device__ __forceinline__ void ld8(const float *p, float *v) {   // p 16-byte aligned
@@ -245,8 +243,8 @@ enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_
 // Work is split into 4-pixel row items and scheduled in seven barrier intervals.  The BTV
 // gradient depends only on x' and is the heaviest stage (16 psi' evaluations per pixel, each
 // pair evaluated from both ends instead of staged in shared memory); its items are split over
-// I2 and I3, one per thread on the first threads, with the light data-term items of the same
-// interval spread over the other threads.
+// I2 and I3, one per thread on whole warps, with the light data-term items of the same
+// interval spread over the other warps.
 //   I1 A: p, x'                        I2 BTV (part) + B1 (forward horizontal blur)
 //   I3 BTV (the rest) + B2             I4 C1 (adjoint horizontal blur)
 //   I5 C2 + r'                         I6 horizontal blurs of r' and p
