@@ -586,6 +586,30 @@ def main():
            "d2h_bytes_per_step": int(H * W * 4), "api": "misr_solve_host_many (copies overlapped with solves)",
            "one_call_per_step": {"value": serial_rate, "unit": UNIT, "api": "misr_solve_host"}}
 
+    # the batch form on this configuration: NB projections advanced by one pass launch per SCG
+    # step (misr_batch_solve), against the plain one-projection-at-a-time rate above
+    from paper_2108_04315_b300.binding import Batch
+    NB = 4
+    plans_b = [Plan(wl["h"], wl["w"], wl["f"], shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3,
+                    iters=wl["iters"], tile_shape=tuned) for _ in range(NB)]
+    batch = Batch(plans_b)
+    xs_b = [torch.empty((H, W), dtype=torch.float32, device=device) for _ in range(NB)]
+    batch.solve([y] * NB, xs_b, stats=False)
+    n_b = max(1, (args.steps + NB - 1) // NB)
+    ev4, ev5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev4.record(stream)
+    for _ in range(n_b):
+        batch.solve([y] * NB, xs_b, stats=False)
+    ev5.record(stream)
+    ev5.synchronize()
+    batched_rate, _ = job_rate(n_b * NB, ev4.elapsed_time(ev5) / 1e3, dist, device)
+    batch.close()
+    for pb in plans_b:
+        pb.close()
+    batched = {"value": batched_rate, "unit": UNIT, "projections_per_launch": NB, "over_plain": batched_rate / value,
+               "api": "misr_batch_solve (%d projections of this configuration per fused-pass launch)" % NB}
+
     peak, peak_kind = load_peaks()
     achieved = PASS_BYTES_PER_PX * H * W / (pass_ms * 1e-3) / 1e9
     out = {
@@ -605,6 +629,7 @@ def main():
                      "timed_as": "one SCG pass: the fused pass kernel and its reduction kernel, "
                                  "(T(100 it) - T(0 it)) / 100 with CUDA events on the solve's stream"},
         "e2e": e2e,
+        "batched": batched,
         # per solve: prepare, the initial pass and every SCG pass (the fused pass kernel and its
         # reduction kernel), finalize
         "gpu_launches": args.steps * (2 * wl["iters"] + 4),
