@@ -76,6 +76,9 @@ def kernel_source_tag():
     return h.hexdigest()
 
 
+# the B300's nominal HBM3e bandwidth (GB/s), beside the measured copy peak
+SPEC_HBM_GBS = 7700.0
+
 # MISR_TILE_* -> (tile rows, tile columns, threads per CTA)
 TILE_SHAPES = {1: (32, 64, 512), 2: (32, 32, 256), 3: (16, 64, 256)}
 
@@ -624,6 +627,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": load_traffic(kernel_source_tag(), shape_name),
                      "kernel": f"scg_pass_kernel<{th},{tw},{nt}>", "peak_kind": peak_kind,
+                     "spec_peak": SPEC_HBM_GBS, "frac_of_spec": achieved / SPEC_HBM_GBS,
                      "algorithmic_bytes_per_launch": PASS_BYTES_PER_PX * H * W,
                      "ms_per_launch": pass_ms,
                      "timed_as": "one SCG pass: the fused pass kernel and its reduction kernel, "
