@@ -125,6 +125,16 @@ misr_status misr_plan_destroy(misr_plan_t plan);
 /* Device bytes the plan holds. */
 misr_status misr_plan_workspace_bytes(misr_plan_t plan, size_t *bytes);
 
+/* Failure-path hook of the fused pass (for tests and diagnosis).  Every tile load is waited for
+ * with at most `tries` polls before the tile is reported late; the default, 2^24, is far beyond
+ * any healthy load.  A late load flags the projection: its SCG state is marked done and its
+ * solve (or probe) returns MISR_ETIMEOUT; the copies already in flight are still waited for
+ * (with the default limit) before the CTA stops, so the device context stays usable.
+ * tries = 0 reports every load late without waiting.  Applies to solves of this plan launched
+ * after the call; a batch or a server copies the plan's record when it is created or admits the
+ * projection.  Synchronises the device.  Errors: MISR_EINVAL (NULL plan), MISR_ECUDA. */
+misr_status misr_plan_set_wait_limit(misr_plan_t plan, uint32_t tries);
+
 /* y_k = D B M_k x for every frame (Eq. 1 without noise): x_dev is the HR float32 image,
  * y_dev receives K float32 frames.  Asynchronous on stream.  Used to synthesise
  * acquisitions. */

@@ -73,6 +73,7 @@ def lib():
         L.misr_plan_create.argtypes = [C.POINTER(misr_desc), C.POINTER(VP)]
         L.misr_plan_destroy.argtypes = [VP]
         L.misr_plan_workspace_bytes.argtypes = [VP, C.POINTER(C.c_size_t)]
+        L.misr_plan_set_wait_limit.argtypes = [VP, C.c_uint32]
         L.misr_forward.argtypes = [VP, VP, VP, VP]
         L.misr_gradient.argtypes = [VP, VP, VP, VP, DP, VP]
         L.misr_pass_probe.argtypes = [VP, VP, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, DP, VP]
@@ -90,7 +91,8 @@ def lib():
         L.misr_poll.argtypes = [VP, C.c_uint64, C.POINTER(misr_stats), DP]
         L.misr_server_wait.argtypes = [VP, C.c_uint64, C.c_double]
         L.misr_server_counters.argtypes = [VP, C.POINTER(C.c_int64)]
-        for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_forward",
+        for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_plan_set_wait_limit",
+                     "misr_forward",
                      "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_solve_host_many",
                      "misr_get_trace",
                      "misr_batch_create", "misr_batch_destroy", "misr_batch_solve", "misr_server_create",
@@ -148,6 +150,13 @@ def misr_pass_probe(plan, y_dev, x_dev, r_dev, p_old_dev, alpha, beta, x_out, r_
                                  float(beta), VP(x_out), VP(r_out), VP(p_out), sums, VP(stream)),
            "misr_pass_probe")
     return dict(zip(PASS_SUM_FIELDS, list(sums)))
+
+
+TMA_WAIT_TRIES_DEFAULT = 1 << 24
+
+
+def misr_plan_set_wait_limit(plan: int, tries: int):
+    _check(lib().misr_plan_set_wait_limit(VP(plan), int(tries)), "misr_plan_set_wait_limit")
 
 
 def misr_solve(plan: int, y_dev: int, x_dev: int, stream: int = 0, want_stats: bool = True):

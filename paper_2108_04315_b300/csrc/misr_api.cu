@@ -375,6 +375,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
     hp.H = f * d.lr_h; hp.W = f * d.lr_w;
     hp.pitch = (hp.W + 7) & ~7;   // 16-byte rows for float and bf16 planes
+    hp.wait_tries = (int)TMA_WAIT_TRIES;
     hp.iters = d.iters;
     for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
     for (int k = 0; k < d.K; ++k) {
@@ -423,7 +424,6 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     const size_t o_img = off; off += 3 * img + 4 * rp_img;   // X[2], Y (float); R[2], P[2]
     const size_t o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(float2), 256);
     const size_t o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(float2), 256);
-    const size_t o_gcnt = off; off += align_up((size_t)hp.n_groups * sizeof(unsigned int), 256);
     const size_t o_cnt = off; off += 256;
     const size_t o_work = off; off += 256;
     const size_t o_st = off; off += align_up(sizeof(ScgState), 256);
@@ -448,7 +448,6 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     hp.rp_bf16 = d.iterate_dtype == MISR_BF16;
     hp.partials = (float2 *)(b + o_part);
     hp.gpartials = (float2 *)(b + o_gpart);
-    hp.gcount = (unsigned int *)(b + o_gcnt);
     hp.counter = (unsigned int *)(b + o_cnt);
     p->work = (unsigned int *)(b + o_work);
     hp.st = (ScgState *)(b + o_st);
@@ -509,6 +508,15 @@ misr_status misr_plan_destroy(misr_plan_t p) {
     if (p->st_ring) cudaFree(p->st_ring);
     if (p->ws) cudaFree(p->ws);
     delete p;
+    return MISR_OK;
+}
+
+misr_status misr_plan_set_wait_limit(misr_plan_t p, uint32_t tries) {
+    if (!p) return fail(MISR_EINVAL, "plan is NULL");
+    DeviceGuard g(p->device);
+    p->hp.wait_tries = (int)std::min<uint32_t>(tries, 0x7fffffffu);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(p->dprob, &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice));
     return MISR_OK;
 }
 
@@ -788,8 +796,7 @@ constexpr int NOALLOC_MAX_GROUPS = 128;
 constexpr size_t NA_O_IMG = 0;
 constexpr size_t NA_O_PART = NA_O_IMG + 7 * NOALLOC_IMG;
 constexpr size_t NA_O_GPART = NA_O_PART + na_align(size_t(NOALLOC_MAX_TILES) * NPART * sizeof(float2), 256);
-constexpr size_t NA_O_GCNT = NA_O_GPART + na_align(size_t(NOALLOC_MAX_GROUPS) * NPART * sizeof(float2), 256);
-constexpr size_t NA_O_CNT = NA_O_GCNT + na_align(size_t(NOALLOC_MAX_GROUPS) * sizeof(unsigned int), 256);
+constexpr size_t NA_O_CNT = NA_O_GPART + na_align(size_t(NOALLOC_MAX_GROUPS) * NPART * sizeof(float2), 256);
 constexpr size_t NA_O_WORK = NA_O_CNT + 256;
 constexpr size_t NA_O_ST = NA_O_WORK + 256;
 constexpr size_t NA_O_PROB = NA_O_ST + na_align(sizeof(ScgState), 256);
@@ -840,6 +847,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
     hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
     hp.H = f * d.lr_h; hp.W = f * d.lr_w;
     hp.pitch = (hp.W + 7) & ~7;   // 16-byte rows for float and bf16 planes
+    hp.wait_tries = (int)TMA_WAIT_TRIES;
     hp.iters = 0;
     for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
     for (int k = 0; k < d.K; ++k) {
@@ -877,7 +885,6 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
     hp.Y = reinterpret_cast<float *>(base + NA_O_IMG + 6 * NOALLOC_IMG);
     hp.partials = reinterpret_cast<float2 *>(base + NA_O_PART);
     hp.gpartials = reinterpret_cast<float2 *>(base + NA_O_GPART);
-    hp.gcount = reinterpret_cast<unsigned int *>(base + NA_O_GCNT);
     hp.counter = reinterpret_cast<unsigned int *>(base + NA_O_CNT);
     hp.st = reinterpret_cast<ScgState *>(base + NA_O_ST);
     hp.trace = nullptr;

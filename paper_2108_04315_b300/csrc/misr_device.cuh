@@ -251,7 +251,7 @@ enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_
 //   I7 curvature forms (owned)
 template <int TH, int TW, int NT, bool BORDER, bool RPB, typename Hook>
 __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsigned char *smp, const float *cs,
-                                          uint64_t *ybar, uint32_t yphase, int y0, int x0, float alpha,
+                                          uint64_t *ybar, uint32_t yphase, uint32_t ytries, int y0, int x0, float alpha,
                                           float beta, float *Xn,
                                           float *Rn, float *Pn, PassAcc &A, Hook &&hook) {
     using G = Geo<TH, TW>;
@@ -698,7 +698,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     hook(2);
     __syncthreads();
     // the Y box: a wait that runs out is reported to the caller (the tile's results are void)
-    const bool y_late = !mbar_wait_bounded(ybar, yphase, TMA_WAIT_TRIES);
+    const bool y_late = !mbar_wait_bounded(ybar, yphase, ytries);
     // I3: BTV items [N_BTV2, N_BTV) on the first warps, B2 on the others
     if (tid < N_BTV3) item_btv(N_BTV2 + tid);
     else
@@ -837,7 +837,7 @@ struct TileInfo {
     const DevProblem *P;
     float *Xn, *Rn, *Pn;
     float alpha, beta;
-    int cur, pcur, prob;                 // the problem's fields (rewritten when it changes)
+    int cur, pcur, prob, wait_tries;     // the problem's fields (rewritten when it changes)
     int y0, x0, t, end, restage;         // the tile's
 };
 // The scheduling thread's own state: the CTA's next claimed tile, its list entry (copied
@@ -873,6 +873,7 @@ __device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k
             restage = 1;
             c.P = P;
             c.prob = wt.x;
+            c.wait_tries = P->wait_tries;
             c.cur = ld_cg(&st->cur);
             c.pcur = ld_cg(&st->pcur);
             c.alpha = mode == MODE_PROBE ? (float)probe_alpha : __ldcg(&st->alpha_f);
@@ -889,6 +890,7 @@ __device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k
     if (ti.prob != c.prob) {
         ti.P = c.P; ti.Xn = c.Xn; ti.Rn = c.Rn; ti.Pn = c.Pn;
         ti.alpha = c.alpha; ti.beta = c.beta; ti.cur = c.cur; ti.pcur = c.pcur; ti.prob = c.prob;
+        ti.wait_tries = c.wait_tries;
     }
     const unsigned ty = (unsigned)wt.y >> 16, tx = (unsigned)wt.y & 0xffffu;
     ti.t = (int)(ty * (unsigned)sc.tiles_x + tx);
@@ -989,7 +991,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
         }
         if (tid == SCHED_TID && sched.next < n_tiles) cp_async_8(&sched.wt_pre, tiles + sched.next);
         const uint32_t phase = n & 1;
-        const bool landed = mbar_wait_bounded(&bar[0], phase, TMA_WAIT_TRIES);
+        // a wait that runs out (the problem's limit) is reported; the copies in flight are then
+        // drained with the full limit before the CTA stops
+        const bool landed = mbar_wait_bounded(&bar[0], phase, (uint32_t)ti.wait_tries);
         if (__syncthreads_or(!landed)) {
             // the loads did not land in time: flag the projection, let the copies in flight
             // land, and stop taking tiles
@@ -1030,10 +1034,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
             const int y0 = ti.y0, x0 = ti.x0;
             const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
             if (border)
-                y_late = pass_tile<TH, TW, NT, true, RPB>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
+                y_late = pass_tile<TH, TW, NT, true, RPB>(P, sm, smp, cs, &bar[1], phase, (uint32_t)ti.wait_tries, y0, x0, ti.alpha, ti.beta, ti.Xn,
                                                      ti.Rn, ti.Pn, A, hook);
             else
-                y_late = pass_tile<TH, TW, NT, false, RPB>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
+                y_late = pass_tile<TH, TW, NT, false, RPB>(P, sm, smp, cs, &bar[1], phase, (uint32_t)ti.wait_tries, y0, x0, ti.alpha, ti.beta,
                                                       ti.Xn, ti.Rn, ti.Pn, A, hook);
         }
 
@@ -1143,9 +1147,6 @@ __global__ void prepare_kernel(const DevProblem *__restrict__ probs, int pidx, c
         st->lam = 1e-6; st->lam_bar = 0.0; st->iters = P.iters;
         *P.counter = 0u;
     }
-    if (flags & 4)
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n_groups; i += gridDim.x * blockDim.x)
-            P.gcount[i] = 0u;
     for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
         const int cy = (int)(o / pitch), cx = (int)(o - (size_t)cy * pitch);
         float yv = __int_as_float(0x7fc00000);  // NaN: no frame samples this pixel

@@ -67,7 +67,8 @@ struct DevProblem {
     int H, W, pitch, f, h, w, K;
     int tiles_x, tiles_y, n_tiles, iters;
     int rp_bf16;                                  // r and p stored as bf16 (x stays float)
-    int shape, tile_h, tile_w, pad0;              // tile shape (index into SHAPE_*) and its size
+    int shape, tile_h, tile_w;                    // tile shape (index into SHAPE_*) and its size
+    int wait_tries;                               // polls before a tile load is reported late
     float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];  // separable PSF, h(a, b) = hy[a+R] hx[b+R]
     float lambda, eps, eps2, pad1;
     float gamma[BTV_W * BTV_W];                   // gamma(dx, dy) at [dy * BTV_W + dx]
@@ -75,12 +76,11 @@ struct DevProblem {
     float *X[2], *Rv[2], *Pv[2];                  // x, r (double buffered), p (double buffered);
                                                   // Rv, Pv hold __nv_bfloat16 when rp_bf16
     float *Y;                                     // interleaved frames, NaN where unsampled
-    // Fixed-order reduction of a pass's sums: every tile writes its sums; whoever finishes the
-    // last tile of a group of `group` tiles sums the group in tile order; whoever finishes the
-    // last group sums the groups in order and runs the SCG tail.  Field-major arrays.
+    // Fixed-order reduction of a pass's sums: every tile writes its sums; after the pass, one
+    // warp per group of `group` tiles sums the group in tile order, and the warp that finishes
+    // the last group sums the groups in order and runs the SCG tail.  Field-major arrays.
     float2 *partials;                             // [NPART][n_tiles] tile sums (hi, lo)
     float2 *gpartials;                            // [NPART][n_groups] group sums (hi, lo)
-    unsigned int *gcount;                         // [n_groups] tiles of the group finished
     unsigned int *counter;                        // groups finished in the current pass
     int group, n_groups;                          // tiles per group, groups
     ScgState *st;

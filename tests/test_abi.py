@@ -86,4 +86,5 @@ def test_null_arguments_rejected(L):
     assert L.misr_plan_create(None, None) == binding.MISR_EINVAL
     assert L.misr_solve(None, None, None, None, None) == binding.MISR_EINVAL
     assert L.misr_solve_host_many(None, 1, None, None, None) == binding.MISR_EINVAL
+    assert L.misr_plan_set_wait_limit(None, 0) == binding.MISR_EINVAL
     assert L.misr_plan_destroy(None) == binding.MISR_OK
