@@ -186,6 +186,34 @@ misr_status misr_solve_host(misr_plan_t plan, const void *y_host, float *x_host,
 misr_status misr_solve_host_many(misr_plan_t plan, int32_t n, const void *const *y_host, float *const *x_host,
                                  misr_stats *stats);
 
+/* ---- Checkpoint and resume ----------------------------------------------------------------
+ * A projection's SCG solve can stop after any iteration and continue later, on the same plan or
+ * on another plan of the same geometry and storage type (e.g. one with more iterations), with
+ * the result bit for bit that of one uninterrupted solve.  A checkpoint holds the iterate x_k,
+ * the gradient r_k, the previous direction p_{k-1} (float, or bf16 for MISR_BF16 plans) and
+ * the SCG scalars of Algorithm 1 (Table 1): lambda, lambda-bar, delta, mu, |p|^2, E, beta,
+ * alpha, success and the iteration count.  Layout (little-endian, host memory): a 32-byte
+ * header (magic 0x4353524d, version 1, H, W, bf16 flag, state record size, 2 reserved words),
+ * the state record, then x, r and p as dense H x W row-major planes.
+ *
+ * misr_state_bytes: the size of the plan's checkpoint.
+ * misr_export_state: after a solve (or resume) of the plan has completed (synchronises the
+ *   device), write its checkpoint to host memory `buf` of at least `bytes` bytes.
+ * misr_import_state: load a checkpoint into the plan.  The iteration target becomes the plan's
+ *   desc.iters; a checkpoint stopped by its iteration count is live again if that target is
+ *   larger.  The plan's trace keeps rows only from iterations run on it.  Synchronises.
+ * misr_resume: continue the plan's solve (after misr_import_state, or after a solve whose
+ *   iteration target was reached) to its iteration target: y_dev gives the frames again (the
+ *   plan does not keep them), x_dev receives the image.  Asynchronous on stream unless stats is
+ *   non-NULL, as misr_solve.
+ * Errors: MISR_EINVAL (NULL arguments, too small a buffer, a checkpoint of another geometry,
+ * storage type, state layout or version), MISR_ECUDA, and misr_solve's. */
+misr_status misr_state_bytes(misr_plan_t plan, size_t *bytes);
+misr_status misr_export_state(misr_plan_t plan, void *buf, size_t bytes);
+misr_status misr_import_state(misr_plan_t plan, const void *buf, size_t bytes);
+misr_status misr_resume(misr_plan_t plan, const void *y_dev, float *x_dev, misr_stream_t stream,
+                        misr_stats *stats);
+
 /* Copy the per-iteration trace of the plan's last completed solve (MISR_TRACE_COLS doubles
  * per iteration) into out (host, max_rows rows); *rows receives the number written.
  * Synchronises with the plan's last solve. */

@@ -81,6 +81,10 @@ def lib():
         L.misr_solve_host.argtypes = [VP, VP, VP, C.POINTER(misr_stats)]
         L.misr_solve_host_many.argtypes = [VP, C.c_int32, C.POINTER(VP), C.POINTER(VP), C.POINTER(misr_stats)]
         L.misr_get_trace.argtypes = [VP, DP, C.c_int32, C.POINTER(C.c_int32)]
+        L.misr_state_bytes.argtypes = [VP, C.POINTER(C.c_size_t)]
+        L.misr_export_state.argtypes = [VP, VP, C.c_size_t]
+        L.misr_import_state.argtypes = [VP, VP, C.c_size_t]
+        L.misr_resume.argtypes = [VP, VP, VP, VP, C.POINTER(misr_stats)]
         L.misr_batch_create.argtypes = [C.c_int32, C.POINTER(VP), C.POINTER(VP)]
         L.misr_batch_destroy.argtypes = [VP]
         L.misr_batch_solve.argtypes = [VP, C.POINTER(VP), C.POINTER(VP), VP, C.POINTER(misr_stats)]
@@ -94,7 +98,7 @@ def lib():
         for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_plan_set_wait_limit",
                      "misr_forward",
                      "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_solve_host_many",
-                     "misr_get_trace",
+                     "misr_get_trace", "misr_state_bytes", "misr_export_state", "misr_import_state", "misr_resume",
                      "misr_batch_create", "misr_batch_destroy", "misr_batch_solve", "misr_server_create",
                      "misr_server_destroy", "misr_submit", "misr_poll", "misr_server_wait", "misr_server_counters",
                      "misr_autotune"):
@@ -182,6 +186,30 @@ def misr_solve_host_many(plan: int, y_hosts, x_hosts, want_stats: bool = True):
     st = (misr_stats * max(1, n))()
     _check(lib().misr_solve_host_many(VP(plan), n, ya, xa, st if want_stats else None), "misr_solve_host_many")
     return [_stats_dict(st[k]) for k in range(n)] if want_stats else None
+
+
+def misr_state_bytes(plan: int) -> int:
+    n = C.c_size_t()
+    _check(lib().misr_state_bytes(VP(plan), C.byref(n)), "misr_state_bytes")
+    return int(n.value)
+
+
+def misr_export_state(plan: int) -> np.ndarray:
+    buf = np.zeros(misr_state_bytes(plan), dtype=np.uint8)
+    _check(lib().misr_export_state(VP(plan), buf.ctypes.data, buf.nbytes), "misr_export_state")
+    return buf
+
+
+def misr_import_state(plan: int, buf: np.ndarray):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().misr_import_state(VP(plan), buf.ctypes.data, buf.nbytes), "misr_import_state")
+
+
+def misr_resume(plan: int, y_dev: int, x_dev: int, stream: int = 0, want_stats: bool = True):
+    st = misr_stats()
+    _check(lib().misr_resume(VP(plan), VP(y_dev), VP(x_dev), VP(stream), C.byref(st) if want_stats else None),
+           "misr_resume")
+    return _stats_dict(st) if want_stats else None
 
 
 def misr_get_trace(plan: int, max_rows: int):
@@ -364,6 +392,21 @@ class Plan:
         assert all(x.dtype == np.float32 for x in x_hosts)
         return misr_solve_host_many(self.handle, [a.ctypes.data for a in y_hosts], [a.ctypes.data for a in x_hosts],
                                     stats)
+
+    def export_state(self):
+        """Checkpoint of the last completed solve (x_k, r_k, p_{k-1} and the SCG scalars)."""
+        return misr_export_state(self.handle)
+
+    def import_state(self, buf):
+        misr_import_state(self.handle, buf)
+
+    def resume(self, y, x_out=None, stream=None, stats=True):
+        """Continue the imported (or stopped) solve to this plan's iteration count."""
+        import torch
+        if x_out is None:
+            x_out = torch.empty((self.H, self.W), dtype=torch.float32, device=y.device)
+        st = misr_resume(self.handle, self._ptr(y), self._ptr(x_out, torch.float32), _stream_handle(stream), stats)
+        return x_out, st
 
     def trace(self):
         return misr_get_trace(self.handle, self.iters)

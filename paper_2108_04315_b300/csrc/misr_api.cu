@@ -758,6 +758,112 @@ misr_status misr_solve_host_many(misr_plan_t p, int32_t n, const void *const *y_
     return worst;
 }
 
+// ---- checkpoint and resume
+namespace {
+struct CkptHeader {
+    uint32_t magic, version, H, W, bf16, state_bytes, reserved[2];
+};
+static_assert(sizeof(CkptHeader) == 32, "checkpoint header");
+constexpr uint32_t CKPT_MAGIC = 0x4353524du, CKPT_VERSION = 1u;
+size_t ckpt_bytes(const misr_plan_t p) {
+    const size_t n = (size_t)p->hp.H * p->hp.W, rp = p->hp.rp_bf16 ? 2 : 4;
+    return sizeof(CkptHeader) + sizeof(ScgState) + n * 4 + 2 * n * rp;
+}
+}  // namespace
+
+misr_status misr_state_bytes(misr_plan_t p, size_t *bytes) {
+    if (!p || !bytes) return fail(MISR_EINVAL, "NULL argument");
+    *bytes = ckpt_bytes(p);
+    return MISR_OK;
+}
+
+misr_status misr_export_state(misr_plan_t p, void *buf, size_t bytes) {
+    if (!p || !buf) return fail(MISR_EINVAL, "NULL argument");
+    if (bytes < ckpt_bytes(p)) return fail(MISR_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", bytes, ckpt_bytes(p));
+    DeviceGuard g(p->device);
+    CK(cudaDeviceSynchronize());
+    ScgState st;
+    CK(cudaMemcpy(&st, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost));
+    const size_t W = p->hp.W, H = p->hp.H, pitch = p->hp.pitch, rp = p->hp.rp_bf16 ? 2 : 4;
+    char *out = static_cast<char *>(buf);
+    CkptHeader h{CKPT_MAGIC, CKPT_VERSION, (uint32_t)H, (uint32_t)W, (uint32_t)p->hp.rp_bf16, (uint32_t)sizeof(ScgState),
+                 {0u, 0u}};
+    std::memcpy(out, &h, sizeof h);
+    std::memcpy(out + sizeof h, &st, sizeof st);
+    char *planes = out + sizeof h + sizeof st;
+    CK(cudaMemcpy2D(planes, W * 4, p->hp.X[st.cur], pitch * 4, W * 4, H, cudaMemcpyDeviceToHost));
+    planes += H * W * 4;
+    CK(cudaMemcpy2D(planes, W * rp, p->hp.Rv[st.cur], pitch * rp, W * rp, H, cudaMemcpyDeviceToHost));
+    planes += H * W * rp;
+    CK(cudaMemcpy2D(planes, W * rp, p->hp.Pv[st.pcur], pitch * rp, W * rp, H, cudaMemcpyDeviceToHost));
+    return MISR_OK;
+}
+
+misr_status misr_import_state(misr_plan_t p, const void *buf, size_t bytes) {
+    if (!p || !buf) return fail(MISR_EINVAL, "NULL argument");
+    if (bytes < sizeof(CkptHeader)) return fail(MISR_EINVAL, "checkpoint buffer too small");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != CKPT_MAGIC || h.version != CKPT_VERSION) return fail(MISR_EINVAL, "not a checkpoint of this version");
+    if (h.H != (uint32_t)p->hp.H || h.W != (uint32_t)p->hp.W || h.bf16 != (uint32_t)p->hp.rp_bf16 ||
+        h.state_bytes != (uint32_t)sizeof(ScgState))
+        return fail(MISR_EINVAL, "checkpoint of another geometry, storage type or state layout");
+    if (bytes < ckpt_bytes(p)) return fail(MISR_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", bytes, ckpt_bytes(p));
+    DeviceGuard g(p->device);
+    CK(cudaDeviceSynchronize());
+    const char *in = static_cast<const char *>(buf);
+    ScgState st;
+    std::memcpy(&st, in + sizeof h, sizeof st);
+    const size_t W = p->hp.W, H = p->hp.H, pitch = p->hp.pitch, rp = p->hp.rp_bf16 ? 2 : 4;
+    const char *planes = in + sizeof h + sizeof st;
+    CK(cudaMemcpy2D(p->hp.X[0], pitch * 4, planes, W * 4, W * 4, H, cudaMemcpyHostToDevice));
+    planes += H * W * 4;
+    CK(cudaMemcpy2D(p->hp.Rv[0], pitch * rp, planes, W * rp, W * rp, H, cudaMemcpyHostToDevice));
+    planes += H * W * rp;
+    CK(cudaMemcpy2D(p->hp.Pv[0], pitch * rp, planes, W * rp, W * rp, H, cudaMemcpyHostToDevice));
+    // the buffers now hold the checkpoint's halves at index 0; the iteration target is this
+    // plan's, and a solve stopped only by its count is live again below it
+    st.cur = 0;
+    st.pcur = 0;
+    st.iters = p->d.iters;
+    st.done = (st.status != 0 || st.iter >= st.iters || !(st.pn2 > 0.0) || !std::isfinite(st.alpha)) ? 1 : 0;
+    CK(cudaMemcpy(p->hp.st, &st, sizeof st, cudaMemcpyHostToDevice));
+    CK(cudaMemset(p->hp.counter, 0, sizeof(unsigned int)));
+    CK(cudaMemset(p->work, 0, 2 * sizeof(unsigned int)));
+    CK(cudaMemset(p->hp.trace, 0, (size_t)std::max(p->d.iters, 1) * TRACE_COLS * sizeof(double)));
+    *p->st_host = st;
+    p->solved = true;
+    return MISR_OK;
+}
+
+misr_status misr_resume(misr_plan_t p, const void *y_dev, float *x_dev, misr_stream_t stream, misr_stats *stats) {
+    if (!p || !y_dev || !x_dev) return fail(MISR_EINVAL, "NULL argument");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    misr_status r = ensure_graph(p);
+    if (r != MISR_OK) return r;
+    ScgState st;
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(&st, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost));
+    // the frames again (Y only: no start point, no reset)
+    const float log_i0 = p->d.in_dtype == MISR_U16 ? logf(p->d.flat_field) : 0.f;
+    prepare_kernel<<<grid_for(p->n_pitched, 256), 256, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, nullptr,
+                                                               MISR_X0_ZERO, 0);
+    CK(cudaGetLastError());
+    const int remaining = st.done ? 0 : std::max(st.iters - st.iter, 0);
+    for (int done = 0; done < remaining; done += p->chunk_len) CK(cudaGraphLaunch(p->chunk, s));
+    finalize_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->dprob, 0, x_dev);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(p->done_ev, s));
+    p->solved = true;
+    if (stats) {
+        CK(cudaMemcpyAsync(p->st_host, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return fill_stats(p, stats);
+    }
+    return MISR_OK;
+}
+
 misr_status misr_get_trace(misr_plan_t p, double *out, int32_t max_rows, int32_t *rows) {
     if (!p || !out || !rows || max_rows < 0) return fail(MISR_EINVAL, "bad argument");
     DeviceGuard g(p->device);
