@@ -186,6 +186,15 @@ misr_status misr_solve_host(misr_plan_t plan, const void *y_host, float *x_host,
 misr_status misr_solve_host_many(misr_plan_t plan, int32_t n, const void *const *y_host, float *const *x_host,
                                  misr_stats *stats);
 
+/* Bounds-check record of the library's checked build (libmisr_check.so, compiled with
+ * MISR_BOUNDS_CHECK, where every shared-memory item position, global store, tile or group
+ * index and TMA x coordinate of the device code is checked, and a failed check is recorded and
+ * its access skipped instead of made).  `bits` receives one bit per kind of check that failed
+ * since the last call (0: none); `first` (4 ints, may be NULL) the first failure: the check,
+ * two of its values and the block.  The record is then cleared.  Synchronises the device.
+ * The normal build returns MISR_ENOTIMPL.  Errors: MISR_EINVAL (bits NULL), MISR_ECUDA. */
+misr_status misr_debug_bounds(uint32_t *bits, int32_t *first);
+
 /* ---- Checkpoint and resume ----------------------------------------------------------------
  * A projection's SCG solve can stop after any iteration and continue later, on the same plan or
  * on another plan of the same geometry and storage type (e.g. one with more iterations), with

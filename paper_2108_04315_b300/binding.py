@@ -74,6 +74,7 @@ def lib():
         L.misr_plan_destroy.argtypes = [VP]
         L.misr_plan_workspace_bytes.argtypes = [VP, C.POINTER(C.c_size_t)]
         L.misr_plan_set_wait_limit.argtypes = [VP, C.c_uint32]
+        L.misr_debug_bounds.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]
         L.misr_forward.argtypes = [VP, VP, VP, VP]
         L.misr_gradient.argtypes = [VP, VP, VP, VP, DP, VP]
         L.misr_pass_probe.argtypes = [VP, VP, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, DP, VP]
@@ -96,6 +97,7 @@ def lib():
         L.misr_server_wait.argtypes = [VP, C.c_uint64, C.c_double]
         L.misr_server_counters.argtypes = [VP, C.POINTER(C.c_int64)]
         for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_plan_set_wait_limit",
+                     "misr_debug_bounds",
                      "misr_forward",
                      "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_solve_host_many",
                      "misr_get_trace", "misr_state_bytes", "misr_export_state", "misr_import_state", "misr_resume",
@@ -154,6 +156,14 @@ def misr_pass_probe(plan, y_dev, x_dev, r_dev, p_old_dev, alpha, beta, x_out, r_
                                  float(beta), VP(x_out), VP(r_out), VP(p_out), sums, VP(stream)),
            "misr_pass_probe")
     return dict(zip(PASS_SUM_FIELDS, list(sums)))
+
+
+def misr_debug_bounds():
+    """(bits, first) of the bounds-checked build; raises MisrError(MISR_ENOTIMPL) on the normal one."""
+    bits = C.c_uint32()
+    first = (C.c_int32 * 4)()
+    _check(lib().misr_debug_bounds(C.byref(bits), first), "misr_debug_bounds")
+    return int(bits.value), list(first)
 
 
 TMA_WAIT_TRIES_DEFAULT = 1 << 24

@@ -10,6 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libmisr.so")
+LIB_CHECK = os.path.join(PKG, "libmisr_check.so")   # the bounds-checked variant (MISR_BOUNDS_CHECK)
 SOURCES = [os.path.join(CSRC, f) for f in ("misr_api.cu", "misr_batch.cu", "misr_server.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h", ".cu"))] + \
     [os.path.join(INCLUDE, "misr.h")]
@@ -24,11 +25,14 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in DEPS):
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, "-o", tmp, *SOURCES]
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Build libmisr.so, or with checked=True the bounds-checked libmisr_check.so."""
+    lib = LIB_CHECK if checked else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(d) for d in DEPS):
+        return lib
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = [nvcc(), *NVCC_FLAGS, *(["-DMISR_BOUNDS_CHECK"] if checked else []), "-I", INCLUDE, "-I", CSRC, "-o", tmp,
+           *SOURCES]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -37,9 +41,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         sys.stderr.write(r.stderr)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv)

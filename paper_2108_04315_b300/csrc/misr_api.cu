@@ -360,7 +360,13 @@ misr_status misr_host::check_desc(const misr_desc &d) {
 
 extern "C" {
 
-const char *misr_version(void) { return "misr-b300 0.3 (sm_103a, persistent TMA-fed fused SCG pass; tiles 32x64, 32x32, 16x64)"; }
+const char *misr_version(void) {
+#ifdef MISR_BOUNDS_CHECK
+    return "misr-b300 0.3 (sm_103a, persistent TMA-fed fused SCG pass; tiles 32x64, 32x32, 16x64; bounds-checked)";
+#else
+    return "misr-b300 0.3 (sm_103a, persistent TMA-fed fused SCG pass; tiles 32x64, 32x32, 16x64)";
+#endif
+}
 
 const char *misr_last_error(void) { return g_err.c_str(); }
 
@@ -756,6 +762,28 @@ misr_status misr_solve_host_many(misr_plan_t p, int32_t n, const void *const *y_
         if (sk != MISR_OK) worst = sk;
     }
     return worst;
+}
+
+misr_status misr_debug_bounds(uint32_t *bits, int32_t *first) {
+    if (!bits) return fail(MISR_EINVAL, "bits is NULL");
+#ifdef MISR_BOUNDS_CHECK
+    CK(cudaDeviceSynchronize());
+    unsigned int b = 0;
+    int f[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyFromSymbol(&b, misr::g_bounds_bits, sizeof b));
+    CK(cudaMemcpyFromSymbol(f, misr::g_bounds_first, sizeof f));
+    const unsigned int zero = 0;
+    const int zeros[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyToSymbol(misr::g_bounds_bits, &zero, sizeof zero));
+    CK(cudaMemcpyToSymbol(misr::g_bounds_first, zeros, sizeof zeros));
+    *bits = b;
+    if (first) std::memcpy(first, f, sizeof f);
+    return MISR_OK;
+#else
+    *bits = 0;
+    if (first) std::memset(first, 0, 4 * sizeof(int32_t));
+    return fail(MISR_ENOTIMPL, "this library was built without bounds checks (libmisr_check.so has them)");
+#endif
 }
 
 // ---- checkpoint and resume

@@ -17,6 +17,30 @@ namespace misr {
 
 __device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
 
+// Bounds-checked build (MISR_BOUNDS_CHECK, the library's checked variant): every shared-memory
+// item position, global store, tile or group index and TMA x coordinate is checked before use; a
+// failed check is recorded (which check, two values and the block, first failure only) and the
+// access is skipped instead of made.  In the normal build the checks compile to nothing.
+enum BoundsCode {
+    BC_A = 1, BC_A_STORE, BC_B1, BC_B2, BC_C1, BC_C2, BC_C2_STORE, BC_HP, BC_HR, BC_E, BC_BTV,
+    BC_TILE, BC_TMA_X, BC_GROUP, BC_IMAGE
+};
+#ifdef MISR_BOUNDS_CHECK
+__device__ unsigned int g_bounds_bits;
+__device__ int g_bounds_first[4];
+__device__ __noinline__ void bounds_fail(int code, int a, int b) {
+    if (atomicOr(&g_bounds_bits, 1u << code) == 0u) {
+        g_bounds_first[0] = code;
+        g_bounds_first[1] = a;
+        g_bounds_first[2] = b;
+        g_bounds_first[3] = (int)blockIdx.x;
+    }
+}
+#define MISR_IN_BOUNDS(cond, code, a, b) ((cond) ? true : (::misr::bounds_fail((code), (a), (b)), false))
+#else
+#define MISR_IN_BOUNDS(cond, code, a, b) true
+#endif
+
 // The SCG state read with L2-coherent 8-byte loads (the previous kernel wrote it).
 __device__ __forceinline__ void load_state(ScgState &L, const ScgState *g) {
     static_assert(sizeof(ScgState) % 8 == 0, "8-byte words");
@@ -290,6 +314,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     // it, so the tile works with exactly the p the next pass reads back)
     auto item_A = [&](int it) {
         const int r = it / (XW / 4), c4 = it - r * (XW / 4);
+        if (!MISR_IN_BOUNDS(it >= 0 && r < XH, BC_A, r, c4)) return;
         float4 rv, pov;
         if constexpr (rpb) {
             rv = bf4(RS + 4 * it);
@@ -312,6 +337,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         if (orow >= 0 && orow < TH && ocol >= 0 && ocol < TW) {
             const int gy = y0 + orow, gx = x0 + ocol;
             if (!BORDER || (gy < H && gx + 3 < W)) {
+                if (!MISR_IN_BOUNDS(gy >= 0 && gy < H && gx >= 0 && gx + 3 < W, BC_A_STORE, gy, gx)) return;
                 const size_t o = (size_t)gy * pitch + gx;
                 st4(Xn + o, xn);
                 if (rpb) st_bf4(reinterpret_cast<__nv_bfloat16 *>(Pn) + o, pv);
@@ -333,6 +359,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     auto item_B1 = [&](int it) {
         int r, e;
         item_rc<XH, EW / 4>(it, r, e);
+        if (!MISR_IN_BOUNDS(r >= 0 && r < XH && e >= 0 && e + 11 < XW && e + 3 < EW, BC_B1, r, e)) return;
         float in12[12];
         ld8(XB + r * XW + e, in12);          // x' at E cols e-4 .. e+7 (three 16-byte loads)
         ld4v(XB + r * XW + e + 8, in12 + 8);
@@ -355,6 +382,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     // B2: vertical blur -> Z, residual E = Z - Y (0 where Y is NaN: unsampled or outside)
     auto item_B2 = [&](int it) {
         const int n = it / (EW / 4), e = 4 * (it - n * (EW / 4));
+        if (!MISR_IN_BOUNDS(n >= 0 && n < EH && e + 3 < EW, BC_B2, n, e)) return;
         const int gy = y0 - 4 + n;
         float2 z[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         const int lim = BORDER ? fwd_lim(gy, f, fmag) : 2;
@@ -387,6 +415,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     auto item_C1 = [&](int it) {
         int n, g;
         item_rc<EH, GW / 4>(it, n, g);
+        if (!MISR_IN_BOUNDS(n >= 0 && n < EH && g >= 0 && g + 7 < EW && g + 3 < GW, BC_C1, n, g)) return;
         float in[8];
         ld8(YB + n * EW + g, in);   // E at G cols g-2 .. g+5
         float out[4];
@@ -406,6 +435,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     // horizontal blur of p on rows [-2, TH+2) x owned cols (for the curvature forms)
     auto item_HP = [&](int it) {
         const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
+        if (!MISR_IN_BOUNDS(n >= 0 && n < CH && o + 15 < XW && o + 3 < CW, BC_HP, n, o)) return;
         float in12[12];
         ld8(PB + (n + 4) * XW + o + 4, in12);         // p at owned cols o-4 .. o+7
         ld4v(PB + (n + 4) * XW + o + 12, in12 + 8);
@@ -442,6 +472,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
             n = k / WB;
             g = 4 * (WA + k - n * WB);
         }
+        if (!MISR_IN_BOUNDS(n >= 0 && n < GH && g >= 0 && g + 3 < GW && n + 6 < XH && g + 11 < XW, BC_BTV, n, g)) return;
         const int qy = y0 - 2 + n, qx = x0 - 2 + g;          // image coords of the first pixel
         // x' rows n-2 .. n+2 of the G grid are XB rows n+2 .. n+6; cols g-4 .. g+3 of the G
         // grid (8 values, 16-byte aligned) are XB cols g+4 .. g+11
@@ -512,6 +543,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     auto item_C2r = [&](int it) {
         int n, g;
         item_rc<GH, GW / 4>(it, n, g);
+        if (!MISR_IN_BOUNDS(n >= 0 && n < GH && g >= 0 && g + 3 < GW && n + 4 < EH, BC_C2, n, g)) return;
         const int u = y0 - 2 + n;
         float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
@@ -555,6 +587,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
                 const float2 pq = h == 0 ? make_float2(pa.z, pa.w) : make_float2(pb4.x, pb4.y);
                 const float r0 = rv[2 * h], r1 = rv[2 * h + 1];
                 if (!BORDER || (u < H && gx + 1 < W)) {
+                    if (!MISR_IN_BOUNDS(u >= 0 && u < H && gx >= 0 && gx + 1 < W, BC_C2_STORE, u, gx)) continue;
                     if (rpb)
                         *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(Rn) + (size_t)u * pitch + gx) =
                             __floats2bfloat162_rn(r0, r1);
@@ -576,6 +609,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     // horizontal blur of r' on rows [-2, TH+2) x owned cols
     auto item_HR = [&](int it) {
         const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
+        if (!MISR_IN_BOUNDS(n >= 0 && n < CH && o + 7 < GW && o + 3 < CW, BC_HR, n, o)) return;
         float inr[8];
         ld8(GB + n * GW + o, inr);                    // r' at owned cols o-2 .. o+5
         float out[4];
@@ -596,6 +630,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     // curvature forms on one owned row x four columns
     auto item_E = [&](int it) {
         const int n = it / (TW / 4), o = 4 * (it - n * (TW / 4));
+        if (!MISR_IN_BOUNDS(n >= 0 && n < TH && o + 3 < TW, BC_E, n, o)) return;
         const int gy = y0 + n;
         // data part 2 (B v)(c) (B w)(c) at sampled c, and J_data(x') - J_data(x)
         {
@@ -795,6 +830,7 @@ __global__ void __launch_bounds__(32) reduce_kernel(const DevProblem *__restrict
     if (L.done) return;
     const int g = gi.y;
     const int gsize = min(P.group, P.n_tiles - g * P.group);
+    if (!MISR_IN_BOUNDS(g >= 0 && g < P.n_groups && gsize > 0, BC_GROUP, g, gsize)) return;
     const float2 v = warp_sum_fields(P.partials + (size_t)g * P.group, P.n_tiles, gsize);
     const int slot = lane >> 1;
     if ((lane & 1) == 0 && slot < NPART) P.gpartials[(size_t)slot * P.n_groups + g] = v;
@@ -894,6 +930,10 @@ __device__ __forceinline__ void prepare_tile(TileInfo &ti, SchedState &sc, int k
     }
     const unsigned ty = (unsigned)wt.y >> 16, tx = (unsigned)wt.y & 0xffffu;
     ti.t = (int)(ty * (unsigned)sc.tiles_x + tx);
+    if (!MISR_IN_BOUNDS(tx < (unsigned)sc.tiles_x && ti.t < c.P->n_tiles, BC_TILE, (int)ty, (int)tx)) {
+        ti.end = 1;
+        return;
+    }
     ti.y0 = (int)ty * TH;
     ti.x0 = (int)tx * TW;
     ti.end = 0;
@@ -905,6 +945,8 @@ template <int TH, int TW, bool RPB>
 __device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_t *bar) {
     using Gm = Geo<TH, TW>;
     const DevProblem *P = ti.P;
+    // a TMA x coordinate must be a multiple of 16 bytes (4 floats, 8 bf16)
+    if (!MISR_IN_BOUNDS(((ti.x0 - 8) & 7) == 0 && ((ti.x0 - 4) & 3) == 0, BC_TMA_X, ti.x0, ti.y0)) return;
     // generic-proxy accesses of the previous tile are ordered before these async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     constexpr uint32_t box_x = sizeof(float) * Gm::XH * Gm::XW;
@@ -1111,7 +1153,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
                 lo += ((hi - (s - bb)) + (x - bb)) + (lane == P_JB ? red_lo[w] : 0.f);
                 hi = s;
             }
-            tile_sums[(size_t)lane * n_tiles_p] = make_float2(hi, lo);
+            if (MISR_IN_BOUNDS(ti.t >= 0 && ti.t < n_tiles_p, BC_TILE, ti.t, n_tiles_p))
+                tile_sums[(size_t)lane * n_tiles_p] = make_float2(hi, lo);
         }
     }
     // this CTA takes no more tiles: the reduction kernel may start launching

@@ -1,0 +1,69 @@
+"""Child process of tests/test_gpu_bounds.py: run the odd geometries through a given build of
+the library (argv[1]: library path, argv[2]: output .npz) and print its bounds-check record."""
+import json
+import sys
+
+import numpy as np
+
+
+def cases():
+    import gen
+    from tests.gpu_common import asym_separable_psf
+    return {
+        # name: (h, w, f, shifts, psf)
+        "tiny_f2": (64, 64, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
+        "ragged_f2_asym": (37, 53, 2, gen.half_pixel_shifts(), asym_separable_psf(3)),
+        "ragged_f3_k9": (23, 29, 3, gen.third_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
+        "partial_f2_k3": (30, 41, 2, [(0.0, 0.0), (0.5, 0.0), (0.5, 0.5)], asym_separable_psf(4, 3)),
+        "f1_denoise": (45, 70, 1, [(0.0, 0.0)], gen.gaussian_psf(5, 0.6)),
+        "f4_k16": (17, 21, 4, gen.phase_shifts(4), gen.gaussian_psf(5, 1.0)),
+        "single_pixel": (1, 1, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
+        "thin_strip": (1, 97, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
+        "tall_strip": (90, 1, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
+    }
+
+
+def frames(h, w, shifts, seed):
+    import gen
+    return gen.random_field((len(shifts), h, w), seed, 0.0, 2.0).astype(np.float32)
+
+
+def run(lib_path):
+    import torch
+    import gen
+    from paper_2108_04315_b300 import binding as B
+    B.LIB_PATH = lib_path
+    out = {}
+    plans = []
+    for i, (name, (h, w, f, shifts, psf)) in enumerate(sorted(cases().items())):
+        y = torch.from_numpy(frames(h, w, shifts, 600 + i)).cuda()
+        for shape in (1, 2, 3):
+            for dt in (B.MISR_F32, B.MISR_BF16):
+                plan = B.Plan(h, w, f, shifts, psf, iters=4, tile_shape=shape, iterate_dtype=dt)
+                x, _ = plan.solve(y)
+                out[f"{name}_s{shape}_d{dt}"] = x.cpu().numpy()
+                if dt == B.MISR_F32 and shape == 2:
+                    J, g = plan.gradient(y, x)
+                    out[f"{name}_grad"] = g.cpu().numpy()
+                    plans.append((plan, y))
+    # a batch over mixed geometries, tile shapes and storage types
+    sel = plans[:4]
+    batch = B.Batch([p for p, _ in sel])
+    xs, _ = batch.solve([y for _, y in sel])
+    for k, x in enumerate(xs):
+        out[f"batch_{k}"] = x.cpu().numpy()
+    batch.close()
+    torch.cuda.synchronize()
+    try:
+        bits, first = B.misr_debug_bounds()
+    except B.MisrError as e:                       # the normal build has no checks to report
+        assert e.status == B.MISR_ENOTIMPL
+        bits, first = 0, [0, 0, 0, 0]
+    return out, bits, first
+
+
+if __name__ == "__main__":
+    sys.path.insert(0, sys.argv[3] if len(sys.argv) > 3 else ".")
+    images, bits, first = run(sys.argv[1])
+    np.savez(sys.argv[2], **images)
+    print(json.dumps({"bits": bits, "first": first}))
