@@ -39,7 +39,8 @@ typedef enum {
     MISR_ECUDA = 3,     /* a CUDA runtime call failed */
     MISR_EAGAIN = 4,    /* not ready yet / no free slot */
     MISR_ETIMEOUT = 5,  /* a bounded wait ran out */
-    MISR_ENOTIMPL = 6   /* valid request this build does not support */
+    MISR_ENOTIMPL = 6,  /* valid request this build does not support */
+    MISR_ECANCELED = 7  /* a served request cancelled before it finished */
 } misr_status;
 
 /* element types of the LR frames and of the iterate */
@@ -290,6 +291,13 @@ misr_status misr_submit(misr_server_t server, const misr_desc *desc, const void 
  * clock in seconds (may be NULL); the ticket is then forgotten (a further poll gives
  * MISR_EINVAL). */
 misr_status misr_poll(misr_server_t server, uint64_t ticket, misr_stats *stats, double *times);
+
+/* Cancel a request.  Queued: it is dropped at once.  Running: its slot is freed at the end of
+ * the worker's current tick (when none of its GPU work is in flight); x_dev is then left as
+ * that tick wrote it.  Either way the ticket finishes with MISR_ECANCELED, and its buffers may
+ * be released once misr_poll (or misr_server_wait) reports that.  A ticket that already
+ * finished keeps its result.  Errors: MISR_EINVAL (NULL server, unknown ticket). */
+misr_status misr_cancel(misr_server_t server, uint64_t ticket);
 
 /* Wait at most timeout_s seconds for the ticket to finish (then poll it).  MISR_OK when it
  * finished, MISR_ETIMEOUT otherwise, MISR_EINVAL for an unknown ticket. */

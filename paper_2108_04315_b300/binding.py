@@ -14,7 +14,7 @@ import numpy as np
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libmisr.so")
 
-MISR_OK, MISR_EINVAL, MISR_ENOMEM, MISR_ECUDA, MISR_EAGAIN, MISR_ETIMEOUT, MISR_ENOTIMPL = range(7)
+MISR_OK, MISR_EINVAL, MISR_ENOMEM, MISR_ECUDA, MISR_EAGAIN, MISR_ETIMEOUT, MISR_ENOTIMPL, MISR_ECANCELED = range(8)
 MISR_F32, MISR_U16, MISR_BF16 = 0, 1, 2
 MISR_X0_ZERO, MISR_X0_SHIFT_ADD, MISR_X0_GIVEN = 0, 1, 2
 MISR_TILE_AUTO, MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64 = 0, 1, 2, 3
@@ -95,6 +95,7 @@ def lib():
         L.misr_submit.argtypes = [VP, C.POINTER(misr_desc), VP, VP, C.POINTER(C.c_uint64)]
         L.misr_poll.argtypes = [VP, C.c_uint64, C.POINTER(misr_stats), DP]
         L.misr_server_wait.argtypes = [VP, C.c_uint64, C.c_double]
+        L.misr_cancel.argtypes = [VP, C.c_uint64]
         L.misr_server_counters.argtypes = [VP, C.POINTER(C.c_int64)]
         for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_plan_set_wait_limit",
                      "misr_debug_bounds",
@@ -102,7 +103,7 @@ def lib():
                      "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_solve_host_many",
                      "misr_get_trace", "misr_state_bytes", "misr_export_state", "misr_import_state", "misr_resume",
                      "misr_batch_create", "misr_batch_destroy", "misr_batch_solve", "misr_server_create",
-                     "misr_server_destroy", "misr_submit", "misr_poll", "misr_server_wait", "misr_server_counters",
+                     "misr_server_destroy", "misr_submit", "misr_poll", "misr_server_wait", "misr_server_counters", "misr_cancel",
                      "misr_autotune"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -494,6 +495,10 @@ class Server:
     def wait(self, ticket, timeout_s=60.0):
         misr_server_wait(self.handle, ticket, timeout_s)
         return self.poll(ticket)
+
+    def cancel(self, ticket):
+        """Drop a queued request, or stop a running one after the current tick (MISR_ECANCELED)."""
+        _check(lib().misr_cancel(VP(self.handle), int(ticket)), "misr_cancel")
 
     def counters(self):
         return misr_server_counters(self.handle)

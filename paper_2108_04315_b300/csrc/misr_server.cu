@@ -67,6 +67,7 @@ struct Request {
     float *x = nullptr;
     ReqState state = RQ_QUEUED;
     misr_status status = MISR_OK;
+    bool cancel = false;            // cancelled while running: finish at the end of the tick
     misr_stats stats{};
     double t_submit = 0, t_start = 0, t_end = 0;
     int slot = -1;
@@ -327,15 +328,22 @@ void worker_main(misr_server_t s) {
                 r = fail(MISR_ECUDA, "state copy failed");
         if (r == MISR_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) r = fail(MISR_ECUDA, "server stream failed");
         std::vector<int> done;
+        std::vector<char> cancelled(s->slots.size(), 0);
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            for (size_t i = 0; i < s->slots.size(); ++i)
+                if (s->slots[i].busy) cancelled[i] = s->reqs[s->slots[i].ticket].cancel;
+        }
         for (size_t i = 0; i < s->slots.size(); ++i) {
             Slot &sl = s->slots[i];
             if (!sl.busy) continue;
             sl.passes += k_passes;
-            if (r != MISR_OK || s->st_host[i].done) done.push_back((int)i);
+            if (r != MISR_OK || s->st_host[i].done || cancelled[i]) done.push_back((int)i);
         }
         for (int idx : done) {
             Slot &sl = s->slots[idx];
             misr_status code = r;
+            if (code == MISR_OK && cancelled[idx]) code = MISR_ECANCELED;
             if (code == MISR_OK && s->st_host[idx].status != DEV_OK) code = MISR_ETIMEOUT;
             if (code == MISR_OK) {
                 const Request *rq;
@@ -453,6 +461,24 @@ extern "C" misr_status misr_poll(misr_server_t s, uint64_t ticket, misr_stats *s
     const misr_status st = rq.status;
     s->reqs.erase(it);
     if (st != MISR_OK) return fail(st, "request %llu failed", (unsigned long long)ticket);
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_cancel(misr_server_t s, uint64_t ticket) {
+    if (!s) return fail(MISR_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(MISR_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    Request &rq = it->second;
+    if (rq.state == RQ_QUEUED) {
+        s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), ticket), s->queue.end());
+        rq.state = RQ_FAILED;
+        rq.status = MISR_ECANCELED;
+        rq.t_end = now_s();
+        s->cv_done.notify_all();
+    } else if (rq.state == RQ_RUNNING) {
+        rq.cancel = true;   // the worker finishes it after its current tick
+    }
     return MISR_OK;
 }
 

@@ -88,6 +88,7 @@ def test_null_arguments_rejected(L):
     assert L.misr_solve_host_many(None, 1, None, None, None) == binding.MISR_EINVAL
     assert L.misr_plan_set_wait_limit(None, 0) == binding.MISR_EINVAL
     assert L.misr_debug_bounds(None, None) == binding.MISR_EINVAL
+    assert L.misr_cancel(None, 1) == binding.MISR_EINVAL
     assert L.misr_state_bytes(None, None) == binding.MISR_EINVAL
     assert L.misr_export_state(None, None, 0) == binding.MISR_EINVAL
     assert L.misr_import_state(None, None, 0) == binding.MISR_EINVAL

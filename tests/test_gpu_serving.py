@@ -134,3 +134,37 @@ def test_serving_destroy_with_requests_in_flight():
     time.sleep(0.01)
     srv.close()
     torch.cuda.synchronize()
+
+
+def test_serving_cancel_queued_and_running(orc):
+    from paper_2108_04315_b300 import binding as B
+    (P, plan, xt, y) = _cases(orc)[0]
+    yd = to_dev(y)
+    h, w, f, sh, it = GEOMS[0]
+    x_alone, st_alone = plan.solve(yd)
+    srv = B.Server(max_slots=1, passes_per_tick=2)
+    yl = torch.rand((4, 256, 256), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(11))
+    t_long = srv.submit(yl, 256, 256, 2, gen.half_pixel_shifts(), PSF, iters=5000)   # runs, long
+    t_queued = srv.submit(yd, h, w, f, sh, PSF, iters=it)                          # waits for the slot
+    srv.cancel(t_queued)
+    with pytest.raises(B.MisrError) as e:
+        srv.wait(t_queued, timeout_s=60.0)
+    assert e.value.status == B.MISR_ECANCELED
+    srv.cancel(t_long)
+    with pytest.raises(B.MisrError) as e:
+        srv.wait(t_long, timeout_s=120.0)
+    assert e.value.status == B.MISR_ECANCELED
+    with pytest.raises(B.MisrError) as e:        # forgotten once reported
+        B.misr_poll(srv.handle, t_long)
+    assert e.value.status == B.MISR_EINVAL
+    # the server keeps serving, and a request after the cancellations gets its own solve's result
+    t = srv.submit(yd, h, w, f, sh, PSF, iters=it)
+    x, st, _ = srv.wait(t, timeout_s=60.0)
+    assert torch.equal(x, x_alone) and st == st_alone
+    # cancelling a finished (already reported) or unknown ticket
+    with pytest.raises(B.MisrError) as e:
+        srv.cancel(t)
+    assert e.value.status == B.MISR_EINVAL
+    c = srv.counters()
+    assert c["queued"] == 0 and c["running"] == 0
+    srv.close()
