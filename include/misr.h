@@ -126,9 +126,9 @@ misr_status misr_plan_destroy(misr_plan_t plan);
 /* Device bytes the plan holds. */
 misr_status misr_plan_workspace_bytes(misr_plan_t plan, size_t *bytes);
 
-/* Failure-path hook of the fused pass (for tests and diagnosis).  Every tile load is waited for
- * with at most `tries` polls before the tile is reported late; the default, 2^24, is far beyond
- * any healthy load.  A late load flags the projection: its SCG state is marked done and its
+/* Failure-path hook of the fused pass (for tests and diagnosis).  The wait for a tile's x, r
+ * and p boxes gives up after `tries` polls and reports the tile late (the later wait for its
+ * frames box keeps the default); the default, 2^24, is far beyond any healthy load.  A late load flags the projection: its SCG state is marked done and its
  * solve (or probe) returns MISR_ETIMEOUT; the copies already in flight are still waited for
  * (with the default limit) before the CTA stops, so the device context stays usable.
  * tries = 0 reports every load late without waiting.  Applies to solves of this plan launched

@@ -275,7 +275,7 @@ enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_
 //   I7 curvature forms (owned)
 template <int TH, int TW, int NT, bool BORDER, bool RPB, typename Hook>
 __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsigned char *smp, const float *cs,
-                                          uint64_t *ybar, uint32_t yphase, uint32_t ytries, int y0, int x0, float alpha,
+                                          uint64_t *ybar, uint32_t yphase, int y0, int x0, float alpha,
                                           float beta, float *Xn,
                                           float *Rn, float *Pn, PassAcc &A, Hook &&hook) {
     using G = Geo<TH, TW>;
@@ -733,7 +733,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     hook(2);
     __syncthreads();
     // the Y box: a wait that runs out is reported to the caller (the tile's results are void)
-    const bool y_late = !mbar_wait_bounded(ybar, yphase, ytries);
+    const bool y_late = !mbar_wait_bounded(ybar, yphase, TMA_WAIT_TRIES);
     // I3: BTV items [N_BTV2, N_BTV) on the first warps, B2 on the others
     if (tid < N_BTV3) item_btv(N_BTV2 + tid);
     else
@@ -1076,10 +1076,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
             const int y0 = ti.y0, x0 = ti.x0;
             const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
             if (border)
-                y_late = pass_tile<TH, TW, NT, true, RPB>(P, sm, smp, cs, &bar[1], phase, (uint32_t)ti.wait_tries, y0, x0, ti.alpha, ti.beta, ti.Xn,
+                y_late = pass_tile<TH, TW, NT, true, RPB>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
                                                      ti.Rn, ti.Pn, A, hook);
             else
-                y_late = pass_tile<TH, TW, NT, false, RPB>(P, sm, smp, cs, &bar[1], phase, (uint32_t)ti.wait_tries, y0, x0, ti.alpha, ti.beta,
+                y_late = pass_tile<TH, TW, NT, false, RPB>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
                                                       ti.Xn, ti.Rn, ti.Pn, A, hook);
         }
 
