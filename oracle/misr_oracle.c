@@ -55,6 +55,17 @@ int orc_init(orc_problem *P, int h, int w, int K, int f, const double *shifts_lr
     return 0;
 }
 
+/* Data norm (reading: the paper's experiments use the L1 norm, Sec. 3.1; it is smoothed
+ * like the prior's |.|, psi_d(t) = sqrt(t^2 + eps_d^2) - eps_d).  Returns 0, or -1 for an
+ * unknown norm or eps_d <= 0 with the L1 norm. */
+int orc_set_data_norm(orc_problem *P, int norm, double data_eps) {
+    if (norm != ORC_NORM_L2 && norm != ORC_NORM_L1) return -1;
+    if (norm == ORC_NORM_L1 && !(data_eps > 0)) return -1;
+    P->data_norm = norm;
+    P->data_eps = data_eps;
+    return 0;
+}
+
 /* (A_k x)(i, j) = (D B M_k x)(i, j)                                            Eq. 1
  *   (M_k x)(u, v) = x(u + ty_k, v + tx_k), zero when that pixel is outside the grid;
  *   (B z)(u, v)   = sum_{a,b} h(a, b) z(u - a, v - b), z zero outside the grid;
@@ -245,6 +256,26 @@ double orc_reg_curvature(const orc_problem *P, const double *x, const double *p)
     return total;
 }
 
+/* the data term's value on a residual image: sum of squares (L2) or of psi_d (L1), rows
+ * first */
+static double data_value_lr(const orc_problem *P, const double *e) {
+    double *rows = (double *)calloc((size_t)P->h, sizeof(double));
+    const int l1 = P->data_norm == ORC_NORM_L1;
+    const double ed = P->data_eps;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < P->h; ++i) {
+        double s = 0;
+        for (int j = 0; j < P->w; ++j) {
+            const double t = e[(long)i * P->w + j];
+            s += l1 ? psi(t, ed) : t * t;
+        }
+        rows[i] = s;
+    }
+    double t = sum_rows(rows, P->h);
+    free(rows);
+    return t;
+}
+
 /* sum of squares of an LR image, rows first */
 static double sumsq_lr(const orc_problem *P, const double *e) {
     double *rows = (double *)calloc((size_t)P->h, sizeof(double));
@@ -259,7 +290,8 @@ static double sumsq_lr(const orc_problem *P, const double *e) {
     return t;
 }
 
-/* J(x) = sum_k ||A_k x - y_k||^2 + lambda R(x)        Eq. 9 with p = 2 (Eq. 6).
+/* J(x) = sum_k ||A_k x - y_k||^2 + lambda R(x)        Eq. 9 with p = 2 (Eq. 6),
+ * or with the L1 data term sum_k sum_i psi_d((A_k x - y_k)_i).
  * y holds the K frames back to back, each h x w row-major. */
 double orc_objective(const orc_problem *P, const double *x, const double *y) {
     const long m = (long)P->h * P->w;
@@ -268,13 +300,14 @@ double orc_objective(const orc_problem *P, const double *x, const double *y) {
     for (int k = 0; k < P->K; ++k) {
         orc_forward(P, k, x, e);
         for (long i = 0; i < m; ++i) e[i] -= y[k * m + i];
-        data += sumsq_lr(P, e);
+        data += data_value_lr(P, e);
     }
     free(e);
     return data + P->lambda * orc_reg_value(P, x);
 }
 
-/* g = grad J(x) = 2 sum_k A_k^T (A_k x - y_k) + lambda grad R(x); returns J(x). */
+/* g = grad J(x) = 2 sum_k A_k^T (A_k x - y_k) + lambda grad R(x)  (L2), or
+ * sum_k A_k^T psi_d'(A_k x - y_k) + lambda grad R(x)  (L1); returns J(x). */
 double orc_gradient(const orc_problem *P, const double *x, const double *y, double *g) {
     const long m = (long)P->h * P->w, n = (long)HRH(P) * HRW(P);
     double *e = (double *)malloc(sizeof(double) * m);
@@ -285,42 +318,75 @@ double orc_gradient(const orc_problem *P, const double *x, const double *y, doub
     for (int k = 0; k < P->K; ++k) {
         orc_forward(P, k, x, e);
         for (long i = 0; i < m; ++i) e[i] -= y[k * m + i];
-        data += sumsq_lr(P, e);
-        orc_adjoint(P, k, e, t);
-        for (long i = 0; i < n; ++i) g[i] += 2.0 * t[i];
+        data += data_value_lr(P, e);
+        if (P->data_norm == ORC_NORM_L1) {
+            for (long i = 0; i < m; ++i) e[i] = dpsi(e[i], P->data_eps);
+            orc_adjoint(P, k, e, t);
+            for (long i = 0; i < n; ++i) g[i] += t[i];
+        } else {
+            orc_adjoint(P, k, e, t);
+            for (long i = 0; i < n; ++i) g[i] += 2.0 * t[i];
+        }
     }
     free(e);
     free(t);
     return data + P->lambda * orc_reg_value(P, x);
 }
 
-/* out = H(x) p = 2 sum_k A_k^T A_k p + lambda H_R(x) p. */
-void orc_hessvec(const orc_problem *P, const double *x, const double *p, double *out) {
+/* out = H(x) p = 2 sum_k A_k^T A_k p + lambda H_R(x) p  (L2), or
+ * sum_k A_k^T diag(psi_d''(A_k x - y_k)) A_k p + lambda H_R(x) p  (L1; y is read only then). */
+void orc_hessvec(const orc_problem *P, const double *x, const double *y, const double *p, double *out) {
     const long m = (long)P->h * P->w, n = (long)HRH(P) * HRW(P);
     double *e = (double *)malloc(sizeof(double) * m);
+    double *ex = (double *)malloc(sizeof(double) * m);
     double *t = (double *)malloc(sizeof(double) * n);
+    const int l1 = P->data_norm == ORC_NORM_L1;
     orc_reg_hessvec(P, x, p, out);
     for (long i = 0; i < n; ++i) out[i] *= P->lambda;
     for (int k = 0; k < P->K; ++k) {
         orc_forward(P, k, p, e);
+        if (l1) {
+            orc_forward(P, k, x, ex);
+            for (long i = 0; i < m; ++i) e[i] *= d2psi(ex[i] - y[k * m + i], P->data_eps);
+        }
         orc_adjoint(P, k, e, t);
-        for (long i = 0; i < n; ++i) out[i] += 2.0 * t[i];
+        for (long i = 0; i < n; ++i) out[i] += (l1 ? 1.0 : 2.0) * t[i];
     }
     free(e);
+    free(ex);
     free(t);
 }
 
-/* p . H(x) p in closed form: 2 sum_k ||A_k p||^2 + lambda p . H_R(x) p. */
-double orc_curvature(const orc_problem *P, const double *x, const double *p) {
+/* p . H(x) p in closed form: 2 sum_k ||A_k p||^2 + lambda p . H_R(x) p  (L2), or
+ * sum_k sum_i psi_d''((A_k x - y_k)_i) (A_k p)_i^2 + lambda p . H_R(x) p  (L1). */
+double orc_curvature(const orc_problem *P, const double *x, const double *y, const double *p) {
     const long m = (long)P->h * P->w;
     double *e = (double *)malloc(sizeof(double) * m);
+    double *ex = (double *)malloc(sizeof(double) * m);
+    const int l1 = P->data_norm == ORC_NORM_L1;
     double data = 0.0;
     for (int k = 0; k < P->K; ++k) {
         orc_forward(P, k, p, e);
-        data += sumsq_lr(P, e);
+        if (l1) {
+            orc_forward(P, k, x, ex);
+            double *rows = (double *)calloc((size_t)P->h, sizeof(double));
+            for (int i = 0; i < P->h; ++i) {
+                double s = 0;
+                for (int j = 0; j < P->w; ++j) {
+                    const long o = (long)i * P->w + j;
+                    s += d2psi(ex[o] - y[k * m + o], P->data_eps) * e[o] * e[o];
+                }
+                rows[i] = s;
+            }
+            data += sum_rows(rows, P->h);
+            free(rows);
+        } else {
+            data += 2.0 * sumsq_lr(P, e);
+        }
     }
     free(e);
-    return 2.0 * data + P->lambda * orc_reg_curvature(P, x, p);
+    free(ex);
+    return data + P->lambda * orc_reg_curvature(P, x, p);
 }
 
 /* Multi-image interpolation (Sec. 4.1.1): every LR sample is placed at the HR pixel it was
@@ -405,7 +471,7 @@ int orc_scg(const orc_problem *P, const double *y, const double *x0, int iters, 
                 orc_gradient(P, xt, y, s);                      /* J'(x + sigma p) */
                 for (long i = 0; i < n; ++i) s[i] = (s[i] + r[i]) / sig;  /* J'(x) = -r */
             } else {
-                orc_hessvec(P, x, p, s);
+                orc_hessvec(P, x, y, p, s);
             }
             delta = dot(p, s, n);
         }

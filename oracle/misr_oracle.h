@@ -6,7 +6,9 @@
  *
  * Problem (Sec. 3.1):
  *   image formation   y_k = A_k x + noise,  A_k = D B M_k             (Eq. 1)
- *   data term         sum_k || A_k x - y_k ||_2^2                      (Eq. 6)
+ *   data term         sum_k || A_k x - y_k ||_2^2                      (Eq. 6, p = 2)
+ *                     or sum_k sum_i psi_d((A_k x - y_k)_i), psi_d(t) = sqrt(t^2 + eps_d^2) - eps_d,
+ *                     the L1 norm of the paper's experiments (Sec. 3.1) smoothed like the prior
  *   prior (BTV)       sum_d gamma(d) || x - S_d x ||_1,
  *                     d = (dx, dy), dx, dy in [0, w-1], gamma = alpha^(dx+dy)   (Eq. 8)
  *   objective         J(x) = data + lambda * prior                     (Eq. 9)
@@ -32,6 +34,7 @@
 
 enum { ORC_REG_BTV = 0, ORC_REG_TIKHONOV = 1 };
 enum { ORC_HV_EXACT = 0, ORC_HV_FD = 1 };
+enum { ORC_NORM_L2 = 0, ORC_NORM_L1 = 1 };
 
 typedef struct {
     int h, w;                 /* LR frame size (rows, cols) */
@@ -45,6 +48,8 @@ typedef struct {
     int btv_w;                /* BTV window w */
     double eps;               /* Charbonnier smoothing of |.| */
     int reg;                  /* ORC_REG_BTV or ORC_REG_TIKHONOV */
+    int data_norm;            /* ORC_NORM_L2 (default) or ORC_NORM_L1 */
+    double data_eps;          /* Charbonnier smoothing of the L1 data term (> 0) */
 } orc_problem;
 
 /* one row of the SCG trace per iteration (failed iterations included) */
@@ -66,6 +71,7 @@ extern "C" {
 int orc_init(orc_problem *P, int h, int w, int K, int f, const double *shifts_lr,
              const double *psf, int psf_size, double lambda, double btv_alpha, int btv_w,
              double eps, int reg);
+int orc_set_data_norm(orc_problem *P, int norm, double data_eps);
 int orc_threads(void);
 void orc_forward(const orc_problem *P, int k, const double *x, double *out);
 void orc_adjoint(const orc_problem *P, int k, const double *e, double *out);
@@ -75,8 +81,8 @@ void orc_reg_hessvec(const orc_problem *P, const double *x, const double *p, dou
 double orc_reg_curvature(const orc_problem *P, const double *x, const double *p);
 double orc_objective(const orc_problem *P, const double *x, const double *y);
 double orc_gradient(const orc_problem *P, const double *x, const double *y, double *g);
-void orc_hessvec(const orc_problem *P, const double *x, const double *p, double *out);
-double orc_curvature(const orc_problem *P, const double *x, const double *p);
+void orc_hessvec(const orc_problem *P, const double *x, const double *y, const double *p, double *out);
+double orc_curvature(const orc_problem *P, const double *x, const double *y, const double *p);
 void orc_shift_add(const orc_problem *P, const double *y, double *x0);
 void orc_log_convert(const unsigned short *counts, long n, double flat_field, double *y);
 int orc_scg(const orc_problem *P, const double *y, const double *x0, int iters, int hv_mode,

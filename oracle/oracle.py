@@ -16,6 +16,7 @@ MAXK = 64
 MAXPSF = 15
 REG_BTV, REG_TIKHONOV = 0, 1
 HV_EXACT, HV_FD = 0, 1
+NORM_L2, NORM_L1 = 0, 1
 
 
 class _Problem(C.Structure):
@@ -25,6 +26,7 @@ class _Problem(C.Structure):
         ("psf_size", C.c_int), ("psf", C.c_double * (MAXPSF * MAXPSF)),
         ("lambda_", C.c_double), ("btv_alpha", C.c_double), ("btv_w", C.c_int),
         ("eps", C.c_double), ("reg", C.c_int),
+        ("data_norm", C.c_int), ("data_eps", C.c_double),
     ]
 
 
@@ -50,6 +52,8 @@ def lib():
                                C.c_double, C.c_double, C.c_int, C.c_double, C.c_int]
         L.orc_init.restype = C.c_int
         L.orc_threads.restype = C.c_int
+        L.orc_set_data_norm.argtypes = [pp, C.c_int, C.c_double]
+        L.orc_set_data_norm.restype = C.c_int
         for name in ("orc_forward", "orc_adjoint"):
             getattr(L, name).argtypes = [pp, C.c_int, dp, dp]
         L.orc_reg_value.argtypes = [pp, dp]
@@ -62,8 +66,8 @@ def lib():
         L.orc_objective.restype = C.c_double
         L.orc_gradient.argtypes = [pp, dp, dp, dp]
         L.orc_gradient.restype = C.c_double
-        L.orc_hessvec.argtypes = [pp, dp, dp, dp]
-        L.orc_curvature.argtypes = [pp, dp, dp]
+        L.orc_hessvec.argtypes = [pp, dp, dp, dp, dp]
+        L.orc_curvature.argtypes = [pp, dp, dp, dp]
         L.orc_curvature.restype = C.c_double
         L.orc_shift_add.argtypes = [pp, dp, dp]
         L.orc_log_convert.argtypes = [C.POINTER(C.c_ushort), C.c_long, C.c_double, dp]
@@ -89,7 +93,7 @@ class Problem:
     """One MISR problem: K LR frames of h x w, magnification f, shifts (dx, dy) in LR px."""
 
     def __init__(self, h, w, f, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3,
-                 reg=REG_BTV):
+                 reg=REG_BTV, data_norm=NORM_L2, data_eps=0.0):
         self.h, self.w, self.f = int(h), int(w), int(f)
         self.K = len(shifts)
         self.H, self.W = self.f * self.h, self.f * self.w
@@ -101,6 +105,9 @@ class Problem:
                             float(eps), int(reg))
         if rc != 0:
             raise ValueError(f"orc_init failed ({rc})")
+        if lib().orc_set_data_norm(C.byref(self._p), int(data_norm), float(data_eps)) != 0:
+            raise ValueError("data norm: L2, or L1 with data_eps > 0")
+        self.data_norm = int(data_norm)
 
     @property
     def shifts_hr(self):
@@ -161,13 +168,23 @@ class Problem:
         J = lib().orc_gradient(C.byref(self._p), _d(self._x(x)), _d(self._y(y)), _d(g))
         return float(J), g
 
-    def hessvec(self, x, p):
+    def _y_or_null(self, y):
+        # the frames enter the Hessian only through the L1 data term's weights
+        if y is None:
+            assert self.data_norm == NORM_L2, "the L1 data term's Hessian needs the frames"
+            return None, None
+        y = self._y(y)
+        return y, _d(y)
+
+    def hessvec(self, x, p, y=None):
         out = np.empty((self.H, self.W))
-        lib().orc_hessvec(C.byref(self._p), _d(self._x(x)), _d(self._x(p)), _d(out))
+        keep, yp = self._y_or_null(y)
+        lib().orc_hessvec(C.byref(self._p), _d(self._x(x)), yp, _d(self._x(p)), _d(out))
         return out
 
-    def curvature(self, x, p):
-        return float(lib().orc_curvature(C.byref(self._p), _d(self._x(x)), _d(self._x(p))))
+    def curvature(self, x, p, y=None):
+        keep, yp = self._y_or_null(y)
+        return float(lib().orc_curvature(C.byref(self._p), _d(self._x(x)), yp, _d(self._x(p))))
 
     def shift_add(self, y):
         out = np.empty((self.H, self.W))

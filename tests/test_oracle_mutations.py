@@ -21,7 +21,12 @@ MUTANTS = {
     "dpsi_sign": ("if (eps > 0) return t / sqrt(t * t + eps * eps);", "if (eps > 0) return -t / sqrt(t * t + eps * eps);"),
     "d2psi_power": ("return eps * eps / (s * sqrt(s));", "return eps * eps / s;"),
     "grad_factor_2_dropped": ("for (long i = 0; i < n; ++i) g[i] += 2.0 * t[i];", "for (long i = 0; i < n; ++i) g[i] += t[i];"),
-    "hessvec_factor": ("for (long i = 0; i < n; ++i) out[i] += 2.0 * t[i];", "for (long i = 0; i < n; ++i) out[i] += t[i];"),
+    "hessvec_factor": ("for (long i = 0; i < n; ++i) out[i] += (l1 ? 1.0 : 2.0) * t[i];",
+                       "for (long i = 0; i < n; ++i) out[i] += (l1 ? 1.0 : 1.0) * t[i];"),
+    "l1_gradient_factor_2_kept": ("for (long i = 0; i < n; ++i) g[i] += t[i];", "for (long i = 0; i < n; ++i) g[i] += 2.0 * t[i];"),
+    "l1_hessian_weight_dropped": ("for (long i = 0; i < m; ++i) e[i] *= d2psi(ex[i] - y[k * m + i], P->data_eps);",
+                                  "for (long i = 0; i < m; ++i) e[i] *= 1.0;"),
+    "l1_value_squared": ("s += l1 ? psi(t, ed) : t * t;", "s += l1 ? t * t : t * t;"),
     "beta_fletcher_reeves": ("const double beta = (rr_new - rr_cross) / mu;", "const double beta = rr_new / dot(r, r, n);"),
     "lambda_not_reduced": ("if (Delta >= 0.75) lam = lam / 4.0;", "if (Delta >= 0.75) lam = lam / 2.0;"),
     "delta_not_scaled": ("delta += (lam - lam_bar) * pn2;", "delta += 0.0 * (lam - lam_bar) * pn2;"),

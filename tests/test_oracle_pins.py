@@ -382,3 +382,99 @@ def test_oracle_matches_committed_golden_trace(orc):
     for k, v in ref["trace"].items():
         np.testing.assert_allclose(tr[k], v, rtol=1e-9, atol=1e-300, err_msg=k)
     assert P.objective(x, y) == pytest.approx(ref["J_final"], rel=1e-12)
+
+
+# ------------------------------------------------------- L1 data term (Sec. 3.1, reading 1)
+
+def _l1_problem(orc, data_eps, lam=0.3, eps=0.1):
+    P = orc.Problem(7, 6, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.6), lam=lam, eps=eps,
+                    data_norm=orc.NORM_L1, data_eps=data_eps)
+    y = gen.random_field((P.K, P.h, P.w), 31, 0, 2)
+    return P, y
+
+
+def test_l1_objective_equals_dense_residual(orc):
+    """J(x) = sum_k sum_i psi_d((A_k x - y_k)_i) + lambda R(x), the residual from the dense
+    textbook matrices and R from the ramp closed form."""
+    h, w, f, lam, eps, data_eps = 4, 5, 2, 0.7, 1e-3, 0.05
+    shifts = gen.half_pixel_shifts()
+    psf = _asym_psf(21, 3)
+    P = orc.Problem(h, w, f, shifts, psf, lam=lam, eps=eps, data_norm=orc.NORM_L1, data_eps=data_eps)
+    A = dm.system_matrices(h, w, f, shifts, psf)
+    s = 0.21
+    x = s * np.tile(np.arange(P.W, dtype=np.float64), (P.H, 1))
+    y = gen.random_field((4, h, w), 22)
+    data = sum(_psi(float(t), data_eps) for k in range(4) for t in A[k] @ x.ravel() - y[k].ravel())
+    reg = sum(0.4 ** (dx + dy) * (P.H - dy) * (P.W - dx) * _psi(s * dx, eps)
+              for dy in range(3) for dx in range(3) if (dx, dy) != (0, 0))
+    assert P.objective(x, y) == pytest.approx(data + lam * reg, rel=1e-13)
+
+
+@pytest.mark.parametrize("data_eps,tol", [(0.1, 1e-7), (1e-2, 1e-6)])
+def test_l1_gradient_central_differences(orc, data_eps, tol):
+    """grad J = sum_k A_k^T psi_d'(A_k x - y_k) + lambda grad R against central differences."""
+    P, y = _l1_problem(orc, data_eps)
+    x = _distinct_levels(P, 3)
+    J0, g = P.gradient(x, y)
+    assert J0 == pytest.approx(P.objective(x, y), rel=1e-14)
+    hstep = 1e-6
+    fd = np.empty_like(x)
+    for i in range(P.H):
+        for j in range(P.W):
+            xp = x.copy(); xp[i, j] += hstep
+            xm = x.copy(); xm[i, j] -= hstep
+            fd[i, j] = (P.objective(xp, y) - P.objective(xm, y)) / (2 * hstep)
+    assert np.linalg.norm(fd - g) <= tol * np.linalg.norm(g)
+
+
+@pytest.mark.parametrize("data_eps", [0.1, 1e-2])
+def test_l1_hessvec_and_curvature_central_differences(orc, data_eps):
+    """H(x) p = sum_k A_k^T diag(psi_d'') A_k p + lambda H_R p against central differences of
+    the gradient; the closed-form curvature equals p.H p."""
+    P, y = _l1_problem(orc, data_eps)
+    x = _distinct_levels(P, 4)
+    p = gen.random_field((P.H, P.W), 9)
+    hstep = 1e-7
+    _, gp = P.gradient(x + hstep * p, y)
+    _, gm = P.gradient(x - hstep * p, y)
+    fd = (gp - gm) / (2 * hstep)
+    hv = P.hessvec(x, p, y)
+    assert np.linalg.norm(fd - hv) <= 2e-6 * np.linalg.norm(hv)
+    assert P.curvature(x, p, y) == pytest.approx(float(np.sum(p * hv)), rel=1e-12)
+
+
+def test_l1_tends_to_scaled_l2(orc):
+    """psi_d(t) = t^2 / (2 eps_d) + O(t^4 / eps_d^3): with a large eps_d the L1 data term, its
+    gradient and its curvature are the (independently pinned) L2 ones divided by 2 eps_d."""
+    big = 1e4
+    common = dict(lam=0.0, eps=0.1)
+    P1 = orc.Problem(7, 6, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.6), data_norm=orc.NORM_L1,
+                     data_eps=big, **common)
+    P2 = orc.Problem(7, 6, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.6), **common)
+    y = gen.random_field((4, 7, 6), 41, 0, 2)
+    x = gen.random_field((14, 12), 42, 0, 2)
+    p = gen.random_field((14, 12), 43)
+    J1, g1 = P1.gradient(x, y)
+    J2, g2 = P2.gradient(x, y)
+    assert 2 * big * J1 == pytest.approx(J2, rel=1e-7)
+    assert np.linalg.norm(2 * big * g1 - g2) <= 1e-7 * np.linalg.norm(g2)
+    assert 2 * big * P1.curvature(x, p, y) == pytest.approx(P2.curvature(x, p), rel=1e-7)
+
+
+def test_l1_scg_monotone_and_rejections_consistent(orc):
+    """SCG on the L1 objective: the accepted objective never rises, rejections are exactly
+    the steps whose trial objective is above the current one."""
+    P = orc.Problem(32, 32, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), lam=0.01, eps=1e-3,
+                    data_norm=orc.NORM_L1, data_eps=0.01)
+    xt = gen.phantom(64, 64, 7)
+    y = P.forward_all(xt) + gen.gaussian_noise((4, 32, 32), 0.01, 8)
+    x, tr = P.scg(y, P.shift_add(y), 40)
+    acc = tr["accept"] == 1
+    assert np.all(tr["delta"] > 0)
+    assert np.all((tr["J_trial"] <= tr["E"]) == acc)
+    E_next = np.where(acc, tr["J_trial"], tr["E"])
+    assert np.all(np.diff(np.concatenate([tr["E"][:1], E_next])) <= 0)
+    assert E_next[-1] < 0.5 * tr["E"][0]
+    with pytest.raises(ValueError):
+        orc.Problem(4, 4, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), data_norm=orc.NORM_L1,
+                    data_eps=0.0)
