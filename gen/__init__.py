@@ -11,6 +11,7 @@ from .inputs import (  # noqa: F401
     third_pixel_shifts,
     phase_shifts,
     gaussian_noise,
+    impulse_noise,
     poisson_counts,
     random_field,
     smooth_field,

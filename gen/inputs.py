@@ -114,6 +114,15 @@ def poisson_counts(line_integrals: np.ndarray, flat_field: float, seed: int) -> 
     return np.clip(c, 1, 65535).astype(np.uint16)
 
 
+def impulse_noise(shape, frac: float, amp: float, seed: int) -> np.ndarray:
+    """Sparse outliers (defective or saturated detector pixels): a fraction `frac` of the
+    samples, chosen at random, offset by +-amp; zero elsewhere."""
+    rng = _rng(seed)
+    hit = rng.uniform(size=shape) < frac
+    sign = np.where(rng.uniform(size=shape) < 0.5, -1.0, 1.0)
+    return np.where(hit, amp * sign, 0.0)
+
+
 def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     return _rng(seed).uniform(lo, hi, size=shape)
 

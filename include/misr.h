@@ -3,7 +3,8 @@
  *
  * The library solves, on one GPU, the MAP problem of Sec. 3.1 of the paper
  *     min_x  J(x) = sum_k || D B M_k x - y_k ||_2^2 + lambda * sum_d gamma(d) || x - S_d x ||_1
- * (Eq. 1 image formation, Eq. 6 data term, Eq. 8 BTV prior, Eq. 9 objective) with Moller's
+ * (Eq. 1 image formation, Eq. 6 data term, Eq. 8 BTV prior, Eq. 9 objective), or with the
+ * smoothed L1 data term of the paper's experiments (misr_desc.data_norm), with Moller's
  * scaled conjugate gradient (Sec. 3.1, Algorithm 1, Table 1), for K low-resolution (LR)
  * frames taken with known subpixel detector shifts (Sec. 3.2).
  *
@@ -80,7 +81,17 @@ typedef struct misr_desc {
                                 way.  misr_pass_probe needs MISR_F32. */
     int32_t tile_shape;      /* MISR_TILE_AUTO (0): the shape misr_autotune chose for this HR size
                                 in this process, else the default; or one of MISR_TILE_* */
+    int32_t data_norm;       /* MISR_NORM_L2 (0): the squared L2 data term of Eq. 6 above.
+                                MISR_NORM_L1: the L1 data term of the paper's experiments
+                                (Sec. 3.1), each residual t smoothed like the prior's |t|:
+                                sum_k sum_i psi_d((A_k x - y_k)_i), psi_d(t) = sqrt(t^2 +
+                                data_eps^2) - data_eps */
+    double data_eps;         /* MISR_NORM_L1: the smoothing data_eps, in [1e-15, 1e15];
+                                ignored for MISR_NORM_L2 */
 } misr_desc;
+
+/* data terms (misr_desc.data_norm) */
+enum { MISR_NORM_L2 = 0, MISR_NORM_L1 = 1 };
 
 /* Tile shapes of the fused pass (HR pixels per CTA tile; threads per CTA).  The paper has no
  * counterpart: its partitions are whole sub-images per GPU (Sec. 3.1). */
@@ -217,7 +228,7 @@ misr_status misr_debug_bounds(uint32_t *bits, int32_t *first);
  *   plan does not keep them), x_dev receives the image.  Asynchronous on stream unless stats is
  *   non-NULL, as misr_solve.
  * Errors: MISR_EINVAL (NULL arguments, too small a buffer, a checkpoint of another geometry,
- * storage type, state layout or version), MISR_ECUDA, and misr_solve's. */
+ * storage type, data term, state layout or version), MISR_ECUDA, and misr_solve's. */
 misr_status misr_state_bytes(misr_plan_t plan, size_t *bytes);
 misr_status misr_export_state(misr_plan_t plan, void *buf, size_t bytes);
 misr_status misr_import_state(misr_plan_t plan, const void *buf, size_t bytes);

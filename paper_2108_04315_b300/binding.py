@@ -19,6 +19,7 @@ MISR_F32, MISR_U16, MISR_BF16 = 0, 1, 2
 MISR_X0_ZERO, MISR_X0_SHIFT_ADD, MISR_X0_GIVEN = 0, 1, 2
 MISR_TILE_AUTO, MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64 = 0, 1, 2, 3
 MISR_N_TILE_SHAPES = 3
+MISR_NORM_L2, MISR_NORM_L1 = 0, 1
 MISR_TRACE_COLS = 10
 MISR_PASS_SUMS = 10
 TRACE_FIELDS = ("E", "J_trial", "alpha", "delta", "mu", "lam", "Delta", "pn2", "rn2", "accept")
@@ -32,7 +33,7 @@ class misr_desc(C.Structure):
         ("lambda_", C.c_double), ("btv_alpha", C.c_double), ("btv_w", C.c_int32),
         ("eps", C.c_double), ("iters", C.c_int32), ("x0_mode", C.c_int32),
         ("in_dtype", C.c_int32), ("flat_field", C.c_float), ("iterate_dtype", C.c_int32),
-        ("tile_shape", C.c_int32),
+        ("tile_shape", C.c_int32), ("data_norm", C.c_int32), ("data_eps", C.c_double),
     ]
 
 
@@ -307,7 +308,7 @@ def _stats_dict(st: misr_stats):
 # ---------------------------------------------------------------- torch convenience layer
 def make_desc(lr_h, lr_w, factor, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, iters=100,
               x0_mode=MISR_X0_SHIFT_ADD, in_dtype=MISR_F32, flat_field=40000.0, iterate_dtype=MISR_F32,
-              tile_shape=MISR_TILE_AUTO):
+              tile_shape=MISR_TILE_AUTO, data_norm=MISR_NORM_L2, data_eps=0.0):
     sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float32).reshape(-1))
     ps = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
     d = misr_desc()
@@ -319,6 +320,7 @@ def make_desc(lr_h, lr_w, factor, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3,
     d.iters, d.x0_mode, d.in_dtype = int(iters), int(x0_mode), int(in_dtype)
     d.flat_field, d.iterate_dtype = float(flat_field), int(iterate_dtype)
     d.tile_shape = int(tile_shape)
+    d.data_norm, d.data_eps = int(data_norm), float(data_eps)
     d._keep = (sh, ps)  # keep the host arrays alive while the descriptor is used
     return d
 

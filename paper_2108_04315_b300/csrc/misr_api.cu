@@ -113,6 +113,10 @@ static misr_status validate(const misr_desc *d) {
         return fail(MISR_EINVAL, "iterate_dtype must be MISR_F32 or MISR_BF16");
     if (d->tile_shape < MISR_TILE_AUTO || d->tile_shape > MISR_N_TILE_SHAPES)
         return fail(MISR_EINVAL, "tile_shape must be MISR_TILE_AUTO or a MISR_TILE_* shape");
+    if (d->data_norm != MISR_NORM_L2 && d->data_norm != MISR_NORM_L1)
+        return fail(MISR_EINVAL, "data_norm must be MISR_NORM_L2 or MISR_NORM_L1");
+    if (d->data_norm == MISR_NORM_L1 && !(d->data_eps >= 1e-15 && d->data_eps <= 1e15))
+        return fail(MISR_EINVAL, "data_eps must be in [1e-15, 1e15] for MISR_NORM_L1");
     return MISR_OK;
 }
 
@@ -156,10 +160,29 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <int S, bool B>
+// the pass kernel of shape S and variant V (bit 0 bf16 r and p, bit 1 the L1 data term), and
+// its dynamic shared memory
+template <int S, int V>
+constexpr auto pass_kernel() {
+    return scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], (V & 1) != 0, (V & 2) != 0>;
+}
+template <int S, int V>
+constexpr size_t pass_smem() { return ShapeGeo<S>::smem_bytes((V & 2) != 0); }
+template <typename F>
+auto with_variant(int v, F &&f) {
+    static_assert(N_VARIANTS == 4, "one case per compiled variant");
+    switch (v) {
+    case 0: return f(std::integral_constant<int, 0>());
+    case 1: return f(std::integral_constant<int, 1>());
+    case 2: return f(std::integral_constant<int, 2>());
+    default: return f(std::integral_constant<int, 3>());
+    }
+}
+
+template <int S, int V>
 static misr_status set_attrs_one() {
-    auto *k = scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], B>;
-    CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ShapeGeo<S>::SMEM_BYTES));
+    auto *k = pass_kernel<S, V>();
+    CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<S, V>()));
     CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     return MISR_OK;
 }
@@ -167,37 +190,42 @@ static misr_status set_attrs_one() {
 static misr_status set_pass_attrs() {
     static bool done = false;
     if (done) return MISR_OK;
-    for (int sh = 0; sh < N_SHAPES; ++sh) {
-        misr_status r = with_shape(sh, [](auto S) {
-            misr_status q = set_attrs_one<decltype(S)::value, false>();
-            return q != MISR_OK ? q : set_attrs_one<decltype(S)::value, true>();
-        });
-        if (r != MISR_OK) return r;
-    }
+    for (int sh = 0; sh < N_SHAPES; ++sh)
+        for (int v = 0; v < N_VARIANTS; ++v) {
+            misr_status r = with_shape(sh, [v](auto S) {
+                return with_variant(v, [](auto V) { return set_attrs_one<decltype(S)::value, decltype(V)::value>(); });
+            });
+            if (r != MISR_OK) return r;
+        }
     done = true;
     return MISR_OK;
 }
 
-// CTAs of the fused pass resident on the whole GPU, per shape
-static int resident_ctas(int shape) {
-    static int cached[N_SHAPES] = {-1, -1, -1};
-    if (cached[shape] >= 0) return cached[shape];
+// CTAs of the fused pass resident on the whole GPU, per shape and data term (the L1 variant
+// takes more shared memory)
+static int resident_ctas(int shape, bool l1) {
+    static int cached[N_SHAPES][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
+    if (cached[shape][l1] >= 0) return cached[shape][l1];
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     with_shape(shape, [&](auto S) {
         constexpr int s = decltype(S)::value;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scg_pass_kernel<SHAPE_TH[s], SHAPE_TW[s], SHAPE_NT[s], false>,
-                                                      SHAPE_NT[s], ShapeGeo<s>::SMEM_BYTES);
+        if (l1)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<s, 2>(), SHAPE_NT[s], pass_smem<s, 2>());
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<s, 0>(), SHAPE_NT[s], pass_smem<s, 0>());
         return 0;
     });
     cudaGetLastError();
-    cached[shape] = sms * per_sm;
-    return cached[shape];
+    cached[shape][l1] = sms * per_sm;
+    return cached[shape][l1];
 }
 
 // persistent grid: one CTA per resident slot, at most one per tile
-static int pass_grid(int shape, int n_tiles) { return std::max(1, std::min(n_tiles, resident_ctas(shape))); }
+static int pass_grid(int shape, bool l1, int n_tiles) {
+    return std::max(1, std::min(n_tiles, resident_ctas(shape, l1)));
+}
 
 static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double beta, cudaStream_t s) {
     return launch_pass_raw(p->dprob, p->dtile, p->segs, p->dgroup, p->hp.n_groups, p->work, mode, alpha, beta, s);
@@ -220,11 +248,11 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
                                  std::vector<int2> &tiles, std::vector<int2> &groups, PassSegs &segs) {
     segs = PassSegs{};
     for (int sh = 0; sh < N_SHAPES; ++sh)
-        for (int b = 0; b < 2; ++b)
+        for (int v = 0; v < N_VARIANTS; ++v)
             for (size_t i = 0; i < recs.size(); ++i)
-                if (recs[i]->shape == sh && (recs[i]->rp_bf16 != 0) == (b == 1)) {
+                if (recs[i]->shape == sh && pass_variant(*recs[i]) == v) {
                     append_tiles(*recs[i], idx[i], tiles);
-                    segs.n[sh][b] += recs[i]->n_tiles;
+                    segs.n[sh][v] += recs[i]->n_tiles;
                 }
     for (size_t i = 0; i < recs.size(); ++i)
         for (int g = 0; g < recs[i]->n_groups; ++g) groups.push_back(make_int2(idx[i], g));
@@ -242,6 +270,12 @@ static int pick_shape(const misr_desc &d) {
     for (auto &e : g_tuned)
         if (e.first.first == H && e.first.second == W) return e.second;
     return DEFAULT_SHAPE;
+}
+
+// The data term of a descriptor (checked by check_desc).
+static void set_data_norm(DevProblem &hp, const misr_desc &d) {
+    hp.l1 = d.data_norm == MISR_NORM_L1;
+    hp.data_eps = hp.l1 ? (float)d.data_eps : 0.f;
 }
 
 // Tile grid of a shape; the TMA maps of the workspace images with that shape's boxes.
@@ -300,20 +334,17 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
     if (r != MISR_OK) return r;
     int off = 0;
     for (int sh = 0; sh < N_SHAPES; ++sh)
-        for (int b = 0; b < 2; ++b) {
-            const int n = segs.n[sh][b];
+        for (int v = 0; v < N_VARIANTS; ++v) {
+            const int n = segs.n[sh][v];
             if (n <= 0) continue;
             const int2 *t = tiles + off;
             off += n;
             CK(with_shape(sh, [&](auto S) {
-                constexpr int k = decltype(S)::value;
-                constexpr int TH = SHAPE_TH[k], TW = SHAPE_TW[k], NT = SHAPE_NT[k];
-                const size_t smem = ShapeGeo<k>::SMEM_BYTES;
-                if (b)
-                    return launch_pdl(scg_pass_kernel<TH, TW, NT, true>, pass_grid(k, n), NT, smem, s, probs, t, n,
-                                      work, mode, alpha, beta);
-                return launch_pdl(scg_pass_kernel<TH, TW, NT, false>, pass_grid(k, n), NT, smem, s, probs, t, n, work,
-                                  mode, alpha, beta);
+                return with_variant(v, [&](auto V) {
+                    constexpr int k = decltype(S)::value, vv = decltype(V)::value;
+                    return launch_pdl(pass_kernel<k, vv>(), pass_grid(k, (vv & 2) != 0, n), SHAPE_NT[k],
+                                      pass_smem<k, vv>(), s, probs, t, n, work, mode, alpha, beta);
+                });
             }));
         }
     CK(launch_pdl(reduce_kernel, n_groups, 32, 0, s, probs, groups, mode));
@@ -399,6 +430,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     s = psf_taps(desc, hp.hy, hp.hx);
     if (s != MISR_OK) return s;
     hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
+    set_data_norm(hp, d);
     double eps_pairs = 0;
     for (int dy = 0; dy < BTV_W; ++dy)
         for (int dx = 0; dx < BTV_W; ++dx) {
@@ -789,7 +821,7 @@ misr_status misr_debug_bounds(uint32_t *bits, int32_t *first) {
 // ---- checkpoint and resume
 namespace {
 struct CkptHeader {
-    uint32_t magic, version, H, W, bf16, state_bytes, reserved[2];
+    uint32_t magic, version, H, W, bf16, state_bytes, l1, reserved;
 };
 static_assert(sizeof(CkptHeader) == 32, "checkpoint header");
 constexpr uint32_t CKPT_MAGIC = 0x4353524du, CKPT_VERSION = 1u;
@@ -815,7 +847,7 @@ misr_status misr_export_state(misr_plan_t p, void *buf, size_t bytes) {
     const size_t W = p->hp.W, H = p->hp.H, pitch = p->hp.pitch, rp = p->hp.rp_bf16 ? 2 : 4;
     char *out = static_cast<char *>(buf);
     CkptHeader h{CKPT_MAGIC, CKPT_VERSION, (uint32_t)H, (uint32_t)W, (uint32_t)p->hp.rp_bf16, (uint32_t)sizeof(ScgState),
-                 {0u, 0u}};
+                 (uint32_t)p->hp.l1, 0u};
     std::memcpy(out, &h, sizeof h);
     std::memcpy(out + sizeof h, &st, sizeof st);
     char *planes = out + sizeof h + sizeof st;
@@ -834,8 +866,8 @@ misr_status misr_import_state(misr_plan_t p, const void *buf, size_t bytes) {
     std::memcpy(&h, buf, sizeof h);
     if (h.magic != CKPT_MAGIC || h.version != CKPT_VERSION) return fail(MISR_EINVAL, "not a checkpoint of this version");
     if (h.H != (uint32_t)p->hp.H || h.W != (uint32_t)p->hp.W || h.bf16 != (uint32_t)p->hp.rp_bf16 ||
-        h.state_bytes != (uint32_t)sizeof(ScgState))
-        return fail(MISR_EINVAL, "checkpoint of another geometry, storage type or state layout");
+        h.state_bytes != (uint32_t)sizeof(ScgState) || h.l1 != (uint32_t)p->hp.l1)
+        return fail(MISR_EINVAL, "checkpoint of another geometry, storage type, data term or state layout");
     if (bytes < ckpt_bytes(p)) return fail(MISR_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", bytes, ckpt_bytes(p));
     DeviceGuard g(p->device);
     CK(cudaDeviceSynchronize());
@@ -999,6 +1031,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
     misr_status s = psf_taps(&d, hp.hy, hp.hx);
     if (s != MISR_OK) return s;
     hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
+    set_data_norm(hp, d);
     double eps_pairs = 0;
     for (int dy = 0; dy < BTV_W; ++dy)
         for (int dx = 0; dx < BTV_W; ++dx) {

@@ -147,11 +147,16 @@ struct Geo {
     static constexpr int RPS = XH * XW;                  // bf16 r and p boxes (two halves)
     static constexpr int FLOATS = 3 * XH * XW + EH * EW + GH * GW + HS;
     static_assert(RPS <= GH * GW + HS, "the bf16 boxes are staged in the GB and HS area");
+    static_assert(FLOATS % 4 == 0, "the owned-residual buffer after the tile buffers is 16-byte aligned");
     static_assert(((3 * XH * XW + EH * EW) * 4) % 128 == 0 && (3 * XH * XW * 4) % 128 == 0 &&
                       (XH * XW * 4) % 128 == 0 && (XH * XW * 2) % 128 == 0,
                   "TMA destinations must stay 128-byte aligned");
     static constexpr size_t TMA_BYTES = sizeof(float) * (3 * XH * XW + EH * EW);
     static constexpr size_t SMEM_BYTES = 128 /*align slack*/ + sizeof(float) * FLOATS + TH * TW + 64;
+    // the L1 data term keeps the owned residuals (TH x TW floats) after the tile buffers
+    static constexpr size_t EO_FLOATS = TH * TW;
+    static constexpr size_t SMEM_BYTES_L1 = SMEM_BYTES + sizeof(float) * EO_FLOATS;
+    static constexpr size_t smem_bytes(bool l1) { return l1 ? SMEM_BYTES_L1 : SMEM_BYTES; }
 };
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -258,7 +263,10 @@ struct PassAcc {
 };
 
 // per-problem constants staged in shared memory at CTA start
-enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_FMAG = 30, C_IEPS2 = 31, C_N = 32 };
+enum {
+    C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_FMAG = 30, C_IEPS2 = 31,
+    C_DEPS = 32, C_DEPS2 = 33, C_N = 34   // C_DEPS*: the L1 data term's smoothing and its square
+};
 
 // ---------------------------------------------------------------------------------------
 // Body of the fused pass on one tile.  BORDER: the tile's halo reaches outside the image, so
@@ -273,8 +281,11 @@ enum { C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_
 //   I3 BTV (the rest) + B2             I4 C1 (adjoint horizontal blur)
 //   I5 C2 + r'                         I6 horizontal blurs of r' and p
 //   I7 curvature forms (owned)
-template <int TH, int TW, int NT, bool BORDER, bool RPB, typename Hook>
-__device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsigned char *smp, const float *cs,
+// L1: the smoothed L1 data term.  B2 then keeps the owned residuals e' in EO and leaves
+// psi_d'(e') in the residual box for the adjoint, the gradient's data part has factor 1
+// instead of 2, and the curvature forms weight each sample by psi_d''(e').
+template <int TH, int TW, int NT, bool BORDER, bool RPB, bool L1, typename Hook>
+__device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float *EO, unsigned char *smp, const float *cs,
                                           uint64_t *ybar, uint32_t yphase, int y0, int x0, float alpha,
                                           float beta, float *Xn,
                                           float *Rn, float *Pn, PassAcc &A, Hook &&hook) {
@@ -297,6 +308,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
     const int H = P.H, W = P.W, f = P.f, pitch = P.pitch;
     const float eps2 = cs[C_EPS2], lambda = cs[C_LAMBDA];
     const unsigned fmag = __float_as_uint(cs[C_FMAG]);
+    constexpr float DSCALE = L1 ? 1.f : 2.f;   // d/de of the data term's e^2 (L2) or psi_d(e) (L1)
 
     constexpr int N_A = XH * XW / 4, N_B1 = XH * EW / 4, N_B2 = EH * EW / 4, N_C1 = EH * GW / 4;
     constexpr int N_C2 = GH * GW / 4, N_HP = CH * CW / 4, N_HR = CH * CW / 4, N_E = TH * TW / 4;
@@ -379,7 +391,8 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         }
         st4v(HS + r * EW + e, out);
     };
-    // B2: vertical blur -> Z, residual E = Z - Y (0 where Y is NaN: unsampled or outside)
+    // B2: vertical blur -> Z, residual E = Z - Y (0 where Y is NaN: unsampled or outside); with
+    // the L1 term the box keeps psi_d'(E) = E / sqrt(E^2 + eps_d^2) and EO the owned E
     auto item_B2 = [&](int it) {
         const int n = it / (EW / 4), e = 4 * (it - n * (EW / 4));
         if (!MISR_IN_BOUNDS(n >= 0 && n < EH && e + 3 < EW, BC_B2, n, e)) return;
@@ -404,7 +417,20 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
             ev[j] = smp_ok ? zz[j] - yv[j] : 0.f;
             sbits |= (smp_ok ? 1u : 0u) << (8 * j);
         }
-        if (own) {
+        if constexpr (L1) {
+            const float deps = cs[C_DEPS], deps2 = cs[C_DEPS2];
+            if (own) {
+                *reinterpret_cast<unsigned int *>(smp + (n - 4) * TW + e - 4) = sbits;
+                st4v(EO + (n - 4) * TW + e - 4, ev);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float q = fmaf(ev[j], ev[j], deps2), rs = rsqrt_ftz(q);
+                // psi_d(e) = sqrt(e^2 + eps_d^2) - eps_d, as e^2 / (sqrt(e^2 + eps_d^2) + eps_d)
+                if (own) A.jd += __fdividef(ev[j] * ev[j], fmaf(q, rs, deps));
+                ev[j] *= rs;
+            }
+        } else if (own) {
             *reinterpret_cast<unsigned int *>(smp + (n - 4) * TW + e - 4) = sbits;
 #pragma unroll
             for (int j = 0; j < 4; ++j) A.jd = fmaf(ev[j], ev[j], A.jd);
@@ -538,8 +564,9 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         const float2 g0 = f2sub(acc[0], acb[0]), g1 = f2sub(acc[1], acb[1]);
         st4(GB + n * GW + g, make_float4(g0.x, g0.y, g1.x, g1.y));
     };
-    // C2 + r': adjoint vertical blur 2 B^T E, then r' = -(2 B^T E + lambda g_BTV) in place of
-    // the BTV gradient; zero outside the image; owned pixels go to HBM with their sums
+    // C2 + r': adjoint vertical blur 2 B^T E (B^T psi_d'(E) with the L1 term), then
+    // r' = -(2 B^T E + lambda g_BTV) in place of the BTV gradient; zero outside the image; owned
+    // pixels go to HBM with their sums
     auto item_C2r = [&](int it) {
         int n, g;
         item_rc<GH, GW / 4>(it, n, g);
@@ -549,7 +576,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
         for (int a = -2; a <= 2; ++a) {
             const float4 v = ld4(HS + (n + 2 + a) * GW + g);
-            const float2 h = bc2((BORDER && !adj_tap_ok(u, a, f, fmag)) ? 0.f : 2.f * cs[C_HY + a + 2]);
+            const float2 h = bc2((BORDER && !adj_tap_ok(u, a, f, fmag)) ? 0.f : DSCALE * cs[C_HY + a + 2]);
             s2[0] = f2fma(h, make_float2(v.x, v.y), s2[0]);
             s2[1] = f2fma(h, make_float2(v.z, v.w), s2[1]);
         }
@@ -632,7 +659,8 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
         const int n = it / (TW / 4), o = 4 * (it - n * (TW / 4));
         if (!MISR_IN_BOUNDS(n >= 0 && n < TH && o + 3 < TW, BC_E, n, o)) return;
         const int gy = y0 + n;
-        // data part 2 (B v)(c) (B w)(c) at sampled c, and J_data(x') - J_data(x)
+        // data part 2 (B v)(c) (B w)(c) at sampled c (psi_d''(e'(c)) (B v)(c) (B w)(c) with the L1
+        // term), and J_data(x') - J_data(x)
         {
             float2 zr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             float2 zp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -647,7 +675,7 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
                 zp[0] = f2fma(h, make_float2(vp.x, vp.y), zp[0]);
                 zp[1] = f2fma(h, make_float2(vp.z, vp.w), zp[1]);
             }
-            const float4 ev = ld4(YB + (n + 4) * EW + o + 4);
+            const float4 ev = L1 ? ld4(EO + n * TW + o) : ld4(YB + (n + 4) * EW + o + 4);
             const unsigned int sbits = *reinterpret_cast<const unsigned int *>(smp + n * TW + o);
             const float2 msk[2] = {make_float2((sbits & 0xffu) ? 1.f : 0.f, (sbits & 0xff00u) ? 1.f : 0.f),
                                    make_float2((sbits & 0xff0000u) ? 1.f : 0.f, (sbits & 0xff000000u) ? 1.f : 0.f)};
@@ -656,15 +684,34 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, unsign
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const float2 zrm = f2mul(zr[h], msk[h]), zpm = f2mul(zp[h], msk[h]);
-                a2 = f2fma(zrm, zrm, a2);
-                b2 = f2fma(zrm, zpm, b2);
-                c2 = f2fma(zpm, zpm, c2);
                 const float2 azp = f2mul(bc2(alpha), zpm);
-                d2 = f2fma(azp, f2sub(f2mul(bc2(2.f), e2[h]), azp), d2);
+                // e'^2 - e^2 = alpha (B p) (2 e' - alpha (B p)), e the residual at x = x' - alpha p
+                if constexpr (L1) {
+                    // psi_d''(e') = eps_d^2 / S(e')^3, S(t) = sqrt(t^2 + eps_d^2); and
+                    // psi_d(e') - psi_d(e) = (e'^2 - e^2) / (S(e') + S(e))
+                    const float2 dd2 = bc2(cs[C_DEPS2]);
+                    const float2 q1 = f2fma(e2[h], e2[h], dd2), r1 = f2rsqrt(q1);
+                    const float2 w = f2mul(dd2, f2mul(r1, f2mul(r1, r1)));
+                    const float2 eb = f2sub(e2[h], azp);
+                    const float2 q0 = f2fma(eb, eb, dd2), r0 = f2rsqrt(q0);
+                    const float2 ss = f2fma(q1, r1, f2mul(q0, r0));
+                    const float2 wr = f2mul(w, zrm), wp = f2mul(w, zpm);
+                    a2 = f2fma(wr, zrm, a2);
+                    b2 = f2fma(wr, zpm, b2);
+                    c2 = f2fma(wp, zpm, c2);
+                    const float2 de2 = f2mul(azp, f2sub(f2mul(bc2(2.f), e2[h]), azp));
+                    d2.x += __fdividef(de2.x, ss.x);
+                    d2.y += __fdividef(de2.y, ss.y);
+                } else {
+                    a2 = f2fma(zrm, zrm, a2);
+                    b2 = f2fma(zrm, zpm, b2);
+                    c2 = f2fma(zpm, zpm, c2);
+                    d2 = f2fma(azp, f2sub(f2mul(bc2(2.f), e2[h]), azp), d2);
+                }
             }
-            A.a += 2.f * (a2.x + a2.y);
-            A.b += 2.f * (b2.x + b2.y);
-            A.c += 2.f * (c2.x + c2.y);
+            A.a += DSCALE * (a2.x + a2.y);
+            A.b += DSCALE * (b2.x + b2.y);
+            A.c += DSCALE * (c2.x + c2.y);
             A.dj += d2.x + d2.y;
         }
         // prior part: lambda sum_d gamma_d psi''(t_d) (dv_d)(dw_d) over valid pairs, with
@@ -970,10 +1017,11 @@ __device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_
 
 // The fused SCG pass, persistent: one CTA per resident slot takes tiles (problem, tile) from
 // the launch's tile list until it runs out; the problems of one launch share the storage type
-// of r and p (RPB: bf16).  The last thread schedules the tiles and issues their loads; warp 0
-// writes each tile's sums, which reduce_kernel combines after the pass.  `work` (two counters,
-// zero at launch) is the launch's tile counter; the last CTA to finish zeroes it again.
-template <int TH, int TW, int NT, bool RPB>
+// of r and p (RPB: bf16) and the data term (L1: smoothed L1).  The last thread schedules the
+// tiles and issues their loads; warp 0 writes each tile's sums, which reduce_kernel combines
+// after the pass.  `work` (two counters, zero at launch) is the launch's tile counter; the last
+// CTA to finish zeroes it again.
+template <int TH, int TW, int NT, bool RPB, bool L1>
 __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProblem *__restrict__ probs,
                                                          const int2 *__restrict__ tiles, int n_tiles,
                                                          unsigned *work, int mode, double probe_alpha,
@@ -984,7 +1032,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
     // 128-byte aligned tile buffers (TMA destinations), derived from the shared array by
     // pointer arithmetic so that the accesses stay shared-memory accesses
     float *sm = reinterpret_cast<float *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
-    unsigned char *smp = reinterpret_cast<unsigned char *>(sm + Gm::FLOATS);
+    float *EO = L1 ? sm + Gm::FLOATS : nullptr;   // 16-byte aligned (FLOATS is a multiple of 4)
+    unsigned char *smp = reinterpret_cast<unsigned char *>(sm + Gm::FLOATS + (L1 ? Gm::EO_FLOATS : 0));
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float cs[C_N];
     __shared__ float red[NWARP][NPART];
@@ -1029,6 +1078,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
                 cs[C_EPS2] = P.eps2;
                 cs[C_IEPS2] = 1.f / P.eps2;
                 cs[C_FMAG] = __uint_as_float(P.f > 1 ? (unsigned)((0x100000000ull + P.f - 1) / P.f) : 0u);
+                cs[C_DEPS] = P.data_eps;
+                cs[C_DEPS2] = P.data_eps * P.data_eps;
             }
         }
         if (tid == SCHED_TID && sched.next < n_tiles) cp_async_8(&sched.wt_pre, tiles + sched.next);
@@ -1076,10 +1127,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
             const int y0 = ti.y0, x0 = ti.x0;
             const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
             if (border)
-                y_late = pass_tile<TH, TW, NT, true, RPB>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
+                y_late = pass_tile<TH, TW, NT, true, RPB, L1>(P, sm, EO, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
                                                      ti.Rn, ti.Pn, A, hook);
             else
-                y_late = pass_tile<TH, TW, NT, false, RPB>(P, sm, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
+                y_late = pass_tile<TH, TW, NT, false, RPB, L1>(P, sm, EO, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
                                                       ti.Xn, ti.Rn, ti.Pn, A, hook);
         }
 

@@ -45,17 +45,21 @@ misr_status check_desc(const misr_desc &d);
 // of every problem named must be listed exactly once.  `work`: the launch's tile counter (two
 // unsigned ints, zero before the first launch; every launch leaves them zero).  Launches that
 // share a `work` must be stream-ordered.
-// Tiles per pass kernel instantiation: the tile list holds segment (shape 0, float r/p),
-// (shape 0, bf16 r/p), (shape 1, float), ... in that order, n[shape][bf16] tiles each; one pass
-// launch per non-empty segment.
+// Tiles per pass kernel instantiation: the tile list holds segment (shape 0, variant 0),
+// (shape 0, variant 1), ..., (shape 1, variant 0), ... in that order, n[shape][variant] tiles
+// each (variant: bit 0 bf16 r and p, bit 1 the L1 data term); one pass launch per non-empty
+// segment.
 struct PassSegs {
-    int n[misr::N_SHAPES][2] = {};
+    int n[misr::N_SHAPES][misr::N_VARIANTS] = {};
     int total() const {
         int t = 0;
-        for (auto &a : n) t += a[0] + a[1];
+        for (auto &a : n)
+            for (int v : a) t += v;
         return t;
     }
 };
+// the pass kernel variant of a problem
+inline int pass_variant(const misr::DevProblem &p) { return (p.rp_bf16 ? 1 : 0) | (p.l1 ? 2 : 0); }
 misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, const PassSegs &segs,
                             const int2 *groups, int n_groups, unsigned *work, int mode, double alpha, double beta,
                             cudaStream_t s);

@@ -3,6 +3,8 @@
 //
 // Model (Sec. 3.1 of the paper): y_k = D B M_k x (Eq. 1), J(x) = sum_k ||A_k x - y_k||^2 +
 // lambda * BTV(x) (Eq. 6, 8, 9), solved with Moller's scaled conjugate gradient (Algorithm 1).
+// The L1 data term of the paper's experiments replaces ||e||^2 by sum_i psi_d(e_i),
+// psi_d(t) = sqrt(t^2 + data_eps^2) - data_eps.
 //
 // Layout of the data term on the HR grid.  Every frame k is shifted by an integer HR offset
 // t_k in [0, f-1]^2, so its samples sit at HR pixels c = (f i + t_y, f j + t_x), and the
@@ -38,6 +40,9 @@ constexpr int N_SHAPES = 3;
 constexpr int SHAPE_TH[N_SHAPES] = {32, 32, 16};
 constexpr int SHAPE_TW[N_SHAPES] = {64, 32, 64};
 constexpr int SHAPE_NT[N_SHAPES] = {512, 256, 256};
+// Compiled variants of the fused pass per shape: bit 0 r and p stored as bf16, bit 1 the
+// smoothed L1 data term.
+constexpr int N_VARIANTS = 4;
 
 // partial sums of one pass (FP64)
 enum { P_JD = 0, P_DJD, P_JB, P_RR, P_RRX, P_PR, P_PP, P_A, P_B, P_C };
@@ -67,10 +72,11 @@ struct DevProblem {
     int H, W, pitch, f, h, w, K;
     int tiles_x, tiles_y, n_tiles, iters;
     int rp_bf16;                                  // r and p stored as bf16 (x stays float)
+    int l1;                                       // data term: 0 squared L2, 1 smoothed L1
     int shape, tile_h, tile_w;                    // tile shape (index into SHAPE_*) and its size
     int wait_tries;                               // polls before a tile load is reported late
     float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];  // separable PSF, h(a, b) = hy[a+R] hx[b+R]
-    float lambda, eps, eps2, pad1;
+    float lambda, eps, eps2, data_eps;            // data_eps: the L1 data term's smoothing
     float gamma[BTV_W * BTV_W];                   // gamma(dx, dy) at [dy * BTV_W + dx]
     double eps_pairs;                             // eps * sum_d gamma_d * #pairs_d
     float *X[2], *Rv[2], *Pv[2];                  // x, r (double buffered), p (double buffered);

@@ -42,6 +42,12 @@ def run(lib_path):
                 plan = B.Plan(h, w, f, shifts, psf, iters=4, tile_shape=shape, iterate_dtype=dt)
                 x, _ = plan.solve(y)
                 out[f"{name}_s{shape}_d{dt}"] = x.cpu().numpy()
+                # the L1 data term's variant (its owned-residual buffer)
+                p1 = B.Plan(h, w, f, shifts, psf, iters=4, tile_shape=shape, iterate_dtype=dt,
+                            data_norm=B.MISR_NORM_L1, data_eps=0.05)
+                x1, _ = p1.solve(y)
+                out[f"{name}_s{shape}_d{dt}_l1"] = x1.cpu().numpy()
+                p1.close()
                 if dt == B.MISR_F32 and shape == 2:
                     J, g = plan.gradient(y, x)
                     out[f"{name}_grad"] = g.cpu().numpy()

@@ -70,6 +70,10 @@ def _desc(**kw):
     (dict(iters=-1), "EINVAL"),
     (dict(in_dtype=7), "EINVAL"),
     (dict(iterate_dtype=1), "EINVAL"),                            # u16 is an input type only
+    (dict(data_norm=2), "EINVAL"),
+    (dict(data_norm=1, data_eps=0.0), "EINVAL"),                  # the L1 term needs eps_d > 0
+    (dict(data_norm=1, data_eps=1e20), "EINVAL"),
+    (dict(data_norm=1, data_eps=float("nan")), "EINVAL"),
 ])
 def test_invalid_descriptor_rejected_on_host(L, kw, status):
     from paper_2108_04315_b300 import binding
