@@ -160,27 +160,27 @@ def make_inputs(plan, wl, device):
     return xt, y
 
 
-L1_DATA_EPS = 0.01   # smoothing of the L1 data term: the frames' noise sigma
-
-
-def measure_l1(args, wl, shifts, psf, tuned, y, x, stream, dist, device, peak):
-    """The same workload with the smoothed L1 data term (the paper's experiments): solve rate
-    and per-pass time, timed as the headline (K solves of 100 and of 0 iterations, CUDA events
-    on the solve's stream)."""
+def measure_variant(args, wl, shifts, psf, tuned, xt, stream, dist, device, peak, iters, y=None, **kw):
+    """The headline geometry solved with other model options (kw: Plan arguments): solve rate
+    and per-pass time, timed as the headline (K solves of `iters` and of 0 iterations, CUDA
+    events on the solve's stream).  Frames: y, else A x_true + N(0, 0.01^2) with this model's A."""
     import torch
-    from paper_2108_04315_b300.binding import MISR_NORM_L1, Plan
+    from paper_2108_04315_b300.binding import Plan
     H, W = wl["f"] * wl["h"], wl["f"] * wl["w"]
-    kw = dict(lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, tile_shape=tuned, data_norm=MISR_NORM_L1,
-              data_eps=L1_DATA_EPS)
-    p1 = Plan(wl["h"], wl["w"], wl["f"], shifts, psf, iters=wl["iters"], **kw)
+    kw = dict(dict(lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, tile_shape=tuned), **kw)
+    p1 = Plan(wl["h"], wl["w"], wl["f"], shifts, psf, iters=iters, **kw)
     p0 = Plan(wl["h"], wl["w"], wl["f"], shifts, psf, iters=0, **kw)
+    if y is None:
+        y = p1.forward(xt)
+        y += torch.from_numpy(gen.gaussian_noise(tuple(y.shape), 0.01, wl["seed"] + 1).astype(np.float32)).to(device)
+    x = torch.empty((H, W), dtype=torch.float32, device=device)
     for _ in range(max(args.warmup, 3)):
         p1.solve(y, x, stats=False)
         p0.solve(y, x, stats=False)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     ev[0].record(stream)
     for _ in range(args.steps):
         p1.solve(y, x, stats=False)
@@ -190,17 +190,76 @@ def measure_l1(args, wl, shifts, psf, tuned, y, x, stream, dist, device, peak):
     ev[2].record(stream)
     ev[2].synchronize()
     ms1, ms0 = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    pass_ms = max((ms1 - ms0) / args.steps / wl["iters"], 1e-9)
+    pass_ms = max((ms1 - ms0) / args.steps / max(iters, 1), 1e-9)
     rate, _ = job_rate(args.steps, ms1 / 1e3, dist, device)
-    st = p1.solve(y, x, stats=True)[1]
+    xs, st = p1.solve(y, x, stats=True)
+    err = float(torch.linalg.vector_norm(xs - xt) / torch.linalg.vector_norm(xt))
     p1.close()
     p0.close()
     achieved = PASS_BYTES_PER_PX * H * W / (pass_ms * 1e-3) / 1e9
-    return {"value": rate, "unit": UNIT, "data_norm": "L1, psi_d(t) = sqrt(t^2 + eps_d^2) - eps_d",
-            "data_eps": L1_DATA_EPS, "ms_per_pass": pass_ms, "achieved_gbs": achieved, "frac": achieved / peak,
+    return {"value": rate, "unit": UNIT, "iters": iters, "ms_per_pass": pass_ms, "achieved_gbs": achieved,
+            "frac": achieved / peak, "image_rel_error_vs_phantom": err,
             "solve": {"J_final": st["J_final"], "accepted": st["accepted"], "iters_done": st["iters_done"]},
-            "timed_as": "K solves of the headline workload with the L1 data term, CUDA events; per pass "
-                        "(T(100 it) - T(0 it)) / 100"}
+            "timed_as": "K solves, CUDA events; per pass (T(%d it) - T(0 it)) / %d" % (iters, max(iters, 1))}
+
+
+L1_DATA_EPS = 0.01   # smoothing of the L1 data term: the frames' noise sigma
+
+
+def measure_l1(args, wl, shifts, psf, tuned, y, xt, stream, dist, device, peak):
+    """The headline workload with the smoothed L1 data term (the paper's experiments)."""
+    from paper_2108_04315_b300.binding import MISR_NORM_L1
+    out = measure_variant(args, wl, shifts, psf, tuned, xt, stream, dist, device, peak, wl["iters"], y=y,
+                          data_norm=MISR_NORM_L1, data_eps=L1_DATA_EPS)
+    out.update({"data_norm": "L1, psi_d(t) = sqrt(t^2 + eps_d^2) - eps_d", "data_eps": L1_DATA_EPS})
+    return out
+
+
+def measure_paper_ct(args, wl, shifts, tuned, xt, stream, dist, device, peak):
+    """The paper's CT reconstruction setting (Sec. 4) at the headline size: 3x3 Gaussian blur,
+    lambda 0.05, alpha 0.4, 20 SCG iterations, the L1 data term, and the 2x2 binning D of the
+    synthetic study (Sec. 4.1.1); frames made with that model."""
+    from paper_2108_04315_b300.binding import MISR_DECIM_BIN, MISR_NORM_L1
+    psf3 = gen.gaussian_psf(3, 0.5)
+    out = measure_variant(args, wl, shifts, psf3, tuned, xt, stream, dist, device, peak, 20, lam=0.05,
+                          data_norm=MISR_NORM_L1, data_eps=L1_DATA_EPS, decimation=MISR_DECIM_BIN)
+    out["model"] = ("2048^2 -> 4096^2, f=2 half-pixel shifts, 3x3 Gaussian sigma 0.5, 2x2 binning D, L1 data "
+                    "term eps_d 0.01, lambda 0.05, BTV alpha 0.4 w 3 eps 1e-3, 20 SCG iterations")
+    return out
+
+
+def measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak):
+    """Multi-image interpolation (misr_interpolate), the paper's non-iterative comparator, on
+    the same frames: rate, HBM bandwidth (frames read once, HR image written once) and the image
+    error against the phantom beside that of the SCG solve."""
+    import torch
+    H, W = wl["f"] * wl["h"], wl["f"] * wl["w"]
+    xi = torch.empty((H, W), dtype=torch.float32, device=device)
+    for _ in range(max(args.warmup, 3)):
+        plan.interpolate(y, xi)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    reps = 20 * args.steps
+    flush = torch.empty(64 * 2**20, dtype=torch.float32, device=device)   # 256 MB > L2
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        plan.interpolate(y, xi)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / reps
+    del flush
+    rate, _ = job_rate(reps, ms * reps / 1e3, dist, device)
+    nbytes = y.numel() * 4 + H * W * 4
+    xs = plan.solve(y)[0]
+    err = lambda a: float(torch.linalg.vector_norm(a - xt) / torch.linalg.vector_norm(xt))
+    return {"value": rate, "unit": UNIT, "ms": ms, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9,
+            "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "bytes_per_call": nbytes,
+            "image_rel_error_vs_phantom": {"interpolation": err(xi), "scg_%d_it" % wl["iters"]: err(xs)},
+            "timed_as": "%d calls of misr_interpolate, each timed alone with CUDA events on the stream "
+                        "after a 256 MB write that flushes L2" % reps}
 
 
 def cpu_baseline(wl):
@@ -658,7 +717,9 @@ def main():
 
     peak, peak_kind = load_peaks()
     achieved = PASS_BYTES_PER_PX * H * W / (pass_ms * 1e-3) / 1e9
-    l1 = measure_l1(args, wl, shifts, psf, tuned, y, x, stream, dist, device, peak)
+    l1 = measure_l1(args, wl, shifts, psf, tuned, y, xt, stream, dist, device, peak)
+    paper_ct = measure_paper_ct(args, wl, shifts, tuned, xt, stream, dist, device, peak)
+    interp = measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -679,6 +740,8 @@ def main():
         "e2e": e2e,
         "batched": batched,
         "l1": l1,
+        "paper_ct_setting": paper_ct,
+        "interpolation": interp,
         # per solve: prepare, the initial pass and every SCG pass (the fused pass kernel and its
         # reduction kernel), finalize
         "gpu_launches": args.steps * (2 * wl["iters"] + 4),

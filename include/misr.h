@@ -88,10 +88,18 @@ typedef struct misr_desc {
                                 data_eps^2) - data_eps */
     double data_eps;         /* MISR_NORM_L1: the smoothing data_eps, in [1e-15, 1e15];
                                 ignored for MISR_NORM_L2 */
+    int32_t decimation;      /* MISR_DECIM_POINT (0): D samples HR pixel (f i, f j) of B M_k x.
+                                MISR_DECIM_BIN: D is the mean of the f x f block starting there
+                                (the 2 x 2 binning of the synthetic study, Sec. 4.1.1); D B is
+                                then one blur whose taps span psf_size + f - 1 pixels per axis,
+                                which must fit the compiled 5 (psf_size 3 at f <= 2, psf_size 1
+                                at f <= 3, any PSF at f = 1), else MISR_ENOTIMPL */
 } misr_desc;
 
 /* data terms (misr_desc.data_norm) */
 enum { MISR_NORM_L2 = 0, MISR_NORM_L1 = 1 };
+/* decimation D (misr_desc.decimation) */
+enum { MISR_DECIM_POINT = 0, MISR_DECIM_BIN = 1 };
 
 /* Tile shapes of the fused pass (HR pixels per CTA tile; threads per CTA).  The paper has no
  * counterpart: its partitions are whole sub-images per GPU (Sec. 3.1). */
@@ -151,6 +159,15 @@ misr_status misr_plan_set_wait_limit(misr_plan_t plan, uint32_t tries);
  * y_dev receives K float32 frames.  Asynchronous on stream.  Used to synthesise
  * acquisitions. */
 misr_status misr_forward(misr_plan_t plan, const float *x_dev, float *y_dev, misr_stream_t stream);
+
+/* Multi-image interpolation (Sec. 4.1.1), the paper's non-iterative comparator: every LR
+ * sample of y_dev (K frames, the plan's in_dtype; u16 counts are log-converted as for a solve)
+ * is inserted at the HR pixel it was taken at, f*(i, j) + the frame's HR shift, and x_dev (HR
+ * float32, dense) is 0 where no frame samples.  It is also the start point of a
+ * MISR_X0_SHIFT_ADD solve.  Reads only the plan's geometry: the plan's workspace and solve
+ * state are not touched.  Asynchronous on stream.  Errors: MISR_EINVAL (NULL arguments),
+ * MISR_ECUDA. */
+misr_status misr_interpolate(misr_plan_t plan, const void *y_dev, float *x_dev, misr_stream_t stream);
 
 /* Objective and gradient at x (Eq. 9 and its gradient 2 sum_k A_k^T (A_k x - y_k) +
  * lambda grad R): y_dev holds the K frames (in_dtype), x_dev the HR image, g_dev receives

@@ -66,28 +66,46 @@ int orc_set_data_norm(orc_problem *P, int norm, double data_eps) {
     return 0;
 }
 
+/* Decimation (reading: D samples phase 0 unless the binning of the synthetic study, Sec.
+ * 4.1.1, is asked for).  Returns 0, or -1 for an unknown mode. */
+int orc_set_decimation(orc_problem *P, int mode) {
+    if (mode != ORC_DECIM_POINT && mode != ORC_DECIM_BIN) return -1;
+    P->decim = mode;
+    return 0;
+}
+
 /* (A_k x)(i, j) = (D B M_k x)(i, j)                                            Eq. 1
  *   (M_k x)(u, v) = x(u + ty_k, v + tx_k), zero when that pixel is outside the grid;
  *   (B z)(u, v)   = sum_{a,b} h(a, b) z(u - a, v - b), z zero outside the grid;
- *   (D w)(i, j)   = w(f i, f j).                                                       */
+ *   (D w)(i, j)   = w(f i, f j), or with binning
+ *   (D w)(i, j)   = (1 / f^2) sum_{a', b' = 0}^{f-1} w(f i + a', f j + b').              */
 void orc_forward(const orc_problem *P, int k, const double *x, double *out) {
     const int H = HRH(P), W = HRW(P), S = P->psf_size, R = S / 2, f = P->f;
     const int ty = P->ty[k], tx = P->tx[k];
+    const int nb = P->decim == ORC_DECIM_BIN ? f : 1;   /* block side averaged by D */
+    const double wd = 1.0 / ((double)nb * nb);
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < P->h; ++i) {
         for (int j = 0; j < P->w; ++j) {
             double acc = 0.0;
-            for (int a = -R; a <= R; ++a) {
-                int bu = f * i - a;                 /* pixel of B's input, M_k x */
-                if (bu < 0 || bu >= H) continue;
-                int u = bu + ty;                    /* pixel of x read by M_k */
-                if (u < 0 || u >= H) continue;
-                for (int b = -R; b <= R; ++b) {
-                    int bv = f * j - b;
-                    if (bv < 0 || bv >= W) continue;
-                    int v = bv + tx;
-                    if (v < 0 || v >= W) continue;
-                    acc += P->psf[(a + R) * S + (b + R)] * x[(long)u * W + v];
+            for (int a2 = 0; a2 < nb; ++a2) {
+                for (int b2 = 0; b2 < nb; ++b2) {
+                    const int cu = f * i + a2, cv = f * j + b2;   /* pixel of B's output */
+                    double w = 0.0;
+                    for (int a = -R; a <= R; ++a) {
+                        int bu = cu - a;                 /* pixel of B's input, M_k x */
+                        if (bu < 0 || bu >= H) continue;
+                        int u = bu + ty;                 /* pixel of x read by M_k */
+                        if (u < 0 || u >= H) continue;
+                        for (int b = -R; b <= R; ++b) {
+                            int bv = cv - b;
+                            if (bv < 0 || bv >= W) continue;
+                            int v = bv + tx;
+                            if (v < 0 || v >= W) continue;
+                            w += P->psf[(a + R) * S + (b + R)] * x[(long)u * W + v];
+                        }
+                    }
+                    acc += wd * w;
                 }
             }
             out[(long)i * P->w + j] = acc;
@@ -95,25 +113,32 @@ void orc_forward(const orc_problem *P, int k, const double *x, double *out) {
     }
 }
 
-/* out = A_k^T e: the same loop as orc_forward with every multiply-add scattered back. */
+/* out = A_k^T e: the same loops as orc_forward with every multiply-add scattered back. */
 void orc_adjoint(const orc_problem *P, int k, const double *e, double *out) {
     const int H = HRH(P), W = HRW(P), S = P->psf_size, R = S / 2, f = P->f;
     const int ty = P->ty[k], tx = P->tx[k];
+    const int nb = P->decim == ORC_DECIM_BIN ? f : 1;
+    const double wd = 1.0 / ((double)nb * nb);
     memset(out, 0, sizeof(double) * (size_t)H * W);
     for (int i = 0; i < P->h; ++i) {
         for (int j = 0; j < P->w; ++j) {
-            const double ev = e[(long)i * P->w + j];
-            for (int a = -R; a <= R; ++a) {
-                int bu = f * i - a;
-                if (bu < 0 || bu >= H) continue;
-                int u = bu + ty;
-                if (u < 0 || u >= H) continue;
-                for (int b = -R; b <= R; ++b) {
-                    int bv = f * j - b;
-                    if (bv < 0 || bv >= W) continue;
-                    int v = bv + tx;
-                    if (v < 0 || v >= W) continue;
-                    out[(long)u * W + v] += P->psf[(a + R) * S + (b + R)] * ev;
+            const double ev = wd * e[(long)i * P->w + j];
+            for (int a2 = 0; a2 < nb; ++a2) {
+                for (int b2 = 0; b2 < nb; ++b2) {
+                    const int cu = f * i + a2, cv = f * j + b2;
+                    for (int a = -R; a <= R; ++a) {
+                        int bu = cu - a;
+                        if (bu < 0 || bu >= H) continue;
+                        int u = bu + ty;
+                        if (u < 0 || u >= H) continue;
+                        for (int b = -R; b <= R; ++b) {
+                            int bv = cv - b;
+                            if (bv < 0 || bv >= W) continue;
+                            int v = bv + tx;
+                            if (v < 0 || v >= W) continue;
+                            out[(long)u * W + v] += P->psf[(a + R) * S + (b + R)] * ev;
+                        }
+                    }
                 }
             }
         }

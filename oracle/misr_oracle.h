@@ -17,7 +17,8 @@
  * Readings where the paper is silent (each is stated where it is used in the .c file):
  *   M_k  translation by the integer HR shift t_k = f * s_k (s_k in LR px), x zero outside
  *   B    convolution with the PSF h (normalised to sum 1), zero outside the HR grid
- *   D    sampling at HR position (f i, f j)
+ *   D    sampling at HR position (f i, f j), or (ORC_DECIM_BIN) the mean of the f x f block
+ *        whose first pixel is (f i, f j): the 2 x 2 binning of the synthetic study (Sec. 4.1.1)
  *   |.|  in the BTV term is smoothed as psi(t) = sqrt(t^2 + eps^2) - eps  (eps = 0: |t|)
  *   pairs (q, q + d) enter the BTV sum only when both pixels lie inside the grid
  *
@@ -35,6 +36,7 @@
 enum { ORC_REG_BTV = 0, ORC_REG_TIKHONOV = 1 };
 enum { ORC_HV_EXACT = 0, ORC_HV_FD = 1 };
 enum { ORC_NORM_L2 = 0, ORC_NORM_L1 = 1 };
+enum { ORC_DECIM_POINT = 0, ORC_DECIM_BIN = 1 };
 
 typedef struct {
     int h, w;                 /* LR frame size (rows, cols) */
@@ -50,6 +52,7 @@ typedef struct {
     int reg;                  /* ORC_REG_BTV or ORC_REG_TIKHONOV */
     int data_norm;            /* ORC_NORM_L2 (default) or ORC_NORM_L1 */
     double data_eps;          /* Charbonnier smoothing of the L1 data term (> 0) */
+    int decim;                /* ORC_DECIM_POINT (default) or ORC_DECIM_BIN */
 } orc_problem;
 
 /* one row of the SCG trace per iteration (failed iterations included) */
@@ -72,6 +75,7 @@ int orc_init(orc_problem *P, int h, int w, int K, int f, const double *shifts_lr
              const double *psf, int psf_size, double lambda, double btv_alpha, int btv_w,
              double eps, int reg);
 int orc_set_data_norm(orc_problem *P, int norm, double data_eps);
+int orc_set_decimation(orc_problem *P, int mode);
 int orc_threads(void);
 void orc_forward(const orc_problem *P, int k, const double *x, double *out);
 void orc_adjoint(const orc_problem *P, int k, const double *e, double *out);

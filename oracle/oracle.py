@@ -17,6 +17,7 @@ MAXPSF = 15
 REG_BTV, REG_TIKHONOV = 0, 1
 HV_EXACT, HV_FD = 0, 1
 NORM_L2, NORM_L1 = 0, 1
+DECIM_POINT, DECIM_BIN = 0, 1
 
 
 class _Problem(C.Structure):
@@ -26,7 +27,7 @@ class _Problem(C.Structure):
         ("psf_size", C.c_int), ("psf", C.c_double * (MAXPSF * MAXPSF)),
         ("lambda_", C.c_double), ("btv_alpha", C.c_double), ("btv_w", C.c_int),
         ("eps", C.c_double), ("reg", C.c_int),
-        ("data_norm", C.c_int), ("data_eps", C.c_double),
+        ("data_norm", C.c_int), ("data_eps", C.c_double), ("decim", C.c_int),
     ]
 
 
@@ -54,6 +55,8 @@ def lib():
         L.orc_threads.restype = C.c_int
         L.orc_set_data_norm.argtypes = [pp, C.c_int, C.c_double]
         L.orc_set_data_norm.restype = C.c_int
+        L.orc_set_decimation.argtypes = [pp, C.c_int]
+        L.orc_set_decimation.restype = C.c_int
         for name in ("orc_forward", "orc_adjoint"):
             getattr(L, name).argtypes = [pp, C.c_int, dp, dp]
         L.orc_reg_value.argtypes = [pp, dp]
@@ -93,7 +96,7 @@ class Problem:
     """One MISR problem: K LR frames of h x w, magnification f, shifts (dx, dy) in LR px."""
 
     def __init__(self, h, w, f, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3,
-                 reg=REG_BTV, data_norm=NORM_L2, data_eps=0.0):
+                 reg=REG_BTV, data_norm=NORM_L2, data_eps=0.0, decimation=DECIM_POINT):
         self.h, self.w, self.f = int(h), int(w), int(f)
         self.K = len(shifts)
         self.H, self.W = self.f * self.h, self.f * self.w
@@ -107,6 +110,8 @@ class Problem:
             raise ValueError(f"orc_init failed ({rc})")
         if lib().orc_set_data_norm(C.byref(self._p), int(data_norm), float(data_eps)) != 0:
             raise ValueError("data norm: L2, or L1 with data_eps > 0")
+        if lib().orc_set_decimation(C.byref(self._p), int(decimation)) != 0:
+            raise ValueError("decimation: DECIM_POINT or DECIM_BIN")
         self.data_norm = int(data_norm)
 
     @property

@@ -20,6 +20,7 @@ MISR_X0_ZERO, MISR_X0_SHIFT_ADD, MISR_X0_GIVEN = 0, 1, 2
 MISR_TILE_AUTO, MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64 = 0, 1, 2, 3
 MISR_N_TILE_SHAPES = 3
 MISR_NORM_L2, MISR_NORM_L1 = 0, 1
+MISR_DECIM_POINT, MISR_DECIM_BIN = 0, 1
 MISR_TRACE_COLS = 10
 MISR_PASS_SUMS = 10
 TRACE_FIELDS = ("E", "J_trial", "alpha", "delta", "mu", "lam", "Delta", "pn2", "rn2", "accept")
@@ -34,6 +35,7 @@ class misr_desc(C.Structure):
         ("eps", C.c_double), ("iters", C.c_int32), ("x0_mode", C.c_int32),
         ("in_dtype", C.c_int32), ("flat_field", C.c_float), ("iterate_dtype", C.c_int32),
         ("tile_shape", C.c_int32), ("data_norm", C.c_int32), ("data_eps", C.c_double),
+        ("decimation", C.c_int32),
     ]
 
 
@@ -77,6 +79,7 @@ def lib():
         L.misr_plan_set_wait_limit.argtypes = [VP, C.c_uint32]
         L.misr_debug_bounds.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]
         L.misr_forward.argtypes = [VP, VP, VP, VP]
+        L.misr_interpolate.argtypes = [VP, VP, VP, VP]
         L.misr_gradient.argtypes = [VP, VP, VP, VP, DP, VP]
         L.misr_pass_probe.argtypes = [VP, VP, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, DP, VP]
         L.misr_solve.argtypes = [VP, VP, VP, VP, C.POINTER(misr_stats)]
@@ -100,7 +103,7 @@ def lib():
         L.misr_server_counters.argtypes = [VP, C.POINTER(C.c_int64)]
         for name in ("misr_plan_create", "misr_plan_destroy", "misr_plan_workspace_bytes", "misr_plan_set_wait_limit",
                      "misr_debug_bounds",
-                     "misr_forward",
+                     "misr_forward", "misr_interpolate",
                      "misr_gradient", "misr_pass_probe", "misr_solve", "misr_solve_host", "misr_solve_host_many",
                      "misr_get_trace", "misr_state_bytes", "misr_export_state", "misr_import_state", "misr_resume",
                      "misr_batch_create", "misr_batch_destroy", "misr_batch_solve", "misr_server_create",
@@ -143,6 +146,10 @@ def misr_plan_workspace_bytes(plan: int) -> int:
 
 def misr_forward(plan: int, x_dev: int, y_dev: int, stream: int = 0) -> None:
     _check(lib().misr_forward(VP(plan), VP(x_dev), VP(y_dev), VP(stream)), "misr_forward")
+
+
+def misr_interpolate(plan: int, y_dev: int, x_dev: int, stream: int = 0) -> None:
+    _check(lib().misr_interpolate(VP(plan), VP(y_dev), VP(x_dev), VP(stream)), "misr_interpolate")
 
 
 def misr_gradient(plan: int, y_dev: int, x_dev: int, g_dev: int, stream: int = 0) -> float:
@@ -308,7 +315,7 @@ def _stats_dict(st: misr_stats):
 # ---------------------------------------------------------------- torch convenience layer
 def make_desc(lr_h, lr_w, factor, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3, iters=100,
               x0_mode=MISR_X0_SHIFT_ADD, in_dtype=MISR_F32, flat_field=40000.0, iterate_dtype=MISR_F32,
-              tile_shape=MISR_TILE_AUTO, data_norm=MISR_NORM_L2, data_eps=0.0):
+              tile_shape=MISR_TILE_AUTO, data_norm=MISR_NORM_L2, data_eps=0.0, decimation=MISR_DECIM_POINT):
     sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float32).reshape(-1))
     ps = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
     d = misr_desc()
@@ -321,6 +328,7 @@ def make_desc(lr_h, lr_w, factor, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3,
     d.flat_field, d.iterate_dtype = float(flat_field), int(iterate_dtype)
     d.tile_shape = int(tile_shape)
     d.data_norm, d.data_eps = int(data_norm), float(data_eps)
+    d.decimation = int(decimation)
     d._keep = (sh, ps)  # keep the host arrays alive while the descriptor is used
     return d
 
@@ -371,6 +379,14 @@ class Plan:
             y_out = torch.empty((self.K, self.h, self.w), dtype=torch.float32, device=x.device)
         misr_forward(self.handle, self._ptr(x, torch.float32), self._ptr(y_out, torch.float32), _stream_handle(stream))
         return y_out
+
+    def interpolate(self, y, x_out=None, stream=None):
+        """Multi-image interpolation of the frames y (the plan's in_dtype) into an HR image."""
+        import torch
+        if x_out is None:
+            x_out = torch.empty((self.H, self.W), dtype=torch.float32, device=y.device)
+        misr_interpolate(self.handle, self._ptr(y), self._ptr(x_out, torch.float32), _stream_handle(stream))
+        return x_out
 
     def gradient(self, y, x, stream=None):
         import torch

@@ -117,11 +117,17 @@ static misr_status validate(const misr_desc *d) {
         return fail(MISR_EINVAL, "data_norm must be MISR_NORM_L2 or MISR_NORM_L1");
     if (d->data_norm == MISR_NORM_L1 && !(d->data_eps >= 1e-15 && d->data_eps <= 1e15))
         return fail(MISR_EINVAL, "data_eps must be in [1e-15, 1e15] for MISR_NORM_L1");
+    if (d->decimation != MISR_DECIM_POINT && d->decimation != MISR_DECIM_BIN)
+        return fail(MISR_EINVAL, "decimation must be MISR_DECIM_POINT or MISR_DECIM_BIN");
     return MISR_OK;
 }
 
 // Separable PSF taps.  h = u v^T with sum h = 1 implies h = rowsum colsum^T, so the PSF is
 // accepted when it equals the outer product of its row and column sums.
+// With binning, D B is one blur: per axis, (D_bin B z)(i) = (1/f) sum_{a'<f} (B z)(f i + a') =
+// sum_c h'(c) z(f i - c) with h'(c) = (1/f) sum_{a'=0}^{f-1} h(c + a'), c in [-R-f+1, R]; the
+// tap masks of the frames (B's zero padding in front of M_k: the input pixel f i - c >= 0) are
+// those of the point-sampled blur with h' in place of h.
 static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
     const int S = d->psf_size, R = S / 2;
     double sum = 0;
@@ -137,6 +143,20 @@ static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
             if (std::fabs(h[a * S + b] - rs[a] * cs[b]) > 1e-6 * hmax)
                 return fail(MISR_EINVAL, "PSF is not separable");
     for (int i = 0; i < 2 * PSF_R + 1; ++i) { hy[i] = 0.f; hx[i] = 0.f; }
+    if (d->decimation == MISR_DECIM_BIN && d->factor > 1) {
+        const int f = d->factor;
+        if (R + f - 1 > PSF_R)
+            return fail(MISR_ENOTIMPL, "binning at factor %d with a %dx%d PSF spans %d taps per axis; %d are compiled",
+                        f, S, S, S + f - 1, 2 * PSF_R + 1);
+        for (int c = -R - f + 1; c <= R; ++c) {
+            double sy = 0, sx = 0;
+            for (int a2 = 0; a2 < f; ++a2)
+                if (c + a2 >= -R && c + a2 <= R) { sy += rs[c + a2 + R]; sx += cs[c + a2 + R]; }
+            hy[c + PSF_R] = (float)(sy / f);
+            hx[c + PSF_R] = (float)(sx / f);
+        }
+        return MISR_OK;
+    }
     for (int a = -R; a <= R; ++a) { hy[a + PSF_R] = (float)rs[a + R]; hx[a + PSF_R] = (float)cs[a + R]; }
     return MISR_OK;
 }
@@ -569,6 +589,38 @@ misr_status misr_forward(misr_plan_t p, const float *x_dev, float *y_dev, misr_s
     DeviceGuard g(p->device);
     forward_kernel<<<grid_for(p->m_total, 256), 256, 0, (cudaStream_t)stream>>>(p->dprob, 0, x_dev, y_dev);
     CK(cudaGetLastError());
+    return MISR_OK;
+}
+
+}  // extern "C"
+
+template <int F>
+static cudaError_t launch_interpolate(const misr_plan_t p, const void *y_dev, float *x_dev, float log_i0,
+                                      cudaStream_t s) {
+    const int gx = (int)std::min<size_t>(((size_t)p->hp.w + 4 * 256 - 1) / (4 * 256), 64);
+    const int gy = std::min(p->hp.H, 65535);
+    interpolate_kernel<F><<<dim3(gx, gy), 256, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, x_dev);
+    return cudaGetLastError();
+}
+
+extern "C" {
+
+misr_status misr_interpolate(misr_plan_t p, const void *y_dev, float *x_dev, misr_stream_t stream) {
+    if (!p || !y_dev || !x_dev) return fail(MISR_EINVAL, "NULL argument");
+    DeviceGuard g(p->device);
+    const float log_i0 = p->d.in_dtype == MISR_U16 ? logf(p->d.flat_field) : 0.f;
+    cudaStream_t s = (cudaStream_t)stream;
+    static_assert(MAXF == 8, "one case per factor");
+    switch (p->hp.f) {
+    case 1: CK(launch_interpolate<1>(p, y_dev, x_dev, log_i0, s)); break;
+    case 2: CK(launch_interpolate<2>(p, y_dev, x_dev, log_i0, s)); break;
+    case 3: CK(launch_interpolate<3>(p, y_dev, x_dev, log_i0, s)); break;
+    case 4: CK(launch_interpolate<4>(p, y_dev, x_dev, log_i0, s)); break;
+    case 5: CK(launch_interpolate<5>(p, y_dev, x_dev, log_i0, s)); break;
+    case 6: CK(launch_interpolate<6>(p, y_dev, x_dev, log_i0, s)); break;
+    case 7: CK(launch_interpolate<7>(p, y_dev, x_dev, log_i0, s)); break;
+    default: CK(launch_interpolate<8>(p, y_dev, x_dev, log_i0, s)); break;
+    }
     return MISR_OK;
 }
 

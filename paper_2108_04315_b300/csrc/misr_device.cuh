@@ -1301,6 +1301,85 @@ __global__ void forward_kernel(const DevProblem *__restrict__ probs, int pidx, c
     }
 }
 
+// Multi-image interpolation (Sec. 4.1.1): every LR sample inserted at the HR pixel it was
+// taken at, 0 where no frame samples (one frame per HR phase, so no pixel gets two samples).
+// out is dense (row pitch W).  Compiled per factor F.  HR row cy = F i + py takes LR row i of
+// the frames of phases (py, 0 .. F-1); a thread takes 4 LR columns j0 .. j0+3 of each, read with
+// one 16-byte (float) or 8-byte (u16) load per frame where the frames' rows allow it, and
+// writes the 4 F HR pixels F j0 .. F j0 + 4 F - 1 with F 16-byte stores where the HR rows allow.
+// Rows are taken by blockIdx.y (grid-stride).
+template <int F>
+__global__ void __launch_bounds__(256) interpolate_kernel(const DevProblem *__restrict__ probs, int pidx,
+                                                          const void *__restrict__ y_in, int in_dtype,
+                                                          float log_i0, float *__restrict__ out) {
+    __shared__ int fop[MAXF * MAXF];
+    const DevProblem &P = probs[pidx];
+    for (int t = threadIdx.x; t < MAXF * MAXF; t += blockDim.x) fop[t] = P.frame_of_phase[t];
+    __syncthreads();
+    const int H = P.H, W = P.W, w = P.w;
+    const size_t m = (size_t)P.h * w;
+    // vector accesses only where every frame row and every HR row starts on their boundary
+    const bool vin = (w & 3) == 0 && (reinterpret_cast<uintptr_t>(y_in) & (in_dtype == 1 ? 7 : 15)) == 0;
+    const bool vout = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    for (int cy = blockIdx.y; cy < H; cy += gridDim.y) {
+        const int i = cy / F, py = cy - i * F;
+        int k[F];
+#pragma unroll
+        for (int px = 0; px < F; ++px) k[px] = fop[py * F + px];
+        for (int j0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x); j0 < w; j0 += 4 * gridDim.x * blockDim.x) {
+            const bool full = j0 + 4 <= w;
+            float v[4][F];   // HR pixel F j + px is v[j - j0][px]
+#pragma unroll
+            for (int px = 0; px < F; ++px) {
+                float a[4] = {0.f, 0.f, 0.f, 0.f};
+                if (k[px] >= 0) {
+                    const size_t li = (size_t)k[px] * m + (size_t)i * w + j0;
+                    if (in_dtype == 1) {
+                        const unsigned short *src = (const unsigned short *)y_in + li;
+                        unsigned short c[4] = {1, 1, 1, 1};
+                        if (vin && full) {
+                            const ushort4 u = __ldg(reinterpret_cast<const ushort4 *>(src));
+                            c[0] = u.x; c[1] = u.y; c[2] = u.z; c[3] = u.w;
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (j0 + q < w) c[q] = __ldg(src + q);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) a[q] = log_i0 - logf((float)(c[q] < 1 ? 1 : c[q]));
+                    } else {
+                        const float *src = (const float *)y_in + li;
+                        if (vin && full) {
+                            const float4 u = __ldg(reinterpret_cast<const float4 *>(src));
+                            a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (j0 + q < w) a[q] = __ldg(src + q);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q][px] = a[q];
+            }
+            float *o = out + (size_t)cy * W + (size_t)F * j0;
+            const float *flat = &v[0][0];
+            if (vout && full) {
+#pragma unroll
+                for (int t = 0; t < F; ++t)
+                    __stcs(reinterpret_cast<float4 *>(o + 4 * t),
+                           make_float4(flat[4 * t], flat[4 * t + 1], flat[4 * t + 2], flat[4 * t + 3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (j0 + q < w)
+#pragma unroll
+                        for (int px = 0; px < F; ++px) o[F * q + px] = v[q][px];
+            }
+        }
+    }
+}
+
 // out (dense) = x_k, the iterate the state points at (end of a solve)
 __global__ void finalize_kernel(const DevProblem *__restrict__ probs, int pidx, float *__restrict__ out) {
     const DevProblem &P = probs[pidx];

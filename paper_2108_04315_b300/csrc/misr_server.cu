@@ -53,7 +53,7 @@ struct DescCopy {
                a.psf_size == b.psf_size && a.lambda == b.lambda && a.btv_alpha == b.btv_alpha &&
                a.btv_w == b.btv_w && a.eps == b.eps && a.iters == b.iters && a.x0_mode == b.x0_mode &&
                a.in_dtype == b.in_dtype && a.flat_field == b.flat_field && a.iterate_dtype == b.iterate_dtype &&
-               a.tile_shape == b.tile_shape && a.data_norm == b.data_norm &&
+               a.tile_shape == b.tile_shape && a.data_norm == b.data_norm && a.decimation == b.decimation &&
                (a.data_norm != MISR_NORM_L1 || a.data_eps == b.data_eps) &&
                shifts == o.shifts && psf == o.psf;
     }

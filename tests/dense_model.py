@@ -20,6 +20,18 @@ def decimation(h, w, f):
     return D
 
 
+def binning(h, w, f):
+    """D with binning: (h*w) x (H*W), D[(i,j), (f i + a, f j + b)] = 1/f^2 for a, b in [0, f)."""
+    H, W = f * h, f * w
+    D = np.zeros((h * w, H * W))
+    for i in range(h):
+        for j in range(w):
+            for a in range(f):
+                for b in range(f):
+                    D[i * w + j, idx(f * i + a, f * j + b, W)] = 1.0 / (f * f)
+    return D
+
+
 def blur(H, W, psf):
     """B: convolution with the PSF, zero outside the grid:
     (B z)(u, v) = sum_{a,b} h(a, b) z(u - a, v - b)."""
@@ -47,12 +59,12 @@ def motion(H, W, ty, tx):
     return M
 
 
-def system_matrices(h, w, f, shifts_lr, psf):
+def system_matrices(h, w, f, shifts_lr, psf, binned=False):
     """A_k = D B M_k for every frame; psf is normalised to sum 1 here."""
     H, W = f * h, f * w
     psf = np.asarray(psf, dtype=np.float64)
     psf = psf / psf.sum()
-    D = decimation(h, w, f)
+    D = binning(h, w, f) if binned else decimation(h, w, f)
     B = blur(H, W, psf)
     out = []
     for dx, dy in shifts_lr:

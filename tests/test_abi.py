@@ -74,6 +74,9 @@ def _desc(**kw):
     (dict(data_norm=1, data_eps=0.0), "EINVAL"),                  # the L1 term needs eps_d > 0
     (dict(data_norm=1, data_eps=1e20), "EINVAL"),
     (dict(data_norm=1, data_eps=float("nan")), "EINVAL"),
+    (dict(decimation=2), "EINVAL"),
+    (dict(decimation=1), "ENOTIMPL"),                             # 5x5 PSF binned at f=2: 6 taps
+    (dict(decimation=1, factor=3, shifts=[(0.0, 0.0)], psf=np.ones((3, 3))), "ENOTIMPL"),
 ])
 def test_invalid_descriptor_rejected_on_host(L, kw, status):
     from paper_2108_04315_b300 import binding
@@ -93,6 +96,7 @@ def test_null_arguments_rejected(L):
     assert L.misr_plan_set_wait_limit(None, 0) == binding.MISR_EINVAL
     assert L.misr_debug_bounds(None, None) == binding.MISR_EINVAL
     assert L.misr_cancel(None, 1) == binding.MISR_EINVAL
+    assert L.misr_interpolate(None, None, None, None) == binding.MISR_EINVAL
     assert L.misr_state_bytes(None, None) == binding.MISR_EINVAL
     assert L.misr_export_state(None, None, 0) == binding.MISR_EINVAL
     assert L.misr_import_state(None, None, 0) == binding.MISR_EINVAL

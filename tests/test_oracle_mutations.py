@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "misr_oracle.c")
 
 MUTANTS = {
-    "convolution_flipped": ("int bu = f * i - a;", "int bu = f * i + a;"),
+    "convolution_flipped": ("int bu = cu - a;", "int bu = cu + a;"),
     "blur_padding_dropped": ("if (bu < 0 || bu >= H) continue;", "/* row padding dropped */"),
     "shift_sign": ("int u = bu + ty;", "int u = bu - ty;"),
     "gamma_exponent": ("return pow(P->btv_alpha, dx + dy);", "return pow(P->btv_alpha, dx > dy ? dx : dy);"),
@@ -31,6 +31,11 @@ MUTANTS = {
     "lambda_not_reduced": ("if (Delta >= 0.75) lam = lam / 4.0;", "if (Delta >= 0.75) lam = lam / 2.0;"),
     "delta_not_scaled": ("delta += (lam - lam_bar) * pn2;", "delta += 0.0 * (lam - lam_bar) * pn2;"),
     "shift_add_no_average": ("x0[i] = cnt[i] > 0 ? x0[i] / cnt[i] : 0.0;", "x0[i] = x0[i];"),
+    "binning_weight_1_over_f": ("const double wd = 1.0 / ((double)nb * nb);", "const double wd = 1.0 / (double)nb;"),
+    "binning_block_backwards": ("const int cu = f * i + a2, cv = f * j + b2;   /* pixel of B's output */",
+                                "const int cu = f * i - a2, cv = f * j + b2;   /* pixel of B's output */"),
+    "binned_adjoint_weight_dropped": ("const double ev = wd * e[(long)i * P->w + j];",
+                                      "const double ev = e[(long)i * P->w + j];"),
     "log_convert_no_clamp": ("double c = counts[i] < 1 ? 1.0 : (double)counts[i];", "double c = (double)counts[i] + 1e-300;"),
 }
 

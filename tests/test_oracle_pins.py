@@ -478,3 +478,59 @@ def test_l1_scg_monotone_and_rejections_consistent(orc):
     with pytest.raises(ValueError):
         orc.Problem(4, 4, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), data_norm=orc.NORM_L1,
                     data_eps=0.0)
+
+
+# ------------------------------------------------------------------ binning D (Sec. 4.1.1)
+
+@pytest.mark.parametrize("f,shifts", [
+    (2, [(0.0, 0.0), (0.5, 0.0), (0.0, 0.5), (0.5, 0.5)]),
+    (3, gen.third_pixel_shifts()[:4]),
+    (2, [(0.5, 0.0), (0.0, 0.5), (-0.5, 0.0), (0.0, -0.5)]),   # the synthetic study's four directions
+])
+def test_binned_forward_and_adjoint_equal_dense(orc, f, shifts):
+    """Binning D (the mean of each f x f block, Sec. 4.1.1): the oracle's A_k and A_k^T equal
+    the textbook product D_bin B M_k and its transpose; an asymmetric PSF catches a flipped
+    block offset."""
+    h = w = 4 if f == 2 else 3
+    psf = _asym_psf(17, 3)
+    P = orc.Problem(h, w, f, shifts, psf, decimation=orc.DECIM_BIN)
+    A = dm.system_matrices(h, w, f, shifts, psf, binned=True)
+    n, m = P.H * P.W, h * w
+    for k in range(P.K):
+        cols = np.stack([P.forward(k, np.eye(n)[c].reshape(P.H, P.W)).ravel() for c in range(n)], axis=1)
+        np.testing.assert_allclose(cols, A[k], rtol=0, atol=1e-15)
+        cols = np.stack([P.adjoint(k, np.eye(m)[c].reshape(h, w)).ravel() for c in range(m)], axis=1)
+        np.testing.assert_allclose(cols, A[k].T, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("f", [2, 3])
+def test_binning_is_the_block_mean(orc, f):
+    """With a delta PSF and no shift, A x is the mean of each f x f block of x (numpy's
+    reshape-and-mean), at a size the dense test does not reach."""
+    h, w = 13, 9
+    P = orc.Problem(h, w, f, [(0.0, 0.0)], np.ones((1, 1)), decimation=orc.DECIM_BIN)
+    x = gen.random_field((P.H, P.W), 21)
+    ref = x.reshape(h, f, w, f).mean(axis=(1, 3))
+    np.testing.assert_allclose(P.forward(0, x), ref, rtol=1e-15, atol=1e-15)
+
+
+@pytest.mark.parametrize("norm", ["l2", "l1"])
+def test_binned_gradient_central_differences(orc, norm):
+    """grad J with binning against central differences of J (every coordinate), for both
+    data terms."""
+    kw = dict(data_norm=orc.NORM_L1, data_eps=0.05) if norm == "l1" else {}
+    P = orc.Problem(5, 4, 2, gen.half_pixel_shifts(), gen.gaussian_psf(3, 0.6), lam=0.01, eps=0.1,
+                    decimation=orc.DECIM_BIN, **kw)
+    y = gen.random_field((4, 5, 4), 51, 0, 2)
+    x = _distinct_levels(P, 5)
+    J0, g = P.gradient(x, y)
+    hstep = 1e-6
+    fd = np.empty_like(x)
+    for i in range(P.H):
+        for j in range(P.W):
+            xp = x.copy(); xp[i, j] += hstep
+            xm = x.copy(); xm[i, j] -= hstep
+            fd[i, j] = (P.objective(xp, y) - P.objective(xm, y)) / (2 * hstep)
+    assert np.linalg.norm(fd - g) <= 1e-7 * np.linalg.norm(g)
+    with pytest.raises(ValueError):
+        orc.Problem(4, 4, 2, gen.half_pixel_shifts(), gen.gaussian_psf(3, 0.5), decimation=2)
