@@ -27,9 +27,10 @@ static int HRH(const orc_problem *P) { return P->f * P->h; }
 static int HRW(const orc_problem *P) { return P->f * P->w; }
 
 /* Set up a problem.  shifts_lr holds K pairs (dx, dy) in LR pixels (dx along columns).
- * Reading: the detector shift moves the sampling grid by t = f * s HR pixels; only integer
- * t is modelled (every shift pattern of the paper, Sec. 3.2 and Sec. 4.1.4, is a multiple
- * of 1/f LR px).  Returns 0, or a negative code for an invalid argument. */
+ * Reading: the detector shift moves the sampling grid by t = f * s HR pixels (every shift
+ * pattern of the paper, Sec. 3.2 and Sec. 4.1, is a multiple of 1/f LR px, so t is an integer
+ * there); a non-integer t = n + a is modelled by bilinear interpolation between HR pixels
+ * n and n + 1.  Returns 0, or a negative code for an invalid argument. */
 int orc_init(orc_problem *P, int h, int w, int K, int f, const double *shifts_lr,
              const double *psf, int psf_size, double lambda, double btv_alpha, int btv_w,
              double eps, int reg) {
@@ -40,10 +41,14 @@ int orc_init(orc_problem *P, int h, int w, int K, int f, const double *shifts_lr
     P->h = h; P->w = w; P->K = K; P->f = f;
     for (int k = 0; k < K; ++k) {
         double tx = f * shifts_lr[2 * k], ty = f * shifts_lr[2 * k + 1];
+        if (!(fabs(tx) < 1e6 && fabs(ty) < 1e6)) return -4;
         double rx = floor(tx + 0.5), ry = floor(ty + 0.5);
-        if (fabs(tx - rx) > 1e-9 || fabs(ty - ry) > 1e-9) return -4;
-        P->tx[k] = (int)rx;
-        P->ty[k] = (int)ry;
+        if (fabs(tx - rx) <= 1e-9) tx = rx;   /* integer shifts stay exact translations */
+        if (fabs(ty - ry) <= 1e-9) ty = ry;
+        P->tx[k] = (int)floor(tx);
+        P->ty[k] = (int)floor(ty);
+        P->fx[k] = tx - floor(tx);
+        P->fy[k] = ty - floor(ty);
     }
     double s = 0;
     for (int i = 0; i < psf_size * psf_size; ++i) s += psf[i];
@@ -74,8 +79,42 @@ int orc_set_decimation(orc_problem *P, int mode) {
     return 0;
 }
 
+/* (M_k x)(u, v) = sum_{p, q in {0, 1}} wy_p wx_q x(u + ty_k + p, v + tx_k + q), x zero outside
+ * the grid, wy = (1 - fy_k, fy_k), wx = (1 - fx_k, fx_k): a translation for integer shifts,
+ * bilinear interpolation otherwise.  The value at one pixel of B's input: */
+static double motion_at(const orc_problem *P, int k, const double *x, int bu, int bv) {
+    const int H = HRH(P), W = HRW(P);
+    const double wy[2] = {1.0 - P->fy[k], P->fy[k]}, wx[2] = {1.0 - P->fx[k], P->fx[k]};
+    double s = 0.0;
+    for (int p = 0; p < 2; ++p) {
+        const int u = bu + P->ty[k] + p;
+        if (wy[p] == 0.0 || u < 0 || u >= H) continue;
+        for (int q = 0; q < 2; ++q) {
+            const int v = bv + P->tx[k] + q;
+            if (wx[q] == 0.0 || v < 0 || v >= W) continue;
+            s += wy[p] * wx[q] * x[(long)u * W + v];
+        }
+    }
+    return s;
+}
+
+/* The adjoint of motion_at: pixel (bu, bv) of B's input scatters `val` back to x. */
+static void motion_at_adj(const orc_problem *P, int k, double val, int bu, int bv, double *out) {
+    const int H = HRH(P), W = HRW(P);
+    const double wy[2] = {1.0 - P->fy[k], P->fy[k]}, wx[2] = {1.0 - P->fx[k], P->fx[k]};
+    for (int p = 0; p < 2; ++p) {
+        const int u = bu + P->ty[k] + p;
+        if (wy[p] == 0.0 || u < 0 || u >= H) continue;
+        for (int q = 0; q < 2; ++q) {
+            const int v = bv + P->tx[k] + q;
+            if (wx[q] == 0.0 || v < 0 || v >= W) continue;
+            out[(long)u * W + v] += wy[p] * wx[q] * val;
+        }
+    }
+}
+
 /* (A_k x)(i, j) = (D B M_k x)(i, j)                                            Eq. 1
- *   (M_k x)(u, v) = x(u + ty_k, v + tx_k), zero when that pixel is outside the grid;
+ *   (M_k x)(u, v) as above (x(u + ty_k, v + tx_k) for integer shifts), zero outside the grid;
  *   (B z)(u, v)   = sum_{a,b} h(a, b) z(u - a, v - b), z zero outside the grid;
  *   (D w)(i, j)   = w(f i, f j), or with binning
  *   (D w)(i, j)   = (1 / f^2) sum_{a', b' = 0}^{f-1} w(f i + a', f j + b').              */
@@ -84,6 +123,7 @@ void orc_forward(const orc_problem *P, int k, const double *x, double *out) {
     const int ty = P->ty[k], tx = P->tx[k];
     const int nb = P->decim == ORC_DECIM_BIN ? f : 1;   /* block side averaged by D */
     const double wd = 1.0 / ((double)nb * nb);
+    const int frac = P->fy[k] != 0.0 || P->fx[k] != 0.0;
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < P->h; ++i) {
         for (int j = 0; j < P->w; ++j) {
@@ -95,13 +135,15 @@ void orc_forward(const orc_problem *P, int k, const double *x, double *out) {
                     for (int a = -R; a <= R; ++a) {
                         int bu = cu - a;                 /* pixel of B's input, M_k x */
                         if (bu < 0 || bu >= H) continue;
-                        int u = bu + ty;                 /* pixel of x read by M_k */
-                        if (u < 0 || u >= H) continue;
                         for (int b = -R; b <= R; ++b) {
                             int bv = cv - b;
                             if (bv < 0 || bv >= W) continue;
-                            int v = bv + tx;
-                            if (v < 0 || v >= W) continue;
+                            if (frac) {
+                                w += P->psf[(a + R) * S + (b + R)] * motion_at(P, k, x, bu, bv);
+                                continue;
+                            }
+                            int u = bu + ty, v = bv + tx;   /* pixel of x read by M_k */
+                            if (u < 0 || u >= H || v < 0 || v >= W) continue;
                             w += P->psf[(a + R) * S + (b + R)] * x[(long)u * W + v];
                         }
                     }
@@ -119,6 +161,7 @@ void orc_adjoint(const orc_problem *P, int k, const double *e, double *out) {
     const int ty = P->ty[k], tx = P->tx[k];
     const int nb = P->decim == ORC_DECIM_BIN ? f : 1;
     const double wd = 1.0 / ((double)nb * nb);
+    const int frac = P->fy[k] != 0.0 || P->fx[k] != 0.0;
     memset(out, 0, sizeof(double) * (size_t)H * W);
     for (int i = 0; i < P->h; ++i) {
         for (int j = 0; j < P->w; ++j) {
@@ -129,13 +172,15 @@ void orc_adjoint(const orc_problem *P, int k, const double *e, double *out) {
                     for (int a = -R; a <= R; ++a) {
                         int bu = cu - a;
                         if (bu < 0 || bu >= H) continue;
-                        int u = bu + ty;
-                        if (u < 0 || u >= H) continue;
                         for (int b = -R; b <= R; ++b) {
                             int bv = cv - b;
                             if (bv < 0 || bv >= W) continue;
-                            int v = bv + tx;
-                            if (v < 0 || v >= W) continue;
+                            if (frac) {
+                                motion_at_adj(P, k, P->psf[(a + R) * S + (b + R)] * ev, bu, bv, out);
+                                continue;
+                            }
+                            int u = bu + ty, v = bv + tx;
+                            if (u < 0 || u >= H || v < 0 || v >= W) continue;
                             out[(long)u * W + v] += P->psf[(a + R) * S + (b + R)] * ev;
                         }
                     }
@@ -415,7 +460,9 @@ double orc_curvature(const orc_problem *P, const double *x, const double *y, con
 }
 
 /* Multi-image interpolation (Sec. 4.1.1): every LR sample is placed at the HR pixel it was
- * taken at, x0 = sum_k M_k^T D^T y_k / sum_k M_k^T D^T 1, and 0 where no sample falls. */
+ * taken at, x0 = sum_k M_k^T D^T y_k / sum_k M_k^T D^T 1 with D the point sampling, and 0
+ * where no sample falls.  With a non-integer shift M_k^T spreads a sample over the 2 x 2 HR
+ * pixels around its position with the bilinear weights. */
 void orc_shift_add(const orc_problem *P, const double *y, double *x0) {
     const int H = HRH(P), W = HRW(P), f = P->f;
     const long n = (long)H * W, m = (long)P->h * P->w;
@@ -424,10 +471,8 @@ void orc_shift_add(const orc_problem *P, const double *y, double *x0) {
     for (int k = 0; k < P->K; ++k)
         for (int i = 0; i < P->h; ++i)
             for (int j = 0; j < P->w; ++j) {
-                int u = f * i + P->ty[k], v = f * j + P->tx[k];
-                if (u < 0 || u >= H || v < 0 || v >= W) continue;
-                x0[(long)u * W + v] += y[k * m + (long)i * P->w + j];
-                cnt[(long)u * W + v] += 1.0;
+                motion_at_adj(P, k, y[k * m + (long)i * P->w + j], f * i, f * j, x0);
+                motion_at_adj(P, k, 1.0, f * i, f * j, cnt);
             }
     for (long i = 0; i < n; ++i) x0[i] = cnt[i] > 0 ? x0[i] / cnt[i] : 0.0;
     free(cnt);

@@ -15,7 +15,9 @@
  *   solver            Moller's scaled conjugate gradient (Sec. 3.1, Algorithm 1, Table 1)
  *
  * Readings where the paper is silent (each is stated where it is used in the .c file):
- *   M_k  translation by the integer HR shift t_k = f * s_k (s_k in LR px), x zero outside
+ *   M_k  translation by the HR shift t_k = f * s_k (s_k in LR px), x zero outside; for a
+ *        non-integer t_k = n_k + a_k (n_k integer, 0 < a_k < 1) per axis, bilinear
+ *        interpolation: (M_k x)(u) = (1 - a_k) x(u + n_k) + a_k x(u + n_k + 1)
  *   B    convolution with the PSF h (normalised to sum 1), zero outside the HR grid
  *   D    sampling at HR position (f i, f j), or (ORC_DECIM_BIN) the mean of the f x f block
  *        whose first pixel is (f i, f j): the 2 x 2 binning of the synthetic study (Sec. 4.1.1)
@@ -53,6 +55,8 @@ typedef struct {
     int data_norm;            /* ORC_NORM_L2 (default) or ORC_NORM_L1 */
     double data_eps;          /* Charbonnier smoothing of the L1 data term (> 0) */
     int decim;                /* ORC_DECIM_POINT (default) or ORC_DECIM_BIN */
+    double fy[ORC_MAXK];      /* fractional part a_k of the HR shift, rows (ty = floor) */
+    double fx[ORC_MAXK];      /* fractional part a_k of the HR shift, cols (tx = floor) */
 } orc_problem;
 
 /* one row of the SCG trace per iteration (failed iterations included) */

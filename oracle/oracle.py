@@ -28,6 +28,7 @@ class _Problem(C.Structure):
         ("lambda_", C.c_double), ("btv_alpha", C.c_double), ("btv_w", C.c_int),
         ("eps", C.c_double), ("reg", C.c_int),
         ("data_norm", C.c_int), ("data_eps", C.c_double), ("decim", C.c_int),
+        ("fy", C.c_double * MAXK), ("fx", C.c_double * MAXK),
     ]
 
 

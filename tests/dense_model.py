@@ -59,6 +59,23 @@ def motion(H, W, ty, tx):
     return M
 
 
+def motion_frac(H, W, sy, sx):
+    """M_k for a real HR shift (sy, sx): bilinear interpolation, (M x)(u, v) = sum over the
+    4 pixels (floor(u + sy) + p, floor(v + sx) + q), p, q in {0, 1}, of the weights
+    (1 - a_y or a_y) (1 - a_x or a_x), a = the fractional parts; zero outside the grid."""
+    ny, nx = int(np.floor(sy)), int(np.floor(sx))
+    ay, ax = sy - ny, sx - nx
+    M = np.zeros((H * W, H * W))
+    for u in range(H):
+        for v in range(W):
+            for p, wy in ((0, 1 - ay), (1, ay)):
+                for q, wx in ((0, 1 - ax), (1, ax)):
+                    uu, vv = u + ny + p, v + nx + q
+                    if wy * wx != 0 and 0 <= uu < H and 0 <= vv < W:
+                        M[idx(u, v, W), idx(uu, vv, W)] += wy * wx
+    return M
+
+
 def system_matrices(h, w, f, shifts_lr, psf, binned=False):
     """A_k = D B M_k for every frame; psf is normalised to sum 1 here."""
     H, W = f * h, f * w
@@ -68,6 +85,10 @@ def system_matrices(h, w, f, shifts_lr, psf, binned=False):
     B = blur(H, W, psf)
     out = []
     for dx, dy in shifts_lr:
-        ty, tx = int(round(f * dy)), int(round(f * dx))
-        out.append(D @ B @ motion(H, W, ty, tx))
+        sy, sx = f * dy, f * dx
+        if sy == round(sy) and sx == round(sx):
+            M = motion(H, W, int(round(sy)), int(round(sx)))
+        else:
+            M = motion_frac(H, W, sy, sx)
+        out.append(D @ B @ M)
     return out

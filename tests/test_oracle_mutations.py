@@ -14,7 +14,10 @@ SRC = os.path.join(ROOT, "oracle", "misr_oracle.c")
 MUTANTS = {
     "convolution_flipped": ("int bu = cu - a;", "int bu = cu + a;"),
     "blur_padding_dropped": ("if (bu < 0 || bu >= H) continue;", "/* row padding dropped */"),
-    "shift_sign": ("int u = bu + ty;", "int u = bu - ty;"),
+    "shift_sign": ("int u = bu + ty, v = bv + tx;", "int u = bu - ty, v = bv + tx;"),
+    "bilinear_weights_swapped": ("const double wy[2] = {1.0 - P->fy[k], P->fy[k]}, wx[2] = {1.0 - P->fx[k], P->fx[k]};",
+                                 "const double wy[2] = {P->fy[k], 1.0 - P->fy[k]}, wx[2] = {1.0 - P->fx[k], P->fx[k]};"),
+    "bilinear_second_tap_offset": ("const int u = bu + P->ty[k] + p;", "const int u = bu + P->ty[k] - p;"),
     "gamma_exponent": ("return pow(P->btv_alpha, dx + dy);", "return pow(P->btv_alpha, dx > dy ? dx : dy);"),
     "btv_window_short": ("for (int dy = 0; dy < P->btv_w; ++dy) {\n        for (int dx = 0; dx < P->btv_w; ++dx) {\n            if (dx == 0 && dy == 0) continue;\n#pragma omp parallel for schedule(static)\n            for (int u = 0; u < H; ++u) {\n                double s = 0;\n                if (u + dy < H)",
                          "for (int dy = 0; dy < P->btv_w - 1; ++dy) {\n        for (int dx = 0; dx < P->btv_w; ++dx) {\n            if (dx == 0 && dy == 0) continue;\n#pragma omp parallel for schedule(static)\n            for (int u = 0; u < H; ++u) {\n                double s = 0;\n                if (u + dy < H)"),

@@ -534,3 +534,67 @@ def test_binned_gradient_central_differences(orc, norm):
     assert np.linalg.norm(fd - g) <= 1e-7 * np.linalg.norm(g)
     with pytest.raises(ValueError):
         orc.Problem(4, 4, 2, gen.half_pixel_shifts(), gen.gaussian_psf(3, 0.5), decimation=2)
+
+
+# ------------------------------------------------------------------ non-integer shifts (bilinear M_k)
+
+FRAC_SHIFTS = [(0.0, 0.0), (0.6, 0.1), (0.15, 0.55), (-0.3, 0.85)]
+
+
+@pytest.mark.parametrize("binned", [False, True])
+def test_bilinear_forward_and_adjoint_equal_dense(orc, binned):
+    """Non-integer HR shifts (reading: bilinear M_k): the oracle's A_k and A_k^T equal the
+    textbook D B M_k built from a dense bilinear interpolation matrix, and its transpose."""
+    h = w = 4
+    psf = _asym_psf(23, 3)
+    kw = dict(decimation=orc.DECIM_BIN) if binned else {}
+    P = orc.Problem(h, w, 2, FRAC_SHIFTS, psf, **kw)
+    A = dm.system_matrices(h, w, 2, FRAC_SHIFTS, psf, binned=binned)
+    n, m = P.H * P.W, h * w
+    for k in range(P.K):
+        cols = np.stack([P.forward(k, np.eye(n)[c].reshape(P.H, P.W)).ravel() for c in range(n)], axis=1)
+        np.testing.assert_allclose(cols, A[k], rtol=0, atol=1e-15)
+        cols = np.stack([P.adjoint(k, np.eye(m)[c].reshape(h, w)).ravel() for c in range(m)], axis=1)
+        np.testing.assert_allclose(cols, A[k].T, rtol=0, atol=1e-15)
+
+
+def test_half_pixel_shift_is_the_mean_of_two_translations(orc):
+    """A shift of n + 1/2 HR px is the mean of the translations by n and n + 1, exactly, at a
+    size the dense test does not reach (the integer ones are pinned by the dense D B M)."""
+    h, w, f = 9, 11, 2
+    psf = gen.gaussian_psf(5, 0.7)
+    x = gen.random_field((f * h, f * w), 61)
+    Ph = orc.Problem(h, w, f, [(0.75, 0.25)], psf)          # HR shift (0.5, 1.5)
+    P0 = orc.Problem(h, w, f, [(0.5, 0.0), (0.5, 0.5), (1.0, 0.0), (1.0, 0.5)], psf)
+    ref = 0.25 * sum(P0.forward(k, x) for k in range(4))
+    np.testing.assert_allclose(Ph.forward(0, x), ref, rtol=1e-14, atol=1e-14)
+
+
+def test_bilinear_shift_add_closed_form(orc):
+    """f = 1, one frame shifted by half a pixel along x: each sample is spread half and half
+    over its two neighbouring HR pixels, so x0 is the mean of the two samples there (one at the
+    first column)."""
+    h, w = 5, 7
+    y = gen.random_field((1, h, w), 62)
+    P = orc.Problem(h, w, 1, [(0.5, 0.0)], np.ones((1, 1)))
+    ref = np.empty((h, w))
+    ref[:, 0] = y[0, :, 0]
+    ref[:, 1:] = 0.5 * (y[0, :, 1:] + y[0, :, :-1])
+    np.testing.assert_allclose(P.shift_add(y), ref, rtol=1e-15)
+
+
+@pytest.mark.parametrize("norm", ["l2", "l1"])
+def test_bilinear_gradient_central_differences(orc, norm):
+    kw = dict(data_norm=orc.NORM_L1, data_eps=0.05) if norm == "l1" else {}
+    P = orc.Problem(5, 4, 2, FRAC_SHIFTS, gen.gaussian_psf(3, 0.6), lam=0.01, eps=0.1, **kw)
+    y = gen.random_field((4, 5, 4), 63, 0, 2)
+    x = _distinct_levels(P, 6)
+    J0, g = P.gradient(x, y)
+    hstep = 1e-6
+    fd = np.empty_like(x)
+    for i in range(P.H):
+        for j in range(P.W):
+            xp = x.copy(); xp[i, j] += hstep
+            xm = x.copy(); xm[i, j] -= hstep
+            fd[i, j] = (P.objective(xp, y) - P.objective(xm, y)) / (2 * hstep)
+    assert np.linalg.norm(fd - g) <= 1e-7 * np.linalg.norm(g)
