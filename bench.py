@@ -228,6 +228,19 @@ def measure_paper_ct(args, wl, shifts, tuned, xt, stream, dist, device, peak):
     return out
 
 
+def measure_subpixel(args, wl, xt, stream, dist, device, peak):
+    """Non-integer detector shifts (bilinear M_k, per-phase blur taps) at the headline size: the
+    half-pixel pattern with stage errors of a few hundredths of a pixel (x stage 0.02 / 0.51,
+    y stage 0.04 / 0.53 LR px), a 3x3 Gaussian PSF, 100 SCG iterations; frames made with that
+    model.  The tile shape is 32x32 (the one compiled with per-phase taps)."""
+    shifts = [(dx, dy) for dy in (0.04, 0.53) for dx in (0.02, 0.51)]
+    out = measure_variant(args, wl, shifts, gen.gaussian_psf(3, 0.5), 2, xt, stream, dist, device, peak,
+                          wl["iters"])
+    out["model"] = ("2048^2 -> 4096^2, f=2, shifts (dx, dy) in {0.02, 0.51} x {0.04, 0.53} LR px (bilinear M_k), "
+                    "3x3 Gaussian sigma 0.5, L2 data term, lambda 0.01, 100 SCG iterations")
+    return out
+
+
 def measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak):
     """Multi-image interpolation (misr_interpolate), the paper's non-iterative comparator, on
     the same frames: rate, HBM bandwidth (frames read once, HR image written once) and the image
@@ -719,6 +732,7 @@ def main():
     achieved = PASS_BYTES_PER_PX * H * W / (pass_ms * 1e-3) / 1e9
     l1 = measure_l1(args, wl, shifts, psf, tuned, y, xt, stream, dist, device, peak)
     paper_ct = measure_paper_ct(args, wl, shifts, tuned, xt, stream, dist, device, peak)
+    subpixel = measure_subpixel(args, wl, xt, stream, dist, device, peak)
     interp = measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -741,6 +755,7 @@ def main():
         "batched": batched,
         "l1": l1,
         "paper_ct_setting": paper_ct,
+        "subpixel": subpixel,
         "interpolation": interp,
         # per solve: prepare, the initial pass and every SCG pass (the fused pass kernel and its
         # reduction kernel), finalize

@@ -60,8 +60,15 @@ typedef struct misr_desc {
     int32_t lr_h, lr_w;      /* LR frame rows, columns (>= 1) */
     int32_t K;               /* number of frames, 1 <= K <= factor^2 */
     int32_t factor;          /* magnification f, 1 <= f <= 8; HR = f*lr_h x f*lr_w */
-    const float *shifts;     /* host, K pairs (dx, dy) in LR px; f*dx and f*dy must be integers
-                                in [0, f-1] and the K pairs distinct (one frame per HR phase) */
+    const float *shifts;     /* host, K pairs (dx, dy) in LR px, f*dx and f*dy in [0, f) (within
+                                1e-4 of an integer counts as that integer).  Their integer parts
+                                are the frame's HR phase, one frame per phase.  Non-integer parts
+                                make M_k a bilinear interpolation (reading of Eq. 1): they must
+                                form a product lattice (one fractional y shift per HR row phase,
+                                one x shift per column phase, as x and y detector stages give),
+                                the blur widens by one tap per axis (a PSF of at most 3x3, or 1x1
+                                with binning at f = 2), and the plan runs the 32x32 tile shape;
+                                else MISR_ENOTIMPL */
     const float *psf;        /* host, psf_size^2 row-major PSF of B (Eq. 1); must be separable;
                                 normalised to sum 1 by the plan; B is a convolution with it */
     int32_t psf_size;        /* odd, 1..5 */
@@ -339,7 +346,9 @@ misr_status misr_server_counters(misr_server_t server, int64_t *out);
  * geometry of `desc` (on zeroed device buffers it allocates and frees), and remembers the
  * fastest for plans of the same HR size created with tile_shape = MISR_TILE_AUTO in this
  * process.  shape_out (may be NULL): the chosen MISR_TILE_*; ms_out (may be NULL): the time per
- * pass of each shape, MISR_N_TILE_SHAPES values in MISR_TILE_* order.  passes: 1..1000.
+ * pass of each shape, MISR_N_TILE_SHAPES values in MISR_TILE_* order.  passes: 1..1000.  A
+ * descriptor with non-integer shifts runs on MISR_TILE_32x32 only: that shape is returned at
+ * once, nothing is timed or remembered, and ms_out is zeroed.
  * Errors: MISR_EINVAL (descriptor, passes), MISR_ENOMEM, MISR_ECUDA. */
 misr_status misr_autotune(const misr_desc *desc, int32_t passes, int32_t *shape_out, double *ms_out);
 

@@ -128,7 +128,7 @@ static misr_status validate(const misr_desc *d) {
 // sum_c h'(c) z(f i - c) with h'(c) = (1/f) sum_{a'=0}^{f-1} h(c + a'), c in [-R-f+1, R]; the
 // tap masks of the frames (B's zero padding in front of M_k: the input pixel f i - c >= 0) are
 // those of the point-sampled blur with h' in place of h.
-static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
+static misr_status psf_taps(const misr_desc *d, double *hy, double *hx, int *lowest) {
     const int S = d->psf_size, R = S / 2;
     double sum = 0;
     for (int i = 0; i < S * S; ++i) sum += d->psf[i];
@@ -142,7 +142,8 @@ static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
         for (int b = 0; b < S; ++b)
             if (std::fabs(h[a * S + b] - rs[a] * cs[b]) > 1e-6 * hmax)
                 return fail(MISR_EINVAL, "PSF is not separable");
-    for (int i = 0; i < 2 * PSF_R + 1; ++i) { hy[i] = 0.f; hx[i] = 0.f; }
+    for (int i = 0; i < 2 * PSF_R + 1; ++i) { hy[i] = 0.0; hx[i] = 0.0; }
+    *lowest = -R;
     if (d->decimation == MISR_DECIM_BIN && d->factor > 1) {
         const int f = d->factor;
         if (R + f - 1 > PSF_R)
@@ -152,12 +153,79 @@ static misr_status psf_taps(const misr_desc *d, float *hy, float *hx) {
             double sy = 0, sx = 0;
             for (int a2 = 0; a2 < f; ++a2)
                 if (c + a2 >= -R && c + a2 <= R) { sy += rs[c + a2 + R]; sx += cs[c + a2 + R]; }
-            hy[c + PSF_R] = (float)(sy / f);
-            hx[c + PSF_R] = (float)(sx / f);
+            hy[c + PSF_R] = sy / f;
+            hx[c + PSF_R] = sx / f;
         }
+        *lowest = -R - f + 1;
         return MISR_OK;
     }
-    for (int a = -R; a <= R; ++a) { hy[a + PSF_R] = (float)rs[a + R]; hx[a + PSF_R] = (float)cs[a + R]; }
+    for (int a = -R; a <= R; ++a) { hy[a + PSF_R] = rs[a + R]; hx[a + PSF_R] = cs[a + R]; }
+    return MISR_OK;
+}
+
+// The frames' geometry and the blur taps of a descriptor into the problem record.
+// An HR shift t = f s is split per axis into t = n + a, n = floor(t) in [0, f - 1], 0 <= a < 1
+// (t within 1e-4 of an integer is that integer).  The frame's samples sit at HR pixels
+// f (i, j) + (n_y, n_x): one frame per phase (n_y, n_x).  A non-integer t is bilinear
+// interpolation, (M x)(u) = (1 - a) x(u + n) + a x(u + n + 1), so per axis the frame's blur
+// is h_k(c) = (1 - a) h(c) + a h(c + 1), c in [lowest - 1, R], over x at s - c for a sample at
+// s.  At the top / left border the second part of the tap c = f i (s - c = n) reads B's input
+// pixel -1, which B's zero padding drops: that tap weighs (1 - a) h(c) alone.  The taps of a
+// frame must depend on one axis's phase only (a product lattice of shifts, as x and y stages
+// give): a_y per row phase, a_x per column phase.  phased = 1 when some a is not 0.
+static misr_status setup_geometry(const misr_desc &d, DevProblem &hp) {
+    const int f = d.factor;
+    for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
+    double ay[MAXF], ax[MAXF];
+    bool sy[MAXF] = {}, sx[MAXF] = {};
+    for (int i = 0; i < MAXF; ++i) ay[i] = ax[i] = 0.0;
+    bool frac_y = false, frac_x = false;
+    for (int k = 0; k < d.K; ++k) {
+        double tx = (double)f * d.shifts[2 * k], ty = (double)f * d.shifts[2 * k + 1];
+        if (!std::isfinite(tx) || !std::isfinite(ty)) return fail(MISR_EINVAL, "frame %d: shift is not finite", k);
+        if (std::fabs(tx - std::floor(tx + 0.5)) <= 1e-4) tx = std::floor(tx + 0.5);
+        if (std::fabs(ty - std::floor(ty + 0.5)) <= 1e-4) ty = std::floor(ty + 0.5);
+        if (tx < 0 || tx >= f || ty < 0 || ty >= f)
+            return fail(MISR_EINVAL, "frame %d: shift must lie in [0, 1) LR px", k);
+        const int nx = (int)std::floor(tx), ny = (int)std::floor(ty);
+        const double fx = tx - nx, fy = ty - ny;
+        const int ph = ny * f + nx;
+        if (hp.frame_of_phase[ph] >= 0)
+            return fail(MISR_EINVAL, "frames %d and %d sample the same HR phase", hp.frame_of_phase[ph], k);
+        if ((sy[ny] && std::fabs(ay[ny] - fy) > 1e-6) || (sx[nx] && std::fabs(ax[nx] - fx) > 1e-6))
+            return fail(MISR_ENOTIMPL, "frame %d: non-integer shifts must form a product lattice (one fractional y "
+                                       "shift per HR row phase, one x shift per column phase)", k);
+        sy[ny] = sx[nx] = true;
+        ay[ny] = fy; ax[nx] = fx;
+        frac_y |= fy != 0.0;
+        frac_x |= fx != 0.0;
+        hp.frame_of_phase[ph] = k;
+        hp.ty[k] = ny; hp.tx[k] = nx;
+    }
+    double hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];
+    int lowest = 0;
+    misr_status s = psf_taps(&d, hy, hx, &lowest);
+    if (s != MISR_OK) return s;
+    for (int i = 0; i < 2 * PSF_R + 1; ++i) { hp.hy[i] = (float)hy[i]; hp.hx[i] = (float)hx[i]; }
+    hp.phased = frac_y || frac_x;
+    if (!hp.phased) return MISR_OK;
+    if (lowest - 1 < -PSF_R)
+        return fail(MISR_ENOTIMPL, "non-integer shifts widen the blur by one tap per axis: with this PSF%s it spans "
+                                   "%d taps, %d are compiled (use a 3x3 PSF)",
+                    d.decimation == MISR_DECIM_BIN ? " and binning" : "", PSF_R - lowest + 2, 2 * PSF_R + 1);
+    if (d.tile_shape != MISR_TILE_AUTO && d.tile_shape - 1 != PHASED_SHAPE)
+        return fail(MISR_ENOTIMPL, "non-integer shifts run on the 32x32 tile shape only");
+    for (int p = 0; p < f; ++p) {
+        hp.ay[p] = (float)ay[p];
+        hp.ax[p] = (float)ax[p];
+        for (int c = -PSF_R; c <= PSF_R; ++c) {
+            const double nyt = c + 1 <= PSF_R ? hy[c + 1 + PSF_R] : 0.0, nxt = c + 1 <= PSF_R ? hx[c + 1 + PSF_R] : 0.0;
+            hp.tph[TPH_FY][p][c + PSF_R] = (float)((1.0 - ay[p]) * hy[c + PSF_R] + ay[p] * nyt);
+            hp.tph[TPH_PY][p][c + PSF_R] = (float)((1.0 - ay[p]) * hy[c + PSF_R]);
+            hp.tph[TPH_FX][p][c + PSF_R] = (float)((1.0 - ax[p]) * hx[c + PSF_R] + ax[p] * nxt);
+            hp.tph[TPH_PX][p][c + PSF_R] = (float)((1.0 - ax[p]) * hx[c + PSF_R]);
+        }
+    }
     return MISR_OK;
 }
 
@@ -180,31 +248,43 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// the pass kernel of shape S and variant V (bit 0 bf16 r and p, bit 1 the L1 data term), and
-// its dynamic shared memory
+// the pass kernel of shape S and variant V (bit 0 bf16 r and p, bit 1 the L1 data term, bit 2
+// per-phase taps), and its dynamic shared memory; the per-phase variants exist for the
+// PHASED_SHAPE only
+template <int S, int V>
+constexpr bool compiled_variant() { return (V & 4) == 0 || S == PHASED_SHAPE; }
 template <int S, int V>
 constexpr auto pass_kernel() {
-    return scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], (V & 1) != 0, (V & 2) != 0>;
+    static_assert(compiled_variant<S, V>(), "variant not compiled for this shape");
+    return scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], (V & 1) != 0, (V & 2) != 0, (V & 4) != 0>;
 }
 template <int S, int V>
 constexpr size_t pass_smem() { return ShapeGeo<S>::smem_bytes((V & 2) != 0); }
 template <typename F>
 auto with_variant(int v, F &&f) {
-    static_assert(N_VARIANTS == 4, "one case per compiled variant");
+    static_assert(N_VARIANTS == 8, "one case per compiled variant");
     switch (v) {
     case 0: return f(std::integral_constant<int, 0>());
     case 1: return f(std::integral_constant<int, 1>());
     case 2: return f(std::integral_constant<int, 2>());
-    default: return f(std::integral_constant<int, 3>());
+    case 3: return f(std::integral_constant<int, 3>());
+    case 4: return f(std::integral_constant<int, 4>());
+    case 5: return f(std::integral_constant<int, 5>());
+    case 6: return f(std::integral_constant<int, 6>());
+    default: return f(std::integral_constant<int, 7>());
     }
 }
 
 template <int S, int V>
 static misr_status set_attrs_one() {
-    auto *k = pass_kernel<S, V>();
-    CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<S, V>()));
-    CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    return MISR_OK;
+    if constexpr (!compiled_variant<S, V>()) {
+        return MISR_OK;
+    } else {
+        auto *k = pass_kernel<S, V>();
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<S, V>()));
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        return MISR_OK;
+    }
 }
 
 static misr_status set_pass_attrs() {
@@ -221,30 +301,36 @@ static misr_status set_pass_attrs() {
     return MISR_OK;
 }
 
-// CTAs of the fused pass resident on the whole GPU, per shape and data term (the L1 variant
-// takes more shared memory)
-static int resident_ctas(int shape, bool l1) {
-    static int cached[N_SHAPES][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
-    if (cached[shape][l1] >= 0) return cached[shape][l1];
+// CTAs of the fused pass resident on the whole GPU, per shape and variant (the L1 and
+// per-phase variants take more shared memory)
+static int resident_ctas(int shape, int variant) {
+    static int cached[N_SHAPES][N_VARIANTS];
+    static bool init = false;
+    if (!init) {
+        for (auto &a : cached)
+            for (int &c : a) c = -1;
+        init = true;
+    }
+    if (cached[shape][variant] >= 0) return cached[shape][variant];
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     with_shape(shape, [&](auto S) {
-        constexpr int s = decltype(S)::value;
-        if (l1)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<s, 2>(), SHAPE_NT[s], pass_smem<s, 2>());
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<s, 0>(), SHAPE_NT[s], pass_smem<s, 0>());
-        return 0;
+        return with_variant(variant, [&](auto V) {
+            constexpr int s = decltype(S)::value, v = decltype(V)::value;
+            if constexpr (compiled_variant<s, v>())
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<s, v>(), SHAPE_NT[s], pass_smem<s, v>());
+            return 0;
+        });
     });
     cudaGetLastError();
-    cached[shape][l1] = sms * per_sm;
-    return cached[shape][l1];
+    cached[shape][variant] = sms * std::max(per_sm, 1);
+    return cached[shape][variant];
 }
 
 // persistent grid: one CTA per resident slot, at most one per tile
-static int pass_grid(int shape, bool l1, int n_tiles) {
-    return std::max(1, std::min(n_tiles, resident_ctas(shape, l1)));
+static int pass_grid(int shape, int variant, int n_tiles) {
+    return std::max(1, std::min(n_tiles, resident_ctas(shape, variant)));
 }
 
 static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double beta, cudaStream_t s) {
@@ -362,8 +448,12 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
             CK(with_shape(sh, [&](auto S) {
                 return with_variant(v, [&](auto V) {
                     constexpr int k = decltype(S)::value, vv = decltype(V)::value;
-                    return launch_pdl(pass_kernel<k, vv>(), pass_grid(k, (vv & 2) != 0, n), SHAPE_NT[k],
-                                      pass_smem<k, vv>(), s, probs, t, n, work, mode, alpha, beta);
+                    if constexpr (!compiled_variant<k, vv>()) {
+                        return cudaErrorInvalidValue;   // plans with per-phase taps take the PHASED_SHAPE
+                    } else {
+                        return launch_pdl(pass_kernel<k, vv>(), pass_grid(k, vv, n), SHAPE_NT[k], pass_smem<k, vv>(), s,
+                                          probs, t, n, work, mode, alpha, beta);
+                    }
                 });
             }));
         }
@@ -391,22 +481,9 @@ misr_status misr_host::launch_finalize_raw(const DevProblem *probs, int pidx, si
 misr_status misr_host::check_desc(const misr_desc &d) {
     misr_status s = validate(&d);
     if (s != MISR_OK) return s;
-    const int f = d.factor;
-    int seen[MAXF * MAXF];
-    for (int i = 0; i < MAXF * MAXF; ++i) seen[i] = -1;
-    for (int k = 0; k < d.K; ++k) {
-        const double tx = (double)f * d.shifts[2 * k], ty = (double)f * d.shifts[2 * k + 1];
-        const double rx = std::floor(tx + 0.5), ry = std::floor(ty + 0.5);
-        if (std::fabs(tx - rx) > 1e-4 || std::fabs(ty - ry) > 1e-4)
-            return fail(MISR_ENOTIMPL, "frame %d: shift times factor is not an integer (subpixel HR warps not supported)", k);
-        if (rx < 0 || rx > f - 1 || ry < 0 || ry > f - 1)
-            return fail(MISR_EINVAL, "frame %d: shift must lie in [0, 1 - 1/f] LR px", k);
-        const int ph = (int)ry * f + (int)rx;
-        if (seen[ph] >= 0) return fail(MISR_EINVAL, "frames %d and %d sample the same HR phase", seen[ph], k);
-        seen[ph] = k;
-    }
-    float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];
-    return psf_taps(&d, hy, hx);
+    DevProblem hp{};
+    hp.f = d.factor;
+    return setup_geometry(d, hp);
 }
 
 extern "C" {
@@ -434,20 +511,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     hp.pitch = (hp.W + 7) & ~7;   // 16-byte rows for float and bf16 planes
     hp.wait_tries = (int)TMA_WAIT_TRIES;
     hp.iters = d.iters;
-    for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
-    for (int k = 0; k < d.K; ++k) {
-        const double tx = (double)f * d.shifts[2 * k], ty = (double)f * d.shifts[2 * k + 1];
-        const double rx = std::floor(tx + 0.5), ry = std::floor(ty + 0.5);
-        if (std::fabs(tx - rx) > 1e-4 || std::fabs(ty - ry) > 1e-4)
-            return fail(MISR_ENOTIMPL, "frame %d: shift times factor is not an integer (subpixel HR warps not supported)", k);
-        if (rx < 0 || rx > f - 1 || ry < 0 || ry > f - 1)
-            return fail(MISR_EINVAL, "frame %d: shift must lie in [0, 1 - 1/f] LR px", k);
-        const int ph = (int)ry * f + (int)rx;
-        if (hp.frame_of_phase[ph] >= 0) return fail(MISR_EINVAL, "frames %d and %d sample the same HR phase", hp.frame_of_phase[ph], k);
-        hp.frame_of_phase[ph] = k;
-        hp.ty[k] = (int)ry; hp.tx[k] = (int)rx;
-    }
-    s = psf_taps(desc, hp.hy, hp.hx);
+    s = setup_geometry(d, hp);
     if (s != MISR_OK) return s;
     hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
     set_data_norm(hp, d);
@@ -461,7 +525,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
             if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
         }
     hp.eps_pairs = d.eps * eps_pairs;
-    set_shape(hp, pick_shape(d));
+    set_shape(hp, hp.phased ? PHASED_SHAPE : pick_shape(d));
     set_groups(hp);
 
     misr_plan_t p = new (std::nothrow) misr_plan_s();
@@ -610,6 +674,11 @@ misr_status misr_interpolate(misr_plan_t p, const void *y_dev, float *x_dev, mis
     DeviceGuard g(p->device);
     const float log_i0 = p->d.in_dtype == MISR_U16 ? logf(p->d.flat_field) : 0.f;
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->hp.phased) {   // non-integer shifts: each pixel gathers its bilinear weights
+        interpolate_phased_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, x_dev);
+        CK(cudaGetLastError());
+        return MISR_OK;
+    }
     static_assert(MAXF == 8, "one case per factor");
     switch (p->hp.f) {
     case 1: CK(launch_interpolate<1>(p, y_dev, x_dev, log_i0, s)); break;
@@ -1067,20 +1136,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
     hp.pitch = (hp.W + 7) & ~7;   // 16-byte rows for float and bf16 planes
     hp.wait_tries = (int)TMA_WAIT_TRIES;
     hp.iters = 0;
-    for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
-    for (int k = 0; k < d.K; ++k) {
-        const double tx = (double)f * d.shifts[2 * k], ty = (double)f * d.shifts[2 * k + 1];
-        const double rx = std::floor(tx + 0.5), ry = std::floor(ty + 0.5);
-        if (std::fabs(tx - rx) > 1e-4 || std::fabs(ty - ry) > 1e-4)
-            return fail(MISR_ENOTIMPL, "frame %d: shift times factor is not an integer (subpixel HR warps not supported)", k);
-        if (rx < 0 || rx > f - 1 || ry < 0 || ry > f - 1)
-            return fail(MISR_EINVAL, "frame %d: shift must lie in [0, 1 - 1/f] LR px", k);
-        const int ph = (int)ry * f + (int)rx;
-        if (hp.frame_of_phase[ph] >= 0) return fail(MISR_EINVAL, "frames %d and %d sample the same HR phase", hp.frame_of_phase[ph], k);
-        hp.frame_of_phase[ph] = k;
-        hp.ty[k] = (int)ry; hp.tx[k] = (int)rx;
-    }
-    misr_status s = psf_taps(&d, hp.hy, hp.hx);
+    misr_status s = setup_geometry(d, hp);
     if (s != MISR_OK) return s;
     hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
     set_data_norm(hp, d);
@@ -1163,6 +1219,18 @@ extern "C" misr_status misr_autotune(const misr_desc *desc, int32_t passes, int3
     if (passes < 1 || passes > 1000) return fail(MISR_EINVAL, "passes must be in [1, 1000]");
     misr_status st = check_desc(*desc);
     if (st != MISR_OK) return st;
+    {   // non-integer shifts run on the PHASED_SHAPE only: nothing to choose
+        DevProblem hp{};
+        hp.f = desc->factor;
+        misr_desc d = *desc;
+        d.tile_shape = MISR_TILE_AUTO;
+        if (setup_geometry(d, hp) == MISR_OK && hp.phased) {
+            if (shape_out) *shape_out = PHASED_SHAPE + 1;
+            if (ms_out)
+                for (int sh = 0; sh < N_SHAPES; ++sh) ms_out[sh] = 0.0;
+            return MISR_OK;
+        }
+    }
     const size_t in_bytes = (size_t)desc->K * desc->lr_h * desc->lr_w * (desc->in_dtype == MISR_U16 ? 2 : 4);
     void *y = nullptr;
     cudaError_t e = cudaMalloc(&y, in_bytes);

@@ -265,8 +265,28 @@ struct PassAcc {
 // per-problem constants staged in shared memory at CTA start
 enum {
     C_HX = 0, C_HY = 5, C_GAM = 10, C_CW = 19, C_LAMBDA = 28, C_EPS2 = 29, C_FMAG = 30, C_IEPS2 = 31,
-    C_DEPS = 32, C_DEPS2 = 33, C_N = 34   // C_DEPS*: the L1 data term's smoothing and its square
+    C_DEPS = 32, C_DEPS2 = 33, C_N = 34,  // C_DEPS*: the L1 data term's smoothing and its square
+    // per-phase taps (non-integer shifts): DevProblem::tph copied to C_T0 (16-byte aligned),
+    // table t, phase p at C_T0 + 64 t + 8 p
+    C_T0 = 36, C_NPH = C_T0 + 4 * MAXF * 8
 };
+
+// Per-phase tap weights (non-integer shifts).  Forward tap t of an output whose fwd_lim is lim
+// (BORDER): 0 past lim, the bilinear's first part alone at lim (its second part reads B's input
+// pixel -1), the full tap before.  Adjoint tap t of an output at x coordinate u reading the
+// sample of phase ns: 0 when u < ns, the first part alone when u == ns.
+template <bool BORDER>
+__device__ __forceinline__ float ph_fwd_w(const float *full, const float *part, int t, int lim) {
+    if (BORDER && t > lim) return 0.f;
+    if (BORDER && t == lim) return part[t + 2];
+    return full[t + 2];
+}
+template <bool BORDER>
+__device__ __forceinline__ float ph_adj_w(const float *full, const float *part, int t, int u, int ns) {
+    if (BORDER && u < ns) return 0.f;
+    if (BORDER && u == ns) return part[t + 2];
+    return full[t + 2];
+}
 
 // ---------------------------------------------------------------------------------------
 // Body of the fused pass on one tile.  BORDER: the tile's halo reaches outside the image, so
@@ -284,7 +304,9 @@ enum {
 // L1: the smoothed L1 data term.  B2 then keeps the owned residuals e' in EO and leaves
 // psi_d'(e') in the residual box for the adjoint, the gradient's data part has factor 1
 // instead of 2, and the curvature forms weight each sample by psi_d''(e').
-template <int TH, int TW, int NT, bool BORDER, bool RPB, bool L1, typename Hook>
+// PH: per-phase blur taps (non-integer shifts): every forward tap takes the taps of its
+// output's phase, every adjoint tap those of the sample it reads.
+template <int TH, int TW, int NT, bool BORDER, bool RPB, bool L1, bool PH, typename Hook>
 __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float *EO, unsigned char *smp, const float *cs,
                                           uint64_t *ybar, uint32_t yphase, int y0, int x0, float alpha,
                                           float beta, float *Xn,
@@ -309,6 +331,9 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
     const float eps2 = cs[C_EPS2], lambda = cs[C_LAMBDA];
     const unsigned fmag = __float_as_uint(cs[C_FMAG]);
     constexpr float DSCALE = L1 ? 1.f : 2.f;   // d/de of the data term's e^2 (L2) or psi_d(e) (L1)
+    // PH: the tap table t of the phase of HR coordinate c (negative c: phase 0, such outputs
+    // are outside the image and never used)
+    auto ph_taps = [&](int t, int c) { return cs + C_T0 + 64 * t + 8 * (c < 0 ? 0 : mod_f(c, f, fmag)); };
 
     constexpr int N_A = XH * XW / 4, N_B1 = XH * EW / 4, N_B2 = EH * EW / 4, N_C1 = EH * GW / 4;
     constexpr int N_C2 = GH * GW / 4, N_HP = CH * CW / 4, N_HR = CH * CW / 4, N_E = TH * TW / 4;
@@ -381,11 +406,12 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         for (int j = 0; j < 4; ++j) {
             float s = 0.f;
             const int lim = BORDER ? fwd_lim(x0 - 4 + e + j, f, fmag) : 2;
+            const float *tf = PH ? ph_taps(TPH_FX, x0 - 4 + e + j) : cs, *tp = PH ? tf + 64 * (TPH_PX - TPH_FX) : cs;
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 - b];
-                if (BORDER && b > lim) v = 0.f;
-                s = fmaf(cs[C_HX + b + 2], v, s);
+                if (!PH && BORDER && b > lim) v = 0.f;
+                s = fmaf(PH ? ph_fwd_w<BORDER>(tf, tp, b, lim) : cs[C_HX + b + 2], v, s);
             }
             out[j] = s;
         }
@@ -399,10 +425,11 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         const int gy = y0 - 4 + n;
         float2 z[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         const int lim = BORDER ? fwd_lim(gy, f, fmag) : 2;
+        const float *tf = PH ? ph_taps(TPH_FY, gy) : cs, *tp = PH ? tf + 64 * (TPH_PY - TPH_FY) : cs;
 #pragma unroll
         for (int a = -2; a <= 2; ++a) {
             const float4 v = ld4(HS + (n + 2 - a) * EW + e);
-            const float2 h = bc2((BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
+            const float2 h = bc2(PH ? ph_fwd_w<BORDER>(tf, tp, a, lim) : (BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
             z[0] = f2fma(h, make_float2(v.x, v.y), z[0]);
             z[1] = f2fma(h, make_float2(v.z, v.w), z[1]);
         }
@@ -448,11 +475,17 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float s = 0.f;
+            const int u = x0 - 2 + g + j;
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 + b];
-                if (BORDER && !adj_tap_ok(x0 - 2 + g + j, b, f, fmag)) v = 0.f;
-                s = fmaf(cs[C_HX + b + 2], v, s);
+                if (!PH && BORDER && !adj_tap_ok(u, b, f, fmag)) v = 0.f;
+                float wgt = cs[C_HX + b + 2];
+                if constexpr (PH) {   // the taps of the sample read, at column u + b
+                    const float *tf = ph_taps(TPH_FX, u + b);
+                    wgt = ph_adj_w<BORDER>(tf, tf + 64 * (TPH_PX - TPH_FX), b, u, u + b < 0 ? 0 : mod_f(u + b, f, fmag));
+                }
+                s = fmaf(wgt, v, s);
             }
             out[j] = s;
         }
@@ -471,11 +504,12 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         for (int j = 0; j < 4; ++j) {
             float sp = 0.f;
             const int lim = BORDER ? fwd_lim(x0 + o + j, f, fmag) : 2;
+            const float *tf = PH ? ph_taps(TPH_FX, x0 + o + j) : cs, *tp = PH ? tf + 64 * (TPH_PX - TPH_FX) : cs;
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float vp = inp[j + 2 - b];
-                if (BORDER && b > lim) vp = 0.f;
-                sp = fmaf(cs[C_HX + b + 2], vp, sp);
+                if (!PH && BORDER && b > lim) vp = 0.f;
+                sp = fmaf(PH ? ph_fwd_w<BORDER>(tf, tp, b, lim) : cs[C_HX + b + 2], vp, sp);
             }
             out[j] = sp;
         }
@@ -576,7 +610,14 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
 #pragma unroll
         for (int a = -2; a <= 2; ++a) {
             const float4 v = ld4(HS + (n + 2 + a) * GW + g);
-            const float2 h = bc2((BORDER && !adj_tap_ok(u, a, f, fmag)) ? 0.f : DSCALE * cs[C_HY + a + 2]);
+            float wgt;
+            if constexpr (PH) {   // the taps of the sample read, at row u + a
+                const float *tf = ph_taps(TPH_FY, u + a);
+                wgt = DSCALE * ph_adj_w<BORDER>(tf, tf + 64 * (TPH_PY - TPH_FY), a, u, u + a < 0 ? 0 : mod_f(u + a, f, fmag));
+            } else {
+                wgt = (BORDER && !adj_tap_ok(u, a, f, fmag)) ? 0.f : DSCALE * cs[C_HY + a + 2];
+            }
+            const float2 h = bc2(wgt);
             s2[0] = f2fma(h, make_float2(v.x, v.y), s2[0]);
             s2[1] = f2fma(h, make_float2(v.z, v.w), s2[1]);
         }
@@ -644,11 +685,12 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         for (int j = 0; j < 4; ++j) {
             float sr = 0.f;
             const int lim = BORDER ? fwd_lim(x0 + o + j, f, fmag) : 2;
+            const float *tf = PH ? ph_taps(TPH_FX, x0 + o + j) : cs, *tp = PH ? tf + 64 * (TPH_PX - TPH_FX) : cs;
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float vr = inr[j + 2 - b];
-                if (BORDER && b > lim) vr = 0.f;
-                sr = fmaf(cs[C_HX + b + 2], vr, sr);
+                if (!PH && BORDER && b > lim) vr = 0.f;
+                sr = fmaf(PH ? ph_fwd_w<BORDER>(tf, tp, b, lim) : cs[C_HX + b + 2], vr, sr);
             }
             out[j] = sr;
         }
@@ -665,11 +707,12 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
             float2 zr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             float2 zp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             const int lim = BORDER ? fwd_lim(gy, f, fmag) : 2;
+            const float *tf = PH ? ph_taps(TPH_FY, gy) : cs, *tp = PH ? tf + 64 * (TPH_PY - TPH_FY) : cs;
 #pragma unroll
             for (int a = -2; a <= 2; ++a) {
                 const float4 vr = ld4(HR + (n + 2 - a) * CW + o);
                 const float4 vp = ld4(HS + (n + 2 - a) * CW + o);
-                const float2 h = bc2((BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
+                const float2 h = bc2(PH ? ph_fwd_w<BORDER>(tf, tp, a, lim) : (BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
                 zr[0] = f2fma(h, make_float2(vr.x, vr.y), zr[0]);
                 zr[1] = f2fma(h, make_float2(vr.z, vr.w), zr[1]);
                 zp[0] = f2fma(h, make_float2(vp.x, vp.y), zp[0]);
@@ -1017,11 +1060,12 @@ __device__ __forceinline__ void load_tile(const TileInfo &ti, float *sm, uint64_
 
 // The fused SCG pass, persistent: one CTA per resident slot takes tiles (problem, tile) from
 // the launch's tile list until it runs out; the problems of one launch share the storage type
-// of r and p (RPB: bf16) and the data term (L1: smoothed L1).  The last thread schedules the
+// of r and p (RPB: bf16), the data term (L1: smoothed L1) and the tap layout (PH: per-phase
+// taps, non-integer shifts).  The last thread schedules the
 // tiles and issues their loads; warp 0 writes each tile's sums, which reduce_kernel combines
 // after the pass.  `work` (two counters, zero at launch) is the launch's tile counter; the last
 // CTA to finish zeroes it again.
-template <int TH, int TW, int NT, bool RPB, bool L1>
+template <int TH, int TW, int NT, bool RPB, bool L1, bool PH>
 __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProblem *__restrict__ probs,
                                                          const int2 *__restrict__ tiles, int n_tiles,
                                                          unsigned *work, int mode, double probe_alpha,
@@ -1035,7 +1079,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
     float *EO = L1 ? sm + Gm::FLOATS : nullptr;   // 16-byte aligned (FLOATS is a multiple of 4)
     unsigned char *smp = reinterpret_cast<unsigned char *>(sm + Gm::FLOATS + (L1 ? Gm::EO_FLOATS : 0));
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ float cs[C_N];
+    __shared__ __align__(16) float cs[PH ? C_NPH : C_N];
     __shared__ float red[NWARP][NPART];
     __shared__ float red_lo[NWARP];
     __shared__ TileInfo tinfo[2];
@@ -1081,6 +1125,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
                 cs[C_DEPS] = P.data_eps;
                 cs[C_DEPS2] = P.data_eps * P.data_eps;
             }
+            if constexpr (PH)
+                for (int t = tid; t < 4 * MAXF * 8; t += NT) cs[C_T0 + t] = (&P.tph[0][0][0])[t];
         }
         if (tid == SCHED_TID && sched.next < n_tiles) cp_async_8(&sched.wt_pre, tiles + sched.next);
         const uint32_t phase = n & 1;
@@ -1127,10 +1173,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
             const int y0 = ti.y0, x0 = ti.x0;
             const bool border = (y0 - 6 < 0) || (x0 - 8 < 0) || (y0 + TH + 6 > P.H) || (x0 + TW + 8 > P.W);
             if (border)
-                y_late = pass_tile<TH, TW, NT, true, RPB, L1>(P, sm, EO, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
+                y_late = pass_tile<TH, TW, NT, true, RPB, L1, PH>(P, sm, EO, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta, ti.Xn,
                                                      ti.Rn, ti.Pn, A, hook);
             else
-                y_late = pass_tile<TH, TW, NT, false, RPB, L1>(P, sm, EO, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
+                y_late = pass_tile<TH, TW, NT, false, RPB, L1, PH>(P, sm, EO, smp, cs, &bar[1], phase, y0, x0, ti.alpha, ti.beta,
                                                       ti.Xn, ti.Rn, ti.Pn, A, hook);
         }
 
@@ -1223,6 +1269,44 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
 }
 
 // ---------------------------------------------------------------------------------------
+// Frame value of LR sample li (u16 counts converted to line integrals).
+__device__ __forceinline__ float frame_value(const void *__restrict__ y_in, int in_dtype, float log_i0, size_t li) {
+    if (in_dtype == 1) {
+        const unsigned short c = ((const unsigned short *)y_in)[li];
+        return log_i0 - logf((float)(c < 1 ? 1 : c));
+    }
+    return ((const float *)y_in)[li];
+}
+
+// Multi-image interpolation at HR pixel (cy, cx) with non-integer shifts: sum_k M_k^T D^T y_k
+// over sum_k M_k^T D^T 1 (0 where no weight falls).  The sample at (sy, sx) (phase (ny, nx))
+// spreads over (sy + p, sx + q), p, q in {0, 1}, with weights (1 - a_y, a_y)[p] (1 - a_x,
+// a_x)[q], a_y of its row phase and a_x of its column phase; so (cy, cx) gathers from the
+// samples at (cy - p, cx - q).
+__device__ float shift_add_phased(const DevProblem &P, const void *__restrict__ y_in, int in_dtype, float log_i0,
+                                  int cy, int cx) {
+    const int f = P.f;
+    const size_t m = (size_t)P.h * P.w;
+    float num = 0.f, den = 0.f;
+    for (int p = 0; p < 2; ++p) {
+        const int sy = cy - p;
+        if (sy < 0) continue;
+        const int ny = sy % f;
+        const float wy = p ? P.ay[ny] : 1.f - P.ay[ny];
+        for (int q = 0; q < 2; ++q) {
+            const int sx = cx - q;
+            if (sx < 0) continue;
+            const int nx = sx % f, k = P.frame_of_phase[ny * f + nx];
+            const float wgt = wy * (q ? P.ax[nx] : 1.f - P.ax[nx]);
+            if (k < 0 || wgt == 0.f) continue;
+            num = fmaf(wgt, frame_value(y_in, in_dtype, log_i0, (size_t)k * m + (size_t)(sy / f) * P.w + sx / f), num);
+            den += wgt;
+        }
+    }
+    return den > 0.f ? num / den : 0.f;
+}
+
+// ---------------------------------------------------------------------------------------
 // prepare: interleave the K frames into Y on the HR grid (converting u16 counts to line
 // integrals), write the start point x_1 into X[0], zero r and p_0, and reset the state.
 // flags: 1 = write x0, 2 = zero R[0] and P[0], 4 = reset the SCG state.  x_given is dense
@@ -1256,7 +1340,7 @@ __global__ void prepare_kernel(const DevProblem *__restrict__ probs, int pidx, c
                     yv = ((const float *)y_in)[li];
                 }
             }
-            if (x0_mode == 1) x0 = (k >= 0) ? yv : 0.f;
+            if (x0_mode == 1) x0 = P.phased ? shift_add_phased(P, y_in, in_dtype, log_i0, cy, cx) : (k >= 0) ? yv : 0.f;
             else if (x0_mode == 2) x0 = x_given[(size_t)cy * W + cx];
         }
         P.Y[o] = yv;
@@ -1286,6 +1370,10 @@ __global__ void forward_kernel(const DevProblem *__restrict__ probs, int pidx, c
         const int i = (int)(li / w), j = (int)(li - (size_t)i * w);
         const int cy = f * i + P.ty[k], cx = f * j + P.tx[k];
         float acc = 0.f;
+        // per-phase taps (non-integer shifts): the frame's, and at the row / column of x it
+        // reads at its phase (B's input pixel 0) the bilinear's first part alone
+        const float *fy = P.tph[TPH_FY][P.ty[k]], *py = P.tph[TPH_PY][P.ty[k]];
+        const float *fx = P.tph[TPH_FX][P.tx[k]], *px = P.tph[TPH_PX][P.tx[k]];
         for (int a = -PSF_R; a <= PSF_R; ++a) {
             const int u = cy - a;
             if (u < P.ty[k] || u >= H) continue;   // B's zero padding in front of M_k / x outside
@@ -1293,9 +1381,11 @@ __global__ void forward_kernel(const DevProblem *__restrict__ probs, int pidx, c
             for (int b = -PSF_R; b <= PSF_R; ++b) {
                 const int v = cx - b;
                 if (v < P.tx[k] || v >= W) continue;
-                row = fmaf(P.hx[b + PSF_R], x[(size_t)u * W + v], row);
+                const float wx = !P.phased ? P.hx[b + PSF_R] : v == P.tx[k] ? px[b + PSF_R] : fx[b + PSF_R];
+                row = fmaf(wx, x[(size_t)u * W + v], row);
             }
-            acc = fmaf(P.hy[a + PSF_R], row, acc);
+            const float wy = !P.phased ? P.hy[a + PSF_R] : u == P.ty[k] ? py[a + PSF_R] : fy[a + PSF_R];
+            acc = fmaf(wy, row, acc);
         }
         y[t] = acc;
     }
@@ -1377,6 +1467,17 @@ __global__ void __launch_bounds__(256) interpolate_kernel(const DevProblem *__re
                         for (int px = 0; px < F; ++px) o[F * q + px] = v[q][px];
             }
         }
+    }
+}
+
+// Multi-image interpolation with non-integer shifts (shift_add_phased per pixel), out dense.
+__global__ void interpolate_phased_kernel(const DevProblem *__restrict__ probs, int pidx, const void *__restrict__ y_in,
+                                          int in_dtype, float log_i0, float *__restrict__ out) {
+    const DevProblem &P = probs[pidx];
+    const size_t n = (size_t)P.H * P.W;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int cy = (int)(o / P.W), cx = (int)(o - (size_t)cy * P.W);
+        out[o] = shift_add_phased(P, y_in, in_dtype, log_i0, cy, cx);
     }
 }
 

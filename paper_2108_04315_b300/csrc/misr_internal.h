@@ -47,8 +47,8 @@ misr_status check_desc(const misr_desc &d);
 // share a `work` must be stream-ordered.
 // Tiles per pass kernel instantiation: the tile list holds segment (shape 0, variant 0),
 // (shape 0, variant 1), ..., (shape 1, variant 0), ... in that order, n[shape][variant] tiles
-// each (variant: bit 0 bf16 r and p, bit 1 the L1 data term); one pass launch per non-empty
-// segment.
+// each (variant: bit 0 bf16 r and p, bit 1 the L1 data term, bit 2 per-phase taps, which only
+// the PHASED_SHAPE has); one pass launch per non-empty segment.
 struct PassSegs {
     int n[misr::N_SHAPES][misr::N_VARIANTS] = {};
     int total() const {
@@ -59,7 +59,7 @@ struct PassSegs {
     }
 };
 // the pass kernel variant of a problem
-inline int pass_variant(const misr::DevProblem &p) { return (p.rp_bf16 ? 1 : 0) | (p.l1 ? 2 : 0); }
+inline int pass_variant(const misr::DevProblem &p) { return (p.rp_bf16 ? 1 : 0) | (p.l1 ? 2 : 0) | (p.phased ? 4 : 0); }
 misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, const PassSegs &segs,
                             const int2 *groups, int n_groups, unsigned *work, int mode, double alpha, double beta,
                             cudaStream_t s);

@@ -41,8 +41,13 @@ constexpr int SHAPE_TH[N_SHAPES] = {32, 32, 16};
 constexpr int SHAPE_TW[N_SHAPES] = {64, 32, 64};
 constexpr int SHAPE_NT[N_SHAPES] = {512, 256, 256};
 // Compiled variants of the fused pass per shape: bit 0 r and p stored as bf16, bit 1 the
-// smoothed L1 data term.
-constexpr int N_VARIANTS = 4;
+// smoothed L1 data term, bit 2 per-phase blur taps (non-integer shifts; compiled for the
+// 32x32 shape only).
+constexpr int N_VARIANTS = 8;
+constexpr int PHASED_SHAPE = 1;
+// per-phase tap tables of DevProblem::tph: full y taps, y taps of the bilinear's first part
+// alone (the top border), full x taps, x taps of the first part alone (the left border)
+enum { TPH_FY = 0, TPH_PY = 1, TPH_FX = 2, TPH_PX = 3 };
 
 // partial sums of one pass (FP64)
 enum { P_JD = 0, P_DJD, P_JB, P_RR, P_RRX, P_PR, P_PP, P_A, P_B, P_C };
@@ -73,6 +78,7 @@ struct DevProblem {
     int tiles_x, tiles_y, n_tiles, iters;
     int rp_bf16;                                  // r and p stored as bf16 (x stays float)
     int l1;                                       // data term: 0 squared L2, 1 smoothed L1
+    int phased;                                   // non-integer shifts: blur taps per phase
     int shape, tile_h, tile_w;                    // tile shape (index into SHAPE_*) and its size
     int wait_tries;                               // polls before a tile load is reported late
     float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];  // separable PSF, h(a, b) = hy[a+R] hx[b+R]
@@ -93,6 +99,11 @@ struct DevProblem {
     double *trace;                                // [iters][TRACE_COLS]
     int ty[MAXK], tx[MAXK];
     int frame_of_phase[MAXF * MAXF];              // -1: no frame samples that phase
+    // non-integer shifts: fractional HR shift per row phase (ay) and column phase (ax), and
+    // the blur taps per phase, tph[table][phase][c + PSF_R] for tap c in [-PSF_R, PSF_R]
+    // (8 floats per phase so that a phase's taps start on a 16-byte boundary)
+    float ay[MAXF], ax[MAXF];
+    float tph[4][MAXF][8];
 };
 
 }  // namespace misr

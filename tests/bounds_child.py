@@ -52,6 +52,17 @@ def run(lib_path):
                     J, g = plan.gradient(y, x)
                     out[f"{name}_grad"] = g.cpu().numpy()
                     plans.append((plan, y))
+    # non-integer shifts (per-phase taps), float and bf16 directions, L2 and L1
+    fr_shifts = [(dx, dy) for dy in (0.05, 0.6) for dx in (0.0, 0.55)]
+    for name, (h, w) in (("frac_ragged", (37, 45)), ("frac_strip", (1, 61)), ("frac_pixel", (1, 1))):
+        y = torch.from_numpy(frames(h, w, fr_shifts, 700 + h)).cuda()
+        for dt in (B.MISR_F32, B.MISR_BF16):
+            for norm in (B.MISR_NORM_L2, B.MISR_NORM_L1):
+                p = B.Plan(h, w, 2, fr_shifts, gen.gaussian_psf(3, 0.6), iters=4, iterate_dtype=dt, data_norm=norm,
+                           data_eps=0.05)
+                x, _ = p.solve(y)
+                out[f"{name}_d{dt}_n{norm}"] = x.cpu().numpy()
+                p.close()
     # a batch over mixed geometries, tile shapes and storage types
     sel = plans[:4]
     batch = B.Batch([p for p, _ in sel])

@@ -59,7 +59,10 @@ def _desc(**kw):
     (dict(lr_h=0), "EINVAL"),
     (dict(shifts=[(0.0, 0.0)] * 5), "EINVAL"),                    # K > f^2
     (dict(shifts=[(0.0, 0.0), (0.0, 0.0)]), "EINVAL"),            # same phase twice
-    (dict(shifts=[(0.25, 0.0)]), "ENOTIMPL"),                     # f*s not an integer
+    (dict(shifts=[(0.25, 0.0)]), "ENOTIMPL"),                     # f*s not an integer, 5x5 PSF: 6 taps
+    (dict(shifts=[(0.0, 0.0), (0.6, 0.0), (0.0, 0.5), (0.55, 0.5)], psf=np.ones((3, 3))), "ENOTIMPL"),  # no lattice
+    (dict(shifts=[(0.25, 0.0)], psf=np.ones((3, 3)), tile_shape=1), "ENOTIMPL"),   # per-phase taps: 32x32 only
+    (dict(shifts=[(0.0, float("nan"))]), "EINVAL"),
     (dict(shifts=[(1.0, 0.0)]), "EINVAL"),                        # shift beyond [0, 1-1/f]
     (dict(psf=np.ones((4, 4))), "EINVAL"),                        # even PSF
     (dict(psf=np.ones((7, 7))), "EINVAL"),                        # PSF larger than 5x5
