@@ -226,6 +226,12 @@ static misr_status setup_geometry(const misr_desc &d, DevProblem &hp) {
             hp.tph[TPH_PX][p][c + PSF_R] = (float)((1.0 - ax[p]) * hx[c + PSF_R]);
         }
     }
+    for (int p = 0; p < f; ++p)
+        for (int c = -PSF_R; c <= PSF_R; ++c) {
+            const int q = ((p + c) % f + f) % f;
+            hp.tph[TPH_AFY][p][c + PSF_R] = hp.tph[TPH_FY][q][c + PSF_R];
+            hp.tph[TPH_AFX][p][c + PSF_R] = hp.tph[TPH_FX][q][c + PSF_R];
+        }
     return MISR_OK;
 }
 

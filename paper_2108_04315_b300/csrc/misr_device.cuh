@@ -268,19 +268,31 @@ enum {
     C_DEPS = 32, C_DEPS2 = 33, C_N = 34,  // C_DEPS*: the L1 data term's smoothing and its square
     // per-phase taps (non-integer shifts): DevProblem::tph copied to C_T0 (16-byte aligned),
     // table t, phase p at C_T0 + 64 t + 8 p
-    C_T0 = 36, C_NPH = C_T0 + 4 * MAXF * 8
+    C_T0 = 36, C_NPH = C_T0 + N_TPH * MAXF * 8
 };
+
+// the 5 taps of a per-phase table row (16-byte aligned)
+__device__ __forceinline__ void taps5(const float *t, float *w) {
+    const float4 a = *reinterpret_cast<const float4 *>(t);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = t[4];
+}
+// forward taps of an output with per-phase tables: the full row, and at the border 0 past lim
+// and the first part alone at lim
+template <bool BORDER>
+__device__ __forceinline__ void ph_fwd_taps(const float *full, const float *part, int lim, float *w) {
+    taps5(full, w);
+    if (BORDER) {
+        float q[5];
+        taps5(part, q);
+#pragma unroll
+        for (int t = -2; t <= 2; ++t) w[t + 2] = t > lim ? 0.f : t == lim ? q[t + 2] : w[t + 2];
+    }
+}
 
 // Per-phase tap weights (non-integer shifts).  Forward tap t of an output whose fwd_lim is lim
 // (BORDER): 0 past lim, the bilinear's first part alone at lim (its second part reads B's input
-// pixel -1), the full tap before.  Adjoint tap t of an output at x coordinate u reading the
-// sample of phase ns: 0 when u < ns, the first part alone when u == ns.
-template <bool BORDER>
-__device__ __forceinline__ float ph_fwd_w(const float *full, const float *part, int t, int lim) {
-    if (BORDER && t > lim) return 0.f;
-    if (BORDER && t == lim) return part[t + 2];
-    return full[t + 2];
-}
+// pixel -1), the full tap before (ph_fwd_taps below).  Adjoint tap t of an output at x
+// coordinate u reading the sample of phase ns: 0 when u < ns, the first part alone when u == ns.
 template <bool BORDER>
 __device__ __forceinline__ float ph_adj_w(const float *full, const float *part, int t, int u, int ns) {
     if (BORDER && u < ns) return 0.f;
@@ -406,12 +418,16 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         for (int j = 0; j < 4; ++j) {
             float s = 0.f;
             const int lim = BORDER ? fwd_lim(x0 - 4 + e + j, f, fmag) : 2;
-            const float *tf = PH ? ph_taps(TPH_FX, x0 - 4 + e + j) : cs, *tp = PH ? tf + 64 * (TPH_PX - TPH_FX) : cs;
+            float w5[5];
+            if constexpr (PH) {
+                const float *tf = ph_taps(TPH_FX, x0 - 4 + e + j);
+                ph_fwd_taps<BORDER>(tf, tf + 64 * (TPH_PX - TPH_FX), lim, w5);
+            }
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 - b];
                 if (!PH && BORDER && b > lim) v = 0.f;
-                s = fmaf(PH ? ph_fwd_w<BORDER>(tf, tp, b, lim) : cs[C_HX + b + 2], v, s);
+                s = fmaf(PH ? w5[b + 2] : cs[C_HX + b + 2], v, s);
             }
             out[j] = s;
         }
@@ -425,11 +441,15 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         const int gy = y0 - 4 + n;
         float2 z[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         const int lim = BORDER ? fwd_lim(gy, f, fmag) : 2;
-        const float *tf = PH ? ph_taps(TPH_FY, gy) : cs, *tp = PH ? tf + 64 * (TPH_PY - TPH_FY) : cs;
+        float w5[5];
+        if constexpr (PH) {
+            const float *tf = ph_taps(TPH_FY, gy);
+            ph_fwd_taps<BORDER>(tf, tf + 64 * (TPH_PY - TPH_FY), lim, w5);
+        }
 #pragma unroll
         for (int a = -2; a <= 2; ++a) {
             const float4 v = ld4(HS + (n + 2 - a) * EW + e);
-            const float2 h = bc2(PH ? ph_fwd_w<BORDER>(tf, tp, a, lim) : (BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
+            const float2 h = bc2(PH ? w5[a + 2] : (BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
             z[0] = f2fma(h, make_float2(v.x, v.y), z[0]);
             z[1] = f2fma(h, make_float2(v.z, v.w), z[1]);
         }
@@ -476,12 +496,15 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         for (int j = 0; j < 4; ++j) {
             float s = 0.f;
             const int u = x0 - 2 + g + j;
+            float w5[5];
+            if constexpr (PH && !BORDER) taps5(ph_taps(TPH_AFX, u), w5);   // by the output's phase
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float v = in[j + 2 + b];
                 if (!PH && BORDER && !adj_tap_ok(u, b, f, fmag)) v = 0.f;
                 float wgt = cs[C_HX + b + 2];
-                if constexpr (PH) {   // the taps of the sample read, at column u + b
+                if constexpr (PH && !BORDER) wgt = w5[b + 2];
+                if constexpr (PH && BORDER) {   // the taps of the sample read, at column u + b
                     const float *tf = ph_taps(TPH_FX, u + b);
                     wgt = ph_adj_w<BORDER>(tf, tf + 64 * (TPH_PX - TPH_FX), b, u, u + b < 0 ? 0 : mod_f(u + b, f, fmag));
                 }
@@ -504,12 +527,16 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         for (int j = 0; j < 4; ++j) {
             float sp = 0.f;
             const int lim = BORDER ? fwd_lim(x0 + o + j, f, fmag) : 2;
-            const float *tf = PH ? ph_taps(TPH_FX, x0 + o + j) : cs, *tp = PH ? tf + 64 * (TPH_PX - TPH_FX) : cs;
+            float w5[5];
+            if constexpr (PH) {
+                const float *tf = ph_taps(TPH_FX, x0 + o + j);
+                ph_fwd_taps<BORDER>(tf, tf + 64 * (TPH_PX - TPH_FX), lim, w5);
+            }
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float vp = inp[j + 2 - b];
                 if (!PH && BORDER && b > lim) vp = 0.f;
-                sp = fmaf(PH ? ph_fwd_w<BORDER>(tf, tp, b, lim) : cs[C_HX + b + 2], vp, sp);
+                sp = fmaf(PH ? w5[b + 2] : cs[C_HX + b + 2], vp, sp);
             }
             out[j] = sp;
         }
@@ -607,11 +634,15 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         if (!MISR_IN_BOUNDS(n >= 0 && n < GH && g >= 0 && g + 3 < GW && n + 4 < EH, BC_C2, n, g)) return;
         const int u = y0 - 2 + n;
         float2 s2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        float w5[5];
+        if constexpr (PH && !BORDER) taps5(ph_taps(TPH_AFY, u), w5);   // by the output's phase
 #pragma unroll
         for (int a = -2; a <= 2; ++a) {
             const float4 v = ld4(HS + (n + 2 + a) * GW + g);
             float wgt;
-            if constexpr (PH) {   // the taps of the sample read, at row u + a
+            if constexpr (PH && !BORDER) {
+                wgt = DSCALE * w5[a + 2];
+            } else if constexpr (PH) {   // the taps of the sample read, at row u + a
                 const float *tf = ph_taps(TPH_FY, u + a);
                 wgt = DSCALE * ph_adj_w<BORDER>(tf, tf + 64 * (TPH_PY - TPH_FY), a, u, u + a < 0 ? 0 : mod_f(u + a, f, fmag));
             } else {
@@ -685,12 +716,16 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         for (int j = 0; j < 4; ++j) {
             float sr = 0.f;
             const int lim = BORDER ? fwd_lim(x0 + o + j, f, fmag) : 2;
-            const float *tf = PH ? ph_taps(TPH_FX, x0 + o + j) : cs, *tp = PH ? tf + 64 * (TPH_PX - TPH_FX) : cs;
+            float w5[5];
+            if constexpr (PH) {
+                const float *tf = ph_taps(TPH_FX, x0 + o + j);
+                ph_fwd_taps<BORDER>(tf, tf + 64 * (TPH_PX - TPH_FX), lim, w5);
+            }
 #pragma unroll
             for (int b = -2; b <= 2; ++b) {
                 float vr = inr[j + 2 - b];
                 if (!PH && BORDER && b > lim) vr = 0.f;
-                sr = fmaf(PH ? ph_fwd_w<BORDER>(tf, tp, b, lim) : cs[C_HX + b + 2], vr, sr);
+                sr = fmaf(PH ? w5[b + 2] : cs[C_HX + b + 2], vr, sr);
             }
             out[j] = sr;
         }
@@ -707,12 +742,16 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
             float2 zr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             float2 zp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             const int lim = BORDER ? fwd_lim(gy, f, fmag) : 2;
-            const float *tf = PH ? ph_taps(TPH_FY, gy) : cs, *tp = PH ? tf + 64 * (TPH_PY - TPH_FY) : cs;
+            float w5[5];
+            if constexpr (PH) {
+                const float *tf = ph_taps(TPH_FY, gy);
+                ph_fwd_taps<BORDER>(tf, tf + 64 * (TPH_PY - TPH_FY), lim, w5);
+            }
 #pragma unroll
             for (int a = -2; a <= 2; ++a) {
                 const float4 vr = ld4(HR + (n + 2 - a) * CW + o);
                 const float4 vp = ld4(HS + (n + 2 - a) * CW + o);
-                const float2 h = bc2(PH ? ph_fwd_w<BORDER>(tf, tp, a, lim) : (BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
+                const float2 h = bc2(PH ? w5[a + 2] : (BORDER && a > lim) ? 0.f : cs[C_HY + a + 2]);
                 zr[0] = f2fma(h, make_float2(vr.x, vr.y), zr[0]);
                 zr[1] = f2fma(h, make_float2(vr.z, vr.w), zr[1]);
                 zp[0] = f2fma(h, make_float2(vp.x, vp.y), zp[0]);
@@ -1126,7 +1165,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) scg_pass_kernel(const DevProble
                 cs[C_DEPS2] = P.data_eps * P.data_eps;
             }
             if constexpr (PH)
-                for (int t = tid; t < 4 * MAXF * 8; t += NT) cs[C_T0 + t] = (&P.tph[0][0][0])[t];
+                for (int t = tid; t < N_TPH * MAXF * 8; t += NT) cs[C_T0 + t] = (&P.tph[0][0][0])[t];
         }
         if (tid == SCHED_TID && sched.next < n_tiles) cp_async_8(&sched.wt_pre, tiles + sched.next);
         const uint32_t phase = n & 1;

@@ -46,8 +46,10 @@ constexpr int SHAPE_NT[N_SHAPES] = {512, 256, 256};
 constexpr int N_VARIANTS = 8;
 constexpr int PHASED_SHAPE = 1;
 // per-phase tap tables of DevProblem::tph: full y taps, y taps of the bilinear's first part
-// alone (the top border), full x taps, x taps of the first part alone (the left border)
-enum { TPH_FY = 0, TPH_PY = 1, TPH_FX = 2, TPH_PX = 3 };
+// alone (the top border), full x taps, x taps of the first part alone (the left border), and
+// the adjoint's full taps by output phase: AF[p][c + R] = F[(p + c) mod f][c + R] (the taps
+// of the sample an adjoint tap c reads, from an output of phase p)
+enum { TPH_FY = 0, TPH_PY = 1, TPH_FX = 2, TPH_PX = 3, TPH_AFY = 4, TPH_AFX = 5, N_TPH = 6 };
 
 // partial sums of one pass (FP64)
 enum { P_JD = 0, P_DJD, P_JB, P_RR, P_RRX, P_PR, P_PP, P_A, P_B, P_C };
@@ -103,7 +105,7 @@ struct DevProblem {
     // the blur taps per phase, tph[table][phase][c + PSF_R] for tap c in [-PSF_R, PSF_R]
     // (8 floats per phase so that a phase's taps start on a 16-byte boundary)
     float ay[MAXF], ax[MAXF];
-    float tph[4][MAXF][8];
+    float tph[N_TPH][MAXF][8];
 };
 
 }  // namespace misr
