@@ -127,7 +127,8 @@ static misr_status validate(const misr_desc *d) {
 // With binning, D B is one blur: per axis, (D_bin B z)(i) = (1/f) sum_{a'<f} (B z)(f i + a') =
 // sum_c h'(c) z(f i - c) with h'(c) = (1/f) sum_{a'=0}^{f-1} h(c + a'), c in [-R-f+1, R]; the
 // tap masks of the frames (B's zero padding in front of M_k: the input pixel f i - c >= 0) are
-// those of the point-sampled blur with h' in place of h.
+// those of the point-sampled blur with h' in place of h.  hy, hx receive the taps at [c + R]
+// (c in [-PSF_R, PSF_R], 0 outside the blur); *lowest the lowest tap c with a weight.
 static misr_status psf_taps(const misr_desc *d, double *hy, double *hx, int *lowest) {
     const int S = d->psf_size, R = S / 2;
     double sum = 0;
