@@ -162,23 +162,26 @@ misr_status misr_plan_workspace_bytes(misr_plan_t plan, size_t *bytes);
  * projection.  Synchronises the device.  Errors: MISR_EINVAL (NULL plan), MISR_ECUDA. */
 misr_status misr_plan_set_wait_limit(misr_plan_t plan, uint32_t tries);
 
-/* y_k = D B M_k x for every frame (Eq. 1 without noise): x_dev is the HR float32 image,
- * y_dev receives K float32 frames.  Asynchronous on stream.  Used to synthesise
- * acquisitions. */
+/* y_k = D B M_k x for every frame (Eq. 1 without noise, with the plan's decimation and
+ * shifts): x_dev is the HR float32 image, y_dev receives K float32 frames.  Asynchronous on
+ * stream.  Used to synthesise acquisitions. */
 misr_status misr_forward(misr_plan_t plan, const float *x_dev, float *y_dev, misr_stream_t stream);
 
 /* Multi-image interpolation (Sec. 4.1.1), the paper's non-iterative comparator: every LR
  * sample of y_dev (K frames, the plan's in_dtype; u16 counts are log-converted as for a solve)
  * is inserted at the HR pixel it was taken at, f*(i, j) + the frame's HR shift, and x_dev (HR
- * float32, dense) is 0 where no frame samples.  It is also the start point of a
+ * float32, dense) is 0 where no frame samples.  With non-integer shifts each sample is spread
+ * over the 2 x 2 HR pixels around its position with the bilinear weights of M_k, and x is the
+ * weighted mean there (sum_k M_k^T D^T y_k over sum_k M_k^T D^T 1).  It is also the start point of a
  * MISR_X0_SHIFT_ADD solve.  Reads only the plan's geometry: the plan's workspace and solve
  * state are not touched.  Asynchronous on stream.  Errors: MISR_EINVAL (NULL arguments),
  * MISR_ECUDA. */
 misr_status misr_interpolate(misr_plan_t plan, const void *y_dev, float *x_dev, misr_stream_t stream);
 
 /* Objective and gradient at x (Eq. 9 and its gradient 2 sum_k A_k^T (A_k x - y_k) +
- * lambda grad R): y_dev holds the K frames (in_dtype), x_dev the HR image, g_dev receives
- * grad J(x) (HR float32).  Blocking: *J_out (may be NULL) is valid on return. */
+ * lambda grad R; sum_k A_k^T psi_d'(A_k x - y_k) + lambda grad R with the L1 data term):
+ * y_dev holds the K frames (in_dtype), x_dev the HR image, g_dev receives grad J(x) (HR
+ * float32).  Blocking: *J_out (may be NULL) is valid on return. */
 misr_status misr_gradient(misr_plan_t plan, const void *y_dev, const float *x_dev, float *g_dev,
                           double *J_out, misr_stream_t stream);
 
