@@ -75,7 +75,7 @@ typedef struct misr_desc {
     double lambda;           /* regulariser weight lambda of Eq. 9 (>= 0) */
     double btv_alpha;        /* decay alpha of gamma(d) = alpha^(dx+dy), Eq. 8 */
     int32_t btv_w;           /* BTV window w of Eq. 8, 1..3 */
-    double eps;              /* > 0: |t| of Eq. 8 is smoothed as sqrt(t^2+eps^2) - eps */
+    double eps;              /* in [1e-15, 1e15]: |t| of Eq. 8 is smoothed as sqrt(t^2+eps^2) - eps */
     int32_t iters;           /* SCG iterations, rejected ones included (Algorithm 1), 0..1e6 */
     int32_t x0_mode;         /* MISR_X0_* */
     int32_t in_dtype;        /* MISR_F32 frames, or MISR_U16 detector counts c converted on the

@@ -102,7 +102,7 @@ static misr_status validate(const misr_desc *d) {
     if (d->psf_size < 1 || d->psf_size > 2 * PSF_R + 1 || d->psf_size % 2 == 0)
         return fail(MISR_EINVAL, "psf_size must be odd and <= %d", 2 * PSF_R + 1);
     if (!(d->lambda >= 0)) return fail(MISR_EINVAL, "lambda must be >= 0");
-    if (!(d->eps > 0)) return fail(MISR_EINVAL, "eps must be > 0");
+    if (!(d->eps >= 1e-15 && d->eps <= 1e15)) return fail(MISR_EINVAL, "eps must be in [1e-15, 1e15]");
     if (d->btv_w < 1 || d->btv_w > BTV_W) return fail(MISR_EINVAL, "btv_w must be in [1, %d]", BTV_W);
     if (!(d->btv_alpha >= 0)) return fail(MISR_EINVAL, "btv_alpha must be >= 0");
     if (d->iters < 0 || d->iters > 1000000) return fail(MISR_EINVAL, "iters must be in [0, 1e6]");

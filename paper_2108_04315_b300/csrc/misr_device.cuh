@@ -769,11 +769,13 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
                 const float2 azp = f2mul(bc2(alpha), zpm);
                 // e'^2 - e^2 = alpha (B p) (2 e' - alpha (B p)), e the residual at x = x' - alpha p
                 if constexpr (L1) {
-                    // psi_d''(e') = eps_d^2 / S(e')^3, S(t) = sqrt(t^2 + eps_d^2); and
-                    // psi_d(e') - psi_d(e) = (e'^2 - e^2) / (S(e') + S(e))
+                    // psi_d''(e') = eps_d^2 / S(e')^3, S(t) = sqrt(t^2 + eps_d^2), formed as
+                    // (1/S) (eps_d/S)^2 (eps_d/S <= 1, so no intermediate overflows even at
+                    // the smallest eps_d); and psi_d(e') - psi_d(e) = (e'^2 - e^2) / (S(e') + S(e))
                     const float2 dd2 = bc2(cs[C_DEPS2]);
                     const float2 q1 = f2fma(e2[h], e2[h], dd2), r1 = f2rsqrt(q1);
-                    const float2 w = f2mul(dd2, f2mul(r1, f2mul(r1, r1)));
+                    const float2 er = f2mul(bc2(cs[C_DEPS]), r1);
+                    const float2 w = f2mul(r1, f2mul(er, er));
                     const float2 eb = f2sub(e2[h], azp);
                     const float2 q0 = f2fma(eb, eb, dd2), r0 = f2rsqrt(q0);
                     const float2 ss = f2fma(q1, r1, f2mul(q0, r0));

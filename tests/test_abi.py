@@ -68,6 +68,7 @@ def _desc(**kw):
     (dict(psf=np.ones((7, 7))), "EINVAL"),                        # PSF larger than 5x5
     (dict(psf=np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1.0]])), "EINVAL"),   # not separable
     (dict(eps=0.0), "EINVAL"),
+    (dict(eps=1e-20), "EINVAL"),                                  # eps^2 below the FP32 normals
     (dict(btv_w=4), "EINVAL"),
     (dict(lam=-1.0), "EINVAL"),
     (dict(iters=-1), "EINVAL"),

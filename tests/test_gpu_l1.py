@@ -253,3 +253,22 @@ def test_l1_gradient_noalloc_equals_plan_gradient(orc):
     assert rc == B.MISR_OK, B.misr_last_error()
     assert rel_l2(g.cpu().numpy(), g_ref.cpu().numpy()) <= RTOL_OP
     assert J.value == pytest.approx(J_ref, rel=RTOL_OP)
+
+
+@pytest.mark.parametrize("eps_d", [1e-15, 1e15])
+def test_l1_extreme_smoothing_stays_finite(orc, eps_d):
+    """At the ends of the accepted range of eps_d (the L1 term's psi_d'' reaches 1/eps_d at a
+    zero residual) the solve stays finite and never raises the objective beyond the FP32 noise
+    of its direct sums (1e-6 of J; the accept test itself uses the per-pixel difference)."""
+    P, plan, xt, y = l1_case(orc, "ragged_f2_asym", 1210, eps_d, iters=15)
+    x, st = plan.solve(to_dev(y))
+    tr = plan.trace()
+    assert torch.isfinite(x).all() and np.isfinite(st["J_final"])
+    E_next = np.where(tr["accept"] == 1, tr["J_trial"], tr["E"])
+    E_all = np.concatenate([tr["E"][:1], E_next])
+    assert np.all(np.isfinite(E_next)) and np.all(np.diff(E_all) <= 1e-6 * np.abs(E_all[:-1]))
+    # at eps_d = 1e15 the L1 term is the L2 term over 2 eps_d: the objective at the device's
+    # image is the oracle's
+    if eps_d > 1:
+        assert st["J_final"] == pytest.approx(P.objective(x.cpu().numpy().astype(np.float64), y.astype(np.float64)),
+                                              rel=1e-5)
