@@ -311,14 +311,10 @@ static misr_status set_pass_attrs() {
 // CTAs of the fused pass resident on the whole GPU, per shape and variant (the L1 and
 // per-phase variants take more shared memory)
 static int resident_ctas(int shape, int variant) {
-    static int cached[N_SHAPES][N_VARIANTS];
-    static bool init = false;
-    if (!init) {
-        for (auto &a : cached)
-            for (int &c : a) c = -1;
-        init = true;
-    }
-    if (cached[shape][variant] >= 0) return cached[shape][variant];
+    // 0: not measured yet (a measured count is at least the SM count); concurrent callers may
+    // both measure and store the same value
+    static int cached[N_SHAPES][N_VARIANTS] = {};
+    if (cached[shape][variant] > 0) return cached[shape][variant];
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -331,8 +327,9 @@ static int resident_ctas(int shape, int variant) {
         });
     });
     cudaGetLastError();
-    cached[shape][variant] = sms * std::max(per_sm, 1);
-    return cached[shape][variant];
+    const int n = std::max(sms, 1) * std::max(per_sm, 1);
+    cached[shape][variant] = n;
+    return n;
 }
 
 // persistent grid: one CTA per resident slot, at most one per tile
