@@ -168,3 +168,29 @@ def test_serving_cancel_queued_and_running(orc):
     c = srv.counters()
     assert c["queued"] == 0 and c["running"] == 0
     srv.close()
+
+
+def test_serving_mixes_model_options(orc):
+    """Requests with the L1 term, binning D and non-integer shifts served beside a plain one
+    (different kernel variants in one tick): each equals its own misr_solve bit for bit."""
+    from paper_2108_04315_b300 import binding as B
+    h, w, f = 37, 53, 2
+    psf3 = gen.gaussian_psf(3, 0.6)
+    frac = [(dx, dy) for dy in (0.05, 0.6) for dx in (0.0, 0.55)]
+    kinds = [
+        (gen.half_pixel_shifts(), PSF, dict()),
+        (gen.half_pixel_shifts(), psf3, dict(data_norm=B.MISR_NORM_L1, data_eps=0.02, decimation=B.MISR_DECIM_BIN)),
+        (frac, psf3, dict()),
+        (frac, psf3, dict(data_norm=B.MISR_NORM_L1, data_eps=0.05, iterate_dtype=B.MISR_BF16)),
+    ]
+    y = to_dev(gen.random_field((4, h, w), 2100, 0.0, 2.0).astype(np.float32))
+    alone = []
+    for sh, psf, kw in kinds:
+        x, st = B.Plan(h, w, f, sh, psf, lam=0.01, iters=9, **kw).solve(y)
+        alone.append((x.clone(), st))
+    srv = B.Server(max_slots=8, passes_per_tick=2)
+    tickets = [srv.submit(y, h, w, f, sh, psf, lam=0.01, iters=9, **kw) for sh, psf, kw in kinds]
+    for t, (xa, sa) in zip(tickets, alone):
+        x, st, _ = srv.wait(t, timeout_s=60.0)
+        assert torch.equal(x, xa) and st == sa
+    srv.close()
