@@ -1154,7 +1154,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
             if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
         }
     hp.eps_pairs = d.eps * eps_pairs;
-    set_shape(hp, DEFAULT_SHAPE);
+    set_shape(hp, hp.phased ? PHASED_SHAPE : DEFAULT_SHAPE);
     set_groups(hp);
     for (int i = 0; i < 2; ++i) {
         hp.X[i] = reinterpret_cast<float *>(base + NA_O_IMG + (0 + i) * NOALLOC_IMG);
