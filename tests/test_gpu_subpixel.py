@@ -158,3 +158,23 @@ def test_subpixel_and_integer_in_one_batch_equal_each_alone(orc):
     for (xa, sa), xb, sb in zip(alone, xs, stats):
         assert torch.equal(xa, xb) and sa == sb
     batch.close()
+
+
+def test_subpixel_gradient_noalloc_equals_plan_gradient(orc):
+    import ctypes as C
+    from paper_2108_04315_b300 import binding as B
+    h, w, f, shifts, psf, binned = CASES["f3_frac_k9"]
+    P, plan, xt, y = frac_case(orc, "f3_frac_k9", 1110)
+    yd, xd = to_dev(y), to_dev(xt.astype(np.float32))
+    J_ref, g_ref = plan.gradient(yd, xd)
+    fn = B.lib().misr_gradient_noalloc
+    fn.argtypes = [C.POINTER(B.misr_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]
+    fn.restype = C.c_int
+    desc = B.make_desc(h, w, f, shifts, psf, lam=0.01, iters=1)
+    g = torch.full_like(xd, float("nan"))
+    J = C.c_double()
+    rc = fn(C.byref(desc), yd.data_ptr(), xd.data_ptr(), g.data_ptr(), C.byref(J),
+            torch.cuda.current_stream().cuda_stream)
+    assert rc == B.MISR_OK, B.misr_last_error()
+    assert rel_l2(g.cpu().numpy(), g_ref.cpu().numpy()) <= RTOL_OP
+    assert J.value == pytest.approx(J_ref, rel=RTOL_OP)
