@@ -28,6 +28,9 @@
  * check that does not call the oracle twice: a dense D*B*M product built from the textbook
  * matrices, closed-form BTV values, central finite differences, exact recovery, a dense
  * normal-equation solve and conjugate-gradient identities.
+ * Parity unpinned: two branches of orc_scg, the scale increase after a poor step (Delta < 0.25)
+ * and the negative-curvature correction (delta <= 0), follow Moller's algorithm as restated
+ * there; neither occurs on the quadratic pins, and no closed form covers them on the BTV problem.
  */
 #ifndef MISR_ORACLE_H
 #define MISR_ORACLE_H
