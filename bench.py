@@ -254,16 +254,21 @@ def measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak):
         dist.barrier()
     torch.cuda.synchronize()
     reps = 20 * args.steps
-    flush = torch.empty(64 * 2**20, dtype=torch.float32, device=device)   # 256 MB > L2
+    # L2 flush before each call: a 256 MB write evicts the call's data, and a 256 MB read of
+    # another buffer then evicts the written (dirty) lines, so that their write-back happens
+    # here and not inside the timed call
+    flush = torch.empty(64 * 2**20, dtype=torch.float32, device=device)
+    flush_r = torch.zeros(64 * 2**20, dtype=torch.float32, device=device)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     for e0, e1 in evs:
         flush.zero_()
+        flush_r.sum()
         e0.record(stream)
         plan.interpolate(y, xi)
         e1.record(stream)
     torch.cuda.synchronize()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / reps
-    del flush
+    del flush, flush_r
     rate, _ = job_rate(reps, ms * reps / 1e3, dist, device)
     nbytes = y.numel() * 4 + H * W * 4
     xs = plan.solve(y)[0]
@@ -272,7 +277,8 @@ def measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak):
             "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "bytes_per_call": nbytes,
             "image_rel_error_vs_phantom": {"interpolation": err(xi), "scg_%d_it" % wl["iters"]: err(xs)},
             "timed_as": "%d calls of misr_interpolate, each timed alone with CUDA events on the stream "
-                        "after a 256 MB write that flushes L2" % reps}
+                        "after a 256 MB write and a 256 MB read of another buffer that flush L2 "
+                        "(the written lines are evicted, and written back, before the call)" % reps}
 
 
 def cpu_baseline(wl):
