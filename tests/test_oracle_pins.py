@@ -598,3 +598,32 @@ def test_bilinear_gradient_central_differences(orc, norm):
             xm = x.copy(); xm[i, j] -= hstep
             fd[i, j] = (P.objective(xp, y) - P.objective(xm, y)) / (2 * hstep)
     assert np.linalg.norm(fd - g) <= 1e-7 * np.linalg.norm(g)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_options_forward_equals_dense(orc, seed):
+    """Seeded random models (factor 1-3, 1-5 frames with integer or non-integer shifts of
+    either sign, PSF 1/3/5 with random asymmetric taps, point or binning D): the oracle's A_k
+    and A_k^T equal the dense textbook product and its transpose."""
+    rng = np.random.default_rng(5000 + seed)
+    f = int(rng.integers(1, 4))
+    h, w = (int(v) for v in rng.integers(1, 5, size=2))
+    K = int(rng.integers(1, 6))
+    frac = bool(rng.integers(0, 2))
+    shifts = []
+    for _ in range(K):
+        t = rng.integers(-f, 2 * f, size=2).astype(np.float64)
+        if frac:
+            t = t + rng.uniform(0, 1, size=2)
+        shifts.append((t[0] / f, t[1] / f))
+    size = int(rng.choice([1, 3, 5]))
+    psf = rng.uniform(0.1, 1.0, size=(size, size))
+    binned = bool(rng.integers(0, 2))
+    P = orc.Problem(h, w, f, shifts, psf, **(dict(decimation=orc.DECIM_BIN) if binned else {}))
+    A = dm.system_matrices(h, w, f, shifts, psf, binned=binned)
+    n, m = P.H * P.W, h * w
+    for k in range(P.K):
+        cols = np.stack([P.forward(k, np.eye(n)[c].reshape(P.H, P.W)).ravel() for c in range(n)], axis=1)
+        np.testing.assert_allclose(cols, A[k], rtol=0, atol=1e-14)
+        cols = np.stack([P.adjoint(k, np.eye(m)[c].reshape(h, w)).ravel() for c in range(m)], axis=1)
+        np.testing.assert_allclose(cols, A[k].T, rtol=0, atol=1e-14)
