@@ -268,10 +268,10 @@ misr_status misr_resume(misr_plan_t plan, const void *y_dev, float *x_dev, misr_
 misr_status misr_get_trace(misr_plan_t plan, double *out, int32_t max_rows, int32_t *rows);
 
 /* ---- Batched solves (many projections per launch) ---------------------------------------
- * A batch groups plans (uneven sizes, factors, frame counts, tile shapes and r/p storage types
- * are fine; all on one device) so that every SCG step of all of them is one fused-pass launch
- * over the tiles of all projections (one per tile shape and storage type present), then one
- * reduction launch, replayed as a CUDA graph.  The CT setting of Sec. 3.2 produces one independent projection per
+ * A batch groups plans (uneven sizes, factors, frame counts, tile shapes, r/p storage types,
+ * data terms, decimations and shift sets are fine; all on one device) so that every SCG step of
+ * all of them is one fused-pass launch over the tiles of all projections (one per tile shape
+ * and kernel variant present), then one reduction launch, replayed as a CUDA graph.  The CT setting of Sec. 3.2 produces one independent projection per
  * rotation angle; a batch advances many of them at once.  Each projection keeps its own
  * workspace, SCG state and fixed-order reductions, so its result equals its own misr_solve.
  * A plan may belong to several batches but runs one solve at a time. */

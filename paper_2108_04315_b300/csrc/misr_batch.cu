@@ -71,7 +71,8 @@ extern "C" misr_status misr_batch_create(int32_t n, const misr_plan_t *plans, mi
         idx[i] = i;
         b->max_iters = std::max(b->max_iters, plans[i]->d.iters);
     }
-    // one pass launch per (tile shape, storage type of r and p) present in the batch
+    // one pass launch per (tile shape, kernel variant: r/p storage type, data term, tap layout)
+    // present in the batch
     build_pass_lists(rp, idx, items, groups, b->segs);
     b->total_items = (int)items.size();
     b->total_groups = (int)groups.size();
