@@ -48,3 +48,39 @@ def test_detector_short_solve(detector):
     assert rel_l2(xg, xr) <= RTOL_X
     assert abs(P.objective(xg, y64) - P.objective(xr, y64)) <= RTOL_J * P.objective(xr, y64)
     plan.close()
+
+
+@pytest.mark.parametrize("model", ["l1", "paper_ct", "subpixel"])
+def test_full_size_model_options(orc, model):
+    """The other lines bench.py times, at their full size (4 x 2048^2 -> 4096^2): the L1 data
+    term (eps_d 0.01), the paper's CT setting (3x3 PSF, binning D, L1, lambda 0.05) and
+    non-integer shifts (x 0.02 / 0.51, y 0.04 / 0.53 LR px, 3x3 PSF): the forward operator and
+    the gradient over the whole image against the FP64 oracle."""
+    from paper_2108_04315_b300 import binding as B
+    h = w = 2048
+    f = 2
+    psf3 = gen.gaussian_psf(3, 0.5)
+    if model == "l1":
+        sh, psf, lam = gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), 0.01
+        kp, ko = dict(data_norm=B.MISR_NORM_L1, data_eps=0.01), dict(data_norm=orc.NORM_L1, data_eps=0.01)
+    elif model == "paper_ct":
+        sh, psf, lam = gen.half_pixel_shifts(), psf3, 0.05
+        kp = dict(data_norm=B.MISR_NORM_L1, data_eps=0.01, decimation=B.MISR_DECIM_BIN)
+        ko = dict(data_norm=orc.NORM_L1, data_eps=0.01, decimation=orc.DECIM_BIN)
+    else:
+        sh, psf, lam = [(dx, dy) for dy in (0.04, 0.53) for dx in (0.02, 0.51)], psf3, 0.01
+        kp, ko = dict(tile_shape=B.MISR_TILE_32x32), {}
+    P = orc.Problem(h, w, f, sh, psf, lam=lam, **ko)
+    plan = B.Plan(h, w, f, sh, psf, lam=lam, iters=1, **kp)
+    xt = gen.phantom(f * h, f * w, gen.CONFIG_SEEDS["detector"])
+    yf = plan.forward(to_dev(xt.astype(np.float32)))
+    assert rel_l2(yf.cpu().numpy(), P.forward_all(xt.astype(np.float32).astype(np.float64))) <= RTOL_OP
+    y = (P.forward_all(xt) + gen.gaussian_noise((4, h, w), 0.01, gen.CONFIG_SEEDS["detector"] + 1)).astype(np.float32)
+    x = (xt + 0.05 * gen.smooth_field(f * h, f * w, 72)).astype(np.float32)
+    J, g = plan.gradient(to_dev(y), to_dev(x))
+    Jr, gr = P.gradient(x.astype(np.float64), y.astype(np.float64))
+    # the L1 bar of tests/test_gpu_l1.py where the L1 term is used
+    tol = RTOL_OP + (16 * 2.0 ** -24 * float(np.abs(y).max()) / 0.01 if model != "subpixel" else 0.0)
+    assert rel_l2(g.cpu().numpy(), gr) <= tol
+    assert J == pytest.approx(Jr, rel=RTOL_J)
+    plan.close()
