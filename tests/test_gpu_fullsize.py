@@ -84,3 +84,13 @@ def test_full_size_model_options(orc, model):
     assert rel_l2(g.cpu().numpy(), gr) <= tol
     assert J == pytest.approx(Jr, rel=RTOL_J)
     plan.close()
+
+
+def test_full_size_interpolation_is_the_oracle_bitwise(detector):
+    """misr_interpolate at the full size, in the bench's configuration: the oracle's
+    shift-and-add rounded to float32, bit for bit."""
+    B, P, xt, y, (h, w, f, sh, psf) = detector
+    plan = B.Plan(h, w, f, sh, psf, lam=0.01, iters=1)
+    xi = plan.interpolate(to_dev(y)).cpu().numpy()
+    assert np.array_equal(xi, P.shift_add(y.astype(np.float64)).astype(np.float32))
+    plan.close()
