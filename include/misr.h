@@ -255,7 +255,9 @@ misr_status misr_debug_bounds(uint32_t *bits, int32_t *first);
  *   plan does not keep them), x_dev receives the image.  Asynchronous on stream unless stats is
  *   non-NULL, as misr_solve.
  * Errors: MISR_EINVAL (NULL arguments, too small a buffer, a checkpoint of another geometry,
- * storage type, data term, state layout or version), MISR_ECUDA, and misr_solve's. */
+ * storage type, data term, model (shifts, PSF, decimation, the prior's and the data term's
+ * constants; the iteration count may differ), state layout or version), MISR_ECUDA, and
+ * misr_solve's. */
 misr_status misr_state_bytes(misr_plan_t plan, size_t *bytes);
 misr_status misr_export_state(misr_plan_t plan, void *buf, size_t bytes);
 misr_status misr_import_state(misr_plan_t plan, const void *buf, size_t bytes);

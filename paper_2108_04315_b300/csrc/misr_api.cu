@@ -946,10 +946,39 @@ misr_status misr_debug_bounds(uint32_t *bits, int32_t *first) {
 // ---- checkpoint and resume
 namespace {
 struct CkptHeader {
-    uint32_t magic, version, H, W, bf16, state_bytes, l1, reserved;
+    uint32_t magic, version, H, W, bf16, state_bytes, l1, model;
 };
 static_assert(sizeof(CkptHeader) == 32, "checkpoint header");
-constexpr uint32_t CKPT_MAGIC = 0x4353524du, CKPT_VERSION = 1u;
+constexpr uint32_t CKPT_MAGIC = 0x4353524du, CKPT_VERSION = 2u;
+// FNV-1a hash of the model a state belongs to: frames and shifts, blur taps (with binning and
+// per-phase taps folded in), the prior's and the data term's constants.  A checkpoint resumes
+// only on a plan of the same model (the iteration count may differ).
+uint32_t model_hash(const DevProblem &hp) {
+    uint32_t hsh = 2166136261u;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) hsh = (hsh ^ b[i]) * 16777619u;
+    };
+    mix(&hp.f, sizeof hp.f);
+    mix(&hp.K, sizeof hp.K);
+    mix(hp.ty, sizeof(int) * hp.K);
+    mix(hp.tx, sizeof(int) * hp.K);
+    mix(hp.frame_of_phase, sizeof hp.frame_of_phase);
+    mix(hp.hy, sizeof hp.hy);
+    mix(hp.hx, sizeof hp.hx);
+    mix(&hp.phased, sizeof hp.phased);
+    if (hp.phased) {
+        mix(hp.ay, sizeof hp.ay);
+        mix(hp.ax, sizeof hp.ax);
+        mix(hp.tph, sizeof hp.tph);
+    }
+    mix(&hp.lambda, sizeof hp.lambda);
+    mix(&hp.eps, sizeof hp.eps);
+    mix(hp.gamma, sizeof hp.gamma);
+    mix(&hp.l1, sizeof hp.l1);
+    mix(&hp.data_eps, sizeof hp.data_eps);
+    return hsh;
+}
 size_t ckpt_bytes(const misr_plan_t p) {
     const size_t n = (size_t)p->hp.H * p->hp.W, rp = p->hp.rp_bf16 ? 2 : 4;
     return sizeof(CkptHeader) + sizeof(ScgState) + n * 4 + 2 * n * rp;
@@ -972,7 +1001,7 @@ misr_status misr_export_state(misr_plan_t p, void *buf, size_t bytes) {
     const size_t W = p->hp.W, H = p->hp.H, pitch = p->hp.pitch, rp = p->hp.rp_bf16 ? 2 : 4;
     char *out = static_cast<char *>(buf);
     CkptHeader h{CKPT_MAGIC, CKPT_VERSION, (uint32_t)H, (uint32_t)W, (uint32_t)p->hp.rp_bf16, (uint32_t)sizeof(ScgState),
-                 (uint32_t)p->hp.l1, 0u};
+                 (uint32_t)p->hp.l1, model_hash(p->hp)};
     std::memcpy(out, &h, sizeof h);
     std::memcpy(out + sizeof h, &st, sizeof st);
     char *planes = out + sizeof h + sizeof st;
@@ -993,6 +1022,8 @@ misr_status misr_import_state(misr_plan_t p, const void *buf, size_t bytes) {
     if (h.H != (uint32_t)p->hp.H || h.W != (uint32_t)p->hp.W || h.bf16 != (uint32_t)p->hp.rp_bf16 ||
         h.state_bytes != (uint32_t)sizeof(ScgState) || h.l1 != (uint32_t)p->hp.l1)
         return fail(MISR_EINVAL, "checkpoint of another geometry, storage type, data term or state layout");
+    if (h.model != model_hash(p->hp))
+        return fail(MISR_EINVAL, "checkpoint of another model (shifts, PSF, decimation or prior/data constants)");
     if (bytes < ckpt_bytes(p)) return fail(MISR_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", bytes, ckpt_bytes(p));
     DeviceGuard g(p->device);
     CK(cudaDeviceSynchronize());

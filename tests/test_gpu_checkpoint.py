@@ -84,4 +84,14 @@ def test_bad_checkpoints_rejected():
     with pytest.raises(B.MisrError) as e:
         a.import_state(bad)
     assert e.value.status == B.MISR_EINVAL
+    for other in (dict(psf=gen.gaussian_psf(5, 0.8)), dict(lam=0.02), dict(eps=2e-3),
+                  dict(shifts=[(0.0, 0.0), (0.5, 0.0), (0.0, 0.5)]), dict(psf=gen.gaussian_psf(3, 0.5),
+                                                                           decimation=B.MISR_DECIM_BIN)):
+        kw = dict(shifts=gen.half_pixel_shifts(), psf=PSF, lam=0.01, eps=1e-3)
+        kw.update(other)
+        d = B.Plan(16, 16, 2, kw.pop("shifts"), kw.pop("psf"), iters=2, **kw)
+        with pytest.raises(B.MisrError) as e:            # another model of the same geometry
+            d.import_state(ck)
+        assert e.value.status == B.MISR_EINVAL
+    B.Plan(16, 16, 2, gen.half_pixel_shifts(), PSF, iters=7).import_state(ck)   # another count: fine
     a.import_state(ck)                                   # the real one still loads
