@@ -162,6 +162,7 @@ struct Geo {
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 __device__ __forceinline__ void ld8(const float *p, float *v) {   // p 16-byte aligned
     const float4 a = ld4(p), b = ld4(p + 4);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
@@ -514,6 +515,42 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         }
         st4v(HS + n * GW + g, out);
     };
+    // C1 on pair h (G cols g + 2h, g + 2h + 1) of item it: the items past a whole round of the
+    // CTA are taken in halves, so that no thread of the interval does two whole items
+    auto item_C1_half = [&](int it, int h) {
+        int n, g;
+        item_rc<EH, GW / 4>(it, n, g);
+        if (!MISR_IN_BOUNDS(n >= 0 && n < EH && g >= 0 && g + 7 < EW && g + 3 < GW && (h == 0 || h == 1), BC_C1, n,
+                            g)) return;
+        const int gp = g + 2 * h;
+        float in[6];                 // E at G cols gp-2 .. gp+3 (8-byte aligned pairs)
+        {
+            const float2 a0 = ld2(YB + n * EW + gp), a1 = ld2(YB + n * EW + gp + 2), a2 = ld2(YB + n * EW + gp + 4);
+            in[0] = a0.x; in[1] = a0.y; in[2] = a1.x; in[3] = a1.y; in[4] = a2.x; in[5] = a2.y;
+        }
+        float out[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float s = 0.f;
+            const int u = x0 - 2 + gp + j;
+            float w5[5];
+            if constexpr (PH && !BORDER) taps5(ph_taps(TPH_AFX, u), w5);
+#pragma unroll
+            for (int b = -2; b <= 2; ++b) {
+                float v = in[j + 2 + b];
+                if (!PH && BORDER && !adj_tap_ok(u, b, f, fmag)) v = 0.f;
+                float wgt = cs[C_HX + b + 2];
+                if constexpr (PH && !BORDER) wgt = w5[b + 2];
+                if constexpr (PH && BORDER) {
+                    const float *tf = ph_taps(TPH_FX, u + b);
+                    wgt = ph_adj_w<BORDER>(tf, tf + 64 * (TPH_PX - TPH_FX), b, u, u + b < 0 ? 0 : mod_f(u + b, f, fmag));
+                }
+                s = fmaf(wgt, v, s);
+            }
+            out[j] = s;
+        }
+        st2(HS + n * GW + gp, make_float2(out[0], out[1]));
+    };
     // horizontal blur of p on rows [-2, TH+2) x owned cols (for the curvature forms)
     auto item_HP = [&](int it) {
         const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
@@ -705,6 +742,64 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
             }
         }
     };
+    // C2 + r' on pair h (G cols g + 2h, g + 2h + 1) of item it, as item_C2r does for both pairs
+    auto item_C2r_half = [&](int it, int h) {
+        int n, g;
+        item_rc<GH, GW / 4>(it, n, g);
+        if (!MISR_IN_BOUNDS(n >= 0 && n < GH && g >= 0 && g + 3 < GW && n + 4 < EH && (h == 0 || h == 1), BC_C2, n, g))
+            return;
+        const int u = y0 - 2 + n, gp = g + 2 * h;
+        float2 s2 = make_float2(0.f, 0.f);
+        float w5[5];
+        if constexpr (PH && !BORDER) taps5(ph_taps(TPH_AFY, u), w5);
+#pragma unroll
+        for (int a = -2; a <= 2; ++a) {
+            const float2 v = ld2(HS + (n + 2 + a) * GW + gp);
+            float wgt;
+            if constexpr (PH && !BORDER) {
+                wgt = DSCALE * w5[a + 2];
+            } else if constexpr (PH) {
+                const float *tf = ph_taps(TPH_FY, u + a);
+                wgt = DSCALE * ph_adj_w<BORDER>(tf, tf + 64 * (TPH_PY - TPH_FY), a, u, u + a < 0 ? 0 : mod_f(u + a, f, fmag));
+            } else {
+                wgt = (BORDER && !adj_tap_ok(u, a, f, fmag)) ? 0.f : DSCALE * cs[C_HY + a + 2];
+            }
+            s2 = f2fma(bc2(wgt), v, s2);
+        }
+        const float2 gb = ld2(GB + n * GW + gp);
+        float r0 = -fmaf(lambda, gb.x, s2.x), r1 = -fmaf(lambda, gb.y, s2.y);
+        if (BORDER) {
+            const int gx = x0 - 2 + gp;
+            if (!(u >= 0 && u < H && gx >= 0 && gx < W)) r0 = 0.f;
+            if (!(u >= 0 && u < H && gx + 1 >= 0 && gx + 1 < W)) r1 = 0.f;
+        }
+        if constexpr (rpb) {
+            r0 = __bfloat162float(__float2bfloat16_rn(r0));
+            r1 = __bfloat162float(__float2bfloat16_rn(r1));
+        }
+        st2(GB + n * GW + gp, make_float2(r0, r1));
+        const int orow = n - 2, oc = gp - 2;   // owned tile cols oc, oc + 1 (XB cols oc + 8, oc + 9)
+        if (orow < 0 || orow >= TH || oc < 0 || oc >= TW) return;
+        const float2 ro = ld2(RB + (orow + 6) * XW + gp + 6), pq = ld2(PB + (orow + 6) * XW + gp + 6);
+        const int gx = x0 + oc;
+        if (!BORDER || (u < H && gx + 1 < W)) {
+            if (!MISR_IN_BOUNDS(u >= 0 && u < H && gx >= 0 && gx + 1 < W, BC_C2_STORE, u, gx)) return;
+            if (rpb)
+                *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(Rn) + (size_t)u * pitch + gx) =
+                    __floats2bfloat162_rn(r0, r1);
+            else
+                st2(Rn + (size_t)u * pitch + gx, make_float2(r0, r1));
+            A.rr = fmaf(r0, r0, fmaf(r1, r1, A.rr));
+            A.rrx = fmaf(r0, ro.x, fmaf(r1, ro.y, A.rrx));
+            A.pr = fmaf(pq.x, r0, fmaf(pq.y, r1, A.pr));
+        } else if (u < H && gx < W) {
+            if (rpb) reinterpret_cast<__nv_bfloat16 *>(Rn)[(size_t)u * pitch + gx] = __float2bfloat16_rn(r0);
+            else Rn[(size_t)u * pitch + gx] = r0;
+            A.rr = fmaf(r0, r0, A.rr);
+            A.rrx = fmaf(r0, ro.x, A.rrx);
+            A.pr = fmaf(pq.x, r0, A.pr);
+        }
+    };
     // horizontal blur of r' on rows [-2, TH+2) x owned cols
     auto item_HR = [&](int it) {
         const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
@@ -870,11 +965,25 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
     else
         for (int it = tid - N_BTV3; it < N_B2; it += NT - N_BTV3) item_B2(it);
     __syncthreads();
-    // I4: adjoint horizontal blur
-    for (int it = tid; it < N_C1; it += NT) item_C1(it);
+    // I4: adjoint horizontal blur.  I4 and I5 have between one and one and a half rounds of
+    // items for the CTA: the first NT items go whole, one per thread, and the rest in halves
+    // (a pair of pixels each, the two halves of an item on neighbouring threads), so that no
+    // thread does two whole items
+    constexpr bool C1_SPLIT = N_C1 > NT && 2 * (N_C1 - NT) <= NT, C2_SPLIT = N_C2 > NT && 2 * (N_C2 - NT) <= NT;
+    if constexpr (C1_SPLIT) {
+        item_C1(tid);
+        if (tid < 2 * (N_C1 - NT)) item_C1_half(NT + (tid >> 1), tid & 1);
+    } else {
+        for (int it = tid; it < N_C1; it += NT) item_C1(it);
+    }
     __syncthreads();
     // I5: adjoint vertical blur and r'
-    for (int it = tid; it < N_C2; it += NT) item_C2r(it);
+    if constexpr (C2_SPLIT) {
+        item_C2r(tid);
+        if (tid < 2 * (N_C2 - NT)) item_C2r_half(NT + (tid >> 1), tid & 1);
+    } else {
+        for (int it = tid; it < N_C2; it += NT) item_C2r(it);
+    }
     hook(5);
     __syncthreads();
     // I6: horizontal blurs of r' and p (HS is free once C2 has read it)
