@@ -579,6 +579,37 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
         }
         st4v(HS + n * CW + o, out);
     };
+    // the p blur on pair h (owned cols o + 2h, o + 2h + 1) of item it (see the split of I4)
+    auto item_HP_half = [&](int it, int h) {
+        const int n = it / (CW / 4), o = 4 * (it - n * (CW / 4));
+        if (!MISR_IN_BOUNDS(n >= 0 && n < CH && o + 15 < XW && o + 3 < CW && (h == 0 || h == 1), BC_HP, n, o)) return;
+        const int op = o + 2 * h;
+        float in6[6];                                 // p at owned cols op-2 .. op+3 (XB cols op+6 ..)
+        {
+            const float *q = PB + (n + 4) * XW + op + 6;
+            const float2 a0 = ld2(q), a1 = ld2(q + 2), a2 = ld2(q + 4);
+            in6[0] = a0.x; in6[1] = a0.y; in6[2] = a1.x; in6[3] = a1.y; in6[4] = a2.x; in6[5] = a2.y;
+        }
+        float out[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float sp = 0.f;
+            const int lim = BORDER ? fwd_lim(x0 + op + j, f, fmag) : 2;
+            float w5[5];
+            if constexpr (PH) {
+                const float *tf = ph_taps(TPH_FX, x0 + op + j);
+                ph_fwd_taps<BORDER>(tf, tf + 64 * (TPH_PX - TPH_FX), lim, w5);
+            }
+#pragma unroll
+            for (int b = -2; b <= 2; ++b) {
+                float vp = in6[j + 2 - b];
+                if (!PH && BORDER && b > lim) vp = 0.f;
+                sp = fmaf(PH ? w5[b + 2] : cs[C_HX + b + 2], vp, sp);
+            }
+            out[j] = sp;
+        }
+        st2(HS + n * CW + op, make_float2(out[0], out[1]));
+    };
     // BTV gradient (without lambda) of the prior at x' on the G grid (origin (-2, -2)):
     // g(q) = sum_d gamma_d [psi'(x_q - x_{q+d}) - psi'(x_{q-d} - x_q)] over pairs inside the
     // image (the prior's value is summed with the curvature forms, over owned q only)
@@ -986,11 +1017,18 @@ __device__ __forceinline__ bool pass_tile(const DevProblem &P, float *sm, float 
     }
     hook(5);
     __syncthreads();
-    // I6: horizontal blurs of r' and p (HS is free once C2 has read it)
-    for (int it = tid; it < N_HR + N_HP; it += NT) {
+    // I6: horizontal blurs of r' and p (HS is free once C2 has read it).  When the items past
+    // the last whole round of the CTA are p-blur items, they are taken in halves as in I4
+    constexpr int N6 = N_HR + N_HP, R6 = N6 / NT, Q6 = N6 - R6 * NT;
+    constexpr bool I6_SPLIT = Q6 > 0 && 2 * Q6 <= NT && N_HR <= R6 * NT;
+#pragma unroll 1
+    for (int r = 0; r < (I6_SPLIT ? R6 : (N6 + NT - 1) / NT); ++r) {
+        const int it = tid + r * NT;
         if (it < N_HR) item_HR(it);
-        else item_HP(it - N_HR);
+        else if (it < N6) item_HP(it - N_HR);
     }
+    if constexpr (I6_SPLIT)
+        if (tid < 2 * Q6) item_HP_half(R6 * NT - N_HR + (tid >> 1), tid & 1);
     __syncthreads();
     // I7: curvature forms
     for (int it = tid; it < N_E; it += NT) item_E(it);
