@@ -366,13 +366,24 @@ misr_status misr_autotune(const misr_desc *desc, int32_t passes, int32_t *shape_
  * that cannot afford the implicit device synchronisation of cudaMalloc / cudaFree.
  * The workspace is a fixed array inside the library, sized for HR images of at most
  * 512 x 512 pixels (about 7 MB, held on every GPU that loads the library until the process
- * exits); larger problems return MISR_EINVAL.  The first call on a device looks up the
- * array's device address and sets the pass kernel's attributes; make that first call before
- * any stream capture.  Every call uses the same array, so calls that overlap on the GPU
- * (other streams or host threads) race.  y_dev, x_dev, g_dev as for misr_gradient.
- * Blocking: g_dev and *J_out (may be NULL) are valid on return. */
+ * exits); larger problems return MISR_EINVAL.  It computes in FP32 only: a descriptor with
+ * iterate_dtype other than MISR_F32 returns MISR_EINVAL.  The first call on a device looks up
+ * the array's device address and sets the pass kernel's attributes.  Every call uses the same
+ * array, so calls that overlap on the GPU (other streams or host threads) race.  y_dev, x_dev,
+ * g_dev as for misr_gradient.
+ * Blocking: the call copies its problem record from host memory and synchronises `stream`
+ * before it returns, so g_dev and *J_out (may be NULL) are valid on return; it must not be
+ * called on a stream that is being captured into a CUDA graph.  A tile load that does not land
+ * within the wait limit (misr_noalloc_set_wait_limit) returns MISR_ETIMEOUT; the next call
+ * starts from a clean array. */
 misr_status misr_gradient_noalloc(const misr_desc *desc, const void *y_dev, const float *x_dev, float *g_dev,
                                   double *J_out, misr_stream_t stream);
+
+/* Polls of a tile-load wait before misr_gradient_noalloc reports the load late (the
+ * counterpart of misr_plan_set_wait_limit for the plan-free call; process-wide, default
+ * 2^24).  0 reports every load late, which the failure tests use to exercise the timeout path
+ * without a fault.  Errors: none. */
+misr_status misr_noalloc_set_wait_limit(uint32_t tries);
 
 #ifdef __cplusplus
 }

@@ -79,6 +79,20 @@ int orc_set_decimation(orc_problem *P, int mode) {
     return 0;
 }
 
+/* FP32 storage of the SCG state as a perturbation model: with it on, orc_scg rounds x, r and
+ * p to the nearest FP32 value after every update; every other operation stays FP64.  It
+ * measures how far an implementation that keeps its state in FP32 must drift from the FP64
+ * run.  Returns 0, or -1 for a value other than 0 or 1. */
+int orc_set_state_f32(orc_problem *P, int on) {
+    if (on != 0 && on != 1) return -1;
+    P->state_f32 = on;
+    return 0;
+}
+
+static void round_f32(double *v, long n) {
+    for (long i = 0; i < n; ++i) v[i] = (double)(float)v[i];
+}
+
 /* (M_k x)(u, v) = sum_{p, q in {0, 1}} wy_p wx_q x(u + ty_k + p, v + tx_k + q), x zero outside
  * the grid, wy = (1 - fy_k, fy_k), wx = (1 - fx_k, fx_k): a translation for integer shifts,
  * bilinear interpolation otherwise.  The value at one pixel of B's input: */
@@ -528,8 +542,10 @@ int orc_scg(const orc_problem *P, const double *y, const double *x0, int iters, 
     int success = 1, it;
 
     memcpy(x, x0, sizeof(double) * n);
+    if (P->state_f32) round_f32(x, n);
     double E = orc_gradient(P, x, y, r);
     for (long i = 0; i < n; ++i) { r[i] = -r[i]; p[i] = r[i]; }
+    if (P->state_f32) { round_f32(r, n); round_f32(p, n); }
 
     for (it = 0; it < iters; ++it) {
         if (success) {
@@ -564,6 +580,7 @@ int orc_scg(const orc_problem *P, const double *y, const double *x0, int iters, 
             const double beta = (rr_new - rr_cross) / mu;
             memcpy(x, xt, sizeof(double) * n);
             for (long i = 0; i < n; ++i) { p[i] = rt[i] + beta * p[i]; r[i] = rt[i]; }
+            if (P->state_f32) { round_f32(x, n); round_f32(r, n); round_f32(p, n); }
             E = Et;
             lam_bar = 0.0;
             success = 1;

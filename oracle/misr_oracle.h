@@ -28,9 +28,12 @@
  * check that does not call the oracle twice: a dense D*B*M product built from the textbook
  * matrices, closed-form BTV values, central finite differences, exact recovery, a dense
  * normal-equation solve and conjugate-gradient identities.
- * Parity unpinned: two branches of orc_scg, the scale increase after a poor step (Delta < 0.25)
- * and the negative-curvature correction (delta <= 0), follow Moller's algorithm as restated
- * there; neither occurs on the quadratic pins, and no closed form covers them on the BTV problem.
+ * Moller's scale increase after a poor step (Delta < 0.25) is pinned through the identity it
+ * implies after a rejected step: the next step's curvature is delta_k (2 - Delta_k) and its
+ * step alpha_k / (2 - Delta_k).  The negative-curvature correction (delta <= 0) cannot run for
+ * a convex J with Moller's lambda > 0 (delta is p.H p + lambda |p|^2 > 0 on a fresh direction
+ * and grows after a rejection); the pins check that every first attempt along a direction has
+ * delta_k = p_k.H p_k + lambda_{k-1} |p_k|^2, which a correction would break.
  */
 #ifndef MISR_ORACLE_H
 #define MISR_ORACLE_H
@@ -60,6 +63,9 @@ typedef struct {
     int decim;                /* ORC_DECIM_POINT (default) or ORC_DECIM_BIN */
     double fy[ORC_MAXK];      /* fractional part a_k of the HR shift, rows (ty = floor) */
     double fx[ORC_MAXK];      /* fractional part a_k of the HR shift, cols (tx = floor) */
+    int state_f32;            /* 1: orc_scg rounds x, r and p to FP32 after every update (a
+                                 model of FP32 storage of the SCG state, for sensitivity
+                                 studies; 0, the default, keeps everything in FP64) */
 } orc_problem;
 
 /* one row of the SCG trace per iteration (failed iterations included) */
@@ -83,6 +89,7 @@ int orc_init(orc_problem *P, int h, int w, int K, int f, const double *shifts_lr
              double eps, int reg);
 int orc_set_data_norm(orc_problem *P, int norm, double data_eps);
 int orc_set_decimation(orc_problem *P, int mode);
+int orc_set_state_f32(orc_problem *P, int on);
 int orc_threads(void);
 void orc_forward(const orc_problem *P, int k, const double *x, double *out);
 void orc_adjoint(const orc_problem *P, int k, const double *e, double *out);

@@ -29,6 +29,7 @@ class _Problem(C.Structure):
         ("eps", C.c_double), ("reg", C.c_int),
         ("data_norm", C.c_int), ("data_eps", C.c_double), ("decim", C.c_int),
         ("fy", C.c_double * MAXK), ("fx", C.c_double * MAXK),
+        ("state_f32", C.c_int),
     ]
 
 
@@ -58,6 +59,8 @@ def lib():
         L.orc_set_data_norm.restype = C.c_int
         L.orc_set_decimation.argtypes = [pp, C.c_int]
         L.orc_set_decimation.restype = C.c_int
+        L.orc_set_state_f32.argtypes = [pp, C.c_int]
+        L.orc_set_state_f32.restype = C.c_int
         for name in ("orc_forward", "orc_adjoint"):
             getattr(L, name).argtypes = [pp, C.c_int, dp, dp]
         L.orc_reg_value.argtypes = [pp, dp]
@@ -97,7 +100,7 @@ class Problem:
     """One MISR problem: K LR frames of h x w, magnification f, shifts (dx, dy) in LR px."""
 
     def __init__(self, h, w, f, shifts, psf, lam=0.01, btv_alpha=0.4, btv_w=3, eps=1e-3,
-                 reg=REG_BTV, data_norm=NORM_L2, data_eps=0.0, decimation=DECIM_POINT):
+                 reg=REG_BTV, data_norm=NORM_L2, data_eps=0.0, decimation=DECIM_POINT, state_f32=False):
         self.h, self.w, self.f = int(h), int(w), int(f)
         self.K = len(shifts)
         self.H, self.W = self.f * self.h, self.f * self.w
@@ -113,6 +116,9 @@ class Problem:
             raise ValueError("data norm: L2, or L1 with data_eps > 0")
         if lib().orc_set_decimation(C.byref(self._p), int(decimation)) != 0:
             raise ValueError("decimation: DECIM_POINT or DECIM_BIN")
+        # FP32 storage of the SCG state (a sensitivity model; FP64 by default)
+        if lib().orc_set_state_f32(C.byref(self._p), int(bool(state_f32))) != 0:
+            raise ValueError("state_f32: a bool")
         self.data_norm = int(data_norm)
 
     @property

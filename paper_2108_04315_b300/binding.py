@@ -81,6 +81,8 @@ def lib():
         L.misr_forward.argtypes = [VP, VP, VP, VP]
         L.misr_interpolate.argtypes = [VP, VP, VP, VP]
         L.misr_gradient.argtypes = [VP, VP, VP, VP, DP, VP]
+        L.misr_gradient_noalloc.argtypes = [C.POINTER(misr_desc), VP, VP, VP, DP, VP]
+        L.misr_noalloc_set_wait_limit.argtypes = [C.c_uint32]
         L.misr_pass_probe.argtypes = [VP, VP, VP, VP, VP, C.c_double, C.c_double, VP, VP, VP, DP, VP]
         L.misr_solve.argtypes = [VP, VP, VP, VP, C.POINTER(misr_stats)]
         L.misr_solve_host.argtypes = [VP, VP, VP, C.POINTER(misr_stats)]
@@ -108,7 +110,7 @@ def lib():
                      "misr_get_trace", "misr_state_bytes", "misr_export_state", "misr_import_state", "misr_resume",
                      "misr_batch_create", "misr_batch_destroy", "misr_batch_solve", "misr_server_create",
                      "misr_server_destroy", "misr_submit", "misr_poll", "misr_server_wait", "misr_server_counters", "misr_cancel",
-                     "misr_autotune"):
+                     "misr_autotune", "misr_gradient_noalloc", "misr_noalloc_set_wait_limit"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -180,6 +182,17 @@ TMA_WAIT_TRIES_DEFAULT = 1 << 24
 
 def misr_plan_set_wait_limit(plan: int, tries: int):
     _check(lib().misr_plan_set_wait_limit(VP(plan), int(tries)), "misr_plan_set_wait_limit")
+
+
+def misr_gradient_noalloc(desc: misr_desc, y_dev: int, x_dev: int, g_dev: int, stream: int = 0) -> float:
+    J = C.c_double()
+    _check(lib().misr_gradient_noalloc(C.byref(desc), VP(y_dev), VP(x_dev), VP(g_dev), C.byref(J), VP(stream)),
+           "misr_gradient_noalloc")
+    return J.value
+
+
+def misr_noalloc_set_wait_limit(tries: int):
+    _check(lib().misr_noalloc_set_wait_limit(int(tries)), "misr_noalloc_set_wait_limit")
 
 
 def misr_solve(plan: int, y_dev: int, x_dev: int, stream: int = 0, want_stats: bool = True):

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -294,29 +295,50 @@ static misr_status set_attrs_one() {
     }
 }
 
+// Per-device state of the pass kernels: whether their attributes (dynamic shared memory above
+// 48 KB, carveout) are set on that device, and their resident CTAs on the whole GPU per shape
+// and variant (0: not measured yet).  Function attributes are per device, so every device a
+// plan, batch, server or allocation-free call runs on sets them once, with it current.
+constexpr int MAX_DEVICES = 64;
+struct PassDeviceState {
+    bool attrs = false;
+    int resident[N_SHAPES][N_VARIANTS] = {};
+};
+std::mutex g_pass_dev_mu;
+PassDeviceState g_pass_dev[MAX_DEVICES];
+
+static misr_status current_device(int *dev) {
+    CK(cudaGetDevice(dev));
+    if (*dev < 0 || *dev >= MAX_DEVICES) return fail(MISR_EINVAL, "device %d out of range", *dev);
+    return MISR_OK;
+}
+
 static misr_status set_pass_attrs() {
-    static bool done = false;
-    if (done) return MISR_OK;
+    int dev = 0;
+    misr_status r = current_device(&dev);
+    if (r != MISR_OK) return r;
+    std::lock_guard<std::mutex> lock(g_pass_dev_mu);
+    if (g_pass_dev[dev].attrs) return MISR_OK;
     for (int sh = 0; sh < N_SHAPES; ++sh)
         for (int v = 0; v < N_VARIANTS; ++v) {
-            misr_status r = with_shape(sh, [v](auto S) {
+            r = with_shape(sh, [v](auto S) {
                 return with_variant(v, [](auto V) { return set_attrs_one<decltype(S)::value, decltype(V)::value>(); });
             });
             if (r != MISR_OK) return r;
         }
-    done = true;
+    g_pass_dev[dev].attrs = true;
     return MISR_OK;
 }
 
-// CTAs of the fused pass resident on the whole GPU, per shape and variant (the L1 and
+// CTAs of the fused pass resident on the whole current GPU, per shape and variant (the L1 and
 // per-phase variants take more shared memory)
 static int resident_ctas(int shape, int variant) {
-    // 0: not measured yet (a measured count is at least the SM count); concurrent callers may
-    // both measure and store the same value
-    static int cached[N_SHAPES][N_VARIANTS] = {};
-    if (cached[shape][variant] > 0) return cached[shape][variant];
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
+    int dev = 0;
+    if (current_device(&dev) != MISR_OK) return 1;
+    std::lock_guard<std::mutex> lock(g_pass_dev_mu);
+    int &cached = g_pass_dev[dev].resident[shape][variant];
+    if (cached > 0) return cached;
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     with_shape(shape, [&](auto S) {
         return with_variant(variant, [&](auto V) {
@@ -327,9 +349,8 @@ static int resident_ctas(int shape, int variant) {
         });
     });
     cudaGetLastError();
-    const int n = std::max(sms, 1) * std::max(per_sm, 1);
-    cached[shape][variant] = n;
-    return n;
+    cached = std::max(sms, 1) * std::max(per_sm, 1);
+    return cached;
 }
 
 // persistent grid: one CTA per resident slot, at most one per tile
@@ -422,6 +443,71 @@ static void set_groups(DevProblem &hp) {
     hp.n_groups = (hp.n_tiles + hp.group - 1) / hp.group;
 }
 
+int misr_host::row_pitch(int W) { return (W + 7) & ~7; }   // 16-byte rows for float and bf16 planes
+
+// The problem record of a descriptor without its buffers: geometry, taps, prior and data-term
+// constants, tile shape (`shape`, or -1 for the plan's choice) and reduction groups.  Plans and
+// the allocation-free gradient both build their records here, so they cannot disagree.
+static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevProblem &hp) {
+    const int f = d.factor;
+    hp = DevProblem{};
+    hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
+    hp.H = f * d.lr_h; hp.W = f * d.lr_w;
+    hp.pitch = row_pitch(hp.W);
+    hp.wait_tries = (int)TMA_WAIT_TRIES;
+    hp.iters = iters;
+    misr_status s = setup_geometry(d, hp);
+    if (s != MISR_OK) return s;
+    hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
+    set_data_norm(hp, d);
+    double eps_pairs = 0;
+    for (int dy = 0; dy < BTV_W; ++dy)
+        for (int dx = 0; dx < BTV_W; ++dx) {
+            const int dd = dy * BTV_W + dx;
+            float g = 0.f;
+            if (dd != 0 && dx < d.btv_w && dy < d.btv_w) g = (float)std::pow(d.btv_alpha, dx + dy);
+            hp.gamma[dd] = g;
+            if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
+        }
+    hp.eps_pairs = d.eps * eps_pairs;
+    hp.rp_bf16 = d.iterate_dtype == MISR_BF16;
+    set_shape(hp, hp.phased ? PHASED_SHAPE : shape >= 0 ? shape : pick_shape(d));
+    set_groups(hp);
+    return MISR_OK;
+}
+
+// Byte offsets of a plan's workspace (one allocation): X[2], Y (float), R[2], P[2] (float or
+// bf16) | tile and group sums, group counters, pass counter, launch tile counter | state |
+// trace | problem | tile list | group list.
+struct PlanLayout {
+    size_t img, rp_img, o_img, o_part, o_gpart, o_cnt, o_work, o_st, o_tr, o_pr, o_tm, o_gl, total;
+};
+static PlanLayout plan_layout(const misr_desc &d, const DevProblem &hp) {
+    PlanLayout L{};
+    const size_t n_pitched = (size_t)hp.H * hp.pitch;
+    L.img = align_up(n_pitched * sizeof(float), 256);
+    L.rp_img = d.iterate_dtype == MISR_BF16 ? align_up(n_pitched * 2, 256) : L.img;
+    size_t off = 0;
+    L.o_img = off; off += 3 * L.img + 4 * L.rp_img;
+    L.o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(float2), 256);
+    L.o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(float2), 256);
+    L.o_cnt = off; off += 256;
+    L.o_work = off; off += 256;
+    L.o_st = off; off += align_up(sizeof(ScgState), 256);
+    L.o_tr = off; off += align_up((size_t)std::max(d.iters, 1) * TRACE_COLS * sizeof(double), 256);
+    L.o_pr = off; off += align_up(sizeof(DevProblem), 256);
+    L.o_tm = off; off += align_up((size_t)hp.n_tiles * sizeof(int2), 256);
+    L.o_gl = off; off += align_up((size_t)hp.n_groups * sizeof(int2), 256);
+    L.total = off;
+    return L;
+}
+
+size_t misr_host::plan_bytes(const misr_desc &d) {
+    DevProblem hp;
+    if (fill_problem(d, d.iters, -1, hp) != MISR_OK) return 0;
+    return plan_layout(d, hp).total;
+}
+
 int misr_host::grid_for(size_t n, int threads) {
     size_t b = (n + threads - 1) / threads;
     return (int)std::min<size_t>(std::max<size_t>(b, 1), 148 * 16);
@@ -508,29 +594,9 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     misr_status s = validate(desc);
     if (s != MISR_OK) return s;
     const misr_desc &d = *desc;
-    const int f = d.factor;
-    DevProblem hp{};
-    hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
-    hp.H = f * d.lr_h; hp.W = f * d.lr_w;
-    hp.pitch = (hp.W + 7) & ~7;   // 16-byte rows for float and bf16 planes
-    hp.wait_tries = (int)TMA_WAIT_TRIES;
-    hp.iters = d.iters;
-    s = setup_geometry(d, hp);
+    DevProblem hp;
+    s = fill_problem(d, d.iters, -1, hp);
     if (s != MISR_OK) return s;
-    hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
-    set_data_norm(hp, d);
-    double eps_pairs = 0;
-    for (int dy = 0; dy < BTV_W; ++dy)
-        for (int dx = 0; dx < BTV_W; ++dx) {
-            const int dd = dy * BTV_W + dx;
-            float g = 0.f;
-            if (dd != 0 && dx < d.btv_w && dy < d.btv_w) g = (float)std::pow(d.btv_alpha, dx + dy);
-            hp.gamma[dd] = g;
-            if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
-        }
-    hp.eps_pairs = d.eps * eps_pairs;
-    set_shape(hp, hp.phased ? PHASED_SHAPE : pick_shape(d));
-    set_groups(hp);
 
     misr_plan_t p = new (std::nothrow) misr_plan_s();
     if (!p) return fail(MISR_ENOMEM, "host allocation failed");
@@ -542,21 +608,10 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     p->n_pitched = (size_t)hp.H * hp.pitch;
     p->m_total = (size_t)d.K * d.lr_h * d.lr_w;
 
-    // workspace: X[2], R[2], P[2], Y | tile and group sums, group counters, pass counter,
-    // launch tile counter | state | trace | problem | tile list
-    const size_t img = align_up(p->n_pitched * sizeof(float), 256);
-    const size_t rp_img = d.iterate_dtype == MISR_BF16 ? align_up(p->n_pitched * 2, 256) : img;
-    size_t off = 0;
-    const size_t o_img = off; off += 3 * img + 4 * rp_img;   // X[2], Y (float); R[2], P[2]
-    const size_t o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(float2), 256);
-    const size_t o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(float2), 256);
-    const size_t o_cnt = off; off += 256;
-    const size_t o_work = off; off += 256;
-    const size_t o_st = off; off += align_up(sizeof(ScgState), 256);
-    const size_t o_tr = off; off += align_up((size_t)std::max(d.iters, 1) * TRACE_COLS * sizeof(double), 256);
-    const size_t o_pr = off; off += align_up(sizeof(DevProblem), 256);
-    const size_t o_tm = off; off += align_up((size_t)hp.n_tiles * sizeof(int2), 256);
-    const size_t o_gl = off; off += align_up((size_t)hp.n_groups * sizeof(int2), 256);
+    const PlanLayout lay = plan_layout(d, hp);
+    const size_t off = lay.total, img = lay.img, rp_img = lay.rp_img, o_img = lay.o_img;
+    const size_t o_part = lay.o_part, o_gpart = lay.o_gpart, o_cnt = lay.o_cnt, o_work = lay.o_work;
+    const size_t o_st = lay.o_st, o_tr = lay.o_tr, o_pr = lay.o_pr, o_tm = lay.o_tm, o_gl = lay.o_gl;
     p->ws_bytes = off;
     cudaError_t e = cudaMalloc((void **)&p->ws, off);
     if (e != cudaSuccess) {
@@ -571,7 +626,6 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
         hp.Pv[i] = (float *)(b + o_img + 3 * img + (2 + i) * rp_img);
     }
     hp.Y = (float *)(b + o_img + 2 * img);
-    hp.rp_bf16 = d.iterate_dtype == MISR_BF16;
     hp.partials = (float2 *)(b + o_part);
     hp.gpartials = (float2 *)(b + o_gpart);
     hp.counter = (unsigned int *)(b + o_cnt);
@@ -1136,6 +1190,8 @@ struct NoallocDevice {
     bool ready = false;
     unsigned char *base = nullptr;   // device address of g_noalloc_scratch on this device
 };
+// polls of a tile-load wait before the allocation-free gradient reports it late
+std::atomic<uint32_t> g_noalloc_wait_tries{TMA_WAIT_TRIES};
 constexpr int NOALLOC_MAX_DEVICES = 64;
 NoallocDevice g_noalloc_devices[NOALLOC_MAX_DEVICES];
 std::mutex g_noalloc_mutex;
@@ -1164,29 +1220,9 @@ misr_status noalloc_setup(unsigned char **base) {
 
 // The problem record of the descriptor with its buffers inside the scratch array.
 misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem &hp) {
-    const int f = d.factor;
-    hp = DevProblem{};
-    hp.h = d.lr_h; hp.w = d.lr_w; hp.f = f; hp.K = d.K;
-    hp.H = f * d.lr_h; hp.W = f * d.lr_w;
-    hp.pitch = (hp.W + 7) & ~7;   // 16-byte rows for float and bf16 planes
-    hp.wait_tries = (int)TMA_WAIT_TRIES;
-    hp.iters = 0;
-    misr_status s = setup_geometry(d, hp);
+    misr_status s = fill_problem(d, 0, DEFAULT_SHAPE, hp);
     if (s != MISR_OK) return s;
-    hp.lambda = (float)d.lambda; hp.eps = (float)d.eps; hp.eps2 = (float)(d.eps * d.eps);
-    set_data_norm(hp, d);
-    double eps_pairs = 0;
-    for (int dy = 0; dy < BTV_W; ++dy)
-        for (int dx = 0; dx < BTV_W; ++dx) {
-            const int dd = dy * BTV_W + dx;
-            float g = 0.f;
-            if (dd != 0 && dx < d.btv_w && dy < d.btv_w) g = (float)std::pow(d.btv_alpha, dx + dy);
-            hp.gamma[dd] = g;
-            if (dd != 0 && hp.H > dy && hp.W > dx) eps_pairs += (double)g * (double)(hp.H - dy) * (double)(hp.W - dx);
-        }
-    hp.eps_pairs = d.eps * eps_pairs;
-    set_shape(hp, hp.phased ? PHASED_SHAPE : DEFAULT_SHAPE);
-    set_groups(hp);
+    hp.wait_tries = (int)std::min<uint32_t>(g_noalloc_wait_tries.load(), 0x7fffffffu);
     for (int i = 0; i < 2; ++i) {
         hp.X[i] = reinterpret_cast<float *>(base + NA_O_IMG + (0 + i) * NOALLOC_IMG);
         hp.Rv[i] = reinterpret_cast<float *>(base + NA_O_IMG + (2 + i) * NOALLOC_IMG);
@@ -1208,6 +1244,8 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     if (!y_dev || !x_dev || !g_dev) return fail(MISR_EINVAL, "NULL argument");
     misr_status s = validate(desc);
     if (s != MISR_OK) return s;
+    if (desc->iterate_dtype != MISR_F32)
+        return fail(MISR_EINVAL, "the allocation-free gradient computes in FP32 only (iterate_dtype MISR_F32)");
     const int H = desc->factor * desc->lr_h, W = desc->factor * desc->lr_w;
     if (H > NOALLOC_MAX_H || W > NOALLOC_MAX_W)
         return fail(MISR_EINVAL, "HR image %d x %d exceeds the allocation-free limit %d x %d", H, W, NOALLOC_MAX_H,
@@ -1246,6 +1284,11 @@ extern "C" misr_status misr_gradient_noalloc(const misr_desc *desc, const void *
     CK(cudaStreamSynchronize(st));
     if (hst.status != DEV_OK) return fail(MISR_ETIMEOUT, "a tile load of the fused pass did not complete in time");
     if (J_out) *J_out = hst.sums[P_JD] + (double)hp.lambda * (hst.sums[P_JB] - hp.eps_pairs);
+    return MISR_OK;
+}
+
+extern "C" misr_status misr_noalloc_set_wait_limit(uint32_t tries) {
+    g_noalloc_wait_tries.store(tries);
     return MISR_OK;
 }
 

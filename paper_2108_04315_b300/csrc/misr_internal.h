@@ -38,6 +38,10 @@ struct DeviceGuard {
 };
 
 int grid_for(size_t n, int threads);
+// row pitch (elements) of the workspace images of an HR image W pixels wide
+int row_pitch(int W);
+// device bytes misr_plan_create allocates for a descriptor (0 if the descriptor is refused)
+size_t plan_bytes(const misr_desc &d);
 // every check misr_plan_create makes before allocating
 misr_status check_desc(const misr_desc &d);
 // one fused SCG pass (the pass kernel, then its reduction) over the tiles (problem index, tile)

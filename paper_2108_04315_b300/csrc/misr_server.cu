@@ -84,10 +84,12 @@ struct Slot {
     PassSegs segs;
 };
 
+// device bytes of one slot: its plan's workspace (the layout misr_plan_create allocates) plus
+// the slot's own tile and group list
 size_t plan_bytes_estimate(const misr_desc &d) {
-    const size_t H = (size_t)d.factor * d.lr_h, W = (size_t)d.factor * d.lr_w, pitch = (W + 3) & ~size_t(3);
-    const size_t tiles = ((H + 31) / 32) * ((W + 63) / 64);   // groups and blocks are at most this
-    return 7 * ((H * pitch * 4 + 255) / 256 * 256) + tiles * 100 + (size_t)std::max(d.iters, 1) * 80 + (1 << 16);
+    const size_t H = (size_t)d.factor * d.lr_h, W = (size_t)d.factor * d.lr_w;
+    const size_t tiles = ((H + 15) / 16) * ((W + 31) / 32);   // a bound on any shape's tiles
+    return plan_bytes(d) + tiles * sizeof(int2) + (1 << 16);
 }
 
 }  // namespace

@@ -1,6 +1,11 @@
 """The detector workload at full size (4 x 2048^2 frames -> 4096^2 HR) in the launch
 configuration bench.py times (its tile shape tuned first): the forward operator and the
-gradient over the whole image, and a short solve, against the FP64 oracle."""
+gradient over the whole image, a short solve, the full 100-iteration solve against the
+oracle's committed run (tests/golden/detector_100it.json, written by
+tests/golden/make_golden.py from oracle calls alone) and a live 20-iteration solve element by
+element, against the FP64 oracle."""
+import json
+
 import numpy as np
 import pytest
 
@@ -48,6 +53,51 @@ def test_detector_short_solve(detector):
     assert rel_l2(xg, xr) <= RTOL_X
     assert abs(P.objective(xg, y64) - P.objective(xr, y64)) <= RTOL_J * P.objective(xr, y64)
     plan.close()
+
+
+def test_detector_full_length_solve_against_golden(detector):
+    """The number bench.py sells: 100 SCG iterations at 4096^2.  The oracle's run of the same
+    frames is committed; the device's objective trace meets it at 1e-5 and J_final at 1e-5,
+    the accept decisions agree wherever the step changes J by more than 1e-6 J (the FP32
+    noise floor of the prior's sum), and the final image's sum, norm and 256 x 256 block sums
+    meet the oracle's at the image tolerance."""
+    B, P, xt, y, (h, w, f, sh, psf) = detector
+    from tests.golden.make_golden import DETECTOR_ITERS, OUT_DETECTOR, block_sums
+    ref = json.load(open(OUT_DETECTOR))
+    tr = {k: np.asarray(v) for k, v in ref["trace"].items()}
+    plan = B.Plan(h, w, f, sh, psf, lam=0.01, iters=DETECTOR_ITERS)
+    x, st = plan.solve(to_dev(y))
+    tg = plan.trace()
+    xg = x.cpu().numpy().astype(np.float64)
+    plan.close()
+    assert st["iters_done"] == DETECTOR_ITERS == len(tr["E"])
+    assert st["J_final"] == pytest.approx(ref["J_final"], rel=RTOL_J)
+    np.testing.assert_allclose(tg["E"], tr["E"], rtol=RTOL_J)
+    sig = np.abs(tr["E"] - tr["J_trial"]) > 1e-6 * np.abs(tr["E"])
+    assert sig.sum() >= 20
+    assert np.array_equal(tg["accept"][sig], tr["accept"][sig])
+    np.testing.assert_allclose(tg["alpha"][sig], tr["alpha"][sig], rtol=1e-3)
+    assert abs(xg.sum() - ref["x_sum"]) <= RTOL_X * abs(ref["x_sum"])
+    assert abs(np.linalg.norm(xg) - ref["x_norm"]) <= RTOL_X * ref["x_norm"]
+    assert rel_l2(block_sums(xg), np.asarray(ref["block_sums"])) <= RTOL_X
+    # the objective at the device's own image, evaluated by the oracle
+    assert P.objective(xg, y.astype(np.float64)) == pytest.approx(ref["J_final"], rel=RTOL_J)
+
+
+def test_detector_20_iterations_element_by_element(detector):
+    """Twenty iterations (the paper's longest runtime column, Table 4) at 4096^2, the image
+    compared pixel by pixel with a live oracle run."""
+    B, P, xt, y, (h, w, f, sh, psf) = detector
+    iters = 20
+    plan = B.Plan(h, w, f, sh, psf, lam=0.01, iters=iters)
+    x, st = plan.solve(to_dev(y))
+    xg = x.cpu().numpy().astype(np.float64)
+    plan.close()
+    y64 = y.astype(np.float64)
+    xr, _ = P.scg(y64, P.shift_add(y64), iters)
+    assert rel_l2(xg, xr) <= RTOL_X
+    assert np.max(np.abs(xg - xr)) <= 1e-2 * np.max(np.abs(xr))
+    assert st["J_final"] == pytest.approx(P.objective(xr, y64), rel=RTOL_J)
 
 
 @pytest.mark.parametrize("model", ["l1", "paper_ct", "subpixel"])

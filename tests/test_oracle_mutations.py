@@ -33,6 +33,13 @@ MUTANTS = {
     "beta_fletcher_reeves": ("const double beta = (rr_new - rr_cross) / mu;", "const double beta = rr_new / dot(r, r, n);"),
     "lambda_not_reduced": ("if (Delta >= 0.75) lam = lam / 4.0;", "if (Delta >= 0.75) lam = lam / 2.0;"),
     "delta_not_scaled": ("delta += (lam - lam_bar) * pn2;", "delta += 0.0 * (lam - lam_bar) * pn2;"),
+    # Moller's scale increase after a poor step (step 8) and the lambda_bar it works against
+    "lambda_raise_times_4": ("if (Delta < 0.25) lam = lam + delta * (1.0 - Delta) / pn2;",
+                             "if (Delta < 0.25) lam = 4.0 * lam + delta * (1.0 - Delta) / pn2;"),
+    "lambda_raise_sign": ("if (Delta < 0.25) lam = lam + delta * (1.0 - Delta) / pn2;",
+                          "if (Delta < 0.25) lam = lam + delta * (1.0 + Delta) / pn2;"),
+    "lambda_bar_left_at_0": ("lam_bar = lam;\n            success = 0;", "lam_bar = 0.0;\n            success = 0;"),
+    "negative_curvature_branch_always": ("if (delta <= 0) {", "if (delta <= 0 || it >= 0) {"),
     "shift_add_no_average": ("x0[i] = cnt[i] > 0 ? x0[i] / cnt[i] : 0.0;", "x0[i] = x0[i];"),
     "binning_weight_1_over_f": ("const double wd = 1.0 / ((double)nb * nb);", "const double wd = 1.0 / (double)nb;"),
     "binning_block_backwards": ("const int cu = f * i + a2, cv = f * j + b2;   /* pixel of B's output */",

@@ -303,6 +303,65 @@ def test_scg_btv_monotone_and_rejections_consistent(orc):
     assert P.objective(x, y) == pytest.approx(E_next[-1], rel=1e-14)
 
 
+def _rejecting_btv_problem(orc):
+    """A BTV problem whose SCG run rejects several steps, the first one among them."""
+    h = 32
+    P = orc.Problem(h, h, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), lam=0.05, eps=1e-3)
+    xt = gen.phantom(2 * h, 2 * h, 2)
+    y = P.forward_all(xt) + gen.gaussian_noise((4, h, h), 0.01, 102)
+    return P, y
+
+
+def test_scg_scale_increase_after_rejection(orc):
+    """Moller's steps 3, 7 and 8 after a rejected step k: x, p and mu stay, lambda_bar = lambda_k
+    and lambda rises by delta_k (1 - Delta_k) / |p_k|^2, so the next attempt along p_k has the
+    curvature delta_{k+1} = delta_k + (lambda_{k+1} - lambda_bar) |p_k|^2 = delta_k (2 - Delta_k)
+    and the step alpha_{k+1} = alpha_k / (2 - Delta_k): a smaller step after every failure."""
+    P, y = _rejecting_btv_problem(orc)
+    x, tr = P.scg(y, P.shift_add(y), 20)
+    rej = np.where(tr["accept"][:-1] == 0)[0]
+    assert len(rej) >= 3 and rej[0] == 0
+    for k in rej:
+        D = tr["Delta"][k]
+        assert D < 0
+        assert tr["delta"][k + 1] == pytest.approx(tr["delta"][k] * (2.0 - D), rel=1e-12)
+        assert tr["alpha"][k + 1] == pytest.approx(tr["alpha"][k] / (2.0 - D), rel=1e-12)
+        assert tr["mu"][k + 1] == tr["mu"][k] and tr["pn2"][k + 1] == tr["pn2"][k]
+        assert tr["E"][k + 1] == tr["E"][k]
+
+
+def test_scg_fresh_direction_curvature(orc):
+    """Every first attempt along a direction p_k (k = 0, or after an accepted step) uses
+    delta_k = p_k.H(x_k) p_k + lambda_{k-1} |p_k|^2 (step 2, then step 3 with lambda_bar = 0):
+    x_k and p_k are read off the iterates (p_k = (x_{j+1} - x_j) / alpha_j at the first accepted
+    j >= k) and H from the independently pinned curvature.  The negative-curvature branch of
+    step 4 never runs here (it would change delta); it cannot on a convex J with lambda > 0."""
+    P, y = _rejecting_btv_problem(orc)
+    x0 = P.shift_add(y)
+    n = 16
+    _, tr = P.scg(y, x0, n)
+    acc = tr["accept"]
+    iterates = [P.scg(y, x0, k)[0] for k in range(n + 1)]
+    checked = 0
+    for k in range(n):
+        if not (k == 0 or acc[k - 1] == 1):
+            continue
+        later = [j for j in range(k, n) if acc[j] == 1]
+        if not later:
+            continue
+        j = later[0]
+        p = (iterates[j + 1] - iterates[j]) / tr["alpha"][j]
+        if k == 0:
+            np.testing.assert_allclose(p, -P.gradient(x0, y)[1], rtol=0, atol=1e-9 * np.abs(p).max())
+        lam_prev = 1e-6 if k == 0 else tr["lam"][k - 1]
+        want = P.curvature(iterates[k], p) + lam_prev * float(np.sum(p * p))
+        assert tr["delta"][k] == pytest.approx(want, rel=1e-9), k
+        assert tr["pn2"][k] == pytest.approx(float(np.sum(p * p)), rel=1e-9), k
+        assert tr["delta"][k] > 0
+        checked += 1
+    assert checked >= 8
+
+
 def test_scg_fd_mode_matches_exact_curvature(orc):
     """Moller's finite-difference s_k and its sigma -> 0 limit H p give the same run up
     to O(sigma) on a smooth prior."""
