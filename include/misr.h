@@ -110,7 +110,8 @@ enum { MISR_DECIM_POINT = 0, MISR_DECIM_BIN = 1 };
 
 /* Tile shapes of the fused pass (HR pixels per CTA tile; threads per CTA).  The paper has no
  * counterpart: its partitions are whole sub-images per GPU (Sec. 3.1). */
-enum { MISR_TILE_AUTO = 0, MISR_TILE_32x64 = 1, MISR_TILE_32x32 = 2, MISR_TILE_16x64 = 3, MISR_N_TILE_SHAPES = 3 };
+enum { MISR_TILE_AUTO = 0, MISR_TILE_32x64 = 1, MISR_TILE_32x32 = 2, MISR_TILE_16x64 = 3, MISR_TILE_STREAM = 4,
+       MISR_N_TILE_SHAPES = 4 };
 
 /* Solve summary.  J_final, rnorm2 are FP64 reductions computed on the device. */
 typedef struct misr_stats {

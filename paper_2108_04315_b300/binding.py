@@ -17,8 +17,8 @@ LIB_PATH = os.path.join(PKG, "libmisr.so")
 MISR_OK, MISR_EINVAL, MISR_ENOMEM, MISR_ECUDA, MISR_EAGAIN, MISR_ETIMEOUT, MISR_ENOTIMPL, MISR_ECANCELED = range(8)
 MISR_F32, MISR_U16, MISR_BF16 = 0, 1, 2
 MISR_X0_ZERO, MISR_X0_SHIFT_ADD, MISR_X0_GIVEN = 0, 1, 2
-MISR_TILE_AUTO, MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64 = 0, 1, 2, 3
-MISR_N_TILE_SHAPES = 3
+MISR_TILE_AUTO, MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64, MISR_TILE_STREAM = 0, 1, 2, 3, 4
+MISR_N_TILE_SHAPES = 4
 MISR_NORM_L2, MISR_NORM_L1 = 0, 1
 MISR_DECIM_POINT, MISR_DECIM_BIN = 0, 1
 MISR_TRACE_COLS = 10

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -38,16 +39,18 @@ misr_status misr_host::fail(misr_status s, const char *fmt, ...) {
 
 namespace {
 
-// The compiled tile shapes of the fused pass (SHAPE_* in misr_types.cuh), dispatched at run time.
+// The compiled shapes of the fused pass (SHAPE_* in misr_types.cuh), dispatched at run time:
+// the tile shapes (Geo), and the streaming shape (no shared-memory tile).
 template <int S>
-using ShapeGeo = Geo<SHAPE_TH[S], SHAPE_TW[S]>;
+using ShapeGeo = Geo<SHAPE_TH[S < N_TILE_SHAPES ? S : 0], SHAPE_TW[S < N_TILE_SHAPES ? S : 0]>;
 template <typename F>
 auto with_shape(int s, F &&f) {
-    static_assert(N_SHAPES == 3 && MISR_N_TILE_SHAPES == N_SHAPES, "one case per compiled shape");
+    static_assert(N_SHAPES == 4 && MISR_N_TILE_SHAPES == N_SHAPES && STREAM_SHAPE == 3, "one case per compiled shape");
     switch (s) {
     case 0: return f(std::integral_constant<int, 0>());
     case 1: return f(std::integral_constant<int, 1>());
-    default: return f(std::integral_constant<int, 2>());
+    case 2: return f(std::integral_constant<int, 2>());
+    default: return f(std::integral_constant<int, 3>());
     }
 }
 // the shape untuned geometries get (fastest on the B300 at 4096^2 and 768^2 HR)
@@ -260,14 +263,22 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 // per-phase taps), and its dynamic shared memory; the per-phase variants exist for the
 // PHASED_SHAPE only
 template <int S, int V>
-constexpr bool compiled_variant() { return (V & 4) == 0 || S == PHASED_SHAPE; }
+constexpr bool compiled_variant() { return S == STREAM_SHAPE ? V < 2 : (V & 4) == 0 || S == PHASED_SHAPE; }
+// whether a problem of variant v can run on shape sh
+static bool shape_takes_variant(int sh, int v) { return sh == STREAM_SHAPE ? v < 2 : (v & 4) == 0 || sh == PHASED_SHAPE; }
 template <int S, int V>
 constexpr auto pass_kernel() {
     static_assert(compiled_variant<S, V>(), "variant not compiled for this shape");
-    return scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], (V & 1) != 0, (V & 2) != 0, (V & 4) != 0>;
+    if constexpr (S == STREAM_SHAPE)
+        return scg_stream_kernel<(V & 1) != 0>;
+    else
+        return scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], (V & 1) != 0, (V & 2) != 0, (V & 4) != 0>;
 }
 template <int S, int V>
-constexpr size_t pass_smem() { return ShapeGeo<S>::smem_bytes((V & 2) != 0); }
+constexpr size_t pass_smem() {
+    if constexpr (S == STREAM_SHAPE) return SW_SMEM_BYTES;
+    else return ShapeGeo<S>::smem_bytes((V & 2) != 0);
+}
 template <typename F>
 auto with_variant(int v, F &&f) {
     static_assert(N_VARIANTS == 8, "one case per compiled variant");
@@ -289,8 +300,13 @@ static misr_status set_attrs_one() {
         return MISR_OK;
     } else {
         auto *k = pass_kernel<S, V>();
-        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<S, V>()));
-        CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        if constexpr (S == STREAM_SHAPE) {
+            CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<S, V>()));
+            CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        } else {
+            CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<S, V>()));
+            CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        }
         return MISR_OK;
     }
 }
@@ -366,6 +382,10 @@ static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double bet
 // interior tiles).  An entry is (problem, ty << 16 | tx); an HR side of at most 2^20 pixels
 // keeps both tile coordinates below 2^16.
 static void append_tiles(const DevProblem &hp, int pi, std::vector<int2> &tiles) {
+    if (hp.shape == STREAM_SHAPE) {   // item t: strip t % tiles_x, rows (t / tiles_x) tile_h ..
+        for (int t = 0; t < hp.n_tiles; ++t) tiles.push_back(make_int2(pi, t));
+        return;
+    }
     const int tx = hp.tiles_x, TH = hp.tile_h, TW = hp.tile_w;
     for (int pass = 0; pass < 2; ++pass)
         for (int t = 0; t < hp.n_tiles; ++t) {
@@ -375,31 +395,83 @@ static void append_tiles(const DevProblem &hp, int pi, std::vector<int2> &tiles)
         }
 }
 
+StreamConsts misr_host::stream_consts(const DevProblem &p) {
+    StreamConsts k{};
+    for (int i = 0; i < 2 * PSF_R + 1; ++i) { k.hx[i] = p.hx[i]; k.hy[i] = p.hy[i]; }
+    for (int i = 0; i < BTV_W * BTV_W; ++i) {
+        k.gam[i] = p.gamma[i];
+        k.lgam[i] = p.lambda * p.gamma[i];
+    }
+    k.eps2 = p.eps2;
+    k.lambda = p.lambda;
+    k.f = p.f;
+    k.fmag = p.f > 1 ? (unsigned)((0x100000000ull + p.f - 1) / p.f) : 0u;
+    return k;
+}
+
 void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, const std::vector<int> &idx,
                                  std::vector<int2> &tiles, std::vector<int2> &groups, PassSegs &segs) {
     segs = PassSegs{};
     for (int sh = 0; sh < N_SHAPES; ++sh)
-        for (int v = 0; v < N_VARIANTS; ++v)
+        for (int v = 0; v < N_VARIANTS; ++v) {
+            if (sh == STREAM_SHAPE) {
+                // runs of consecutive problems that share the launch constants
+                std::vector<size_t> run;
+                auto flush = [&]() {
+                    if (run.empty()) return;
+                    StreamRun r;
+                    r.variant = v;
+                    r.k = stream_consts(*recs[run[0]]);
+                    for (size_t i : run) {
+                        append_tiles(*recs[i], idx[i], tiles);
+                        r.count += recs[i]->n_tiles;
+                    }
+                    segs.n[sh][v] += r.count;
+                    segs.runs.push_back(r);
+                    run.clear();
+                };
+                for (size_t i = 0; i < recs.size(); ++i) {
+                    if (recs[i]->shape != sh || pass_variant(*recs[i]) != v) continue;
+                    if (!run.empty()) {
+                        const StreamConsts a = stream_consts(*recs[run[0]]), b = stream_consts(*recs[i]);
+                        if (std::memcmp(&a, &b, sizeof(a)) != 0) flush();
+                    }
+                    run.push_back(i);
+                }
+                flush();
+                continue;
+            }
             for (size_t i = 0; i < recs.size(); ++i)
                 if (recs[i]->shape == sh && pass_variant(*recs[i]) == v) {
                     append_tiles(*recs[i], idx[i], tiles);
                     segs.n[sh][v] += recs[i]->n_tiles;
                 }
+        }
     for (size_t i = 0; i < recs.size(); ++i)
         for (int g = 0; g < recs[i]->n_groups; ++g) groups.push_back(make_int2(idx[i], g));
 }
 
-// The process's tuned shapes: HR image size -> the fastest shape misr_autotune measured.
+// The process's tuning: HR image size -> the time per pass misr_autotune measured for each shape
+// (0: not timed, e.g. a shape the tuned descriptor's variant cannot run on).
 std::mutex g_tuned_mu;
-std::vector<std::pair<std::pair<int, int>, int>> g_tuned;
+std::vector<std::pair<std::pair<int, int>, std::array<double, N_SHAPES>>> g_tuned;
 
 // The shape of a plan: the descriptor's, else the tuned one for its HR size, else the default.
-static int pick_shape(const misr_desc &d) {
+static int desc_variant(const misr_desc &d, bool phased) {
+    return (d.iterate_dtype == MISR_BF16 ? 1 : 0) | (d.data_norm == MISR_NORM_L1 ? 2 : 0) | (phased ? 4 : 0);
+}
+static int pick_shape(const misr_desc &d, int variant) {
     if (d.tile_shape >= 1 && d.tile_shape <= N_SHAPES) return d.tile_shape - 1;
     const int H = d.factor * d.lr_h, W = d.factor * d.lr_w;
     std::lock_guard<std::mutex> lock(g_tuned_mu);
     for (auto &e : g_tuned)
-        if (e.first.first == H && e.first.second == W) return e.second;
+        if (e.first.first == H && e.first.second == W) {
+            int best = -1;
+            for (int sh = 0; sh < N_SHAPES; ++sh)
+                if (e.second[sh] > 0 && shape_takes_variant(sh, variant) && (best < 0 || e.second[sh] < e.second[best]))
+                    best = sh;
+            if (best >= 0) return best;
+        }
     return DEFAULT_SHAPE;
 }
 
@@ -410,17 +482,28 @@ static void set_data_norm(DevProblem &hp, const misr_desc &d) {
 }
 
 // Tile grid of a shape; the TMA maps of the workspace images with that shape's boxes.
+static int resident_ctas(int shape, int variant);
+// Rows of a streaming work item: the lowest height (at least 24 rows; its pipeline adds 12)
+// whose items all fit one wave of the GPU's resident warps.
+static int stream_rows(const DevProblem &hp) {
+    const int strips = (hp.W + SW_OWN - 1) / SW_OWN;
+    const long warps = std::max(1L, (long)resident_ctas(STREAM_SHAPE, pass_variant(hp)) * (SW_NT / 32));
+    long rows = std::max(24L, ((long)hp.H * strips + warps - 1) / warps);
+    while (rows < hp.H && (long)((hp.H + rows - 1) / rows) * strips > warps) ++rows;
+    return (int)std::min<long>(rows, 1 << 20);
+}
 static void set_shape(DevProblem &hp, int shape) {
     hp.shape = shape;
-    hp.tile_h = SHAPE_TH[shape];
     hp.tile_w = SHAPE_TW[shape];
+    hp.tile_h = shape == STREAM_SHAPE ? stream_rows(hp) : SHAPE_TH[shape];
     hp.tiles_y = (hp.H + hp.tile_h - 1) / hp.tile_h;
     hp.tiles_x = (hp.W + hp.tile_w - 1) / hp.tile_w;
     hp.n_tiles = hp.tiles_y * hp.tiles_x;
 }
 static misr_status make_maps(DevProblem &hp) {
     int xw = 0, xh = 0, ew = 0, eh = 0;
-    with_shape(hp.shape, [&](auto S) {
+    // (the streaming kernel uses no tensor maps; its problems get those of the 32 x 32 tiles)
+    with_shape(hp.shape == STREAM_SHAPE ? 1 : hp.shape, [&](auto S) {
         using G = ShapeGeo<decltype(S)::value>;
         xw = G::XW; xh = G::XH; ew = G::EW; eh = G::EH;
         return 0;
@@ -471,7 +554,11 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
         }
     hp.eps_pairs = d.eps * eps_pairs;
     hp.rp_bf16 = d.iterate_dtype == MISR_BF16;
-    set_shape(hp, hp.phased ? PHASED_SHAPE : shape >= 0 ? shape : pick_shape(d));
+    const int variant = desc_variant(d, hp.phased);
+    const int sh = hp.phased ? PHASED_SHAPE : shape >= 0 ? shape : pick_shape(d, variant);
+    if (!shape_takes_variant(sh, variant))
+        return fail(MISR_ENOTIMPL, "the streaming pass runs the squared L2 data term with integer shifts only");
+    set_shape(hp, sh);
     set_groups(hp);
     return MISR_OK;
 }
@@ -533,12 +620,27 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
         for (int v = 0; v < N_VARIANTS; ++v) {
             const int n = segs.n[sh][v];
             if (n <= 0) continue;
+            if (sh == STREAM_SHAPE) {   // one launch per run of shared constants
+                for (const StreamRun &run : segs.runs) {
+                    if (run.variant != v) continue;
+                    const int2 *t = tiles + off;
+                    off += run.count;
+                    const int grid = pass_grid(sh, v, (run.count + 7) / 8);
+                    if (v == 0)
+                        CK(launch_pdl(scg_stream_kernel<false>, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.count, work,
+                                      mode, alpha, beta, run.k));
+                    else
+                        CK(launch_pdl(scg_stream_kernel<true>, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.count, work,
+                                      mode, alpha, beta, run.k));
+                }
+                continue;
+            }
             const int2 *t = tiles + off;
             off += n;
             CK(with_shape(sh, [&](auto S) {
                 return with_variant(v, [&](auto V) {
                     constexpr int k = decltype(S)::value, vv = decltype(V)::value;
-                    if constexpr (!compiled_variant<k, vv>()) {
+                    if constexpr (!compiled_variant<k, vv>() || k == STREAM_SHAPE) {
                         return cudaErrorInvalidValue;   // plans with per-phase taps take the PHASED_SHAPE
                     } else {
                         return launch_pdl(pass_kernel<k, vv>(), pass_grid(k, vv, n), SHAPE_NT[k], pass_smem<k, vv>(), s,
@@ -580,9 +682,11 @@ extern "C" {
 
 const char *misr_version(void) {
 #ifdef MISR_BOUNDS_CHECK
-    return "misr-b300 0.3 (sm_103a, persistent TMA-fed fused SCG pass; tiles 32x64, 32x32, 16x64; bounds-checked)";
+    return "misr-b300 0.4 (sm_103a, fused SCG pass: row-streaming warps, or persistent TMA-fed tiles 32x64, 32x32, "
+           "16x64; bounds-checked)";
 #else
-    return "misr-b300 0.3 (sm_103a, persistent TMA-fed fused SCG pass; tiles 32x64, 32x32, 16x64)";
+    return "misr-b300 0.4 (sm_103a, fused SCG pass: row-streaming warps, or persistent TMA-fed tiles 32x64, 32x32, "
+           "16x64)";
 #endif
 }
 
@@ -1318,14 +1422,16 @@ extern "C" misr_status misr_autotune(const misr_desc *desc, int32_t passes, int3
     }
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double ms[N_SHAPES];
+    double ms[N_SHAPES] = {};
     int best = DEFAULT_SHAPE;
+    const int variant = desc_variant(*desc, false);
     do {
         if ((e = cudaMemset(y, 0, in_bytes)) != cudaSuccess) break;
         if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaEventCreate(&e0)) != cudaSuccess) break;
         if ((e = cudaEventCreate(&e1)) != cudaSuccess) break;
         for (int sh = 0; sh < N_SHAPES && st == MISR_OK; ++sh) {
+            if (!shape_takes_variant(sh, variant)) continue;   // not compiled for this variant
             misr_desc d = *desc;
             d.tile_shape = sh + 1;
             d.iters = 1;
@@ -1347,7 +1453,7 @@ extern "C" misr_status misr_autotune(const misr_desc *desc, int32_t passes, int3
         }
         if (st != MISR_OK) break;
         for (int sh = 0; sh < N_SHAPES; ++sh)
-            if (ms[sh] < ms[best]) best = sh;
+            if (ms[sh] > 0 && ms[sh] < ms[best]) best = sh;
     } while (0);
     if (e1) cudaEventDestroy(e1);
     if (e0) cudaEventDestroy(e0);
@@ -1357,11 +1463,17 @@ extern "C" misr_status misr_autotune(const misr_desc *desc, int32_t passes, int3
     if (e != cudaSuccess) return fail(MISR_ECUDA, "autotune: %s", cudaGetErrorString(e));
     {
         const int H = desc->factor * desc->lr_h, W = desc->factor * desc->lr_w;
+        std::array<double, N_SHAPES> t{};
+        for (int sh = 0; sh < N_SHAPES; ++sh) t[sh] = ms[sh];
         std::lock_guard<std::mutex> lock(g_tuned_mu);
         bool found = false;
         for (auto &en : g_tuned)
-            if (en.first.first == H && en.first.second == W) { en.second = best; found = true; }
-        if (!found) g_tuned.push_back({{H, W}, best});
+            if (en.first.first == H && en.first.second == W) {
+                for (int sh = 0; sh < N_SHAPES; ++sh)
+                    if (t[sh] > 0) en.second[sh] = t[sh];
+                found = true;
+            }
+        if (!found) g_tuned.push_back({{H, W}, t});
     }
     if (shape_out) *shape_out = best + 1;
     if (ms_out)

@@ -1694,3 +1694,5 @@ __global__ void scale_copy_kernel(const T *__restrict__ src, int pitch, float si
 }
 
 }  // namespace misr
+
+#include "misr_stream.cuh"

@@ -53,8 +53,15 @@ misr_status check_desc(const misr_desc &d);
 // (shape 0, variant 1), ..., (shape 1, variant 0), ... in that order, n[shape][variant] tiles
 // each (variant: bit 0 bf16 r and p, bit 1 the L1 data term, bit 2 per-phase taps, which only
 // the PHASED_SHAPE has); one pass launch per non-empty segment.
+// The streaming shape's tiles are further split into runs of problems that share their
+// constants (kernel parameters of one launch): one launch per run, in list order.
+struct StreamRun {
+    int variant = 0, count = 0;
+    misr::StreamConsts k{};
+};
 struct PassSegs {
     int n[misr::N_SHAPES][misr::N_VARIANTS] = {};
+    std::vector<StreamRun> runs;
     int total() const {
         int t = 0;
         for (auto &a : n)
@@ -62,6 +69,8 @@ struct PassSegs {
         return t;
     }
 };
+// the constants of the streaming pass for a problem
+misr::StreamConsts stream_consts(const misr::DevProblem &p);
 // the pass kernel variant of a problem
 inline int pass_variant(const misr::DevProblem &p) { return (p.rp_bf16 ? 1 : 0) | (p.l1 ? 2 : 0) | (p.phased ? 4 : 0); }
 misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, const PassSegs &segs,

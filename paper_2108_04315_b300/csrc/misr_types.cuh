@@ -34,15 +34,21 @@ constexpr int NPART = 10;
 constexpr int TRACE_COLS = 10;
 constexpr uint32_t TMA_WAIT_TRIES = 1u << 24;   // bounded wait for the tile loads
 
-// Tile shapes of the fused pass: TH x TW HR pixels per tile, NT threads per CTA (1024 / NT
-// CTAs resident per SM).  The autotuner picks one per HR image size.
-constexpr int N_SHAPES = 3;
-constexpr int SHAPE_TH[N_SHAPES] = {32, 32, 16};
-constexpr int SHAPE_TW[N_SHAPES] = {64, 32, 64};
-constexpr int SHAPE_NT[N_SHAPES] = {512, 256, 256};
+// Shapes of the fused pass.  Tile shapes 0..2: TH x TW HR pixels per tile, NT threads per CTA
+// (1024 / NT CTAs resident per SM).  STREAM_SHAPE: the row-streaming kernel, whose work item is
+// a strip of SHAPE_TW = 112 columns by a height chosen per plan (SHAPE_TH 0: at run time), one
+// warp each, NT = 256 threads (8 independent warps) per CTA.  The autotuner picks one per HR
+// image size.
+constexpr int N_SHAPES = 4;
+constexpr int N_TILE_SHAPES = 3;
+constexpr int STREAM_SHAPE = 3;
+constexpr int SHAPE_TH[N_SHAPES] = {32, 32, 16, 0};
+constexpr int SHAPE_TW[N_SHAPES] = {64, 32, 64, 112};
+constexpr int SHAPE_NT[N_SHAPES] = {512, 256, 256, 256};
 // Compiled variants of the fused pass per shape: bit 0 r and p stored as bf16, bit 1 the
 // smoothed L1 data term, bit 2 per-phase blur taps (non-integer shifts; compiled for the
-// 32x32 shape only).
+// 32x32 shape only).  The streaming shape has variants 0 and 1 (squared L2 data term, shared
+// taps).
 constexpr int N_VARIANTS = 8;
 constexpr int PHASED_SHAPE = 1;
 // per-phase tap tables of DevProblem::tph: full y taps, y taps of the bilinear's first part
@@ -106,6 +112,18 @@ struct DevProblem {
     // (8 floats per phase so that a phase's taps start on a 16-byte boundary)
     float ay[MAXF], ax[MAXF];
     float tph[N_TPH][MAXF][8];
+};
+
+// Per-launch constants of the streaming pass (every problem of one launch shares them; the
+// host splits launches where they differ).  They are kernel parameters, so the arithmetic
+// reads them from the constant bank instead of holding them in registers.
+struct StreamConsts {
+    float hx[2 * PSF_R + 1], hy[2 * PSF_R + 1];   // forward taps, tap b at [b + R]
+    float gam[BTV_W * BTV_W];                     // gamma(dx, dy) at [dy * 3 + dx]
+    float lgam[BTV_W * BTV_W];                    // lambda gamma: the psi'' weight of a pair
+    float eps2, lambda;
+    int f;
+    unsigned fmag;                                // ceil(2^32 / f) (0 for f = 1), for c mod f
 };
 
 }  // namespace misr

