@@ -286,75 +286,93 @@ def measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak):
                         "(the written lines are evicted, and written back, before the call)" % reps}
 
 
-def cpu_baseline(wl):
-    """The FP64 oracle on the host cores: initial gradient plus 2 SCG iterations at full size,
-    extrapolated to the workload's iteration count."""
+ORACLE_SAMPLE_ITERS = 3
+
+
+def oracle_timing(h, w, f, seed, iters):
+    """Seconds of the FP64 oracle for one problem of h x w LR frames: (init, per SCG iteration).
+    init = shift-and-add plus the initial gradient; the iteration time is (T(init + iters SCG
+    iterations) - T(init)) / iters, so that the first iteration's extra work is averaged in."""
     from oracle import oracle
-    P = oracle.Problem(wl["h"], wl["w"], wl["f"], gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), lam=0.01)
-    xt = gen.phantom(P.H, P.W, wl["seed"])
-    y = P.forward_all(xt) + gen.gaussian_noise((4, wl["h"], wl["w"]), 0.01, wl["seed"] + 1)
+    P = oracle.Problem(h, w, f, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), lam=0.01)
+    xt = gen.phantom(P.H, P.W, seed)
+    y = P.forward_all(xt) + gen.gaussian_noise((4, h, w), 0.01, seed + 1)
+    del xt
     t = time.perf_counter()
-    x0 = P.shift_add(y)
-    P.scg(y, x0, 0)
+    P.scg(y, P.shift_add(y), 0)
     t0 = time.perf_counter() - t
     t = time.perf_counter()
-    x0 = P.shift_add(y)
-    P.scg(y, x0, 2)
-    t2 = time.perf_counter() - t
-    t_iter = max((t2 - t0) / 2.0, 1e-9)
+    P.scg(y, P.shift_add(y), iters)
+    tk = time.perf_counter() - t
+    return t0, max((tk - t0) / iters, 1e-9), oracle.threads()
+
+
+def _one_core_timing(h, w, f, seed, iters):
+    """oracle_timing in a child process whose OpenMP runtime has one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_timing(%d, %d, %d, %d, %d)))" % (ROOT, h, w, f, seed, iters))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle on the host cores at the workload's full size (init + 3 SCG iterations,
+    extrapolated to the workload's iteration count), and on one core for a 1/16 crop of it
+    (h/4 x w/4 LR frames, same recipe), scaled to full size by the HR pixel count (the oracle's
+    work per iteration is linear in the pixels)."""
+    t0, t_iter, cores = oracle_timing(wl["h"], wl["w"], wl["f"], wl["seed"], ORACLE_SAMPLE_ITERS)
     per_proj = t0 + wl["iters"] * t_iter
-    return {"value": 1.0 / per_proj, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"FP64 oracle, full-size problem: init {t0:.2f} s + 2 SCG iterations "
-                      f"({t_iter:.2f} s each), extrapolated to {wl['iters']} iterations"}
+    out = {"value": 1.0 / per_proj, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"FP64 oracle, full-size problem: init {t0:.2f} s, then {ORACLE_SAMPLE_ITERS} SCG iterations "
+                     f"at {t_iter:.2f} s each; projections/s = 1 / (init + {wl['iters']} iterations)"}
+    h1, w1 = wl["h"] // 4, wl["w"] // 4
+    one = _one_core_timing(h1, w1, wl["f"], wl["seed"], ORACLE_SAMPLE_ITERS)
+    if one is not None:
+        scale = (wl["h"] * wl["w"]) / (h1 * w1)
+        per1 = scale * (one[0] + wl["iters"] * one[1])
+        out["one_core"] = {"value": 1.0 / per1, "unit": UNIT, "cores": one[2],
+                           "sample": f"{h1}x{w1} LR crop on one thread: init {one[0]:.2f} s, SCG iteration "
+                                     f"{one[1]:.2f} s, x{scale:.0f} to full size"}
+    return out
 
 
 def run_reference(args, wl):
-    """Reference arm: the FP64 oracle as it stands, on the host cores."""
-    from oracle import oracle
-    P = oracle.Problem(wl["h"], wl["w"], wl["f"], gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), lam=0.01)
-    xt = gen.phantom(P.H, P.W, wl["seed"])
-    y = P.forward_all(xt) + gen.gaussian_noise((4, wl["h"], wl["w"]), 0.01, wl["seed"] + 1)
-    x0 = P.shift_add(y)
-
-    def init_time():
-        t = time.perf_counter()
-        P.scg(y, P.shift_add(y), 0)
-        return time.perf_counter() - t
-
-    def step_time():
-        t = time.perf_counter()
-        P.scg(y, P.shift_add(y), 1)
-        return time.perf_counter() - t
-
-    for _ in range(max(0, min(args.warmup, 1))):
-        step_time()
-    t_init = init_time()
-    steps = [step_time() for _ in range(args.steps)]
-    t_iter = max(statistics.median(steps) - t_init, 1e-9)
-    per_proj = t_init + wl["iters"] * t_iter
+    """Reference arm: the FP64 oracle as it stands, on the host cores, with cpu_baseline's
+    estimator.  Every step is one full-size sample (init + 3 SCG iterations); the line reports
+    the median step's rate."""
+    warm = max(0, min(args.warmup, 1))
+    for _ in range(warm):
+        oracle_timing(wl["h"], wl["w"], wl["f"], wl["seed"], 1)
+    samples = [oracle_timing(wl["h"], wl["w"], wl["f"], wl["seed"], ORACLE_SAMPLE_ITERS) for _ in range(args.steps)]
+    per = sorted(t0 + wl["iters"] * ti for t0, ti, _ in samples)
+    per_proj = statistics.median(per)
+    cores = samples[0][2] if samples else 0
     value = 1.0 / per_proj
-    sample = (f"FP64 oracle, full-size problem; each step = init + 1 SCG iteration "
-              f"(median {statistics.median(steps):.2f} s, init {t_init:.2f} s), extrapolated to {wl['iters']} iterations")
-    del x0
+    sample = (f"FP64 oracle, full-size problem; each step = init + {ORACLE_SAMPLE_ITERS} SCG iterations, "
+              f"extrapolated to {wl['iters']} iterations (median of {len(per)} steps; "
+              f"range {per[0]:.1f}-{per[-1]:.1f} s per projection)")
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": per_proj * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": warm, "ms_per_step": per_proj * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": wl["desc"], "lr": [wl["h"], wl["w"]], "K": 4, "factor": wl["f"], "iters": wl["iters"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
-def run_batch(args):
-    """64 projections of uneven sizes (LR sides U{512..2048}; half f=2/K=4, half f=3/K=9), 60 SCG
-    iterations each: one batched solve (one fused-pass launch per step over all projections) vs
-    the same projections solved one after another with misr_solve, on the same GPU."""
+def batch_uneven_record(n, iters, steps, warmup):
+    """The batch form on uneven projections: the first n of 64 seeded ROIs (LR sides
+    U{512..2048}; alternately f=2/K=4 and f=3/K=9), `iters` SCG iterations each.  One batched
+    solve (one fused-pass launch per SCG step over all n projections) against the same
+    projections solved one after another with misr_solve, on the same GPU and stream."""
     import torch
     from paper_2108_04315_b300.binding import Batch, Plan
-    device = torch.device("cuda", 0)
-    rois = gen.batch_rois(gen.CONFIG_SEEDS["batch"], n=args.batch_n)
-    iters = 60
+    device = torch.device("cuda", torch.cuda.current_device())
+    rois = gen.batch_rois(gen.CONFIG_SEEDS["batch"], n=64)[:n]
     big = torch.from_numpy(gen.phantom(6144, 6144, gen.CONFIG_SEEDS["batch"]).astype(np.float32)).to(device)
     g = torch.Generator(device=device)
     g.manual_seed(gen.CONFIG_SEEDS["batch"])
@@ -369,53 +387,64 @@ def run_batch(args):
         y += 0.01 * torch.randn(y.shape, generator=g, device=device)
         plans.append(p)
         ys.append(y)
+    del big
     xs = [torch.empty((p.H, p.W), dtype=torch.float32, device=device) for p in plans]
     batch = Batch(plans)
     stream = torch.cuda.current_stream()
-    for _ in range(max(1, min(args.warmup, 2))):
+    for _ in range(max(1, warmup)):
         batch.solve(ys, xs, stats=False)
         for p, y, x in zip(plans, ys, xs):
             p.solve(y, x, stats=False)
     torch.cuda.synchronize()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    e0.record(stream)
-    for _ in range(args.steps):
-        batch.solve(ys, xs, stats=False)
-    e1.record(stream)
-    for _ in range(args.steps):
-        for p, y, x in zip(plans, ys, xs):
-            p.solve(y, x, stats=False)
-    e2.record(stream)
-    e2.synchronize()
+    with ClockSampler(device.index) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            batch.solve(ys, xs, stats=False)
+        e1.record(stream)
+        for _ in range(steps):
+            for p, y, x in zip(plans, ys, xs):
+                p.solve(y, x, stats=False)
+        e2.record(stream)
+        e2.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3
     t_plain = e1.elapsed_time(e2) / 1e3
-    n = len(plans)
     px = sum(p.H * p.W for p in plans)
-    out = {"metric": "SR projections/s (64 uneven projections, 60 SCG it, batched)", "value": n * args.steps / t_batch,
-           "unit": "projections/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True, "dtype": "f32",
-           "data": "synthetic", "impl": "misr-batch",
-           "config": {"workload": "64 projections, LR sides U{512..2048}, 32 x (f=2, K=4) + 32 x (f=3, K=9), "
-                                  "60 SCG iterations", "hr_pixels_total": px, "projections": n},
-           "plain": {"value": n * args.steps / t_plain, "unit": "projections/s",
-                     "ms_per_step": t_plain / args.steps * 1e3},
-           "batched_over_plain": t_plain / t_batch,
-           "hr_pixels_per_s": px * args.steps / t_batch}
-    print(json.dumps(out), flush=True)
+    n_f3 = sum(1 for r in rois if r["f"] == 3)
+    out = {"value": n * steps / t_batch, "unit": UNIT, "steps": steps, "warmup": max(1, warmup),
+           "ms_per_step": t_batch / steps * 1e3, "api": "misr_batch_solve",
+           "config": {"workload": f"{n} projections, LR sides U{{512..2048}}, {n - n_f3} x (f=2, K=4) + "
+                                  f"{n_f3} x (f=3, K=9), {iters} SCG iterations",
+                      "hr_pixels_total": px, "projections": n, "iters": iters},
+           "plain": {"value": n * steps / t_plain, "unit": UNIT, "ms_per_step": t_plain / steps * 1e3,
+                     "api": "misr_solve, one projection after another"},
+           "over_plain": t_plain / t_batch,
+           "hr_pixels_per_s": px * steps / t_batch,
+           "clocks": clk.summary()}
     batch.close()
     for p in plans:
         p.close()
+    return out
 
 
-def run_precision(args):
-    """The precision form at full size: 4 x 3072^2 uint16 counts (Poisson, I0 40000) of a
-    seeded phantom, log-converted on the device, 6144^2 HR, 100 SCG iterations; r and p stored
-    in bf16 with the float master x, against the all-float solve on the same GPU."""
+def run_batch(args):
+    """`--workload batch`: the 64-projection uneven batch at 60 SCG iterations."""
+    import torch
+    torch.cuda.set_device(0)
+    rec = batch_uneven_record(args.batch_n, 60, args.steps, min(args.warmup, 2))
+    out = {"metric": "SR projections/s (64 uneven projections, 60 SCG it, batched)", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic", "impl": "misr-batch", **rec}
+    print(json.dumps(out), flush=True)
+
+
+def precision_record(h, steps, warmup):
+    """The precision form: 4 x h^2 uint16 counts (Poisson, I0 40000) of a seeded phantom,
+    log-converted on the device, (2h)^2 HR, 100 SCG iterations; r and p stored in bf16 with the
+    float master x, against the all-float solve of the same counts on the same GPU."""
     import torch
     from paper_2108_04315_b300.binding import MISR_BF16, MISR_F32, MISR_U16, Plan
-    device = torch.device("cuda", 0)
-    torch.cuda.set_device(device)
-    h = w = 3072
+    device = torch.device("cuda", torch.cuda.current_device())
+    w = h
     f, iters, seed = 2, 100, gen.CONFIG_SEEDS["precision"]
     sh, psf = gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)
     plans = {name: Plan(h, w, f, sh, psf, lam=0.01, iters=iters, in_dtype=MISR_U16, flat_field=FLAT_FIELD,
@@ -426,40 +455,51 @@ def run_precision(args):
     g.manual_seed(seed)
     c = torch.poisson(FLAT_FIELD * torch.exp(-m), generator=g).clamp_(1, 65535).to(torch.int32)
     y = torch.where(c > 32767, c - 65536, c).to(torch.int16).contiguous()
+    del c, m, xt
     xs = {k: torch.empty((f * h, f * w), dtype=torch.float32, device=device) for k in plans}
     stream = torch.cuda.current_stream()
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         for k, p in plans.items():
             p.solve(y, xs[k], stats=False)
     torch.cuda.synchronize()
     res = {}
-    with ClockSampler(0) as clk:
+    with ClockSampler(device.index) as clk:
         for k, p in plans.items():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 p.solve(y, xs[k], stats=False)
             e1.record(stream)
             e1.synchronize()
-            res[k] = e0.elapsed_time(e1) / args.steps
+            res[k] = e0.elapsed_time(e1) / steps
     st = {k: p.solve(y, xs[k])[1] for k, p in plans.items()}
     diff = float(torch.linalg.vector_norm(xs["bf16"] - xs["f32"]) / torch.linalg.vector_norm(xs["f32"]))
-    out = {"metric": "SR projections/s (3072^2 u16 -> 6144^2, 100 SCG it, bf16 r and p)", "value": 1e3 / res["bf16"],
-           "unit": "projections/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
-           "ms_per_step": res["bf16"], "higher_is_better": True, "dtype": "f32 (x) + bf16 (r, p)",
-           "data": "synthetic", "impl": "misr-precision",
-           "config": {"workload": "4 x 3072^2 u16 counts (Poisson, I0 40000) -> 6144^2 HR, f=2, half-pixel shifts, "
-                                  "lambda 0.01, 100 SCG iterations", "hr_pixels": f * h * f * w},
-           "f32": {"value": 1e3 / res["f32"], "unit": "projections/s", "ms_per_step": res["f32"],
-                   "workspace_bytes": plans["f32"].workspace_bytes()},
-           "bf16_workspace_bytes": plans["bf16"].workspace_bytes(),
-           "bf16_vs_f32_image_rel_l2": diff,
-           "J_final": {k: v["J_final"] for k, v in st.items()},
+    out = {"value": 1e3 / res["bf16"], "unit": UNIT, "steps": steps, "warmup": max(warmup, 3),
+           "ms_per_step": res["bf16"], "dtype": "f32 (x) + bf16 (r, p); u16 frames",
+           "config": {"workload": f"4 x {h}^2 u16 counts (Poisson, I0 40000) -> {f * h}^2 HR, f=2, half-pixel "
+                                  "shifts, lambda 0.01, 100 SCG iterations", "hr_pixels": f * h * f * w},
+           "plain": {"value": 1e3 / res["f32"], "unit": UNIT, "ms_per_step": res["f32"],
+                     "dtype": "f32 (x, r, p); u16 frames", "workspace_bytes": plans["f32"].workspace_bytes()},
+           "over_plain": res["f32"] / res["bf16"],
+           "workspace_bytes": plans["bf16"].workspace_bytes(),
+           "workspace_over_plain": plans["bf16"].workspace_bytes() / plans["f32"].workspace_bytes(),
+           "image_rel_l2_vs_plain": diff,
+           "J_final_rel_vs_plain": abs(st["bf16"]["J_final"] - st["f32"]["J_final"]) / st["f32"]["J_final"],
            "accepted": {k: v["accepted"] for k, v in st.items()},
            "clocks": clk.summary()}
-    print(json.dumps(out), flush=True)
     for p in plans.values():
         p.close()
+    return out
+
+
+def run_precision(args):
+    """`--workload precision`: the 3072^2 u16 workload at full length."""
+    import torch
+    torch.cuda.set_device(0)
+    rec = precision_record(3072, args.steps, args.warmup)
+    out = {"metric": "SR projections/s (3072^2 u16 -> 6144^2, 100 SCG it, bf16 r and p)", "n_gpus": 1,
+           "higher_is_better": True, "data": "synthetic", "impl": "misr-precision", **rec}
+    print(json.dumps(out), flush=True)
 
 
 SERVE_SCANS = {
@@ -500,21 +540,19 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v), q)) * 1e3 if v else None
 
 
-def run_serving(args):
+def serving_record(n, slots, tick):
     """Simulated CT acquisition (the served form): a projection every 1/30 s, scan A and scan B
     alternating, 80 SCG iterations each from uint16 counts.  Served = misr_submit at arrival
     (continuous batching on the device); plain = one misr_solve at a time in arrival order.
     Then an open-loop overload run (all requests at once) for the peak served rate."""
     import torch
     from paper_2108_04315_b300.binding import MISR_U16, Server
-    device = torch.device("cuda", 0)
-    torch.cuda.set_device(device)
-    n = args.serve_n
+    device = torch.device("cuda", torch.cuda.current_device())
     scans = _serving_inputs(device, n_pool=4)
     names = ["A" if i % 2 == 0 else "B" for i in range(n)]
     xs = [torch.empty((scans[k]["plan"].H, scans[k]["plan"].W), dtype=torch.float32, device=device) for k in names]
     ys = [scans[k]["pool"][(i // 2) % len(scans[k]["pool"])] for i, k in enumerate(names)]
-    srv = Server(max_slots=args.serve_slots, passes_per_tick=args.serve_tick)
+    srv = Server(max_slots=slots, passes_per_tick=tick)
 
     def submit(i):
         sc = scans[names[i]]
@@ -527,7 +565,7 @@ def run_serving(args):
         scans[names[i]]["plan"].solve(ys[i], xs[i], stats=False)
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(device.index)
     with clocks:
         # 1. served, paced arrivals
         t0 = time.monotonic() + 0.05
@@ -575,23 +613,35 @@ def run_serving(args):
         peak_plain = n / (e0.elapsed_time(e1) / 1e3)
     counters = srv.counters()
     srv.close()
-    out = {"metric": "served SR projections/s (CT acquisition at 30/s, scans A/B alternating, 80 SCG it)",
-           "value": served_rate, "unit": "projections/s", "n_gpus": 1, "steps": n, "warmup": min(4, n),
-           "higher_is_better": True, "dtype": "f32", "data": "synthetic", "impl": "misr-serve",
+    out = {"value": served_rate, "unit": UNIT, "steps": n, "warmup": min(4, n),
            "config": {"workload": "scan A: 4 x 1536x1920 u16 counts, f=2, half-pixel shifts; scan B: 9 x 768x960 u16 "
                                   "counts, f=3, third-pixel shifts; I0 40000, lambda 0.01, 80 SCG iterations; one "
                                   f"projection every {1 / SERVE_RATE:.4f} s alternating A/B; {n} projections",
-                      "max_slots": args.serve_slots, "passes_per_tick": args.serve_tick,
+                      "max_slots": slots, "passes_per_tick": tick,
                       "inputs": "resident in HBM (frames > L2 per projection)"},
+           "api": "misr_submit at arrival, misr_wait",
            "latency_ms": {"served_p50": _pct(lat_srv, 50), "served_p99": _pct(lat_srv, 99),
                           "plain_p50": _pct(lat_plain, 50), "plain_p99": _pct(lat_plain, 99)},
-           "plain": {"value": plain_rate, "unit": "projections/s"},
+           "plain": {"value": plain_rate, "unit": UNIT, "api": "misr_solve at arrival, one at a time",
+                     "latency_p50_ms": _pct(lat_plain, 50), "latency_p99_ms": _pct(lat_plain, 99)},
+           "p50_over_plain": _pct(lat_plain, 50) / _pct(lat_srv, 50),
+           "p99_over_plain": _pct(lat_plain, 99) / _pct(lat_srv, 99),
            "overload": {"served": peak_served, "plain": peak_plain, "served_over_plain": peak_served / peak_plain,
-                        "unit": "projections/s"},
+                        "unit": UNIT},
            "server_counters": counters, "clocks": clocks.summary()}
-    print(json.dumps(out), flush=True)
     for sc in scans.values():
         sc["plan"].close()
+    return out
+
+
+def run_serving(args):
+    """`--workload serving`: the paced acquisition with --serve-n projections."""
+    import torch
+    torch.cuda.set_device(0)
+    rec = serving_record(args.serve_n, args.serve_slots, args.serve_tick)
+    out = {"metric": "served SR projections/s (CT acquisition at 30/s, scans A/B alternating, 80 SCG it)",
+           "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic", "impl": "misr-serve", **rec}
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -602,6 +652,8 @@ def main():
     ap.add_argument("--impl", default="misr", choices=["misr", "reference"])
     ap.add_argument("--workload", default="detector", choices=sorted(WORKLOADS) + ["batch", "serving", "precision"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the serving, precision and uneven-batch records of the default run")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--serve-n", type=int, default=240)
     ap.add_argument("--serve-slots", type=int, default=32)
@@ -748,6 +800,14 @@ def main():
     paper_ct = measure_paper_ct(args, wl, shifts, tuned_tile, xt, stream, dist, device, peak)
     subpixel = measure_subpixel(args, wl, xt, stream, dist, device, peak)
     interp = measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak)
+    # the three forms beside their plain counterparts, at sizes that keep the default run
+    # within minutes: the paced acquisition (60 projections), the 3072^2 u16 precision
+    # workload (3 solves per arm) and 16 of the 64 uneven projections (2 batched steps)
+    forms = None
+    if world == 1 and not args.no_forms and args.workload == "detector":
+        forms = {"serving": serving_record(60, args.serve_slots, args.serve_tick),
+                 "precision": precision_record(3072, 3, 3),
+                 "batch_uneven": batch_uneven_record(16, 60, 2, 1)}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -772,6 +832,7 @@ def main():
         "paper_ct_setting": paper_ct,
         "subpixel": subpixel,
         "interpolation": interp,
+        "forms": forms,
         # per solve: prepare, the initial pass and every SCG pass (the fused pass kernel and its
         # reduction kernel), finalize
         "gpu_launches": args.steps * (2 * wl["iters"] + 4),

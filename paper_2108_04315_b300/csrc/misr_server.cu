@@ -40,6 +40,20 @@ double now_s() {
 struct DescCopy {
     misr_desc d{};
     std::vector<float> shifts, psf;
+    DescCopy() = default;
+    // a copy points its descriptor at its own shift and PSF vectors
+    DescCopy(const DescCopy &o) : d(o.d), shifts(o.shifts), psf(o.psf) { repoint(); }
+    DescCopy &operator=(const DescCopy &o) {
+        d = o.d;
+        shifts = o.shifts;
+        psf = o.psf;
+        repoint();
+        return *this;
+    }
+    void repoint() {
+        d.shifts = shifts.empty() ? nullptr : shifts.data();
+        d.psf = psf.empty() ? nullptr : psf.data();
+    }
     void set(const misr_desc &src) {
         d = src;
         shifts.assign(src.shifts, src.shifts + 2 * src.K);
@@ -147,90 +161,122 @@ bool can_create(misr_server_t s, const misr_desc &d) {
     return free_b > need + s->cfg.hbm_reserve_bytes;
 }
 
-// Free one idle slot of another class (when memory or the slot count blocks a request).
+// Free one idle slot of another class (when memory or the slot count blocks a request).  The
+// slot is emptied under the server lock (misr_server_counters reads the table); its plan is
+// destroyed after the lock is released.
 bool evict_idle(misr_server_t s, const DescCopy &want) {
     for (size_t i = 0; i < s->slots.size(); ++i) {
         Slot &sl = s->slots[i];
         if (!sl.busy && sl.plan && !sl.desc.same_class(want)) {
             cudaStreamSynchronize(s->stream);
-            s->slot_bytes -= plan_bytes_estimate(sl.desc.d);
-            misr_plan_destroy(sl.plan);
-            cudaFree(sl.items);
-            sl.plan = nullptr;
-            sl.items = nullptr;
-            // keep the slot index (records are per index); mark it empty
+            misr_plan_t p = sl.plan;
+            int2 *items = sl.items;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                s->slot_bytes -= plan_bytes_estimate(sl.desc.d);
+                sl.plan = nullptr;   // the index stays (records are per index), empty
+                sl.items = nullptr;
+            }
+            misr_plan_destroy(p);
+            cudaFree(items);
             return true;
         }
     }
     return false;
 }
 
-// Assign queued requests to slots; returns the slots admitted this tick.
+// Make a slot of `d`'s class (creating its plan and its own tile and group lists), freeing
+// idle slots of other classes when memory or the slot count is short.  Worker thread only.
+// The plan and the lists are made without the server lock, so that submit and poll are not
+// held up by the allocations and copies; the slot is entered in the table under the lock.
+// Returns the slot index, -1 when no room can be made now, or -2 with *status set when the
+// descriptor cannot be served at all.
+int make_slot(misr_server_t s, const DescCopy &want, misr_status *status) {
+    const misr_desc &d = want.d;
+    bool ok = can_create(s, d);
+    while (!ok && evict_idle(s, want)) ok = can_create(s, d);
+    if (!ok) return -1;
+    int idx = -1;   // reuse an empty index first
+    for (size_t i = 0; i < s->slots.size(); ++i)
+        if (!s->slots[i].plan) { idx = (int)i; break; }
+    const bool grow = idx < 0;
+    if (grow) {
+        if ((int)s->slots.size() >= s->cfg.max_slots) return -1;
+        idx = (int)s->slots.size();
+    }
+    misr_plan_t p = nullptr;
+    const misr_status pc = misr_plan_create(&d, &p);
+    if (pc != MISR_OK) {
+        cudaGetLastError();
+        if (pc == MISR_ENOMEM || pc == MISR_ECUDA) return -1;
+        *status = pc;
+        return -2;
+    }
+    std::vector<int2> t, gl;
+    PassSegs segs;
+    build_pass_lists({&p->hp}, {idx}, t, gl, segs);
+    t.insert(t.end(), gl.begin(), gl.end());
+    int2 *items = nullptr;
+    const bool ok2 = cudaMalloc(&items, sizeof(int2) * t.size()) == cudaSuccess &&
+                     cudaMemcpy(items, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                     cudaMemcpy(&s->dprobs[idx], &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok2) {
+        cudaGetLastError();
+        misr_plan_destroy(p);
+        if (items) cudaFree(items);
+        return -1;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (grow) s->slots.emplace_back();   // capacity reserved at creation: no reallocation
+    Slot &sl = s->slots[idx];
+    sl.plan = p;
+    sl.items = items;
+    sl.segs = std::move(segs);
+    sl.desc = want;
+    s->slot_bytes += plan_bytes_estimate(d);
+    return idx;
+}
+
+// Assign queued requests to slots; returns the slots admitted this tick.  The queue is read and
+// every decision recorded under the server lock; slots are made without it.
 std::vector<int> admit(misr_server_t s) {
     std::vector<int> started;
-    std::lock_guard<std::mutex> lock(s->mu);
-    for (auto it = s->queue.begin(); it != s->queue.end();) {
-        Request &rq = s->reqs[*it];
+    std::vector<std::pair<uint64_t, DescCopy>> queued;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (uint64_t t : s->queue) queued.push_back({t, s->reqs[t].desc});
+    }
+    std::vector<char> taken(s->slots.size() + queued.size(), 0);   // slots given out this tick
+    for (auto &q : queued) {
         int use = -1;
         for (size_t i = 0; i < s->slots.size(); ++i)
-            if (s->slots[i].plan && !s->slots[i].busy && s->slots[i].desc.same_class(rq.desc)) { use = (int)i; break; }
-        if (use < 0) {
-            bool ok = can_create(s, rq.desc.d);
-            while (!ok && evict_idle(s, rq.desc)) ok = can_create(s, rq.desc.d);
-            if (ok) {
-                int idx = -1;   // reuse an empty index first
-                for (size_t i = 0; i < s->slots.size(); ++i)
-                    if (!s->slots[i].plan) { idx = (int)i; break; }
-                if (idx < 0 && (int)s->slots.size() < s->cfg.max_slots) { s->slots.emplace_back(); idx = (int)s->slots.size() - 1; }
-                misr_plan_t p = nullptr;
-                const misr_status pc = idx >= 0 ? misr_plan_create(&rq.desc.d, &p) : MISR_EAGAIN;
-                if (pc != MISR_OK && pc != MISR_ENOMEM && pc != MISR_ECUDA && pc != MISR_EAGAIN) {
-                    rq.state = RQ_FAILED;
-                    rq.status = pc;
-                    rq.t_end = now_s();
-                    it = s->queue.erase(it);
-                    s->cv_done.notify_all();
-                    continue;
-                }
-                if (pc == MISR_OK) {
-                    Slot &sl = s->slots[idx];
-                    sl.plan = p;
-                    sl.desc.set(rq.desc.d);
-                    s->slot_bytes += plan_bytes_estimate(rq.desc.d);
-                    std::vector<int2> t, gl;
-                    build_pass_lists({&p->hp}, {idx}, t, gl, sl.segs);
-                    t.insert(t.end(), gl.begin(), gl.end());
-                    bool ok2 = cudaMalloc(&sl.items, sizeof(int2) * t.size()) == cudaSuccess &&
-                               cudaMemcpy(sl.items, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-                               cudaMemcpy(&s->dprobs[idx], &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice) == cudaSuccess;
-                    if (!ok2) {
-                        cudaGetLastError();
-                        misr_plan_destroy(p);
-                        if (sl.items) cudaFree(sl.items);
-                        sl.plan = nullptr;
-                        sl.items = nullptr;
-                        s->slot_bytes -= plan_bytes_estimate(rq.desc.d);
-                    } else {
-                        use = idx;
-                    }
-                } else {
-                    cudaGetLastError();
-                }
+            if (s->slots[i].plan && !s->slots[i].busy && !taken[i] && s->slots[i].desc.same_class(q.second)) {
+                use = (int)i;
+                break;
             }
-        }
+        misr_status bad = MISR_OK;
         if (use < 0) {
-            bool any_busy = false;
-            for (auto &sl : s->slots) any_busy |= sl.busy;
-            if (any_busy) { ++it; continue; }   // stays queued until a running projection frees room
-            // nothing running will ever free room for it
+            use = make_slot(s, q.second, &bad);
+            if (use >= 0 && (size_t)use >= taken.size()) taken.resize(use + 1, 0);
+        }
+        bool any_busy = false;
+        for (auto &sl : s->slots) any_busy |= sl.busy;
+        std::lock_guard<std::mutex> lock(s->mu);
+        auto qit = std::find(s->queue.begin(), s->queue.end(), q.first);
+        if (qit == s->queue.end()) continue;   // cancelled meanwhile (a slot made for it stays idle)
+        Request &rq = s->reqs[q.first];
+        if (use < 0) {
+            if (use == -1 && any_busy) continue;   // stays queued until a running projection frees room
             rq.state = RQ_FAILED;
-            rq.status = fail(MISR_ENOMEM, "a %dx%d x%d projection does not fit the server's HBM budget",
-                             rq.desc.d.lr_h, rq.desc.d.lr_w, rq.desc.d.factor);
+            rq.status = use == -2 ? bad
+                                  : fail(MISR_ENOMEM, "a %dx%d x%d projection does not fit the server's HBM budget",
+                                         rq.desc.d.lr_h, rq.desc.d.lr_w, rq.desc.d.factor);
             rq.t_end = now_s();
-            it = s->queue.erase(it);
+            s->queue.erase(qit);
             s->cv_done.notify_all();
             continue;
         }
+        taken[use] = 1;
         Slot &sl = s->slots[use];
         sl.busy = true;
         sl.ticket = rq.ticket;
@@ -239,7 +285,7 @@ std::vector<int> admit(misr_server_t s) {
         rq.slot = use;
         rq.t_start = now_s();
         started.push_back(use);
-        it = s->queue.erase(it);
+        s->queue.erase(qit);
         s->items_dirty = true;
     }
     return started;
