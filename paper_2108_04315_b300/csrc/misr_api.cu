@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <queue>
 #include <vector>
 
 #include "misr.h"
@@ -378,14 +379,10 @@ static misr_status launch_pass(misr_plan_t p, int mode, double alpha, double bet
     return launch_pass_raw(p->dprob, p->dtile, p->segs, p->dgroup, p->hp.n_groups, p->work, mode, alpha, beta, s);
 }
 
-// The tile list of problem `pi` (border tiles first: they cost more, so a pass ends on
-// interior tiles).  An entry is (problem, ty << 16 | tx); an HR side of at most 2^20 pixels
+// The tile list of problem `pi` for a tile shape (border tiles first: they cost more, so a pass
+// ends on interior tiles; the streaming shape's items are listed by build_pass_lists).  An entry is (problem, ty << 16 | tx); an HR side of at most 2^20 pixels
 // keeps both tile coordinates below 2^16.
 static void append_tiles(const DevProblem &hp, int pi, std::vector<int2> &tiles) {
-    if (hp.shape == STREAM_SHAPE) {   // item t: strip t % tiles_x, rows (t / tiles_x) tile_h ..
-        for (int t = 0; t < hp.n_tiles; ++t) tiles.push_back(make_int2(pi, t));
-        return;
-    }
     const int tx = hp.tiles_x, TH = hp.tile_h, TW = hp.tile_w;
     for (int pass = 0; pass < 2; ++pass)
         for (int t = 0; t < hp.n_tiles; ++t) {
@@ -422,10 +419,21 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
                     StreamRun r;
                     r.variant = v;
                     r.k = stream_consts(*recs[run[0]]);
-                    for (size_t i : run) {
-                        append_tiles(*recs[i], idx[i], tiles);
-                        r.count += recs[i]->n_tiles;
-                    }
+                    // the run's edge items, then the rest
+                    for (int part = 0; part < 2; ++part)
+                        for (size_t i : run) {
+                            const DevProblem &q = *recs[i];
+                            const int ne = q.n_left + q.n_top;
+                            for (int t = part ? ne : 0; t < (part ? q.n_tiles : ne); ++t)
+                                tiles.push_back(make_int2(idx[i], t));
+                            if (part) continue;
+                            r.count += q.n_tiles;
+                            r.n_edge += ne;
+                            r.edge_work += (STREAM_LEFT_COST * q.n_left + STREAM_TOP_COST * q.n_top) *
+                                           (std::min(q.edge_h, q.H) + 12);
+                            r.int_work += (double)(q.n_tiles - ne) * (q.tile_h + 12);
+                        }
+                    r.edge_ctas = run.size() == 1 ? recs[run[0]]->edge_ctas : 0;
                     segs.n[sh][v] += r.count;
                     segs.runs.push_back(r);
                     run.clear();
@@ -483,22 +491,83 @@ static void set_data_norm(DevProblem &hp, const misr_desc &d) {
 
 // Tile grid of a shape; the TMA maps of the workspace images with that shape's boxes.
 static int resident_ctas(int shape, int variant);
-// Rows of a streaming work item: the lowest height (at least 24 rows; its pipeline adds 12)
-// whose items all fit one wave of the GPU's resident warps.
-static int stream_rows(const DevProblem &hp) {
-    const int strips = (hp.W + SW_OWN - 1) / SW_OWN;
-    const long warps = std::max(1L, (long)resident_ctas(STREAM_SHAPE, pass_variant(hp)) * (SW_NT / 32));
-    long rows = std::max(24L, ((long)hp.H * strips + warps - 1) / warps);
-    while (rows < hp.H && (long)((hp.H + rows - 1) / rows) * strips > warps) ++rows;
-    return (int)std::min<long>(rows, 1 << 20);
+// Finish time of the busiest of `warps` warps that take, in list order, n_left items of cost
+// a and then n_top items of cost b, each warp taking the next item when it is free.
+static double edge_makespan(long warps, long n_left, double a, long n_top, double b) {
+    if (warps <= 0) return n_left + n_top > 0 ? 1e300 : 0.0;
+    const long q = n_left / warps, r = n_left % warps;
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (long w = 0; w < warps; ++w) free_at.push((q + (w < r ? 1 : 0)) * a);
+    double end = q > 0 || r > 0 ? (q + (r > 0 ? 1 : 0)) * a : 0.0;
+    for (long i = 0; i < n_top; ++i) {
+        const double t = free_at.top() + b;
+        free_at.pop();
+        free_at.push(t);
+        end = std::max(end, t);
+    }
+    return end;
+}
+
+// Items of the streaming shape (DevProblem: n_left, n_top, edge_h, tile_h, tiles_y, edge_ctas).
+// An item of r rows takes r + 12 row steps (its pipeline); a step of a left-strip item costs
+// STREAM_LEFT_COST and one of a top item STREAM_TOP_COST of an interior step.  Over the
+// resident warps (8 per CTA, the launch's full grid), the split picks the number of edge CTAs
+// E, the edge item height and the interior item height that minimise the later of the two
+// paths' finish times, the interior items in one wave; those start at row edge_h >= 24 (below
+// every top frame mask).  For a launch over this problem alone.
+static void stream_split(DevProblem &hp) {
+    const int H = hp.H, strips = hp.tiles_x;
+    const int G = std::max(1, resident_ctas(STREAM_SHAPE, pass_variant(hp)));
+    const int n_top = strips > 1 ? strips - 1 : 0;
+    double best = -1.0;
+    int b_e = G, b_eh = std::max(24, H), b_th = 24;
+    const int e_lo = strips > 1 && G > 1 ? 1 : G, e_hi = strips > 1 && G > 1 ? G - 1 : G;
+    for (int E = e_lo; E <= e_hi; ++E) {
+        const long we = 8L * E, wi = 8L * (G - E);
+        // edge item heights: the lowest height for each count of left-strip items
+        for (long nl = (H + 23) / 24; nl >= 1; --nl) {
+            const int eh = std::max(24, (int)((H + nl - 1) / nl));
+            if ((H + eh - 1) / eh != nl) continue;
+            const double steps = std::min(eh, H) + 12;
+            const double te = edge_makespan(we, nl, STREAM_LEFT_COST * steps, n_top, STREAM_TOP_COST * steps);
+            if (best >= 0 && te >= best) {
+                if (nl + n_top <= we) break;   // one wave: taller items only finish later
+                continue;
+            }
+            double ti = 0.0;
+            int th = 24;
+            const long R = (long)H - eh;
+            if (strips > 1 && R > 0) {
+                if (wi <= 0) continue;
+                th = (int)std::max(24L, (R * (strips - 1) + wi - 1) / wi);
+                while (th < R && ((R + th - 1) / th) * (strips - 1) > wi) ++th;
+                ti = (double)(std::min<long>(th, R) + 12);
+            }
+            const double c = std::max(te, ti);
+            if (best < 0 || c < best) { best = c; b_e = E; b_eh = eh; b_th = th; }
+        }
+    }
+    hp.edge_h = b_eh;
+    hp.tile_h = b_th;
+    hp.edge_ctas = b_e;
+    hp.n_left = (H + b_eh - 1) / b_eh;
+    hp.n_top = n_top;
+    const long R = (long)H - b_eh;
+    hp.tiles_y = strips > 1 && R > 0 ? (int)((R + b_th - 1) / b_th) : 0;
+    hp.n_tiles = hp.n_left + hp.n_top + (strips - 1) * hp.tiles_y;
 }
 static void set_shape(DevProblem &hp, int shape) {
     hp.shape = shape;
     hp.tile_w = SHAPE_TW[shape];
-    hp.tile_h = shape == STREAM_SHAPE ? stream_rows(hp) : SHAPE_TH[shape];
-    hp.tiles_y = (hp.H + hp.tile_h - 1) / hp.tile_h;
     hp.tiles_x = (hp.W + hp.tile_w - 1) / hp.tile_w;
+    if (shape == STREAM_SHAPE) {
+        stream_split(hp);
+        return;
+    }
+    hp.tile_h = SHAPE_TH[shape];
+    hp.tiles_y = (hp.H + hp.tile_h - 1) / hp.tile_h;
     hp.n_tiles = hp.tiles_y * hp.tiles_x;
+    hp.n_left = hp.n_top = hp.edge_h = hp.edge_ctas = 0;
 }
 static misr_status make_maps(DevProblem &hp) {
     int xw = 0, xh = 0, ew = 0, eh = 0;
@@ -609,6 +678,19 @@ static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float 
     return MISR_OK;
 }
 
+// Edge CTAs of a streaming launch: the split planned for a problem alone when the launch
+// has that problem's full grid, else a share of the grid proportional to the edge items'
+// work (at least one CTA while there are edge items, and one CTA left for the rest).
+static int stream_edge_ctas(const StreamRun &run, int grid) {
+    if (run.n_edge >= run.count) return grid;
+    if (run.edge_ctas > 0 && run.edge_ctas <= grid) return run.edge_ctas;
+    const double tot = run.edge_work + run.int_work;
+    int e = tot > 0 ? (int)std::lround(grid * run.edge_work / tot) : 1;
+    e = std::max(e, 1);
+    if (grid > 1) e = std::min(e, grid - 1);
+    return e;
+}
+
 misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tiles, const PassSegs &segs,
                                        const int2 *groups, int n_groups, unsigned *work, int mode, double alpha,
                                        double beta, cudaStream_t s) {
@@ -625,13 +707,15 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
                     if (run.variant != v) continue;
                     const int2 *t = tiles + off;
                     off += run.count;
-                    const int grid = pass_grid(sh, v, (run.count + 7) / 8);
+                    // a problem alone gets the full grid its items were split for
+                    const int grid = run.edge_ctas > 0 ? resident_ctas(sh, v) : pass_grid(sh, v, (run.count + 7) / 8);
+                    const int ne = stream_edge_ctas(run, grid);
                     if (v == 0)
-                        CK(launch_pdl(scg_stream_kernel<false>, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.count, work,
-                                      mode, alpha, beta, run.k));
+                        CK(launch_pdl(scg_stream_kernel<false>, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.n_edge,
+                                      run.count, ne, work, mode, alpha, beta, run.k));
                     else
-                        CK(launch_pdl(scg_stream_kernel<true>, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.count, work,
-                                      mode, alpha, beta, run.k));
+                        CK(launch_pdl(scg_stream_kernel<true>, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.n_edge,
+                                      run.count, ne, work, mode, alpha, beta, run.k));
                 }
                 continue;
             }
@@ -1203,7 +1287,7 @@ misr_status misr_import_state(misr_plan_t p, const void *buf, size_t bytes) {
     st.done = (st.status != 0 || st.iter >= st.iters || !(st.pn2 > 0.0) || !std::isfinite(st.alpha)) ? 1 : 0;
     CK(cudaMemcpy(p->hp.st, &st, sizeof st, cudaMemcpyHostToDevice));
     CK(cudaMemset(p->hp.counter, 0, sizeof(unsigned int)));
-    CK(cudaMemset(p->work, 0, 2 * sizeof(unsigned int)));
+    CK(cudaMemset(p->work, 0, 4 * sizeof(unsigned int)));
     CK(cudaMemset(p->hp.trace, 0, (size_t)std::max(p->d.iters, 1) * TRACE_COLS * sizeof(double)));
     *p->st_host = st;
     p->solved = true;

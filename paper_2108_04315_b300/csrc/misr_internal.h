@@ -57,6 +57,9 @@ misr_status check_desc(const misr_desc &d);
 // constants (kernel parameters of one launch): one launch per run, in list order.
 struct StreamRun {
     int variant = 0, count = 0;
+    int n_edge = 0;                      // the run's edge items (listed first)
+    int edge_ctas = 0;                   // planned edge CTAs of a run of one problem, else 0
+    double edge_work = 0, int_work = 0;  // row steps of the edge and the other items (edge weighted)
     misr::StreamConsts k{};
 };
 struct PassSegs {

@@ -197,7 +197,9 @@ __device__ __forceinline__ void with_ext(const float *v, float *e) {
 
 // Horizontal forward blur: out(v) = sum_b hx(b) e(v - b).  At the left edge the frame masks
 // drop tap b of output v when b > fwd_lim(v): those taps are taken out again (an item whose
-// window meets the edge enters that block; the rest skip it).
+// window meets the edge enters that block; the rest skip it).  EDGE: compiled with the
+// border corrections (the interior path leaves them out).
+template <bool EDGE>
 __device__ __forceinline__ void hblur_fwd(const StreamConsts &k, const SegGeo &g, const float *e, float *out) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -206,7 +208,7 @@ __device__ __forceinline__ void hblur_fwd(const StreamConsts &k, const SegGeo &g
         for (int b = -2; b <= 2; ++b) s = fmaf(k.hx[b + 2], e[2 + j - b], s);
         out[j] = s;
     }
-    if (g.left) {
+    if (EDGE && g.left) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int lim = fwd_lim(g.v0 + j, k.f, k.fmag);
@@ -218,6 +220,7 @@ __device__ __forceinline__ void hblur_fwd(const StreamConsts &k, const SegGeo &g
 }
 // Horizontal adjoint blur: out(u) = sum_b hx(b) e(u + b); at the left edge the adjoint's frame
 // masks (tap b dropped when !adj_tap_ok(u, b)) are taken out again.
+template <bool EDGE>
 __device__ __forceinline__ void hblur_adj(const StreamConsts &k, const SegGeo &g, const float *e, float *out) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -226,7 +229,7 @@ __device__ __forceinline__ void hblur_adj(const StreamConsts &k, const SegGeo &g
         for (int b = -2; b <= 2; ++b) s = fmaf(k.hx[b + 2], e[2 + j + b], s);
         out[j] = s;
     }
-    if (g.left) {
+    if (EDGE && g.left) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int u = g.v0 + j;
@@ -241,7 +244,7 @@ __device__ __forceinline__ void hblur_adj(const StreamConsts &k, const SegGeo &g
 // K + OFF) into the pending rows row + a, a = -2..2.  Near the top edge (rows below
 // 2 MAXF + 2) tap a of output row row + a is dropped when a > fwd_lim(row + a); it is taken out
 // again there.
-template <int K, int OFF>
+template <int K, int OFF, bool EDGE>
 __device__ __forceinline__ void vscatter_fwd(const StreamConsts &k, float (*acc)[4], const float *h, int row) {
 #pragma unroll
     for (int a = -2; a <= 2; ++a) {
@@ -249,7 +252,7 @@ __device__ __forceinline__ void vscatter_fwd(const StreamConsts &k, float (*acc)
 #pragma unroll
         for (int j = 0; j < 4; ++j) z[j] = fmaf(k.hy[a + 2], h[j], z[j]);
     }
-    if (row < 2 * MAXF + 2) {
+    if (EDGE && row < 2 * MAXF + 2) {
 #pragma unroll
         for (int a = -1; a <= 2; ++a) {
             if (a > fwd_lim(row + a, k.f, k.fmag)) {
@@ -276,7 +279,9 @@ __device__ __forceinline__ void rotate_rows(float (*w)[NV]) {
 
 // One step of the item: input row n.  Row n + off sits at slot off mod 5 of every register
 // window (K = 0; the windows are rotated at the end of the step).  RPB: r and p stored as bf16.
-template <int K, bool RPB>
+// EDGE: the path with the frame-mask corrections of the top and left borders (any item);
+// without it, only items whose rows start at 24 or below and whose strip is not the first.
+template <int K, bool RPB, bool EDGE>
 __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &k, const SegGeo &g, int n,
                                             float alpha, float beta, const float *__restrict__ X,
                                             const float *__restrict__ R, const float *__restrict__ PO,
@@ -335,15 +340,15 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
     {
         float e[8], h[4];
         with_ext(xp, e);
-        hblur_fwd(k, g, e, h);
-        vscatter_fwd<K, 0>(k, S.za, h, n);
+        hblur_fwd<EDGE>(k, g, e, h);
+        vscatter_fwd<K, 0, EDGE>(k, S.za, h, n);
 #pragma unroll
         for (int j = 0; j < 4; ++j) S.xw[sN][j] = (row_n_in && g.in(j)) ? xp[j] : SW_BIG;
         S.xw[sN][4] = __shfl_down_sync(FULL, S.xw[sN][0], 1);
         S.xw[sN][5] = __shfl_down_sync(FULL, S.xw[sN][1], 1);
         with_ext(p, e);
-        hblur_fwd(k, g, e, h);
-        vscatter_fwd<K, 0>(k, S.bpa, h, n);
+        hblur_fwd<EDGE>(k, g, e, h);
+        vscatter_fwd<K, 0, EDGE>(k, S.bpa, h, n);
     }
 
     // ---- row n-2: residual, J_data, dJ_data and the data part of c; then its adjoint
@@ -377,7 +382,7 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
         }
         float e[8], h[4];
         with_ext(E, e);
-        hblur_adj(k, g, e, h);
+        hblur_adj<EDGE>(k, g, e, h);
 #pragma unroll
         for (int a = -2; a <= 2; ++a) {
             // tap a of output row m - a reads sample row m
@@ -385,7 +390,7 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
 #pragma unroll
             for (int j = 0; j < 4; ++j) ga[j] = fmaf(2.f * k.hy[a + 2], h[j], ga[j]);
         }
-        if (m < 2 * MAXF) {   // the adjoint's frame masks near the top: dropped when !adj_tap_ok(m - a, a)
+        if (EDGE && m < 2 * MAXF) {   // the adjoint's frame masks near the top: dropped when !adj_tap_ok(m - a, a)
 #pragma unroll
             for (int a = -2; a <= 2; ++a)
                 if (!adj_tap_ok(m - a, a, k.f, k.fmag)) {
@@ -498,8 +503,8 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
         for (int j = 0; j < 4; ++j) S.rw[sN4][j] = rv[j];
         S.rw[sN4][4] = e[6];
         S.rw[sN4][5] = e[7];
-        hblur_fwd(k, g, e, h);
-        vscatter_fwd<K, -4>(k, S.bra, h, m);
+        hblur_fwd<EDGE>(k, g, e, h);
+        vscatter_fwd<K, -4, EDGE>(k, S.bra, h, m);
         // p(m) with the next lane's two columns, for the BTV curvature
 #pragma unroll
         for (int j = 0; j < 4; ++j) S.pw[sN4][j] = p4[j];
@@ -586,7 +591,7 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
 }
 
 // One item: steps n = y0 - 6 .. ye + 5.
-template <bool RPB>
+template <bool RPB, bool EDGE>
 __device__ __forceinline__ void stream_item(StreamState &S, const StreamConsts &k, const SegGeo &g, float alpha,
                                             float beta, const float *__restrict__ X, const float *__restrict__ R,
                                             const float *__restrict__ PO, const float *__restrict__ Y,
@@ -616,29 +621,49 @@ __device__ __forceinline__ void stream_item(StreamState &S, const StreamConsts &
     issue_step_rows<RPB>(g, S.wb, S.cur, n0, X, R, PO, Y);
     const int n_end = g.ye + 6;   // one past the last step
 #pragma unroll 1
-    for (int n = n0; n < n_end; ++n) stream_step<0, RPB>(S, k, g, n, alpha, beta, X, R, PO, Y, Xn, Rn, Pn);
+    for (int n = n0; n < n_end; ++n) stream_step<0, RPB, EDGE>(S, k, g, n, alpha, beta, X, R, PO, Y, Xn, Rn, Pn);
 }
 
-// The streaming pass: every warp takes items (problem, item index) from the launch's counter
-// until the list runs out.  Item t of a problem is strip t % tiles_x, rows [ty tile_h,
-// (ty + 1) tile_h) with ty = t / tiles_x.  Every item's ten sums are written as (hi, lo) pairs
-// in a fixed order; reduce_kernel combines them after the pass as it does the tile sums.
-template <bool RPB>
-__global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *__restrict__ probs,
-                                                              const int2 *__restrict__ items, int n_items,
-                                                              unsigned *work, int mode, double probe_alpha,
-                                                              double probe_beta, const StreamConsts k) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    extern __shared__ __align__(16) unsigned char stream_smem[];   // SW_SMEM_BYTES
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    StreamState S;
-    S.wb = stream_smem + warp * SW_WARP_BYTES + 16 * lane;
-    S.cur = 0;
-    S.nxt = SW_STAGE_BYTES;
+// Geometry of item t of problem P (the item order of the problem record: the left strip's
+// items, the top items of the other strips, then their remaining rows).
+__device__ __forceinline__ void stream_item_rows(const DevProblem &P, int t, int &tx, int &y0, int &ye) {
+    if (t < P.n_left) {
+        tx = 0;
+        y0 = t * P.edge_h;
+        ye = min(y0 + P.edge_h, P.H);
+    } else if (t < P.n_left + P.n_top) {
+        tx = 1 + (t - P.n_left);
+        y0 = 0;
+        ye = min(P.edge_h, P.H);
+    } else {
+        const int u = t - P.n_left - P.n_top, sx = P.tiles_x - 1;
+        const int c = u / sx;
+        tx = 1 + (u - c * sx);
+        y0 = P.edge_h + c * P.tile_h;
+        ye = min(y0 + P.tile_h, P.H);
+    }
+}
+
+// One warp's share of the pass: items from the launch's lists until they run out.  The edge
+// path (EDGE) first takes the edge items [0, n_edge) from counter work[0], then helps with the
+// rest; the interior path takes only the items [n_edge, n_items), from counter work[2].  Every
+// item's ten sums are written as (hi, lo) pairs at its index; reduce_kernel combines them after
+// the pass as it does the tile sums.
+template <bool RPB, bool EDGE>
+__device__ __forceinline__ void stream_worker(StreamState &S, const DevProblem *__restrict__ probs,
+                                              const int2 *__restrict__ items, int n_edge, int n_items,
+                                              unsigned *work, int mode, double probe_alpha, double probe_beta,
+                                              const StreamConsts &k) {
+    const int lane = threadIdx.x & 31;
+    bool edge_list = EDGE;
     for (;;) {
         unsigned it = 0;
-        if (lane == 0) it = atomicAdd(&work[0], 1u);
+        if (lane == 0) it = edge_list ? atomicAdd(&work[0], 1u) : (unsigned)n_edge + atomicAdd(&work[2], 1u);
         it = __shfl_sync(FULL, it, 0);
+        if (edge_list && it >= (unsigned)n_edge) {
+            edge_list = false;
+            continue;
+        }
         if (it >= (unsigned)n_items) break;
         const int2 wt = items[it];
         const DevProblem &P = probs[wt.x];
@@ -646,14 +671,17 @@ __global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *
         if (ld_cg(&st->done)) continue;
         const int t = wt.y;
         if (!MISR_IN_BOUNDS(t >= 0 && t < P.n_tiles, BC_TILE, t, P.n_tiles)) continue;
-        const int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
+        // the interior path takes no edge item (its list holds none; checked all the same)
+        if (!EDGE && !MISR_IN_BOUNDS(t >= P.n_left + P.n_top, BC_TILE, t, P.n_left)) continue;
+        int tx, y0, ye;
+        stream_item_rows(P, t, tx, y0, ye);
         const int cur = ld_cg(&st->cur), pcur = ld_cg(&st->pcur);
         const float alpha = mode == MODE_PROBE ? (float)probe_alpha : __ldcg(&st->alpha_f);
         const float beta = mode == MODE_PROBE ? (float)probe_beta : __ldcg(&st->beta_f);
         SegGeo g;
         g.H = P.H; g.W = P.W; g.pitch = P.pitch;
-        g.y0 = ty * P.tile_h;
-        g.ye = min(g.y0 + P.tile_h, g.H);
+        g.y0 = y0;
+        g.ye = ye;
         const int x0 = tx * SW_OWN, c0 = x0 - SW_HALO;
         g.v0 = c0 + 4 * lane;
         g.own_lane = lane >= SW_HALO / 4 && lane < (SW_HALO + SW_OWN) / 4;
@@ -664,12 +692,12 @@ __global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *
         g.in3 = g.v0 + 3 >= 0 && g.v0 + 3 < g.W;
         g.all_in = g.in0 && g.in3;
         g.left = c0 < 2 * MAXF + 2;
-        if (!MISR_IN_BOUNDS(g.y0 < g.H && x0 < g.W, BC_IMAGE, g.y0, x0)) continue;
+        if (!MISR_IN_BOUNDS(g.y0 < g.ye && x0 < g.W, BC_IMAGE, g.y0, x0)) continue;
 #pragma unroll
         for (int i = 0; i < NPART; ++i) S.s[i] = 0.f;
         S.lo_jb = S.lo_rr = S.lo_rrx = S.lo_pr = 0.f;
-        stream_item<RPB>(S, k, g, alpha, beta, P.X[cur], P.Rv[cur], P.Pv[pcur], P.Y, P.X[cur ^ 1], P.Rv[cur ^ 1],
-                         P.Pv[pcur ^ 1]);
+        stream_item<RPB, EDGE>(S, k, g, alpha, beta, P.X[cur], P.Rv[cur], P.Pv[pcur], P.Y, P.X[cur ^ 1],
+                               P.Rv[cur ^ 1], P.Pv[pcur ^ 1]);
         // the item's sums: lanes outside the owned strip drop theirs; then a fixed-order warp
         // sum of (hi, lo) pairs
         const bool keep = g.own_lane;
@@ -692,14 +720,37 @@ __global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *
             P.partials[(size_t)lane * P.n_tiles + t] = mine;
         }
     }
+}
+
+// The streaming pass.  The launch's item list holds its n_edge edge items, then the rest.  CTAs
+// below n_edge_ctas run the edge path, the others the interior path: one CTA per SM, so an SM
+// keeps one path in its instruction cache.
+template <bool RPB>
+__global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *__restrict__ probs,
+                                                              const int2 *__restrict__ items, int n_edge,
+                                                              int n_items, int n_edge_ctas, unsigned *work, int mode,
+                                                              double probe_alpha, double probe_beta,
+                                                              const StreamConsts k) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char stream_smem[];   // SW_SMEM_BYTES
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    StreamState S;
+    S.wb = stream_smem + warp * SW_WARP_BYTES + 16 * lane;
+    S.cur = 0;
+    S.nxt = SW_STAGE_BYTES;
+    if ((int)blockIdx.x < n_edge_ctas)
+        stream_worker<RPB, true>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k);
+    else
+        stream_worker<RPB, false>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k);
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    // the last warp to stop zeroes the launch's counter for the next launch
+    // the last warp to stop zeroes the launch's counters for the next launch
     if (lane == 0) {
         __threadfence();
         if (atomicAdd(&work[1], 1u) == gridDim.x * (SW_NT / 32) - 1) {
             work[0] = 0u;
             work[1] = 0u;
+            work[2] = 0u;
             __threadfence();
         }
     }

@@ -38,13 +38,17 @@ constexpr uint32_t TMA_WAIT_TRIES = 1u << 24;   // bounded wait for the tile loa
 // (1024 / NT CTAs resident per SM).  STREAM_SHAPE: the row-streaming kernel, whose work item is
 // a strip of SHAPE_TW = 112 columns by a height chosen per plan (SHAPE_TH 0: at run time), one
 // warp each, NT = 256 threads (8 independent warps) per CTA.  The autotuner picks one per HR
-// image size.
+// image size.  STREAM_LEFT_COST, STREAM_TOP_COST: time per row step of a streaming item of the
+// left strip and of a top item, both on the path compiled with the border corrections,
+// relative to an item on the interior path (per-warp globaltimer spans at 4096^2 HR: 2.56 and
+// about 1.5 against 1.78 us per step), for the split of the items between the two paths.
 constexpr int N_SHAPES = 4;
 constexpr int N_TILE_SHAPES = 3;
 constexpr int STREAM_SHAPE = 3;
 constexpr int SHAPE_TH[N_SHAPES] = {32, 32, 16, 0};
 constexpr int SHAPE_TW[N_SHAPES] = {64, 32, 64, 112};
 constexpr int SHAPE_NT[N_SHAPES] = {512, 256, 256, 256};
+constexpr double STREAM_LEFT_COST = 1.45, STREAM_TOP_COST = 1.0;
 // Compiled variants of the fused pass per shape: bit 0 r and p stored as bf16, bit 1 the
 // smoothed L1 data term, bit 2 per-phase blur taps (non-integer shifts; compiled for the
 // 32x32 shape only).  The streaming shape has variants 0 and 1 (squared L2 data term, shared
@@ -88,6 +92,12 @@ struct DevProblem {
     int l1;                                       // data term: 0 squared L2, 1 smoothed L1
     int phased;                                   // non-integer shifts: blur taps per phase
     int shape, tile_h, tile_w;                    // tile shape (index into SHAPE_*) and its size
+    // Streaming shape: the edge items come first, the n_left items of the left strip (edge_h
+    // rows each) and the n_top items at the top of the other strips (rows [0, edge_h)); then
+    // those strips' remaining rows in items of tile_h rows (tiles_y per strip).  Only the edge
+    // items meet the frame masks of the top and left borders.  edge_ctas: CTAs of a launch
+    // over this problem alone that start on the edge items.
+    int n_left, n_top, edge_h, edge_ctas;
     int wait_tries;                               // polls before a tile load is reported late
     float hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];  // separable PSF, h(a, b) = hy[a+R] hx[b+R]
     float lambda, eps, eps2, data_eps;            // data_eps: the L1 data term's smoothing

@@ -70,3 +70,44 @@ def test_autotune_picks_a_shape_that_later_plans_use(orc):
     with pytest.raises(B.MisrError) as e:
         B.misr_autotune(B.make_desc(h, w, f, sh, psf), passes=0)
     assert e.value.status == B.MISR_EINVAL
+
+
+# Geometries of the streaming shape's item split: one strip (no interior items), images no
+# taller than one edge item (the top items hold every row), a row more than that, a tall thin
+# image whose left strip takes several waves of edge items, and a wide short one.
+STREAM_GEOMETRIES = {
+    "one_strip": (40, 50, 2),       # HR 80 x 100
+    "short": (10, 150, 2),          # HR 20 x 300
+    "edge_plus_one": (25, 120, 1),  # HR 25 x 120
+    "tall_thin": (700, 64, 2),      # HR 1400 x 128
+    "wide_short": (20, 900, 2),     # HR 40 x 1800
+}
+
+
+@pytest.mark.parametrize("name", sorted(STREAM_GEOMETRIES))
+def test_streaming_item_split_matches_the_oracle(orc, name):
+    from paper_2108_04315_b300 import binding as B
+    h, w, f = STREAM_GEOMETRIES[name]
+    sh = gen.half_pixel_shifts() if f == 2 else [(0.0, 0.0)]
+    psf = gen.gaussian_psf(5, 0.5)
+    P = orc.Problem(h, w, f, sh, psf, lam=0.01)
+    xt = gen.phantom(f * h, f * w, 70)
+    y = (P.forward_all(xt) + gen.gaussian_noise((len(sh), h, w), 0.01, 71)).astype(np.float32)
+    x = gen.smooth_field(f * h, f * w, 72).astype(np.float32)
+    plan = B.Plan(h, w, f, sh, psf, lam=0.01, iters=6, tile_shape=4)
+    J, g = plan.gradient(to_dev(y), to_dev(x))
+    Jr, gr = P.gradient(x.astype(np.float64), y.astype(np.float64))
+    assert rel_l2(g.cpu().numpy(), gr) <= RTOL_OP
+    assert J == pytest.approx(Jr, rel=RTOL_OP)
+    # the pass's ten sums equal those of the 32 x 32 tile shape (same arithmetic, other order)
+    tile = B.Plan(h, w, f, sh, psf, lam=0.01, iters=6, tile_shape=2)
+    r = gen.random_field(xt.shape, 73, -0.3, 0.3).astype(np.float32)
+    po = gen.random_field(xt.shape, 74, -0.3, 0.3).astype(np.float32)
+    sums = [p.pass_probe(to_dev(y), to_dev(x), to_dev(r), to_dev(po), 0.3, 0.7)[3] for p in (plan, tile)]
+    for k in sums[1]:
+        assert sums[0][k] == pytest.approx(sums[1][k], rel=1e-5, abs=1e-6 * abs(sums[1]["J_data"]) + 1e-12), k
+    xs, st = plan.solve(to_dev(y))
+    xr, _ = P.scg(y.astype(np.float64), P.shift_add(y.astype(np.float64)), 6)
+    assert rel_l2(xs.cpu().numpy(), xr) <= RTOL_X
+    plan.close()
+    tile.close()
