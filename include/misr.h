@@ -87,7 +87,9 @@ typedef struct misr_desc {
                                 stencils accumulate in float and the SCG scalars stay FP64 either
                                 way.  misr_pass_probe needs MISR_F32. */
     int32_t tile_shape;      /* MISR_TILE_AUTO (0): the shape misr_autotune chose for this HR size
-                                in this process, else the default; or one of MISR_TILE_* */
+                                in this process, else the default (MISR_TILE_STREAM from 5e6 HR
+                                pixels up where the plan's data term and shifts allow it,
+                                MISR_TILE_32x32 otherwise); or one of MISR_TILE_* */
     int32_t data_norm;       /* MISR_NORM_L2 (0): the squared L2 data term of Eq. 6 above.
                                 MISR_NORM_L1: the L1 data term of the paper's experiments
                                 (Sec. 3.1), each residual t smoothed like the prior's |t|:

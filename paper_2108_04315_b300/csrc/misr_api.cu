@@ -14,7 +14,6 @@
 #include <mutex>
 #include <new>
 #include <string>
-#include <queue>
 #include <vector>
 
 #include "misr.h"
@@ -432,19 +431,28 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
                             r.edge_work += (STREAM_LEFT_COST * q.n_left + STREAM_TOP_COST * q.n_top) *
                                            (std::min(q.edge_h, q.H) + 12);
                             r.int_work += (double)(q.n_tiles - ne) * (q.tile_h + 12);
+                            r.edge_ctas_w += (double)q.edge_ctas * ((double)(q.n_tiles - ne) * (q.tile_h + 12) +
+                                                                     (STREAM_LEFT_COST * q.n_left + STREAM_TOP_COST * q.n_top) *
+                                                                         (std::min(q.edge_h, q.H) + 12));
                         }
                     r.edge_ctas = run.size() == 1 ? recs[run[0]]->edge_ctas : 0;
                     segs.n[sh][v] += r.count;
                     segs.runs.push_back(r);
                     run.clear();
                 };
+                // a problem whose items fill at least half the grid's warps gets a launch of its
+                // own, split as planned (merged, such problems ran slower than one after another:
+                // the launch's last items straggled); smaller ones share launches
+                const long grid_warps = 8L * resident_ctas(STREAM_SHAPE, v);
                 for (size_t i = 0; i < recs.size(); ++i) {
                     if (recs[i]->shape != sh || pass_variant(*recs[i]) != v) continue;
+                    const bool alone = 2L * recs[i]->n_tiles >= grid_warps;
                     if (!run.empty()) {
                         const StreamConsts a = stream_consts(*recs[run[0]]), b = stream_consts(*recs[i]);
-                        if (std::memcmp(&a, &b, sizeof(a)) != 0) flush();
+                        if (alone || std::memcmp(&a, &b, sizeof(a)) != 0) flush();
                     }
                     run.push_back(i);
+                    if (alone) flush();
                 }
                 flush();
                 continue;
@@ -468,6 +476,10 @@ std::vector<std::pair<std::pair<int, int>, std::array<double, N_SHAPES>>> g_tune
 static int desc_variant(const misr_desc &d, bool phased) {
     return (d.iterate_dtype == MISR_BF16 ? 1 : 0) | (d.data_norm == MISR_NORM_L1 ? 2 : 0) | (phased ? 4 : 0);
 }
+// Untuned default: the streaming shape from STREAM_DEFAULT_PIXELS HR pixels up (where it can
+// run the plan's variant), else 32 x 32 tiles.  Measured per pass, stream over the best tile
+// shape: 1.10 at 2048^2, 0.91 at 2560^2, 0.90 at 3072^2, 0.86 at 3072 x 3840, 0.84 at 6144^2.
+constexpr long STREAM_DEFAULT_PIXELS = 5000000;
 static int pick_shape(const misr_desc &d, int variant) {
     if (d.tile_shape >= 1 && d.tile_shape <= N_SHAPES) return d.tile_shape - 1;
     const int H = d.factor * d.lr_h, W = d.factor * d.lr_w;
@@ -480,6 +492,7 @@ static int pick_shape(const misr_desc &d, int variant) {
                     best = sh;
             if (best >= 0) return best;
         }
+    if ((long)H * W >= STREAM_DEFAULT_PIXELS && shape_takes_variant(STREAM_SHAPE, variant)) return STREAM_SHAPE;
     return DEFAULT_SHAPE;
 }
 
@@ -492,18 +505,19 @@ static void set_data_norm(DevProblem &hp, const misr_desc &d) {
 // Tile grid of a shape; the TMA maps of the workspace images with that shape's boxes.
 static int resident_ctas(int shape, int variant);
 // Finish time of the busiest of `warps` warps that take, in list order, n_left items of cost
-// a and then n_top items of cost b, each warp taking the next item when it is free.
+// a and then n_top items of cost b, each warp taking the next item when it is free.  After the
+// left items, r warps are free at (q + 1) a and the rest at q a; the top items then finish at
+// the merged times q a + k b and (q + 1) a + k b, k >= 1, that many warps at each.
 static double edge_makespan(long warps, long n_left, double a, long n_top, double b) {
     if (warps <= 0) return n_left + n_top > 0 ? 1e300 : 0.0;
     const long q = n_left / warps, r = n_left % warps;
-    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
-    for (long w = 0; w < warps; ++w) free_at.push((q + (w < r ? 1 : 0)) * a);
-    double end = q > 0 || r > 0 ? (q + (r > 0 ? 1 : 0)) * a : 0.0;
-    for (long i = 0; i < n_top; ++i) {
-        const double t = free_at.top() + b;
-        free_at.pop();
-        free_at.push(t);
-        end = std::max(end, t);
+    double end = (q + (r > 0 ? 1 : 0)) * a;
+    long left = n_top, k0 = 1, k1 = 1;
+    const long c0 = warps - r, c1 = r;
+    while (left > 0) {
+        const double t0 = q * a + k0 * b, t1 = c1 > 0 ? (q + 1) * a + k1 * b : 1e300;
+        if (t0 <= t1) { left -= c0; ++k0; end = std::max(end, t0); }
+        else { left -= c1; ++k1; end = std::max(end, t1); }
     }
     return end;
 }
@@ -678,14 +692,16 @@ static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float 
     return MISR_OK;
 }
 
-// Edge CTAs of a streaming launch: the split planned for a problem alone when the launch
-// has that problem's full grid, else a share of the grid proportional to the edge items'
-// work (at least one CTA while there are edge items, and one CTA left for the rest).
+// Edge CTAs of a streaming launch: the split planned for a problem alone, or for several
+// problems the average of their planned splits weighted by their work (each planned for the
+// full grid), scaled to the launch's grid; at least one CTA while there are edge items, and
+// one left for the rest.
 static int stream_edge_ctas(const StreamRun &run, int grid) {
     if (run.n_edge >= run.count) return grid;
     if (run.edge_ctas > 0 && run.edge_ctas <= grid) return run.edge_ctas;
     const double tot = run.edge_work + run.int_work;
-    int e = tot > 0 ? (int)std::lround(grid * run.edge_work / tot) : 1;
+    const int full = resident_ctas(STREAM_SHAPE, run.variant);
+    int e = tot > 0 ? (int)std::lround(run.edge_ctas_w / tot * grid / std::max(full, 1)) : 1;
     e = std::max(e, 1);
     if (grid > 1) e = std::min(e, grid - 1);
     return e;

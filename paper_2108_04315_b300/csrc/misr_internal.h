@@ -60,6 +60,7 @@ struct StreamRun {
     int n_edge = 0;                      // the run's edge items (listed first)
     int edge_ctas = 0;                   // planned edge CTAs of a run of one problem, else 0
     double edge_work = 0, int_work = 0;  // row steps of the edge and the other items (edge weighted)
+    double edge_ctas_w = 0;              // sum of the problems' planned edge CTAs times their work
     misr::StreamConsts k{};
 };
 struct PassSegs {
