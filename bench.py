@@ -625,7 +625,14 @@ def serving_record(n, slots, tick):
                       "warmup": "one untimed burst of all requests (the slot pool is made), 2 plain solves"},
            "api": "misr_submit at arrival, misr_wait",
            "latency_ms": {"served_p50": _pct(lat_srv, 50), "served_p99": _pct(lat_srv, 99),
-                          "plain_p50": _pct(lat_plain, 50), "plain_p99": _pct(lat_plain, 99)},
+                          "plain_p50": _pct(lat_plain, 50), "plain_p99": _pct(lat_plain, 99),
+                          # per scan (the two scans' latencies are far apart, so the medians of
+                          # the mix above jump between them)
+                          "by_scan": {k: {"served_p50": _pct([l for l, q in zip(lat_srv, names) if q == k], 50),
+                                          "served_p99": _pct([l for l, q in zip(lat_srv, names) if q == k], 99),
+                                          "plain_p50": _pct([l for l, q in zip(lat_plain, names) if q == k], 50),
+                                          "plain_p99": _pct([l for l, q in zip(lat_plain, names) if q == k], 99)}
+                                      for k in sorted(set(names))}},
            "plain": {"value": plain_rate, "unit": UNIT, "api": "misr_solve at arrival, one at a time",
                      "latency_p50_ms": _pct(lat_plain, 50), "latency_p99_ms": _pct(lat_plain, 99)},
            "p50_over_plain": _pct(lat_plain, 50) / _pct(lat_srv, 50),
