@@ -20,6 +20,9 @@ def cases():
         "single_pixel": (1, 1, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
         "thin_strip": (1, 97, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
         "tall_strip": (90, 1, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
+        # the streaming shape's item split: several waves of left-strip items; top items only
+        "split_tall": (700, 64, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
+        "split_short": (10, 150, 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5)),
     }
 
 
@@ -37,11 +40,14 @@ def run(lib_path):
     plans = []
     for i, (name, (h, w, f, shifts, psf)) in enumerate(sorted(cases().items())):
         y = torch.from_numpy(frames(h, w, shifts, 600 + i)).cuda()
-        for shape in (1, 2, 3):
+        for shape in (1, 2, 3, 4):
             for dt in (B.MISR_F32, B.MISR_BF16):
                 plan = B.Plan(h, w, f, shifts, psf, iters=4, tile_shape=shape, iterate_dtype=dt)
                 x, _ = plan.solve(y)
                 out[f"{name}_s{shape}_d{dt}"] = x.cpu().numpy()
+                if shape == 4:   # the streaming shape runs the squared L2 term only
+                    plan.close()
+                    continue
                 # the L1 data term's variant (its owned-residual buffer)
                 p1 = B.Plan(h, w, f, shifts, psf, iters=4, tile_shape=shape, iterate_dtype=dt,
                             data_norm=B.MISR_NORM_L1, data_eps=0.05)

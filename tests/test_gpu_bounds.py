@@ -1,6 +1,7 @@
 """The bounds-checked build (libmisr_check.so, compiled with MISR_BOUNDS_CHECK) on the odd
-geometries: every tile shape and storage type, ragged and one-pixel images, frame counts below
-f^2, f = 1, 3 and 4, the gradient and a mixed batch.  No shared-memory item position, global
+geometries: every tile shape, the streaming shape (its item split included) and both storage
+types, ragged and one-pixel images, frame counts below f^2, f = 1, 3 and 4, the gradient and a
+mixed batch.  No shared-memory item position, global
 store, tile or group index or TMA x coordinate may fail its check, and the images must equal
 the normal build's bit for bit (the checks change nothing when they pass).  compute-sanitizer
 is closed on this machine; this build stands in for it."""
