@@ -804,11 +804,9 @@ def main():
 
     peak, peak_kind = load_peaks()
     achieved = PASS_BYTES_PER_PX * H * W / (pass_ms * 1e-3) / 1e9
-    # the L1 data term runs on the tile shapes: MISR_TILE_AUTO takes the fastest the tuning
-    # timed for it (or the fixed --tile-shape when that is a tile shape)
-    tuned_tile = tuned if tuned != 4 else 0
-    l1 = measure_l1(args, wl, shifts, psf, tuned_tile, y, xt, stream, dist, device, peak)
-    paper_ct = measure_paper_ct(args, wl, shifts, tuned_tile, xt, stream, dist, device, peak)
+    # the L1 lines run on the shape tuned for this image size (every shape takes the L1 term)
+    l1 = measure_l1(args, wl, shifts, psf, tuned, y, xt, stream, dist, device, peak)
+    paper_ct = measure_paper_ct(args, wl, shifts, tuned, xt, stream, dist, device, peak)
     subpixel = measure_subpixel(args, wl, xt, stream, dist, device, peak)
     interp = measure_interpolation(args, wl, plan, y, xt, stream, dist, device, peak)
     # the three forms beside their plain counterparts, at sizes that keep the default run

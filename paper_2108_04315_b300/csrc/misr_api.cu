@@ -263,14 +263,14 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 // per-phase taps), and its dynamic shared memory; the per-phase variants exist for the
 // PHASED_SHAPE only
 template <int S, int V>
-constexpr bool compiled_variant() { return S == STREAM_SHAPE ? V < 2 : (V & 4) == 0 || S == PHASED_SHAPE; }
+constexpr bool compiled_variant() { return S == STREAM_SHAPE ? V < 4 : (V & 4) == 0 || S == PHASED_SHAPE; }
 // whether a problem of variant v can run on shape sh
-static bool shape_takes_variant(int sh, int v) { return sh == STREAM_SHAPE ? v < 2 : (v & 4) == 0 || sh == PHASED_SHAPE; }
+static bool shape_takes_variant(int sh, int v) { return sh == STREAM_SHAPE ? v < 4 : (v & 4) == 0 || sh == PHASED_SHAPE; }
 template <int S, int V>
 constexpr auto pass_kernel() {
     static_assert(compiled_variant<S, V>(), "variant not compiled for this shape");
     if constexpr (S == STREAM_SHAPE)
-        return scg_stream_kernel<(V & 1) != 0>;
+        return scg_stream_kernel<(V & 1) != 0, (V & 2) != 0>;
     else
         return scg_pass_kernel<SHAPE_TH[S], SHAPE_TW[S], SHAPE_NT[S], (V & 1) != 0, (V & 2) != 0, (V & 4) != 0>;
 }
@@ -400,6 +400,8 @@ StreamConsts misr_host::stream_consts(const DevProblem &p) {
     }
     k.eps2 = p.eps2;
     k.lambda = p.lambda;
+    k.deps = p.l1 ? p.data_eps : 0.f;
+    k.deps2 = k.deps * k.deps;
     k.f = p.f;
     k.fmag = p.f > 1 ? (unsigned)((0x100000000ull + p.f - 1) / p.f) : 0u;
     return k;
@@ -640,7 +642,7 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
     const int variant = desc_variant(d, hp.phased);
     const int sh = hp.phased ? PHASED_SHAPE : shape >= 0 ? shape : pick_shape(d, variant);
     if (!shape_takes_variant(sh, variant))
-        return fail(MISR_ENOTIMPL, "the streaming pass runs the squared L2 data term with integer shifts only");
+        return fail(MISR_ENOTIMPL, "the streaming pass runs integer shifts only");
     set_shape(hp, sh);
     set_groups(hp);
     return MISR_OK;
@@ -726,12 +728,10 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
                     // a problem alone gets the full grid its items were split for
                     const int grid = run.edge_ctas > 0 ? resident_ctas(sh, v) : pass_grid(sh, v, (run.count + 7) / 8);
                     const int ne = stream_edge_ctas(run, grid);
-                    if (v == 0)
-                        CK(launch_pdl(scg_stream_kernel<false>, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.n_edge,
-                                      run.count, ne, work, mode, alpha, beta, run.k));
-                    else
-                        CK(launch_pdl(scg_stream_kernel<true>, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.n_edge,
-                                      run.count, ne, work, mode, alpha, beta, run.k));
+                    auto kern = v == 0 ? scg_stream_kernel<false, false> : v == 1 ? scg_stream_kernel<true, false>
+                              : v == 2 ? scg_stream_kernel<false, true> : scg_stream_kernel<true, true>;
+                    CK(launch_pdl(kern, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.n_edge, run.count, ne, work, mode,
+                                  alpha, beta, run.k));
                 }
                 continue;
             }

@@ -1,6 +1,6 @@
 // The fused SCG pass as a row-streaming kernel (sm_103a): one warp per work item, its row
-// windows in registers, no block barriers.  Included by misr_device.cuh; it runs the squared-L2,
-// shared-tap problems (integer shifts, point or binned D).
+// windows in registers, no block barriers.  Included by misr_device.cuh; it runs the shared-tap
+// problems (integer shifts, point or binned D) with the squared L2 or the smoothed L1 data term.
 //
 // What one pass computes is the tile kernel's (Algorithm 1's loop body with Moller's curvature
 // taken at the trial point): p = r + beta p_old, x' = x + alpha p, the residual of the
@@ -119,11 +119,14 @@ constexpr uint32_t SW_ROW_BYTES = 4 * SW_WIN;
 constexpr uint32_t SW_STAGE_BYTES = SW_ROWS * SW_ROW_BYTES;
 enum { LR_X = 0, LR_R, LR_PO, LR_Y, LR_R4, LR_PO4 };
 // the ring, per warp after its two stages: w1[slot][dx] (2 slots), w2[slot][dx] (3 slots),
-// bpw[slot] (5 slots), each a row of 32 lanes x 16 bytes.  The slots rotate by step: w1 is read
-// one step after it is written, w2 two steps after, bpw four.
+// bpw[slot] (5 slots) and, for the L1 data term, wd[slot] (5 slots), each a row of 32 lanes x
+// 16 bytes.  The slots rotate by step: w1 is read one step after it is written, w2 two steps
+// after, bpw and wd four.  bpw holds the masked B p of a row (times psi_d''(e') with the L1
+// term), wd the row's psi_d''(e') (0 where unsampled).
 constexpr uint32_t SW_W_SLOT = 3 * SW_ROW_BYTES;
 constexpr uint32_t SW_RING_W1 = 0, SW_RING_W2 = 2 * SW_W_SLOT, SW_RING_BP = 5 * SW_W_SLOT;
-constexpr uint32_t SW_RING_BYTES = SW_RING_BP + SW_U * SW_ROW_BYTES;
+constexpr uint32_t SW_RING_WD = SW_RING_BP + SW_U * SW_ROW_BYTES;
+constexpr uint32_t SW_RING_BYTES = SW_RING_WD + SW_U * SW_ROW_BYTES;
 constexpr uint32_t SW_WARP_BYTES = 2 * SW_STAGE_BYTES + SW_RING_BYTES;
 constexpr size_t SW_SMEM_BYTES = (size_t)(SW_NT / 32) * SW_WARP_BYTES;
 
@@ -281,7 +284,8 @@ __device__ __forceinline__ void rotate_rows(float (*w)[NV]) {
 // window (K = 0; the windows are rotated at the end of the step).  RPB: r and p stored as bf16.
 // EDGE: the path with the frame-mask corrections of the top and left borders (any item);
 // without it, only items whose rows start at 24 or below and whose strip is not the first.
-template <int K, bool RPB, bool EDGE>
+// L1: the smoothed L1 data term psi_d(e) = sqrt(e^2 + eps_d^2) - eps_d instead of e^2.
+template <int K, bool RPB, bool EDGE, bool L1>
 __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &k, const SegGeo &g, int n,
                                             float alpha, float beta, const float *__restrict__ X,
                                             const float *__restrict__ R, const float *__restrict__ PO,
@@ -351,10 +355,14 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
         vscatter_fwd<K, 0, EDGE>(k, S.bpa, h, n);
     }
 
-    // ---- row n-2: residual, J_data, dJ_data and the data part of c; then its adjoint
+    // ---- row n-2: residual, J_data, dJ_data and the data part of c; then its adjoint.  With
+    // the L1 term the adjoint takes psi_d'(e) = e / S(e), S(t) = sqrt(t^2 + eps_d^2), the sums
+    // weigh by psi_d''(e) = eps_d^2 / S(e)^3, J_data sums psi_d(e) = e^2 / (S(e) + eps_d) and
+    // J_data(x') - J_data(x) sums (e'^2 - e^2) / (S(e') + S(e)), so that no term cancels
+    constexpr float DS = L1 ? 1.f : 2.f;   // d/de of the data term's e^2 (L2) or psi_d(e) (L1)
     {
         const int m = n - 2;
-        float cy[4], E[4], bpm[4];
+        float cy[4], E[4], bpm[4], wdm[4];
         read_row4<false>(S.wb, S.cur + LR_Y * SW_ROW_BYTES, cy);
         unsigned bits = 0;
         float jd = 0.f, dj = 0.f, cd = 0.f;
@@ -364,21 +372,38 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
             E[j] = smp ? S.za[sN2][j] - cy[j] : 0.f;
             const float bp = smp ? S.bpa[sN2][j] : 0.f;
             bits |= (smp ? 1u : 0u) << j;
-            bpm[j] = bp;                           // masked B p, for b at row n-2 four steps on
-            jd = fmaf(E[j], E[j], jd);
             const float abp = alpha * bp;
             // e'^2 - e^2 = alpha (B p) (2 e' - alpha (B p)), e the residual at x = x' - alpha p
-            dj = fmaf(abp, fmaf(2.f, E[j], -abp), dj);
-            cd = fmaf(bp, bp, cd);
+            if constexpr (L1) {
+                const float de2 = abp * fmaf(2.f, E[j], -abp);
+                const float q1 = fmaf(E[j], E[j], k.deps2), r1 = rsqrt_ftz(q1);
+                const float eb = E[j] - abp;
+                const float q0 = fmaf(eb, eb, k.deps2), r0 = rsqrt_ftz(q0);
+                jd += __fdividef(E[j] * E[j], fmaf(q1, r1, k.deps));
+                dj += __fdividef(de2, fmaf(q1, r1, q0 * r0));
+                const float er = k.deps * r1;
+                const float w = smp ? r1 * (er * er) : 0.f;   // psi_d''(e'), as (1/S) (eps_d/S)^2
+                const float wbp = w * bp;
+                cd = fmaf(wbp, bp, cd);
+                bpm[j] = wbp;
+                wdm[j] = w;
+                E[j] *= r1;
+            } else {
+                bpm[j] = bp;                       // masked B p, for b at row n-2 four steps on
+                jd = fmaf(E[j], E[j], jd);
+                dj = fmaf(abp, fmaf(2.f, E[j], -abp), dj);
+                cd = fmaf(bp, bp, cd);
+            }
             S.za[sN2][j] = 0.f;
             S.bpa[sN2][j] = 0.f;
         }
         S.mbits = (S.mbits << 4) | bits;
         sts4(S.wb, SW_RING + SW_RING_BP + S.bpo, bpm);
+        if constexpr (L1) sts4(S.wb, SW_RING + SW_RING_WD + S.bpo, wdm);
         if (m >= g.y0 && m < g.ye) {
             S.s[P_JD] += jd;
             S.s[P_DJD] += dj;
-            S.s[P_C] = fmaf(2.f, cd, S.s[P_C]);
+            S.s[P_C] = fmaf(DS, cd, S.s[P_C]);
         }
         float e[8], h[4];
         with_ext(E, e);
@@ -388,7 +413,7 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
             // tap a of output row m - a reads sample row m
             float *ga = S.ga[((K - 2 - a) % SW_U + SW_U) % SW_U];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) ga[j] = fmaf(2.f * k.hy[a + 2], h[j], ga[j]);
+            for (int j = 0; j < 4; ++j) ga[j] = fmaf(DS * k.hy[a + 2], h[j], ga[j]);
         }
         if (EDGE && m < 2 * MAXF) {   // the adjoint's frame masks near the top: dropped when !adj_tap_ok(m - a, a)
 #pragma unroll
@@ -396,7 +421,7 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
                 if (!adj_tap_ok(m - a, a, k.f, k.fmag)) {
                     float *ga = S.ga[((K - 2 - a) % SW_U + SW_U) % SW_U];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) ga[j] = fmaf(-2.f * k.hy[a + 2], h[j], ga[j]);
+                    for (int j = 0; j < 4; ++j) ga[j] = fmaf(-DS * k.hy[a + 2], h[j], ga[j]);
                 }
         }
     }
@@ -513,19 +538,21 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
 
         const int m6 = n - 6;
         const unsigned b6 = (S.mbits >> 16) & 0xfu;   // rows n-6 .. n-2 sit at bits 16 .. 0
-        float ad = 0.f, bd = 0.f, bp6[4];
+        float ad = 0.f, bd = 0.f, bp6[4], wd6[4];
         // row n-6's slot: written four steps ago, the one after this step's (mod 5)
-        lds4(S.wb, SW_RING + SW_RING_BP + (S.bpo == 4 * SW_ROW_BYTES ? 0 : S.bpo + SW_ROW_BYTES), bp6);
+        const uint32_t o6 = S.bpo == 4 * SW_ROW_BYTES ? 0 : S.bpo + SW_ROW_BYTES;
+        lds4(S.wb, SW_RING + SW_RING_BP + o6, bp6);
+        if constexpr (L1) lds4(S.wb, SW_RING + SW_RING_WD + o6, wd6);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float br = ((b6 >> j) & 1u) ? S.bra[sN6][j] : 0.f;
-            ad = fmaf(br, br, ad);
+            ad = L1 ? fmaf(br * wd6[j], br, ad) : fmaf(br, br, ad);
             bd = fmaf(br, bp6[j], bd);
             S.bra[sN6][j] = 0.f;
         }
         if (m6 >= g.y0 && m6 < g.ye) {
-            S.s[P_A] = fmaf(2.f, ad, S.s[P_A]);
-            S.s[P_B] = fmaf(2.f, bd, S.s[P_B]);
+            S.s[P_A] = fmaf(DS, ad, S.s[P_A]);
+            S.s[P_B] = fmaf(DS, bd, S.s[P_B]);
         }
     }
 
@@ -591,7 +618,7 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
 }
 
 // One item: steps n = y0 - 6 .. ye + 5.
-template <bool RPB, bool EDGE>
+template <bool RPB, bool EDGE, bool L1>
 __device__ __forceinline__ void stream_item(StreamState &S, const StreamConsts &k, const SegGeo &g, float alpha,
                                             float beta, const float *__restrict__ X, const float *__restrict__ R,
                                             const float *__restrict__ PO, const float *__restrict__ Y,
@@ -621,7 +648,7 @@ __device__ __forceinline__ void stream_item(StreamState &S, const StreamConsts &
     issue_step_rows<RPB>(g, S.wb, S.cur, n0, X, R, PO, Y);
     const int n_end = g.ye + 6;   // one past the last step
 #pragma unroll 1
-    for (int n = n0; n < n_end; ++n) stream_step<0, RPB, EDGE>(S, k, g, n, alpha, beta, X, R, PO, Y, Xn, Rn, Pn);
+    for (int n = n0; n < n_end; ++n) stream_step<0, RPB, EDGE, L1>(S, k, g, n, alpha, beta, X, R, PO, Y, Xn, Rn, Pn);
 }
 
 // Geometry of item t of problem P (the item order of the problem record: the left strip's
@@ -649,7 +676,7 @@ __device__ __forceinline__ void stream_item_rows(const DevProblem &P, int t, int
 // rest; the interior path takes only the items [n_edge, n_items), from counter work[2].  Every
 // item's ten sums are written as (hi, lo) pairs at its index; reduce_kernel combines them after
 // the pass as it does the tile sums.
-template <bool RPB, bool EDGE>
+template <bool RPB, bool EDGE, bool L1>
 __device__ __forceinline__ void stream_worker(StreamState &S, const DevProblem *__restrict__ probs,
                                               const int2 *__restrict__ items, int n_edge, int n_items,
                                               unsigned *work, int mode, double probe_alpha, double probe_beta,
@@ -696,7 +723,7 @@ __device__ __forceinline__ void stream_worker(StreamState &S, const DevProblem *
 #pragma unroll
         for (int i = 0; i < NPART; ++i) S.s[i] = 0.f;
         S.lo_jb = S.lo_rr = S.lo_rrx = S.lo_pr = 0.f;
-        stream_item<RPB, EDGE>(S, k, g, alpha, beta, P.X[cur], P.Rv[cur], P.Pv[pcur], P.Y, P.X[cur ^ 1],
+        stream_item<RPB, EDGE, L1>(S, k, g, alpha, beta, P.X[cur], P.Rv[cur], P.Pv[pcur], P.Y, P.X[cur ^ 1],
                                P.Rv[cur ^ 1], P.Pv[pcur ^ 1]);
         // the item's sums: lanes outside the owned strip drop theirs; then a fixed-order warp
         // sum of (hi, lo) pairs
@@ -724,8 +751,9 @@ __device__ __forceinline__ void stream_worker(StreamState &S, const DevProblem *
 
 // The streaming pass.  The launch's item list holds its n_edge edge items, then the rest.  CTAs
 // below n_edge_ctas run the edge path, the others the interior path: one CTA per SM, so an SM
-// keeps one path in its instruction cache.
-template <bool RPB>
+// keeps one path in its instruction cache.  RPB: r and p stored as bf16; L1: the smoothed L1
+// data term.
+template <bool RPB, bool L1>
 __global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *__restrict__ probs,
                                                               const int2 *__restrict__ items, int n_edge,
                                                               int n_items, int n_edge_ctas, unsigned *work, int mode,
@@ -739,9 +767,9 @@ __global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *
     S.cur = 0;
     S.nxt = SW_STAGE_BYTES;
     if ((int)blockIdx.x < n_edge_ctas)
-        stream_worker<RPB, true>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k);
+        stream_worker<RPB, true, L1>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k);
     else
-        stream_worker<RPB, false>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k);
+        stream_worker<RPB, false, L1>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k);
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // the last warp to stop zeroes the launch's counters for the next launch

@@ -51,8 +51,7 @@ constexpr int SHAPE_NT[N_SHAPES] = {512, 256, 256, 256};
 constexpr double STREAM_LEFT_COST = 1.45, STREAM_TOP_COST = 1.0;
 // Compiled variants of the fused pass per shape: bit 0 r and p stored as bf16, bit 1 the
 // smoothed L1 data term, bit 2 per-phase blur taps (non-integer shifts; compiled for the
-// 32x32 shape only).  The streaming shape has variants 0 and 1 (squared L2 data term, shared
-// taps).
+// 32x32 shape only).  The streaming shape has variants 0 to 3 (shared taps).
 constexpr int N_VARIANTS = 8;
 constexpr int PHASED_SHAPE = 1;
 // per-phase tap tables of DevProblem::tph: full y taps, y taps of the bilinear's first part
@@ -132,6 +131,7 @@ struct StreamConsts {
     float gam[BTV_W * BTV_W];                     // gamma(dx, dy) at [dy * 3 + dx]
     float lgam[BTV_W * BTV_W];                    // lambda gamma: the psi'' weight of a pair
     float eps2, lambda;
+    float deps, deps2;                            // the L1 data term's smoothing eps_d and eps_d^2
     int f;
     unsigned fmag;                                // ceil(2^32 / f) (0 for f = 1), for c mod f
 };

@@ -49,11 +49,12 @@ def l1_case(orc, name, seed, eps_d, iters=20, lam=0.01, **plan_kw):
     return P, plan, xt, y.astype(np.float32)
 
 
+@pytest.mark.parametrize("shape", [2, 4])   # MISR_TILE_32x32, MISR_TILE_STREAM
 @pytest.mark.parametrize("eps_d", [0.01, 0.1])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_l1_objective_and_gradient(orc, name, eps_d):
+def test_l1_objective_and_gradient(orc, name, eps_d, shape):
     """J(x) = sum psi_d(A_k x - y_k) + lambda BTV(x) and grad J = sum A_k^T psi_d'(.) + lambda grad BTV."""
-    P, plan, xt, y = l1_case(orc, name, 210, eps_d)
+    P, plan, xt, y = l1_case(orc, name, 210, eps_d, tile_shape=shape)
     x = (xt + gen.random_field(xt.shape, 8, -0.2, 0.2)).astype(np.float32)
     J, g = plan.gradient(to_dev(y), to_dev(x))
     Jr, gr = P.gradient(x.astype(np.float64), y.astype(np.float64))
@@ -64,11 +65,12 @@ def test_l1_objective_and_gradient(orc, name, eps_d):
 @pytest.mark.parametrize("name", ["tiny_f2", "ragged_f2_asym", "ragged_f3_k9", "partial_f2_k3", "f1_denoise",
                                   "thin_strip"])
 @pytest.mark.parametrize("alpha,beta", [(0.3, 0.7), (0.0, 0.0), (1.7, 0.05)])
-def test_l1_fused_pass(orc, name, alpha, beta):
+@pytest.mark.parametrize("shape", [2, 4])   # MISR_TILE_32x32, MISR_TILE_STREAM
+def test_l1_fused_pass(orc, name, alpha, beta, shape):
     """One fused SCG pass with the L1 term: r' = -grad J(x') and the sums, the curvature forms
     with the L1 term's Hessian sum_k A_k^T diag(psi_d''(A_k x' - y_k)) A_k + lambda H_BTV(x')."""
     eps_d = 0.02
-    P, plan, xt, y = l1_case(orc, name, 310, eps_d)
+    P, plan, xt, y = l1_case(orc, name, 310, eps_d, tile_shape=shape)
     x = (xt + gen.random_field(xt.shape, 9, -0.1, 0.1)).astype(np.float32)
     r = gen.random_field(xt.shape, 10, -0.3, 0.3).astype(np.float32)
     po = gen.random_field(xt.shape, 11, -0.3, 0.3).astype(np.float32)
@@ -114,9 +116,10 @@ def _decisions_agree(tg, tr):
 
 @pytest.mark.parametrize("name,iters,eps_d", [("tiny_f2", 20, 0.02), ("ragged_f2_asym", 15, 0.05),
                                               ("ragged_f3_k9", 12, 0.02), ("f1_denoise", 12, 0.05)])
-def test_l1_solve_matches_oracle(orc, name, iters, eps_d):
+@pytest.mark.parametrize("shape", [2, 4])   # MISR_TILE_32x32, MISR_TILE_STREAM
+def test_l1_solve_matches_oracle(orc, name, iters, eps_d, shape):
     """SCG with the L1 term from multi-image interpolation: image, objective and decisions."""
-    P, plan, xt, y = l1_case(orc, name, 410, eps_d, iters=iters)
+    P, plan, xt, y = l1_case(orc, name, 410, eps_d, iters=iters, tile_shape=shape)
     y64 = y.astype(np.float64)
     xg, st = plan.solve(to_dev(y))
     xg = xg.cpu().numpy()
@@ -149,7 +152,7 @@ def test_l1_is_robust_to_outliers_where_l2_is_not(orc):
     assert e1 < 0.8 * min(e2.values()), (e1, e2)
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4])
 def test_l1_every_tile_shape(orc, shape):
     P, plan, xt, y = l1_case(orc, "ragged_f2_asym", 610, 0.02, iters=10, tile_shape=shape)
     y64 = y.astype(np.float64)
@@ -159,10 +162,11 @@ def test_l1_every_tile_shape(orc, shape):
     _decisions_agree(plan.trace(), tr)
 
 
-def test_l1_bf16_directions(orc):
+@pytest.mark.parametrize("shape", [2, 4])   # MISR_TILE_32x32, MISR_TILE_STREAM
+def test_l1_bf16_directions(orc, shape):
     """bf16 r and p with the L1 term: the same image and objective bars as the float run."""
     from paper_2108_04315_b300 import binding as B
-    P, plan, xt, y = l1_case(orc, "tiny_f2", 710, 0.05, iters=15, iterate_dtype=B.MISR_BF16)
+    P, plan, xt, y = l1_case(orc, "tiny_f2", 710, 0.05, iters=15, iterate_dtype=B.MISR_BF16, tile_shape=shape)
     y64 = y.astype(np.float64)
     xg, st = plan.solve(to_dev(y))
     xr, _ = P.scg(y64, P.shift_add(y64), 15)
