@@ -110,8 +110,11 @@ enum { MISR_NORM_L2 = 0, MISR_NORM_L1 = 1 };
 /* decimation D (misr_desc.decimation) */
 enum { MISR_DECIM_POINT = 0, MISR_DECIM_BIN = 1 };
 
-/* Tile shapes of the fused pass (HR pixels per CTA tile; threads per CTA).  The paper has no
- * counterpart: its partitions are whole sub-images per GPU (Sec. 3.1). */
+/* Shapes of the fused pass.  MISR_TILE_32x64, _32x32, _16x64: HR pixels per CTA tile of the
+ * persistent tile kernel (every model option).  MISR_TILE_STREAM: the row-streaming kernel, one
+ * warp per strip of 112 HR columns walking its rows (integer shifts, either data term; a plan
+ * with non-integer shifts gets MISR_ENOTIMPL).  The paper has no counterpart: its partitions are
+ * whole sub-images per GPU (Sec. 3.1). */
 enum { MISR_TILE_AUTO = 0, MISR_TILE_32x64 = 1, MISR_TILE_32x32 = 2, MISR_TILE_16x64 = 3, MISR_TILE_STREAM = 4,
        MISR_N_TILE_SHAPES = 4 };
 
