@@ -128,7 +128,11 @@ struct misr_server_s {
     PassSegs live_segs;
     unsigned int *work = nullptr;   // the fused pass's tile counter
     size_t ditems_cap = 0;
-    ScgState *st_host = nullptr;    // page-locked states, one per slot
+    // page-locked states, one per slot, for two ticks: the worker queues tick t + 1 before it
+    // reads tick t's states, so that the GPU does not wait for the host between ticks
+    ScgState *st_host = nullptr;    // [2][cfg.max_slots]
+    cudaEvent_t tick_done[2] = {nullptr, nullptr};
+    cudaStream_t fin_stream = nullptr;   // copies of finished images, beside the next tick
     std::vector<int2> h_items;
     bool items_dirty = true;
     misr_status worker_error = MISR_OK;
@@ -291,11 +295,10 @@ std::vector<int> admit(misr_server_t s) {
     return started;
 }
 
-void finish(misr_server_t s, int idx, misr_status st_code) {
+void finish(misr_server_t s, int idx, const ScgState &h, misr_status st_code) {
     Slot &sl = s->slots[idx];
     std::lock_guard<std::mutex> lock(s->mu);
     Request &rq = s->reqs[sl.ticket];
-    const ScgState &h = s->st_host[idx];
     rq.stats.iters_done = h.iter;
     rq.stats.accepted = h.accepted;
     rq.stats.status = st_code;
@@ -310,11 +313,83 @@ void finish(misr_server_t s, int idx, misr_status st_code) {
     s->items_dirty = true;
 }
 
+// One tick as queued: the slots (and their tickets) whose states it copies to st_host[buf].
+struct TickRecord {
+    std::vector<std::pair<int, uint64_t>> live;
+    int buf = 0;
+};
+
+void fail_queue(misr_server_t s, misr_status r) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->worker_error = r;
+    for (uint64_t t : s->queue) {
+        Request &rq = s->reqs[t];
+        rq.state = RQ_FAILED;
+        rq.status = r;
+        rq.t_end = now_s();
+    }
+    s->queue.clear();
+    s->cv_done.notify_all();
+}
+
+// Completions of a queued tick, once its states have landed: finished slots copy their image
+// out on the second stream (the passes queued after them skip finished problems), cancelled
+// ones are released.  A slot whose ticket changed since the tick was queued is not this
+// tick's to judge.
+misr_status complete_tick(misr_server_t s, const TickRecord &tk, misr_status r) {
+    const ScgState *sth = s->st_host + (size_t)tk.buf * s->cfg.max_slots;
+    std::vector<char> cancelled(s->slots.size(), 0);
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (auto &lt : tk.live)
+            if (s->slots[lt.first].busy && s->slots[lt.first].ticket == lt.second)
+                cancelled[lt.first] = s->reqs[lt.second].cancel;
+    }
+    std::vector<int> done;
+    for (auto &lt : tk.live) {
+        const int i = lt.first;
+        Slot &sl = s->slots[i];
+        if (!sl.busy || sl.ticket != lt.second) continue;
+        sl.passes += std::max(1, s->cfg.passes_per_tick);
+        if (r != MISR_OK || sth[i].done || cancelled[i]) done.push_back(i);
+    }
+    std::vector<misr_status> codes(done.size(), r);
+    bool copies = false;
+    for (size_t d = 0; d < done.size(); ++d) {
+        const int idx = done[d];
+        Slot &sl = s->slots[idx];
+        misr_status &code = codes[d];
+        if (code == MISR_OK && cancelled[idx]) code = MISR_ECANCELED;
+        if (code == MISR_OK && sth[idx].status != DEV_OK) code = MISR_ETIMEOUT;
+        if (code == MISR_OK) {
+            const Request *rq;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                rq = &s->reqs[sl.ticket];
+            }
+            code = launch_finalize_raw(s->dprobs, idx, sl.plan->n, rq->x, s->fin_stream);
+            copies = true;
+        }
+    }
+    if (copies && cudaStreamSynchronize(s->fin_stream) != cudaSuccess) {
+        const misr_status e = fail(MISR_ECUDA, "server copy stream failed");
+        for (auto &c : codes)
+            if (c == MISR_OK) c = e;
+        r = e;
+    }
+    for (size_t d = 0; d < done.size(); ++d) finish(s, done[d], sth[done[d]], codes[d]);
+    if (!done.empty()) s->cv_done.notify_all();
+    return r;
+}
+
 void worker_main(misr_server_t s) {
     cudaSetDevice(s->device);
     const int k_passes = std::max(1, s->cfg.passes_per_tick);
+    TickRecord pending;          // the tick queued last, whose states are not read yet
+    bool have_pending = false;
+    int buf = 0;
     for (;;) {
-        {
+        if (!have_pending) {
             std::unique_lock<std::mutex> lock(s->mu);
             s->cv_work.wait(lock, [&] {
                 if (s->stop || !s->queue.empty()) return true;
@@ -322,9 +397,13 @@ void worker_main(misr_server_t s) {
                     if (sl.busy) return true;
                 return false;
             });
+        }
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
             if (s->stop) break;
         }
-        // 1. admission: prepare + initial pass of each newly admitted projection
+        // 1. admission: prepare + initial pass of each newly admitted projection (queued
+        // behind the pending tick, whose passes skip finished problems)
         std::vector<int> started = admit(s);
         misr_status r = MISR_OK;
         for (int idx : started) {
@@ -340,7 +419,8 @@ void worker_main(misr_server_t s) {
             if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, sl.segs, sl.items + p->hp.n_tiles, p->hp.n_groups,
                                                   s->work, MODE_INIT, 0.0, 0.0, s->stream);
         }
-        // 2. the live slots' tile and group lists
+        // 2. the live slots' tile and group lists (uploaded in stream order, after the
+        // pending tick's passes have read the old ones)
         if (r == MISR_OK && s->items_dirty) {
             s->h_items.clear();
             std::vector<int2> gl;
@@ -362,64 +442,57 @@ void worker_main(misr_server_t s) {
                 r = fail(MISR_ECUDA, "tile list upload failed");
             s->items_dirty = false;
         }
-        // 3. k SCG iterations of every live projection, one launch each
+        // 3. k SCG iterations of every live projection, then their states into this tick's
+        // half of st_host
         const int nt = s->live_tiles;
-        for (int it = 0; it < k_passes && r == MISR_OK && nt > 0; ++it) {
-            r = launch_pass_raw(s->dprobs, s->ditems, s->live_segs, s->ditems + nt, s->live_groups, s->work, MODE_ITER,
-                                0.0, 0.0, s->stream);
-            ++s->passes_launched;
-        }
-        // 4. completion: read the live states, copy finished projections out
-        for (size_t i = 0; i < s->slots.size() && r == MISR_OK; ++i)
-            if (s->slots[i].busy &&
-                cudaMemcpyAsync(&s->st_host[i], s->slots[i].plan->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost,
-                                s->stream) != cudaSuccess)
-                r = fail(MISR_ECUDA, "state copy failed");
-        if (r == MISR_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) r = fail(MISR_ECUDA, "server stream failed");
-        std::vector<int> done;
-        std::vector<char> cancelled(s->slots.size(), 0);
-        {
-            std::lock_guard<std::mutex> lock(s->mu);
-            for (size_t i = 0; i < s->slots.size(); ++i)
-                if (s->slots[i].busy) cancelled[i] = s->reqs[s->slots[i].ticket].cancel;
-        }
-        for (size_t i = 0; i < s->slots.size(); ++i) {
-            Slot &sl = s->slots[i];
-            if (!sl.busy) continue;
-            sl.passes += k_passes;
-            if (r != MISR_OK || s->st_host[i].done || cancelled[i]) done.push_back((int)i);
-        }
-        for (int idx : done) {
-            Slot &sl = s->slots[idx];
-            misr_status code = r;
-            if (code == MISR_OK && cancelled[idx]) code = MISR_ECANCELED;
-            if (code == MISR_OK && s->st_host[idx].status != DEV_OK) code = MISR_ETIMEOUT;
-            if (code == MISR_OK) {
-                const Request *rq;
-                {
-                    std::lock_guard<std::mutex> lock(s->mu);
-                    rq = &s->reqs[sl.ticket];
+        TickRecord tk;
+        tk.buf = buf;
+        if (nt > 0) {
+            for (int it = 0; it < k_passes && r == MISR_OK; ++it) {
+                r = launch_pass_raw(s->dprobs, s->ditems, s->live_segs, s->ditems + nt, s->live_groups, s->work,
+                                    MODE_ITER, 0.0, 0.0, s->stream);
+                ++s->passes_launched;
+            }
+            ScgState *sth = s->st_host + (size_t)buf * s->cfg.max_slots;
+            for (size_t i = 0; i < s->slots.size() && r == MISR_OK; ++i)
+                if (s->slots[i].busy) {
+                    if (cudaMemcpyAsync(&sth[i], s->slots[i].plan->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost,
+                                        s->stream) != cudaSuccess)
+                        r = fail(MISR_ECUDA, "state copy failed");
+                    tk.live.push_back({(int)i, s->slots[i].ticket});
                 }
-                code = launch_finalize_raw(s->dprobs, idx, sl.plan->n, rq->x, s->stream);
-                if (code == MISR_OK && cudaStreamSynchronize(s->stream) != cudaSuccess)
-                    code = fail(MISR_ECUDA, "server stream failed");
-            }
-            finish(s, idx, code);
+            if (r == MISR_OK && cudaEventRecord(s->tick_done[buf], s->stream) != cudaSuccess)
+                r = fail(MISR_ECUDA, "tick event failed");
         }
-        if (!done.empty()) s->cv_done.notify_all();
-        if (r != MISR_OK) {   // the stream is unusable: fail what is queued and stop serving
-            std::lock_guard<std::mutex> lock(s->mu);
-            s->worker_error = r;
-            for (uint64_t t : s->queue) {
-                Request &rq = s->reqs[t];
-                rq.state = RQ_FAILED;
-                rq.status = r;
-                rq.t_end = now_s();
-            }
-            s->queue.clear();
-            s->cv_done.notify_all();
+        // 4. the previous tick's completions, while this one runs
+        if (have_pending) {
+            if (r == MISR_OK && cudaEventSynchronize(s->tick_done[pending.buf]) != cudaSuccess)
+                r = fail(MISR_ECUDA, "server stream failed");
+            r = complete_tick(s, pending, r);
+            have_pending = false;
+        }
+        if (r == MISR_OK && nt > 0) {
+            pending = std::move(tk);
+            have_pending = true;
+            buf ^= 1;
+        } else if (r != MISR_OK && nt > 0) {
+            cudaStreamSynchronize(s->stream);
+            complete_tick(s, tk, r);
+        }
+        if (r != MISR_OK) {   // the stream is unusable: fail what runs and what is queued, stop serving
+            cudaStreamSynchronize(s->stream);
+            cudaGetLastError();
+            const ScgState none{};
+            for (size_t i = 0; i < s->slots.size(); ++i)
+                if (s->slots[i].busy) finish(s, (int)i, none, r);
+            fail_queue(s, r);
             break;
         }
+    }
+    // stopping: let the last queued tick finish before the slots are torn down
+    if (have_pending) {
+        cudaStreamSynchronize(s->stream);
+        complete_tick(s, pending, MISR_OK);
     }
 }
 
@@ -439,10 +512,16 @@ extern "C" misr_status misr_server_create(const misr_server_cfg *cfg, misr_serve
     if (e == cudaSuccess) e = cudaMalloc(&s->dprobs, sizeof(DevProblem) * cfg->max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&s->work, 256);
     if (e == cudaSuccess) e = cudaMemset(s->work, 0, 256);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->st_host, sizeof(ScgState) * cfg->max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->st_host, 2 * sizeof(ScgState) * cfg->max_slots);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->fin_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->tick_done[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         misr_status r = fail(MISR_ENOMEM, "server setup: %s", cudaGetErrorString(e));
+        for (auto &ev : s->tick_done)
+            if (ev) cudaEventDestroy(ev);
+        if (s->fin_stream) cudaStreamDestroy(s->fin_stream);
+        if (s->st_host) cudaFreeHost(s->st_host);
         if (s->stream) cudaStreamDestroy(s->stream);
         if (s->dprobs) cudaFree(s->dprobs);
         if (s->work) cudaFree(s->work);
@@ -473,6 +552,10 @@ extern "C" misr_status misr_server_destroy(misr_server_t s) {
     if (s->dprobs) cudaFree(s->dprobs);
     if (s->work) cudaFree(s->work);
     if (s->st_host) cudaFreeHost(s->st_host);
+    for (auto &ev : s->tick_done)
+        if (ev) cudaEventDestroy(ev);
+    cudaStreamSynchronize(s->fin_stream);
+    cudaStreamDestroy(s->fin_stream);
     cudaStreamDestroy(s->stream);
     delete s;
     return MISR_OK;
