@@ -45,10 +45,8 @@ def run(lib_path):
                 plan = B.Plan(h, w, f, shifts, psf, iters=4, tile_shape=shape, iterate_dtype=dt)
                 x, _ = plan.solve(y)
                 out[f"{name}_s{shape}_d{dt}"] = x.cpu().numpy()
-                if shape == 4:   # the streaming shape runs the squared L2 term only
-                    plan.close()
-                    continue
-                # the L1 data term's variant (its owned-residual buffer)
+                # the L1 data term's variant (its owned-residual buffer; on the streaming shape,
+                # the ring rows of its curvature weights)
                 p1 = B.Plan(h, w, f, shifts, psf, iters=4, tile_shape=shape, iterate_dtype=dt,
                             data_norm=B.MISR_NORM_L1, data_eps=0.05)
                 x1, _ = p1.solve(y)
