@@ -833,7 +833,8 @@ def main():
                      "spec_peak": SPEC_HBM_GBS, "frac_of_spec": achieved / SPEC_HBM_GBS,
                      "algorithmic_bytes_per_launch": PASS_BYTES_PER_PX * H * W,
                      "ms_per_launch": pass_ms,
-                     "timed_as": "one SCG pass: the fused pass kernel and its reduction kernel, "
+                     "timed_as": "one SCG pass (the fused pass kernel with its reduction: in the pass for the "
+                                 "streaming kernel, a reduction kernel after it for the tile shapes), "
                                  "(T(100 it) - T(0 it)) / 100 with CUDA events on the solve's stream"},
         "e2e": e2e,
         "batched": batched,
@@ -842,9 +843,10 @@ def main():
         "subpixel": subpixel,
         "interpolation": interp,
         "forms": forms,
-        # per solve: prepare, the initial pass and every SCG pass (the fused pass kernel and its
-        # reduction kernel), finalize
-        "gpu_launches": args.steps * (2 * wl["iters"] + 4),
+        # per solve: prepare, the initial pass and every SCG pass (the fused pass kernel, and
+        # for the tile shapes its reduction kernel; the streaming pass reduces in the pass),
+        # finalize
+        "gpu_launches": args.steps * ((wl["iters"] + 1) * (1 if tuned == 4 else 2) + 2),
         "tile_shape": {"tuned": shape_name, "threads": nt,
                        "ms_per_pass_by_shape": {shape_label(k): (None if v is None else round(float(v), 5))
                                                 for k, v in zip(sorted(TILE_SHAPES), tune_ms)}},

@@ -465,8 +465,12 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
                     segs.n[sh][v] += recs[i]->n_tiles;
                 }
         }
-    for (size_t i = 0; i < recs.size(); ++i)
+    // the reduction launch's groups: the streaming pass reduces its problems itself
+    for (size_t i = 0; i < recs.size(); ++i) {
+        if (recs[i]->shape == STREAM_SHAPE) continue;
         for (int g = 0; g < recs[i]->n_groups; ++g) groups.push_back(make_int2(idx[i], g));
+        segs.n_reduce += recs[i]->n_groups;
+    }
 }
 
 // The process's tuning: HR image size -> the time per pass misr_autotune measured for each shape
@@ -663,7 +667,7 @@ static PlanLayout plan_layout(const misr_desc &d, const DevProblem &hp) {
     L.o_img = off; off += 3 * L.img + 4 * L.rp_img;
     L.o_part = off; off += align_up((size_t)hp.n_tiles * NPART * sizeof(float2), 256);
     L.o_gpart = off; off += align_up((size_t)hp.n_groups * NPART * sizeof(float2), 256);
-    L.o_cnt = off; off += 256;
+    L.o_cnt = off; off += 1024;   // the group counter, then the per-group item counters
     L.o_work = off; off += 256;
     L.o_st = off; off += align_up(sizeof(ScgState), 256);
     L.o_tr = off; off += align_up((size_t)std::max(d.iters, 1) * TRACE_COLS * sizeof(double), 256);
@@ -749,7 +753,8 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
                 });
             }));
         }
-    CK(launch_pdl(reduce_kernel, n_groups, 32, 0, s, probs, groups, mode));
+    (void)n_groups;   // the list's length is the segments' count
+    if (segs.n_reduce > 0) CK(launch_pdl(reduce_kernel, segs.n_reduce, 32, 0, s, probs, groups, mode));
     return MISR_OK;
 }
 
@@ -833,6 +838,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     hp.partials = (float2 *)(b + o_part);
     hp.gpartials = (float2 *)(b + o_gpart);
     hp.counter = (unsigned int *)(b + o_cnt);
+    hp.gcounter = (unsigned int *)(b + o_cnt + 256);
     p->work = (unsigned int *)(b + o_work);
     hp.st = (ScgState *)(b + o_st);
     hp.trace = (double *)(b + o_tr);
@@ -1302,7 +1308,7 @@ misr_status misr_import_state(misr_plan_t p, const void *buf, size_t bytes) {
     st.iters = p->d.iters;
     st.done = (st.status != 0 || st.iter >= st.iters || !(st.pn2 > 0.0) || !std::isfinite(st.alpha)) ? 1 : 0;
     CK(cudaMemcpy(p->hp.st, &st, sizeof st, cudaMemcpyHostToDevice));
-    CK(cudaMemset(p->hp.counter, 0, sizeof(unsigned int)));
+    CK(cudaMemset(p->hp.counter, 0, 1024));
     CK(cudaMemset(p->work, 0, 4 * sizeof(unsigned int)));
     CK(cudaMemset(p->hp.trace, 0, (size_t)std::max(p->d.iters, 1) * TRACE_COLS * sizeof(double)));
     *p->st_host = st;
@@ -1436,6 +1442,7 @@ misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem 
     hp.partials = reinterpret_cast<float2 *>(base + NA_O_PART);
     hp.gpartials = reinterpret_cast<float2 *>(base + NA_O_GPART);
     hp.counter = reinterpret_cast<unsigned int *>(base + NA_O_CNT);
+    hp.gcounter = nullptr;   // (the allocation-free call runs the tile shape)
     hp.st = reinterpret_cast<ScgState *>(base + NA_O_ST);
     hp.trace = nullptr;
     return make_maps(hp);

@@ -66,6 +66,7 @@ struct StreamRun {
 struct PassSegs {
     int n[misr::N_SHAPES][misr::N_VARIANTS] = {};
     std::vector<StreamRun> runs;
+    int n_reduce = 0;                    // groups of the reduction launch (tile-shape problems)
     int total() const {
         int t = 0;
         for (auto &a : n)

@@ -671,6 +671,53 @@ __device__ __forceinline__ void stream_item_rows(const DevProblem &P, int t, int
     }
 }
 
+// The pass's reduction, in the pass: after item t's sums are written, the warp that completes
+// the item's group sums the group in item order into the group sums, and the warp that
+// completes the problem's last group sums the groups in order and runs the SCG tail.  The sums
+// and their order are reduce_kernel's, so the results are the same bit for bit; what goes is
+// the reduction's launch and its wait for the whole pass.  A group's counter is reset by the
+// warp that completes it, the problem's by the tail.  Not inlined: inlined into the item loop
+// it cost the pass 7% (its registers and code in the loop's way), as a call 0.6% less than the
+// reduction launch.
+__device__ __noinline__ void stream_reduce(const DevProblem &P, int t, int mode) {
+    const int lane = threadIdx.x & 31;
+    const int g = t / P.group;
+    const int gsize = min(P.group, P.n_tiles - g * P.group);
+    // every lane's stores of the item's sums are made visible before the warp counts the item
+    __threadfence();
+    __syncwarp();
+    unsigned old = 0;
+    if (lane == 0) old = atomicAdd(&P.gcounter[g], 1u);
+    old = __shfl_sync(FULL, old, 0);
+    if (old != (unsigned)(gsize - 1)) return;
+    __threadfence();
+    if (lane == 0) P.gcounter[g] = 0u;
+    const float2 v = warp_sum_fields(P.partials + (size_t)g * P.group, P.n_tiles, gsize);
+    const int slot = lane >> 1;
+    if ((lane & 1) == 0 && slot < NPART) P.gpartials[(size_t)slot * P.n_groups + g] = v;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) old = atomicAdd(P.counter, 1u);
+    old = __shfl_sync(FULL, old, 0);
+    if (old != (unsigned)(P.n_groups - 1)) return;
+    __threadfence();
+    ScgState L;
+    load_state(L, P.st);
+    const float2 w = warp_sum_fields(P.gpartials, P.n_groups, P.n_groups);
+    double S[NPART];
+#pragma unroll
+    for (int j = 0; j < NPART; ++j) {
+        const float hi = __shfl_sync(FULL, w.x, 2 * j), lo = __shfl_sync(FULL, w.y, 2 * j);
+        S[j] = (double)hi + (double)lo;
+    }
+    if (lane == 0) {
+        scg_tail_local(P, &L, S, mode);
+        *P.st = L;
+        *P.counter = 0u;
+        __threadfence();
+    }
+}
+
 // One warp's share of the pass: items from the launch's lists until they run out.  The edge
 // path (EDGE) first takes the edge items [0, n_edge) from counter work[0], then helps with the
 // rest; the interior path takes only the items [n_edge, n_items), from counter work[2].  Every
@@ -746,6 +793,7 @@ __device__ __forceinline__ void stream_worker(StreamState &S, const DevProblem *
                 if (lane == i) mine = v[i];
             P.partials[(size_t)lane * P.n_tiles + t] = mine;
         }
+        stream_reduce(P, t, mode);
     }
 }
 

@@ -105,12 +105,16 @@ struct DevProblem {
     float *X[2], *Rv[2], *Pv[2];                  // x, r (double buffered), p (double buffered);
                                                   // Rv, Pv hold __nv_bfloat16 when rp_bf16
     float *Y;                                     // interleaved frames, NaN where unsampled
-    // Fixed-order reduction of a pass's sums: every tile writes its sums; after the pass, one
-    // warp per group of `group` tiles sums the group in tile order, and the warp that finishes
-    // the last group sums the groups in order and runs the SCG tail.  Field-major arrays.
+    // Fixed-order reduction of a pass's sums: every tile writes its sums; one warp per group of
+    // `group` tiles sums the group in tile order, and the warp that finishes the last group sums
+    // the groups in order and runs the SCG tail.  The tile kernel leaves this to reduce_kernel
+    // after the pass; in the streaming pass the warp that completes a group does it.
+    // Field-major arrays.
     float2 *partials;                             // [NPART][n_tiles] tile sums (hi, lo)
     float2 *gpartials;                            // [NPART][n_groups] group sums (hi, lo)
     unsigned int *counter;                        // groups finished in the current pass
+    unsigned int *gcounter;                       // [n_groups] items finished per group (the
+                                                  // streaming pass reduces in the pass itself)
     int group, n_groups;                          // tiles per group, groups
     ScgState *st;
     double *trace;                                // [iters][TRACE_COLS]
