@@ -465,9 +465,16 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
                     segs.n[sh][v] += recs[i]->n_tiles;
                 }
         }
-    // the reduction launch's groups: the streaming pass reduces its problems itself
+    // The reduction.  A step of one streaming launch and nothing else reduces in that launch
+    // (no reduction launch, and the launch's last warps run the tail); a step of several
+    // launches keeps the reduction kernel, which sums every problem's groups in parallel after
+    // the last launch (reduced in each launch, the tails would run one after another).
+    bool others = false;
+    for (size_t i = 0; i < recs.size(); ++i) others |= recs[i]->shape != STREAM_SHAPE;
+    const bool in_pass = !others && segs.runs.size() == 1;
+    if (in_pass) segs.runs[0].reduce_in_pass = true;
     for (size_t i = 0; i < recs.size(); ++i) {
-        if (recs[i]->shape == STREAM_SHAPE) continue;
+        if (in_pass && recs[i]->shape == STREAM_SHAPE) continue;
         for (int g = 0; g < recs[i]->n_groups; ++g) groups.push_back(make_int2(idx[i], g));
         segs.n_reduce += recs[i]->n_groups;
     }
@@ -735,7 +742,7 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
                     auto kern = v == 0 ? scg_stream_kernel<false, false> : v == 1 ? scg_stream_kernel<true, false>
                               : v == 2 ? scg_stream_kernel<false, true> : scg_stream_kernel<true, true>;
                     CK(launch_pdl(kern, grid, SW_NT, SW_SMEM_BYTES, s, probs, t, run.n_edge, run.count, ne, work, mode,
-                                  alpha, beta, run.k));
+                                  alpha, beta, run.k, run.reduce_in_pass ? 1 : 0));
                 }
                 continue;
             }

@@ -61,6 +61,7 @@ struct StreamRun {
     int edge_ctas = 0;                   // planned edge CTAs of a run of one problem, else 0
     double edge_work = 0, int_work = 0;  // row steps of the edge and the other items (edge weighted)
     double edge_ctas_w = 0;              // sum of the problems' planned edge CTAs times their work
+    bool reduce_in_pass = false;         // the launch reduces its problems' sums itself
     misr::StreamConsts k{};
 };
 struct PassSegs {

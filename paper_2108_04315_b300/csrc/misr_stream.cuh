@@ -727,7 +727,7 @@ template <bool RPB, bool EDGE, bool L1>
 __device__ __forceinline__ void stream_worker(StreamState &S, const DevProblem *__restrict__ probs,
                                               const int2 *__restrict__ items, int n_edge, int n_items,
                                               unsigned *work, int mode, double probe_alpha, double probe_beta,
-                                              const StreamConsts &k) {
+                                              const StreamConsts &k, int reduce) {
     const int lane = threadIdx.x & 31;
     bool edge_list = EDGE;
     for (;;) {
@@ -793,20 +793,21 @@ __device__ __forceinline__ void stream_worker(StreamState &S, const DevProblem *
                 if (lane == i) mine = v[i];
             P.partials[(size_t)lane * P.n_tiles + t] = mine;
         }
-        stream_reduce(P, t, mode);
+        if (reduce) stream_reduce(P, t, mode);
     }
 }
 
 // The streaming pass.  The launch's item list holds its n_edge edge items, then the rest.  CTAs
 // below n_edge_ctas run the edge path, the others the interior path: one CTA per SM, so an SM
 // keeps one path in its instruction cache.  RPB: r and p stored as bf16; L1: the smoothed L1
-// data term.
+// data term.  reduce: the launch reduces its problems' sums itself (stream_reduce), else
+// reduce_kernel follows it.
 template <bool RPB, bool L1>
 __global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *__restrict__ probs,
                                                               const int2 *__restrict__ items, int n_edge,
                                                               int n_items, int n_edge_ctas, unsigned *work, int mode,
                                                               double probe_alpha, double probe_beta,
-                                                              const StreamConsts k) {
+                                                              const StreamConsts k, int reduce) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     extern __shared__ __align__(16) unsigned char stream_smem[];   // SW_SMEM_BYTES
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -815,9 +816,9 @@ __global__ void __launch_bounds__(SW_NT, 1) scg_stream_kernel(const DevProblem *
     S.cur = 0;
     S.nxt = SW_STAGE_BYTES;
     if ((int)blockIdx.x < n_edge_ctas)
-        stream_worker<RPB, true, L1>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k);
+        stream_worker<RPB, true, L1>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k, reduce);
     else
-        stream_worker<RPB, false, L1>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k);
+        stream_worker<RPB, false, L1>(S, probs, items, n_edge, n_items, work, mode, probe_alpha, probe_beta, k, reduce);
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // the last warp to stop zeroes the launch's counters for the next launch
