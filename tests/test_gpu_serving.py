@@ -194,3 +194,40 @@ def test_serving_mixes_model_options(orc):
         x, st, _ = srv.wait(t, timeout_s=60.0)
         assert torch.equal(x, xa) and st == sa
     srv.close()
+
+
+def test_serving_streaming_shape_equals_alone(orc):
+    """Requests on the row-streaming shape, served alone (a tick of one slot reduces its sums in
+    the pass) and in a burst (a tick of several launches reduces in the reduction kernel), with
+    the L1 term and bf16 directions among them: each result equals its own misr_solve (which
+    reduces in the pass) bit for bit."""
+    from paper_2108_04315_b300 import binding as B
+    geoms = [(64, 64, 2, gen.half_pixel_shifts(), {}), (40, 120, 2, gen.half_pixel_shifts(), {}),
+             (23, 29, 3, gen.third_pixel_shifts(), {}),
+             (48, 64, 2, gen.half_pixel_shifts(), dict(data_norm=B.MISR_NORM_L1, data_eps=0.05)),
+             (48, 72, 2, gen.half_pixel_shifts(), dict(iterate_dtype=B.MISR_BF16))]
+    ys, alone = [], []
+    for i, (h, w, f, sh, kw) in enumerate(geoms):
+        P, plan, xt, y = make_case(orc, h, w, f, sh, PSF, seed=2600 + i, iters=12, tile_shape=4, **kw)
+        yd = to_dev(y)
+        x, st = plan.solve(yd)
+        ys.append(yd)
+        alone.append((x.clone(), st))
+        plan.close()
+    srv = B.Server(max_slots=8, passes_per_tick=4)
+
+    def submit(i):
+        h, w, f, sh, kw = geoms[i]
+        return srv.submit(ys[i], h, w, f, sh, PSF, iters=12, tile_shape=4, **kw)
+
+    def check(i, t):
+        x, st, _ = srv.wait(t, timeout_s=60.0)
+        assert torch.equal(x, alone[i][0]), f"request {i}: served image differs from misr_solve"
+        assert st == alone[i][1]
+
+    check(0, submit(0))                                   # alone
+    burst = [(i, submit(i)) for i in (1, 2, 3, 4, 0, 3)]  # several slots per tick
+    for i, t in burst:
+        check(i, t)
+    check(4, submit(4))                                   # alone again, a warm slot
+    srv.close()
