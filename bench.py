@@ -66,13 +66,18 @@ def load_traffic(kernel_tag, shape_name):
 
 
 def kernel_source_tag():
-    """Hash of the fused pass's device code (its tile shapes included)."""
+    """Hash of the fused pass's device code (its tile shapes included), comments and blank
+    space left out: a traffic record stays valid across comment edits, not across code ones."""
     import hashlib
+    import re
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2108_04315_b300", "csrc")
     for f in ("misr_types.cuh", "misr_device.cuh", "misr_stream.cuh", "tma.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

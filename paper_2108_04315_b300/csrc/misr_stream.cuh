@@ -29,18 +29,23 @@
 // the end of the step (register moves).  The loop body is one step: an unrolled body kept
 // several copies of the step hot and overflowed the instruction cache.
 //
-// One code path serves every item, the image border included, so that an SM keeps one path in
-// its instruction cache:
+// The image border is handled by the data, on the same code as the interior:
 //   - outside the image x, r, p_old read as 0 (rows and lanes outside the row pitch are
 //     zero-filled by the copies; the pitch's pad columns hold zeros) and Y as NaN ("no sample":
 //     the pads hold NaN, the rest is written so), which is B's zero padding and the data mask;
 //   - r' is set to 0 outside the image;
 //   - the BTV's copy of x' holds SW_BIG outside the image: a pair with one end outside then has
 //     t^2 = +inf, rsqrt = 0, and its psi', psi'' and value t psi' + eps^2 rsqrt are exactly 0,
-//     which drops it as the prior's definition does (only pairs inside the image count);
-//   - the frame masks (B's zero padding in front of the shift M_k, within f + R pixels of the
-//     top and left edges) are subtracted again from the blurs in blocks that only the items at
-//     those edges enter.
+//     which drops it as the prior's definition does (only pairs inside the image count).
+// The frame masks (B's zero padding in front of the shift M_k, within f + R pixels of the top
+// and left edges) are subtracted again from the blurs in correction blocks.  Those are compiled
+// into the edge path only: the items that meet those edges run on the launch's first CTAs with
+// that path, the rest on the others with a path without them (EDGE).  With one CTA per SM, an
+// SM keeps one path in its instruction cache; present but unused, the blocks had cost the
+// interior 20%.
+//
+// The pass's sums are reduced in the pass when its launch is the step's only one
+// (stream_reduce), else by reduce_kernel after it.
 #pragma once
 
 namespace misr {
