@@ -307,8 +307,11 @@ misr_status misr_batch_solve(misr_batch_t batch, const void *const *y_dev, float
  * the HBM budget, and idle slots of other classes are freed to make room.  Every tick runs
  * passes_per_tick fused-pass launches over the tiles of all live slots (one SCG iteration per
  * launch for each), so a request that arrives while others are on the GPU joins the next
- * launch.  Finished projections are copied out and their slots reused.  Each projection keeps
- * its own state and fixed-order reductions: its result is the same alone and in the mix. */
+ * launch.  The worker queues a tick before it reads the states of the previous one, so the GPU
+ * does not wait for the host between ticks.  Finished projections are copied out and their
+ * slots reused.  Each projection keeps its own state and fixed-order reductions: its result is
+ * the same alone and in the mix.  A request's frames are read once, when it is admitted (into
+ * the slot's workspace), and its output is written once, when it finishes. */
 typedef struct misr_server_s *misr_server_t;
 
 typedef struct misr_server_cfg {
@@ -338,11 +341,12 @@ misr_status misr_submit(misr_server_t server, const misr_desc *desc, const void 
  * MISR_EINVAL). */
 misr_status misr_poll(misr_server_t server, uint64_t ticket, misr_stats *stats, double *times);
 
-/* Cancel a request.  Queued: it is dropped at once.  Running: its slot is freed at the end of
- * the worker's current tick (when none of its GPU work is in flight); x_dev is then left as
- * that tick wrote it.  Either way the ticket finishes with MISR_ECANCELED, and its buffers may
- * be released once misr_poll (or misr_server_wait) reports that.  A ticket that already
- * finished keeps its result.  Errors: MISR_EINVAL (NULL server, unknown ticket). */
+/* Cancel a request.  Queued: it is dropped at once.  Running: it stops when the worker reads
+ * the states of the tick in which it sees the cancel; x_dev is not written (passes already
+ * queued may still run on the slot's own workspace, which the request no longer reads or
+ * writes).  Either way the ticket finishes with MISR_ECANCELED, and its buffers may be released
+ * once misr_poll (or misr_server_wait) reports that.  A ticket that already finished keeps its
+ * result.  Errors: MISR_EINVAL (NULL server, unknown ticket). */
 misr_status misr_cancel(misr_server_t server, uint64_t ticket);
 
 /* Wait at most timeout_s seconds for the ticket to finish (then poll it).  MISR_OK when it
