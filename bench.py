@@ -333,6 +333,18 @@ def cpu_baseline(wl):
     out = {"value": 1.0 / per_proj, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"FP64 oracle, full-size problem: init {t0:.2f} s, then {ORACLE_SAMPLE_ITERS} SCG iterations "
                      f"at {t_iter:.2f} s each; projections/s = 1 / (init + {wl['iters']} iterations)"}
+    # the tiny workload end to end (every SCG iteration run, nothing extrapolated)
+    tw = WORKLOADS["tiny"]
+    from oracle import oracle
+    Pt = oracle.Problem(tw["h"], tw["w"], tw["f"], gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), lam=0.01)
+    yt = Pt.forward_all(gen.phantom(Pt.H, Pt.W, tw["seed"])) + gen.gaussian_noise((4, tw["h"], tw["w"]), 0.01,
+                                                                                  tw["seed"] + 1)
+    t = time.perf_counter()
+    Pt.scg(yt, Pt.shift_add(yt), tw["iters"])
+    t_tiny = time.perf_counter() - t
+    out["tiny_end_to_end"] = {"value": 1.0 / t_tiny, "unit": UNIT, "cores": oracle.threads(),
+                              "sample": f"{tw['desc']}: shift-and-add and the full {tw['iters']}-iteration solve, "
+                                        f"{t_tiny * 1e3:.0f} ms"}
     h1, w1 = wl["h"] // 4, wl["w"] // 4
     one = _one_core_timing(h1, w1, wl["f"], wl["seed"], ORACLE_SAMPLE_ITERS)
     if one is not None:
