@@ -118,20 +118,24 @@ struct SegGeo {
 // Input rows of a step, staged in shared memory by cp.async one step ahead: per warp two stages
 // of SW_ROWS rows of 128 floats (bf16 rows use the first 8 bytes of each lane's 16), each lane
 // copying and reading only its own 16 bytes, so no warp synchronisation is needed.  Rows of
-// step n: x(n), r(n), p_old(n), Y(n-2), r(n-4), p_old(n-4).
-constexpr int SW_ROWS = 6;
+// step n: x(n), r(n), p_old(n), Y(n-2).
+constexpr int SW_ROWS = 4;
 constexpr uint32_t SW_ROW_BYTES = 4 * SW_WIN;
 constexpr uint32_t SW_STAGE_BYTES = SW_ROWS * SW_ROW_BYTES;
-enum { LR_X = 0, LR_R, LR_PO, LR_Y, LR_R4, LR_PO4 };
+enum { LR_X = 0, LR_R, LR_PO, LR_Y };
 // the ring, per warp after its two stages: w1[slot][dx] (2 slots), w2[slot][dx] (3 slots),
 // bpw[slot] (5 slots) and, for the L1 data term, wd[slot] (5 slots), each a row of 32 lanes x
 // 16 bytes.  The slots rotate by step: w1 is read one step after it is written, w2 two steps
 // after, bpw and wd four.  bpw holds the masked B p of a row (times psi_d''(e') with the L1
-// term), wd the row's psi_d''(e') (0 where unsampled).
+// term), wd the row's psi_d''(e') (0 where unsampled).  pr and rr (5 slots each) hold p(n) and
+// r(n) of a row (as the pass uses them: rounded to bf16 when r and p are stored so), for the
+// r' stage four steps on.
 constexpr uint32_t SW_W_SLOT = 3 * SW_ROW_BYTES;
 constexpr uint32_t SW_RING_W1 = 0, SW_RING_W2 = 2 * SW_W_SLOT, SW_RING_BP = 5 * SW_W_SLOT;
 constexpr uint32_t SW_RING_WD = SW_RING_BP + SW_U * SW_ROW_BYTES;
-constexpr uint32_t SW_RING_BYTES = SW_RING_WD + SW_U * SW_ROW_BYTES;
+constexpr uint32_t SW_RING_PR = SW_RING_WD + SW_U * SW_ROW_BYTES;
+constexpr uint32_t SW_RING_RR = SW_RING_PR + SW_U * SW_ROW_BYTES;
+constexpr uint32_t SW_RING_BYTES = SW_RING_RR + SW_U * SW_ROW_BYTES;
 constexpr uint32_t SW_WARP_BYTES = 2 * SW_STAGE_BYTES + SW_RING_BYTES;
 constexpr size_t SW_SMEM_BYTES = (size_t)(SW_NT / 32) * SW_WARP_BYTES;
 
@@ -177,8 +181,6 @@ __device__ __forceinline__ void issue_step_rows(const SegGeo &g, unsigned char *
     issue_row<RPB, false>(R, g, n, wb, o + LR_R * SW_ROW_BYTES);
     issue_row<RPB, false>(PO, g, n, wb, o + LR_PO * SW_ROW_BYTES);
     issue_row<false, true>(Y, g, n - 2, wb, o + LR_Y * SW_ROW_BYTES);
-    issue_row<RPB, false>(R, g, n - 4, wb, o + LR_R4 * SW_ROW_BYTES);
-    issue_row<RPB, false>(PO, g, n - 4, wb, o + LR_PO4 * SW_ROW_BYTES);
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
@@ -319,6 +321,12 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
             if (RPB) p[j] = __bfloat162float(__float2bfloat16_rn(p[j]));
             xp[j] = fmaf(alpha, p[j], cx[j]);
         }
+        // p(n) and r(n) for the r' stage of row n four steps on: row n's slot is two after row
+        // n-2's (bpo)
+        uint32_t o = S.bpo + 2 * SW_ROW_BYTES;
+        if (o >= SW_U * SW_ROW_BYTES) o -= SW_U * SW_ROW_BYTES;
+        sts4(S.wb, SW_RING + SW_RING_PR + o, p);
+        sts4(S.wb, SW_RING + SW_RING_RR + o, cr);
     }
     const bool row_n_in = n >= 0 && n < H;
     if (n >= g.y0 && n < g.ye) {
@@ -482,17 +490,18 @@ __device__ __forceinline__ void stream_step(StreamState &S, const StreamConsts &
     float rv[4], p4[4], cr4[4];
     {
         const bool row_in = m >= 0 && m < H;
-        float cpo4[4];
-        read_row4<RPB>(S.wb, S.cur + LR_R4 * SW_ROW_BYTES, cr4);
-        read_row4<RPB>(S.wb, S.cur + LR_PO4 * SW_ROW_BYTES, cpo4);
+        {   // p and r of row m = n-4 as step m stored them (row m's slot: three after bpo)
+            uint32_t o = S.bpo + 3 * SW_ROW_BYTES;
+            if (o >= SW_U * SW_ROW_BYTES) o -= SW_U * SW_ROW_BYTES;
+            lds4(S.wb, SW_RING + SW_RING_PR + o, p4);
+            lds4(S.wb, SW_RING + SW_RING_RR + o, cr4);
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float r = -fmaf(k.lambda, S.gr[sN4][j], S.ga[sN4][j]);
             if (!(row_in && g.in(j))) r = 0.f;
             if (RPB) r = __bfloat162float(__float2bfloat16_rn(r));
             rv[j] = r;
-            p4[j] = fmaf(beta, cpo4[j], cr4[j]);
-            if (RPB) p4[j] = __bfloat162float(__float2bfloat16_rn(p4[j]));
             S.ga[sN4][j] = 0.f;
         }
 #pragma unroll
