@@ -357,7 +357,8 @@ misr_status misr_server_wait(misr_server_t server, uint64_t ticket, double timeo
  * out[4] fused-pass launches so far. */
 misr_status misr_server_counters(misr_server_t server, int64_t *out);
 
-/* Autotuner of the tile shape.  Times `passes` fused passes of every compiled tile shape on the
+/* Autotuner of the pass's shape.  Times `passes` fused passes of every compiled shape that can
+ * run the descriptor (the three tile shapes and, for integer shifts, the streaming one) on the
  * geometry of `desc` (on zeroed device buffers it allocates and frees), and remembers the
  * fastest for plans of the same HR size created with tile_shape = MISR_TILE_AUTO in this
  * process.  shape_out (may be NULL): the chosen MISR_TILE_*; ms_out (may be NULL): the time per
