@@ -111,3 +111,26 @@ def test_streaming_item_split_matches_the_oracle(orc, name):
     assert rel_l2(xs.cpu().numpy(), xr) <= RTOL_X
     plan.close()
     tile.close()
+
+
+def test_streaming_batch_mixing_variants_equals_each_alone(orc):
+    """A batch of streaming-shape problems with the L1 term, bf16 directions and the L2 term
+    (one launch per variant group, the reduction kernel after them) gives each projection its
+    own solve (whose single launch reduces in the pass) bit for bit."""
+    from paper_2108_04315_b300 import binding as B
+    psf = gen.gaussian_psf(5, 0.5)
+    variants = [dict(), dict(data_norm=B.MISR_NORM_L1, data_eps=0.02), dict(iterate_dtype=B.MISR_BF16),
+                dict(data_norm=B.MISR_NORM_L1, data_eps=0.05, iterate_dtype=B.MISR_BF16), dict()]
+    plans, ys = [], []
+    for i, kw in enumerate(variants):
+        h, w = 36 + 8 * i, 60 + 20 * i
+        P = orc.Problem(h, w, 2, gen.half_pixel_shifts(), psf, lam=0.01)
+        y = P.forward_all(gen.phantom(2 * h, 2 * w, 80 + i)) + gen.gaussian_noise((4, h, w), 0.01, 90 + i)
+        plans.append(B.Plan(h, w, 2, gen.half_pixel_shifts(), psf, lam=0.01, iters=10, tile_shape=4, **kw))
+        ys.append(to_dev(y.astype(np.float32)))
+    alone = [p.solve(y)[0].clone() for p, y in zip(plans, ys)]
+    batch = B.Batch(plans)
+    xs, _ = batch.solve(ys)
+    for i, (a, b) in enumerate(zip(alone, xs)):
+        assert torch.equal(a, b), f"projection {i} ({variants[i]})"
+    batch.close()
