@@ -3,7 +3,7 @@ configuration bench.py times (its tile shape tuned first): the forward operator 
 gradient over the whole image, a short solve, the full 100-iteration solve against the
 oracle's committed run (tests/golden/detector_100it.json, written by
 tests/golden/make_golden.py from oracle calls alone) and a live 20-iteration solve element by
-element, against the FP64 oracle."""
+element, against the FP64 oracle; and the precision workload's size (u16 counts -> 6144^2)."""
 import json
 
 import numpy as np
@@ -143,4 +143,25 @@ def test_full_size_interpolation_is_the_oracle_bitwise(detector):
     plan = B.Plan(h, w, f, sh, psf, lam=0.01, iters=1)
     xi = plan.interpolate(to_dev(y)).cpu().numpy()
     assert np.array_equal(xi, P.shift_add(y.astype(np.float64)).astype(np.float32))
+    plan.close()
+
+
+def test_precision_size_gradient_against_oracle(orc):
+    """The precision workload's size (4 x 3072^2 u16 counts -> 6144^2 HR) on the shape its plans
+    get by default: the device's log conversion and the gradient over the whole image against
+    the FP64 oracle's (its items split into four waves of edge items and one of interior)."""
+    from paper_2108_04315_b300 import binding as B
+    h = w = 3072
+    f, sh, psf, i0 = 2, gen.half_pixel_shifts(), gen.gaussian_psf(5, 0.5), 40000.0
+    seed = gen.CONFIG_SEEDS["precision"]
+    P = orc.Problem(h, w, f, sh, psf, lam=0.01)
+    xt = gen.phantom(f * h, f * w, seed)
+    counts = gen.poisson_counts(P.forward_all(xt), i0, seed + 1)
+    y64 = orc.log_convert(counts, i0)
+    plan = B.Plan(h, w, f, sh, psf, lam=0.01, iters=1, in_dtype=B.MISR_U16, flat_field=i0)
+    x = (xt + 0.05 * gen.smooth_field(f * h, f * w, 73)).astype(np.float32)
+    J, g = plan.gradient(to_dev(counts.view(np.int16)), to_dev(x))
+    Jr, gr = P.gradient(x.astype(np.float64), y64)
+    assert rel_l2(g.cpu().numpy(), gr) <= RTOL_OP
+    assert J == pytest.approx(Jr, rel=RTOL_J)
     plan.close()
