@@ -1,7 +1,8 @@
 """Checkpoint and resume: a solve stopped after N1 iterations, exported, imported into a plan of
 the same geometry with N iterations and resumed, gives the image, statistics and trace of one
-uninterrupted N-iteration solve bit for bit (float and bf16 directions, two tile shapes), and the
-checkpoint survives a solve of other data on the plan in between.  Malformed checkpoints fail
+uninterrupted N-iteration solve bit for bit (float and bf16 directions, two tile shapes and the
+streaming one), and the checkpoint survives a solve of other data on the plan in between.
+Malformed checkpoints fail
 with a status."""
 import numpy as np
 import pytest
@@ -15,7 +16,7 @@ torch = pytest.importorskip("torch")
 PSF = gen.gaussian_psf(5, 0.5)
 
 
-@pytest.mark.parametrize("iterate,tile_shape", [("f32", 2), ("bf16", 2), ("f32", 3)])
+@pytest.mark.parametrize("iterate,tile_shape", [("f32", 2), ("bf16", 2), ("f32", 3), ("f32", 4), ("bf16", 4)])
 def test_resume_equals_uninterrupted(orc, iterate, tile_shape):
     from paper_2108_04315_b300 import binding as B
     dt = B.MISR_BF16 if iterate == "bf16" else B.MISR_F32
