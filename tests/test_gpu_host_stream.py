@@ -25,9 +25,9 @@ def _pinned(a):
     return t, t.numpy()
 
 
-@pytest.mark.parametrize("n", [1, 2, 5])
-def test_stream_equals_one_at_a_time(orc, n):
-    P, plan, ys = _frames(orc, n)
+@pytest.mark.parametrize("n,shape", [(1, 0), (2, 0), (5, 0), (3, 4)])   # 4: MISR_TILE_STREAM
+def test_stream_equals_one_at_a_time(orc, n, shape):
+    P, plan, ys = _frames(orc, n, tile_shape=shape)
     H, W = plan.H, plan.W
     alone = []
     for y in ys:
