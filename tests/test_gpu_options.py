@@ -21,20 +21,21 @@ OPTIONS = [
 ]
 
 
-def case(orc, opt, seed, iters=10):
+def case(orc, opt, seed, iters=10, shape=0):
     from paper_2108_04315_b300 import binding as B
     lam, w_, a_, eps = opt
     h, w, f, shifts, psf = 37, 53, 2, gen.half_pixel_shifts(), asym_separable_psf(3)
     P = orc.Problem(h, w, f, shifts, psf, lam=lam, btv_alpha=a_, btv_w=w_, eps=eps)
     xt = gen.phantom(f * h, f * w, seed)
     y = (P.forward_all(xt) + gen.gaussian_noise((4, h, w), 0.01, seed + 1)).astype(np.float32)
-    plan = B.Plan(h, w, f, shifts, psf, lam=lam, btv_alpha=a_, btv_w=w_, eps=eps, iters=iters)
+    plan = B.Plan(h, w, f, shifts, psf, lam=lam, btv_alpha=a_, btv_w=w_, eps=eps, iters=iters, tile_shape=shape)
     return P, plan, xt, y
 
 
+@pytest.mark.parametrize("shape", [0, 4])   # the size default (tiles) and MISR_TILE_STREAM
 @pytest.mark.parametrize("opt", OPTIONS, ids=[f"lam{o[0]}_w{o[1]}_a{o[2]}_eps{o[3]}" for o in OPTIONS])
-def test_prior_options_gradient_and_pass(orc, opt):
-    P, plan, xt, y = case(orc, opt, 100)
+def test_prior_options_gradient_and_pass(orc, opt, shape):
+    P, plan, xt, y = case(orc, opt, 100, shape=shape)
     x = (xt + gen.random_field(xt.shape, 9, -0.1, 0.1)).astype(np.float32)
     J, g = plan.gradient(to_dev(y), to_dev(x))
     Jr, gr = P.gradient(x.astype(np.float64), y.astype(np.float64))
@@ -53,9 +54,10 @@ def test_prior_options_gradient_and_pass(orc, opt):
         assert abs(S[k] - v) <= RTOL_OP * abs(v) + slack, (k, S[k], v)
 
 
+@pytest.mark.parametrize("shape", [0, 4])
 @pytest.mark.parametrize("opt", OPTIONS, ids=[f"lam{o[0]}_w{o[1]}_a{o[2]}_eps{o[3]}" for o in OPTIONS])
-def test_prior_options_solve(orc, opt):
-    P, plan, xt, y = case(orc, opt, 200, iters=10)
+def test_prior_options_solve(orc, opt, shape):
+    P, plan, xt, y = case(orc, opt, 200, iters=10, shape=shape)
     y64 = y.astype(np.float64)
     xg, st = plan.solve(to_dev(y))
     xr, tr = P.scg(y64, P.shift_add(y64), 10)
