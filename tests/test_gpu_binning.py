@@ -58,10 +58,11 @@ def test_binned_objective_and_gradient(orc, name):
 
 @pytest.mark.parametrize("name", ["ct_f2_psf3", "f3_delta_k9", "f2_asym3_partial"])
 @pytest.mark.parametrize("l1_eps", [None, 0.05])
-def test_binned_fused_pass(orc, name, l1_eps):
+@pytest.mark.parametrize("shape", [0, 4])   # the size default (tiles) and MISR_TILE_STREAM
+def test_binned_fused_pass(orc, name, l1_eps, shape):
     """One fused pass with binning: r' and the ten sums, curvature forms included."""
     alpha, beta = 0.3, 0.7
-    P, plan, xt, y = binned_case(orc, name, 300, l1_eps=l1_eps)
+    P, plan, xt, y = binned_case(orc, name, 300, l1_eps=l1_eps, tile_shape=shape)
     x = (xt + gen.random_field(xt.shape, 9, -0.1, 0.1)).astype(np.float32)
     r = gen.random_field(xt.shape, 10, -0.3, 0.3).astype(np.float32)
     po = gen.random_field(xt.shape, 11, -0.3, 0.3).astype(np.float32)
@@ -94,8 +95,9 @@ def test_binned_fused_pass(orc, name, l1_eps):
 
 
 @pytest.mark.parametrize("name,iters", [("ct_f2_psf3", 20), ("f3_delta_k9", 12), ("f2_delta", 15)])
-def test_binned_solve_matches_oracle(orc, name, iters):
-    P, plan, xt, y = binned_case(orc, name, 400, iters=iters)
+@pytest.mark.parametrize("shape", [0, 4])
+def test_binned_solve_matches_oracle(orc, name, iters, shape):
+    P, plan, xt, y = binned_case(orc, name, 400, iters=iters, tile_shape=shape)
     y64 = y.astype(np.float64)
     xg, st = plan.solve(to_dev(y))
     xr, tr = P.scg(y64, P.shift_add(y64), iters)

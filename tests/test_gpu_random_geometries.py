@@ -75,3 +75,9 @@ def test_random_geometry_matches_oracle(orc, seed):
     assert J == pytest.approx(Jr, rel=RTOL_J), d
     assert rel_l2(g.cpu().numpy(), gr) <= tol, d
     plan.close()
+    if not d["frac"]:   # integer shifts: the streaming shape too
+        plan = B.Plan(d["h"], d["w"], d["f"], d["shifts"], d["psf"], tile_shape=B.MISR_TILE_STREAM, **kw_p)
+        J, g = plan.gradient(to_dev(y), to_dev(x))
+        assert J == pytest.approx(Jr, rel=RTOL_J), d
+        assert rel_l2(g.cpu().numpy(), gr) <= tol, d
+        plan.close()
