@@ -97,8 +97,7 @@ static misr_status validate(const misr_desc *d) {
     if (!d) return fail(MISR_EINVAL, "desc is NULL");
     if (d->lr_h < 1 || d->lr_w < 1) return fail(MISR_EINVAL, "lr_h, lr_w must be >= 1");
     if (d->factor < 1 || d->factor > MAXF) return fail(MISR_EINVAL, "factor must be in [1, %d]", MAXF);
-    if (d->K < 1 || d->K > d->factor * d->factor || d->K > MAXK)
-        return fail(MISR_EINVAL, "K must be in [1, factor^2]");
+    if (d->K < 1 || d->K > MAXK) return fail(MISR_EINVAL, "K must be in [1, %d]", MAXK);
     if ((int64_t)d->factor * d->lr_h > (1 << 20) || (int64_t)d->factor * d->lr_w > (1 << 20))
         return fail(MISR_EINVAL, "HR image side above 2^20");
     if (!d->shifts) return fail(MISR_EINVAL, "shifts is NULL");
@@ -126,34 +125,42 @@ static misr_status validate(const misr_desc *d) {
     return MISR_OK;
 }
 
-// Separable PSF taps.  h = u v^T with sum h = 1 implies h = rowsum colsum^T, so the PSF is
-// accepted when it equals the outer product of its row and column sums.
-// With binning, D B is one blur: per axis, (D_bin B z)(i) = (1/f) sum_{a'<f} (B z)(f i + a') =
-// sum_c h'(c) z(f i - c) with h'(c) = (1/f) sum_{a'=0}^{f-1} h(c + a'), c in [-R-f+1, R]; the
-// tap masks of the frames (B's zero padding in front of M_k: the input pixel f i - c >= 0) are
-// those of the point-sampled blur with h' in place of h.  hy, hx receive the taps at [c + R]
-// (c in [-PSF_R, PSF_R], 0 outside the blur); *lowest the lowest tap c with a weight.
-static misr_status psf_taps(const misr_desc *d, double *hy, double *hx, int *lowest) {
-    const int S = d->psf_size, R = S / 2;
+// The PSF normalised to sum 1 as its row sums rs and column sums cs.  h = u v^T with sum h = 1
+// implies h = rs cs^T, so the PSF is accepted when it equals the outer product of its row and
+// column sums.
+static misr_status psf_factors(const misr_desc &d, std::vector<double> &rs, std::vector<double> &cs) {
+    const int S = d.psf_size;
     double sum = 0;
-    for (int i = 0; i < S * S; ++i) sum += d->psf[i];
+    for (int i = 0; i < S * S; ++i) sum += d.psf[i];
     if (!(sum > 0)) return fail(MISR_EINVAL, "PSF must have a positive sum");
-    std::vector<double> h(S * S), rs(S, 0.0), cs(S, 0.0);
+    std::vector<double> h(S * S);
+    rs.assign(S, 0.0);
+    cs.assign(S, 0.0);
     double hmax = 0;
-    for (int i = 0; i < S * S; ++i) { h[i] = d->psf[i] / sum; hmax = std::max(hmax, std::fabs(h[i])); }
+    for (int i = 0; i < S * S; ++i) { h[i] = d.psf[i] / sum; hmax = std::max(hmax, std::fabs(h[i])); }
     for (int a = 0; a < S; ++a)
         for (int b = 0; b < S; ++b) { rs[a] += h[a * S + b]; cs[b] += h[a * S + b]; }
     for (int a = 0; a < S; ++a)
         for (int b = 0; b < S; ++b)
             if (std::fabs(h[a * S + b] - rs[a] * cs[b]) > 1e-6 * hmax)
                 return fail(MISR_EINVAL, "PSF is not separable");
+    return MISR_OK;
+}
+
+// Separable taps of the fused passes.  With binning, D B is one blur: per axis, (D_bin B z)(i) =
+// (1/f) sum_{a'<f} (B z)(f i + a') = sum_c h'(c) z(f i - c) with h'(c) = (1/f) sum_{a'=0}^{f-1}
+// h(c + a'), c in [-R-f+1, R]; the tap masks of the frames (B's zero padding in front of M_k:
+// the input pixel f i - c >= 0) are those of the point-sampled blur with h' in place of h.
+// hy, hx receive the taps at [c + R] (c in [-PSF_R, PSF_R], 0 outside the blur); *lowest the
+// lowest tap c with a weight.  The caller has checked that the taps fit (R + f - 1 <= PSF_R
+// with binning).
+static void psf_taps(const misr_desc *d, const std::vector<double> &rs, const std::vector<double> &cs, double *hy,
+                     double *hx, int *lowest) {
+    const int S = d->psf_size, R = S / 2;
     for (int i = 0; i < 2 * PSF_R + 1; ++i) { hy[i] = 0.0; hx[i] = 0.0; }
     *lowest = -R;
     if (d->decimation == MISR_DECIM_BIN && d->factor > 1) {
         const int f = d->factor;
-        if (R + f - 1 > PSF_R)
-            return fail(MISR_ENOTIMPL, "binning at factor %d with a %dx%d PSF spans %d taps per axis; %d are compiled",
-                        f, S, S, S + f - 1, 2 * PSF_R + 1);
         for (int c = -R - f + 1; c <= R; ++c) {
             double sy = 0, sx = 0;
             for (int a2 = 0; a2 < f; ++a2)
@@ -162,44 +169,64 @@ static misr_status psf_taps(const misr_desc *d, double *hy, double *hx, int *low
             hx[c + PSF_R] = sx / f;
         }
         *lowest = -R - f + 1;
-        return MISR_OK;
+        return;
     }
     for (int a = -R; a <= R; ++a) { hy[a + PSF_R] = rs[a + R]; hx[a + PSF_R] = cs[a + R]; }
-    return MISR_OK;
 }
 
 // The frames' geometry and the blur taps of a descriptor into the problem record.
-// An HR shift t = f s is split per axis into t = n + a, n = floor(t) in [0, f - 1], 0 <= a < 1
-// (t within 1e-4 of an integer is that integer).  The frame's samples sit at HR pixels
-// f (i, j) + (n_y, n_x): one frame per phase (n_y, n_x).  A non-integer t is bilinear
-// interpolation, (M x)(u) = (1 - a) x(u + n) + a x(u + n + 1), so per axis the frame's blur
-// is h_k(c) = (1 - a) h(c) + a h(c + 1), c in [lowest - 1, R], over x at s - c for a sample at
-// s.  At the top / left border the second part of the tap c = f i (s - c = n) reads B's input
-// pixel -1, which B's zero padding drops: that tap weighs (1 - a) h(c) alone.  The taps of a
-// frame must depend on one axis's phase only (a product lattice of shifts, as x and y stages
-// give): a_y per row phase, a_x per column phase.  phased = 1 when some a is not 0.
+// An HR shift t = f s (t within 1e-4 of an integer is that integer) is split per axis into
+// t = n + a, n = floor(t), 0 <= a < 1.  A non-integer t is bilinear interpolation,
+// (M x)(u) = (1 - a) x(u + n) + a x(u + n + 1).
+//
+// Interleaved frames (the fused passes): every n in [0, f - 1], one frame per phase (n_y, n_x),
+// so the frame's samples sit at HR pixels f (i, j) + (n_y, n_x).  Per axis a frame's blur is
+// then h_k(c) = (1 - a) h(c) + a h(c + 1), c in [lowest - 1, R], over x at s - c for a sample
+// at s; at the top / left border the second part of the tap c = f i (s - c = n) reads B's
+// input pixel -1, which B's zero padding drops: that tap weighs (1 - a) h(c) alone.  The taps
+// of a frame must depend on one axis's phase only (a product lattice of shifts, as x and y
+// stages give): a_y per row phase, a_x per column phase.  phased = 1 when some a is not 0.
+// The combined taps must fit the compiled 2 PSF_R + 1.
+//
+// Any other frame set runs the frame-wise pass (general = 1): ty, tx hold n (any sign), gfy,
+// gfx the fractional parts, and the tap tables are built by gen_tables.
+// HR shift of frame k (within 1e-4 of an integer: that integer)
+static void hr_shift(const misr_desc &d, int k, double *ty, double *tx) {
+    *tx = (double)d.factor * d.shifts[2 * k];
+    *ty = (double)d.factor * d.shifts[2 * k + 1];
+    if (std::fabs(*tx - std::floor(*tx + 0.5)) <= 1e-4) *tx = std::floor(*tx + 0.5);
+    if (std::fabs(*ty - std::floor(*ty + 0.5)) <= 1e-4) *ty = std::floor(*ty + 0.5);
+}
 static misr_status setup_geometry(const misr_desc &d, DevProblem &hp) {
     const int f = d.factor;
     for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
+    std::vector<double> rs, cs;
+    misr_status s = psf_factors(d, rs, cs);
+    if (s != MISR_OK) return s;
     double ay[MAXF], ax[MAXF];
     bool sy[MAXF] = {}, sx[MAXF] = {};
     for (int i = 0; i < MAXF; ++i) ay[i] = ax[i] = 0.0;
-    bool frac_y = false, frac_x = false;
+    bool frac_y = false, frac_x = false, interleaved = true, any_frac = false;
+    double tys[MAXK], txs[MAXK];
     for (int k = 0; k < d.K; ++k) {
-        double tx = (double)f * d.shifts[2 * k], ty = (double)f * d.shifts[2 * k + 1];
+        double tx, ty;
+        hr_shift(d, k, &ty, &tx);
         if (!std::isfinite(tx) || !std::isfinite(ty)) return fail(MISR_EINVAL, "frame %d: shift is not finite", k);
-        if (std::fabs(tx - std::floor(tx + 0.5)) <= 1e-4) tx = std::floor(tx + 0.5);
-        if (std::fabs(ty - std::floor(ty + 0.5)) <= 1e-4) ty = std::floor(ty + 0.5);
-        if (tx < 0 || tx >= f || ty < 0 || ty >= f)
-            return fail(MISR_EINVAL, "frame %d: shift must lie in [0, 1) LR px", k);
+        if (std::fabs(tx) > (double)(1 << 20) || std::fabs(ty) > (double)(1 << 20))
+            return fail(MISR_EINVAL, "frame %d: shift beyond 2^20 HR px", k);
+        tys[k] = ty;
+        txs[k] = tx;
+        any_frac |= tx != std::floor(tx) || ty != std::floor(ty);
+        if (!interleaved) continue;
+        if (tx < 0 || tx >= f || ty < 0 || ty >= f) { interleaved = false; continue; }
         const int nx = (int)std::floor(tx), ny = (int)std::floor(ty);
         const double fx = tx - nx, fy = ty - ny;
         const int ph = ny * f + nx;
-        if (hp.frame_of_phase[ph] >= 0)
-            return fail(MISR_EINVAL, "frames %d and %d sample the same HR phase", hp.frame_of_phase[ph], k);
-        if ((sy[ny] && std::fabs(ay[ny] - fy) > 1e-6) || (sx[nx] && std::fabs(ax[nx] - fx) > 1e-6))
-            return fail(MISR_ENOTIMPL, "frame %d: non-integer shifts must form a product lattice (one fractional y "
-                                       "shift per HR row phase, one x shift per column phase)", k);
+        if (hp.frame_of_phase[ph] >= 0 || (sy[ny] && std::fabs(ay[ny] - fy) > 1e-6) ||
+            (sx[nx] && std::fabs(ax[nx] - fx) > 1e-6)) {
+            interleaved = false;
+            continue;
+        }
         sy[ny] = sx[nx] = true;
         ay[ny] = fy; ax[nx] = fx;
         frac_y |= fy != 0.0;
@@ -207,19 +234,43 @@ static misr_status setup_geometry(const misr_desc &d, DevProblem &hp) {
         hp.frame_of_phase[ph] = k;
         hp.ty[k] = ny; hp.tx[k] = nx;
     }
+    // the combined taps of the fused passes: binning widens the blur by f - 1, a non-integer
+    // shift by 1
+    const int R = d.psf_size / 2;
+    const int lowest = d.decimation == MISR_DECIM_BIN && f > 1 ? -R - f + 1 : -R;
+    if (interleaved && lowest - ((frac_y || frac_x) ? 1 : 0) < -PSF_R) interleaved = false;
+    if (!interleaved) {
+        if (d.iterate_dtype == MISR_BF16)
+            return fail(MISR_ENOTIMPL, "frames that do not interleave into one HR image (several frames per phase, "
+                                       "shifts outside [0, 1) LR px or off a product lattice, or a combined blur "
+                                       "wider than %d taps) run the frame-wise pass, which keeps r and p in float",
+                        2 * PSF_R + 1);
+        hp.general = 1;
+        hp.phased = 0;
+        for (int i = 0; i < MAXF * MAXF; ++i) hp.frame_of_phase[i] = -1;
+        for (int k = 0; k < d.K; ++k) {
+            const double fy = std::floor(tys[k]), fx = std::floor(txs[k]);
+            hp.ty[k] = (int)fy;
+            hp.tx[k] = (int)fx;
+            hp.gfy[k] = (float)(tys[k] - fy);
+            hp.gfx[k] = (float)(txs[k] - fx);
+            hp.gfy0[k] = (float)(1.0 - (tys[k] - fy));
+            hp.gfx0[k] = (float)(1.0 - (txs[k] - fx));
+        }
+        const int nb = d.decimation == MISR_DECIM_BIN ? f : 1;
+        hp.g_r = R;
+        hp.g_tw = nb + 2 * R + (any_frac ? 1 : 0);
+        return MISR_OK;
+    }
+    hp.general = 0;
     double hy[2 * PSF_R + 1], hx[2 * PSF_R + 1];
-    int lowest = 0;
-    misr_status s = psf_taps(&d, hy, hx, &lowest);
-    if (s != MISR_OK) return s;
+    int low = 0;
+    psf_taps(&d, rs, cs, hy, hx, &low);
     for (int i = 0; i < 2 * PSF_R + 1; ++i) { hp.hy[i] = (float)hy[i]; hp.hx[i] = (float)hx[i]; }
     hp.phased = frac_y || frac_x;
     if (!hp.phased) return MISR_OK;
-    if (lowest - 1 < -PSF_R)
-        return fail(MISR_ENOTIMPL, "non-integer shifts widen the blur by one tap per axis: with this PSF%s it spans "
-                                   "%d taps, %d are compiled (use a 3x3 PSF)",
-                    d.decimation == MISR_DECIM_BIN ? " and binning" : "", PSF_R - lowest + 2, 2 * PSF_R + 1);
     if (d.tile_shape != MISR_TILE_AUTO && d.tile_shape - 1 != PHASED_SHAPE)
-        return fail(MISR_ENOTIMPL, "non-integer shifts run on the 32x32 tile shape only");
+        return fail(MISR_ENOTIMPL, "non-integer shifts on a product lattice run on the 32x32 tile shape only");
     for (int p = 0; p < f; ++p) {
         hp.ay[p] = (float)ay[p];
         hp.ax[p] = (float)ax[p];
@@ -237,6 +288,47 @@ static misr_status setup_geometry(const misr_desc &d, DevProblem &hp) {
             hp.tph[TPH_AFY][p][c + PSF_R] = hp.tph[TPH_FY][q][c + PSF_R];
             hp.tph[TPH_AFX][p][c + PSF_R] = hp.tph[TPH_FX][q][c + PSF_R];
         }
+    return MISR_OK;
+}
+
+// Tap tables of the frame-wise pass, per axis (Eq. 1 with the readings of B, D and M_k): for
+// LR index i of frame k, T[k][i][a' - a + q + R] accumulates h(a) w_q / nb over the block
+// offsets a' < nb (nb = f with binning, else 1), the PSF taps a in [-R, R] whose input pixel
+// s = f i + a' - a lies inside the grid, and the bilinear parts q in {0, 1} with weights
+// (1 - frac, frac) whose x pixel s + n + q lies inside the grid (n = floor of the HR shift).
+// Computed in FP64 and rounded once.
+static void gen_axis_table(int n_lr, int f, int HR, int nb, int R, const std::vector<double> &h1, int n, double frac,
+                           int tw, float *T) {
+    std::vector<double> acc(tw);
+    for (int i = 0; i < n_lr; ++i) {
+        std::fill(acc.begin(), acc.end(), 0.0);
+        for (int a2 = 0; a2 < nb; ++a2)
+            for (int a = -R; a <= R; ++a) {
+                const long s = (long)f * i + a2 - a;
+                if (s < 0 || s >= HR) continue;
+                for (int q = 0; q < 2; ++q) {
+                    const double wq = q ? frac : 1.0 - frac;
+                    const long u = s + n + q;
+                    if (wq == 0.0 || u < 0 || u >= HR) continue;
+                    acc[a2 - a + q + R] += h1[a + R] * wq / nb;
+                }
+            }
+        for (int t = 0; t < tw; ++t) T[(size_t)i * tw + t] = (float)acc[t];
+    }
+}
+static misr_status gen_tables(const misr_desc &d, const DevProblem &hp, std::vector<float> &Ty, std::vector<float> &Tx) {
+    std::vector<double> rs, cs;
+    misr_status s = psf_factors(d, rs, cs);
+    if (s != MISR_OK) return s;
+    const int f = d.factor, nb = d.decimation == MISR_DECIM_BIN ? f : 1, tw = hp.g_tw, R = hp.g_r;
+    Ty.assign((size_t)d.K * hp.h * tw, 0.f);
+    Tx.assign((size_t)d.K * hp.w * tw, 0.f);
+    for (int k = 0; k < d.K; ++k) {
+        double ty, tx;
+        hr_shift(d, k, &ty, &tx);
+        gen_axis_table(hp.h, f, hp.H, nb, R, rs, hp.ty[k], ty - std::floor(ty), tw, Ty.data() + (size_t)k * hp.h * tw);
+        gen_axis_table(hp.w, f, hp.W, nb, R, cs, hp.tx[k], tx - std::floor(tx), tw, Tx.data() + (size_t)k * hp.w * tw);
+    }
     return MISR_OK;
 }
 
@@ -447,7 +539,7 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
                 // the launch's last items straggled); smaller ones share launches
                 const long grid_warps = 8L * resident_ctas(STREAM_SHAPE, v);
                 for (size_t i = 0; i < recs.size(); ++i) {
-                    if (recs[i]->shape != sh || pass_variant(*recs[i]) != v) continue;
+                    if (recs[i]->general || recs[i]->shape != sh || pass_variant(*recs[i]) != v) continue;
                     const bool alone = 2L * recs[i]->n_tiles >= grid_warps;
                     if (!run.empty()) {
                         const StreamConsts a = stream_consts(*recs[run[0]]), b = stream_consts(*recs[i]);
@@ -460,7 +552,7 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
                 continue;
             }
             for (size_t i = 0; i < recs.size(); ++i)
-                if (recs[i]->shape == sh && pass_variant(*recs[i]) == v) {
+                if (!recs[i]->general && recs[i]->shape == sh && pass_variant(*recs[i]) == v) {
                     append_tiles(*recs[i], idx[i], tiles);
                     segs.n[sh][v] += recs[i]->n_tiles;
                 }
@@ -470,11 +562,20 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
     // launches keeps the reduction kernel, which sums every problem's groups in parallel after
     // the last launch (reduced in each launch, the tails would run one after another).
     bool others = false;
-    for (size_t i = 0; i < recs.size(); ++i) others |= recs[i]->shape != STREAM_SHAPE;
+    for (size_t i = 0; i < recs.size(); ++i) {
+        others |= recs[i]->general || recs[i]->shape != STREAM_SHAPE;
+        if (recs[i]->general) {
+            GenRun g;
+            g.pidx = idx[i];
+            g.ctas = recs[i]->g_ctas;
+            g.l1 = recs[i]->l1 != 0;
+            segs.gen.push_back(g);
+        }
+    }
     const bool in_pass = !others && segs.runs.size() == 1;
     if (in_pass) segs.runs[0].reduce_in_pass = true;
     for (size_t i = 0; i < recs.size(); ++i) {
-        if (in_pass && recs[i]->shape == STREAM_SHAPE) continue;
+        if (in_pass && !recs[i]->general && recs[i]->shape == STREAM_SHAPE) continue;
         for (int g = 0; g < recs[i]->n_groups; ++g) groups.push_back(make_int2(idx[i], g));
         segs.n_reduce += recs[i]->n_groups;
     }
@@ -650,6 +751,17 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
         }
     hp.eps_pairs = d.eps * eps_pairs;
     hp.rp_bf16 = d.iterate_dtype == MISR_BF16;
+    if (hp.general) {
+        // the frame-wise pass: GEN_TILES kernels' CTAs of g_ctas each (the last one 2 g_ctas),
+        // at least 8 elements per thread of the larger of the HR image and the frames, at most
+        // 8 CTAs of 256 threads per SM of a 148-SM GPU
+        const size_t n_max = std::max((size_t)hp.H * hp.W, (size_t)d.K * hp.h * hp.w);
+        set_shape(hp, DEFAULT_SHAPE);
+        hp.g_ctas = (int)std::min<size_t>(148 * 8, std::max<size_t>(1, (n_max + 2047) / 2048));
+        hp.n_tiles = GEN_TILES * hp.g_ctas;
+        set_groups(hp);
+        return MISR_OK;
+    }
     const int variant = desc_variant(d, hp.phased);
     const int sh = hp.phased ? PHASED_SHAPE : shape >= 0 ? shape : pick_shape(d, variant);
     if (!shape_takes_variant(sh, variant))
@@ -661,9 +773,11 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
 
 // Byte offsets of a plan's workspace (one allocation): X[2], Y (float), R[2], P[2] (float or
 // bf16) | tile and group sums, group counters, pass counter, launch tile counter | state |
-// trace | problem | tile list | group list.
+// trace | problem | tile list | group list | frame-wise pass only: the frames, the per-sample
+// buffers DS psi_d'(e'), A_k p and psi_d''(e'), the tap tables.
 struct PlanLayout {
     size_t img, rp_img, o_img, o_part, o_gpart, o_cnt, o_work, o_st, o_tr, o_pr, o_tm, o_gl, total;
+    size_t lr, o_gy, o_ge, o_gap, o_gw, o_gty, o_gtx;
 };
 static PlanLayout plan_layout(const misr_desc &d, const DevProblem &hp) {
     PlanLayout L{};
@@ -681,6 +795,15 @@ static PlanLayout plan_layout(const misr_desc &d, const DevProblem &hp) {
     L.o_pr = off; off += align_up(sizeof(DevProblem), 256);
     L.o_tm = off; off += align_up((size_t)hp.n_tiles * sizeof(int2), 256);
     L.o_gl = off; off += align_up((size_t)hp.n_groups * sizeof(int2), 256);
+    if (hp.general) {
+        L.lr = align_up((size_t)d.K * hp.h * hp.w * sizeof(float), 256);
+        L.o_gy = off; off += L.lr;
+        L.o_ge = off; off += L.lr;
+        L.o_gap = off; off += L.lr;
+        L.o_gw = off; off += hp.l1 ? L.lr : 0;
+        L.o_gty = off; off += align_up((size_t)d.K * hp.h * hp.g_tw * sizeof(float), 256);
+        L.o_gtx = off; off += align_up((size_t)d.K * hp.w * hp.g_tw * sizeof(float), 256);
+    }
     L.total = off;
     return L;
 }
@@ -698,11 +821,7 @@ int misr_host::grid_for(size_t n, int threads) {
 
 static misr_status launch_prepare(misr_plan_t p, const void *y_dev, const float *x_given, int flags,
                                   cudaStream_t s) {
-    const float log_i0 = p->d.in_dtype == MISR_U16 ? logf(p->d.flat_field) : 0.f;
-    prepare_kernel<<<grid_for(p->n_pitched, 256), 256, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, x_given,
-                                                       p->d.x0_mode, flags);
-    CK(cudaGetLastError());
-    return MISR_OK;
+    return launch_prepare_raw(p->dprob, 0, p->hp, p->d, y_dev, x_given, p->d.x0_mode, flags, s);
 }
 
 // Edge CTAs of a streaming launch: the split planned for a problem alone, or for several
@@ -726,6 +845,16 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
     if (segs.total() <= 0) return MISR_OK;
     misr_status r = set_pass_attrs();
     if (r != MISR_OK) return r;
+    // frame-wise problems: their four kernels each, one after the other
+    for (const GenRun &g : segs.gen) {
+        gen_pass_a<<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+        if (g.l1) gen_pass_b<true><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+        else gen_pass_b<false><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+        gen_pass_c<<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+        if (g.l1) gen_pass_d<true><<<2 * g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+        else gen_pass_d<false><<<2 * g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+        CK(cudaGetLastError());
+    }
     int off = 0;
     for (int sh = 0; sh < N_SHAPES; ++sh)
         for (int v = 0; v < N_VARIANTS; ++v) {
@@ -765,12 +894,19 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
     return MISR_OK;
 }
 
-misr_status misr_host::launch_prepare_raw(const DevProblem *probs, int pidx, const misr_desc &d, size_t n_pitched,
+misr_status misr_host::launch_prepare_raw(const DevProblem *probs, int pidx, const DevProblem &hp, const misr_desc &d,
                                           const void *y_dev, const float *x_given, int x0_mode, int flags,
                                           cudaStream_t s) {
     const float log_i0 = d.in_dtype == MISR_U16 ? logf(d.flat_field) : 0.f;
-    prepare_kernel<<<grid_for(n_pitched, 256), 256, 0, s>>>(probs, pidx, y_dev, d.in_dtype, log_i0, x_given, x0_mode,
-                                                            flags);
+    const size_t n_pitched = (size_t)hp.H * hp.pitch;
+    if (hp.general) {
+        const size_t n = std::max(n_pitched, (size_t)hp.K * hp.h * hp.w);
+        gen_prepare_kernel<<<grid_for(n, GEN_NT), GEN_NT, 0, s>>>(probs, pidx, y_dev, d.in_dtype, log_i0, x_given,
+                                                                  x0_mode, flags);
+    } else {
+        prepare_kernel<<<grid_for(n_pitched, 256), 256, 0, s>>>(probs, pidx, y_dev, d.in_dtype, log_i0, x_given,
+                                                                x0_mode, flags);
+    }
     CK(cudaGetLastError());
     return MISR_OK;
 }
@@ -794,11 +930,11 @@ extern "C" {
 
 const char *misr_version(void) {
 #ifdef MISR_BOUNDS_CHECK
-    return "misr-b300 0.4 (sm_103a, fused SCG pass: row-streaming warps, or persistent TMA-fed tiles 32x64, 32x32, "
-           "16x64; bounds-checked)";
+    return "misr-b300 0.5 (sm_103a, fused SCG pass: row-streaming warps, or persistent TMA-fed tiles 32x64, 32x32, "
+           "16x64; frame-wise pass for any shift set; bounds-checked)";
 #else
-    return "misr-b300 0.4 (sm_103a, fused SCG pass: row-streaming warps, or persistent TMA-fed tiles 32x64, 32x32, "
-           "16x64)";
+    return "misr-b300 0.5 (sm_103a, fused SCG pass: row-streaming warps, or persistent TMA-fed tiles 32x64, 32x32, "
+           "16x64; frame-wise pass for any shift set)";
 #endif
 }
 
@@ -852,6 +988,14 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     p->dprob = (DevProblem *)(b + o_pr);
     p->dtile = (int2 *)(b + o_tm);
     p->dgroup = (int2 *)(b + o_gl);
+    if (hp.general) {
+        hp.Yg = (float *)(b + lay.o_gy);
+        hp.Eg = (float *)(b + lay.o_ge);
+        hp.APg = (float *)(b + lay.o_gap);
+        hp.Wg = hp.l1 ? (float *)(b + lay.o_gw) : nullptr;
+        hp.Ty = (float *)(b + lay.o_gty);
+        hp.Tx = (float *)(b + lay.o_gtx);
+    }
     {
         const misr_status ms = make_maps(hp);
         if (ms != MISR_OK) {
@@ -868,7 +1012,15 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
     do {
         if ((e = cudaMemset(p->ws, 0, off)) != cudaSuccess) break;
         if ((e = cudaMemcpy(p->dprob, &p->hp, sizeof(DevProblem), cudaMemcpyHostToDevice)) != cudaSuccess) break;
-        if ((e = cudaMemcpy(p->dtile, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        if (!tiles.empty() &&
+            (e = cudaMemcpy(p->dtile, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+            break;
+        if (p->hp.general) {
+            std::vector<float> Ty, Tx;
+            if ((rs = gen_tables(d, p->hp, Ty, Tx)) != MISR_OK) break;
+            if ((e = cudaMemcpy(p->hp.Ty, Ty.data(), Ty.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+            if ((e = cudaMemcpy(p->hp.Tx, Tx.data(), Tx.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        }
         if ((e = cudaMemcpy(p->dgroup, groups.data(), groups.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) break;
         if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming)) != cudaSuccess) break;
@@ -926,7 +1078,10 @@ misr_status misr_plan_workspace_bytes(misr_plan_t p, size_t *bytes) {
 misr_status misr_forward(misr_plan_t p, const float *x_dev, float *y_dev, misr_stream_t stream) {
     if (!p || !x_dev || !y_dev) return fail(MISR_EINVAL, "NULL argument");
     DeviceGuard g(p->device);
-    forward_kernel<<<grid_for(p->m_total, 256), 256, 0, (cudaStream_t)stream>>>(p->dprob, 0, x_dev, y_dev);
+    if (p->hp.general)
+        gen_forward_kernel<<<grid_for(p->m_total, GEN_NT), GEN_NT, 0, (cudaStream_t)stream>>>(p->dprob, 0, x_dev, y_dev);
+    else
+        forward_kernel<<<grid_for(p->m_total, 256), 256, 0, (cudaStream_t)stream>>>(p->dprob, 0, x_dev, y_dev);
     CK(cudaGetLastError());
     return MISR_OK;
 }
@@ -949,6 +1104,11 @@ misr_status misr_interpolate(misr_plan_t p, const void *y_dev, float *x_dev, mis
     DeviceGuard g(p->device);
     const float log_i0 = p->d.in_dtype == MISR_U16 ? logf(p->d.flat_field) : 0.f;
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->hp.general) {   // frame-wise problems: each pixel gathers every frame's samples
+        gen_interpolate_kernel<<<grid_for(p->n, GEN_NT), GEN_NT, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, x_dev);
+        CK(cudaGetLastError());
+        return MISR_OK;
+    }
     if (p->hp.phased) {   // non-integer shifts: each pixel gathers its bilinear weights
         interpolate_phased_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, x_dev);
         CK(cudaGetLastError());
@@ -1333,10 +1493,8 @@ misr_status misr_resume(misr_plan_t p, const void *y_dev, float *x_dev, misr_str
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpy(&st, p->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost));
     // the frames again (Y only: no start point, no reset)
-    const float log_i0 = p->d.in_dtype == MISR_U16 ? logf(p->d.flat_field) : 0.f;
-    prepare_kernel<<<grid_for(p->n_pitched, 256), 256, 0, s>>>(p->dprob, 0, y_dev, p->d.in_dtype, log_i0, nullptr,
-                                                               MISR_X0_ZERO, 0);
-    CK(cudaGetLastError());
+    r = launch_prepare_raw(p->dprob, 0, p->hp, p->d, y_dev, nullptr, MISR_X0_ZERO, 0, s);
+    if (r != MISR_OK) return r;
     const int remaining = st.done ? 0 : std::max(st.iters - st.iter, 0);
     for (int done = 0; done < remaining; done += p->chunk_len) CK(cudaGraphLaunch(p->chunk, s));
     finalize_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->dprob, 0, x_dev);
@@ -1439,6 +1597,9 @@ misr_status noalloc_setup(unsigned char **base) {
 misr_status noalloc_problem(const misr_desc &d, unsigned char *base, DevProblem &hp) {
     misr_status s = fill_problem(d, 0, DEFAULT_SHAPE, hp);
     if (s != MISR_OK) return s;
+    if (hp.general)
+        return fail(MISR_ENOTIMPL, "frames that do not interleave into one HR image run the frame-wise pass, whose "
+                                   "frame copies and tap tables need a plan's workspace: use misr_gradient");
     hp.wait_tries = (int)std::min<uint32_t>(g_noalloc_wait_tries.load(), 0x7fffffffu);
     for (int i = 0; i < 2; ++i) {
         hp.X[i] = reinterpret_cast<float *>(base + NA_O_IMG + (0 + i) * NOALLOC_IMG);
@@ -1520,7 +1681,13 @@ extern "C" misr_status misr_autotune(const misr_desc *desc, int32_t passes, int3
         hp.f = desc->factor;
         misr_desc d = *desc;
         d.tile_shape = MISR_TILE_AUTO;
-        if (setup_geometry(d, hp) == MISR_OK && hp.phased) {
+        if (setup_geometry(d, hp) == MISR_OK && hp.general) {   // one frame-wise pass: nothing to choose
+            if (shape_out) *shape_out = MISR_TILE_AUTO;
+            if (ms_out)
+                for (int sh = 0; sh < N_SHAPES; ++sh) ms_out[sh] = 0.0;
+            return MISR_OK;
+        }
+        if (hp.phased) {
             if (shape_out) *shape_out = PHASED_SHAPE + 1;
             if (ms_out)
                 for (int sh = 0; sh < N_SHAPES; ++sh) ms_out[sh] = 0.0;

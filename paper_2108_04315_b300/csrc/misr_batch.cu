@@ -136,7 +136,7 @@ extern "C" misr_status misr_batch_solve(misr_batch_t b, const void *const *y_dev
     if (r != MISR_OK) return r;
     for (int i = 0; i < b->n && r == MISR_OK; ++i) {
         const misr_plan_t p = b->plans[i];
-        r = launch_prepare_raw(b->dprobs, i, p->d, p->n_pitched, y_dev[i], x_dev[i], p->d.x0_mode, 1 | 2 | 4, s);
+        r = launch_prepare_raw(b->dprobs, i, p->hp, p->d, y_dev[i], x_dev[i], p->d.x0_mode, 1 | 2 | 4, s);
     }
     if (r == MISR_OK)
         r = launch_pass_raw(b->dprobs, b->ditems, b->segs, b->ditems + b->total_items,

@@ -1696,3 +1696,4 @@ __global__ void scale_copy_kernel(const T *__restrict__ src, int pitch, float si
 }  // namespace misr
 
 #include "misr_stream.cuh"
+#include "misr_general.cuh"

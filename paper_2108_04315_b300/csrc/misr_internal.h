@@ -64,12 +64,19 @@ struct StreamRun {
     bool reduce_in_pass = false;         // the launch reduces its problems' sums itself
     misr::StreamConsts k{};
 };
+// A problem of the frame-wise pass (frames that do not interleave into one HR image): its
+// kernels run per problem, before the fused launches, and its groups join the reduction.
+struct GenRun {
+    int pidx = 0, ctas = 0;
+    bool l1 = false;
+};
 struct PassSegs {
     int n[misr::N_SHAPES][misr::N_VARIANTS] = {};
     std::vector<StreamRun> runs;
+    std::vector<GenRun> gen;
     int n_reduce = 0;                    // groups of the reduction launch (tile-shape problems)
     int total() const {
-        int t = 0;
+        int t = (int)gen.size();
         for (auto &a : n)
             for (int v : a) t += v;
         return t;
@@ -86,8 +93,9 @@ misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, co
 // launch's record array), ordered by segment, each problem's border tiles first.
 void build_pass_lists(const std::vector<const misr::DevProblem *> &recs, const std::vector<int> &idx,
                       std::vector<int2> &tiles, std::vector<int2> &groups, PassSegs &segs);
-// prepare problem `pidx` of `probs`: interleave frames, start point, reset (flags as prepare_kernel)
-misr_status launch_prepare_raw(const misr::DevProblem *probs, int pidx, const misr_desc &d, size_t n_pitched,
+// prepare problem `pidx` of `probs` (host mirror `hp`): interleave frames (or copy them for the
+// frame-wise pass), start point, reset (flags as prepare_kernel)
+misr_status launch_prepare_raw(const misr::DevProblem *probs, int pidx, const misr::DevProblem &hp, const misr_desc &d,
                                const void *y_dev, const float *x_given, int x0_mode, int flags, cudaStream_t s);
 // copy problem `pidx`'s iterate out (dense H x W)
 misr_status launch_finalize_raw(const misr::DevProblem *probs, int pidx, size_t n, float *out, cudaStream_t s);

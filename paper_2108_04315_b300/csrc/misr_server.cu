@@ -95,6 +95,7 @@ struct Slot {
     uint64_t ticket = 0;
     int passes = 0;        // fused passes run since admission
     int2 *items = nullptr;  // device tile and group lists of this slot alone (for its init pass)
+    int n_list = 0;         // tiles in that list (the groups follow)
     PassSegs segs;
 };
 
@@ -219,6 +220,7 @@ int make_slot(misr_server_t s, const DescCopy &want, misr_status *status) {
     std::vector<int2> t, gl;
     PassSegs segs;
     build_pass_lists({&p->hp}, {idx}, t, gl, segs);
+    const int n_list = (int)t.size();
     t.insert(t.end(), gl.begin(), gl.end());
     int2 *items = nullptr;
     const bool ok2 = cudaMalloc(&items, sizeof(int2) * t.size()) == cudaSuccess &&
@@ -235,6 +237,7 @@ int make_slot(misr_server_t s, const DescCopy &want, misr_status *status) {
     Slot &sl = s->slots[idx];
     sl.plan = p;
     sl.items = items;
+    sl.n_list = n_list;
     sl.segs = std::move(segs);
     sl.desc = want;
     s->slot_bytes += plan_bytes_estimate(d);
@@ -415,8 +418,8 @@ void worker_main(misr_server_t s) {
             }
             misr_plan_t p = sl.plan;
             if (r == MISR_OK)
-                r = launch_prepare_raw(s->dprobs, idx, p->d, p->n_pitched, rq->y, rq->x, p->d.x0_mode, 1 | 2 | 4, s->stream);
-            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, sl.segs, sl.items + p->hp.n_tiles, p->hp.n_groups,
+                r = launch_prepare_raw(s->dprobs, idx, p->hp, p->d, rq->y, rq->x, p->d.x0_mode, 1 | 2 | 4, s->stream);
+            if (r == MISR_OK) r = launch_pass_raw(s->dprobs, sl.items, sl.segs, sl.items + sl.n_list, p->hp.n_groups,
                                                   s->work, MODE_INIT, 0.0, 0.0, s->stream);
         }
         // 2. the live slots' tile and group lists (uploaded in stream order, after the
@@ -445,9 +448,10 @@ void worker_main(misr_server_t s) {
         // 3. k SCG iterations of every live projection, then their states into this tick's
         // half of st_host
         const int nt = s->live_tiles;
+        const bool live = s->live_segs.total() > 0;   // tiles of the fused passes or frame-wise problems
         TickRecord tk;
         tk.buf = buf;
-        if (nt > 0) {
+        if (live) {
             for (int it = 0; it < k_passes && r == MISR_OK; ++it) {
                 r = launch_pass_raw(s->dprobs, s->ditems, s->live_segs, s->ditems + nt, s->live_groups, s->work,
                                     MODE_ITER, 0.0, 0.0, s->stream);
@@ -471,11 +475,11 @@ void worker_main(misr_server_t s) {
             r = complete_tick(s, pending, r);
             have_pending = false;
         }
-        if (r == MISR_OK && nt > 0) {
+        if (r == MISR_OK && live) {
             pending = std::move(tk);
             have_pending = true;
             buf ^= 1;
-        } else if (r != MISR_OK && nt > 0) {
+        } else if (r != MISR_OK && live) {
             cudaStreamSynchronize(s->stream);
             complete_tick(s, tk, r);
         }

@@ -125,7 +125,27 @@ struct DevProblem {
     // (8 floats per phase so that a phase's taps start on a 16-byte boundary)
     float ay[MAXF], ax[MAXF];
     float tph[N_TPH][MAXF][8];
+    // Frame-wise pass (general: the frames do not interleave into one HR image: several frames
+    // on one phase, shifts outside [0, f), shifts off a product lattice, or a combined blur
+    // wider than the compiled taps).  Frame k's operator is separable, A_k = G_y,k (x) G_x,k:
+    // LR sample (i, j) reads x at rows f i + ty[k] - g_r + dy and columns f j + tx[k] - g_r + dx,
+    // dy, dx in [0, g_tw), with weights Ty[k][i][dy] Tx[k][j][dx] that hold B, D, the bilinear
+    // weights of M_k and every mask (ty, tx: the integer parts floor(t) of the HR shifts, any
+    // sign; gfy, gfx: the fractional parts).  Each of the pass's kernels runs g_ctas CTAs (the
+    // last one 2 g_ctas) and writes one tile of sums per CTA: n_tiles = GEN_TILES * g_ctas.
+    int general, g_tw, g_r, g_ctas;
+    float gfy[MAXK], gfx[MAXK];                   // and 1 minus them, each rounded once from FP64
+    float gfy0[MAXK], gfx0[MAXK];
+    float *Yg;                                    // [K][h][w] frames (float; u16 converted)
+    float *Ty, *Tx;                               // [K][h][g_tw], [K][w][g_tw] tap tables
+    float *Eg;                                    // [K][h][w] DS psi_d'(e') of the trial point
+    float *APg;                                   // [K][h][w] A_k p
+    float *Wg;                                    // [K][h][w] psi_d''(e') (L1 data term)
 };
+// taps per axis of a frame's D B M_k at most (binning f, PSF 2 PSF_R + 1, bilinear + 1); tiles
+// of sums per CTA of the frame-wise pass's kernels
+constexpr int GEN_TW = MAXF + 2 * PSF_R + 1;
+constexpr int GEN_TILES = 5;
 
 // Per-launch constants of the streaming pass (every problem of one launch shares them; the
 // host splits launches where they differ).  They are kernel parameters, so the arithmetic

@@ -78,3 +78,48 @@ def make_case(orc, h, w, f, shifts, psf, seed, lam=0.01, eps=1e-3, noise=0.01, i
     P, xt, y32 = oracle_case(orc, h, w, f, shifts, psf, seed, lam=lam, eps=eps, noise=noise)
     plan = Plan(h, w, f, shifts, psf, lam=lam, eps=eps, iters=iters, **plan_kw)
     return P, plan, xt, y32
+
+
+# Frame sets that do not interleave into one HR image (the frame-wise pass): name -> (h, w, f,
+# shifts, psf, decimation: 0 point, 1 binning).  STUDY_SHIFTS: the synthetic study's one-pixel
+# shifts right, down, left and up at 2x (Sec. 4.1.1), two frames on each of two phases.
+STUDY_SHIFTS = [(0.5, 0.0), (0.0, 0.5), (-0.5, 0.0), (0.0, -0.5)]
+GENERAL_CASES = {
+    "study_bin_psf3": (40, 52, 2, STUDY_SHIFTS, gen.gaussian_psf(3, 0.6), 1),
+    "study_point_psf5": (37, 45, 2, STUDY_SHIFTS, gen.gaussian_psf(5, 0.5), 0),
+    "dup_phase_k6": (30, 41, 2, [(0.0, 0.0), (0.5, 0.0), (0.0, 0.5), (0.5, 0.5), (0.0, 0.0), (0.5, 0.5)],
+                     asym_separable_psf(4), 0),
+    "neg_large": (29, 33, 2, [(-0.5, -0.5), (1.0, 0.0), (0.0, 1.5), (0.5, -1.0)], gen.gaussian_psf(5, 0.5), 0),
+    "off_lattice": (31, 27, 2, [(0.0, 0.0), (0.3, 0.0), (0.0, 0.55), (0.45, 0.6)], gen.gaussian_psf(5, 0.5), 0),
+    "off_lattice_bin": (26, 30, 2, [(0.1, 0.2), (0.6, 0.05), (0.35, 0.7), (0.8, 0.9)], gen.gaussian_psf(3, 0.6), 1),
+    "wide_bin_f3": (21, 25, 3, gen.third_pixel_shifts(), gen.gaussian_psf(5, 0.6), 1),
+    "f1_subpixel": (45, 50, 1, [(0.0, 0.0), (0.5, 0.0), (0.0, 0.5), (0.5, 0.5)], gen.gaussian_psf(3, 0.7), 0),
+    "far_shifts": (12, 14, 2, [(0.0, 0.0), (8.0, 0.0), (-3.5, 2.25), (30.0, -30.0)], gen.gaussian_psf(3, 0.6), 0),
+    "thin_strip": (1, 61, 2, STUDY_SHIFTS, gen.gaussian_psf(3, 0.6), 1),
+    "single_pixel": (1, 1, 2, STUDY_SHIFTS, gen.gaussian_psf(5, 0.5), 0),
+}
+# Solves on these geometries (seed GENERAL_SEED): the paper's setting (L1 data term with eps_d
+# 0.01, lambda 0.05, alpha 0.4, 20 iterations, Sec. 4) and the squared L2 term at lambda 0.01
+# for as many iterations as the FP32-state floor allows (tests/test_fp32_sensitivity.py: up to
+# these counts it stays at a fifth of the objective bar and a tenth of the image bar).
+GENERAL_SEED = 400
+GENERAL_PAPER_ITERS = {"study_bin_psf3": 20, "study_point_psf5": 20, "dup_phase_k6": 20, "neg_large": 20,
+                       "off_lattice": 20, "off_lattice_bin": 9, "wide_bin_f3": 20, "f1_subpixel": 20}
+GENERAL_L2_ITERS = {"study_bin_psf3": 7, "study_point_psf5": 7, "dup_phase_k6": 9, "neg_large": 20,
+                    "off_lattice": 20, "off_lattice_bin": 7, "wide_bin_f3": 9, "f1_subpixel": 20}
+PAPER_SETTING = dict(lam=0.05, l1_eps=0.01)
+
+
+def general_case(orc, name, seed, lam=0.01, l1_eps=None, iters=20, noise=0.01, oracle_only=False, **plan_kw):
+    """(oracle problem, GPU plan or None, x_true, y float32) for a frame-wise geometry."""
+    h, w, f, shifts, psf, dec = GENERAL_CASES[name]
+    kw_o = dict(data_norm=orc.NORM_L1, data_eps=l1_eps) if l1_eps else {}
+    P = orc.Problem(h, w, f, shifts, psf, lam=lam, decimation=dec, **kw_o)
+    xt = gen.phantom(f * h, f * w, seed)
+    y = (P.forward_all(xt) + gen.gaussian_noise((len(shifts), h, w), noise, seed + 1)).astype(np.float32)
+    if oracle_only:
+        return P, None, xt, y
+    from paper_2108_04315_b300 import binding as B
+    kw_p = dict(data_norm=B.MISR_NORM_L1, data_eps=l1_eps) if l1_eps else {}
+    plan = B.Plan(h, w, f, shifts, psf, lam=lam, iters=iters, decimation=dec, **kw_p, **plan_kw)
+    return P, plan, xt, y

@@ -57,13 +57,11 @@ def _desc(**kw):
 @pytest.mark.parametrize("kw,status", [
     (dict(factor=0), "EINVAL"),
     (dict(lr_h=0), "EINVAL"),
-    (dict(shifts=[(0.0, 0.0)] * 5), "EINVAL"),                    # K > f^2
-    (dict(shifts=[(0.0, 0.0), (0.0, 0.0)]), "EINVAL"),            # same phase twice
-    (dict(shifts=[(0.25, 0.0)]), "ENOTIMPL"),                     # f*s not an integer, 5x5 PSF: 6 taps
-    (dict(shifts=[(0.0, 0.0), (0.6, 0.0), (0.0, 0.5), (0.55, 0.5)], psf=np.ones((3, 3))), "ENOTIMPL"),  # no lattice
+    (dict(shifts=[(0.0, 0.0)] * 65), "EINVAL"),                   # K > 64
     (dict(shifts=[(0.25, 0.0)], psf=np.ones((3, 3)), tile_shape=1), "ENOTIMPL"),   # per-phase taps: 32x32 only
     (dict(shifts=[(0.0, float("nan"))]), "EINVAL"),
-    (dict(shifts=[(1.0, 0.0)]), "EINVAL"),                        # shift beyond [0, 1-1/f]
+    (dict(shifts=[(0.0, 2.0 ** 20)]), "EINVAL"),                  # shift beyond 2^20 HR px
+    (dict(shifts=[(0.0, 0.0), (0.0, 0.0)], iterate_dtype=2), "ENOTIMPL"),   # frame-wise pass: float r and p
     (dict(psf=np.ones((4, 4))), "EINVAL"),                        # even PSF
     (dict(psf=np.ones((7, 7))), "EINVAL"),                        # PSF larger than 5x5
     (dict(psf=np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1.0]])), "EINVAL"),   # not separable
@@ -79,8 +77,6 @@ def _desc(**kw):
     (dict(data_norm=1, data_eps=1e20), "EINVAL"),
     (dict(data_norm=1, data_eps=float("nan")), "EINVAL"),
     (dict(decimation=2), "EINVAL"),
-    (dict(decimation=1), "ENOTIMPL"),                             # 5x5 PSF binned at f=2: 6 taps
-    (dict(decimation=1, factor=3, shifts=[(0.0, 0.0)], psf=np.ones((3, 3))), "ENOTIMPL"),
 ])
 def test_invalid_descriptor_rejected_on_host(L, kw, status):
     from paper_2108_04315_b300 import binding
@@ -106,3 +102,24 @@ def test_null_arguments_rejected(L):
     assert L.misr_import_state(None, None, 0) == binding.MISR_EINVAL
     assert L.misr_resume(None, None, None, None, None) == binding.MISR_EINVAL
     assert L.misr_plan_destroy(None) == binding.MISR_OK
+
+
+@pytest.mark.parametrize("kw", [
+    dict(shifts=[(0.0, 0.0)] * 5),                                # K > f^2
+    dict(shifts=[(0.0, 0.0), (0.0, 0.0)]),                        # same phase twice
+    dict(shifts=[(0.5, 0.0), (0.0, 0.5), (-0.5, 0.0), (0.0, -0.5)], decimation=1, psf=np.ones((3, 3))),  # the study's
+    dict(shifts=[(0.25, 0.0)]),                                   # f*s not an integer, 5x5 PSF: 6 taps
+    dict(shifts=[(0.0, 0.0), (0.6, 0.0), (0.0, 0.5), (0.55, 0.5)], psf=np.ones((3, 3))),  # off a product lattice
+    dict(shifts=[(1.0, 0.0)]),                                    # shift beyond [0, 1-1/f]
+    dict(decimation=1),                                           # 5x5 PSF binned at f=2: 6 taps
+    dict(decimation=1, factor=3, shifts=[(0.0, 0.0)], psf=np.ones((3, 3))),
+])
+def test_frame_wise_geometries_accepted_on_host(L, kw):
+    """Frame sets the fused passes cannot interleave go to the frame-wise pass: the descriptor
+    checks accept them, and misr_autotune (nothing to choose: one pass kernel) answers
+    MISR_TILE_AUTO before any device work."""
+    from paper_2108_04315_b300 import binding
+    d = _desc(**kw)
+    shape, ms = binding.misr_autotune(d, 1)
+    assert shape == binding.MISR_TILE_AUTO
+    assert not np.any(ms)

@@ -87,3 +87,45 @@ def test_state_rounding_is_a_perturbation_only(orc):
     a, _ = P64.scg(y, x0, 1)
     b, _ = P32.scg(y, x0, 1)
     assert 0 < rel_l2(b, a) <= 1e-6
+
+
+def _general_pair(orc, name, lam, l1_eps):
+    from tests.gpu_common import GENERAL_CASES, GENERAL_SEED, general_case
+    h, w, f, shifts, psf, dec = GENERAL_CASES[name]
+    P64, _, _, y = general_case(orc, name, GENERAL_SEED, lam=lam, l1_eps=l1_eps, oracle_only=True)
+    kw = dict(data_norm=orc.NORM_L1, data_eps=l1_eps) if l1_eps else {}
+    P32 = orc.Problem(h, w, f, shifts, psf, lam=lam, decimation=dec, state_f32=True, **kw)
+    return P64, P32, y.astype(np.float64)
+
+
+def _general_settings():
+    from tests.gpu_common import GENERAL_L2_ITERS, GENERAL_PAPER_ITERS, PAPER_SETTING
+    out = [(n, it, PAPER_SETTING["lam"], PAPER_SETTING["l1_eps"]) for n, it in sorted(GENERAL_PAPER_ITERS.items())]
+    return out + [(n, it, 0.01, None) for n, it in sorted(GENERAL_L2_ITERS.items())]
+
+
+@pytest.mark.parametrize("name,iters,lam,l1_eps", _general_settings())
+def test_fp32_state_floor_frame_wise_geometries(orc, name, iters, lam, l1_eps):
+    """The solve counts of tests/test_gpu_general.py: at every iteration up to them the
+    FP32-state run's objective stays within a fifth of the 1e-5 bar of the FP64 run's (the
+    objective at each iterate, from the two traces), and the final image within a tenth of the
+    1e-3 bar."""
+    P64, P32, y = _general_pair(orc, name, lam, l1_eps)
+    x0 = P64.shift_add(y)
+    a, ta = P64.scg(y, x0, iters)
+    b, tb = P32.scg(y, x0, iters)
+    Ea, Eb = np.append(ta["E"], P64.objective(a, y)), np.append(tb["E"], P64.objective(b, y))
+    assert np.all(np.abs(Eb - Ea) <= RTOL_J / 5 * np.abs(Ea)), (name, np.max(np.abs(Eb - Ea) / np.abs(Ea)))
+    assert rel_l2(b, a) <= 0.1 * RTOL_X
+
+
+def test_fp32_state_floor_rules_out_longer_l2_study_runs(orc):
+    """The synthetic study's geometry with the squared L2 term at lambda 0.01 (two of the four
+    HR phases unsampled with point sampling): 20 iterations move J by more than the 1e-5 bar
+    through FP32 storage alone, which fixes the L2 solve's shorter count; the paper's setting
+    (L1 data term, lambda 0.05) runs the full 20."""
+    P64, P32, y = _general_pair(orc, "study_point_psf5", 0.01, None)
+    x0 = P64.shift_add(y)
+    a, _ = P64.scg(y, x0, 20)
+    b, _ = P32.scg(y, x0, 20)
+    assert abs(P64.objective(b, y) - P64.objective(a, y)) > RTOL_J * abs(P64.objective(a, y))

@@ -95,11 +95,12 @@ def test_serving_errors_and_timeouts():
     from paper_2108_04315_b300 import binding as B
     srv = B.Server(max_slots=2, passes_per_tick=1)
     y = torch.zeros((4, 32, 32), dtype=torch.float32, device="cuda")
-    with pytest.raises(B.MisrError) as e:   # non-integer shifts off a product lattice
-        srv.submit(y, 32, 32, 2, [(0, 0), (0.6, 0), (0, 0.5), (0.55, 0.5)], gen.gaussian_psf(3, 0.5))
+    with pytest.raises(B.MisrError) as e:   # frames off a product lattice (frame-wise pass) with bf16 r, p
+        srv.submit(y, 32, 32, 2, [(0, 0), (0.6, 0), (0, 0.5), (0.55, 0.5)], gen.gaussian_psf(3, 0.5),
+                   iterate_dtype=B.MISR_BF16)
     assert e.value.status == B.MISR_ENOTIMPL
-    with pytest.raises(B.MisrError) as e:   # two frames on one HR phase
-        srv.submit(y, 32, 32, 2, [(0, 0), (0, 0), (0, 0.5), (0.5, 0.5)], PSF)
+    with pytest.raises(B.MisrError) as e:   # a shift that is not finite
+        srv.submit(y, 32, 32, 2, [(0, 0), (0, float("nan")), (0, 0.5), (0.5, 0.5)], PSF)
     assert e.value.status == B.MISR_EINVAL
     with pytest.raises(B.MisrError) as e:   # even PSF size
         srv.submit(y, 32, 32, 2, gen.half_pixel_shifts(), np.full((4, 4), 1 / 16.0), iters=1)

@@ -124,21 +124,24 @@ def test_subpixel_interpolation_and_start_point(orc, name):
     assert np.array_equal(x0.cpu().numpy(), xi)
 
 
-def test_subpixel_rejections():
+def test_subpixel_routing():
+    """Shift sets the per-phase-tap pass cannot take run the frame-wise pass (checked against the
+    oracle in tests/test_gpu_general.py); an explicit tile shape other than 32x32 for a product
+    lattice of non-integer shifts is refused."""
     from paper_2108_04315_b300 import binding as B
     psf3 = gen.gaussian_psf(3, 0.5)
-    with pytest.raises(B.MisrError) as e:              # not a product lattice
-        B.Plan(16, 16, 2, [(0.0, 0.0), (0.55, 0.0), (0.0, 0.5), (0.6, 0.5)], psf3, iters=1)
-    assert e.value.status == B.MISR_ENOTIMPL
-    with pytest.raises(B.MisrError) as e:              # 5x5 PSF: 6 taps with the bilinear
-        B.Plan(16, 16, 2, lattice([0.0, 0.55], [0.0, 0.5]), gen.gaussian_psf(5, 0.5), iters=1)
-    assert e.value.status == B.MISR_ENOTIMPL
+    for sh, psf in (([(0.0, 0.0), (0.55, 0.0), (0.0, 0.5), (0.6, 0.5)], psf3),     # not a product lattice
+                    (lattice([0.0, 0.55], [0.0, 0.5]), gen.gaussian_psf(5, 0.5)),  # 5x5 PSF: 6 taps
+                    ([(1.0, 0.0)], psf3)):                                           # a whole LR pixel
+        assert B.misr_autotune(B.make_desc(16, 16, 2, sh, psf, iters=1), 1)[0] == B.MISR_TILE_AUTO
+        p = B.Plan(16, 16, 2, sh, psf, iters=1)
+        y = torch.zeros((len(sh), 16, 16), dtype=torch.float32, device="cuda")
+        x, st = p.solve(y)
+        assert st["iters_done"] == 0 and not torch.any(x)   # zero frames: the gradient at x_1 = 0 is 0
+        p.close()
     with pytest.raises(B.MisrError) as e:              # per-phase taps on another tile shape
         B.Plan(16, 16, 2, lattice([0.0, 0.55], [0.0, 0.5]), psf3, iters=1, tile_shape=B.MISR_TILE_32x64)
     assert e.value.status == B.MISR_ENOTIMPL
-    with pytest.raises(B.MisrError) as e:              # a shift of a whole LR pixel
-        B.Plan(16, 16, 2, [(1.0, 0.0)], psf3, iters=1)
-    assert e.value.status == B.MISR_EINVAL
 
 
 def test_subpixel_and_integer_in_one_batch_equal_each_alone(orc):
