@@ -51,24 +51,36 @@ enum { MISR_F32 = 0, MISR_U16 = 1, MISR_BF16 = 2 };
 enum {
     MISR_X0_ZERO = 0,       /* x_1 = 0 */
     MISR_X0_SHIFT_ADD = 1,  /* multi-image interpolation (Sec. 4.1.1): each LR sample placed
-                               at the HR pixel it was taken at, 0 where no sample falls */
+                               at the HR pixel it was taken at (spread over the 2 x 2 pixels
+                               around it with the bilinear weights for a non-integer shift),
+                               several samples of one pixel averaged, 0 where none falls */
     MISR_X0_GIVEN = 2       /* x_1 = the caller's x buffer on entry */
 };
 
 /* Problem descriptor, copied by misr_plan_create (the pointers are read only during it). */
 typedef struct misr_desc {
     int32_t lr_h, lr_w;      /* LR frame rows, columns (>= 1) */
-    int32_t K;               /* number of frames, 1 <= K <= factor^2 */
+    int32_t K;               /* number of frames, 1 <= K <= 64 */
     int32_t factor;          /* magnification f, 1 <= f <= 8; HR = f*lr_h x f*lr_w */
-    const float *shifts;     /* host, K pairs (dx, dy) in LR px, f*dx and f*dy in [0, f) (within
-                                1e-4 of an integer counts as that integer).  Their integer parts
-                                are the frame's HR phase, one frame per phase.  Non-integer parts
-                                make M_k a bilinear interpolation (reading of Eq. 1): they must
-                                form a product lattice (one fractional y shift per HR row phase,
-                                one x shift per column phase, as x and y detector stages give),
-                                the blur widens by one tap per axis (a PSF of at most 3x3, or 1x1
-                                with binning at f = 2), and the plan runs the 32x32 tile shape;
-                                else MISR_ENOTIMPL */
+    const float *shifts;     /* host, K pairs (dx, dy) in LR px; the HR shift t = f*s (within 1e-4
+                                of an integer counts as that integer), |t| <= 2^20.  M_k moves
+                                the sampling grid by t, x zero outside the grid; a non-integer t
+                                makes M_k a bilinear interpolation (reading of Eq. 1).
+                                Two passes compute the same model.  The fused passes take frame
+                                sets that interleave into one HR image: every t in [0, f) per
+                                axis, one frame per HR phase floor(t), non-integer parts on a
+                                product lattice (one fractional y shift per HR row phase, one x
+                                shift per column phase, as x and y detector stages give; the
+                                plan then runs the 32x32 tile shape, MISR_ENOTIMPL for another
+                                explicit tile_shape), and a combined D B blur (psf_size, + f - 1
+                                with binning, + 1 for non-integer shifts) of at most 5 taps per
+                                axis.  Every other frame set (several frames on one phase, such
+                                as the synthetic study's one-pixel shifts right, down, left and
+                                up, Sec. 4.1.1; shifts outside [0, f); shifts off a product
+                                lattice; a wider combined blur) runs the frame-wise pass,
+                                whatever tile_shape asks; it keeps r and p in float
+                                (iterate_dtype MISR_BF16: MISR_ENOTIMPL) and has no
+                                allocation-free gradient */
     const float *psf;        /* host, psf_size^2 row-major PSF of B (Eq. 1); must be separable;
                                 normalised to sum 1 by the plan; B is a convolution with it */
     int32_t psf_size;        /* odd, 1..5 */
@@ -100,9 +112,10 @@ typedef struct misr_desc {
     int32_t decimation;      /* MISR_DECIM_POINT (0): D samples HR pixel (f i, f j) of B M_k x.
                                 MISR_DECIM_BIN: D is the mean of the f x f block starting there
                                 (the 2 x 2 binning of the synthetic study, Sec. 4.1.1); D B is
-                                then one blur whose taps span psf_size + f - 1 pixels per axis,
-                                which must fit the compiled 5 (psf_size 3 at f <= 2, psf_size 1
-                                at f <= 3, any PSF at f = 1), else MISR_ENOTIMPL */
+                                then one blur whose taps span psf_size + f - 1 pixels per axis
+                                (the fused passes take at most 5: psf_size 3 at f <= 2,
+                                psf_size 1 at f <= 3, any PSF at f = 1; wider ones run the
+                                frame-wise pass) */
 } misr_desc;
 
 /* data terms (misr_desc.data_norm) */
@@ -113,8 +126,9 @@ enum { MISR_DECIM_POINT = 0, MISR_DECIM_BIN = 1 };
 /* Shapes of the fused pass.  MISR_TILE_32x64, _32x32, _16x64: HR pixels per CTA tile of the
  * persistent tile kernel (every model option).  MISR_TILE_STREAM: the row-streaming kernel, one
  * warp per strip of 112 HR columns walking its rows (integer shifts, either data term; a plan
- * with non-integer shifts gets MISR_ENOTIMPL).  The paper has no counterpart: its partitions are
- * whole sub-images per GPU (Sec. 3.1). */
+ * with non-integer shifts on a product lattice gets MISR_ENOTIMPL).  Frame sets that do not
+ * interleave (misr_desc.shifts) run the frame-wise pass whatever the shape.  The paper has no
+ * counterpart: its partitions are whole sub-images per GPU (Sec. 3.1). */
 enum { MISR_TILE_AUTO = 0, MISR_TILE_32x64 = 1, MISR_TILE_32x32 = 2, MISR_TILE_16x64 = 3, MISR_TILE_STREAM = 4,
        MISR_N_TILE_SHAPES = 4 };
 
@@ -146,7 +160,9 @@ const char *misr_last_error(void);
 
 /* Validate the descriptor and build a plan on the current device: the separable PSF taps,
  * the phase-to-frame table and the device workspace of one solve (7 HR float32 images plus
- * O(tiles) partial sums), allocated here with cudaMalloc.  The plan plays the part of the
+ * O(tiles) partial sums; for the frame-wise pass also a copy of the frames, three per-sample
+ * buffers and the per-frame, per-row tap tables of D B M_k, computed here in FP64), allocated
+ * here with cudaMalloc.  The plan plays the part of the
  * system matrices that the paper builds once per scan and reuses for every rotation angle
  * (Sec. 3.2); no matrix is formed.
  * Errors: MISR_EINVAL (descriptor), MISR_ENOMEM, MISR_ECUDA, MISR_ENOTIMPL. */
@@ -363,8 +379,10 @@ misr_status misr_server_counters(misr_server_t server, int64_t *out);
  * fastest for plans of the same HR size created with tile_shape = MISR_TILE_AUTO in this
  * process.  shape_out (may be NULL): the chosen MISR_TILE_*; ms_out (may be NULL): the time per
  * pass of each shape, MISR_N_TILE_SHAPES values in MISR_TILE_* order.  passes: 1..1000.  A
- * descriptor with non-integer shifts runs on MISR_TILE_32x32 only: that shape is returned at
- * once, nothing is timed or remembered, and ms_out is zeroed.
+ * descriptor with non-integer shifts on a product lattice runs on MISR_TILE_32x32 only: that
+ * shape is returned at once, nothing is timed or remembered, and ms_out is zeroed.  A frame set
+ * that runs the frame-wise pass has no shape to choose: MISR_TILE_AUTO is returned the same way,
+ * before any device work.
  * Errors: MISR_EINVAL (descriptor, passes), MISR_ENOMEM, MISR_ECUDA. */
 misr_status misr_autotune(const misr_desc *desc, int32_t passes, int32_t *shape_out, double *ms_out);
 
@@ -378,7 +396,9 @@ misr_status misr_autotune(const misr_desc *desc, int32_t passes, int32_t *shape_
  * The workspace is a fixed array inside the library, sized for HR images of at most
  * 512 x 512 pixels (about 7 MB, held on every GPU that loads the library until the process
  * exits); larger problems return MISR_EINVAL.  It computes in FP32 only: a descriptor with
- * iterate_dtype other than MISR_F32 returns MISR_EINVAL.  The first call on a device looks up
+ * iterate_dtype other than MISR_F32 returns MISR_EINVAL, and a frame set that runs the
+ * frame-wise pass (misr_desc.shifts: its frame copies and tap tables need a plan's workspace)
+ * MISR_ENOTIMPL.  The first call on a device looks up
  * the array's device address and sets the pass kernel's attributes.  Every call uses the same
  * array, so calls that overlap on the GPU (other streams or host threads) race.  y_dev, x_dev,
  * g_dev as for misr_gradient.

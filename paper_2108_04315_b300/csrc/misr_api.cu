@@ -259,7 +259,11 @@ static misr_status setup_geometry(const misr_desc &d, DevProblem &hp) {
         }
         const int nb = d.decimation == MISR_DECIM_BIN ? f : 1;
         hp.g_r = R;
+        hp.g_nb = nb;
         hp.g_tw = nb + 2 * R + (any_frac ? 1 : 0);
+        // the PSF's factors (the fused passes' tap slots; here they identify the model)
+        for (int i = 0; i < 2 * PSF_R + 1; ++i) hp.hy[i] = hp.hx[i] = 0.f;
+        for (int a = -R; a <= R; ++a) { hp.hy[a + PSF_R] = (float)rs[a + R]; hp.hx[a + PSF_R] = (float)cs[a + R]; }
         return MISR_OK;
     }
     hp.general = 0;
@@ -434,6 +438,14 @@ static misr_status set_pass_attrs() {
             });
             if (r != MISR_OK) return r;
         }
+    // the frame-wise pass's tiles: their shared memory grows with the factor and the taps
+    // (at most GEN_SMEM_MAX bytes, a forward tile of two images at f = MAXF, GEN_TW taps)
+    const int gmax = (int)GEN_SMEM_MAX;
+    CK(cudaFuncSetAttribute(gen_pass_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
+    CK(cudaFuncSetAttribute(gen_pass_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
+    CK(cudaFuncSetAttribute(gen_pass_c, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
+    CK(cudaFuncSetAttribute(gen_pass_d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
+    CK(cudaFuncSetAttribute(gen_pass_d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
     g_pass_dev[dev].attrs = true;
     return MISR_OK;
 }
@@ -568,6 +580,16 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
             GenRun g;
             g.pidx = idx[i];
             g.ctas = recs[i]->g_ctas;
+            g.f = recs[i]->f;
+            g.tw = recs[i]->g_tw;
+            g.K = recs[i]->K;
+            int y0 = recs[i]->ty[0], y1 = y0, x0 = recs[i]->tx[0], x1 = x0;
+            for (int k = 1; k < g.K; ++k) {
+                y0 = std::min(y0, recs[i]->ty[k]); y1 = std::max(y1, recs[i]->ty[k]);
+                x0 = std::min(x0, recs[i]->tx[k]); x1 = std::max(x1, recs[i]->tx[k]);
+            }
+            g.sy = y1 - y0;
+            g.sx = x1 - x0;
             g.l1 = recs[i]->l1 != 0;
             segs.gen.push_back(g);
         }
@@ -756,6 +778,10 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
         // at least 8 elements per thread of the larger of the HR image and the frames, at most
         // 8 CTAs of 256 threads per SM of a 148-SM GPU
         const size_t n_max = std::max((size_t)hp.H * hp.W, (size_t)d.K * hp.h * hp.w);
+        // the kernels index their tiles (at least 256 elements each) in 32 bits
+        if ((size_t)d.K * ((hp.h + 7) / 8) * ((hp.w + 31) / 32) >= (1u << 31) ||
+            (size_t)((hp.H + 15) / 16) * ((hp.W + 31) / 32) >= (1u << 31))
+            return fail(MISR_EINVAL, "frame-wise pass: more than 2^31 tiles");
         set_shape(hp, DEFAULT_SHAPE);
         hp.g_ctas = (int)std::min<size_t>(148 * 8, std::max<size_t>(1, (n_max + 2047) / 2048));
         hp.n_tiles = GEN_TILES * hp.g_ctas;
@@ -847,12 +873,17 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
     if (r != MISR_OK) return r;
     // frame-wise problems: their four kernels each, one after the other
     for (const GenRun &g : segs.gen) {
+        // the union footprint of all frames where it is small, a chunk of frames per adjoint stage
+        const int uni = gen_fwd_union(g.f, g.tw, g.sy, g.sx) ? 1 : 0;
+        const int sy = uni ? g.sy : 0, sx = uni ? g.sx : 0, kc = gen_adj_kc(g.f, g.tw, g.K);
+        const size_t sb = gen_fwd_smem(g.f, g.tw, 2, sy, sx), sd = gen_fwd_smem(g.f, g.tw, 1, sy, sx);
+        const size_t sc = gen_adj_smem(g.f, g.tw, kc);
         gen_pass_a<<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-        if (g.l1) gen_pass_b<true><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-        else gen_pass_b<false><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-        gen_pass_c<<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-        if (g.l1) gen_pass_d<true><<<2 * g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-        else gen_pass_d<false><<<2 * g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+        if (g.l1) gen_pass_b<true><<<g.ctas, GEN_NT, sb, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+        else gen_pass_b<false><<<g.ctas, GEN_NT, sb, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+        gen_pass_c<<<g.ctas, GEN_NT, sc, s>>>(probs, g.pidx, mode, alpha, beta, kc);
+        if (g.l1) gen_pass_d<true><<<2 * g.ctas, GEN_NT, sd, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+        else gen_pass_d<false><<<2 * g.ctas, GEN_NT, sd, s>>>(probs, g.pidx, mode, alpha, beta, uni);
         CK(cudaGetLastError());
     }
     int off = 0;
@@ -1380,7 +1411,7 @@ struct CkptHeader {
     uint32_t magic, version, H, W, bf16, state_bytes, l1, model;
 };
 static_assert(sizeof(CkptHeader) == 32, "checkpoint header");
-constexpr uint32_t CKPT_MAGIC = 0x4353524du, CKPT_VERSION = 2u;
+constexpr uint32_t CKPT_MAGIC = 0x4353524du, CKPT_VERSION = 3u;
 // FNV-1a hash of the model a state belongs to: frames and shifts, blur taps (with binning and
 // per-phase taps folded in), the prior's and the data term's constants.  A checkpoint resumes
 // only on a plan of the same model (the iteration count may differ).
@@ -1398,6 +1429,14 @@ uint32_t model_hash(const DevProblem &hp) {
     mix(hp.hy, sizeof hp.hy);
     mix(hp.hx, sizeof hp.hx);
     mix(&hp.phased, sizeof hp.phased);
+    mix(&hp.general, sizeof hp.general);
+    if (hp.general) {   // the frame-wise pass: fractional shifts, D's block, the tap window
+        mix(hp.gfy, sizeof(float) * hp.K);
+        mix(hp.gfx, sizeof(float) * hp.K);
+        mix(&hp.g_nb, sizeof hp.g_nb);
+        mix(&hp.g_r, sizeof hp.g_r);
+        mix(&hp.g_tw, sizeof hp.g_tw);
+    }
     if (hp.phased) {
         mix(hp.ay, sizeof hp.ay);
         mix(hp.ax, sizeof hp.ax);

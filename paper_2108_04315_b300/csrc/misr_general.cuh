@@ -33,6 +33,16 @@ constexpr int GEN_NT = 256;
 
 // floor(a / f) for f > 0 and any sign of a
 __device__ __forceinline__ int gen_floordiv(int a, int f) { return a >= 0 ? a / f : -((-a + f - 1) / f); }
+// The same without a division, for a in [-2^21, 2^22] and f <= 8: a + f 2^21 >= 0, and with
+// m = ceil(2^32 / f), floor(n m / 2^32) = floor(n / f) for n < 2^25 (the error n (m f - 2^32) /
+// (f 2^32) stays below 1 / f).  m = gen_fdiv_magic(f); f = 1 needs no division.
+constexpr int GEN_DIV_OFF = 1 << 21;
+__device__ __forceinline__ unsigned gen_fdiv_magic(int f) {
+    return f > 1 ? (unsigned)((0x100000000ull + (unsigned)f - 1) / (unsigned)f) : 0u;
+}
+__device__ __forceinline__ int gen_fdiv(int a, int f, unsigned m) {
+    return f == 1 ? a : (int)__umulhi((unsigned)(a + f * GEN_DIV_OFF), m) - GEN_DIV_OFF;
+}
 
 struct GenStep {
     int cur, pcur, done;
@@ -186,14 +196,24 @@ __global__ void __launch_bounds__(GEN_NT) gen_interpolate_kernel(const DevProble
     }
 }
 
+// HR tiles of the prior's stencils: GEN_TILE_H x GEN_TILE_W owned pixels, staged in shared memory
+// with a halo of BTV_W - 1 pixels (both sides for the gradient, the far side for the forms)
+constexpr int GEN_TILE_H = 16, GEN_TILE_W = 64, GEN_HALO = BTV_W - 1;
+constexpr int GEN_RH = GEN_TILE_H + 2 * GEN_HALO, GEN_RW = GEN_TILE_W + 2 * GEN_HALO;
+constexpr int GEN_FH = GEN_TILE_H + GEN_HALO, GEN_FW = GEN_TILE_W + GEN_HALO;
+static_assert(GEN_TILE_H * GEN_TILE_W % GEN_NT == 0, "owned pixels per thread");
+
 // A: p = r + beta p_old, x' = x + alpha p (to the other halves of the double buffers); the BTV
 // prior at x': each pixel q takes the pairs (q, q + d) and (q - d, q) of every offset d of the
 // window (Eq. 8), its gradient gamma_d psi'(x'_q - x'_{q+d}) - gamma_d psi'(x'_{q-d} - x'_q),
-// and the value of the pairs it starts, gamma_d sqrt(t^2 + eps^2).  A neighbour's x' is formed
-// again from x, r and p_old with the same operations as its own thread's.  lambda grad BTV(x')
-// goes to r's buffer, which gen_pass_c completes to r'.  Tile blockIdx.x: |p|^2, the BTV value.
+// and the value of the pairs it starts, gamma_d sqrt(t^2 + eps^2).  Per HR tile, x' of the tile
+// and its halo is formed once into shared memory (0 outside the image, where no pair reads).
+// lambda grad BTV(x') goes to r's buffer, which gen_pass_c completes to r'.  Tile blockIdx.x:
+// |p|^2, the BTV value.
 __global__ void __launch_bounds__(GEN_NT) gen_pass_a(const DevProblem *__restrict__ probs, int pidx, int mode,
                                                      double probe_alpha, double probe_beta) {
+    __shared__ float xs[GEN_RH * GEN_RW];
+    __shared__ float ps[GEN_TILE_H * GEN_TILE_W];
     const DevProblem &P = probs[pidx];
     const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
     if (s.done) return;
@@ -204,41 +224,206 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_a(const DevProblem *__restric
     float *__restrict__ Rn = P.Rv[s.cur ^ 1];
     float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
     const int H = P.H, W = P.W, pitch = P.pitch;
-    const float alpha = s.alpha, beta = s.beta, eps2 = P.eps2;
-    auto xp = [&](int u, int v) {
-        const size_t o = (size_t)u * pitch + v;
-        return fmaf(alpha, fmaf(beta, Po[o], R[o]), X[o]);
-    };
+    const float alpha = s.alpha, beta = s.beta, eps2 = P.eps2, lam = P.lambda;
+    float gm[BTV_W * BTV_W];
+#pragma unroll
+    for (int d = 0; d < BTV_W * BTV_W; ++d) gm[d] = P.gamma[d];
+    const int tiles_x = (W + GEN_TILE_W - 1) / GEN_TILE_W, n_t = tiles_x * ((H + GEN_TILE_H - 1) / GEN_TILE_H);
     float pp = 0.f, jb = 0.f;
-    for (size_t t = (size_t)blockIdx.x * GEN_NT + threadIdx.x; t < (size_t)H * W; t += (size_t)gridDim.x * GEN_NT) {
-        const int u = (int)(t / W), v = (int)(t - (size_t)u * W);
-        const size_t o = (size_t)u * pitch + v;
-        const float p = fmaf(beta, Po[o], R[o]);
-        const float xq = fmaf(alpha, p, X[o]);
-        pp = fmaf(p, p, pp);
-        float g = 0.f, jq = 0.f;
-        for (int dy = 0; dy < BTV_W; ++dy)
-            for (int dx = 0; dx < BTV_W; ++dx) {
-                const float gm = P.gamma[dy * BTV_W + dx];
-                if ((dx | dy) == 0 || gm == 0.f) continue;
-                if (u + dy < H && v + dx < W) {
-                    const float d = xq - xp(u + dy, v + dx), q = fmaf(d, d, eps2);
-                    g = fmaf(gm, d * rsqrtf(q), g);
-                    jq = fmaf(gm, sqrtf(q), jq);
-                }
-                if (u >= dy && v >= dx) {
-                    const float d = xp(u - dy, v - dx) - xq, q = fmaf(d, d, eps2);
-                    g = fmaf(-gm, d * rsqrtf(q), g);
-                }
+    for (int t = blockIdx.x; t < n_t; t += gridDim.x) {
+        const int y0 = (t / tiles_x) * GEN_TILE_H, x0 = (t % tiles_x) * GEN_TILE_W;
+        for (int e = threadIdx.x; e < GEN_RH * GEN_RW; e += GEN_NT) {
+            const int ry = e / GEN_RW, rx = e - ry * GEN_RW, u = y0 - GEN_HALO + ry, v = x0 - GEN_HALO + rx;
+            float xv = 0.f, pv = 0.f;
+            if (u >= 0 && u < H && v >= 0 && v < W) {
+                const size_t o = (size_t)u * pitch + v;
+                pv = fmaf(beta, Po[o], R[o]);
+                xv = fmaf(alpha, pv, X[o]);
             }
-        jb += jq;
-        Xn[o] = xq;
-        Pn[o] = p;
-        Rn[o] = P.lambda * g;
+            xs[e] = xv;
+            const int oy = ry - GEN_HALO, ox = rx - GEN_HALO;
+            if (oy >= 0 && oy < GEN_TILE_H && ox >= 0 && ox < GEN_TILE_W) ps[oy * GEN_TILE_W + ox] = pv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < GEN_TILE_H * GEN_TILE_W / GEN_NT; ++q) {
+            const int e = (int)threadIdx.x + GEN_NT * q, oy = e / GEN_TILE_W, ox = e - oy * GEN_TILE_W;
+            const int u = y0 + oy, v = x0 + ox;
+            if (u >= H || v >= W) continue;
+            const float *c = xs + (oy + GEN_HALO) * GEN_RW + ox + GEN_HALO;
+            const float xq = c[0], p = ps[e];
+            pp = fmaf(p, p, pp);
+            float g = 0.f, jq = 0.f;
+#pragma unroll
+            for (int dy = 0; dy < BTV_W; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < BTV_W; ++dx) {
+                    const float gd = gm[dy * BTV_W + dx];
+                    if ((dx | dy) == 0 || gd == 0.f) continue;
+                    if (u + dy < H && v + dx < W) {
+                        const float d = xq - c[dy * GEN_RW + dx], q2 = fmaf(d, d, eps2), rq = rsqrtf(q2);
+                        g = fmaf(gd, d * rq, g);
+                        jq = fmaf(gd, q2 * rq, jq);   // sqrt(t^2 + eps^2)
+                    }
+                    if (u >= dy && v >= dx) {
+                        const float d = c[-dy * GEN_RW - dx] - xq, q2 = fmaf(d, d, eps2);
+                        g = fmaf(-gd, d * rsqrtf(q2), g);
+                    }
+                }
+            jb += jq;
+            const size_t o = (size_t)u * pitch + v;
+            Xn[o] = xq;
+            Pn[o] = p;
+            Rn[o] = lam * g;
+        }
+        __syncthreads();
     }
     const int fld[2] = {P_PP, P_JB};
     const float val[2] = {pp, jb};
     gen_write_sums<2>(P, blockIdx.x, fld, val);
+}
+
+// Separable tiles of the data term.  Forward: a tile of GF_TI x GF_TJ LR samples (one per
+// thread: warp w takes LR row i0 + w).  The HR footprint of the tile is staged in shared memory
+// (0 outside the image: the tables' masks then see what the definitions give), either once for
+// all frames (their integer shifts spread over sy x sx pixels: the union footprint) or per frame;
+// per frame, a horizontal pass forms, per footprint row and LR column, sum_dx Tx[k][j][dx]
+// x(row, .), and a vertical pass sum_dy Ty[k][i][dy] of those.  Adjoint: a tile of GA_TU x GA_TV
+// HR pixels (one per thread); for a chunk of frames at a time, the LR samples whose taps reach
+// it are staged, a horizontal pass gathers sum_j Tx[k][j][v - f j - ox] e(i, j) per LR row and
+// HR column, and a vertical pass sum_i Ty[k][i][u - f i - oy] of those.
+constexpr int GF_TI = 8, GF_TJ = 32, GA_TU = 8, GA_TV = 32;
+static_assert(GF_TI * GF_TJ == GEN_NT && GA_TU * GA_TV == GEN_NT, "one sample or pixel per thread");
+__host__ __device__ inline int gen_fwd_rh(int f, int tw) { return f * (GF_TI - 1) + tw; }
+__host__ __device__ inline int gen_fwd_rw(int f, int tw) { return f * (GF_TJ - 1) + tw; }
+__host__ __device__ inline int gen_adj_li(int f, int tw) { return (GA_TU + tw - 2) / f + 2; }
+__host__ __device__ inline int gen_adj_lj(int f, int tw) { return (GA_TV + tw - 2) / f + 2; }
+// Dynamic shared memory (bytes) of a forward tile over na images whose staged footprint is
+// widened by (sy, sx), and of an adjoint tile of kc frames.
+__host__ __device__ inline size_t gen_fwd_smem(int f, int tw, int na, int sy, int sx) {
+    const size_t rh = gen_fwd_rh(f, tw), rw = gen_fwd_rw(f, tw);
+    return (size_t)na * ((rh + sy) * (rw + sx) + rh * GF_TJ) * sizeof(float);
+}
+__host__ __device__ inline size_t gen_adj_smem(int f, int tw, int kc) {
+    return (size_t)kc * ((size_t)gen_adj_li(f, tw) * gen_adj_lj(f, tw) + (size_t)gen_adj_li(f, tw) * GA_TV) * sizeof(float);
+}
+// the largest forward tile of one frame: two images, f = MAXF, GEN_TW taps (162 KB)
+constexpr size_t GEN_SMEM_MAX = 2 * ((size_t)(MAXF * (GF_TI - 1) + GEN_TW) * (MAXF * (GF_TJ - 1) + GEN_TW) +
+                                     (size_t)(MAXF * (GF_TI - 1) + GEN_TW) * GF_TJ) * sizeof(float);
+static_assert(GEN_SMEM_MAX + 16384 <= 227 * 1024, "frame-wise tiles fit the shared memory of a CTA");
+// The union footprint is staged when it is at most twice one frame's and its tile fits
+// GEN_SMEM_MAX; an adjoint chunk takes the frames that fit GEN_ADJ_BYTES.
+__host__ __device__ inline bool gen_fwd_union(int f, int tw, int sy, int sx) {
+    const long rh = gen_fwd_rh(f, tw), rw = gen_fwd_rw(f, tw);
+    return (rh + sy) * (rw + sx) <= 2 * rh * rw && gen_fwd_smem(f, tw, 2, sy, sx) <= GEN_SMEM_MAX;
+}
+constexpr size_t GEN_ADJ_BYTES = 48 * 1024;
+__host__ __device__ inline int gen_adj_kc(int f, int tw, int K) {
+    const int kc = (int)(GEN_ADJ_BYTES / gen_adj_smem(f, tw, 1));
+    return kc < 1 ? 1 : kc > K ? K : kc;
+}
+
+// Stage the footprint of the LR tile at (i0, j0) for integer shifts (ty0 .. ty0 + sy, tx0 .. tx0
+// + sx): URH x URW pixels of a (and b) from HR row f i0 + ty0 - R, column f j0 + tx0 - R.
+template <bool TWO>
+__device__ __forceinline__ void gen_stage(const DevProblem &P, int i0, int j0, int ty0, int tx0, int URH, int URW,
+                                          const float *__restrict__ a, const float *__restrict__ b, float *ra,
+                                          float *rb) {
+    const int f = P.f, H = P.H, W = P.W, pitch = P.pitch;
+    const int U0 = f * i0 + ty0 - P.g_r, V0 = f * j0 + tx0 - P.g_r;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();   // the previous tile's reads of the buffers are done
+    for (int r = warp; r < URH; r += GEN_NT / 32) {   // footprint rows by warp, columns by lane
+        const int u = U0 + r;
+        const bool row_in = u >= 0 && u < H;
+        const float *ar = a + (row_in ? (size_t)u * pitch : 0), *br = TWO ? b + (row_in ? (size_t)u * pitch : 0) : nullptr;
+        for (int c = lane; c < URW; c += 32) {
+            const int v = V0 + c;
+            const bool in = row_in && v >= 0 && v < W;
+            ra[r * URW + c] = in ? ar[v] : 0.f;
+            if (TWO) rb[r * URW + c] = in ? br[v] : 0.f;
+        }
+    }
+    __syncthreads();
+}
+
+// A_k a (and A_k b) for the thread's sample (i0 + tid / GF_TJ, j0 + tid % GF_TJ) of frame k from
+// the staged footprint, frame k's rows and columns starting (dyk, dxk) into it (0 outside the
+// frame).  Every thread of the CTA calls it.
+template <bool TWO>
+__device__ __forceinline__ float2 gen_eval(const DevProblem &P, int k, int i0, int j0, int dyk, int dxk, int URW,
+                                           const float *ra, const float *rb, float *ha, float *hb) {
+    const int f = P.f, tw = P.g_tw, RH = gen_fwd_rh(f, tw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();   // the previous frame's reads of ha, hb are done
+    {   // horizontal: lane = LR column of the tile (GF_TJ = 32)
+        const int j = j0 + lane;
+        const float *tx = P.Tx + ((size_t)k * P.w + (j < P.w ? j : 0)) * tw;
+        for (int r = warp; r < RH; r += GEN_NT / 32) {
+            float sa = 0.f, sb = 0.f;
+            const int o = (r + dyk) * URW + f * lane + dxk;
+            if (j < P.w)
+                for (int dx = 0; dx < tw; ++dx) {
+                    const float wx = __ldg(tx + dx);
+                    sa = fmaf(wx, ra[o + dx], sa);
+                    if (TWO) sb = fmaf(wx, rb[o + dx], sb);
+                }
+            ha[r * GF_TJ + lane] = sa;
+            if (TWO) hb[r * GF_TJ + lane] = sb;
+        }
+    }
+    __syncthreads();
+    const int ii = warp, i = i0 + ii;
+    float za = 0.f, zb = 0.f;
+    if (i < P.h && j0 + lane < P.w) {
+        const float *ty = P.Ty + ((size_t)k * P.h + i) * tw;
+        const float *qa = ha + f * ii * GF_TJ + lane, *qb = hb + f * ii * GF_TJ + lane;
+        for (int dy = 0; dy < tw; ++dy) {
+            const float wy = __ldg(ty + dy);
+            za = fmaf(wy, qa[dy * GF_TJ], za);
+            if (TWO) zb = fmaf(wy, qb[dy * GF_TJ], zb);
+        }
+    }
+    return make_float2(za, zb);
+}
+
+// Forward tiles of all frames; body(z, t, in) for each frame's tile, t the thread's sample's
+// index in the frames' layout and in whether the sample exists.  uni: the union footprint (the
+// frames' integer shifts from (ymin, xmin), spread sy x sx); else one frame per item.
+template <bool TWO, typename F>
+__device__ __forceinline__ void gen_fwd_tiles(const DevProblem &P, int uni, int cta, int ctas,
+                                              const float *__restrict__ a, const float *__restrict__ b, float *sm,
+                                              F &&body) {
+    const int f = P.f, tw = P.g_tw, RH = gen_fwd_rh(f, tw), RW = gen_fwd_rw(f, tw);
+    int ymin = P.ty[0], ymax = P.ty[0], xmin = P.tx[0], xmax = P.tx[0];
+    for (int k = 1; k < P.K; ++k) {
+        ymin = min(ymin, P.ty[k]); ymax = max(ymax, P.ty[k]);
+        xmin = min(xmin, P.tx[k]); xmax = max(xmax, P.tx[k]);
+    }
+    const int URH = uni ? RH + ymax - ymin : RH, URW = uni ? RW + xmax - xmin : RW;
+    float *ra = sm, *rb = sm + URH * URW;
+    float *ha = sm + (TWO ? 2 : 1) * URH * URW, *hb = ha + RH * GF_TJ;
+    // (the plan keeps K nti ntj below 2^31: 32-bit item indices)
+    const int nti = (P.h + GF_TI - 1) / GF_TI, ntj = (P.w + GF_TJ - 1) / GF_TJ;
+    const int per_frame = nti * ntj, items = uni ? per_frame : per_frame * P.K;
+    const int ii = threadIdx.x / GF_TJ, jj = threadIdx.x % GF_TJ;
+    for (int it = cta; it < items; it += ctas) {
+        const int k0 = uni ? 0 : it / per_frame, rem = it - k0 * per_frame;
+        const int ti = rem / ntj, tj = rem - ti * ntj;
+        const int i0 = ti * GF_TI, j0 = tj * GF_TJ, i = i0 + ii, j = j0 + jj;
+        const bool in = i < P.h && j < P.w;
+        if (uni) {
+            gen_stage<TWO>(P, i0, j0, ymin, xmin, URH, URW, a, b, ra, rb);
+            for (int k = 0; k < P.K; ++k) {
+                const float2 z = gen_eval<TWO>(P, k, i0, j0, P.ty[k] - ymin, P.tx[k] - xmin, URW, ra, rb, ha, hb);
+                body(z, ((size_t)k * P.h + i) * P.w + j, in);
+            }
+        } else {
+            gen_stage<TWO>(P, i0, j0, P.ty[k0], P.tx[k0], URH, URW, a, b, ra, rb);
+            const float2 z = gen_eval<TWO>(P, k0, i0, j0, 0, 0, URW, ra, rb, ha, hb);
+            body(z, ((size_t)k0 * P.h + i) * P.w + j, in);
+        }
+    }
 }
 
 // B: per LR sample of every frame, z = A_k x', zp = A_k p and the residual e' = z - y; the data
@@ -248,30 +433,30 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_a(const DevProblem *__restric
 // DS psi_d'(e') (2 e' for L2), zp and w.  Tile g_ctas + blockIdx.x.
 template <bool L1>
 __global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restrict__ probs, int pidx, int mode,
-                                                     double probe_alpha, double probe_beta) {
+                                                     double probe_alpha, double probe_beta, int uni) {
+    extern __shared__ float gsm[];
     const DevProblem &P = probs[pidx];
     const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
     if (s.done) return;
     const float *__restrict__ Xn = P.X[s.cur ^ 1];
     const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
-    const size_t m = (size_t)P.h * P.w;
     const float alpha = s.alpha, deps = P.data_eps, deps2 = deps * deps;
     float jd = 0.f, dj = 0.f, cd = 0.f;
-    for (size_t t = (size_t)blockIdx.x * GEN_NT + threadIdx.x; t < m * P.K; t += (size_t)gridDim.x * GEN_NT) {
-        const int k = (int)(t / m);
-        const size_t li = t - (size_t)k * m;
-        const int i = (int)(li / P.w), j = (int)(li - (size_t)i * P.w);
-        const float2 z = gen_apply2(P, k, i, j, Xn, Pn, P.pitch);
+    gen_fwd_tiles<true>(P, uni, blockIdx.x, gridDim.x, Xn, Pn, gsm, [&](float2 z, size_t t, bool in) {
+        if (!in) return;
         const float e = z.x - P.Yg[t], zp = z.y, abp = alpha * zp;
         const float de2 = abp * fmaf(2.f, e, -abp);   // e'^2 - (e' - alpha zp)^2
         if constexpr (L1) {
-            const float s1 = sqrtf(fmaf(e, e, deps2)), eb = e - abp, s0 = sqrtf(fmaf(eb, eb, deps2));
-            jd += e * e / (s1 + deps);                  // sqrt(e^2 + eps_d^2) - eps_d
-            dj += de2 / (s1 + s0);
-            const float w = deps2 / (s1 * s1 * s1);
-            cd = fmaf(w * zp, zp, cd);
-            P.Eg[t] = e / s1;
-            P.Wg[t] = w;
+            // s = sqrt(e^2 + eps_d^2) as q rsqrt(q); psi_d(e') = e'^2 / (s1 + eps_d), psi_d' = e' / s1,
+            // psi_d'' = eps_d^2 / s1^3, and the change (e'^2 - eb^2) / (s1 + s0)
+            const float q1 = fmaf(e, e, deps2), r1 = rsqrtf(q1), s1 = q1 * r1;
+            const float eb = e - abp, q0 = fmaf(eb, eb, deps2), s0 = q0 * rsqrtf(q0);
+            jd += __fdividef(e * e, s1 + deps);
+            dj += __fdividef(de2, s1 + s0);
+            const float wd = deps2 * (r1 * r1 * r1);
+            cd = fmaf(wd * zp, zp, cd);
+            P.Eg[t] = e * r1;
+            P.Wg[t] = wd;
         } else {
             jd = fmaf(e, e, jd);
             dj += de2;
@@ -279,46 +464,81 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restric
             P.Eg[t] = 2.f * e;
         }
         P.APg[t] = zp;
-    }
+    });
     const int fld[3] = {P_JD, P_DJD, P_C};
     const float val[3] = {jd, dj, (L1 ? 1.f : 2.f) * cd};
     gen_write_sums<3>(P, P.g_ctas + blockIdx.x, fld, val);
 }
 
-// C: r'(u, v) = -(sum_k A_k^T (DS psi_d'(e'_k)) + lambda grad BTV(x')) by gathering, for each
-// frame, the LR samples whose taps reach (u, v); |r'|^2, r'.r, p.r'.  Tile 2 g_ctas + blockIdx.x.
+// C: r'(u, v) = -(sum_k A_k^T (DS psi_d'(e'_k)) + lambda grad BTV(x')) over adjoint tiles (one
+// HR pixel per thread: warp w takes HR row u0 + w); |r'|^2, r'.r, p.r'.  Tile 2 g_ctas + blockIdx.x.
 __global__ void __launch_bounds__(GEN_NT) gen_pass_c(const DevProblem *__restrict__ probs, int pidx, int mode,
-                                                     double probe_alpha, double probe_beta) {
+                                                     double probe_alpha, double probe_beta, int kc) {
+    extern __shared__ float gsm[];
     const DevProblem &P = probs[pidx];
     const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
     if (s.done) return;
     const float *__restrict__ R = P.Rv[s.cur];
     const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
     float *__restrict__ Rn = P.Rv[s.cur ^ 1];
-    const int H = P.H, W = P.W, f = P.f, h = P.h, w = P.w, tw = P.g_tw, gr = P.g_r;
+    const int f = P.f, h = P.h, w = P.w, tw = P.g_tw, gr = P.g_r, H = P.H, W = P.W, K = P.K;
+    const int LI = gen_adj_li(f, tw), LJ = gen_adj_lj(f, tw);
+    float *es = gsm, *hs = gsm + kc * LI * LJ;   // kc frames' staged samples, then their row sums
+    const int tiles_x = (W + GA_TV - 1) / GA_TV, n_t = tiles_x * ((H + GA_TU - 1) / GA_TU);
+    const int uu = threadIdx.x / GA_TV, vv = threadIdx.x % GA_TV;   // warp = HR row, lane = column
+    const unsigned fm = gen_fdiv_magic(f);
     float rr = 0.f, rrx = 0.f, pr = 0.f;
-    for (size_t t = (size_t)blockIdx.x * GEN_NT + threadIdx.x; t < (size_t)H * W; t += (size_t)gridDim.x * GEN_NT) {
-        const int u = (int)(t / W), v = (int)(t - (size_t)u * W);
-        const size_t o = (size_t)u * P.pitch + v;
+    for (int t = blockIdx.x; t < n_t; t += gridDim.x) {
+        const int ty_ = t / tiles_x, u0 = ty_ * GA_TU, v0 = (t - ty_ * tiles_x) * GA_TV;
+        const int u = u0 + uu, v = v0 + vv;
         float acc = 0.f;
-        for (int k = 0; k < P.K; ++k) {
-            const int a = u - P.ty[k] + gr, b = v - P.tx[k] + gr;   // f i + dy, f j + dx
-            const int ilo = max(gen_floordiv(a - tw + f, f), 0), ihi = min(gen_floordiv(a, f), h - 1);
-            const int jlo = max(gen_floordiv(b - tw + f, f), 0), jhi = min(gen_floordiv(b, f), w - 1);
-            for (int i = ilo; i <= ihi; ++i) {
-                const float wy = P.Ty[((size_t)k * h + i) * tw + (a - f * i)];
-                if (wy == 0.f) continue;
-                const float *e = P.Eg + ((size_t)k * h + i) * w;
-                float row = 0.f;
-                for (int j = jlo; j <= jhi; ++j) row = fmaf(P.Tx[((size_t)k * w + j) * tw + (b - f * j)], e[j], row);
-                acc = fmaf(wy, row, acc);
+        for (int k0 = 0; k0 < K; k0 += kc) {
+            const int nk = min(kc, K - k0);
+            __syncthreads();   // the previous chunk's (or tile's) reads of es and hs are done
+            for (int q = 0; q < nk; ++q) {   // stage: LR rows by warp, columns by lane
+                const int k = k0 + q, oy = P.ty[k] - gr, ox = P.tx[k] - gr;
+                const int IL = gen_fdiv(u0 - oy - tw + f, f, fm), JL = gen_fdiv(v0 - ox - tw + f, f, fm);
+                float *eq = es + q * LI * LJ;
+                for (int li = uu; li < LI; li += GA_TU) {
+                    const int i = IL + li;
+                    const bool row_in = i >= 0 && i < h;
+                    const float *er = P.Eg + (row_in ? ((size_t)k * h + i) * w : 0);
+                    for (int lj = vv; lj < LJ; lj += GA_TV) {
+                        const int j = JL + lj;
+                        eq[li * LJ + lj] = (row_in && j >= 0 && j < w) ? er[j] : 0.f;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int q = 0; q < nk; ++q) {   // horizontal: lane = HR column; its LR columns once per frame
+                const int k = k0 + q, ox = P.tx[k] - gr, b = v - ox;
+                const int JL = gen_fdiv(v0 - ox - tw + f, f, fm);
+                const int jlo = max(gen_fdiv(b - tw + f, f, fm), 0), jhi = min(gen_fdiv(b, f, fm), w - 1);
+                const float *Txk = P.Tx + (size_t)k * w * tw, *eq = es + q * LI * LJ;
+                float *hq = hs + q * LI * GA_TV;
+                for (int li = uu; li < LI; li += GA_TU) {
+                    float sum = 0.f;
+                    for (int j = jlo; j <= jhi; ++j) sum = fmaf(__ldg(Txk + j * tw + (b - f * j)), eq[li * LJ + (j - JL)], sum);
+                    hq[li * GA_TV + vv] = sum;
+                }
+            }
+            __syncthreads();
+            for (int q = 0; q < nk; ++q) {   // vertical
+                const int k = k0 + q, oy = P.ty[k] - gr, a = u - oy;
+                const int IL = gen_fdiv(u0 - oy - tw + f, f, fm);
+                const int ilo = max(gen_fdiv(a - tw + f, f, fm), 0), ihi = min(gen_fdiv(a, f, fm), h - 1);
+                const float *Tyk = P.Ty + (size_t)k * h * tw, *hq = hs + q * LI * GA_TV;
+                for (int i = ilo; i <= ihi; ++i) acc = fmaf(__ldg(Tyk + i * tw + (a - f * i)), hq[(i - IL) * GA_TV + vv], acc);
             }
         }
-        const float rn = -(acc + Rn[o]);
-        Rn[o] = rn;
-        rr = fmaf(rn, rn, rr);
-        rrx = fmaf(rn, R[o], rrx);
-        pr = fmaf(Pn[o], rn, pr);
+        if (u < H && v < W) {
+            const size_t o = (size_t)u * P.pitch + v;
+            const float rn = -(acc + Rn[o]);
+            Rn[o] = rn;
+            rr = fmaf(rn, rn, rr);
+            rrx = fmaf(rn, R[o], rrx);
+            pr = fmaf(Pn[o], rn, pr);
+        }
     }
     const int fld[3] = {P_RR, P_RRX, P_PR};
     const float val[3] = {rr, rrx, pr};
@@ -326,13 +546,15 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_c(const DevProblem *__restric
 }
 
 // D, CTAs [0, g_ctas): per LR sample, zr = A_k r'; the data parts of r'.H r' and r'.H p,
-// DS sum w zr^2 and DS sum w zr zp.  CTAs [g_ctas, 2 g_ctas): the prior's parts of the three
-// forms, lambda sum_d gamma_d sum_q psi''(x'_q - x'_{q+d}) (a_q - a_{q+d}) (b_q - b_{q+d}) for
+// DS sum w zr^2 and DS sum w zr zp.  CTAs [g_ctas, 2 g_ctas): per HR tile (x', r', p of the tile
+// and its far-side halo in shared memory), the prior's parts of the three forms,
+// lambda sum_d gamma_d sum_q psi''(x'_q - x'_{q+d}) (a_q - a_{q+d}) (b_q - b_{q+d}) for
 // (a, b) = (r', r'), (r', p), (p, p), psi''(t) = eps^2 / (t^2 + eps^2)^(3/2).
 // Tile 3 g_ctas + blockIdx.x.
 template <bool L1>
 __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restrict__ probs, int pidx, int mode,
-                                                     double probe_alpha, double probe_beta) {
+                                                     double probe_alpha, double probe_beta, int uni) {
+    __shared__ float xs[GEN_FH * GEN_FW], rs[GEN_FH * GEN_FW], qs[GEN_FH * GEN_FW];
     const DevProblem &P = probs[pidx];
     const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
     if (s.done) return;
@@ -341,17 +563,14 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
     const int G = P.g_ctas;
     if ((int)blockIdx.x < G) {
-        const size_t m = (size_t)P.h * P.w;
+        extern __shared__ float gsm[];
         float a = 0.f, b = 0.f;
-        for (size_t t = (size_t)blockIdx.x * GEN_NT + threadIdx.x; t < m * P.K; t += (size_t)G * GEN_NT) {
-            const int k = (int)(t / m);
-            const size_t li = t - (size_t)k * m;
-            const int i = (int)(li / P.w), j = (int)(li - (size_t)i * P.w);
-            const float zr = gen_apply2(P, k, i, j, Rn, nullptr, P.pitch).x;
-            const float wzr = L1 ? P.Wg[t] * zr : zr;
+        gen_fwd_tiles<false>(P, uni, blockIdx.x, G, Rn, nullptr, gsm, [&](float2 z, size_t t, bool in) {
+            if (!in) return;
+            const float zr = z.x, wzr = L1 ? P.Wg[t] * zr : zr;
             a = fmaf(wzr, zr, a);
             b = fmaf(wzr, P.APg[t], b);
-        }
+        });
         const float ds = L1 ? 1.f : 2.f;
         const int fld[2] = {P_A, P_B};
         const float val[2] = {ds * a, ds * b};
@@ -360,23 +579,46 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     }
     const int H = P.H, W = P.W, pitch = P.pitch;
     const float eps2 = P.eps2;
+    float gm[BTV_W * BTV_W];
+#pragma unroll
+    for (int d = 0; d < BTV_W * BTV_W; ++d) gm[d] = P.gamma[d];
+    const int tiles_x = (W + GEN_TILE_W - 1) / GEN_TILE_W, n_t = tiles_x * ((H + GEN_TILE_H - 1) / GEN_TILE_H);
     float a = 0.f, b = 0.f, c = 0.f;
-    for (size_t t = (size_t)(blockIdx.x - G) * GEN_NT + threadIdx.x; t < (size_t)H * W; t += (size_t)G * GEN_NT) {
-        const int u = (int)(t / W), v = (int)(t - (size_t)u * W);
-        const size_t o = (size_t)u * pitch + v;
-        const float xq = Xn[o], rq = Rn[o], pq = Pn[o];
-        for (int dy = 0; dy < BTV_W; ++dy)
-            for (int dx = 0; dx < BTV_W; ++dx) {
-                const float gm = P.gamma[dy * BTV_W + dx];
-                if ((dx | dy) == 0 || gm == 0.f || u + dy >= H || v + dx >= W) continue;
-                const size_t o2 = o + (size_t)dy * pitch + dx;
-                const float d = xq - Xn[o2], q = fmaf(d, d, eps2), rs = rsqrtf(q);
-                const float w2 = gm * eps2 * (rs * rs * rs);
-                const float dr = rq - Rn[o2], dp = pq - Pn[o2], wdr = w2 * dr;
-                a = fmaf(wdr, dr, a);
-                b = fmaf(wdr, dp, b);
-                c = fmaf(w2 * dp, dp, c);
+    for (int t = (int)blockIdx.x - G; t < n_t; t += G) {
+        const int y0 = (t / tiles_x) * GEN_TILE_H, x0 = (t % tiles_x) * GEN_TILE_W;
+        for (int e = threadIdx.x; e < GEN_FH * GEN_FW; e += GEN_NT) {
+            const int ry = e / GEN_FW, rx = e - ry * GEN_FW, u = y0 + ry, v = x0 + rx;
+            float xv = 0.f, rv = 0.f, pv = 0.f;
+            if (u < H && v < W) {
+                const size_t o = (size_t)u * pitch + v;
+                xv = Xn[o]; rv = Rn[o]; pv = Pn[o];
             }
+            xs[e] = xv; rs[e] = rv; qs[e] = pv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < GEN_TILE_H * GEN_TILE_W / GEN_NT; ++q) {
+            const int e = (int)threadIdx.x + GEN_NT * q, oy = e / GEN_TILE_W, ox = e - oy * GEN_TILE_W;
+            const int u = y0 + oy, v = x0 + ox;
+            if (u >= H || v >= W) continue;
+            const int o = oy * GEN_FW + ox;
+            const float xq = xs[o], rq = rs[o], pq = qs[o];
+#pragma unroll
+            for (int dy = 0; dy < BTV_W; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < BTV_W; ++dx) {
+                    const float gd = gm[dy * BTV_W + dx];
+                    if ((dx | dy) == 0 || gd == 0.f || u + dy >= H || v + dx >= W) continue;
+                    const int o2 = o + dy * GEN_FW + dx;
+                    const float d = xq - xs[o2], q2 = fmaf(d, d, eps2), r3 = rsqrtf(q2);
+                    const float w2 = gd * eps2 * (r3 * r3 * r3);
+                    const float dr = rq - rs[o2], dp = pq - qs[o2], wdr = w2 * dr;
+                    a = fmaf(wdr, dr, a);
+                    b = fmaf(wdr, dp, b);
+                    c = fmaf(w2 * dp, dp, c);
+                }
+        }
+        __syncthreads();
     }
     const float lam = P.lambda;
     const int fld[3] = {P_A, P_B, P_C};

@@ -133,7 +133,7 @@ struct DevProblem {
     // weights of M_k and every mask (ty, tx: the integer parts floor(t) of the HR shifts, any
     // sign; gfy, gfx: the fractional parts).  Each of the pass's kernels runs g_ctas CTAs (the
     // last one 2 g_ctas) and writes one tile of sums per CTA: n_tiles = GEN_TILES * g_ctas.
-    int general, g_tw, g_r, g_ctas;
+    int general, g_tw, g_r, g_nb, g_ctas;         // g_nb: the block side of D (f with binning, else 1)
     float gfy[MAXK], gfx[MAXK];                   // and 1 minus them, each rounded once from FP64
     float gfy0[MAXK], gfx0[MAXK];
     float *Yg;                                    // [K][h][w] frames (float; u16 converted)

@@ -225,3 +225,27 @@ def test_general_refusals(orc):
         B.misr_gradient_noalloc(desc, to_dev(y).data_ptr(), to_dev(xt.astype(np.float32)).data_ptr(), g.data_ptr())
     assert e.value.status == B.MISR_ENOTIMPL
     plan.close()
+
+
+def test_general_checkpoint_refused_on_another_model(orc):
+    """A frame-wise checkpoint resumes only on a plan of the same model: another PSF, another
+    fractional shift, point sampling instead of binning, or the fused passes' geometry refuse it
+    with MISR_EINVAL."""
+    from paper_2108_04315_b300 import binding as B
+    h, w, f, shifts, psf, dec = GENERAL_CASES["study_bin_psf3"]
+    P, plan, xt, y = general_case(orc, "study_bin_psf3", 650, iters=3)
+    plan.solve(to_dev(y))
+    ck = plan.export_state()
+    others = [B.Plan(h, w, f, shifts, gen.gaussian_psf(3, 0.9), iters=5, decimation=dec),
+              B.Plan(h, w, f, [(0.5, 0.0), (0.0, 0.5), (-0.5, 0.0), (0.0, -0.45)], psf, iters=5, decimation=dec),
+              B.Plan(h, w, f, shifts, psf, iters=5),
+              B.Plan(h, w, f, gen.half_pixel_shifts(), psf, iters=5, decimation=dec)]
+    for o in others:
+        with pytest.raises(B.MisrError) as e:
+            o.import_state(ck)
+        assert e.value.status == B.MISR_EINVAL
+        o.close()
+    same = B.Plan(h, w, f, shifts, psf, iters=5, decimation=dec)
+    same.import_state(ck)
+    same.close()
+    plan.close()
