@@ -425,6 +425,14 @@ static misr_status current_device(int *dev) {
     return MISR_OK;
 }
 
+// the frame-wise pass's kernels are compiled for at most 4, 8 or GEN_TW taps per axis
+template <typename F>
+auto with_gen_taps(int tw, F &&f) {
+    if (tw <= 4) return f(std::integral_constant<int, 4>());
+    if (tw <= 8) return f(std::integral_constant<int, 8>());
+    return f(std::integral_constant<int, GEN_TW>());
+}
+
 static misr_status set_pass_attrs() {
     int dev = 0;
     misr_status r = current_device(&dev);
@@ -441,11 +449,17 @@ static misr_status set_pass_attrs() {
     // the frame-wise pass's tiles: their shared memory grows with the factor and the taps
     // (at most GEN_SMEM_MAX bytes, a forward tile of two images at f = MAXF, GEN_TW taps)
     const int gmax = (int)GEN_SMEM_MAX;
-    CK(cudaFuncSetAttribute(gen_pass_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
-    CK(cudaFuncSetAttribute(gen_pass_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
-    CK(cudaFuncSetAttribute(gen_pass_c, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
-    CK(cudaFuncSetAttribute(gen_pass_d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
-    CK(cudaFuncSetAttribute(gen_pass_d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax));
+    for (int twm : {4, 8, GEN_TW}) {
+        const cudaError_t ge = with_gen_taps(twm, [&](auto T) {
+            constexpr int t = decltype(T)::value;
+            cudaError_t e = cudaFuncSetAttribute(gen_pass_b<false, t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(gen_pass_b<true, t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(gen_pass_d<false, t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(gen_pass_d<true, t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax);
+            return e;
+        });
+        CK(ge);
+    }
     g_pass_dev[dev].attrs = true;
     return MISR_OK;
 }
@@ -779,8 +793,10 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
         // 8 CTAs of 256 threads per SM of a 148-SM GPU
         const size_t n_max = std::max((size_t)hp.H * hp.W, (size_t)d.K * hp.h * hp.w);
         // the kernels index their tiles (at least 256 elements each) in 32 bits
+        const size_t segs = (size_t)(hp.W + 1023) / 1024;
         if ((size_t)d.K * ((hp.h + 7) / 8) * ((hp.w + 31) / 32) >= (1u << 31) ||
-            (size_t)((hp.H + 15) / 16) * ((hp.W + 31) / 32) >= (1u << 31))
+            (size_t)((hp.H + 15) / 16) * ((hp.W + 31) / 32) >= (1u << 31) ||
+            (size_t)d.K * hp.h * segs >= (1u << 31))
             return fail(MISR_EINVAL, "frame-wise pass: more than 2^31 tiles");
         set_shape(hp, DEFAULT_SHAPE);
         hp.g_ctas = (int)std::min<size_t>(148 * 8, std::max<size_t>(1, (n_max + 2047) / 2048));
@@ -803,7 +819,7 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
 // buffers DS psi_d'(e'), A_k p and psi_d''(e'), the tap tables.
 struct PlanLayout {
     size_t img, rp_img, o_img, o_part, o_gpart, o_cnt, o_work, o_st, o_tr, o_pr, o_tm, o_gl, total;
-    size_t lr, o_gy, o_ge, o_gap, o_gw, o_gty, o_gtx;
+    size_t lr, o_gy, o_ge, o_gap, o_gw, o_gty, o_gtx, o_gt;
 };
 static PlanLayout plan_layout(const misr_desc &d, const DevProblem &hp) {
     PlanLayout L{};
@@ -829,6 +845,7 @@ static PlanLayout plan_layout(const misr_desc &d, const DevProblem &hp) {
         L.o_gw = off; off += hp.l1 ? L.lr : 0;
         L.o_gty = off; off += align_up((size_t)d.K * hp.h * hp.g_tw * sizeof(float), 256);
         L.o_gtx = off; off += align_up((size_t)d.K * hp.w * hp.g_tw * sizeof(float), 256);
+        L.o_gt = off; off += align_up((size_t)d.K * hp.h * hp.W * sizeof(float), 256);
     }
     L.total = off;
     return L;
@@ -873,17 +890,21 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
     if (r != MISR_OK) return r;
     // frame-wise problems: their four kernels each, one after the other
     for (const GenRun &g : segs.gen) {
-        // the union footprint of all frames where it is small, a chunk of frames per adjoint stage
+        // the union footprint of all frames where it is small
         const int uni = gen_fwd_union(g.f, g.tw, g.sy, g.sx) ? 1 : 0;
-        const int sy = uni ? g.sy : 0, sx = uni ? g.sx : 0, kc = gen_adj_kc(g.f, g.tw, g.K);
+        const int sy = uni ? g.sy : 0, sx = uni ? g.sx : 0;
         const size_t sb = gen_fwd_smem(g.f, g.tw, 2, sy, sx), sd = gen_fwd_smem(g.f, g.tw, 1, sy, sx);
-        const size_t sc = gen_adj_smem(g.f, g.tw, kc);
         gen_pass_a<<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-        if (g.l1) gen_pass_b<true><<<g.ctas, GEN_NT, sb, s>>>(probs, g.pidx, mode, alpha, beta, uni);
-        else gen_pass_b<false><<<g.ctas, GEN_NT, sb, s>>>(probs, g.pidx, mode, alpha, beta, uni);
-        gen_pass_c<<<g.ctas, GEN_NT, sc, s>>>(probs, g.pidx, mode, alpha, beta, kc);
-        if (g.l1) gen_pass_d<true><<<2 * g.ctas, GEN_NT, sd, s>>>(probs, g.pidx, mode, alpha, beta, uni);
-        else gen_pass_d<false><<<2 * g.ctas, GEN_NT, sd, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+        with_gen_taps(g.tw, [&](auto T) {
+            constexpr int twm = decltype(T)::value;
+            if (g.l1) gen_pass_b<true, twm><<<g.ctas, GEN_NT, sb, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+            else gen_pass_b<false, twm><<<g.ctas, GEN_NT, sb, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+            gen_pass_c1<twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            gen_pass_c2<twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            if (g.l1) gen_pass_d<true, twm><<<2 * g.ctas, GEN_NT, sd, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+            else gen_pass_d<false, twm><<<2 * g.ctas, GEN_NT, sd, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+            return 0;
+        });
         CK(cudaGetLastError());
     }
     int off = 0;
@@ -1026,6 +1047,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
         hp.Wg = hp.l1 ? (float *)(b + lay.o_gw) : nullptr;
         hp.Ty = (float *)(b + lay.o_gty);
         hp.Tx = (float *)(b + lay.o_gtx);
+        hp.Tg = (float *)(b + lay.o_gt);
     }
     {
         const misr_status ms = make_maps(hp);

@@ -15,11 +15,12 @@
 //
 // One pass computes what the fused pass computes (p = r + beta p_old, x' = x + alpha p,
 // r' = -grad J(x'), and the ten sums J_data(x'), J_data(x') - J_data(x), R_BTV(x') + eps
-// pairs, |r'|^2, r'.r, p.r', |p|^2, r'.H r', r'.H p, p.H p), in four kernels:
+// pairs, |r'|^2, r'.r, p.r', |p|^2, r'.H r', r'.H p, p.H p), in five kernels:
 //   gen_pass_a  (HR)  p, x', the BTV value and lambda grad BTV(x') into r's buffer; |p|^2
 //   gen_pass_b  (LR)  A_k x', A_k p: the residual, J_data, dJ_data, the data part of p.H p;
 //                     DS psi_d'(e'), A_k p and psi_d''(e') kept per sample
-//   gen_pass_c  (HR)  r' = -(A^T DS psi_d' + lambda grad BTV); |r'|^2, r'.r, p.r'
+//   gen_pass_c1 (LR rows x HR columns)  the adjoint's horizontal part of every frame
+//   gen_pass_c2 (HR)  its vertical part, r' = -(A^T DS psi_d' + lambda grad BTV); |r'|^2, r'.r, p.r'
 //   gen_pass_d  (LR)  A_k r': the data parts of r'.H r' and r'.H p;
 //               (HR)  the BTV parts of the three curvature forms (second half of its CTAs)
 // then reduce_kernel sums the tiles and runs the SCG tail.  Each CTA writes one tile of sums
@@ -288,39 +289,27 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_a(const DevProblem *__restric
 // (0 outside the image: the tables' masks then see what the definitions give), either once for
 // all frames (their integer shifts spread over sy x sx pixels: the union footprint) or per frame;
 // per frame, a horizontal pass forms, per footprint row and LR column, sum_dx Tx[k][j][dx]
-// x(row, .), and a vertical pass sum_dy Ty[k][i][dy] of those.  Adjoint: a tile of GA_TU x GA_TV
-// HR pixels (one per thread); for a chunk of frames at a time, the LR samples whose taps reach
-// it are staged, a horizontal pass gathers sum_j Tx[k][j][v - f j - ox] e(i, j) per LR row and
-// HR column, and a vertical pass sum_i Ty[k][i][u - f i - oy] of those.
-constexpr int GF_TI = 8, GF_TJ = 32, GA_TU = 8, GA_TV = 32;
-static_assert(GF_TI * GF_TJ == GEN_NT && GA_TU * GA_TV == GEN_NT, "one sample or pixel per thread");
+// x(row, .), and a vertical pass sum_dy Ty[k][i][dy] of those.  (The adjoint, gen_pass_c1 and
+// gen_pass_c2, needs no staging.)
+constexpr int GF_TI = 8, GF_TJ = 32;
+static_assert(GF_TI * GF_TJ == GEN_NT, "one sample per thread");
 __host__ __device__ inline int gen_fwd_rh(int f, int tw) { return f * (GF_TI - 1) + tw; }
 __host__ __device__ inline int gen_fwd_rw(int f, int tw) { return f * (GF_TJ - 1) + tw; }
-__host__ __device__ inline int gen_adj_li(int f, int tw) { return (GA_TU + tw - 2) / f + 2; }
-__host__ __device__ inline int gen_adj_lj(int f, int tw) { return (GA_TV + tw - 2) / f + 2; }
 // Dynamic shared memory (bytes) of a forward tile over na images whose staged footprint is
-// widened by (sy, sx), and of an adjoint tile of kc frames.
+// widened by (sy, sx).
 __host__ __device__ inline size_t gen_fwd_smem(int f, int tw, int na, int sy, int sx) {
     const size_t rh = gen_fwd_rh(f, tw), rw = gen_fwd_rw(f, tw);
     return (size_t)na * ((rh + sy) * (rw + sx) + rh * GF_TJ) * sizeof(float);
-}
-__host__ __device__ inline size_t gen_adj_smem(int f, int tw, int kc) {
-    return (size_t)kc * ((size_t)gen_adj_li(f, tw) * gen_adj_lj(f, tw) + (size_t)gen_adj_li(f, tw) * GA_TV) * sizeof(float);
 }
 // the largest forward tile of one frame: two images, f = MAXF, GEN_TW taps (162 KB)
 constexpr size_t GEN_SMEM_MAX = 2 * ((size_t)(MAXF * (GF_TI - 1) + GEN_TW) * (MAXF * (GF_TJ - 1) + GEN_TW) +
                                      (size_t)(MAXF * (GF_TI - 1) + GEN_TW) * GF_TJ) * sizeof(float);
 static_assert(GEN_SMEM_MAX + 16384 <= 227 * 1024, "frame-wise tiles fit the shared memory of a CTA");
 // The union footprint is staged when it is at most twice one frame's and its tile fits
-// GEN_SMEM_MAX; an adjoint chunk takes the frames that fit GEN_ADJ_BYTES.
+// GEN_SMEM_MAX.
 __host__ __device__ inline bool gen_fwd_union(int f, int tw, int sy, int sx) {
     const long rh = gen_fwd_rh(f, tw), rw = gen_fwd_rw(f, tw);
     return (rh + sy) * (rw + sx) <= 2 * rh * rw && gen_fwd_smem(f, tw, 2, sy, sx) <= GEN_SMEM_MAX;
-}
-constexpr size_t GEN_ADJ_BYTES = 48 * 1024;
-__host__ __device__ inline int gen_adj_kc(int f, int tw, int K) {
-    const int kc = (int)(GEN_ADJ_BYTES / gen_adj_smem(f, tw, 1));
-    return kc < 1 ? 1 : kc > K ? K : kc;
 }
 
 // Stage the footprint of the LR tile at (i0, j0) for integer shifts (ty0 .. ty0 + sy, tx0 .. tx0
@@ -350,23 +339,27 @@ __device__ __forceinline__ void gen_stage(const DevProblem &P, int i0, int j0, i
 // A_k a (and A_k b) for the thread's sample (i0 + tid / GF_TJ, j0 + tid % GF_TJ) of frame k from
 // the staged footprint, frame k's rows and columns starting (dyk, dxk) into it (0 outside the
 // frame).  Every thread of the CTA calls it.
-template <bool TWO>
+template <bool TWO, int TWM>
 __device__ __forceinline__ float2 gen_eval(const DevProblem &P, int k, int i0, int j0, int dyk, int dxk, int URW,
                                            const float *ra, const float *rb, float *ha, float *hb) {
     const int f = P.f, tw = P.g_tw, RH = gen_fwd_rh(f, tw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();   // the previous frame's reads of ha, hb are done
-    {   // horizontal: lane = LR column of the tile (GF_TJ = 32)
+    {   // horizontal: lane = LR column of the tile (GF_TJ = 32); its taps in registers
         const int j = j0 + lane;
-        const float *tx = P.Tx + ((size_t)k * P.w + (j < P.w ? j : 0)) * tw;
+        const bool jin = j < P.w;
+        const float *tx = P.Tx + ((size_t)k * P.w + (jin ? j : 0)) * tw;
+        float wx[TWM];
+#pragma unroll
+        for (int dx = 0; dx < TWM; ++dx) wx[dx] = (jin && dx < tw) ? __ldg(tx + dx) : 0.f;
         for (int r = warp; r < RH; r += GEN_NT / 32) {
-            float sa = 0.f, sb = 0.f;
             const int o = (r + dyk) * URW + f * lane + dxk;
-            if (j < P.w)
-                for (int dx = 0; dx < tw; ++dx) {
-                    const float wx = __ldg(tx + dx);
-                    sa = fmaf(wx, ra[o + dx], sa);
-                    if (TWO) sb = fmaf(wx, rb[o + dx], sb);
+            float sa = 0.f, sb = 0.f;
+#pragma unroll
+            for (int dx = 0; dx < TWM; ++dx)
+                if (dx < tw) {
+                    sa = fmaf(wx[dx], ra[o + dx], sa);
+                    if (TWO) sb = fmaf(wx[dx], rb[o + dx], sb);
                 }
             ha[r * GF_TJ + lane] = sa;
             if (TWO) hb[r * GF_TJ + lane] = sb;
@@ -374,23 +367,24 @@ __device__ __forceinline__ float2 gen_eval(const DevProblem &P, int k, int i0, i
     }
     __syncthreads();
     const int ii = warp, i = i0 + ii;
+    const bool in = i < P.h && j0 + lane < P.w;
+    const float *ty = P.Ty + ((size_t)k * P.h + (i < P.h ? i : 0)) * tw;
+    const float *qa = ha + f * ii * GF_TJ + lane, *qb = hb + f * ii * GF_TJ + lane;
     float za = 0.f, zb = 0.f;
-    if (i < P.h && j0 + lane < P.w) {
-        const float *ty = P.Ty + ((size_t)k * P.h + i) * tw;
-        const float *qa = ha + f * ii * GF_TJ + lane, *qb = hb + f * ii * GF_TJ + lane;
-        for (int dy = 0; dy < tw; ++dy) {
-            const float wy = __ldg(ty + dy);
+#pragma unroll
+    for (int dy = 0; dy < TWM; ++dy)
+        if (dy < tw) {
+            const float wy = in ? __ldg(ty + dy) : 0.f;
             za = fmaf(wy, qa[dy * GF_TJ], za);
             if (TWO) zb = fmaf(wy, qb[dy * GF_TJ], zb);
         }
-    }
     return make_float2(za, zb);
 }
 
 // Forward tiles of all frames; body(z, t, in) for each frame's tile, t the thread's sample's
 // index in the frames' layout and in whether the sample exists.  uni: the union footprint (the
 // frames' integer shifts from (ymin, xmin), spread sy x sx); else one frame per item.
-template <bool TWO, typename F>
+template <bool TWO, int TWM, typename F>
 __device__ __forceinline__ void gen_fwd_tiles(const DevProblem &P, int uni, int cta, int ctas,
                                               const float *__restrict__ a, const float *__restrict__ b, float *sm,
                                               F &&body) {
@@ -415,12 +409,12 @@ __device__ __forceinline__ void gen_fwd_tiles(const DevProblem &P, int uni, int 
         if (uni) {
             gen_stage<TWO>(P, i0, j0, ymin, xmin, URH, URW, a, b, ra, rb);
             for (int k = 0; k < P.K; ++k) {
-                const float2 z = gen_eval<TWO>(P, k, i0, j0, P.ty[k] - ymin, P.tx[k] - xmin, URW, ra, rb, ha, hb);
+                const float2 z = gen_eval<TWO, TWM>(P, k, i0, j0, P.ty[k] - ymin, P.tx[k] - xmin, URW, ra, rb, ha, hb);
                 body(z, ((size_t)k * P.h + i) * P.w + j, in);
             }
         } else {
             gen_stage<TWO>(P, i0, j0, P.ty[k0], P.tx[k0], URH, URW, a, b, ra, rb);
-            const float2 z = gen_eval<TWO>(P, k0, i0, j0, 0, 0, URW, ra, rb, ha, hb);
+            const float2 z = gen_eval<TWO, TWM>(P, k0, i0, j0, 0, 0, URW, ra, rb, ha, hb);
             body(z, ((size_t)k0 * P.h + i) * P.w + j, in);
         }
     }
@@ -431,7 +425,7 @@ __device__ __forceinline__ void gen_fwd_tiles(const DevProblem &P, int uni, int 
 // - alpha zp) (for L2 alpha zp (2 e' - alpha zp)), and the data part of p.H p, DS sum w zp^2
 // (w = 1 for L2, psi_d''(e') for L1; DS = 2 for L2, 1 for L1).  Kept per sample for C and D:
 // DS psi_d'(e') (2 e' for L2), zp and w.  Tile g_ctas + blockIdx.x.
-template <bool L1>
+template <bool L1, int TWM>
 __global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restrict__ probs, int pidx, int mode,
                                                      double probe_alpha, double probe_beta, int uni) {
     extern __shared__ float gsm[];
@@ -442,7 +436,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restric
     const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
     const float alpha = s.alpha, deps = P.data_eps, deps2 = deps * deps;
     float jd = 0.f, dj = 0.f, cd = 0.f;
-    gen_fwd_tiles<true>(P, uni, blockIdx.x, gridDim.x, Xn, Pn, gsm, [&](float2 z, size_t t, bool in) {
+    gen_fwd_tiles<true, TWM>(P, uni, blockIdx.x, gridDim.x, Xn, Pn, gsm, [&](float2 z, size_t t, bool in) {
         if (!in) return;
         const float e = z.x - P.Yg[t], zp = z.y, abp = alpha * zp;
         const float de2 = abp * fmaf(2.f, e, -abp);   // e'^2 - (e' - alpha zp)^2
@@ -470,70 +464,87 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restric
     gen_write_sums<3>(P, P.g_ctas + blockIdx.x, fld, val);
 }
 
-// C: r'(u, v) = -(sum_k A_k^T (DS psi_d'(e'_k)) + lambda grad BTV(x')) over adjoint tiles (one
-// HR pixel per thread: warp w takes HR row u0 + w); |r'|^2, r'.r, p.r'.  Tile 2 g_ctas + blockIdx.x.
-__global__ void __launch_bounds__(GEN_NT) gen_pass_c(const DevProblem *__restrict__ probs, int pidx, int mode,
-                                                     double probe_alpha, double probe_beta, int kc) {
-    extern __shared__ float gsm[];
+// C, in two stages (no shared memory).  C1, the adjoint's horizontal part for every LR row i of
+// every frame and every HR column v: T[k][i][v] = sum_j Tx[k][j][v - f j - ox_k] DS psi_d'(e'_k)(i, j)
+// over the j with 0 <= v - f j - ox_k < tw (ox_k = tx_k - R).  C2, the vertical part and r':
+// r'(u, v) = -(sum_k sum_i Ty[k][i][u - f i - oy_k] T[k][i][v] + lambda grad BTV(x')(u, v)), the
+// i with 0 <= u - f i - oy_k < tw; |r'|^2, r'.r, p.r' (tile 2 g_ctas + blockIdx.x).  Items of both:
+// GEN_SEG columns of one row, thread t taking columns c0 + t + GEN_NT q, q < 4.
+constexpr int GEN_SEG = 4 * GEN_NT;
+template <int TWM>
+__global__ void __launch_bounds__(GEN_NT) gen_pass_c1(const DevProblem *__restrict__ probs, int pidx, int mode,
+                                                      double probe_alpha, double probe_beta) {
+    const DevProblem &P = probs[pidx];
+    const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
+    if (s.done) return;
+    const int f = P.f, h = P.h, w = P.w, tw = P.g_tw, W = P.W;
+    const unsigned fm = gen_fdiv_magic(f);
+    const int segs = (W + GEN_SEG - 1) / GEN_SEG, items = P.K * h * segs;   // < 2^31 (plan check)
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int r = it / segs, c0 = (it - r * segs) * GEN_SEG, k = r / h;
+        const int ox = P.tx[k] - P.g_r;
+        const float *__restrict__ er = P.Eg + (size_t)r * w;
+        const float *__restrict__ Txk = P.Tx + (size_t)k * w * tw;
+        float *__restrict__ tr = P.Tg + (size_t)r * W;
+#pragma unroll
+        for (int q = 0; q < GEN_SEG / GEN_NT; ++q) {
+            const int v = c0 + (int)threadIdx.x + GEN_NT * q;
+            if (v >= W) continue;
+            const int b = v - ox;
+            const int jlo = max(gen_fdiv(b - tw + f, f, fm), 0), jhi = min(gen_fdiv(b, f, fm), w - 1);
+            float sum = 0.f;
+#pragma unroll
+            for (int n = 0; n < TWM; ++n) {
+                const int j = jlo + n;
+                if (j <= jhi) sum = fmaf(__ldg(Txk + j * tw + (b - f * j)), __ldg(er + j), sum);
+            }
+            tr[v] = sum;
+        }
+    }
+}
+
+template <int TWM>
+__global__ void __launch_bounds__(GEN_NT) gen_pass_c2(const DevProblem *__restrict__ probs, int pidx, int mode,
+                                                      double probe_alpha, double probe_beta) {
     const DevProblem &P = probs[pidx];
     const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
     if (s.done) return;
     const float *__restrict__ R = P.Rv[s.cur];
     const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
     float *__restrict__ Rn = P.Rv[s.cur ^ 1];
-    const int f = P.f, h = P.h, w = P.w, tw = P.g_tw, gr = P.g_r, H = P.H, W = P.W, K = P.K;
-    const int LI = gen_adj_li(f, tw), LJ = gen_adj_lj(f, tw);
-    float *es = gsm, *hs = gsm + kc * LI * LJ;   // kc frames' staged samples, then their row sums
-    const int tiles_x = (W + GA_TV - 1) / GA_TV, n_t = tiles_x * ((H + GA_TU - 1) / GA_TU);
-    const int uu = threadIdx.x / GA_TV, vv = threadIdx.x % GA_TV;   // warp = HR row, lane = column
+    const int f = P.f, h = P.h, tw = P.g_tw, H = P.H, W = P.W, K = P.K, pitch = P.pitch;
     const unsigned fm = gen_fdiv_magic(f);
+    constexpr int NQ = GEN_SEG / GEN_NT;
+    const int segs = (W + GEN_SEG - 1) / GEN_SEG, items = H * segs;
     float rr = 0.f, rrx = 0.f, pr = 0.f;
-    for (int t = blockIdx.x; t < n_t; t += gridDim.x) {
-        const int ty_ = t / tiles_x, u0 = ty_ * GA_TU, v0 = (t - ty_ * tiles_x) * GA_TV;
-        const int u = u0 + uu, v = v0 + vv;
-        float acc = 0.f;
-        for (int k0 = 0; k0 < K; k0 += kc) {
-            const int nk = min(kc, K - k0);
-            __syncthreads();   // the previous chunk's (or tile's) reads of es and hs are done
-            for (int q = 0; q < nk; ++q) {   // stage: LR rows by warp, columns by lane
-                const int k = k0 + q, oy = P.ty[k] - gr, ox = P.tx[k] - gr;
-                const int IL = gen_fdiv(u0 - oy - tw + f, f, fm), JL = gen_fdiv(v0 - ox - tw + f, f, fm);
-                float *eq = es + q * LI * LJ;
-                for (int li = uu; li < LI; li += GA_TU) {
-                    const int i = IL + li;
-                    const bool row_in = i >= 0 && i < h;
-                    const float *er = P.Eg + (row_in ? ((size_t)k * h + i) * w : 0);
-                    for (int lj = vv; lj < LJ; lj += GA_TV) {
-                        const int j = JL + lj;
-                        eq[li * LJ + lj] = (row_in && j >= 0 && j < w) ? er[j] : 0.f;
-                    }
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int u = it / segs, c0 = (it - u * segs) * GEN_SEG;
+        float acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
+        for (int k = 0; k < K; ++k) {   // the row's LR rows and weights of frame k, once for its columns
+            const int a = u - (P.ty[k] - P.g_r);
+            const int ilo = max(gen_fdiv(a - tw + f, f, fm), 0), ihi = min(gen_fdiv(a, f, fm), h - 1);
+            const float *Tyk = P.Ty + (size_t)k * h * tw;
+#pragma unroll
+            for (int n = 0; n < TWM; ++n) {
+                const int i = ilo + n;
+                if (i > ihi) break;
+                const float wy = __ldg(Tyk + i * tw + (a - f * i));
+                const float *__restrict__ tr = P.Tg + ((size_t)k * h + i) * W;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int v = c0 + (int)threadIdx.x + GEN_NT * q;
+                    if (v < W) acc[q] = fmaf(wy, __ldcs(tr + v), acc[q]);
                 }
-            }
-            __syncthreads();
-            for (int q = 0; q < nk; ++q) {   // horizontal: lane = HR column; its LR columns once per frame
-                const int k = k0 + q, ox = P.tx[k] - gr, b = v - ox;
-                const int JL = gen_fdiv(v0 - ox - tw + f, f, fm);
-                const int jlo = max(gen_fdiv(b - tw + f, f, fm), 0), jhi = min(gen_fdiv(b, f, fm), w - 1);
-                const float *Txk = P.Tx + (size_t)k * w * tw, *eq = es + q * LI * LJ;
-                float *hq = hs + q * LI * GA_TV;
-                for (int li = uu; li < LI; li += GA_TU) {
-                    float sum = 0.f;
-                    for (int j = jlo; j <= jhi; ++j) sum = fmaf(__ldg(Txk + j * tw + (b - f * j)), eq[li * LJ + (j - JL)], sum);
-                    hq[li * GA_TV + vv] = sum;
-                }
-            }
-            __syncthreads();
-            for (int q = 0; q < nk; ++q) {   // vertical
-                const int k = k0 + q, oy = P.ty[k] - gr, a = u - oy;
-                const int IL = gen_fdiv(u0 - oy - tw + f, f, fm);
-                const int ilo = max(gen_fdiv(a - tw + f, f, fm), 0), ihi = min(gen_fdiv(a, f, fm), h - 1);
-                const float *Tyk = P.Ty + (size_t)k * h * tw, *hq = hs + q * LI * GA_TV;
-                for (int i = ilo; i <= ihi; ++i) acc = fmaf(__ldg(Tyk + i * tw + (a - f * i)), hq[(i - IL) * GA_TV + vv], acc);
             }
         }
-        if (u < H && v < W) {
-            const size_t o = (size_t)u * P.pitch + v;
-            const float rn = -(acc + Rn[o]);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int v = c0 + (int)threadIdx.x + GEN_NT * q;
+            if (v >= W) continue;
+            const size_t o = (size_t)u * pitch + v;
+            const float rn = -(acc[q] + Rn[o]);
             Rn[o] = rn;
             rr = fmaf(rn, rn, rr);
             rrx = fmaf(rn, R[o], rrx);
@@ -551,7 +562,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_c(const DevProblem *__restric
 // lambda sum_d gamma_d sum_q psi''(x'_q - x'_{q+d}) (a_q - a_{q+d}) (b_q - b_{q+d}) for
 // (a, b) = (r', r'), (r', p), (p, p), psi''(t) = eps^2 / (t^2 + eps^2)^(3/2).
 // Tile 3 g_ctas + blockIdx.x.
-template <bool L1>
+template <bool L1, int TWM>
 __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restrict__ probs, int pidx, int mode,
                                                      double probe_alpha, double probe_beta, int uni) {
     __shared__ float xs[GEN_FH * GEN_FW], rs[GEN_FH * GEN_FW], qs[GEN_FH * GEN_FW];
@@ -565,7 +576,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     if ((int)blockIdx.x < G) {
         extern __shared__ float gsm[];
         float a = 0.f, b = 0.f;
-        gen_fwd_tiles<false>(P, uni, blockIdx.x, G, Rn, nullptr, gsm, [&](float2 z, size_t t, bool in) {
+        gen_fwd_tiles<false, TWM>(P, uni, blockIdx.x, G, Rn, nullptr, gsm, [&](float2 z, size_t t, bool in) {
             if (!in) return;
             const float zr = z.x, wzr = L1 ? P.Wg[t] * zr : zr;
             a = fmaf(wzr, zr, a);
