@@ -43,11 +43,12 @@ WORKLOADS = {
 PASS_BYTES_PER_PX = 28  # fused pass: read x, r, p_old, Y; write x', r', p (float32)
 # Frame-wise pass (frames that do not interleave), f = 2 with 4 frames (one LR sample per HR
 # pixel), every image read or written once by each kernel that uses it: A reads x, r, p_old and
-# writes x', p, lambda grad BTV (24); B reads x', p, the frames and writes DS psi_d', A p and
-# (L1) psi_d'' (24); C1 reads DS psi_d' and writes the adjoint's horizontal part, K h W floats
-# (4 + 8); C2 reads that, lambda grad BTV, r, p and writes r' (8 + 16); D reads r', (L1) psi_d'',
-# A p (12) and x', r', p (12).  108 B/px with the L1 term, 100 with L2.
-GEN_PASS_BYTES_PER_PX_L1 = 108
+# writes x', p, lambda grad BTV (24); F1 reads x', p and writes their horizontal parts, 2 K H w
+# floats (8 + 16); B reads those and the frames and writes DS psi_d', A p and (L1) psi_d''
+# (16 + 4 + 12); C1 reads DS psi_d' and writes the adjoint's horizontal part, K h W floats
+# (4 + 8); C2 reads that, lambda grad BTV, r, p and writes r' (8 + 16); F1 of r' (4 + 8); D reads
+# its part, (L1) psi_d'', A p (16) and x', r', p (12).  156 B/px with the L1 term, 148 with L2.
+GEN_PASS_BYTES_PER_PX_L1 = 156
 
 
 def load_peaks():
@@ -273,11 +274,11 @@ def measure_study(args, wl, xt, stream, dist, device, peak):
     out.update({"model": ("2048^2 -> 4096^2, f=2, shifts (dx, dy) (0.5, 0), (0, 0.5), (-0.5, 0), (0, -0.5) LR px, "
                           "2x2 binning D, 3x3 Gaussian sigma 0.5, L1 data term eps_d 0.01, lambda 0.05, BTV alpha "
                           "0.4 w 3 eps 1e-3, 20 SCG iterations"),
-                "pass": "frame-wise (5 gather kernels and the reduction per SCG pass)",
+                "pass": "frame-wise (7 gather kernels and the reduction per SCG pass)",
                 "pass_bytes_per_px": GEN_PASS_BYTES_PER_PX_L1, "pass_achieved_gbs": gen_achieved,
                 "pass_frac": gen_achieved / peak,
                 "frac_basis": "frac and achieved_gbs: the fused pass's 28 B/px; pass_frac: the frame-wise pass's "
-                              "own 108 B/px"})
+                              "own 156 B/px"})
     return out
 
 

@@ -446,20 +446,6 @@ static misr_status set_pass_attrs() {
             });
             if (r != MISR_OK) return r;
         }
-    // the frame-wise pass's tiles: their shared memory grows with the factor and the taps
-    // (at most GEN_SMEM_MAX bytes, a forward tile of two images at f = MAXF, GEN_TW taps)
-    const int gmax = (int)GEN_SMEM_MAX;
-    for (int twm : {4, 8, GEN_TW}) {
-        const cudaError_t ge = with_gen_taps(twm, [&](auto T) {
-            constexpr int t = decltype(T)::value;
-            cudaError_t e = cudaFuncSetAttribute(gen_pass_b<false, t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(gen_pass_b<true, t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(gen_pass_d<false, t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(gen_pass_d<true, t>, cudaFuncAttributeMaxDynamicSharedMemorySize, gmax);
-            return e;
-        });
-        CK(ge);
-    }
     g_pass_dev[dev].attrs = true;
     return MISR_OK;
 }
@@ -594,16 +580,8 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
             GenRun g;
             g.pidx = idx[i];
             g.ctas = recs[i]->g_ctas;
-            g.f = recs[i]->f;
             g.tw = recs[i]->g_tw;
-            g.K = recs[i]->K;
-            int y0 = recs[i]->ty[0], y1 = y0, x0 = recs[i]->tx[0], x1 = x0;
-            for (int k = 1; k < g.K; ++k) {
-                y0 = std::min(y0, recs[i]->ty[k]); y1 = std::max(y1, recs[i]->ty[k]);
-                x0 = std::min(x0, recs[i]->tx[k]); x1 = std::max(x1, recs[i]->tx[k]);
-            }
-            g.sy = y1 - y0;
-            g.sx = x1 - x0;
+
             g.l1 = recs[i]->l1 != 0;
             segs.gen.push_back(g);
         }
@@ -796,7 +774,8 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
         const size_t segs = (size_t)(hp.W + 1023) / 1024;
         if ((size_t)d.K * ((hp.h + 7) / 8) * ((hp.w + 31) / 32) >= (1u << 31) ||
             (size_t)((hp.H + 15) / 16) * ((hp.W + 31) / 32) >= (1u << 31) ||
-            (size_t)d.K * hp.h * segs >= (1u << 31))
+            (size_t)d.K * hp.h * segs >= (1u << 31) ||
+            (size_t)d.K * hp.H * ((hp.w + 1023) / 1024) >= (1u << 31))
             return fail(MISR_EINVAL, "frame-wise pass: more than 2^31 tiles");
         set_shape(hp, DEFAULT_SHAPE);
         hp.g_ctas = (int)std::min<size_t>(148 * 8, std::max<size_t>(1, (n_max + 2047) / 2048));
@@ -819,7 +798,7 @@ static misr_status fill_problem(const misr_desc &d, int iters, int shape, DevPro
 // buffers DS psi_d'(e'), A_k p and psi_d''(e'), the tap tables.
 struct PlanLayout {
     size_t img, rp_img, o_img, o_part, o_gpart, o_cnt, o_work, o_st, o_tr, o_pr, o_tm, o_gl, total;
-    size_t lr, o_gy, o_ge, o_gap, o_gw, o_gty, o_gtx, o_gt;
+    size_t lr, o_gy, o_ge, o_gap, o_gw, o_gty, o_gtx, o_gt, o_gh;
 };
 static PlanLayout plan_layout(const misr_desc &d, const DevProblem &hp) {
     PlanLayout L{};
@@ -846,6 +825,7 @@ static PlanLayout plan_layout(const misr_desc &d, const DevProblem &hp) {
         L.o_gty = off; off += align_up((size_t)d.K * hp.h * hp.g_tw * sizeof(float), 256);
         L.o_gtx = off; off += align_up((size_t)d.K * hp.w * hp.g_tw * sizeof(float), 256);
         L.o_gt = off; off += align_up((size_t)d.K * hp.h * hp.W * sizeof(float), 256);
+        L.o_gh = off; off += 2 * align_up((size_t)d.K * hp.H * hp.w * sizeof(float), 256);
     }
     L.total = off;
     return L;
@@ -890,19 +870,17 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
     if (r != MISR_OK) return r;
     // frame-wise problems: their four kernels each, one after the other
     for (const GenRun &g : segs.gen) {
-        // the union footprint of all frames where it is small
-        const int uni = gen_fwd_union(g.f, g.tw, g.sy, g.sx) ? 1 : 0;
-        const int sy = uni ? g.sy : 0, sx = uni ? g.sx : 0;
-        const size_t sb = gen_fwd_smem(g.f, g.tw, 2, sy, sx), sd = gen_fwd_smem(g.f, g.tw, 1, sy, sx);
         gen_pass_a<<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
         with_gen_taps(g.tw, [&](auto T) {
             constexpr int twm = decltype(T)::value;
-            if (g.l1) gen_pass_b<true, twm><<<g.ctas, GEN_NT, sb, s>>>(probs, g.pidx, mode, alpha, beta, uni);
-            else gen_pass_b<false, twm><<<g.ctas, GEN_NT, sb, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+            gen_pass_f1<twm, true><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            if (g.l1) gen_pass_b<true, twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            else gen_pass_b<false, twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
             gen_pass_c1<twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
             gen_pass_c2<twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-            if (g.l1) gen_pass_d<true, twm><<<2 * g.ctas, GEN_NT, sd, s>>>(probs, g.pidx, mode, alpha, beta, uni);
-            else gen_pass_d<false, twm><<<2 * g.ctas, GEN_NT, sd, s>>>(probs, g.pidx, mode, alpha, beta, uni);
+            gen_pass_f1<twm, false><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            if (g.l1) gen_pass_d<true, twm><<<2 * g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            else gen_pass_d<false, twm><<<2 * g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
             return 0;
         });
         CK(cudaGetLastError());
@@ -1048,6 +1026,8 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
         hp.Ty = (float *)(b + lay.o_gty);
         hp.Tx = (float *)(b + lay.o_gtx);
         hp.Tg = (float *)(b + lay.o_gt);
+        hp.Hg[0] = (float *)(b + lay.o_gh);
+        hp.Hg[1] = (float *)(b + lay.o_gh + align_up((size_t)d.K * hp.H * hp.w * sizeof(float), 256));
     }
     {
         const misr_status ms = make_maps(hp);

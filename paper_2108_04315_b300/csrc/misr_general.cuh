@@ -15,13 +15,15 @@
 //
 // One pass computes what the fused pass computes (p = r + beta p_old, x' = x + alpha p,
 // r' = -grad J(x'), and the ten sums J_data(x'), J_data(x') - J_data(x), R_BTV(x') + eps
-// pairs, |r'|^2, r'.r, p.r', |p|^2, r'.H r', r'.H p, p.H p), in five kernels:
+// pairs, |r'|^2, r'.r, p.r', |p|^2, r'.H r', r'.H p, p.H p), in seven kernels:
 //   gen_pass_a  (HR)  p, x', the BTV value and lambda grad BTV(x') into r's buffer; |p|^2
-//   gen_pass_b  (LR)  A_k x', A_k p: the residual, J_data, dJ_data, the data part of p.H p;
-//                     DS psi_d'(e'), A_k p and psi_d''(e') kept per sample
+//   gen_pass_f1 (HR rows x LR columns)  the forward's horizontal part of x' and p, every frame
+//   gen_pass_b  (LR)  its vertical part, A_k x', A_k p: the residual, J_data, dJ_data, the data
+//                     part of p.H p; DS psi_d'(e'), A_k p and psi_d''(e') kept per sample
 //   gen_pass_c1 (LR rows x HR columns)  the adjoint's horizontal part of every frame
 //   gen_pass_c2 (HR)  its vertical part, r' = -(A^T DS psi_d' + lambda grad BTV); |r'|^2, r'.r, p.r'
-//   gen_pass_d  (LR)  A_k r': the data parts of r'.H r' and r'.H p;
+//   gen_pass_f1 (HR rows x LR columns)  the forward's horizontal part of r'
+//   gen_pass_d  (LR)  its vertical part, A_k r': the data parts of r'.H r' and r'.H p;
 //               (HR)  the BTV parts of the three curvature forms (second half of its CTAs)
 // then reduce_kernel sums the tiles and runs the SCG tail.  Each CTA writes one tile of sums
 // (every field, zero where the kernel has no part), so the tail sees the same fields.
@@ -284,181 +286,130 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_a(const DevProblem *__restric
     gen_write_sums<2>(P, blockIdx.x, fld, val);
 }
 
-// Separable tiles of the data term.  Forward: a tile of GF_TI x GF_TJ LR samples (one per
-// thread: warp w takes LR row i0 + w).  The HR footprint of the tile is staged in shared memory
-// (0 outside the image: the tables' masks then see what the definitions give), either once for
-// all frames (their integer shifts spread over sy x sx pixels: the union footprint) or per frame;
-// per frame, a horizontal pass forms, per footprint row and LR column, sum_dx Tx[k][j][dx]
-// x(row, .), and a vertical pass sum_dy Ty[k][i][dy] of those.  (The adjoint, gen_pass_c1 and
-// gen_pass_c2, needs no staging.)
-constexpr int GF_TI = 8, GF_TJ = 32;
-static_assert(GF_TI * GF_TJ == GEN_NT, "one sample per thread");
-__host__ __device__ inline int gen_fwd_rh(int f, int tw) { return f * (GF_TI - 1) + tw; }
-__host__ __device__ inline int gen_fwd_rw(int f, int tw) { return f * (GF_TJ - 1) + tw; }
-// Dynamic shared memory (bytes) of a forward tile over na images whose staged footprint is
-// widened by (sy, sx).
-__host__ __device__ inline size_t gen_fwd_smem(int f, int tw, int na, int sy, int sx) {
-    const size_t rh = gen_fwd_rh(f, tw), rw = gen_fwd_rw(f, tw);
-    return (size_t)na * ((rh + sy) * (rw + sx) + rh * GF_TJ) * sizeof(float);
-}
-// the largest forward tile of one frame: two images, f = MAXF, GEN_TW taps (162 KB)
-constexpr size_t GEN_SMEM_MAX = 2 * ((size_t)(MAXF * (GF_TI - 1) + GEN_TW) * (MAXF * (GF_TJ - 1) + GEN_TW) +
-                                     (size_t)(MAXF * (GF_TI - 1) + GEN_TW) * GF_TJ) * sizeof(float);
-static_assert(GEN_SMEM_MAX + 16384 <= 227 * 1024, "frame-wise tiles fit the shared memory of a CTA");
-// The union footprint is staged when it is at most twice one frame's and its tile fits
-// GEN_SMEM_MAX.
-__host__ __device__ inline bool gen_fwd_union(int f, int tw, int sy, int sx) {
-    const long rh = gen_fwd_rh(f, tw), rw = gen_fwd_rw(f, tw);
-    return (rh + sy) * (rw + sx) <= 2 * rh * rw && gen_fwd_smem(f, tw, 2, sy, sx) <= GEN_SMEM_MAX;
-}
-
-// Stage the footprint of the LR tile at (i0, j0) for integer shifts (ty0 .. ty0 + sy, tx0 .. tx0
-// + sx): URH x URW pixels of a (and b) from HR row f i0 + ty0 - R, column f j0 + tx0 - R.
-template <bool TWO>
-__device__ __forceinline__ void gen_stage(const DevProblem &P, int i0, int j0, int ty0, int tx0, int URH, int URW,
-                                          const float *__restrict__ a, const float *__restrict__ b, float *ra,
-                                          float *rb) {
-    const int f = P.f, H = P.H, W = P.W, pitch = P.pitch;
-    const int U0 = f * i0 + ty0 - P.g_r, V0 = f * j0 + tx0 - P.g_r;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();   // the previous tile's reads of the buffers are done
-    for (int r = warp; r < URH; r += GEN_NT / 32) {   // footprint rows by warp, columns by lane
-        const int u = U0 + r;
-        const bool row_in = u >= 0 && u < H;
-        const float *ar = a + (row_in ? (size_t)u * pitch : 0), *br = TWO ? b + (row_in ? (size_t)u * pitch : 0) : nullptr;
-        for (int c = lane; c < URW; c += 32) {
-            const int v = V0 + c;
-            const bool in = row_in && v >= 0 && v < W;
-            ra[r * URW + c] = in ? ar[v] : 0.f;
-            if (TWO) rb[r * URW + c] = in ? br[v] : 0.f;
-        }
-    }
-    __syncthreads();
-}
-
-// A_k a (and A_k b) for the thread's sample (i0 + tid / GF_TJ, j0 + tid % GF_TJ) of frame k from
-// the staged footprint, frame k's rows and columns starting (dyk, dxk) into it (0 outside the
-// frame).  Every thread of the CTA calls it.
-template <bool TWO, int TWM>
-__device__ __forceinline__ float2 gen_eval(const DevProblem &P, int k, int i0, int j0, int dyk, int dxk, int URW,
-                                           const float *ra, const float *rb, float *ha, float *hb) {
-    const int f = P.f, tw = P.g_tw, RH = gen_fwd_rh(f, tw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();   // the previous frame's reads of ha, hb are done
-    {   // horizontal: lane = LR column of the tile (GF_TJ = 32); its taps in registers
-        const int j = j0 + lane;
-        const bool jin = j < P.w;
-        const float *tx = P.Tx + ((size_t)k * P.w + (jin ? j : 0)) * tw;
-        float wx[TWM];
-#pragma unroll
-        for (int dx = 0; dx < TWM; ++dx) wx[dx] = (jin && dx < tw) ? __ldg(tx + dx) : 0.f;
-        for (int r = warp; r < RH; r += GEN_NT / 32) {
-            const int o = (r + dyk) * URW + f * lane + dxk;
-            float sa = 0.f, sb = 0.f;
-#pragma unroll
-            for (int dx = 0; dx < TWM; ++dx)
-                if (dx < tw) {
-                    sa = fmaf(wx[dx], ra[o + dx], sa);
-                    if (TWO) sb = fmaf(wx[dx], rb[o + dx], sb);
-                }
-            ha[r * GF_TJ + lane] = sa;
-            if (TWO) hb[r * GF_TJ + lane] = sb;
-        }
-    }
-    __syncthreads();
-    const int ii = warp, i = i0 + ii;
-    const bool in = i < P.h && j0 + lane < P.w;
-    const float *ty = P.Ty + ((size_t)k * P.h + (i < P.h ? i : 0)) * tw;
-    const float *qa = ha + f * ii * GF_TJ + lane, *qb = hb + f * ii * GF_TJ + lane;
-    float za = 0.f, zb = 0.f;
-#pragma unroll
-    for (int dy = 0; dy < TWM; ++dy)
-        if (dy < tw) {
-            const float wy = in ? __ldg(ty + dy) : 0.f;
-            za = fmaf(wy, qa[dy * GF_TJ], za);
-            if (TWO) zb = fmaf(wy, qb[dy * GF_TJ], zb);
-        }
-    return make_float2(za, zb);
-}
-
-// Forward tiles of all frames; body(z, t, in) for each frame's tile, t the thread's sample's
-// index in the frames' layout and in whether the sample exists.  uni: the union footprint (the
-// frames' integer shifts from (ymin, xmin), spread sy x sx); else one frame per item.
-template <bool TWO, int TWM, typename F>
-__device__ __forceinline__ void gen_fwd_tiles(const DevProblem &P, int uni, int cta, int ctas,
-                                              const float *__restrict__ a, const float *__restrict__ b, float *sm,
-                                              F &&body) {
-    const int f = P.f, tw = P.g_tw, RH = gen_fwd_rh(f, tw), RW = gen_fwd_rw(f, tw);
-    int ymin = P.ty[0], ymax = P.ty[0], xmin = P.tx[0], xmax = P.tx[0];
-    for (int k = 1; k < P.K; ++k) {
-        ymin = min(ymin, P.ty[k]); ymax = max(ymax, P.ty[k]);
-        xmin = min(xmin, P.tx[k]); xmax = max(xmax, P.tx[k]);
-    }
-    const int URH = uni ? RH + ymax - ymin : RH, URW = uni ? RW + xmax - xmin : RW;
-    float *ra = sm, *rb = sm + URH * URW;
-    float *ha = sm + (TWO ? 2 : 1) * URH * URW, *hb = ha + RH * GF_TJ;
-    // (the plan keeps K nti ntj below 2^31: 32-bit item indices)
-    const int nti = (P.h + GF_TI - 1) / GF_TI, ntj = (P.w + GF_TJ - 1) / GF_TJ;
-    const int per_frame = nti * ntj, items = uni ? per_frame : per_frame * P.K;
-    const int ii = threadIdx.x / GF_TJ, jj = threadIdx.x % GF_TJ;
-    for (int it = cta; it < items; it += ctas) {
-        const int k0 = uni ? 0 : it / per_frame, rem = it - k0 * per_frame;
-        const int ti = rem / ntj, tj = rem - ti * ntj;
-        const int i0 = ti * GF_TI, j0 = tj * GF_TJ, i = i0 + ii, j = j0 + jj;
-        const bool in = i < P.h && j < P.w;
-        if (uni) {
-            gen_stage<TWO>(P, i0, j0, ymin, xmin, URH, URW, a, b, ra, rb);
-            for (int k = 0; k < P.K; ++k) {
-                const float2 z = gen_eval<TWO, TWM>(P, k, i0, j0, P.ty[k] - ymin, P.tx[k] - xmin, URW, ra, rb, ha, hb);
-                body(z, ((size_t)k * P.h + i) * P.w + j, in);
-            }
-        } else {
-            gen_stage<TWO>(P, i0, j0, P.ty[k0], P.tx[k0], URH, URW, a, b, ra, rb);
-            const float2 z = gen_eval<TWO, TWM>(P, k0, i0, j0, 0, 0, URW, ra, rb, ha, hb);
-            body(z, ((size_t)k0 * P.h + i) * P.w + j, in);
-        }
-    }
-}
-
-// B: per LR sample of every frame, z = A_k x', zp = A_k p and the residual e' = z - y; the data
-// term's value psi_d(e') (e'^2 for L2), its change from x = x' - alpha p, psi_d(e') - psi_d(e'
-// - alpha zp) (for L2 alpha zp (2 e' - alpha zp)), and the data part of p.H p, DS sum w zp^2
-// (w = 1 for L2, psi_d''(e') for L1; DS = 2 for L2, 1 for L1).  Kept per sample for C and D:
-// DS psi_d'(e') (2 e' for L2), zp and w.  Tile g_ctas + blockIdx.x.
-template <bool L1, int TWM>
-__global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restrict__ probs, int pidx, int mode,
-                                                     double probe_alpha, double probe_beta, int uni) {
-    extern __shared__ float gsm[];
+// The forward operator in two stages (no shared memory).  F1, the horizontal part for every HR
+// row u of every frame and every LR column j: Hg[0][k][u][j] = sum_dx Tx[k][j][dx] a(u, f j + ox_k
+// + dx) over the columns inside the grid (ox_k = tx_k - R), and Hg[1] the same of b (TWO: a = x',
+// b = p for B; else a = r' for D).  F2, in B and D: the vertical part for the LR sample (i, j),
+// sum_dy Ty[k][i][dy] Hg[k][f i + oy_k + dy][j] over the rows inside the grid.  Items: GEN_SEG
+// columns of one row, thread t taking columns c0 + t + GEN_NT q, q < 4.
+constexpr int GEN_SEG = 4 * GEN_NT;
+template <int TWM, bool TWO>
+__global__ void __launch_bounds__(GEN_NT) gen_pass_f1(const DevProblem *__restrict__ probs, int pidx, int mode,
+                                                      double probe_alpha, double probe_beta) {
     const DevProblem &P = probs[pidx];
     const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
     if (s.done) return;
-    const float *__restrict__ Xn = P.X[s.cur ^ 1];
-    const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
-    const float alpha = s.alpha, deps = P.data_eps, deps2 = deps * deps;
-    float jd = 0.f, dj = 0.f, cd = 0.f;
-    gen_fwd_tiles<true, TWM>(P, uni, blockIdx.x, gridDim.x, Xn, Pn, gsm, [&](float2 z, size_t t, bool in) {
-        if (!in) return;
-        const float e = z.x - P.Yg[t], zp = z.y, abp = alpha * zp;
-        const float de2 = abp * fmaf(2.f, e, -abp);   // e'^2 - (e' - alpha zp)^2
-        if constexpr (L1) {
-            // s = sqrt(e^2 + eps_d^2) as q rsqrt(q); psi_d(e') = e'^2 / (s1 + eps_d), psi_d' = e' / s1,
-            // psi_d'' = eps_d^2 / s1^3, and the change (e'^2 - eb^2) / (s1 + s0)
-            const float q1 = fmaf(e, e, deps2), r1 = rsqrtf(q1), s1 = q1 * r1;
-            const float eb = e - abp, q0 = fmaf(eb, eb, deps2), s0 = q0 * rsqrtf(q0);
-            jd += __fdividef(e * e, s1 + deps);
-            dj += __fdividef(de2, s1 + s0);
-            const float wd = deps2 * (r1 * r1 * r1);
-            cd = fmaf(wd * zp, zp, cd);
-            P.Eg[t] = e * r1;
-            P.Wg[t] = wd;
-        } else {
-            jd = fmaf(e, e, jd);
-            dj += de2;
-            cd = fmaf(zp, zp, cd);
-            P.Eg[t] = 2.f * e;
+    const float *__restrict__ a = TWO ? P.X[s.cur ^ 1] : P.Rv[s.cur ^ 1];
+    const float *__restrict__ b = P.Pv[s.pcur ^ 1];
+    const int f = P.f, H = P.H, W = P.W, w = P.w, tw = P.g_tw, pitch = P.pitch;
+    const int segs = (w + GEN_SEG - 1) / GEN_SEG, items = H * segs;
+    // items by HR row segment, every frame inside: the frames' reads of the row hit L1
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int u = it / segs, c0 = (it - u * segs) * GEN_SEG;
+        const float *__restrict__ ar = a + (size_t)u * pitch;
+        const float *__restrict__ br = b + (size_t)u * pitch;
+        for (int k = 0; k < P.K; ++k) {
+            const int ox = P.tx[k] - P.g_r;
+            const float *__restrict__ Txk = P.Tx + (size_t)k * w * tw;
+            float *__restrict__ ha = P.Hg[0] + ((size_t)k * H + u) * w;
+            float *__restrict__ hb = P.Hg[1] + ((size_t)k * H + u) * w;
+#pragma unroll
+            for (int q = 0; q < GEN_SEG / GEN_NT; ++q) {
+                const int j = c0 + (int)threadIdx.x + GEN_NT * q;
+                if (j >= w) continue;
+                const int v0 = f * j + ox;
+                float sa = 0.f, sb = 0.f;
+#pragma unroll
+                for (int dx = 0; dx < TWM; ++dx) {
+                    const int v = v0 + dx;
+                    if (dx < tw && v >= 0 && v < W) {
+                        const float wx = __ldg(Txk + j * tw + dx);
+                        sa = fmaf(wx, ar[v], sa);
+                        if (TWO) sb = fmaf(wx, br[v], sb);
+                    }
+                }
+                ha[j] = sa;
+                if (TWO) hb[j] = sb;
+            }
         }
-        P.APg[t] = zp;
-    });
+    }
+}
+
+// The vertical part of A_k for the samples of LR row i of frame k (columns c0 + t + GEN_NT q):
+// the row's taps once, then per column its rows of Hg[0] (and Hg[1]).
+template <int TWM, bool TWO>
+__device__ __forceinline__ void gen_f2_row(const DevProblem &P, int k, int i, int c0, float (&za)[GEN_SEG / GEN_NT],
+                                           float (&zb)[GEN_SEG / GEN_NT]) {
+    const int f = P.f, H = P.H, w = P.w, tw = P.g_tw;
+    const int u0 = f * i + P.ty[k] - P.g_r;
+    const float *Tyi = P.Ty + ((size_t)k * P.h + i) * tw;
+#pragma unroll
+    for (int q = 0; q < GEN_SEG / GEN_NT; ++q) { za[q] = 0.f; zb[q] = 0.f; }
+#pragma unroll
+    for (int dy = 0; dy < TWM; ++dy) {
+        const int u = u0 + dy;
+        if (dy >= tw || u < 0 || u >= H) continue;
+        const float wy = __ldg(Tyi + dy);
+        const float *__restrict__ ha = P.Hg[0] + ((size_t)k * H + u) * w;
+        const float *__restrict__ hb = P.Hg[1] + ((size_t)k * H + u) * w;
+#pragma unroll
+        for (int q = 0; q < GEN_SEG / GEN_NT; ++q) {
+            const int j = c0 + (int)threadIdx.x + GEN_NT * q;
+            if (j < w) {
+                za[q] = fmaf(wy, __ldcs(ha + j), za[q]);
+                if (TWO) zb[q] = fmaf(wy, __ldcs(hb + j), zb[q]);
+            }
+        }
+    }
+}
+
+// B: per LR sample of every frame, z = A_k x', zp = A_k p (F2 over F1's rows) and the residual
+// e' = z - y; the data term's value psi_d(e') (e'^2 for L2), its change from x = x' - alpha p,
+// psi_d(e') - psi_d(e' - alpha zp) (for L2 alpha zp (2 e' - alpha zp)), and the data part of p.H p,
+// DS sum w zp^2 (w = 1 for L2, psi_d''(e') for L1; DS = 2 for L2, 1 for L1).  Kept per sample for
+// C and D: DS psi_d'(e') (2 e' for L2), zp and w.  Tile g_ctas + blockIdx.x.
+template <bool L1, int TWM>
+__global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restrict__ probs, int pidx, int mode,
+                                                     double probe_alpha, double probe_beta) {
+    const DevProblem &P = probs[pidx];
+    const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
+    if (s.done) return;
+    const float alpha = s.alpha, deps = P.data_eps, deps2 = deps * deps;
+    const int h = P.h, w = P.w;
+    constexpr int NQ = GEN_SEG / GEN_NT;
+    const int segs = (w + GEN_SEG - 1) / GEN_SEG, items = P.K * h * segs;
+    float jd = 0.f, dj = 0.f, cd = 0.f;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int r = it / segs, c0 = (it - r * segs) * GEN_SEG, k = r / h, i = r - k * h;
+        float zx[NQ], zq[NQ];
+        gen_f2_row<TWM, true>(P, k, i, c0, zx, zq);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int j = c0 + (int)threadIdx.x + GEN_NT * q;
+            if (j >= w) continue;
+            const size_t t = (size_t)r * w + j;
+            const float e = zx[q] - P.Yg[t], zp = zq[q], abp = alpha * zp;
+            const float de2 = abp * fmaf(2.f, e, -abp);   // e'^2 - (e' - alpha zp)^2
+            if constexpr (L1) {
+                // s = sqrt(e^2 + eps_d^2) as q rsqrt(q); psi_d(e') = e'^2 / (s1 + eps_d), psi_d' = e' / s1,
+                // psi_d'' = eps_d^2 / s1^3, and the change (e'^2 - eb^2) / (s1 + s0)
+                const float q1 = fmaf(e, e, deps2), r1 = rsqrtf(q1), s1 = q1 * r1;
+                const float eb = e - abp, q0 = fmaf(eb, eb, deps2), s0 = q0 * rsqrtf(q0);
+                jd += __fdividef(e * e, s1 + deps);
+                dj += __fdividef(de2, s1 + s0);
+                const float wd = deps2 * (r1 * r1 * r1);
+                cd = fmaf(wd * zp, zp, cd);
+                P.Eg[t] = e * r1;
+                P.Wg[t] = wd;
+            } else {
+                jd = fmaf(e, e, jd);
+                dj += de2;
+                cd = fmaf(zp, zp, cd);
+                P.Eg[t] = 2.f * e;
+            }
+            P.APg[t] = zp;
+        }
+    }
     const int fld[3] = {P_JD, P_DJD, P_C};
     const float val[3] = {jd, dj, (L1 ? 1.f : 2.f) * cd};
     gen_write_sums<3>(P, P.g_ctas + blockIdx.x, fld, val);
@@ -470,7 +421,6 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restric
 // r'(u, v) = -(sum_k sum_i Ty[k][i][u - f i - oy_k] T[k][i][v] + lambda grad BTV(x')(u, v)), the
 // i with 0 <= u - f i - oy_k < tw; |r'|^2, r'.r, p.r' (tile 2 g_ctas + blockIdx.x).  Items of both:
 // GEN_SEG columns of one row, thread t taking columns c0 + t + GEN_NT q, q < 4.
-constexpr int GEN_SEG = 4 * GEN_NT;
 template <int TWM>
 __global__ void __launch_bounds__(GEN_NT) gen_pass_c1(const DevProblem *__restrict__ probs, int pidx, int mode,
                                                       double probe_alpha, double probe_beta) {
@@ -556,7 +506,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_c2(const DevProblem *__restri
     gen_write_sums<3>(P, 2 * P.g_ctas + blockIdx.x, fld, val);
 }
 
-// D, CTAs [0, g_ctas): per LR sample, zr = A_k r'; the data parts of r'.H r' and r'.H p,
+// D, CTAs [0, g_ctas): per LR sample, zr = A_k r' (F2 over F1's rows of r'); the data parts of r'.H r' and r'.H p,
 // DS sum w zr^2 and DS sum w zr zp.  CTAs [g_ctas, 2 g_ctas): per HR tile (x', r', p of the tile
 // and its far-side halo in shared memory), the prior's parts of the three forms,
 // lambda sum_d gamma_d sum_q psi''(x'_q - x'_{q+d}) (a_q - a_{q+d}) (b_q - b_{q+d}) for
@@ -564,7 +514,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_c2(const DevProblem *__restri
 // Tile 3 g_ctas + blockIdx.x.
 template <bool L1, int TWM>
 __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restrict__ probs, int pidx, int mode,
-                                                     double probe_alpha, double probe_beta, int uni) {
+                                                     double probe_alpha, double probe_beta) {
     __shared__ float xs[GEN_FH * GEN_FW], rs[GEN_FH * GEN_FW], qs[GEN_FH * GEN_FW];
     const DevProblem &P = probs[pidx];
     const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
@@ -573,15 +523,25 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     const float *__restrict__ Rn = P.Rv[s.cur ^ 1];
     const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
     const int G = P.g_ctas;
-    if ((int)blockIdx.x < G) {
-        extern __shared__ float gsm[];
+    if ((int)blockIdx.x < G) {   // A_k r' by F2 over F1's rows of r'
+        const int h = P.h, w = P.w;
+        constexpr int NQ = GEN_SEG / GEN_NT;
+        const int segs = (w + GEN_SEG - 1) / GEN_SEG, items = P.K * h * segs;
         float a = 0.f, b = 0.f;
-        gen_fwd_tiles<false, TWM>(P, uni, blockIdx.x, G, Rn, nullptr, gsm, [&](float2 z, size_t t, bool in) {
-            if (!in) return;
-            const float zr = z.x, wzr = L1 ? P.Wg[t] * zr : zr;
-            a = fmaf(wzr, zr, a);
-            b = fmaf(wzr, P.APg[t], b);
-        });
+        for (int it = blockIdx.x; it < items; it += G) {
+            const int r = it / segs, c0 = (it - r * segs) * GEN_SEG, k = r / h, i = r - k * h;
+            float zr[NQ], unused[NQ];
+            gen_f2_row<TWM, false>(P, k, i, c0, zr, unused);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int j = c0 + (int)threadIdx.x + GEN_NT * q;
+                if (j >= w) continue;
+                const size_t t = (size_t)r * w + j;
+                const float wzr = L1 ? P.Wg[t] * zr[q] : zr[q];
+                a = fmaf(wzr, zr[q], a);
+                b = fmaf(wzr, P.APg[t], b);
+            }
+        }
         const float ds = L1 ? 1.f : 2.f;
         const int fld[2] = {P_A, P_B};
         const float val[2] = {ds * a, ds * b};

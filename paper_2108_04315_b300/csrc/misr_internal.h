@@ -68,8 +68,7 @@ struct StreamRun {
 // kernels run per problem, before the fused launches, and its groups join the reduction.
 struct GenRun {
     int pidx = 0, ctas = 0;
-    int f = 1, tw = 1;                   // factor and taps per axis (the kernels' shared memory)
-    int K = 1, sy = 0, sx = 0;           // frames, and the spread of their integer shifts
+    int tw = 1;                          // taps per axis (the kernels' compiled bucket)
     bool l1 = false;
 };
 struct PassSegs {

@@ -142,6 +142,7 @@ struct DevProblem {
     float *APg;                                   // [K][h][w] A_k p
     float *Wg;                                    // [K][h][w] psi_d''(e') (L1 data term)
     float *Tg;                                    // [K][h][W] the adjoint's horizontal part
+    float *Hg[2];                                 // [K][H][w] the forward's horizontal parts
 };
 // taps per axis of a frame's D B M_k at most (binning f, PSF 2 PSF_R + 1, bilinear + 1); tiles
 // of sums per CTA of the frame-wise pass's kernels
