@@ -3,7 +3,9 @@ configuration bench.py times (its tile shape tuned first): the forward operator 
 gradient over the whole image, a short solve, the full 100-iteration solve against the
 oracle's committed run (tests/golden/detector_100it.json, written by
 tests/golden/make_golden.py from oracle calls alone) and a live 20-iteration solve element by
-element, against the FP64 oracle; and the precision workload's size (u16 counts -> 6144^2)."""
+element, against the FP64 oracle; the precision workload's size (u16 counts -> 6144^2); and the
+synthetic study's frame set at the headline size as bench.py times it (the frame-wise pass):
+forward, gradient and a short solve against the oracle."""
 import json
 
 import numpy as np
@@ -164,4 +166,38 @@ def test_precision_size_gradient_against_oracle(orc):
     Jr, gr = P.gradient(x.astype(np.float64), y64)
     assert rel_l2(g.cpu().numpy(), gr) <= RTOL_OP
     assert J == pytest.approx(Jr, rel=RTOL_J)
+    plan.close()
+
+
+def test_study_frames_full_size(orc):
+    """bench.py's synthetic_study_frames workload: 4 x 2048^2 frames with the one-pixel shifts
+    right, down, left and up, 2x2 binning, 3x3 Gaussian PSF sigma 0.5, the L1 data term (eps_d
+    0.01), lambda 0.05 (the frame-wise pass): every frame of the forward operator, the gradient
+    and a 5-iteration solve against the oracle."""
+    from paper_2108_04315_b300 import binding as B
+    from tests.gpu_common import STUDY_SHIFTS
+    h = w = 2048
+    f, psf, eps_d = 2, gen.gaussian_psf(3, 0.5), 0.01
+    kw_o = dict(lam=0.05, decimation=orc.DECIM_BIN, data_norm=orc.NORM_L1, data_eps=eps_d)
+    P = orc.Problem(h, w, f, STUDY_SHIFTS, psf, **kw_o)
+    xt = gen.phantom(f * h, f * w, gen.CONFIG_SEEDS["detector"])
+    y = (P.forward_all(xt) + gen.gaussian_noise((4, h, w), 0.01, gen.CONFIG_SEEDS["detector"] + 1)).astype(np.float32)
+    kw_p = dict(lam=0.05, decimation=B.MISR_DECIM_BIN, data_norm=B.MISR_NORM_L1, data_eps=eps_d)
+    plan = B.Plan(h, w, f, STUDY_SHIFTS, psf, iters=5, **kw_p)
+    yf = plan.forward(to_dev(xt.astype(np.float32))).cpu().numpy()
+    ref = P.forward_all(xt.astype(np.float32).astype(np.float64))
+    for k in range(4):
+        assert rel_l2(yf[k], ref[k]) <= RTOL_OP, k
+    x = (xt + 0.05 * gen.smooth_field(f * h, f * w, 71)).astype(np.float32)
+    J, g = plan.gradient(to_dev(y), to_dev(x))
+    Jr, gr = P.gradient(x.astype(np.float64), y.astype(np.float64))
+    tol = RTOL_OP + 16 * 2.0 ** -24 * float(np.abs(y).max()) / eps_d
+    assert rel_l2(g.cpu().numpy(), gr) <= tol
+    assert J == pytest.approx(Jr, rel=RTOL_J)
+    xs, st = plan.solve(to_dev(y))
+    y64 = y.astype(np.float64)
+    xr, _ = P.scg(y64, P.shift_add(y64), 5)
+    assert st["iters_done"] == 5
+    assert rel_l2(xs.cpu().numpy(), xr) <= RTOL_X
+    assert st["J_final"] == pytest.approx(P.objective(xr, y64), rel=RTOL_J)
     plan.close()
