@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -425,12 +426,44 @@ static misr_status current_device(int *dev) {
     return MISR_OK;
 }
 
+// Grid of a frame-wise kernel: at most `want` CTAs, at most as many as are resident at once on
+// the current device (one wave); cached per device and kernel.
+template <typename... A>
+static int gen_grid(void (*kernel)(A...), int want) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(dev, reinterpret_cast<const void *>(kernel));
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        int per_sm = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, GEN_NT, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        it = cache.emplace(key, std::max(1, per_sm) * std::max(1, sms)).first;
+    }
+    return std::max(1, std::min(want, it->second));
+}
+
 // the frame-wise pass's kernels are compiled for at most 4, 8 or GEN_TW taps per axis
 template <typename F>
 auto with_gen_taps(int tw, F &&f) {
     if (tw <= 4) return f(std::integral_constant<int, 4>());
     if (tw <= 8) return f(std::integral_constant<int, 8>());
     return f(std::integral_constant<int, GEN_TW>());
+}
+// the occupancy of a frame-wise plan's kernels, queried once before any stream capture
+static void gen_prime_grids(int tw) {
+    gen_grid(gen_pass_a, 1);
+    with_gen_taps(tw, [](auto T) {
+        constexpr int t = decltype(T)::value;
+        gen_grid(gen_pass_f1<t, true>, 1); gen_grid(gen_pass_f1<t, false>, 1);
+        gen_grid(gen_pass_b<true, t>, 1); gen_grid(gen_pass_b<false, t>, 1);
+        gen_grid(gen_pass_c1<t>, 1); gen_grid(gen_pass_c2<t>, 1);
+        return 0;
+    });
 }
 
 static misr_status set_pass_attrs() {
@@ -870,17 +903,22 @@ misr_status misr_host::launch_pass_raw(const DevProblem *probs, const int2 *tile
     if (r != MISR_OK) return r;
     // frame-wise problems: their four kernels each, one after the other
     for (const GenRun &g : segs.gen) {
-        gen_pass_a<<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+        // each kernel in one wave, at most its resident CTAs (measured faster for all but D, whose
+        // two roles run g_ctas CTAs each: one wave of its own 4 per SM left each role too few)
+        const int G = g.ctas;
+        gen_pass_a<<<gen_grid(gen_pass_a, G), GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
         with_gen_taps(g.tw, [&](auto T) {
             constexpr int twm = decltype(T)::value;
-            gen_pass_f1<twm, true><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-            if (g.l1) gen_pass_b<true, twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-            else gen_pass_b<false, twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-            gen_pass_c1<twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-            gen_pass_c2<twm><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-            gen_pass_f1<twm, false><<<g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-            if (g.l1) gen_pass_d<true, twm><<<2 * g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
-            else gen_pass_d<false, twm><<<2 * g.ctas, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            auto kb = g.l1 ? gen_pass_b<true, twm> : gen_pass_b<false, twm>;
+            auto kd = g.l1 ? gen_pass_d<true, twm> : gen_pass_d<false, twm>;
+            const int hd = G;
+            gen_pass_f1<twm, true><<<gen_grid(gen_pass_f1<twm, true>, G), GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            kb<<<gen_grid(kb, G), GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            gen_pass_c1<twm><<<gen_grid(gen_pass_c1<twm>, G), GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            gen_pass_c2<twm><<<gen_grid(gen_pass_c2<twm>, G), GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta);
+            gen_pass_f1<twm, false><<<gen_grid(gen_pass_f1<twm, false>, G), GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha,
+                                                                                          beta);
+            kd<<<2 * hd, GEN_NT, 0, s>>>(probs, g.pidx, mode, alpha, beta, hd);
             return 0;
         });
         CK(cudaGetLastError());
@@ -1049,6 +1087,7 @@ misr_status misr_plan_create(const misr_desc *desc, misr_plan_t *out) {
             (e = cudaMemcpy(p->dtile, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
             break;
         if (p->hp.general) {
+            gen_prime_grids(p->hp.g_tw);
             std::vector<float> Ty, Tx;
             if ((rs = gen_tables(d, p->hp, Ty, Tx)) != MISR_OK) break;
             if ((e = cudaMemcpy(p->hp.Ty, Ty.data(), Ty.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) break;

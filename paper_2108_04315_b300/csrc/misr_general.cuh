@@ -26,7 +26,9 @@
 //   gen_pass_d  (LR)  its vertical part, A_k r': the data parts of r'.H r' and r'.H p;
 //               (HR)  the BTV parts of the three curvature forms (second half of its CTAs)
 // then reduce_kernel sums the tiles and runs the SCG tail.  Each CTA writes one tile of sums
-// (every field, zero where the kernel has no part), so the tail sees the same fields.
+// (every field, zero where the kernel has no part), so the tail sees the same fields; a kernel
+// runs at most g_ctas CTAs per role (as many as are resident at once), and the slots of CTAs it
+// does not run hold the zeros the plan's workspace starts with.
 // Per-thread sums are FP32 over the thread's grid-stride elements, the CTA sums FP64.
 #pragma once
 
@@ -511,10 +513,10 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_c2(const DevProblem *__restri
 // and its far-side halo in shared memory), the prior's parts of the three forms,
 // lambda sum_d gamma_d sum_q psi''(x'_q - x'_{q+d}) (a_q - a_{q+d}) (b_q - b_{q+d}) for
 // (a, b) = (r', r'), (r', p), (p, p), psi''(t) = eps^2 / (t^2 + eps^2)^(3/2).
-// Tile 3 g_ctas + blockIdx.x.
+// The grid is 2 half CTAs (half <= g_ctas); tiles 3 g_ctas + blockIdx.x and 4 g_ctas + blockIdx.x - half.
 template <bool L1, int TWM>
 __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restrict__ probs, int pidx, int mode,
-                                                     double probe_alpha, double probe_beta) {
+                                                     double probe_alpha, double probe_beta, int half) {
     __shared__ float xs[GEN_FH * GEN_FW], rs[GEN_FH * GEN_FW], qs[GEN_FH * GEN_FW];
     const DevProblem &P = probs[pidx];
     const GenStep s = gen_step(P, mode, probe_alpha, probe_beta);
@@ -522,13 +524,13 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     const float *__restrict__ Xn = P.X[s.cur ^ 1];
     const float *__restrict__ Rn = P.Rv[s.cur ^ 1];
     const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
-    const int G = P.g_ctas;
-    if ((int)blockIdx.x < G) {   // A_k r' by F2 over F1's rows of r'
+    const int G = P.g_ctas;   // tile slots per role (half <= G CTAs take each role)
+    if ((int)blockIdx.x < half) {   // A_k r' by F2 over F1's rows of r'
         const int h = P.h, w = P.w;
         constexpr int NQ = GEN_SEG / GEN_NT;
         const int segs = (w + GEN_SEG - 1) / GEN_SEG, items = P.K * h * segs;
         float a = 0.f, b = 0.f;
-        for (int it = blockIdx.x; it < items; it += G) {
+        for (int it = blockIdx.x; it < items; it += half) {
             const int r = it / segs, c0 = (it - r * segs) * GEN_SEG, k = r / h, i = r - k * h;
             float zr[NQ], unused[NQ];
             gen_f2_row<TWM, false>(P, k, i, c0, zr, unused);
@@ -555,7 +557,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     for (int d = 0; d < BTV_W * BTV_W; ++d) gm[d] = P.gamma[d];
     const int tiles_x = (W + GEN_TILE_W - 1) / GEN_TILE_W, n_t = tiles_x * ((H + GEN_TILE_H - 1) / GEN_TILE_H);
     float a = 0.f, b = 0.f, c = 0.f;
-    for (int t = (int)blockIdx.x - G; t < n_t; t += G) {
+    for (int t = (int)blockIdx.x - half; t < n_t; t += half) {
         const int y0 = (t / tiles_x) * GEN_TILE_H, x0 = (t % tiles_x) * GEN_TILE_W;
         for (int e = threadIdx.x; e < GEN_FH * GEN_FW; e += GEN_NT) {
             const int ry = e / GEN_FW, rx = e - ry * GEN_FW, u = y0 + ry, v = x0 + rx;
@@ -594,7 +596,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     const float lam = P.lambda;
     const int fld[3] = {P_A, P_B, P_C};
     const float val[3] = {lam * a, lam * b, lam * c};
-    gen_write_sums<3>(P, 3 * G + blockIdx.x, fld, val);
+    gen_write_sums<3>(P, 4 * G + (int)blockIdx.x - half, fld, val);
 }
 
 }  // namespace misr
