@@ -161,8 +161,9 @@ const char *misr_last_error(void);
 /* Validate the descriptor and build a plan on the current device: the separable PSF taps,
  * the phase-to-frame table and the device workspace of one solve (7 HR float32 images plus
  * O(tiles) partial sums; for the frame-wise pass also a copy of the frames, three per-sample
- * buffers and the per-frame, per-row tap tables of D B M_k, computed here in FP64), allocated
- * here with cudaMalloc.  The plan plays the part of the
+ * buffers, the horizontal parts of the operator and of its adjoint (2 K H w + K h W floats) and
+ * the per-frame, per-row tap tables of D B M_k, computed here in FP64), allocated here with
+ * cudaMalloc.  The plan plays the part of the
  * system matrices that the paper builds once per scan and reuses for every rotation angle
  * (Sec. 3.2); no matrix is formed.
  * Errors: MISR_EINVAL (descriptor), MISR_ENOMEM, MISR_ECUDA, MISR_ENOTIMPL. */
