@@ -22,17 +22,24 @@ OPTIONS = [
 
 
 def case(orc, opt, seed, iters=10, shape=0):
+    """shape: a MISR_TILE_* shape, or "frame" for the synthetic study's frame set with binning
+    (the frame-wise pass, whose prior kernels are its own)"""
     from paper_2108_04315_b300 import binding as B
+    from tests.gpu_common import STUDY_SHIFTS
     lam, w_, a_, eps = opt
     h, w, f, shifts, psf = 37, 53, 2, gen.half_pixel_shifts(), asym_separable_psf(3)
-    P = orc.Problem(h, w, f, shifts, psf, lam=lam, btv_alpha=a_, btv_w=w_, eps=eps)
+    kw_o, kw_p = {}, {"tile_shape": shape}
+    if shape == "frame":
+        shifts, psf = STUDY_SHIFTS, asym_separable_psf(3, 3)
+        kw_o, kw_p = {"decimation": orc.DECIM_BIN}, {"decimation": B.MISR_DECIM_BIN}
+    P = orc.Problem(h, w, f, shifts, psf, lam=lam, btv_alpha=a_, btv_w=w_, eps=eps, **kw_o)
     xt = gen.phantom(f * h, f * w, seed)
     y = (P.forward_all(xt) + gen.gaussian_noise((4, h, w), 0.01, seed + 1)).astype(np.float32)
-    plan = B.Plan(h, w, f, shifts, psf, lam=lam, btv_alpha=a_, btv_w=w_, eps=eps, iters=iters, tile_shape=shape)
+    plan = B.Plan(h, w, f, shifts, psf, lam=lam, btv_alpha=a_, btv_w=w_, eps=eps, iters=iters, **kw_p)
     return P, plan, xt, y
 
 
-@pytest.mark.parametrize("shape", [0, 4])   # the size default (tiles) and MISR_TILE_STREAM
+@pytest.mark.parametrize("shape", [0, 4, "frame"])   # the size default (tiles), MISR_TILE_STREAM, frame-wise
 @pytest.mark.parametrize("opt", OPTIONS, ids=[f"lam{o[0]}_w{o[1]}_a{o[2]}_eps{o[3]}" for o in OPTIONS])
 def test_prior_options_gradient_and_pass(orc, opt, shape):
     P, plan, xt, y = case(orc, opt, 100, shape=shape)
@@ -54,12 +61,13 @@ def test_prior_options_gradient_and_pass(orc, opt, shape):
         assert abs(S[k] - v) <= RTOL_OP * abs(v) + slack, (k, S[k], v)
 
 
-@pytest.mark.parametrize("shape", [0, 4])
+@pytest.mark.parametrize("shape", [0, 4, "frame"])
 @pytest.mark.parametrize("opt", OPTIONS, ids=[f"lam{o[0]}_w{o[1]}_a{o[2]}_eps{o[3]}" for o in OPTIONS])
 def test_prior_options_solve(orc, opt, shape):
-    P, plan, xt, y = case(orc, opt, 200, iters=10, shape=shape)
+    iters = 7 if shape == "frame" else 10   # the study's frames: the FP32-state floor of the L2 term
+    P, plan, xt, y = case(orc, opt, 200, iters=iters, shape=shape)
     y64 = y.astype(np.float64)
     xg, st = plan.solve(to_dev(y))
-    xr, tr = P.scg(y64, P.shift_add(y64), 10)
+    xr, tr = P.scg(y64, P.shift_add(y64), iters)
     assert rel_l2(xg.cpu().numpy(), xr) <= RTOL_X
     assert st["J_final"] == pytest.approx(P.objective(xr, y64), rel=1e-4)
