@@ -295,14 +295,18 @@ misr_status misr_get_trace(misr_plan_t plan, double *out, int32_t max_rows, int3
 /* ---- Batched solves (many projections per launch) ---------------------------------------
  * A batch groups plans (uneven sizes, factors, frame counts, tile shapes, r/p storage types,
  * data terms, decimations and shift sets are fine; all on one device) so that every SCG step of
- * all of them is one fused-pass launch over the tiles of all projections (one per tile shape
- * and kernel variant present), then one reduction launch, replayed as a CUDA graph.  The CT setting of Sec. 3.2 produces one independent projection per
+ * all of them is one fused-pass launch over the tiles of the projections that share launches
+ * (one per tile shape and kernel variant present), then one reduction launch, while each
+ * projection that fills the GPU on its own (or runs the frame-wise pass) takes its own plan's
+ * pass on a stream of its own, forked and joined within the step; the steps are replayed as a
+ * CUDA graph.  The CT setting of Sec. 3.2 produces one independent projection per
  * rotation angle; a batch advances many of them at once.  Each projection keeps its own
  * workspace, SCG state and fixed-order reductions, so its result equals its own misr_solve.
  * A plan may belong to several batches but runs one solve at a time. */
 typedef struct misr_batch_s *misr_batch_t;
 
-/* Build the batch tables (problem records, the combined tile and group lists) on the plans' device.
+/* Build the batch tables (problem records, the shared tile and group lists, the streams of the
+ * projections that launch alone) on the plans' device.
  * plans: n plans (host array, copied).  Errors: MISR_EINVAL, MISR_ENOMEM, MISR_ECUDA. */
 misr_status misr_batch_create(int32_t n, const misr_plan_t *plans, misr_batch_t *out);
 
@@ -324,7 +328,9 @@ misr_status misr_batch_solve(misr_batch_t batch, const void *const *y_dev, float
  * the HBM budget, and idle slots of other classes are freed to make room.  Every tick runs
  * passes_per_tick fused-pass launches over the tiles of all live slots (one SCG iteration per
  * launch for each), so a request that arrives while others are on the GPU joins the next
- * launch.  The worker queues a tick before it reads the states of the previous one, so the GPU
+ * launch; a slot whose projection fills the GPU on its own (or runs the frame-wise pass) takes
+ * its passes on a stream of its own, forked from the worker's stream and joined back within
+ * the tick, so that independent projections' launches overlap.  The worker queues a tick before it reads the states of the previous one, so the GPU
  * does not wait for the host between ticks.  Finished projections are copied out and their
  * slots reused.  Each projection keeps its own state and fixed-order reductions: its result is
  * the same alone and in the mix.  A request's frames are read once, when it is admitted (into

@@ -544,6 +544,12 @@ StreamConsts misr_host::stream_consts(const DevProblem &p) {
     return k;
 }
 
+bool misr_host::launch_alone(const DevProblem &p) {
+    if (p.general) return true;
+    if (p.shape != STREAM_SHAPE) return false;
+    return 2L * p.n_tiles >= 8L * resident_ctas(STREAM_SHAPE, pass_variant(p));
+}
+
 void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, const std::vector<int> &idx,
                                  std::vector<int2> &tiles, std::vector<int2> &groups, PassSegs &segs) {
     segs = PassSegs{};
@@ -582,10 +588,9 @@ void misr_host::build_pass_lists(const std::vector<const DevProblem *> &recs, co
                 // a problem whose items fill at least half the grid's warps gets a launch of its
                 // own, split as planned (merged, such problems ran slower than one after another:
                 // the launch's last items straggled); smaller ones share launches
-                const long grid_warps = 8L * resident_ctas(STREAM_SHAPE, v);
                 for (size_t i = 0; i < recs.size(); ++i) {
                     if (recs[i]->general || recs[i]->shape != sh || pass_variant(*recs[i]) != v) continue;
-                    const bool alone = 2L * recs[i]->n_tiles >= grid_warps;
+                    const bool alone = launch_alone(*recs[i]);
                     if (!run.empty()) {
                         const StreamConsts a = stream_consts(*recs[run[0]]), b = stream_consts(*recs[i]);
                         if (alone || std::memcmp(&a, &b, sizeof(a)) != 0) flush();

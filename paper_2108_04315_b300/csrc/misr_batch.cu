@@ -1,6 +1,7 @@
 // Batched SCG solves: many independent projections (uneven sizes, magnification factors and
-// frame counts) advanced together, one fused-pass launch per SCG step over the tiles of all of
-// them, the step loop replayed as a CUDA graph.  Each projection keeps its own plan workspace,
+// frame counts) advanced together, one fused-pass launch per SCG step over the tiles of those
+// that share launches and each of the others' own pass on a stream of its own, the step loop replayed
+// as a CUDA graph.  Each projection keeps its own plan workspace,
 // SCG state and fixed-order reductions, so its result is the same alone and in a batch.
 #include <cuda_runtime.h>
 
@@ -19,13 +20,21 @@ struct misr_batch_s {
     int n = 0;
     std::vector<misr_plan_t> plans;
     DevProblem *dprobs = nullptr;   // n problem records (copies of the plans' records)
-    int2 *ditems = nullptr;         // tiles of all problems, problem after problem
     unsigned int *work = nullptr;   // the fused pass's tile counter
     void *mem = nullptr;
-    int total_items = 0;            // tiles, by segment
-    PassSegs segs;
-    int total_groups = 0;           // groups (listed after the tiles in ditems)
     int max_iters = 0;
+    // Problems whose passes run in launches of their own (launch_alone) take them, in the step
+    // graph, on a stream each (their plan's own pass: its lists and tile counter), forked from
+    // the capture stream and joined back; the others share the step's launches.  Independent
+    // problems' launches then overlap, the next one filling the SMs the last items of the
+    // previous one leave idle.
+    std::vector<int> own;           // indices of those problems
+    PassSegs segs_shared;           // the step's launches over the others
+    int shared_items = 0, shared_groups = 0;
+    int2 *dshared = nullptr;        // their tile list, then their group list
+    std::vector<cudaStream_t> own_streams;
+    std::vector<cudaEvent_t> own_joins;
+    cudaEvent_t fork = nullptr;
     cudaStream_t cap = nullptr;     // private stream used for graph capture
     cudaGraphExec_t chunk = nullptr;
     int chunk_len = 0;
@@ -39,6 +48,11 @@ extern "C" misr_status misr_batch_destroy(misr_batch_t b) {
     DeviceGuard g(b->device);
     cudaDeviceSynchronize();
     if (b->chunk) cudaGraphExecDestroy(b->chunk);
+    for (cudaStream_t st : b->own_streams)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->own_joins)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->st_host) cudaFreeHost(b->st_host);
     if (b->mem) cudaFree(b->mem);
@@ -62,36 +76,48 @@ extern "C" misr_status misr_batch_create(int32_t n, const misr_plan_t *plans, mi
     b->n = n;
     b->plans.assign(plans, plans + n);
     std::vector<DevProblem> recs(n);
-    std::vector<int2> items, groups;
-    std::vector<const DevProblem *> rp(n);
-    std::vector<int> idx(n);
     for (int i = 0; i < n; ++i) {
         recs[i] = plans[i]->hp;
-        rp[i] = &plans[i]->hp;
-        idx[i] = i;
         b->max_iters = std::max(b->max_iters, plans[i]->d.iters);
     }
-    // one pass launch per (tile shape, kernel variant: r/p storage type, data term, tap layout)
-    // present in the batch
-    build_pass_lists(rp, idx, items, groups, b->segs);
-    b->total_items = (int)items.size();
-    b->total_groups = (int)groups.size();
-    items.insert(items.end(), groups.begin(), groups.end());   // tiles, then groups
+    // the shared launches: one per (tile shape, kernel variant: r/p storage type, data term, tap
+    // layout) present among the projections that do not launch alone
+    std::vector<const DevProblem *> rps;
+    std::vector<int> idxs;
+    for (int i = 0; i < n; ++i) {
+        if (launch_alone(plans[i]->hp)) b->own.push_back(i);
+        else { rps.push_back(&plans[i]->hp); idxs.push_back(i); }
+    }
+    std::vector<int2> sitems, sgroups;
+    if (!rps.empty()) build_pass_lists(rps, idxs, sitems, sgroups, b->segs_shared);
+    b->shared_items = (int)sitems.size();
+    b->shared_groups = (int)sgroups.size();
+    sitems.insert(sitems.end(), sgroups.begin(), sgroups.end());
     DeviceGuard g(b->device);
     const size_t rec_bytes = round_up(sizeof(DevProblem) * n, 256);
-    const size_t list_bytes = round_up(sizeof(int2) * items.size(), 256);
-    cudaError_t e = cudaMalloc(&b->mem, rec_bytes + list_bytes + 256);
+    const size_t shared_bytes = round_up(sizeof(int2) * std::max<size_t>(sitems.size(), 1), 256);
+    cudaError_t e = cudaMalloc(&b->mem, rec_bytes + 256 + shared_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete b;
         return fail(MISR_ENOMEM, "cudaMalloc for the batch tables failed: %s", cudaGetErrorString(e));
     }
     b->dprobs = static_cast<DevProblem *>(b->mem);
-    b->ditems = reinterpret_cast<int2 *>(static_cast<char *>(b->mem) + rec_bytes);
-    b->work = reinterpret_cast<unsigned int *>(static_cast<char *>(b->mem) + rec_bytes + list_bytes);
+    b->work = reinterpret_cast<unsigned int *>(static_cast<char *>(b->mem) + rec_bytes);
+    b->dshared = reinterpret_cast<int2 *>(static_cast<char *>(b->mem) + rec_bytes + 256);
+    b->own_streams.assign(b->own.size(), nullptr);
+    b->own_joins.assign(b->own.size(), nullptr);
     do {
+        if (!sitems.empty() &&
+            (e = cudaMemcpy(b->dshared, sitems.data(), sizeof(int2) * sitems.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            break;
+        if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) break;
+        for (size_t q = 0; q < b->own.size() && e == cudaSuccess; ++q) {
+            e = cudaStreamCreateWithFlags(&b->own_streams[q], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->own_joins[q], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) break;
         if ((e = cudaMemcpy(b->dprobs, recs.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice)) != cudaSuccess) break;
-        if ((e = cudaMemcpy(b->ditems, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess) break;
         if ((e = cudaMemset(b->work, 0, 256)) != cudaSuccess) break;
         if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) break;
         if ((e = cudaMallocHost((void **)&b->st_host, sizeof(ScgState) * n)) != cudaSuccess) break;
@@ -105,6 +131,29 @@ extern "C" misr_status misr_batch_create(int32_t n, const misr_plan_t *plans, mi
     return MISR_OK;
 }
 
+// One SCG step of every projection on stream s: the shared launches over the projections that
+// share them, and each of the others' own pass on its stream, forked from s and joined back.
+static misr_status batch_step(misr_batch_t b, int mode, cudaStream_t s) {
+    if (!b->own.empty()) {
+        CK(cudaEventRecord(b->fork, s));
+        for (cudaStream_t st : b->own_streams) CK(cudaStreamWaitEvent(st, b->fork, 0));
+    }
+    misr_status r = MISR_OK;
+    if (b->segs_shared.total() > 0)
+        r = launch_pass_raw(b->dprobs, b->dshared, b->segs_shared, b->dshared + b->shared_items, b->shared_groups,
+                            b->work, mode, 0.0, 0.0, s);
+    for (size_t q = 0; q < b->own.size() && r == MISR_OK; ++q) {
+        const misr_plan_t p = b->plans[b->own[q]];
+        r = launch_pass_raw(p->dprob, p->dtile, p->segs, p->dgroup, p->hp.n_groups, p->work, mode, 0.0, 0.0,
+                            b->own_streams[q]);
+    }
+    for (size_t q = 0; q < b->own.size(); ++q) {   // join (also after a failed launch: no stream left forked)
+        CK(cudaEventRecord(b->own_joins[q], b->own_streams[q]));
+        CK(cudaStreamWaitEvent(s, b->own_joins[q], 0));
+    }
+    return r;
+}
+
 static misr_status batch_graph(misr_batch_t b) {
     const int want = std::max(1, std::min(b->max_iters, GRAPH_CHUNK));
     if (b->chunk && b->chunk_len == want) return MISR_OK;
@@ -112,9 +161,7 @@ static misr_status batch_graph(misr_batch_t b) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     misr_status r = MISR_OK;
-    for (int i = 0; i < want && r == MISR_OK; ++i)
-        r = launch_pass_raw(b->dprobs, b->ditems, b->segs, b->ditems + b->total_items,
-                            b->total_groups, b->work, MODE_ITER, 0.0, 0.0, b->cap);
+    for (int i = 0; i < want && r == MISR_OK; ++i) r = batch_step(b, MODE_ITER, b->cap);
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (r != MISR_OK) { if (graph) cudaGraphDestroy(graph); return r; }
     if (e != cudaSuccess) return fail(MISR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
@@ -138,9 +185,7 @@ extern "C" misr_status misr_batch_solve(misr_batch_t b, const void *const *y_dev
         const misr_plan_t p = b->plans[i];
         r = launch_prepare_raw(b->dprobs, i, p->hp, p->d, y_dev[i], x_dev[i], p->d.x0_mode, 1 | 2 | 4, s);
     }
-    if (r == MISR_OK)
-        r = launch_pass_raw(b->dprobs, b->ditems, b->segs, b->ditems + b->total_items,
-                            b->total_groups, b->work, MODE_INIT, 0.0, 0.0, s);
+    if (r == MISR_OK) r = batch_step(b, MODE_INIT, s);
     if (r != MISR_OK) return r;
     for (int done = 0; done < b->max_iters; done += b->chunk_len) CK(cudaGraphLaunch(b->chunk, s));
     for (int i = 0; i < b->n && r == MISR_OK; ++i) r = launch_finalize_raw(b->dprobs, i, b->plans[i]->n, x_dev[i], s);

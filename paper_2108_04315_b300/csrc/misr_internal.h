@@ -90,6 +90,10 @@ inline int pass_variant(const misr::DevProblem &p) { return (p.rp_bf16 ? 1 : 0) 
 misr_status launch_pass_raw(const misr::DevProblem *probs, const int2 *tiles, const PassSegs &segs,
                             const int2 *groups, int n_groups, unsigned *work, int mode, double alpha, double beta,
                             cudaStream_t s);
+// Whether a problem's pass runs in launches of its own: a streaming problem whose items fill at
+// least half the grid's warps (merged with others, such problems ran slower than one after
+// another), or a problem of the frame-wise pass (its kernels are per problem).
+bool launch_alone(const misr::DevProblem &p);
 // The tile and group lists of a launch over problems recs[i] (problem index idx[i] in the
 // launch's record array), ordered by segment, each problem's border tiles first.
 void build_pass_lists(const std::vector<const misr::DevProblem *> &recs, const std::vector<int> &idx,

@@ -138,6 +138,13 @@ struct misr_server_s {
     bool items_dirty = true;
     misr_status worker_error = MISR_OK;
     uint64_t passes_launched = 0;
+    // Slots whose problem runs in launches of its own (launch_alone) take their SCG passes on a
+    // stream per slot index, forked from `stream` after the tick's admissions and joined back
+    // before its states are read: independent problems' launches then overlap, the next one
+    // filling the SMs the last items of the previous one leave idle.  Created on first use.
+    std::vector<cudaStream_t> slot_streams;   // [cfg.max_slots]
+    std::vector<cudaEvent_t> slot_joins;      // [cfg.max_slots]
+    cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -158,7 +165,9 @@ misr_status grow_items(misr_server_t s, size_t need) {
 
 // Can a new slot for `d` be created?  (slot count, explicit budget, free device memory)
 bool can_create(misr_server_t s, const misr_desc &d) {
-    if ((int)s->slots.size() >= s->cfg.max_slots) return false;
+    int held = 0;   // slots holding a plan (an evicted slot keeps its index, empty)
+    for (const Slot &sl : s->slots) held += sl.plan != nullptr;
+    if (held >= s->cfg.max_slots) return false;
     const size_t need = plan_bytes_estimate(d);
     if (s->cfg.hbm_budget_bytes > 0) return s->slot_bytes + need <= s->cfg.hbm_budget_bytes;
     size_t free_b = 0, total_b = 0;
@@ -174,6 +183,7 @@ bool evict_idle(misr_server_t s, const DescCopy &want) {
         Slot &sl = s->slots[i];
         if (!sl.busy && sl.plan && !sl.desc.same_class(want)) {
             cudaStreamSynchronize(s->stream);
+            if (s->slot_streams[i]) cudaStreamSynchronize(s->slot_streams[i]);
             misr_plan_t p = sl.plan;
             int2 *items = sl.items;
             {
@@ -430,7 +440,7 @@ void worker_main(misr_server_t s) {
             std::vector<const DevProblem *> rp;
             std::vector<int> idx;
             for (size_t i = 0; i < s->slots.size(); ++i)
-                if (s->slots[i].busy) {
+                if (s->slots[i].busy && !launch_alone(s->slots[i].plan->hp)) {
                     rp.push_back(&s->slots[i].plan->hp);
                     idx.push_back((int)i);
                 }
@@ -448,14 +458,50 @@ void worker_main(misr_server_t s) {
         // 3. k SCG iterations of every live projection, then their states into this tick's
         // half of st_host
         const int nt = s->live_tiles;
-        const bool live = s->live_segs.total() > 0;   // tiles of the fused passes or frame-wise problems
+        std::vector<int> own;   // busy slots that run on their own streams
+        bool live = s->live_segs.total() > 0;
+        for (size_t i = 0; i < s->slots.size(); ++i)
+            if (s->slots[i].busy && launch_alone(s->slots[i].plan->hp)) {
+                own.push_back((int)i);
+                live = true;
+            }
         TickRecord tk;
         tk.buf = buf;
         if (live) {
+            if (!own.empty()) {
+                if (!s->fork && cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess)
+                    r = fail(MISR_ECUDA, "server fork event failed");
+                for (int i : own) {
+                    if (r == MISR_OK && !s->slot_streams[i] &&
+                        cudaStreamCreateWithFlags(&s->slot_streams[i], cudaStreamNonBlocking) != cudaSuccess)
+                        r = fail(MISR_ECUDA, "slot stream failed");
+                    if (r == MISR_OK && !s->slot_joins[i] &&
+                        cudaEventCreateWithFlags(&s->slot_joins[i], cudaEventDisableTiming) != cudaSuccess)
+                        r = fail(MISR_ECUDA, "slot event failed");
+                }
+                if (r == MISR_OK && cudaEventRecord(s->fork, s->stream) != cudaSuccess) r = fail(MISR_ECUDA, "fork failed");
+                for (int i : own)
+                    if (r == MISR_OK && cudaStreamWaitEvent(s->slot_streams[i], s->fork, 0) != cudaSuccess)
+                        r = fail(MISR_ECUDA, "fork wait failed");
+            }
             for (int it = 0; it < k_passes && r == MISR_OK; ++it) {
-                r = launch_pass_raw(s->dprobs, s->ditems, s->live_segs, s->ditems + nt, s->live_groups, s->work,
-                                    MODE_ITER, 0.0, 0.0, s->stream);
-                ++s->passes_launched;
+                if (s->live_segs.total() > 0) {
+                    r = launch_pass_raw(s->dprobs, s->ditems, s->live_segs, s->ditems + nt, s->live_groups, s->work,
+                                        MODE_ITER, 0.0, 0.0, s->stream);
+                    ++s->passes_launched;
+                }
+                for (size_t q = 0; q < own.size() && r == MISR_OK; ++q) {   // each on the slot's plan's counter
+                    Slot &sl = s->slots[own[q]];
+                    r = launch_pass_raw(s->dprobs, sl.items, sl.segs, sl.items + sl.n_list, sl.plan->hp.n_groups,
+                                        sl.plan->work, MODE_ITER, 0.0, 0.0, s->slot_streams[own[q]]);
+                    ++s->passes_launched;
+                }
+            }
+            for (int i : own) {   // join before the states are read
+                if (r == MISR_OK && cudaEventRecord(s->slot_joins[i], s->slot_streams[i]) != cudaSuccess)
+                    r = fail(MISR_ECUDA, "join failed");
+                if (r == MISR_OK && cudaStreamWaitEvent(s->stream, s->slot_joins[i], 0) != cudaSuccess)
+                    r = fail(MISR_ECUDA, "join wait failed");
             }
             ScgState *sth = s->st_host + (size_t)buf * s->cfg.max_slots;
             for (size_t i = 0; i < s->slots.size() && r == MISR_OK; ++i)
@@ -485,6 +531,8 @@ void worker_main(misr_server_t s) {
         }
         if (r != MISR_OK) {   // the stream is unusable: fail what runs and what is queued, stop serving
             cudaStreamSynchronize(s->stream);
+            for (cudaStream_t st : s->slot_streams)
+                if (st) cudaStreamSynchronize(st);
             cudaGetLastError();
             const ScgState none{};
             for (size_t i = 0; i < s->slots.size(); ++i)
@@ -533,6 +581,8 @@ extern "C" misr_status misr_server_create(const misr_server_cfg *cfg, misr_serve
         return r;
     }
     s->slots.reserve(cfg->max_slots);
+    s->slot_streams.assign(cfg->max_slots, nullptr);
+    s->slot_joins.assign(cfg->max_slots, nullptr);
     s->worker = std::thread(worker_main, s);
     *out = s;
     return MISR_OK;
@@ -548,6 +598,14 @@ extern "C" misr_status misr_server_destroy(misr_server_t s) {
     if (s->worker.joinable()) s->worker.join();
     DeviceGuard g(s->device);
     cudaStreamSynchronize(s->stream);
+    for (cudaStream_t st : s->slot_streams)
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    for (cudaEvent_t ev : s->slot_joins)
+        if (ev) cudaEventDestroy(ev);
+    if (s->fork) cudaEventDestroy(s->fork);
     for (auto &sl : s->slots) {
         if (sl.plan) misr_plan_destroy(sl.plan);
         if (sl.items) cudaFree(sl.items);
