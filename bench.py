@@ -847,8 +847,9 @@ def main():
     batch.close()
     for pb in plans_b:
         pb.close()
-    batched = {"value": batched_rate, "unit": UNIT, "projections_per_launch": NB, "over_plain": batched_rate / value,
-               "api": "misr_batch_solve (%d projections of this configuration per fused-pass launch)" % NB}
+    batched = {"value": batched_rate, "unit": UNIT, "projections": NB, "over_plain": batched_rate / value,
+               "api": "misr_batch_solve (%d projections of this configuration; each fills the GPU, so each runs its "
+                      "own pass launches on a stream of its own, overlapped within every step)" % NB}
 
     peak, peak_kind = load_peaks()
     achieved = PASS_BYTES_PER_PX * H * W / (pass_ms * 1e-3) / 1e9
