@@ -1,5 +1,6 @@
 """Batched solves (misr_batch_*): several projections of uneven sizes, magnification factors,
-frame counts and iteration counts advanced by one fused-pass launch per SCG step.  Each
+frame counts and iteration counts advanced by one fused-pass launch per SCG step (and the
+projections that fill the GPU on their own by their own passes on streams of their own).  Each
 projection keeps its own state and fixed-order reductions, so its result must equal its own
 misr_solve bit for bit, and both must match the FP64 oracle."""
 import numpy as np
@@ -55,3 +56,44 @@ def test_batch_rejects_duplicate_plans(orc):
     with pytest.raises(B.MisrError) as e:
         B.Batch([plan, plan])
     assert e.value.status == B.MISR_EINVAL
+
+
+def _large_frames(h, w, seed):
+    """Frames of a 2h x 2w projection made on the device (the oracle is not needed here: the
+    check is bitwise equality with the projection's own misr_solve)."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return (0.5 + 0.1 * torch.rand((4, h, w), device="cuda", generator=g)).contiguous()
+
+
+def test_grid_filling_projections_on_their_own_streams_equal_each_alone():
+    """Projections that fill the GPU on their own (streaming shape, 2048^2 and 2560 x 2048 HR)
+    run their plans' own passes on streams of their own inside the batch step and in the server's
+    ticks, beside a small projection that shares the step's launches: every result equals its
+    own misr_solve bit for bit."""
+    from paper_2108_04315_b300 import binding as B
+    psf = gen.gaussian_psf(5, 0.5)
+    geoms = [(1024, 1024, 6), (1280, 1024, 5), (40, 52, 7)]
+    plans = [B.Plan(h, w, 2, gen.half_pixel_shifts(), psf, iters=it,
+                    tile_shape=B.MISR_TILE_STREAM if h > 100 else B.MISR_TILE_AUTO) for h, w, it in geoms]
+    ys = [_large_frames(h, w, 70 + i) for i, (h, w, _) in enumerate(geoms)]
+    alone = []
+    for p, y in zip(plans, ys):
+        x, st = p.solve(y)
+        alone.append((x.clone(), st))
+    batch = B.Batch(plans)
+    for _ in range(2):   # the step graph replayed
+        xs, stats = batch.solve(ys)
+        for (xa, sa), xb, sb in zip(alone, xs, stats):
+            assert torch.equal(xa, xb) and sa == sb
+    batch.close()
+    srv = B.Server(max_slots=4, passes_per_tick=2)
+    tickets = [srv.submit(y, h, w, 2, gen.half_pixel_shifts(), psf, iters=it,
+                          tile_shape=B.MISR_TILE_STREAM if h > 100 else B.MISR_TILE_AUTO)
+               for (h, w, it), y in zip(geoms, ys)]
+    for t, (xa, sa) in zip(tickets, alone):
+        x, st, _ = srv.wait(t, timeout_s=120.0)
+        assert torch.equal(x, xa) and st == sa
+    srv.close()
+    for p in plans:
+        p.close()
