@@ -36,9 +36,7 @@ namespace misr {
 
 constexpr int GEN_NT = 256;
 
-// floor(a / f) for f > 0 and any sign of a
-__device__ __forceinline__ int gen_floordiv(int a, int f) { return a >= 0 ? a / f : -((-a + f - 1) / f); }
-// The same without a division, for a in [-2^21, 2^22] and f <= 8: a + f 2^21 >= 0, and with
+// floor(a / f) without a division, for a in [-2^21, 2^22] and 1 <= f <= 8: a + f 2^21 >= 0, and with
 // m = ceil(2^32 / f), floor(n m / 2^32) = floor(n / f) for n < 2^25 (the error n (m f - 2^32) /
 // (f 2^32) stays below 1 / f).  m = gen_fdiv_magic(f); f = 1 needs no division.
 constexpr int GEN_DIV_OFF = 1 << 21;
@@ -213,7 +211,7 @@ static_assert(GEN_TILE_H * GEN_TILE_W % GEN_NT == 0, "owned pixels per thread");
 // window (Eq. 8), its gradient gamma_d psi'(x'_q - x'_{q+d}) - gamma_d psi'(x'_{q-d} - x'_q),
 // and the value of the pairs it starts, gamma_d sqrt(t^2 + eps^2).  Per HR tile, x' of the tile
 // and its halo is formed once into shared memory (0 outside the image, where no pair reads).
-// lambda grad BTV(x') goes to r's buffer, which gen_pass_c completes to r'.  Tile blockIdx.x:
+// lambda grad BTV(x') goes to r's buffer, which gen_pass_c2 completes to r'.  Tile blockIdx.x:
 // |p|^2, the BTV value.
 __global__ void __launch_bounds__(GEN_NT) gen_pass_a(const DevProblem *__restrict__ probs, int pidx, int mode,
                                                      double probe_alpha, double probe_beta) {
