@@ -85,3 +85,27 @@ def test_stream_rejects_null_entries():
     with pytest.raises(B.MisrError) as e:
         B.misr_solve_host_many(plan.handle, [y.ctypes.data, 0], [0, 0])
     assert e.value.status == B.MISR_EINVAL
+
+
+def test_stream_frame_wise_projections(orc):
+    """The synthetic study's frame set (the frame-wise pass) streamed from host memory: each
+    projection equals its own misr_solve_host bit for bit, the first one the oracle."""
+    from tests.gpu_common import GENERAL_SEED, general_case
+    P, plan, xt, y0 = general_case(orc, "study_bin_psf3", GENERAL_SEED, iters=7)
+    ys = [y0] + [(y0 + gen.gaussian_noise(y0.shape, 0.05, 3200 + k)).astype(np.float32) for k in range(1, 3)]
+    H, W = plan.H, plan.W
+    alone = []
+    for y in ys:
+        x = np.empty((H, W), dtype=np.float32)
+        st = plan.solve_host(np.ascontiguousarray(y), x)
+        alone.append((x, st))
+    keep = [_pinned(y) for y in ys]
+    outs = [_pinned(np.zeros((H, W), dtype=np.float32)) for _ in ys]
+    stats = plan.solve_host_many([k[1] for k in keep], [o[1] for o in outs])
+    for k in range(len(ys)):
+        assert np.array_equal(outs[k][1], alone[k][0]), f"projection {k}"
+        assert stats[k] == alone[k][1]
+    y64 = ys[0].astype(np.float64)
+    xr, _ = P.scg(y64, P.shift_add(y64), 7)
+    assert rel_l2(outs[0][1], xr) <= RTOL_X
+    plan.close()
