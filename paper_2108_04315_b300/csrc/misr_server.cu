@@ -93,7 +93,9 @@ struct Slot {
     DescCopy desc;
     bool busy = false;
     uint64_t ticket = 0;
-    int passes = 0;        // fused passes run since admission
+    int passes = 0;        // fused passes run since admission (counted as their ticks are read)
+    int queued = 0;        // SCG passes queued since admission: at the plan's iteration count the
+                           // solve ends within them, and the slot gets no more
     int2 *items = nullptr;  // device tile and group lists of this slot alone (for its init pass)
     int n_list = 0;         // tiles in that list (the groups follow)
     PassSegs segs;
@@ -135,6 +137,7 @@ struct misr_server_s {
     cudaEvent_t tick_done[2] = {nullptr, nullptr};
     cudaStream_t fin_stream = nullptr;   // copies of finished images, beside the next tick
     std::vector<int2> h_items;
+    std::vector<int> live_idx;   // the slots in those lists
     bool items_dirty = true;
     misr_status worker_error = MISR_OK;
     uint64_t passes_launched = 0;
@@ -298,6 +301,7 @@ std::vector<int> admit(misr_server_t s) {
         sl.busy = true;
         sl.ticket = rq.ticket;
         sl.passes = 0;
+        sl.queued = 0;
         rq.state = RQ_RUNNING;
         rq.slot = use;
         rq.t_start = now_s();
@@ -328,7 +332,8 @@ void finish(misr_server_t s, int idx, const ScgState &h, misr_status st_code) {
 
 // One tick as queued: the slots (and their tickets) whose states it copies to st_host[buf].
 struct TickRecord {
-    std::vector<std::pair<int, uint64_t>> live;
+    std::vector<std::pair<int, uint64_t>> live;   // (slot, ticket) whose states the tick copies
+    std::vector<char> ran;                         // per entry of live: the tick ran passes on it
     int buf = 0;
 };
 
@@ -359,12 +364,17 @@ misr_status complete_tick(misr_server_t s, const TickRecord &tk, misr_status r) 
                 cancelled[lt.first] = s->reqs[lt.second].cancel;
     }
     std::vector<int> done;
-    for (auto &lt : tk.live) {
+    for (size_t e = 0; e < tk.live.size(); ++e) {
+        const auto &lt = tk.live[e];
         const int i = lt.first;
         Slot &sl = s->slots[i];
         if (!sl.busy || sl.ticket != lt.second) continue;
-        sl.passes += std::max(1, s->cfg.passes_per_tick);
+        if (tk.ran[e]) sl.passes += std::max(1, s->cfg.passes_per_tick);
         if (r != MISR_OK || sth[i].done || cancelled[i]) done.push_back(i);
+        else if (sl.queued >= sl.plan->d.iters && sl.passes >= sl.queued) {   // not done at its count:
+            sl.queued = sl.passes - sl.plan->d.iters;                         // queue passes again
+            s->items_dirty = true;
+        }
     }
     std::vector<misr_status> codes(done.size(), r);
     bool copies = false;
@@ -440,11 +450,13 @@ void worker_main(misr_server_t s) {
             std::vector<const DevProblem *> rp;
             std::vector<int> idx;
             for (size_t i = 0; i < s->slots.size(); ++i)
-                if (s->slots[i].busy && !launch_alone(s->slots[i].plan->hp)) {
+                if (s->slots[i].busy && s->slots[i].queued < s->slots[i].plan->d.iters &&
+                    !launch_alone(s->slots[i].plan->hp)) {
                     rp.push_back(&s->slots[i].plan->hp);
                     idx.push_back((int)i);
                 }
             build_pass_lists(rp, idx, s->h_items, gl, s->live_segs);
+            s->live_idx = idx;
             s->live_tiles = (int)s->h_items.size();
             s->live_groups = (int)gl.size();
             s->h_items.insert(s->h_items.end(), gl.begin(), gl.end());
@@ -458,13 +470,23 @@ void worker_main(misr_server_t s) {
         // 3. k SCG iterations of every live projection, then their states into this tick's
         // half of st_host
         const int nt = s->live_tiles;
-        std::vector<int> own;   // busy slots that run on their own streams
+        std::vector<int> own;       // busy slots that run on their own streams
+        std::vector<int> observe;   // busy slots with no pass queued or in flight (their count is
+                                    // reached, or 0): a state read only, to see them finish
         bool live = s->live_segs.total() > 0;
-        for (size_t i = 0; i < s->slots.size(); ++i)
-            if (s->slots[i].busy && launch_alone(s->slots[i].plan->hp)) {
-                own.push_back((int)i);
+        for (size_t i = 0; i < s->slots.size(); ++i) {
+            const Slot &sl = s->slots[i];
+            if (!sl.busy) continue;
+            if (sl.queued < sl.plan->d.iters) {
+                if (launch_alone(sl.plan->hp)) {
+                    own.push_back((int)i);
+                    live = true;
+                }
+            } else if (sl.passes >= sl.queued) {
+                observe.push_back((int)i);
                 live = true;
             }
+        }
         TickRecord tk;
         tk.buf = buf;
         if (live) {
@@ -503,14 +525,26 @@ void worker_main(misr_server_t s) {
                 if (r == MISR_OK && cudaStreamWaitEvent(s->stream, s->slot_joins[i], 0) != cudaSuccess)
                     r = fail(MISR_ECUDA, "join wait failed");
             }
+            // the states of the slots this tick ran passes on; a slot whose passes now reach its
+            // iteration count gets no more (its last tick decides it)
+            std::vector<int> ran = own;
+            if (s->live_segs.total() > 0) ran.insert(ran.end(), s->live_idx.begin(), s->live_idx.end());
+            const size_t n_ran = ran.size();
+            ran.insert(ran.end(), observe.begin(), observe.end());
             ScgState *sth = s->st_host + (size_t)buf * s->cfg.max_slots;
-            for (size_t i = 0; i < s->slots.size() && r == MISR_OK; ++i)
-                if (s->slots[i].busy) {
-                    if (cudaMemcpyAsync(&sth[i], s->slots[i].plan->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost,
-                                        s->stream) != cudaSuccess)
-                        r = fail(MISR_ECUDA, "state copy failed");
-                    tk.live.push_back({(int)i, s->slots[i].ticket});
-                }
+            for (size_t q = 0; q < ran.size(); ++q) {
+                const int i = ran[q];
+                Slot &sl = s->slots[i];
+                if (r != MISR_OK || !sl.busy) continue;
+                if (cudaMemcpyAsync(&sth[i], sl.plan->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s->stream) !=
+                    cudaSuccess)
+                    r = fail(MISR_ECUDA, "state copy failed");
+                tk.live.push_back({i, sl.ticket});
+                tk.ran.push_back(q < n_ran ? 1 : 0);
+                if (q >= n_ran) continue;   // observed only
+                sl.queued += k_passes;
+                if (sl.queued >= sl.plan->d.iters && !launch_alone(sl.plan->hp)) s->items_dirty = true;
+            }
             if (r == MISR_OK && cudaEventRecord(s->tick_done[buf], s->stream) != cudaSuccess)
                 r = fail(MISR_ECUDA, "tick event failed");
         }
