@@ -36,6 +36,11 @@ namespace misr {
 
 constexpr int GEN_NT = 256;
 
+// Checks of the bounds-checked build (MISR_BOUNDS_CHECK) on the frame-wise pass: the tap index
+// of every adjoint gather (its LR row or column range comes from the division-free floor
+// division) and every CTA's tile slot of sums (each role owns g_ctas slots).
+enum GenBoundsCode { BC_GEN_TAP = 16, BC_GEN_TILE = 17 };
+
 // floor(a / f) without a division, for a in [-2^21, 2^22] and 1 <= f <= 8: a + f 2^21 >= 0, and with
 // m = ceil(2^32 / f), floor(n m / 2^32) = floor(n / f) for n < 2^25 (the error n (m f - 2^32) /
 // (f 2^32) stays below 1 / f).  m = gen_fdiv_magic(f); f = 1 needs no division.
@@ -63,9 +68,11 @@ __device__ __forceinline__ GenStep gen_step(const DevProblem &P, int mode, doubl
 
 // One tile of sums: the CTA's NF per-thread values of fields fld[] summed in FP64 in a fixed
 // order (warp butterfly, then the warps in order), every other field zero.  Every thread of the
-// CTA calls it.
+// CTA calls it.  tile = role * g_ctas + slot, slot < g_ctas.
 template <int NF>
-__device__ __forceinline__ void gen_write_sums(const DevProblem &P, int tile, const int (&fld)[NF], const float (&v)[NF]) {
+__device__ __forceinline__ void gen_write_sums(const DevProblem &P, int role, int slot, const int (&fld)[NF],
+                                               const float (&v)[NF]) {
+    const int tile = role * P.g_ctas + slot;
     __shared__ double red[GEN_NT / 32][NPART];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -76,7 +83,8 @@ __device__ __forceinline__ void gen_write_sums(const DevProblem &P, int tile, co
         if (lane == 0) red[warp][j] = d;
     }
     __syncthreads();
-    if (threadIdx.x < NPART) {
+    if (threadIdx.x < NPART &&
+        MISR_IN_BOUNDS(slot >= 0 && slot < P.g_ctas && tile < P.n_tiles, BC_GEN_TILE, role, slot)) {
         double s = 0.0;
         for (int j = 0; j < NF; ++j)
             if (fld[j] == (int)threadIdx.x)
@@ -283,7 +291,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_a(const DevProblem *__restric
     }
     const int fld[2] = {P_PP, P_JB};
     const float val[2] = {pp, jb};
-    gen_write_sums<2>(P, blockIdx.x, fld, val);
+    gen_write_sums<2>(P, 0, (int)blockIdx.x, fld, val);
 }
 
 // The forward operator in two stages (no shared memory).  F1, the horizontal part for every HR
@@ -412,7 +420,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_b(const DevProblem *__restric
     }
     const int fld[3] = {P_JD, P_DJD, P_C};
     const float val[3] = {jd, dj, (L1 ? 1.f : 2.f) * cd};
-    gen_write_sums<3>(P, P.g_ctas + blockIdx.x, fld, val);
+    gen_write_sums<3>(P, 1, (int)blockIdx.x, fld, val);
 }
 
 // C, in two stages (no shared memory).  C1, the adjoint's horizontal part for every LR row i of
@@ -446,7 +454,8 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_c1(const DevProblem *__restri
 #pragma unroll
             for (int n = 0; n < TWM; ++n) {
                 const int j = jlo + n;
-                if (j <= jhi) sum = fmaf(__ldg(Txk + j * tw + (b - f * j)), __ldg(er + j), sum);
+                if (j <= jhi && MISR_IN_BOUNDS(j >= 0 && b - f * j >= 0 && b - f * j < tw, BC_GEN_TAP, v, j))
+                    sum = fmaf(__ldg(Txk + j * tw + (b - f * j)), __ldg(er + j), sum);
             }
             tr[v] = sum;
         }
@@ -480,6 +489,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_c2(const DevProblem *__restri
             for (int n = 0; n < TWM; ++n) {
                 const int i = ilo + n;
                 if (i > ihi) break;
+                if (!MISR_IN_BOUNDS(i >= 0 && a - f * i >= 0 && a - f * i < tw, BC_GEN_TAP, u, i)) continue;
                 const float wy = __ldg(Tyk + i * tw + (a - f * i));
                 const float *__restrict__ tr = P.Tg + ((size_t)k * h + i) * W;
 #pragma unroll
@@ -503,7 +513,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_c2(const DevProblem *__restri
     }
     const int fld[3] = {P_RR, P_RRX, P_PR};
     const float val[3] = {rr, rrx, pr};
-    gen_write_sums<3>(P, 2 * P.g_ctas + blockIdx.x, fld, val);
+    gen_write_sums<3>(P, 2, (int)blockIdx.x, fld, val);
 }
 
 // D, CTAs [0, g_ctas): per LR sample, zr = A_k r' (F2 over F1's rows of r'); the data parts of r'.H r' and r'.H p,
@@ -522,7 +532,6 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     const float *__restrict__ Xn = P.X[s.cur ^ 1];
     const float *__restrict__ Rn = P.Rv[s.cur ^ 1];
     const float *__restrict__ Pn = P.Pv[s.pcur ^ 1];
-    const int G = P.g_ctas;   // tile slots per role (half <= G CTAs take each role)
     if ((int)blockIdx.x < half) {   // A_k r' by F2 over F1's rows of r'
         const int h = P.h, w = P.w;
         constexpr int NQ = GEN_SEG / GEN_NT;
@@ -545,7 +554,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
         const float ds = L1 ? 1.f : 2.f;
         const int fld[2] = {P_A, P_B};
         const float val[2] = {ds * a, ds * b};
-        gen_write_sums<2>(P, 3 * G + blockIdx.x, fld, val);
+        gen_write_sums<2>(P, 3, (int)blockIdx.x, fld, val);
         return;
     }
     const int H = P.H, W = P.W, pitch = P.pitch;
@@ -594,7 +603,7 @@ __global__ void __launch_bounds__(GEN_NT) gen_pass_d(const DevProblem *__restric
     const float lam = P.lambda;
     const int fld[3] = {P_A, P_B, P_C};
     const float val[3] = {lam * a, lam * b, lam * c};
-    gen_write_sums<3>(P, 4 * G + (int)blockIdx.x - half, fld, val);
+    gen_write_sums<3>(P, 4, (int)blockIdx.x - half, fld, val);
 }
 
 }  // namespace misr

@@ -67,8 +67,37 @@ def run(lib_path):
                 x, _ = p.solve(y)
                 out[f"{name}_d{dt}_n{norm}"] = x.cpu().numpy()
                 p.close()
-    # a batch over mixed geometries, tile shapes and storage types
-    sel = plans[:4]
+    # frame sets that run the frame-wise pass (several frames per phase, shifts outside [0, f),
+    # off-lattice shifts, binning, one-pixel and one-row images, the three tap widths), L2 and
+    # L1, the solve from the shift-and-add start point and the gradient
+    study = [(0.5, 0.0), (0.0, 0.5), (-0.5, 0.0), (0.0, -0.5)]
+    general = {
+        "gen_study_bin": (21, 26, 2, study, gen.gaussian_psf(3, 0.6), B.MISR_DECIM_BIN),
+        "gen_far": (12, 14, 2, [(0.0, 0.0), (8.0, 0.0), (-3.5, 2.25), (30.0, -30.0)], gen.gaussian_psf(3, 0.6),
+                    B.MISR_DECIM_POINT),
+        "gen_off_bin": (13, 15, 2, [(0.1, 0.2), (0.6, 0.05), (0.35, 0.7), (0.8, 0.9)], gen.gaussian_psf(3, 0.6),
+                        B.MISR_DECIM_BIN),
+        "gen_wide_f4": (9, 11, 4, [(0.1, 0.0), (0.6, 0.3), (0.3, 0.8), (-0.4, 0.5)], gen.gaussian_psf(5, 0.8),
+                        B.MISR_DECIM_BIN),
+        "gen_pixel": (1, 1, 2, study, gen.gaussian_psf(5, 0.5), B.MISR_DECIM_POINT),
+        "gen_strip": (1, 61, 2, study, gen.gaussian_psf(3, 0.6), B.MISR_DECIM_BIN),
+        "gen_column": (40, 1, 3, study, gen.gaussian_psf(3, 0.6), B.MISR_DECIM_POINT),
+    }
+    gen_plans = []
+    for i, (name, (h, w, f, shifts, psf, dec)) in enumerate(sorted(general.items())):
+        y = torch.from_numpy(frames(h, w, shifts, 800 + i)).cuda()
+        for norm in (B.MISR_NORM_L2, B.MISR_NORM_L1):
+            p = B.Plan(h, w, f, shifts, psf, iters=4, decimation=dec, data_norm=norm, data_eps=0.05)
+            x, _ = p.solve(y)
+            out[f"{name}_n{norm}"] = x.cpu().numpy()
+            J, g = p.gradient(y, x)
+            out[f"{name}_n{norm}_grad"] = g.cpu().numpy()
+            if norm == B.MISR_NORM_L2:
+                gen_plans.append((p, y))
+            else:
+                p.close()
+    # a batch over mixed geometries, tile shapes and storage types, and two frame-wise problems
+    sel = plans[:4] + gen_plans[:2]
     batch = B.Batch([p for p, _ in sel])
     xs, _ = batch.solve([y for _, y in sel])
     for k, x in enumerate(xs):

@@ -1,7 +1,9 @@
 """The bounds-checked build (libmisr_check.so, compiled with MISR_BOUNDS_CHECK) on the odd
 geometries: every tile shape, the streaming shape (its item split included) and both storage
 types, ragged and one-pixel images, frame counts below f^2, f = 1, 3 and 4, the gradient and a
-mixed batch.  No shared-memory item position, global
+mixed batch; and the frame-wise pass on frame sets it alone runs (several frames per phase, far
+and off-lattice shifts, binning, its three tap widths), whose adjoint gathers' tap indices and
+tile slots of sums are checked too.  No shared-memory item position, global
 store, tile or group index or TMA x coordinate may fail its check, and the images must equal
 the normal build's bit for bit (the checks change nothing when they pass).  compute-sanitizer
 is closed on this machine; this build stands in for it."""
