@@ -594,18 +594,19 @@ def serving_record(n, slots, tick):
     (continuous batching on the device); plain = one misr_solve at a time in arrival order.
     Then an open-loop overload run (all requests at once) for the peak served rate."""
     import torch
-    from paper_2108_04315_b300.binding import MISR_U16, Server
+    from paper_2108_04315_b300.binding import MISR_U16, Server, make_desc
     device = torch.device("cuda", torch.cuda.current_device())
     scans = _serving_inputs(device, n_pool=4)
     names = ["A" if i % 2 == 0 else "B" for i in range(n)]
     xs = [torch.empty((scans[k]["plan"].H, scans[k]["plan"].W), dtype=torch.float32, device=device) for k in names]
     ys = [scans[k]["pool"][(i // 2) % len(scans[k]["pool"])] for i, k in enumerate(names)]
     srv = Server(max_slots=slots, passes_per_tick=tick)
+    # one descriptor per scan, made once (as the plain arm's plans are)
+    descs = {k: make_desc(sc["h"], sc["w"], sc["f"], sc["shifts"], sc["psf"], lam=0.01, iters=SERVE_ITERS,
+                          in_dtype=MISR_U16, flat_field=FLAT_FIELD) for k, sc in scans.items()}
 
     def submit(i):
-        sc = scans[names[i]]
-        return srv.submit(ys[i], sc["h"], sc["w"], sc["f"], sc["shifts"], sc["psf"], x_out=xs[i], lam=0.01,
-                          iters=SERVE_ITERS, in_dtype=MISR_U16, flat_field=FLAT_FIELD)
+        return srv.submit_desc(ys[i], descs[names[i]], xs[i])
 
     # warm-up: one untimed burst of every request, so that the server's slot pool (a plan per
     # slot, kept between requests as a running server keeps it) exists before the timed runs;

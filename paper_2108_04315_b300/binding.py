@@ -502,12 +502,19 @@ class Server:
             pass
 
     def submit(self, y, lr_h, lr_w, factor, shifts, psf, x_out=None, **kw):
+        return self.submit_desc(y, make_desc(lr_h, lr_w, factor, shifts, psf, **kw), x_out)
+
+    def submit_desc(self, y, desc, x_out=None):
+        """submit with a descriptor made once by make_desc (an acquisition loop's scan class):
+        no per-request marshalling of the shifts, the PSF and the options."""
         import torch
-        desc = make_desc(lr_h, lr_w, factor, shifts, psf, **kw)
         if x_out is None:
-            x_out = torch.empty((factor * lr_h, factor * lr_w), dtype=torch.float32, device=y.device)
+            x_out = torch.empty((desc.factor * desc.lr_h, desc.factor * desc.lr_w), dtype=torch.float32,
+                                device=y.device)
         # work queued on the caller's stream (e.g. the frames' upload) must be done first
-        torch.cuda.current_stream(y.device).synchronize()
+        stream = torch.cuda.current_stream(y.device)
+        if not stream.query():
+            stream.synchronize()
         t = misr_submit(self.handle, desc, Plan._ptr(y), Plan._ptr(x_out, torch.float32))
         self._live[t] = (y, x_out)
         return t

@@ -99,6 +99,7 @@ struct Slot {
     int2 *items = nullptr;  // device tile and group lists of this slot alone (for its init pass)
     int n_list = 0;         // tiles in that list (the groups follow)
     PassSegs segs;
+    bool fork = true;       // its own stream must wait for the server stream (its admission) first
 };
 
 // device bytes of one slot: its plan's workspace (the layout misr_plan_create allocates) plus
@@ -134,6 +135,10 @@ struct misr_server_s {
     // page-locked states, one per slot, for two ticks: the worker queues tick t + 1 before it
     // reads tick t's states, so that the GPU does not wait for the host between ticks
     ScgState *st_host = nullptr;    // [2][cfg.max_slots]
+    // device copies of the states of slots on their own streams, taken on those streams after
+    // each tick's last pass: the next tick's passes then follow on the slot's stream at once,
+    // without waiting for the state's copy to the host on the server stream
+    ScgState *st_snap = nullptr;    // [2][cfg.max_slots]
     cudaEvent_t tick_done[2] = {nullptr, nullptr};
     cudaStream_t fin_stream = nullptr;   // copies of finished images, beside the next tick
     std::vector<int2> h_items;
@@ -142,9 +147,9 @@ struct misr_server_s {
     misr_status worker_error = MISR_OK;
     uint64_t passes_launched = 0;
     // Slots whose problem runs in launches of its own (launch_alone) take their SCG passes on a
-    // stream per slot index, forked from `stream` after the tick's admissions and joined back
-    // before its states are read: independent problems' launches then overlap, the next one
-    // filling the SMs the last items of the previous one leave idle.  Created on first use.
+    // stream per slot index, forked from `stream` after the slot's admission and joined back
+    // before each tick's states are read: independent problems' launches then overlap, the next
+    // one filling the SMs the last items of the previous one leave idle.  Created on first use.
     std::vector<cudaStream_t> slot_streams;   // [cfg.max_slots]
     std::vector<cudaEvent_t> slot_joins;      // [cfg.max_slots]
     cudaEvent_t fork = nullptr;
@@ -302,6 +307,7 @@ std::vector<int> admit(misr_server_t s) {
         sl.ticket = rq.ticket;
         sl.passes = 0;
         sl.queued = 0;
+        sl.fork = true;
         rq.state = RQ_RUNNING;
         rq.slot = use;
         rq.t_start = now_s();
@@ -501,10 +507,18 @@ void worker_main(misr_server_t s) {
                         cudaEventCreateWithFlags(&s->slot_joins[i], cudaEventDisableTiming) != cudaSuccess)
                         r = fail(MISR_ECUDA, "slot event failed");
                 }
-                if (r == MISR_OK && cudaEventRecord(s->fork, s->stream) != cudaSuccess) r = fail(MISR_ECUDA, "fork failed");
+                // a slot admitted since its last tick waits for its prepare and initial pass on
+                // the server stream; the others' streams are already ordered behind those
+                bool any_fork = false;
+                for (int i : own) any_fork |= s->slots[i].fork;
+                if (r == MISR_OK && any_fork && cudaEventRecord(s->fork, s->stream) != cudaSuccess)
+                    r = fail(MISR_ECUDA, "fork failed");
                 for (int i : own)
-                    if (r == MISR_OK && cudaStreamWaitEvent(s->slot_streams[i], s->fork, 0) != cudaSuccess)
-                        r = fail(MISR_ECUDA, "fork wait failed");
+                    if (r == MISR_OK && s->slots[i].fork) {
+                        if (cudaStreamWaitEvent(s->slot_streams[i], s->fork, 0) != cudaSuccess)
+                            r = fail(MISR_ECUDA, "fork wait failed");
+                        s->slots[i].fork = false;
+                    }
             }
             for (int it = 0; it < k_passes && r == MISR_OK; ++it) {
                 if (s->live_segs.total() > 0) {
@@ -519,7 +533,11 @@ void worker_main(misr_server_t s) {
                     ++s->passes_launched;
                 }
             }
-            for (int i : own) {   // join before the states are read
+            for (int i : own) {   // the state as this tick left it, then join before it is read
+                if (r == MISR_OK && cudaMemcpyAsync(s->st_snap + (size_t)buf * s->cfg.max_slots + i,
+                                                    s->slots[i].plan->hp.st, sizeof(ScgState),
+                                                    cudaMemcpyDeviceToDevice, s->slot_streams[i]) != cudaSuccess)
+                    r = fail(MISR_ECUDA, "state snapshot failed");
                 if (r == MISR_OK && cudaEventRecord(s->slot_joins[i], s->slot_streams[i]) != cudaSuccess)
                     r = fail(MISR_ECUDA, "join failed");
                 if (r == MISR_OK && cudaStreamWaitEvent(s->stream, s->slot_joins[i], 0) != cudaSuccess)
@@ -536,7 +554,10 @@ void worker_main(misr_server_t s) {
                 const int i = ran[q];
                 Slot &sl = s->slots[i];
                 if (r != MISR_OK || !sl.busy) continue;
-                if (cudaMemcpyAsync(&sth[i], sl.plan->hp.st, sizeof(ScgState), cudaMemcpyDeviceToHost, s->stream) !=
+                // own slots' states from their snapshots (their streams may run on into the next
+                // tick); the others' (and observed slots', with no pass in flight) directly
+                const ScgState *src = q < own.size() ? s->st_snap + (size_t)buf * s->cfg.max_slots + i : sl.plan->hp.st;
+                if (cudaMemcpyAsync(&sth[i], src, sizeof(ScgState), cudaMemcpyDeviceToHost, s->stream) !=
                     cudaSuccess)
                     r = fail(MISR_ECUDA, "state copy failed");
                 tk.live.push_back({i, sl.ticket});
@@ -599,6 +620,7 @@ extern "C" misr_status misr_server_create(const misr_server_cfg *cfg, misr_serve
     if (e == cudaSuccess) e = cudaMalloc(&s->work, 256);
     if (e == cudaSuccess) e = cudaMemset(s->work, 0, 256);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->st_host, 2 * sizeof(ScgState) * cfg->max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->st_snap, 2 * sizeof(ScgState) * cfg->max_slots);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->fin_stream, cudaStreamNonBlocking);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->tick_done[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -608,6 +630,7 @@ extern "C" misr_status misr_server_create(const misr_server_cfg *cfg, misr_serve
             if (ev) cudaEventDestroy(ev);
         if (s->fin_stream) cudaStreamDestroy(s->fin_stream);
         if (s->st_host) cudaFreeHost(s->st_host);
+        if (s->st_snap) cudaFree(s->st_snap);
         if (s->stream) cudaStreamDestroy(s->stream);
         if (s->dprobs) cudaFree(s->dprobs);
         if (s->work) cudaFree(s->work);
@@ -648,6 +671,7 @@ extern "C" misr_status misr_server_destroy(misr_server_t s) {
     if (s->dprobs) cudaFree(s->dprobs);
     if (s->work) cudaFree(s->work);
     if (s->st_host) cudaFreeHost(s->st_host);
+    if (s->st_snap) cudaFree(s->st_snap);
     for (auto &ev : s->tick_done)
         if (ev) cudaEventDestroy(ev);
     cudaStreamSynchronize(s->fin_stream);

@@ -35,12 +35,17 @@ def test_serving_mix_equals_alone_and_oracle(orc):
         x, st = plan.solve(yd)
         alone.append((x.clone(), st))
     srv = B.Server(max_slots=8, passes_per_tick=3)
-    # a stream of requests over three geometry classes, arriving while earlier ones run
+    # a stream of requests over three geometry classes, arriving while earlier ones run; every
+    # other one submitted with its class's descriptor made once (submit_desc)
+    descs = [B.make_desc(h, w, f, sh, PSF, iters=it) for h, w, f, sh, it in GEOMS]
     order = [0, 1, 2, 0, 0, 2, 1, 0, 2]
     tickets = []
     for n, i in enumerate(order):
         h, w, f, sh, it = GEOMS[i]
-        tickets.append((i, srv.submit(ys[i], h, w, f, sh, PSF, iters=it)))
+        if n % 2:
+            tickets.append((i, srv.submit_desc(ys[i], descs[i])))
+        else:
+            tickets.append((i, srv.submit(ys[i], h, w, f, sh, PSF, iters=it)))
         if n % 3 == 2:
             time.sleep(0.002)
     for i, t in tickets:
