@@ -1118,6 +1118,7 @@ misr_status misr_plan_destroy(misr_plan_t p) {
     DeviceGuard g(p->device);
     cudaDeviceSynchronize();
     if (p->chunk) cudaGraphExecDestroy(p->chunk);
+    if (p->tail) cudaGraphExecDestroy(p->tail);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->done_ev) cudaEventDestroy(p->done_ev);
     if (p->st_host) cudaFreeHost(p->st_host);
@@ -1261,21 +1262,52 @@ misr_status misr_gradient(misr_plan_t p, const void *y_dev, const float *x_dev, 
     return MISR_OK;
 }
 
-static misr_status ensure_graph(misr_plan_t p) {
-    const int want = std::max(1, std::min(p->d.iters, GRAPH_CHUNK));
-    if (p->chunk && p->chunk_len == want) return MISR_OK;
-    if (p->chunk) { cudaGraphExecDestroy(p->chunk); p->chunk = nullptr; }
+// `len` SCG passes of the plan, captured on its private stream
+static misr_status capture_passes(misr_plan_t p, int len, cudaGraphExec_t *exec) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
     misr_status r = MISR_OK;
-    for (int i = 0; i < want && r == MISR_OK; ++i) r = launch_pass(p, MODE_ITER, 0.0, 0.0, p->cap);
+    for (int i = 0; i < len && r == MISR_OK; ++i) r = launch_pass(p, MODE_ITER, 0.0, 0.0, p->cap);
     cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
     if (r != MISR_OK) { if (graph) cudaGraphDestroy(graph); return r; }
     if (e != cudaSuccess) return fail(MISR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&p->chunk, graph, 0);
+    e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(MISR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return MISR_OK;
+}
+
+// The plan's graphs: a chunk of GRAPH_CHUNK passes and the remainder of its iteration count, so
+// that a solve launches exactly that many passes (none that would only find it done)
+static misr_status ensure_graph(misr_plan_t p) {
+    const int want = std::max(1, std::min(p->d.iters, GRAPH_CHUNK));
+    const int tail = std::max(p->d.iters, 0) % want;
+    if (p->chunk && p->chunk_len == want && p->tail_len == tail) return MISR_OK;
+    if (p->chunk) { cudaGraphExecDestroy(p->chunk); p->chunk = nullptr; }
+    if (p->tail) { cudaGraphExecDestroy(p->tail); p->tail = nullptr; }
+    p->chunk_len = p->tail_len = 0;
+    misr_status r = capture_passes(p, want, &p->chunk);
+    if (r != MISR_OK) return r;
+    if (tail > 0) r = capture_passes(p, tail, &p->tail);
+    if (r != MISR_OK) { cudaGraphExecDestroy(p->chunk); p->chunk = nullptr; return r; }
     p->chunk_len = want;
+    p->tail_len = tail;
+    return MISR_OK;
+}
+
+// n SCG passes: whole chunks, then the tail graph when it is the rest, else single launches
+static misr_status launch_iters(misr_plan_t p, int n, cudaStream_t s) {
+    int done = 0;
+    for (; done + p->chunk_len <= n; done += p->chunk_len) CK(cudaGraphLaunch(p->chunk, s));
+    const int rest = n - done;
+    if (rest > 0 && rest == p->tail_len) {
+        CK(cudaGraphLaunch(p->tail, s));
+        return MISR_OK;
+    }
+    for (int i = 0; i < rest; ++i) {
+        const misr_status r = launch_pass(p, MODE_ITER, 0.0, 0.0, s);
+        if (r != MISR_OK) return r;
+    }
     return MISR_OK;
 }
 
@@ -1305,7 +1337,8 @@ misr_status misr_solve(misr_plan_t p, const void *y_dev, float *x_dev, misr_stre
     if (r != MISR_OK) return r;
     r = launch_pass(p, MODE_INIT, 0.0, 0.0, s);
     if (r != MISR_OK) return r;
-    for (int done = 0; done < p->d.iters; done += p->chunk_len) CK(cudaGraphLaunch(p->chunk, s));
+    r = launch_iters(p, std::max(p->d.iters, 0), s);
+    if (r != MISR_OK) return r;
     finalize_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->dprob, 0, x_dev);
     CK(cudaGetLastError());
     CK(cudaEventRecord(p->done_ev, s));
@@ -1581,7 +1614,8 @@ misr_status misr_resume(misr_plan_t p, const void *y_dev, float *x_dev, misr_str
     r = launch_prepare_raw(p->dprob, 0, p->hp, p->d, y_dev, nullptr, MISR_X0_ZERO, 0, s);
     if (r != MISR_OK) return r;
     const int remaining = st.done ? 0 : std::max(st.iters - st.iter, 0);
-    for (int done = 0; done < remaining; done += p->chunk_len) CK(cudaGraphLaunch(p->chunk, s));
+    r = launch_iters(p, remaining, s);
+    if (r != MISR_OK) return r;
     finalize_kernel<<<grid_for(p->n, 256), 256, 0, s>>>(p->dprob, 0, x_dev);
     CK(cudaGetLastError());
     CK(cudaEventRecord(p->done_ev, s));

@@ -36,8 +36,10 @@ struct misr_batch_s {
     std::vector<cudaEvent_t> own_joins;
     cudaEvent_t fork = nullptr;
     cudaStream_t cap = nullptr;     // private stream used for graph capture
-    cudaGraphExec_t chunk = nullptr;
+    cudaGraphExec_t chunk = nullptr;    // GRAPH_CHUNK steps (or max_iters, if fewer)
     int chunk_len = 0;
+    cudaGraphExec_t tail = nullptr;     // the remainder of max_iters after whole chunks
+    int tail_len = 0;
     ScgState *st_host = nullptr;    // n page-locked states
 };
 
@@ -48,6 +50,7 @@ extern "C" misr_status misr_batch_destroy(misr_batch_t b) {
     DeviceGuard g(b->device);
     cudaDeviceSynchronize();
     if (b->chunk) cudaGraphExecDestroy(b->chunk);
+    if (b->tail) cudaGraphExecDestroy(b->tail);
     for (cudaStream_t st : b->own_streams)
         if (st) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->own_joins)
@@ -154,21 +157,35 @@ static misr_status batch_step(misr_batch_t b, int mode, cudaStream_t s) {
     return r;
 }
 
-static misr_status batch_graph(misr_batch_t b) {
-    const int want = std::max(1, std::min(b->max_iters, GRAPH_CHUNK));
-    if (b->chunk && b->chunk_len == want) return MISR_OK;
-    if (b->chunk) { cudaGraphExecDestroy(b->chunk); b->chunk = nullptr; }
+// `len` SCG steps of the batch, captured on its private stream
+static misr_status capture_steps(misr_batch_t b, int len, cudaGraphExec_t *exec) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     misr_status r = MISR_OK;
-    for (int i = 0; i < want && r == MISR_OK; ++i) r = batch_step(b, MODE_ITER, b->cap);
+    for (int i = 0; i < len && r == MISR_OK; ++i) r = batch_step(b, MODE_ITER, b->cap);
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (r != MISR_OK) { if (graph) cudaGraphDestroy(graph); return r; }
     if (e != cudaSuccess) return fail(MISR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&b->chunk, graph, 0);
+    e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(MISR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return MISR_OK;
+}
+
+// a chunk of GRAPH_CHUNK steps and the remainder of max_iters: a solve launches max_iters steps
+static misr_status batch_graph(misr_batch_t b) {
+    const int want = std::max(1, std::min(b->max_iters, GRAPH_CHUNK));
+    const int tail = std::max(b->max_iters, 0) % want;
+    if (b->chunk && b->chunk_len == want && b->tail_len == tail) return MISR_OK;
+    if (b->chunk) { cudaGraphExecDestroy(b->chunk); b->chunk = nullptr; }
+    if (b->tail) { cudaGraphExecDestroy(b->tail); b->tail = nullptr; }
+    b->chunk_len = b->tail_len = 0;
+    misr_status r = capture_steps(b, want, &b->chunk);
+    if (r != MISR_OK) return r;
+    if (tail > 0) r = capture_steps(b, tail, &b->tail);
+    if (r != MISR_OK) { cudaGraphExecDestroy(b->chunk); b->chunk = nullptr; return r; }
     b->chunk_len = want;
+    b->tail_len = tail;
     return MISR_OK;
 }
 
@@ -187,7 +204,8 @@ extern "C" misr_status misr_batch_solve(misr_batch_t b, const void *const *y_dev
     }
     if (r == MISR_OK) r = batch_step(b, MODE_INIT, s);
     if (r != MISR_OK) return r;
-    for (int done = 0; done < b->max_iters; done += b->chunk_len) CK(cudaGraphLaunch(b->chunk, s));
+    for (int done = 0; done + b->chunk_len <= b->max_iters; done += b->chunk_len) CK(cudaGraphLaunch(b->chunk, s));
+    if (b->tail) CK(cudaGraphLaunch(b->tail, s));
     for (int i = 0; i < b->n && r == MISR_OK; ++i) r = launch_finalize_raw(b->dprobs, i, b->plans[i]->n, x_dev[i], s);
     if (r != MISR_OK) return r;
     for (int i = 0; i < b->n; ++i) {

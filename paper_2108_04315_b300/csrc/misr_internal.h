@@ -121,8 +121,10 @@ struct misr_plan_s {
     size_t n = 0, m_total = 0;          // HR pixels, LR samples of all frames
     size_t n_pitched = 0;               // H * pitch
     cudaStream_t cap = nullptr;         // private stream used for graph capture
-    cudaGraphExec_t chunk = nullptr;
+    cudaGraphExec_t chunk = nullptr;    // GRAPH_CHUNK passes (or the iteration count, if fewer)
     int chunk_len = 0;
+    cudaGraphExec_t tail = nullptr;     // the iteration count's remainder after whole chunks
+    int tail_len = 0;
     cudaEvent_t done_ev = nullptr;
     bool solved = false;
     misr::ScgState *st_host = nullptr;  // page-locked copy of the state
