@@ -329,9 +329,12 @@ misr_status misr_batch_solve(misr_batch_t batch, const void *const *y_dev, float
  * passes_per_tick fused-pass launches over the tiles of all live slots (one SCG iteration per
  * launch for each), so a request that arrives while others are on the GPU joins the next
  * launch; a slot whose projection fills the GPU on its own (or runs the frame-wise pass) takes
- * its passes on a stream of its own, forked from the worker's stream and joined back within
- * the tick, so that independent projections' launches overlap.  The worker queues a tick before it reads the states of the previous one, so the GPU
- * does not wait for the host between ticks.  Finished projections are copied out and their
+ * its passes on a stream of its own, which waits for the worker's stream once after the
+ * slot's admission and is joined back within each tick, so that independent projections'
+ * launches overlap; its state is copied on that stream after the tick's passes, and the
+ * worker reads that copy, so the slot's next tick runs on at once.  The worker queues a tick
+ * before it reads the states of the previous one, so the GPU does not wait for the host
+ * between ticks.  Finished projections are copied out and their
  * slots reused.  Each projection keeps its own state and fixed-order reductions: its result is
  * the same alone and in the mix.  A request's frames are read once, when it is admitted (into
  * the slot's workspace), and its output is written once, when it finishes. */
