@@ -557,6 +557,7 @@ SERVE_SCANS = {
 }
 SERVE_ITERS = 80
 SERVE_RATE = 30.0   # projections arriving per second (A and B alternate)
+SERVE_SPIN_US = 50000   # the served arm's worker polls this long for the next request once idle
 FLAT_FIELD = 40000.0
 
 
@@ -600,7 +601,7 @@ def serving_record(n, slots, tick):
     names = ["A" if i % 2 == 0 else "B" for i in range(n)]
     xs = [torch.empty((scans[k]["plan"].H, scans[k]["plan"].W), dtype=torch.float32, device=device) for k in names]
     ys = [scans[k]["pool"][(i // 2) % len(scans[k]["pool"])] for i, k in enumerate(names)]
-    srv = Server(max_slots=slots, passes_per_tick=tick)
+    srv = Server(max_slots=slots, passes_per_tick=tick, idle_spin_us=SERVE_SPIN_US)
     # one descriptor per scan, made once (as the plain arm's plans are)
     descs = {k: make_desc(sc["h"], sc["w"], sc["f"], sc["shifts"], sc["psf"], lam=0.01, iters=SERVE_ITERS,
                           in_dtype=MISR_U16, flat_field=FLAT_FIELD) for k, sc in scans.items()}
@@ -669,7 +670,7 @@ def serving_record(n, slots, tick):
            "config": {"workload": "scan A: 4 x 1536x1920 u16 counts, f=2, half-pixel shifts; scan B: 9 x 768x960 u16 "
                                   "counts, f=3, third-pixel shifts; I0 40000, lambda 0.01, 80 SCG iterations; one "
                                   f"projection every {1 / SERVE_RATE:.4f} s alternating A/B; {n} projections",
-                      "max_slots": slots, "passes_per_tick": tick,
+                      "max_slots": slots, "passes_per_tick": tick, "idle_spin_us": SERVE_SPIN_US,
                       "inputs": "resident in HBM (frames > L2 per projection)",
                       "warmup": "one untimed burst of all requests (the slot pool is made), 2 plain solves"},
            "api": "misr_submit at arrival, misr_wait",

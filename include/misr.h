@@ -345,6 +345,12 @@ typedef struct misr_server_cfg {
     int32_t passes_per_tick;     /* SCG iterations between admission rounds, 0 = 4 */
     uint64_t hbm_budget_bytes;   /* > 0: slot workspaces use at most this many bytes */
     uint64_t hbm_reserve_bytes;  /* budget 0: admit while free device memory exceeds this */
+    int32_t idle_spin_us;        /* once nothing is queued or running, the worker polls for new
+                                    requests this many microseconds (0..1000000) before it
+                                    sleeps: a request arriving meanwhile starts without a
+                                    thread wake-up, at the cost of one busy CPU core; 0 = sleep
+                                    at once */
+    int32_t reserved;            /* 0 */
 } misr_server_cfg;
 
 /* Start a server on the current device.  Errors: MISR_EINVAL, MISR_ENOMEM. */

@@ -49,7 +49,8 @@ class misr_stats(C.Structure):
 
 class misr_server_cfg(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("passes_per_tick", C.c_int32),
-                ("hbm_budget_bytes", C.c_uint64), ("hbm_reserve_bytes", C.c_uint64)]
+                ("hbm_budget_bytes", C.c_uint64), ("hbm_reserve_bytes", C.c_uint64),
+                ("idle_spin_us", C.c_int32), ("reserved", C.c_int32)]
 
 
 class MisrError(RuntimeError):
@@ -273,8 +274,9 @@ def misr_batch_solve(batch: int, y_devs, x_devs, stream: int = 0, want_stats: bo
 
 
 def misr_server_create(max_slots: int, passes_per_tick: int = 0, hbm_budget_bytes: int = 0,
-                       hbm_reserve_bytes: int = 0) -> int:
-    cfg = misr_server_cfg(int(max_slots), int(passes_per_tick), int(hbm_budget_bytes), int(hbm_reserve_bytes))
+                       hbm_reserve_bytes: int = 0, idle_spin_us: int = 0) -> int:
+    cfg = misr_server_cfg(int(max_slots), int(passes_per_tick), int(hbm_budget_bytes), int(hbm_reserve_bytes),
+                          int(idle_spin_us), 0)
     h = VP()
     _check(lib().misr_server_create(C.byref(cfg), C.byref(h)), "misr_server_create")
     return h.value
@@ -485,8 +487,9 @@ class Server:
     """Continuous-batching solver: submit projections as they arrive, poll or wait for results.
     Frames and outputs are CUDA tensors that must stay alive until their ticket finishes."""
 
-    def __init__(self, max_slots=64, passes_per_tick=0, hbm_budget_bytes=0, hbm_reserve_bytes=0):
-        self.handle = misr_server_create(max_slots, passes_per_tick, hbm_budget_bytes, hbm_reserve_bytes)
+    def __init__(self, max_slots=64, passes_per_tick=0, hbm_budget_bytes=0, hbm_reserve_bytes=0, idle_spin_us=0):
+        self.handle = misr_server_create(max_slots, passes_per_tick, hbm_budget_bytes, hbm_reserve_bytes,
+                                         idle_spin_us)
         self._live = {}
 
     def close(self):

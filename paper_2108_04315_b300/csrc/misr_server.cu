@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -119,6 +120,7 @@ struct misr_server_s {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
+    std::atomic<uint64_t> wakes{0};   // submits and the stop: what an idle worker's poll watches
     uint64_t next_ticket = 1;
     std::deque<uint64_t> queue;
     std::unordered_map<uint64_t, Request> reqs;
@@ -156,6 +158,15 @@ struct misr_server_s {
 };
 
 namespace {
+
+// a short wait inside a polling loop
+inline void cpu_relax() {
+#if defined(__x86_64__) || defined(__i386__)
+    for (int k = 0; k < 64; ++k) __builtin_ia32_pause();
+#else
+    std::this_thread::yield();
+#endif
+}
 
 misr_status grow_items(misr_server_t s, size_t need) {
     if (need <= s->ditems_cap) return MISR_OK;
@@ -419,6 +430,20 @@ void worker_main(misr_server_t s) {
     int buf = 0;
     for (;;) {
         if (!have_pending) {
+            // idle: poll for a new request for idle_spin_us (no wake-up when one comes), then sleep
+            bool idle = true;
+            for (auto &sl : s->slots) idle &= !sl.busy;
+            if (idle && s->cfg.idle_spin_us > 0) {
+                const uint64_t w0 = s->wakes.load(std::memory_order_acquire);
+                bool seen = false;
+                {
+                    std::lock_guard<std::mutex> lock(s->mu);
+                    seen = s->stop || !s->queue.empty();
+                }
+                const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(s->cfg.idle_spin_us);
+                while (!seen && s->wakes.load(std::memory_order_acquire) == w0 && std::chrono::steady_clock::now() < until)
+                    cpu_relax();
+            }
             std::unique_lock<std::mutex> lock(s->mu);
             s->cv_work.wait(lock, [&] {
                 if (s->stop || !s->queue.empty()) return true;
@@ -610,6 +635,7 @@ extern "C" misr_status misr_server_create(const misr_server_cfg *cfg, misr_serve
     *out = nullptr;
     if (cfg->max_slots < 1 || cfg->max_slots > 4096) return fail(MISR_EINVAL, "max_slots must be in [1, 4096]");
     if (cfg->passes_per_tick < 0 || cfg->passes_per_tick > 1000) return fail(MISR_EINVAL, "passes_per_tick must be in [0, 1000]");
+    if (cfg->idle_spin_us < 0 || cfg->idle_spin_us > 1000000) return fail(MISR_EINVAL, "idle_spin_us must be in [0, 1e6]");
     misr_server_t s = new (std::nothrow) misr_server_s();
     if (!s) return fail(MISR_ENOMEM, "host allocation failed");
     s->cfg = *cfg;
@@ -651,6 +677,7 @@ extern "C" misr_status misr_server_destroy(misr_server_t s) {
         std::lock_guard<std::mutex> lock(s->mu);
         s->stop = true;
     }
+    s->wakes.fetch_add(1, std::memory_order_release);
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     DeviceGuard g(s->device);
@@ -697,6 +724,7 @@ extern "C" misr_status misr_submit(misr_server_t s, const misr_desc *desc, const
     rq.t_submit = now_s();
     s->queue.push_back(t);
     *ticket = t;
+    s->wakes.fetch_add(1, std::memory_order_release);
     s->cv_work.notify_all();
     return MISR_OK;
 }

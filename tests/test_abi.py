@@ -104,6 +104,17 @@ def test_null_arguments_rejected(L):
     assert L.misr_plan_destroy(None) == binding.MISR_OK
 
 
+@pytest.mark.parametrize("cfg", [(0, 0, 0), (4097, 0, 0), (4, -1, 0), (4, 1001, 0), (4, 0, -1), (4, 0, 1000001)])
+def test_server_config_rejected_on_host(L, cfg):
+    """misr_server_create checks its configuration before it touches the device"""
+    from paper_2108_04315_b300 import binding
+    slots, tick, spin = cfg
+    c = binding.misr_server_cfg(slots, tick, 0, 0, spin, 0)
+    h = C.c_void_p()
+    assert L.misr_server_create(C.byref(c), C.byref(h)) == binding.MISR_EINVAL
+    assert h.value is None
+
+
 @pytest.mark.parametrize("kw", [
     dict(shifts=[(0.0, 0.0)] * 5),                                # K > f^2
     dict(shifts=[(0.0, 0.0), (0.0, 0.0)]),                        # same phase twice

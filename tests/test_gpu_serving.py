@@ -237,3 +237,28 @@ def test_serving_streaming_shape_equals_alone(orc):
         check(i, t)
     check(4, submit(4))                                   # alone again, a warm slot
     srv.close()
+
+
+def test_serving_idle_poll_equals_alone_and_stops(orc):
+    """A worker that polls for requests when idle (idle_spin_us): results equal the projection's
+    own solve, whether a request comes while it polls or after it has gone to sleep, and the
+    server stops at once while it polls."""
+    from paper_2108_04315_b300 import binding as B
+    (P, plan, xt, y) = _cases(orc)[1]
+    yd = to_dev(y)
+    h, w, f, sh, it = GEOMS[1]
+    x_alone, st_alone = plan.solve(yd)
+    srv = B.Server(max_slots=2, passes_per_tick=2, idle_spin_us=300000)
+    desc = B.make_desc(h, w, f, sh, PSF, iters=it)
+    for pause in (0.0, 0.02, 0.5):   # during the poll, during it, after it
+        time.sleep(pause)
+        x, st, times = srv.wait(srv.submit_desc(yd, desc), timeout_s=60.0)
+        assert torch.equal(x, x_alone) and st == st_alone
+    srv.submit_desc(yd, desc)
+    time.sleep(0.05)
+    t0 = time.monotonic()
+    srv.close()
+    assert time.monotonic() - t0 < 0.25
+    with pytest.raises(B.MisrError) as e:
+        B.Server(max_slots=2, idle_spin_us=-1)
+    assert e.value.status == B.MISR_EINVAL
